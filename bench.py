@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the VBGS CAVI update on a continual RGB-D stream.
+
+Workload: a procedural textured box room seen from random camera poses,
+200 x 200 RGB-D frames lifted to <= 40,000 joint (xyz, rgb) points each, fed
+one frame per step into K = 50,000 components with 3 CAVI iterations per
+frame (Alg. 1 `fit`, continual and replay-free).  One step = one frame =
+vbgs_update (E-step passes, fused statistics contraction, FP64 posterior
+update, ELBO) through the C ABI.
+
+Metric: point-component CAVI updates per second = sum_t N_t * K * iters /
+device time.  `value` times device-resident inputs with CUDA events (L2
+flushed between steps, outside the timed events); `e2e` times the same call
+with pinned host inputs (host->device copy and ELBO read-back inside).
+
+--impl reference times the FP64 CPU oracle on bounded samples of the same
+workload (the reference arm of this repository: there is no reference code
+to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "point·component CAVI updates/s vs plain FP64 GPU form; ELBO rel. err vs FP64"
+UNIT = "updates/s"
+K_COMP = 50_000
+ITERS = 3
+WORKLOAD = ("continual RGB-D room stream: 200x200 frames (<=40,000 lifted points, depth 0.5-5 m), "
+            "K=50,000 NW/Dirichlet components, 3 CAVI iterations per frame, no replay")
+DTYPES = {"fp64": "f64", "fp32": "f32", "fp16x3": "f16x3 (fp32 acc)", "bf16x3": "bf16x3 (fp32 acc)"}
+
+# Peaks for the ALU rooflines, derived from unit counts and the maximum SM
+# clock (152 SMs, 2070 MHz): FP32 128 lanes/SM/clk x 2 flops; MUFU ex2
+# 16/SM/clk.  FP64: the nominal GB300 rate (1.25 TFLOP/s).
+SMS, SM_MHZ = 152, 2070.0
+PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12
+PEAK_FP64_TFLOPS = 1.25
+PEAK_EX2_G = SMS * 16 * SM_MHZ * 1e6 / 1e9
+
+# Algorithmic work per (point, component) pair of each pass:
+# factored logit c - 1/2 |M (x - m)|^2 = 6 sub + 21 FMA + 6 FMA + 1 FMA = 62 flops;
+# pass 1 adds the online max/sum (2 flops) and one exp; pass 2 adds the
+# subtraction of lse (1 flop), one exp and 28 FMAs into the statistics (56).
+FLOPS_PASS1 = 64
+FLOPS_PASS2 = 119
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, lrank
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = Path(os.environ.get("TMPDIR", "/tmp")) / f"vbgs_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.path.read_text().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        try:
+            self.path.unlink()
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_frames(n: int, seed: int = 2):
+    from paper_2603_08499_gb300 import synth
+    room = synth.Room(seed)
+    return [synth.room_frame(t, seed=seed, room=room) for t in range(n)]
+
+
+def cpu_oracle_rate(frames, prior, iters: int, budget_s: float, S_past=None):
+    """Time the FP64 oracle on a bounded sample: the first n points of each
+    frame, n calibrated so that the sample takes about budget_s seconds."""
+    from oracle import oracle as O
+    K = prior["m0"].shape[0]
+    S = np.zeros((K, 28)) if S_past is None else S_past
+    probe = frames[0][:64]
+    t0 = time.perf_counter()
+    O.cavi_frame(probe, prior, S, 1)
+    rate = 64 * K / max(time.perf_counter() - t0, 1e-6)
+    n = int(max(64, min(frames[0].shape[0], budget_s * rate / (K * iters * max(1, len(frames))))))
+    pairs, secs = 0, 0.0
+    for X in frames:
+        Xs = X[:n]
+        t0 = time.perf_counter()
+        _, S, _, _ = O.cavi_frame(Xs, prior, S, iters)
+        secs += time.perf_counter() - t0
+        pairs += Xs.shape[0] * K * iters
+    return pairs / secs, {"points_per_frame": n, "frames": len(frames), "K": K, "iters": iters,
+                          "seconds": round(secs, 3), "cores": O.num_threads()}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    from paper_2603_08499_gb300 import synth
+    prior = synth.room_prior(K_COMP, seed=2)
+    frames = make_frames(args.warmup + args.steps)
+    per_step = max(3.0, 90.0 / max(1, args.warmup + args.steps))
+    from oracle import oracle as O
+    O.build()
+    _, _ = cpu_oracle_rate(frames[:args.warmup], prior, ITERS, per_step * max(1, args.warmup))
+    val, info = cpu_oracle_rate(frames[args.warmup:], prior, ITERS, per_step * args.steps)
+    sample = (f"first {info['points_per_frame']} points of each of {info['frames']} room frames, "
+              f"K={K_COMP}, {ITERS} CAVI iterations each, FP64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": info["seconds"] * 1e3 / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "K": K_COMP, "iters": ITERS},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def timed_stream(V, prior, dev_frames, form, warmup, steps, stream, flush, profile=False, host_frames=None):
+    """Run warmup + steps frames through a fresh model; per-step device times
+    with CUDA events (or host wall time for host inputs)."""
+    import torch
+    m = V.Model(prior, form, cuda_stream=stream.cuda_stream)
+    traces, times, launches = [], [], 0
+    pairs = 0
+    for t in range(warmup + steps):
+        timed = t >= warmup
+        if timed and profile and t == warmup:
+            m.profile(True)
+            m.profile_read(reset=True)
+        flush.zero_()
+        X = dev_frames[t] if host_frames is None else host_frames[t]
+        if host_frames is None:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            tr = m.update(X, ITERS)
+            e1.record(stream)
+            e1.synchronize()
+            dt = e0.elapsed_time(e1) * 1e-3
+        else:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tr = m.update(X, ITERS)     # H2D inside, ELBO trace read back (the call synchronises)
+            dt = time.perf_counter() - t0
+        if timed:
+            times.append(dt)
+            traces.append(tr)
+            launches += m.launches()
+            pairs += X.shape[0] * K_COMP * ITERS
+    prof = m.profile_read() if profile else None
+    m.close()
+    return {"times": times, "traces": traces, "launches": launches, "pairs": pairs, "prof": prof}
+
+
+def roofline(form, prof, n_points_timed, steps):
+    """Roofline of the dominant kernel from the library's live event timing."""
+    if not prof:
+        return None
+    name = max(("pass1", "pass2"), key=lambda k: prof[k][0])
+    ms, n = prof[name]
+    if n == 0:
+        return None
+    pairs_per_launch = n_points_timed * K_COMP * ITERS / n
+    flops = (FLOPS_PASS1 if name == "pass1" else FLOPS_PASS2) * pairs_per_launch
+    avg_s = ms * 1e-3 / n
+    achieved = flops / avg_s / 1e12
+    peak = PEAK_FP64_TFLOPS if form == "fp64" else PEAK_FP32_TFLOPS
+    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "avg_launch_ms": ms / n, "launches": n,
+            "peak_source": ("nominal GB300 FP64 rate" if form == "fp64"
+                            else "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"),
+            "share_of_step": ms / max(1e-9, sum(v[0] for v in prof.values()))}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    ws, rank, lrank = dist_info()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+    torch.cuda.set_device(lrank)
+    import __graft_entry__ as G
+    G.build()
+    from paper_2603_08499_gb300 import synth, vbgs as V
+
+    form = args.form
+    prior = synth.room_prior(K_COMP, seed=2 + 17 * rank)
+    n_frames = args.warmup + args.steps
+    frames = make_frames(n_frames, seed=2 + 17 * rank)
+    dev = [torch.from_numpy(X).cuda() for X in frames]
+    host = [torch.from_numpy(X).pin_memory() for X in frames]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    peaks = V.vbgs_probe_peaks(lrank) if rank == 0 else None
+
+    clocks = ClockSampler(lrank)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    res = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, profile=True)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    dev_time = sum(res["times"])
+    if ws > 1:
+        t = torch.tensor([dev_time], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_time = float(t.item())
+        p = torch.tensor([res["pairs"]], device="cuda", dtype=torch.float64)
+        dist.all_reduce(p)
+        total_pairs = float(p.item())
+    else:
+        total_pairs = float(res["pairs"])
+    value = total_pairs / dev_time
+
+    # end to end through the same call with pinned host inputs
+    res_e2e = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, host_frames=host)
+    e2e_time = sum(res_e2e["times"])
+    if ws > 1:
+        t = torch.tensor([e2e_time], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_time = float(t.item())
+    e2e_value = total_pairs / e2e_time
+    timed_frames = frames[args.warmup:]
+    h2d = int(np.mean([X.shape[0] * 6 * 8 for X in timed_frames]))
+
+    extra = {}
+    if form != "fp64" and rank == 0:
+        ref = timed_stream(V, prior, dev, "fp64", args.warmup, args.steps, stream, flush)
+        fp64_value = ref["pairs"] / sum(ref["times"])
+        errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(res["traces"], ref["traces"])]
+        extra["fp64_form"] = {"value": fp64_value, "unit": UNIT, "speedup": value / fp64_value}
+        extra["elbo_relerr_vs_fp64"] = max(errs)
+
+    if rank == 0:
+        n_pts = sum(X.shape[0] for X in timed_frames)
+        rl = roofline(form, res["prof"], n_pts, args.steps)
+        cpu_val, cpu_info = (None, None)
+        if not args.no_cpu_baseline:
+            cpu_val, cpu_info = cpu_oracle_rate(timed_frames[:2], prior, ITERS, args.cpu_budget)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_time * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[form], "data": "synthetic",
+            "config": {"workload": WORKLOAD, "K": K_COMP, "iters": ITERS, "form": form,
+                       "mean_points_per_frame": n_pts / args.steps,
+                       "l2": "flushed between steps (256 MB write outside the timed events)",
+                       "parallelism": f"replicas x{ws} (independent streams)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": ITERS * 8 + 16},
+            "gpu_launches": res["launches"],
+            "roofline": rl,
+            "clocks": clk,
+            "probe_peaks": peaks,
+            "kernel_ms": {k: v[0] for k, v in (res["prof"] or {}).items()},
+        }
+        if cpu_val is not None:
+            line["cpu_baseline"] = {"value": cpu_val, "unit": UNIT, "cores": cpu_info["cores"], "kind": "oracle",
+                                    "sample": (f"first {cpu_info['points_per_frame']} points of 2 timed frames, "
+                                               f"K={K_COMP}, {ITERS} iterations each, FP64 oracle "
+                                               f"({cpu_info['seconds']} s)")}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=list(DTYPES), default="fp32")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warmup raised to 3")
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * vbgs.h -- C ABI of the GB300 (sm_103a) VBGS coordinate-ascent update.
+ *
+ * The library implements the data-parallel hot path of Variational Bayes
+ * Gaussian Splatting: the `fit` step of Algorithm 1 (Section 2.1.2) for a
+ * mixture of K components over joint D = 6 points x = (x, y, z, r, g, b),
+ * each component carrying a conjugate Normal-Wishart prior on its mean and
+ * precision and the mixture weights a Dirichlet prior (Fig. 3; the paper's
+ * NIW(m, kappa, V, n) in precision space: kappa = beta, V = W^-1, n = nu).
+ * One CAVI iteration is
+ *   - `compute_elbo_delta`: log rho_nk for every (point, component) pair,
+ *     the per-point log-sum-exp lse_n, responsibilities r_nk (Alg. 1);
+ *   - `sum_stats_over_samples` as the fused contraction Delta S = R^T S_u of
+ *     Eq. 3, with S_u = phi(x) = [1, x, upper(x x^T)]: no N x K (or larger)
+ *     array is ever stored;
+ *   - `update_from_statistics`: the closed-form FP64 posterior (Alg. 1);
+ *   - the ELBO  sum_n lse_n - sum_k KL(NW_k || NW0_k) - KL(Dir || Dir0).
+ *
+ * Conventions for every entry point:
+ *   - return VBGS_OK (0) on success, a negative VBGS_E* code on failure; the
+ *     message is available from vbgs_last_error(ctx) (or
+ *     vbgs_last_error(NULL) for failures before a context exists);
+ *   - the caller owns every pointer it passes; the context owns all device
+ *     memory it allocates and frees it in vbgs_destroy;
+ *   - point arrays are N x D row-major doubles and may live in host or
+ *     device memory (detected with cudaPointerGetAttributes); all other
+ *     array arguments are host memory;
+ *   - all device work is enqueued on the context's CUDA stream; calls that
+ *     return host outputs synchronise that stream before returning;
+ *   - a context is not thread-safe: one host thread at a time.
+ */
+#ifndef VBGS_H
+#define VBGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VBGS_OK        0
+#define VBGS_EINVAL   -1   /* bad argument: D != 6, K <= 0, N < 0, NULL, non-finite input */
+#define VBGS_ENOMEM   -2   /* device or host allocation failed */
+#define VBGS_ECUDA    -3   /* a CUDA runtime call failed */
+#define VBGS_ENUMERIC -4   /* a posterior W^-1 is not positive definite (component in message) */
+#define VBGS_ETIMEOUT -5   /* a bounded device-side wait gave up */
+
+/* Statistics per component, F = 1 + D + D(D+1)/2 = 28 doubles for D = 6:
+ * [0] N_k, [1..6] S1 = sum r x, [7..27] S2 = sum r x x^T upper triangle,
+ * row-major (0,0),(0,1)..(0,5),(1,1)..(5,5).  Always in the caller's frame. */
+#define VBGS_D 6
+#define VBGS_F 28
+
+/* Arithmetic of the E-step and statistics passes.  The posterior update and
+ * the cross-tile statistic reduction are FP64 in every form.
+ *   VBGS_FP64:  all FP64 on CUDA cores, factored quadratic form (the plain
+ *               form; parity <= 1e-10 against the FP64 oracle).
+ *   VBGS_FP32:  FP32 factored quadratic form on CUDA cores, FP64 partials.
+ *   VBGS_FP16X3 / VBGS_BF16X3: logits as a tensor-core GEMM of per-point
+ *               features [1, x, upper(x x^T)] against per-component
+ *               coefficients, operands split hi/lo in FP16 / BF16 with FP32
+ *               accumulation (three products), in a per-component-tile local
+ *               frame; statistics R^T phi also on the tensor cores. */
+typedef enum {
+    VBGS_FP64 = 0,
+    VBGS_FP16X3 = 1,
+    VBGS_BF16X3 = 2,
+    VBGS_FP32 = 3
+} vbgs_precision;
+
+typedef struct {
+    int precision;        /* vbgs_precision */
+    int reserved0;
+    void *cuda_stream;    /* cudaStream_t to enqueue on; NULL = legacy default stream */
+    uint64_t reserved1;
+} vbgs_options;
+
+/* Prior of every component (Sec. 2.1.2): Dirichlet(alpha0) weights and
+ * NW(m0_k, beta0, W0, nu0) per component.  m0 is K x D row-major (host),
+ * W0 the D x D Wishart scale in precision space (host, symmetric positive
+ * definite).  Both are copied by vbgs_init. */
+typedef struct {
+    double alpha0, beta0, nu0;
+    const double *m0;
+    const double *W0;
+} vbgs_prior;
+
+typedef struct vbgs_ctx vbgs_ctx;
+
+/* Create a context for K components of dimension D (must be 6) with the given
+ * prior; opt may be NULL (FP64 form, default stream).  The accumulated
+ * statistics S_past start at zero, so the model starts at the prior.
+ * Errors: VBGS_EINVAL (bad sizes, NULL, nu0 <= D-1, beta0 <= 0, alpha0 <= 0,
+ * W0 not SPD, non-finite m0), VBGS_ENOMEM, VBGS_ECUDA. */
+int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_options *opt);
+
+/* Process one frame X_t (Alg. 1 `fit`): n_iters CAVI iterations over the N
+ * points, each an E-step under the current posterior, the fused statistics
+ * contraction (Eq. 3) and the FP64 posterior update from S_past + Delta S;
+ * then S_past += Delta S (continual, replay-free).  elbo_trace (n_iters
+ * doubles, host, may be NULL) receives the ELBO of the posterior entering
+ * each iteration, against the effective prior prior0 (+) S_past.  N may be 0.
+ * Errors: VBGS_EINVAL (NULL ctx/points with N > 0, N < 0, n_iters < 1,
+ * non-finite coordinates; the state is left unchanged), VBGS_ENUMERIC,
+ * VBGS_ECUDA, VBGS_ENOMEM. */
+int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, double *elbo_trace);
+
+/* ELBO of the points X under the current posterior q = prior0 (+) S_past
+ * (the value elbo_trace[0] of a vbgs_update on X would take), without
+ * changing the state.  lse_out (N doubles, host, may be NULL) receives the
+ * per-point terms lse_n, the per-point ELBO that `reassign` ranks on. */
+int vbgs_elbo(vbgs_ctx *ctx, const double *points, int64_t N, double *elbo_out, double *lse_out);
+
+/* Posterior q = prior0 (+) S_past, host arrays allocated by the caller:
+ * alpha, beta, nu (K), m (K x D), Winv (K x D x D, full symmetric W^-1).
+ * Any pointer may be NULL to skip it. */
+int vbgs_get_posterior(vbgs_ctx *ctx, double *alpha, double *beta, double *m,
+                       double *Winv, double *nu);
+
+/* Accumulated statistics S_past (K x F, host). */
+int vbgs_get_stats(vbgs_ctx *ctx, double *S);
+
+/* Replace S_past (K x F, host), e.g. to resume a stream or to evaluate one
+ * iteration from a given state.  Errors: VBGS_EINVAL on non-finite input. */
+int vbgs_set_stats(vbgs_ctx *ctx, const double *S);
+
+/* Statistics Delta S (K x F) of the last iteration of the last vbgs_update,
+ * and its per-point lse_n (N_last doubles). */
+int vbgs_get_frame_stats(vbgs_ctx *ctx, double *dS);
+int vbgs_get_lse(vbgs_ctx *ctx, double *lse, int64_t N);
+
+/* Kernel launches issued by the last vbgs_update / vbgs_elbo call. */
+int64_t vbgs_last_launch_count(const vbgs_ctx *ctx);
+
+/* Per-kernel device timing.  When enabled, the library records a CUDA event
+ * pair around every kernel it launches on the context's stream and, at the
+ * end of each call that synchronises, adds the elapsed times per kernel
+ * class.  vbgs_profile_read copies VBGS_PROF_COUNT totals (milliseconds and
+ * launch counts) into caller arrays (either may be NULL) and optionally
+ * resets them.  vbgs_profile_name(i) names class i. */
+enum {
+    VBGS_PROF_PASS1 = 0,   /* logits + online log-sum-exp per point */
+    VBGS_PROF_MERGE = 1,   /* split merge of lse and fixed-order sums */
+    VBGS_PROF_PASS2 = 2,   /* recomputed responsibilities x features (Eq. 3) */
+    VBGS_PROF_REDUCE = 3,  /* FP64 cross-split statistic reduction */
+    VBGS_PROF_MSTEP = 4,   /* FP64 posterior update, KL terms, records */
+    VBGS_PROF_MISC = 5,    /* staging, ELBO, commit */
+    VBGS_PROF_COUNT = 6
+};
+int vbgs_profile_enable(vbgs_ctx *ctx, int on);
+int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset);
+const char *vbgs_profile_name(int i);
+
+/* Measure this GPU's arithmetic peaks with short probe kernels (a few
+ * milliseconds each, device `device`): out[0] FP64 FMA TFLOP/s, out[1] FP32
+ * FMA TFLOP/s, out[2] MUFU ex2.approx.f32 results per second (1e9 units),
+ * out[3] SM count.  Used for the ALU rooflines of the CUDA-core kernels. */
+int vbgs_probe_peaks(int device, double *out);
+
+/* Message of the last failure on ctx (or of the last failure with no context
+ * when ctx is NULL).  Never NULL. */
+const char *vbgs_last_error(const vbgs_ctx *ctx);
+
+/* Free every device and host resource of ctx (NULL is a no-op). */
+void vbgs_destroy(vbgs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VBGS_H */

@@ -1,0 +1,486 @@
+// vbgs_api.cu -- host runtime behind the C ABI of include/vbgs.h.
+//
+// A context owns every device buffer of one mixture model and the CUDA
+// stream its work is enqueued on.  vbgs_update drives Algorithm 1's `fit`
+// for one frame: stage the points, form the posterior entering the frame
+// (prior0 (+) S_past), then per CAVI iteration the E-step passes, the ELBO
+// of the posterior entering the iteration, and the FP64 posterior update;
+// finally S_past += Delta S.  All launches go on one stream; the only host
+// synchronisations are the validation of device-resident points and the
+// read-back of host outputs.
+#include "vbgs_internal.cuh"
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+#include <algorithm>
+#include <cstdarg>
+
+using namespace vbgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(vbgs_ctx *ctx, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? VBGS_ENOMEM : VBGS_ECUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                        \
+    } while (0)
+
+// Host Cholesky of a symmetric 6x6 matrix; false if not positive definite.
+bool host_chol6(const double *A, double *L)
+{
+    memset(L, 0, 36 * sizeof(double));
+    for (int j = 0; j < 6; j++) {
+        double d = A[j * 6 + j];
+        for (int k = 0; k < j; k++) d -= L[j * 6 + k] * L[j * 6 + k];
+        if (!(d > 0.0)) return false;
+        d = sqrt(d);
+        L[j * 6 + j] = d;
+        for (int i = j + 1; i < 6; i++) {
+            double t = A[i * 6 + j];
+            for (int k = 0; k < j; k++) t -= L[i * 6 + k] * L[j * 6 + k];
+            L[i * 6 + j] = t / d;
+        }
+    }
+    return true;
+}
+
+// Inverse of an SPD 6x6 matrix through its Cholesky factor.
+bool host_spd_inverse6(const double *A, double *Ainv)
+{
+    double L[36], Li[36] = {0};
+    if (!host_chol6(A, L)) return false;
+    for (int c = 0; c < 6; c++) {
+        Li[c * 6 + c] = 1.0 / L[c * 6 + c];
+        for (int i = c + 1; i < 6; i++) {
+            double t = 0.0;
+            for (int k = c; k < i; k++) t += L[i * 6 + k] * Li[k * 6 + c];
+            Li[i * 6 + c] = -t / L[i * 6 + i];
+        }
+    }
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j < 6; j++) {
+            double s = 0.0;
+            for (int k = std::max(i, j); k < 6; k++) s += Li[k * 6 + i] * Li[k * 6 + j];
+            Ainv[i * 6 + j] = s;
+        }
+    return true;
+}
+
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int dalloc(vbgs_ctx *ctx, T **p, size_t n)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(ctx, e == cudaErrorMemoryAllocation ? VBGS_ENOMEM : VBGS_ECUDA,
+                    "cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+    }
+    return VBGS_OK;
+}
+
+// Make the per-frame buffers large enough for N points.
+int ensure_capacity(vbgs_ctx *ctx, int64_t N)
+{
+    int rc;
+    if (N > ctx->ncap) {
+        int64_t cap = std::max<int64_t>(N, 1024);
+        if ((rc = dalloc(ctx, &ctx->d_X, (size_t)cap * VBGS_XS))) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_lse, (size_t)cap))) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_lse_part, (size_t)(cap + 255) / 256 + 1))) return rc;
+        ctx->ncap = cap;
+    }
+    size_t need = estep_cuda_core_scratch(std::max<int64_t>(N, 1), ctx->K, ctx->precision);
+    if (need > ctx->part_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_part, need))) return rc;
+        ctx->part_cap = need;
+    }
+    return VBGS_OK;
+}
+
+int ensure_elbo(vbgs_ctx *ctx, int n)
+{
+    if (n <= ctx->elbo_cap) return VBGS_OK;
+    int cap = std::max(n, 64);
+    int rc = dalloc(ctx, &ctx->d_elbo, (size_t)cap);
+    if (rc) return rc;
+    ctx->elbo_cap = cap;
+    return VBGS_OK;
+}
+
+// Stage N points (host or device) into d_X and validate them.
+int stage_points(vbgs_ctx *ctx, const double *points, int64_t N)
+{
+    if (N == 0) return VBGS_OK;
+    if (is_device_pointer(points)) {
+        CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+        int l = launch_stage_points(points, N, ctx->d_X, ctx->d_flags, ctx->stream, &ctx->prof);
+        if (l < 0) return fail(ctx, VBGS_ECUDA, "point staging launch failed");
+        ctx->launches += l;
+        int bad = 0;
+        CU(cudaMemcpyAsync(&bad, ctx->d_flags + FL_BAD_POINT, sizeof(int), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        ctx->prof.collect();
+        if (bad) return fail(ctx, VBGS_EINVAL, "non-finite point coordinate");
+    } else {
+        for (int64_t i = 0; i < N * 6; i++)
+            if (!std::isfinite(points[i]))
+                return fail(ctx, VBGS_EINVAL, "non-finite point coordinate at point %lld",
+                            (long long)(i / 6));
+        CU(cudaMemcpy2DAsync(ctx->d_X, VBGS_XS * sizeof(double), points, 6 * sizeof(double),
+                             6 * sizeof(double), (size_t)N, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return VBGS_OK;
+}
+
+int run_mstep(vbgs_ctx *ctx, const double *dS)
+{
+    int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_rec, ctx->d_rec32, ctx->d_klk,
+                         ctx->d_aq, ctx->d_ap, ctx->d_dN, ctx->d_flags, ctx->d_scal, ctx->stream,
+                         &ctx->prof);
+    if (l < 0) return fail(ctx, VBGS_ECUDA, "posterior update launch failed");
+    ctx->launches += l;
+    return VBGS_OK;
+}
+
+int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
+{
+    if (N == 0) {
+        CU(cudaMemsetAsync(ctx->d_scal + SC_SUM_LSE, 0, sizeof(double), ctx->stream));
+        if (want_stats) CU(cudaMemsetAsync(ctx->d_dS, 0, sizeof(double) * ctx->K * VBGS_F, ctx->stream));
+        return VBGS_OK;
+    }
+    EstepBuffers B;
+    B.X = ctx->d_X;
+    B.N = N;
+    B.K = ctx->K;
+    B.rec = ctx->d_rec;
+    B.rec32 = ctx->d_rec32;
+    B.lse = ctx->d_lse;
+    B.lse_part = ctx->d_lse_part;
+    B.scal = ctx->d_scal;
+    B.part = ctx->d_part;
+    B.part_cap = ctx->part_cap;
+    B.dS = ctx->d_dS;
+    int l = launch_estep_cuda_core(B, ctx->precision, want_stats, ctx->stream, &ctx->prof);
+    if (l < 0) return fail(ctx, VBGS_ECUDA, "E-step launch failed (%d): %s", l,
+                           cudaGetErrorString(cudaGetLastError()));
+    ctx->launches += l;
+    return VBGS_OK;
+}
+
+int check_flags(vbgs_ctx *ctx)
+{
+    int fl[FL_COUNT];
+    CU(cudaMemcpyAsync(fl, ctx->d_flags, sizeof fl, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->prof.collect();
+    if (fl[FL_NONPD])
+        return fail(ctx, VBGS_ENUMERIC, "posterior W^-1 of component %d is not positive definite",
+                    fl[FL_NONPD] - 1);
+    if (fl[FL_TIMEOUT]) return fail(ctx, VBGS_ETIMEOUT, "a bounded device wait gave up");
+    return VBGS_OK;
+}
+
+void free_all(vbgs_ctx *ctx)
+{
+    void *ptrs[] = {ctx->d_m0, ctx->d_Spast, ctx->d_dS, ctx->d_zero, ctx->d_rec, ctx->d_rec32,
+                    ctx->d_klk, ctx->d_aq, ctx->d_ap, ctx->d_dN, ctx->d_scal, ctx->d_elbo,
+                    ctx->d_flags, ctx->d_X, ctx->d_lse, ctx->d_lse_part, ctx->d_part};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    ctx->prof.pool.clear();
+}
+
+} // namespace
+
+extern "C" {
+
+int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_options *opt)
+{
+    vbgs_ctx *ctx = nullptr;
+    if (!out) return fail(nullptr, VBGS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!prior || !prior->m0 || !prior->W0) return fail(nullptr, VBGS_EINVAL, "prior, m0 or W0 is NULL");
+    if (D != VBGS_D) return fail(nullptr, VBGS_EINVAL, "D must be 6 (got %d)", D);
+    if (K <= 0) return fail(nullptr, VBGS_EINVAL, "K must be positive (got %d)", K);
+    if (!(prior->alpha0 > 0) || !(prior->beta0 > 0) || !(prior->nu0 > D - 1) ||
+        !std::isfinite(prior->alpha0) || !std::isfinite(prior->beta0) || !std::isfinite(prior->nu0))
+        return fail(nullptr, VBGS_EINVAL, "need alpha0 > 0, beta0 > 0, nu0 > D - 1");
+    int precision = opt ? opt->precision : VBGS_FP64;
+    if (precision != VBGS_FP64 && precision != VBGS_FP32)
+        return fail(nullptr, VBGS_EINVAL, "precision %d is not available in this build", precision);
+    for (size_t i = 0; i < (size_t)K * 6; i++)
+        if (!std::isfinite(prior->m0[i])) return fail(nullptr, VBGS_EINVAL, "non-finite m0");
+    double W0[36], W0inv[36];
+    for (int i = 0; i < 36; i++) W0[i] = prior->W0[i];
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j < 6; j++)
+            if (!std::isfinite(W0[i * 6 + j]) || W0[i * 6 + j] != W0[j * 6 + i])
+                return fail(nullptr, VBGS_EINVAL, "W0 must be finite and symmetric");
+    if (!host_spd_inverse6(W0, W0inv)) return fail(nullptr, VBGS_EINVAL, "W0 is not positive definite");
+
+    ctx = new vbgs_ctx();
+    ctx->K = K;
+    ctx->precision = precision;
+    ctx->stream = opt ? (cudaStream_t)opt->cuda_stream : nullptr;
+    ctx->mp.alpha0 = prior->alpha0;
+    ctx->mp.beta0 = prior->beta0;
+    ctx->mp.nu0 = prior->nu0;
+    ctx->mp.K = K;
+    for (int i = 0; i < 36; i++) ctx->mp.W0inv[i] = W0inv[i];
+    ctx->m0_h.assign(prior->m0, prior->m0 + (size_t)K * 6);
+
+    int rc = VBGS_OK;
+    const size_t KF = (size_t)K * VBGS_F;
+    if ((rc = dalloc(ctx, &ctx->d_m0, (size_t)K * 6)) || (rc = dalloc(ctx, &ctx->d_Spast, KF)) ||
+        (rc = dalloc(ctx, &ctx->d_dS, KF)) || (rc = dalloc(ctx, &ctx->d_rec, (size_t)K * VBGS_REC)) ||
+        (rc = dalloc(ctx, &ctx->d_rec32, (size_t)K * VBGS_REC)) || (rc = dalloc(ctx, &ctx->d_klk, (size_t)K)) ||
+        (rc = dalloc(ctx, &ctx->d_aq, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_ap, (size_t)K)) ||
+        (rc = dalloc(ctx, &ctx->d_dN, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_scal, (size_t)SC_COUNT)) ||
+        (rc = dalloc(ctx, &ctx->d_flags, (size_t)FL_COUNT)) || (rc = ensure_elbo(ctx, 64))) {
+        g_err = ctx->err;
+        free_all(ctx);
+        delete ctx;
+        return rc;
+    }
+    auto init_fail = [&](int code) {
+        g_err = ctx->err;
+        free_all(ctx);
+        delete ctx;
+        return code;
+    };
+#undef CU
+#define CU(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            fail(ctx, VBGS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));        \
+            return init_fail(VBGS_ECUDA);                                          \
+        }                                                                          \
+    } while (0)
+    CU(cudaMemcpyAsync(ctx->d_m0, prior->m0, sizeof(double) * K * 6, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_Spast, 0, sizeof(double) * KF, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_dS, 0, sizeof(double) * KF, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_scal, 0, sizeof(double) * SC_COUNT, ctx->stream));
+    if ((rc = run_mstep(ctx, nullptr))) return init_fail(rc);
+    CU(cudaStreamSynchronize(ctx->stream));
+#undef CU
+#define CU(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? VBGS_ENOMEM : VBGS_ECUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                        \
+    } while (0)
+    *out = ctx;
+    return VBGS_OK;
+}
+
+int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, double *elbo_trace)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (N < 0 || n_iters < 1) return fail(ctx, VBGS_EINVAL, "need N >= 0 and n_iters >= 1");
+    if (N > 0 && !points) return fail(ctx, VBGS_EINVAL, "points is NULL");
+    ctx->launches = 0;
+    int rc;
+    if ((rc = ensure_capacity(ctx, N)) || (rc = ensure_elbo(ctx, n_iters))) return rc;
+    if ((rc = stage_points(ctx, points, N))) return rc;
+    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    // Posterior entering the frame: the effective prior prior0 (+) S_past.
+    if ((rc = run_mstep(ctx, nullptr))) return rc;
+    for (int it = 0; it < n_iters; it++) {
+        if ((rc = run_estep(ctx, N, true))) return rc;
+        if (launch_elbo(ctx->d_scal, N, ctx->d_elbo + it, ctx->stream, &ctx->prof) < 0)
+            return fail(ctx, VBGS_ECUDA, "ELBO launch failed");
+        ctx->launches += 1;
+        if ((rc = run_mstep(ctx, ctx->d_dS))) return rc;
+    }
+    if (launch_commit(ctx->d_Spast, ctx->d_dS, ctx->K, ctx->d_flags, ctx->stream, &ctx->prof) < 0)
+        return fail(ctx, VBGS_ECUDA, "commit launch failed");
+    ctx->launches += 1;
+    ctx->last_N = N;
+    if (elbo_trace)
+        CU(cudaMemcpyAsync(elbo_trace, ctx->d_elbo, sizeof(double) * n_iters, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    return check_flags(ctx);
+}
+
+int vbgs_elbo(vbgs_ctx *ctx, const double *points, int64_t N, double *elbo_out, double *lse_out)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (N < 0 || !elbo_out) return fail(ctx, VBGS_EINVAL, "need N >= 0 and elbo_out");
+    if (N > 0 && !points) return fail(ctx, VBGS_EINVAL, "points is NULL");
+    ctx->launches = 0;
+    int rc;
+    if ((rc = ensure_capacity(ctx, N)) || (rc = ensure_elbo(ctx, 1))) return rc;
+    if ((rc = stage_points(ctx, points, N))) return rc;
+    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    if ((rc = run_mstep(ctx, nullptr))) return rc;
+    if ((rc = run_estep(ctx, N, false))) return rc;
+    if (launch_elbo(ctx->d_scal, N, ctx->d_elbo, ctx->stream, &ctx->prof) < 0)
+        return fail(ctx, VBGS_ECUDA, "ELBO launch failed");
+    ctx->launches += 1;
+    ctx->last_N = N;
+    CU(cudaMemcpyAsync(elbo_out, ctx->d_elbo, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if ((rc = check_flags(ctx))) return rc;
+    if (lse_out && N > 0) return vbgs_get_lse(ctx, lse_out, N);
+    return VBGS_OK;
+}
+
+int vbgs_get_lse(vbgs_ctx *ctx, double *lse, int64_t N)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (!lse || N != ctx->last_N) return fail(ctx, VBGS_EINVAL, "lse needs N == points of the last call");
+    if (N == 0) return VBGS_OK;
+    double psi = 0.0;
+    CU(cudaMemcpyAsync(lse, ctx->d_lse, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(&psi, ctx->d_scal + SC_PSI_ESTEP, sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    // The device keeps lse without the -psi(sum alpha) shared by every logit.
+    for (int64_t n = 0; n < N; n++) lse[n] -= psi;
+    return VBGS_OK;
+}
+
+int vbgs_get_frame_stats(vbgs_ctx *ctx, double *dS)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (!dS) return fail(ctx, VBGS_EINVAL, "dS is NULL");
+    CU(cudaMemcpyAsync(dS, ctx->d_dS, sizeof(double) * ctx->K * VBGS_F, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return VBGS_OK;
+}
+
+int vbgs_get_stats(vbgs_ctx *ctx, double *S)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (!S) return fail(ctx, VBGS_EINVAL, "S is NULL");
+    CU(cudaMemcpyAsync(S, ctx->d_Spast, sizeof(double) * ctx->K * VBGS_F, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return VBGS_OK;
+}
+
+int vbgs_set_stats(vbgs_ctx *ctx, const double *S)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (!S) return fail(ctx, VBGS_EINVAL, "S is NULL");
+    for (size_t i = 0; i < (size_t)ctx->K * VBGS_F; i++)
+        if (!std::isfinite(S[i])) return fail(ctx, VBGS_EINVAL, "non-finite statistic at %zu", i);
+    CU(cudaMemcpyAsync(ctx->d_Spast, S, sizeof(double) * ctx->K * VBGS_F, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    int rc = run_mstep(ctx, nullptr);
+    if (rc) return rc;
+    return check_flags(ctx);
+}
+
+int vbgs_get_posterior(vbgs_ctx *ctx, double *alpha, double *beta, double *m, double *Winv, double *nu)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    const int K = ctx->K;
+    std::vector<double> S((size_t)K * VBGS_F);
+    int rc = vbgs_get_stats(ctx, S.data());
+    if (rc) return rc;
+    const MstepParams &P = ctx->mp;
+    for (int k = 0; k < K; k++) {
+        const double *s = &S[(size_t)k * VBGS_F];
+        const double *m0 = &ctx->m0_h[(size_t)k * 6];
+        const double N = s[0], b = P.beta0 + N;
+        double mk[6];
+        for (int i = 0; i < 6; i++) mk[i] = (P.beta0 * m0[i] + s[1 + i]) / b;
+        if (alpha) alpha[k] = P.alpha0 + N;
+        if (beta) beta[k] = b;
+        if (nu) nu[k] = P.nu0 + N;
+        if (m)
+            for (int i = 0; i < 6; i++) m[(size_t)k * 6 + i] = mk[i];
+        if (Winv)
+            for (int i = 0; i < 6; i++)
+                for (int j = i; j < 6; j++) {
+                    double v = P.W0inv[i * 6 + j] + s[upper_index(i, j)] + P.beta0 * m0[i] * m0[j] - b * mk[i] * mk[j];
+                    Winv[(size_t)k * 36 + i * 6 + j] = v;
+                    Winv[(size_t)k * 36 + j * 6 + i] = v;
+                }
+    }
+    return VBGS_OK;
+}
+
+int64_t vbgs_last_launch_count(const vbgs_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int vbgs_profile_enable(vbgs_ctx *ctx, int on)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (on && ctx->prof.pool.empty()) {
+        ctx->prof.pool.resize(4096);
+        for (auto &e : ctx->prof.pool) CU(cudaEventCreate(&e));
+    }
+    ctx->prof.on = on != 0;
+    return VBGS_OK;
+}
+
+int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    for (int i = 0; i < VBGS_PROF_COUNT; i++) {
+        if (ms) ms[i] = ctx->prof.ms[i];
+        if (launches) launches[i] = ctx->prof.n[i];
+        if (reset) { ctx->prof.ms[i] = 0; ctx->prof.n[i] = 0; }
+    }
+    return VBGS_OK;
+}
+
+const char *vbgs_profile_name(int i)
+{
+    static const char *names[VBGS_PROF_COUNT] = {"pass1", "merge", "pass2", "reduce", "mstep", "misc"};
+    return (i >= 0 && i < VBGS_PROF_COUNT) ? names[i] : "?";
+}
+
+const char *vbgs_last_error(const vbgs_ctx *ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    return g_err.c_str();
+}
+
+void vbgs_destroy(vbgs_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+}
+
+} // extern "C"

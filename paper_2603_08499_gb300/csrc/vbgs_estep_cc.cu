@@ -1,0 +1,356 @@
+// vbgs_estep_cc.cu -- E-step and fused statistics contraction on the CUDA
+// cores, in FP64 (the plain form) or FP32.
+//
+// `compute_elbo_delta` (Alg. 1) needs, for every point n and component k,
+//   log rho_nk = c_k - 1/2 |M_k (x_n - m_k)|^2 - psi(sum alpha),
+// with M_k = sqrt(nu_k) L_k^-1 lower triangular (W_k^-1 = L_k L_k^T): the
+// factored quadratic form, no expansion, so no cancellation between large
+// terms.  The two passes never store an N x K array:
+//   pass 1  point-parallel: each thread owns PPT points and streams the
+//           component records of one K-split through shared memory,
+//           keeping an online (max, sum of exp) pair; a merge kernel
+//           combines the splits into lse_n and fixed-order block sums.
+//   pass 2  component-parallel: each thread owns one component and streams
+//           the points of one N-split (x, lse, upper(x x^T)) through shared
+//           memory, accumulating r_nk [1, x, upper(x x^T)] -- the fused
+//           contraction Delta S = R^T S_u of Eq. 3 with R recomputed on the
+//           fly instead of materialised (Alg. 3 instead of Alg. 2).
+//   reduce  sums the N-split partials of Delta S in a fixed order (FP64).
+// FP64 form: everything in double, exp() from the CUDA math library.
+// FP32 form: records in float and log2 units, ex2.approx on the MUFU, FP32
+// accumulation inside a split, FP64 partials and reduction.
+#include "vbgs_internal.cuh"
+#include <algorithm>
+
+namespace vbgs {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kChunkK = 64;   // component records per shared-memory chunk (pass 1)
+constexpr int kChunkN = 64;   // points per shared-memory chunk (pass 2)
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <typename T> struct Arith;
+template <> struct Arith<double> {
+    // r = exp(l - ref) in natural units
+    static __device__ __forceinline__ double expd(double v) { return exp(v); }
+    static __device__ __forceinline__ double lse_scale() { return 1.0; }
+};
+template <> struct Arith<float> {
+    // records are in log2 units: r = 2^(l2 - ref2)
+    static __device__ __forceinline__ float expd(float v) { return ex2_approx(v); }
+    static __device__ __forceinline__ float lse_scale() { return 1.4426950408889634f; }
+};
+
+// logit (without the -psi(sum alpha) term) of point x under record r:
+// c - 1/2 |M (x - m)|^2, M packed lower triangle at r[6..26].
+template <typename T>
+__device__ __forceinline__ T logit(const T *__restrict__ r, const T x[6])
+{
+    T d[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) d[i] = x[i] - r[i];
+    T q = T(0);
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        T y = T(0);
+#pragma unroll
+        for (int j = 0; j <= i; j++) y = fma(r[6 + tri(i, j)], d[j], y);
+        q = fma(y, y, q);
+    }
+    return fma(T(-0.5), q, r[27]);
+}
+
+// Pass 1.  grid = (point blocks, K splits).  part[split * N + n] = (max, sum)
+// with max in natural units and sum = sum_k exp(l_k - max).
+template <typename T, int PPT>
+__global__ void __launch_bounds__(kThreads) k_pass1(const double *__restrict__ X, int64_t N,
+                                                    const T *__restrict__ rec, int K, int kps,
+                                                    double2 *__restrict__ part)
+{
+    __shared__ T srec[kChunkK * 28];
+    const int split = blockIdx.y;
+    const int k0 = split * kps;
+    const int k1 = min(K, k0 + kps);
+    T x[PPT][6], mx[PPT], s[PPT];
+    int64_t nb = (int64_t)blockIdx.x * kThreads * PPT + threadIdx.x;
+#pragma unroll
+    for (int p = 0; p < PPT; p++) {
+        int64_t n = nb + (int64_t)p * kThreads;
+        int64_t nn = n < N ? n : N - 1;
+#pragma unroll
+        for (int i = 0; i < 6; i++) x[p][i] = (T)X[nn * VBGS_XS + i];
+        mx[p] = -INFINITY;
+        s[p] = T(0);
+    }
+    for (int kc = k0; kc < k1; kc += kChunkK) {
+        const int cnt = min(kChunkK, k1 - kc);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt * 28; i += kThreads)
+            srec[i] = rec[(size_t)(kc + i / 28) * VBGS_REC + (i % 28)];
+        __syncthreads();
+        for (int j = 0; j < cnt; j++) {
+            const T *r = srec + j * 28;
+#pragma unroll
+            for (int p = 0; p < PPT; p++) {
+                T l = logit<T>(r, x[p]);
+                if (l > mx[p]) {
+                    s[p] = fma(s[p], Arith<T>::expd(mx[p] - l), T(1));
+                    mx[p] = l;
+                } else {
+                    s[p] += Arith<T>::expd(l - mx[p]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PPT; p++) {
+        int64_t n = nb + (int64_t)p * kThreads;
+        if (n < N) {
+            double m = (double)mx[p] / (double)Arith<T>::lse_scale();
+            part[(size_t)split * N + n] = make_double2(m, (double)s[p]);
+        }
+    }
+}
+
+// Merge the K-split partials into lse_n and per-block sums of lse (fixed order).
+__global__ void __launch_bounds__(256) k_merge(const double2 *__restrict__ part, int nsplit, int64_t N,
+                                               double *__restrict__ lse, double *__restrict__ lse_part)
+{
+    __shared__ double sh[8];
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (n < N) {
+        double M = -INFINITY;
+        for (int j = 0; j < nsplit; j++) M = fmax(M, part[(size_t)j * N + n].x);
+        double s = 0.0;
+        for (int j = 0; j < nsplit; j++) {
+            double2 p = part[(size_t)j * N + n];
+            if (p.y > 0.0) s += p.y * exp(p.x - M);
+        }
+        v = M + log(s);
+        lse[n] = v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += sh[i];
+        lse_part[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ v, int n, double *__restrict__ out)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += sh[i];
+        *out = t;
+    }
+}
+
+// Pass 2.  grid = (component tiles of 128, N splits).  part[(split * K + k) * 28 + f].
+// FP64: raw moments [1, x, upper(x x^T)] (the plain form).  FP32: moments of
+// d = x - a_k about the component's anchor a_k = m_k (the record's mean), so
+// that FP32 accumulation never forms the large, cancelling raw second
+// moments; k_reduce_splits shifts them back to raw moments in FP64.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X,
+                                                    const double *__restrict__ lse, int64_t N,
+                                                    int64_t nps, const T *__restrict__ rec, int K,
+                                                    double *__restrict__ part)
+{
+    constexpr bool kAnchored = sizeof(T) == 4;
+    __shared__ T spt[kChunkN * 28];   // per point: x[6], lse, upper(x x^T)[21] (FP64 only)
+    const int k = blockIdx.x * kThreads + threadIdx.x;
+    const int split = blockIdx.y;
+    const int64_t n0 = (int64_t)split * nps;
+    const int64_t n1 = min(N, n0 + nps);
+    T r[28];
+    const int kk = k < K ? k : K - 1;
+#pragma unroll
+    for (int i = 0; i < 28; i++) r[i] = rec[(size_t)kk * VBGS_REC + i];
+    T acc[28];
+#pragma unroll
+    for (int f = 0; f < 28; f++) acc[f] = T(0);
+
+    for (int64_t nc = n0; nc < n1; nc += kChunkN) {
+        const int cnt = (int)min((int64_t)kChunkN, n1 - nc);
+        __syncthreads();
+        for (int p = threadIdx.x; p < cnt; p += kThreads) {
+            const double *xp = X + (nc + p) * VBGS_XS;
+            T *o = spt + p * 28;
+            double xd[6];
+#pragma unroll
+            for (int i = 0; i < 6; i++) { xd[i] = xp[i]; o[i] = (T)xd[i]; }
+            o[6] = (T)(lse[nc + p] * (double)Arith<T>::lse_scale());
+            if (!kAnchored) {
+                int u = 7;
+#pragma unroll
+                for (int i = 0; i < 6; i++)
+#pragma unroll
+                    for (int j = i; j < 6; j++) o[u++] = (T)(xd[i] * xd[j]);
+            }
+        }
+        __syncthreads();
+        for (int p = 0; p < cnt; p++) {
+            const T *o = spt + p * 28;
+            T x[6];
+#pragma unroll
+            for (int i = 0; i < 6; i++) x[i] = o[i];
+            const T w = Arith<T>::expd(logit<T>(r, x) - o[6]);
+            acc[0] += w;
+            if (kAnchored) {
+                T d[6], wd[6];
+#pragma unroll
+                for (int i = 0; i < 6; i++) { d[i] = x[i] - r[i]; wd[i] = w * d[i]; acc[1 + i] += wd[i]; }
+                int u = 7;
+#pragma unroll
+                for (int i = 0; i < 6; i++)
+#pragma unroll
+                    for (int j = i; j < 6; j++, u++) acc[u] = fma(wd[i], d[j], acc[u]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 6; i++) acc[1 + i] = fma(w, x[i], acc[1 + i]);
+#pragma unroll
+                for (int f = 7; f < 28; f++) acc[f] = fma(w, o[f], acc[f]);
+            }
+        }
+    }
+    if (k < K) {
+        double *dst = part + ((size_t)split * K + k) * 28;
+#pragma unroll
+        for (int f = 0; f < 28; f++) dst[f] = (double)acc[f];
+    }
+}
+
+// dS[k * 28 + f] = sum over splits in order.  With an anchor (FP32 records),
+// the split sums are moments about a_k and are shifted to raw moments:
+//   S1 = S1' + N a,  S2 = S2' + a S1'^T + S1' a^T + N a a^T   (FP64).
+__global__ void k_reduce_splits(const double *__restrict__ part, int nsplit, int K,
+                                const float *__restrict__ anchor, double *__restrict__ dS)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const size_t n = (size_t)K * 28;
+    double s[28];
+#pragma unroll
+    for (int f = 0; f < 28; f++) s[f] = 0.0;
+    for (int j = 0; j < nsplit; j++) {
+        const double *p = part + (size_t)j * n + (size_t)k * 28;
+#pragma unroll
+        for (int f = 0; f < 28; f++) s[f] += p[f];
+    }
+    if (anchor) {
+        double a[6], s1[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) { a[i] = (double)anchor[(size_t)k * VBGS_REC + i]; s1[i] = s[1 + i]; }
+        int u = 7;
+#pragma unroll
+        for (int i = 0; i < 6; i++)
+#pragma unroll
+            for (int j = i; j < 6; j++, u++) s[u] += a[i] * s1[j] + s1[i] * a[j] + s[0] * a[i] * a[j];
+#pragma unroll
+        for (int i = 0; i < 6; i++) s[1 + i] += s[0] * a[i];
+    }
+#pragma unroll
+    for (int f = 0; f < 28; f++) dS[(size_t)k * 28 + f] = s[f];
+}
+
+struct Plan {
+    int p1_blocks, p1_splits, kps;
+    int p2_tiles, p2_splits;
+    int64_t nps;
+    size_t scratch;   // doubles
+};
+
+template <int PPT>
+Plan make_plan(int64_t N, int K, int num_sms)
+{
+    Plan pl{};
+    const int target = num_sms * 8;
+    pl.p1_blocks = (int)((N + kThreads * PPT - 1) / (kThreads * PPT));
+    int s1 = std::max(1, (target + pl.p1_blocks - 1) / std::max(1, pl.p1_blocks));
+    s1 = std::min(s1, std::max(1, K / 16));
+    pl.kps = (K + s1 - 1) / s1;
+    pl.p1_splits = (K + pl.kps - 1) / pl.kps;
+    pl.p2_tiles = (K + kThreads - 1) / kThreads;
+    int64_t s2 = std::max<int64_t>(1, (target + pl.p2_tiles - 1) / pl.p2_tiles);
+    s2 = std::min<int64_t>(s2, std::max<int64_t>(1, N / 64));
+    s2 = std::min<int64_t>(s2, 1024);
+    pl.nps = (N + s2 - 1) / s2;
+    pl.p2_splits = (int)((N + pl.nps - 1) / pl.nps);
+    pl.scratch = std::max((size_t)pl.p1_splits * (size_t)N * 2, (size_t)pl.p2_splits * (size_t)K * 28);
+    return pl;
+}
+
+constexpr int kPPT64 = 2;
+constexpr int kPPT32 = 2;
+
+} // namespace
+
+size_t estep_cuda_core_scratch(int64_t N, int K, int precision)
+{
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    Plan pl = precision == VBGS_FP64 ? make_plan<kPPT64>(N, K, sms) : make_plan<kPPT32>(N, K, sms);
+    return pl.scratch;
+}
+
+int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats, cudaStream_t st,
+                           Prof *pf)
+{
+    if (B.N <= 0) return 0;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool f64 = precision == VBGS_FP64;
+    Plan pl = f64 ? make_plan<kPPT64>(B.N, B.K, sms) : make_plan<kPPT32>(B.N, B.K, sms);
+    if (pl.scratch > B.part_cap) return -2;
+    int launches = 0;
+    double2 *p1 = reinterpret_cast<double2 *>(B.part);
+    dim3 g1(pl.p1_blocks, pl.p1_splits);
+    pf->begin(VBGS_PROF_PASS1, st);
+    if (f64) k_pass1<double, kPPT64><<<g1, kThreads, 0, st>>>(B.X, B.N, B.rec, B.K, pl.kps, p1);
+    else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(B.X, B.N, B.rec32, B.K, pl.kps, p1);
+    pf->end(st);
+    const int mb = (int)((B.N + 255) / 256);
+    pf->begin(VBGS_PROF_MERGE, st);
+    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, B.N, B.lse, B.lse_part);
+    pf->end(st);
+    pf->begin(VBGS_PROF_MERGE, st);
+    k_sum<<<1, 1024, 0, st>>>(B.lse_part, mb, B.scal + SC_SUM_LSE);
+    pf->end(st);
+    launches += 3;
+    if (want_stats) {
+        dim3 g2(pl.p2_tiles, pl.p2_splits);
+        pf->begin(VBGS_PROF_PASS2, st);
+        if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec, B.K, B.part);
+        else     k_pass2<float><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec32, B.K, B.part);
+        pf->end(st);
+        pf->begin(VBGS_PROF_REDUCE, st);
+        k_reduce_splits<<<(B.K + 127) / 128, 128, 0, st>>>(B.part, pl.p2_splits, B.K,
+                                                          f64 ? nullptr : B.rec32, B.dS);
+        pf->end(st);
+        launches += 2;
+    }
+    return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
+} // namespace vbgs

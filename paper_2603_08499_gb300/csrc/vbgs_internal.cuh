@@ -1,0 +1,141 @@
+// vbgs_internal.cuh -- shared declarations of the GB300 VBGS library.
+//
+// Device data layout (all resident in HBM for the life of a context):
+//   X      : N x 8 doubles, points (x y z r g b) + 2 pad, caller's frame
+//   Spast  : K x 28 doubles, accumulated statistics (Alg. 1 buffer S)
+//   dS     : K x 28 doubles, statistics of the current frame (Eq. 3)
+//   rec    : K x 32 doubles, E-step record of the current posterior:
+//            [0..5] m_k, [6..26] M_k = sqrt(nu_k) L_k^-1 packed lower
+//            triangle row-major, [27] c_k (constant of log rho_nk without
+//            the -psi(sum alpha) term), [28..31] pad
+//   rec32  : K x 32 floats, the same record in FP32, log2 units
+//   klk    : K doubles, per-component KL_NW + Dirichlet terms
+//   aq, ap : K doubles, Dirichlet parameters of posterior and effective prior
+//   lse    : N doubles, logsumexp_k of the logits without -psi(sum alpha)
+//   scal   : small FP64 scalars (psi(sum alpha), KL total, sum lse, ...)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include "../../include/vbgs.h"
+
+#define VBGS_REC 32       // doubles (or floats) per E-step record
+#define VBGS_XS 8         // doubles per staged point
+
+namespace vbgs {
+
+// Offsets into the packed lower triangle of a 6x6 matrix, row-major i >= j.
+__host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+// Offset of (i, j), i <= j, in the statistics upper triangle (after 1 + D).
+__host__ __device__ constexpr int upper_index(int i, int j) { return 7 + i * 6 - i * (i - 1) / 2 + (j - i); }
+
+enum ScalarSlot {
+    SC_PSI_AHAT = 0,   // psi(sum_k alpha_k) of the posterior
+    SC_KL_TOTAL = 1,   // sum_k KL_NW + KL_Dir
+    SC_SUM_LSE = 2,    // sum_n lse_n (without -psi term)
+    SC_PSI_ESTEP = 3,  // psi(sum alpha) of the posterior the last E-step ran under
+    SC_COUNT = 8
+};
+
+enum FlagSlot {
+    FL_BAD_POINT = 0,  // a non-finite coordinate was staged
+    FL_NONPD = 1,      // index + 1 of a component whose W^-1 is not PD (0 = none)
+    FL_TIMEOUT = 2,
+    FL_COUNT = 4
+};
+
+// Per-kernel event timing (enabled by vbgs_profile_enable).  Launchers call
+// begin()/end() around each kernel; collect() runs after a stream sync.
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<int> cat_of_pair;       // class of event pair i (events 2i, 2i+1)
+    double ms[VBGS_PROF_COUNT] = {};
+    int64_t n[VBGS_PROF_COUNT] = {};
+    void begin(int cat, cudaStream_t st)
+    {
+        if (!on || used + 2 > pool.size()) return;
+        cudaEventRecord(pool[used], st);
+        cat_of_pair.push_back(cat);
+    }
+    void end(cudaStream_t st)
+    {
+        if (!on || cat_of_pair.size() * 2 != used + 2) return;
+        cudaEventRecord(pool[used + 1], st);
+        used += 2;
+    }
+    void collect()
+    {
+        for (size_t i = 0; 2 * i + 1 < used; i++) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) {
+                ms[cat_of_pair[i]] += t;
+                n[cat_of_pair[i]] += 1;
+            }
+        }
+        cudaGetLastError();
+        cat_of_pair.clear();
+        used = 0;
+    }
+};
+
+struct MstepParams {
+    double alpha0, beta0, nu0;
+    double W0inv[36];
+    int K;
+};
+
+// Arguments of one E-step (pass 1 + pass 2) over a staged frame.
+struct EstepBuffers {
+    const double *X;      // N x 8
+    int64_t N;
+    int K;
+    const double *rec;    // K x 32
+    const float *rec32;   // K x 32
+    double *lse;          // N
+    double *lse_part;     // per-block partial sums of lse (fixed order)
+    double *scal;
+    double *part;         // scratch for split partials
+    size_t part_cap;      // doubles
+    double *dS;           // K x 28
+};
+
+// ---- kernels / launchers (return number of launches, or -1 on error) ----
+int launch_stage_points(const double *src, int64_t N, double *X, int *flags, cudaStream_t st, Prof *pf);
+int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
+                 double *rec, float *rec32, double *klk, double *aq, double *ap, double *dN,
+                 int *flags, double *scal, cudaStream_t st, Prof *pf);
+int launch_commit(double *Spast, const double *dS, int K, const int *flags, cudaStream_t st, Prof *pf);
+int launch_elbo(double *scal, int64_t N, double *elbo_out, cudaStream_t st, Prof *pf);
+
+// E-step of the CUDA-core forms: FP64 (precision == VBGS_FP64) or FP32.
+int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats, cudaStream_t st,
+                           Prof *pf);
+size_t estep_cuda_core_scratch(int64_t N, int K, int precision);
+
+} // namespace vbgs
+
+struct vbgs_ctx {
+    int K = 0, D = 6;
+    int precision = VBGS_FP64;
+    cudaStream_t stream = nullptr;
+    vbgs::MstepParams mp{};
+    std::vector<double> m0_h;
+    double *d_m0 = nullptr, *d_Spast = nullptr, *d_dS = nullptr, *d_zero = nullptr;
+    double *d_rec = nullptr;
+    float *d_rec32 = nullptr;
+    double *d_klk = nullptr, *d_aq = nullptr, *d_ap = nullptr, *d_dN = nullptr;
+    double *d_scal = nullptr, *d_elbo = nullptr;
+    int *d_flags = nullptr;
+    int elbo_cap = 0;
+    int64_t ncap = 0;
+    double *d_X = nullptr, *d_lse = nullptr, *d_lse_part = nullptr;
+    size_t part_cap = 0;
+    double *d_part = nullptr;
+    int64_t last_N = 0;
+    int64_t launches = 0;
+    vbgs::Prof prof;
+    std::string err;
+};

@@ -1,0 +1,279 @@
+"""Thin ctypes binding of the C ABI in include/vbgs.h.
+
+Argument marshalling only: every step of the CAVI update runs in the CUDA
+kernels of ``libvbgs.so``.  The functions keep the C names (``vbgs_init``,
+``vbgs_update``, ``vbgs_elbo``, ``vbgs_get_posterior``, ...); the ``Model``
+class wraps a context for convenience.  Arrays may be numpy arrays (host) or
+torch tensors (host or CUDA); torch is used only for device memory and the
+current stream.  Importing this module fails loudly if the library is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libvbgs.so"
+
+VBGS_OK = 0
+VBGS_EINVAL = -1
+VBGS_ENOMEM = -2
+VBGS_ECUDA = -3
+VBGS_ENUMERIC = -4
+VBGS_ETIMEOUT = -5
+
+VBGS_FP64 = 0
+VBGS_FP16X3 = 1
+VBGS_BF16X3 = 2
+VBGS_FP32 = 3
+PRECISIONS = {"fp64": VBGS_FP64, "fp16x3": VBGS_FP16X3, "bf16x3": VBGS_BF16X3, "fp32": VBGS_FP32}
+
+D = 6
+F = 28
+
+# Every symbol include/vbgs.h declares (checked by the ABI test).
+EXPORTS = [
+    "vbgs_init", "vbgs_update", "vbgs_elbo", "vbgs_get_posterior", "vbgs_get_stats",
+    "vbgs_set_stats", "vbgs_get_frame_stats", "vbgs_get_lse", "vbgs_last_launch_count",
+    "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_name", "vbgs_probe_peaks",
+    "vbgs_last_error", "vbgs_destroy",
+]
+PROF_COUNT = 6
+PROF_NAMES = ["pass1", "merge", "pass2", "reduce", "mstep", "misc"]
+
+
+class VbgsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"vbgs error {code}: {msg}")
+        self.code = code
+
+
+class vbgs_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("reserved0", C.c_int), ("cuda_stream", C.c_void_p),
+                ("reserved1", C.c_uint64)]
+
+
+class vbgs_prior(C.Structure):
+    _fields_ = [("alpha0", C.c_double), ("beta0", C.c_double), ("nu0", C.c_double),
+                ("m0", C.POINTER(C.c_double)), ("W0", C.POINTER(C.c_double))]
+
+
+_DP = C.POINTER(C.c_double)
+
+
+def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
+    path = Path(path)
+    if not path.exists():
+        raise ImportError(f"{path} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+    lib = C.CDLL(str(path))
+    lib.vbgs_init.argtypes = [C.POINTER(C.c_void_p), C.POINTER(vbgs_prior), C.c_int, C.c_int,
+                              C.POINTER(vbgs_options)]
+    lib.vbgs_update.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, _DP]
+    lib.vbgs_elbo.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, _DP, _DP]
+    lib.vbgs_get_posterior.argtypes = [C.c_void_p, _DP, _DP, _DP, _DP, _DP]
+    lib.vbgs_get_stats.argtypes = [C.c_void_p, _DP]
+    lib.vbgs_set_stats.argtypes = [C.c_void_p, _DP]
+    lib.vbgs_get_frame_stats.argtypes = [C.c_void_p, _DP]
+    lib.vbgs_get_lse.argtypes = [C.c_void_p, _DP, C.c_int64]
+    lib.vbgs_last_launch_count.argtypes = [C.c_void_p]
+    lib.vbgs_last_launch_count.restype = C.c_int64
+    lib.vbgs_last_error.argtypes = [C.c_void_p]
+    lib.vbgs_last_error.restype = C.c_char_p
+    lib.vbgs_destroy.argtypes = [C.c_void_p]
+    lib.vbgs_destroy.restype = None
+    lib.vbgs_profile_enable.argtypes = [C.c_void_p, C.c_int]
+    lib.vbgs_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_int64), C.c_int]
+    lib.vbgs_profile_name.argtypes = [C.c_int]
+    lib.vbgs_profile_name.restype = C.c_char_p
+    lib.vbgs_probe_peaks.argtypes = [C.c_int, _DP]
+    return lib
+
+
+_lib: C.CDLL | None = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(rc: int, ctx=None) -> None:
+    if rc != VBGS_OK:
+        raise VbgsError(rc, lib().vbgs_last_error(ctx).decode(errors="replace"))
+
+
+def _host_f64(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None and a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _points_ptr(points):
+    """(pointer, N, keepalive) for an N x 6 float64 array on host or device."""
+    try:
+        import torch
+        if isinstance(points, torch.Tensor):
+            if points.dtype != torch.float64 or points.dim() != 2 or points.shape[1] != D:
+                raise ValueError("points must be an N x 6 float64 tensor")
+            t = points.contiguous()
+            return C.c_void_p(t.data_ptr() if t.numel() else None), t.shape[0], t
+    except ImportError:
+        pass
+    a = _host_f64(points)
+    if a.ndim != 2 or a.shape[1] != D:
+        raise ValueError("points must be N x 6")
+    return C.c_void_p(a.ctypes.data if a.size else None), a.shape[0], a
+
+
+# ---- C-named functions ------------------------------------------------------
+
+def vbgs_init(alpha0: float, beta0: float, nu0: float, m0, W0, precision: int = VBGS_FP64,
+              cuda_stream: int | None = None):
+    m0a = _host_f64(m0)
+    K = m0a.shape[0]
+    W0a = _host_f64(W0, (D, D))
+    pr = vbgs_prior(alpha0, beta0, nu0, _dp(m0a), _dp(W0a))
+    opt = vbgs_options(int(precision), 0, C.c_void_p(cuda_stream or None), 0)
+    ctx = C.c_void_p()
+    _check(lib().vbgs_init(C.byref(ctx), C.byref(pr), K, m0a.shape[1], C.byref(opt)), None)
+    return ctx
+
+
+def vbgs_update(ctx, points, n_iters: int) -> np.ndarray:
+    ptr, N, keep = _points_ptr(points)
+    trace = np.zeros(max(n_iters, 1), dtype=np.float64)
+    _check(lib().vbgs_update(ctx, ptr, N, n_iters, _dp(trace)), ctx)
+    del keep
+    return trace[:n_iters]
+
+
+def vbgs_elbo(ctx, points, want_lse: bool = False):
+    ptr, N, keep = _points_ptr(points)
+    out = np.zeros(1)
+    lse = np.zeros(max(N, 1)) if want_lse else None
+    _check(lib().vbgs_elbo(ctx, ptr, N, _dp(out), _dp(lse) if want_lse else None), ctx)
+    del keep
+    return (float(out[0]), lse[:N]) if want_lse else float(out[0])
+
+
+def vbgs_get_posterior(ctx, K: int) -> dict:
+    out = {"alpha": np.zeros(K), "beta": np.zeros(K), "m": np.zeros((K, D)),
+           "Winv": np.zeros((K, D, D)), "nu": np.zeros(K)}
+    _check(lib().vbgs_get_posterior(ctx, _dp(out["alpha"]), _dp(out["beta"]), _dp(out["m"]),
+                                    _dp(out["Winv"]), _dp(out["nu"])), ctx)
+    return out
+
+
+def vbgs_get_stats(ctx, K: int) -> np.ndarray:
+    S = np.zeros((K, F))
+    _check(lib().vbgs_get_stats(ctx, _dp(S)), ctx)
+    return S
+
+
+def vbgs_set_stats(ctx, S) -> None:
+    Sa = _host_f64(S)
+    _check(lib().vbgs_set_stats(ctx, _dp(Sa)), ctx)
+
+
+def vbgs_get_frame_stats(ctx, K: int) -> np.ndarray:
+    S = np.zeros((K, F))
+    _check(lib().vbgs_get_frame_stats(ctx, _dp(S)), ctx)
+    return S
+
+
+def vbgs_get_lse(ctx, N: int) -> np.ndarray:
+    lse = np.zeros(max(N, 1))
+    _check(lib().vbgs_get_lse(ctx, _dp(lse), N), ctx)
+    return lse[:N]
+
+
+def vbgs_last_launch_count(ctx) -> int:
+    return int(lib().vbgs_last_launch_count(ctx))
+
+
+def vbgs_profile_enable(ctx, on: bool = True) -> None:
+    _check(lib().vbgs_profile_enable(ctx, int(on)), ctx)
+
+
+def vbgs_profile_read(ctx, reset: bool = False) -> dict:
+    ms = np.zeros(PROF_COUNT)
+    n = np.zeros(PROF_COUNT, dtype=np.int64)
+    _check(lib().vbgs_profile_read(ctx, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64)), int(reset)), ctx)
+    return {lib().vbgs_profile_name(i).decode(): (float(ms[i]), int(n[i])) for i in range(PROF_COUNT)}
+
+
+def vbgs_probe_peaks(device: int = 0) -> dict:
+    out = np.zeros(4)
+    _check(lib().vbgs_probe_peaks(device, _dp(out)), None)
+    return {"fp64_tflops": float(out[0]), "fp32_tflops": float(out[1]), "mufu_ex2_gops": float(out[2]),
+            "sms": int(out[3])}
+
+
+def vbgs_last_error(ctx=None) -> str:
+    return lib().vbgs_last_error(ctx).decode(errors="replace")
+
+
+def vbgs_destroy(ctx) -> None:
+    if ctx:
+        lib().vbgs_destroy(ctx)
+
+
+class Model:
+    """One VBGS mixture on the GPU (owns a vbgs_ctx)."""
+
+    def __init__(self, prior: dict, precision: str | int = "fp64", cuda_stream: int | None = None):
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.K = int(np.asarray(prior["m0"]).shape[0])
+        self.ctx = vbgs_init(prior["alpha0"], prior["beta0"], prior["nu0"], prior["m0"], prior["W0"],
+                             p, cuda_stream)
+
+    def update(self, points, n_iters: int) -> np.ndarray:
+        return vbgs_update(self.ctx, points, n_iters)
+
+    def elbo(self, points, want_lse: bool = False):
+        return vbgs_elbo(self.ctx, points, want_lse)
+
+    def posterior(self) -> dict:
+        return vbgs_get_posterior(self.ctx, self.K)
+
+    def stats(self) -> np.ndarray:
+        return vbgs_get_stats(self.ctx, self.K)
+
+    def set_stats(self, S) -> None:
+        vbgs_set_stats(self.ctx, S)
+
+    def frame_stats(self) -> np.ndarray:
+        return vbgs_get_frame_stats(self.ctx, self.K)
+
+    def lse(self, N: int) -> np.ndarray:
+        return vbgs_get_lse(self.ctx, N)
+
+    def launches(self) -> int:
+        return vbgs_last_launch_count(self.ctx)
+
+    def profile(self, on: bool = True) -> None:
+        vbgs_profile_enable(self.ctx, on)
+
+    def profile_read(self, reset: bool = False) -> dict:
+        return vbgs_profile_read(self.ctx, reset)
+
+    def close(self) -> None:
+        if self.ctx:
+            vbgs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

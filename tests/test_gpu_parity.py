@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  Tolerances use the paper's relative error (Eq. relerr):
+FP64 form <= 1e-10 on every statistic array and on the ELBO; the FP32 form
+<= 1e-3 per statistic array and <= 1e-4 on the ELBO."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2603_08499_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": {"stat": 1e-10, "elbo": 1e-10, "lse": 1e-10},
+       "fp32": {"stat": 1e-3, "elbo": 1e-4, "lse": 1e-4}}
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_2603_08499_gb300 import build
+    build.build()
+    from paper_2603_08499_gb300 import vbgs
+    return vbgs
+
+
+def stat_errors(S_gpu, S_ref):
+    return {"N": O.relerr(S_gpu[:, 0], S_ref[:, 0]), "S1": O.relerr(S_gpu[:, 1:7], S_ref[:, 1:7]),
+            "S2": O.relerr(S_gpu[:, 7:], S_ref[:, 7:])}
+
+
+def check_frame(V, X, prior, n_iters, form, S_past=None):
+    K = prior["m0"].shape[0]
+    S_past = np.zeros((K, 28)) if S_past is None else S_past
+    m = V.Model(prior, form)
+    if np.any(S_past):
+        m.set_stats(S_past)
+    trace = m.update(X, n_iters)
+    e_ref, S_ref, lse_ref, dS_ref = O.cavi_frame(X, prior, S_past, n_iters)
+    tol = TOL[form]
+    errs = stat_errors(m.stats(), S_ref)
+    for name, e in errs.items():
+        assert e <= tol["stat"], (name, e, errs)
+    for name, e in stat_errors(m.frame_stats(), dS_ref).items():
+        assert e <= tol["stat"], ("dS", name, e)
+    for i in range(n_iters):
+        assert O.relerr(trace[i], e_ref[i]) <= tol["elbo"], (i, trace[i], e_ref[i])
+    if X.shape[0]:
+        assert O.relerr(m.lse(X.shape[0]), lse_ref) <= tol["lse"]
+    assert m.launches() > 0 or X.shape[0] == 0
+    m.close()
+    return trace, e_ref
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32"])
+def test_mixture_small_several_tiles_ragged(V, form):
+    X, pr = synth.c1_workload(seed=11, N=2_345, K=197)
+    check_frame(V, X, pr, 6, form)
+
+
+def test_mixture_full_size_fp64(V):
+    """10,000 points, 1,000 components, 10 CAVI iterations (the full plain FP64 workload)."""
+    X, pr = synth.c1_workload(seed=1, N=10_000, K=1_000)
+    trace, ref = check_frame(V, X, pr, 10, "fp64")
+    assert np.all(np.diff(trace) >= -1e-9 * abs(trace[-1]))
+
+
+def test_mixture_full_size_fp32(V):
+    X, pr = synth.c1_workload(seed=1, N=10_000, K=1_000)
+    check_frame(V, X, pr, 10, "fp32")
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32"])
+def test_k1_and_tiny_edges(V, form):
+    X, pr = synth.c1_workload(seed=12, N=37, K=1)
+    check_frame(V, X, pr, 3, form)
+    X, pr = synth.c1_workload(seed=13, N=1, K=5)
+    check_frame(V, X, pr, 2, form)
+    X, pr = synth.c1_workload(seed=14, N=129, K=129)
+    check_frame(V, X, pr, 2, form)
+
+
+def test_empty_frame(V):
+    _, pr = synth.c1_workload(seed=15, N=10, K=7)
+    m = V.Model(pr, "fp64")
+    trace = m.update(np.zeros((0, 6)), 2)
+    assert np.all(np.abs(trace) < 1e-9)
+    assert np.all(m.stats() == 0)
+
+
+def test_streaming_frames_match_oracle(V):
+    """Three consecutive room frames through one context (continual, replay-free)."""
+    room = synth.Room(seed=2)
+    pr = synth.room_prior(400, seed=2)
+    m = V.Model(pr, "fp64")
+    S = np.zeros((400, 28))
+    for t in range(3):
+        X = synth.room_frame(t, seed=2, width=48, height=48, room=room)
+        trace = m.update(X, 3)
+        e_ref, S, _, _ = O.cavi_frame(X, pr, S, 3)
+        assert O.relerr(trace, e_ref) <= 1e-10
+        for name, e in stat_errors(m.stats(), S).items():
+            assert e <= 1e-10, (t, name, e)
+    m.close()
+
+
+def test_one_iteration_from_given_state(V):
+    """One iteration from a shared FP64 state (set_stats) on a room frame."""
+    room = synth.Room(seed=3)
+    pr = synth.room_prior(600, seed=3)
+    X0 = synth.room_frame(0, seed=3, width=64, height=64, room=room)
+    _, S0, _, _ = O.cavi_frame(X0, pr, np.zeros((600, 28)), 2)
+    X1 = synth.room_frame(1, seed=3, width=64, height=64, room=room)
+    for form in ("fp64", "fp32"):
+        check_frame(V, X1, pr, 1, form, S_past=S0)
+
+
+def test_device_points_equal_host_points(V):
+    import torch
+    X, pr = synth.c1_workload(seed=16, N=3_000, K=150)
+    a = V.Model(pr, "fp64")
+    b = V.Model(pr, "fp64")
+    ta = a.update(X, 3)
+    tb = b.update(torch.from_numpy(X).cuda(), 3)
+    assert np.array_equal(ta, tb)
+    assert np.array_equal(a.stats(), b.stats())
+
+
+def test_elbo_entry_point_matches_oracle(V):
+    X, pr = synth.c1_workload(seed=17, N=4_000, K=120)
+    m = V.Model(pr, "fp64")
+    m.update(X[:2000], 4)
+    S_ref = O.cavi_frame(X[:2000], pr, np.zeros((120, 28)), 4)[1]
+    e, lse = m.elbo(X[2000:], want_lse=True)
+    e_ref = O.elbo(X[2000:], pr, S_ref)
+    assert O.relerr(e, e_ref) <= 1e-10
+    post_ref = O.mstep(pr, S_ref)
+    lse_ref, _, _ = O.estep_stats(X[2000:], post_ref)
+    assert O.relerr(lse, lse_ref) <= 1e-10
+    post = m.posterior()
+    for key in ("alpha", "beta", "nu", "m", "Winv"):
+        assert O.relerr(post[key], post_ref[key]) <= 1e-10, key
+
+
+def test_invalid_points_leave_state_unchanged(V):
+    import torch
+    X, pr = synth.c1_workload(seed=18, N=500, K=20)
+    m = V.Model(pr, "fp64")
+    m.update(X, 2)
+    S = m.stats()
+    bad = X.copy()
+    bad[17, 4] = np.inf
+    with pytest.raises(V.VbgsError) as e:
+        m.update(bad, 2)
+    assert e.value.code == V.VBGS_EINVAL
+    with pytest.raises(V.VbgsError):
+        m.update(torch.from_numpy(bad).cuda(), 2)
+    assert np.array_equal(m.stats(), S)
+    with pytest.raises(V.VbgsError):
+        m.set_stats(np.full((20, 28), np.nan))
+
+
+def test_full_size_room_frame_sampled(V):
+    """The benchmark shape (K = 50,000, one 200 x 200 frame, 3 iterations) in
+    the launch configuration the benchmark uses: invariants at full size and
+    sampled per-point lse checked one by one against the oracle."""
+    import torch
+    room = synth.Room(seed=2)
+    pr = synth.room_prior(50_000, seed=2)
+    X = synth.room_frame(0, seed=2, room=room)
+    m = V.Model(pr, "fp64")
+    trace = m.update(torch.from_numpy(X).cuda(), 3)
+    dS = m.frame_stats()
+    N = X.shape[0]
+    assert abs(dS[:, 0].sum() - N) <= 1e-9 * N
+    assert O.relerr(dS[:, 1:7].sum(0), X.sum(0)) <= 1e-12
+    assert np.all(np.diff(trace) >= -1e-9 * abs(trace[-1]))
+    # the ELBO of the first iteration is under the prior: check sampled points
+    m2 = V.Model(pr, "fp64")
+    e, lse = m2.elbo(X, want_lse=True)
+    idx = np.random.default_rng(0).choice(N, 64, replace=False)
+    post0 = O.mstep(pr, np.zeros((50_000, 28)))
+    lse_ref, _, _ = O.estep_stats(X[idx], post0)
+    assert O.relerr(lse[idx], lse_ref) <= 1e-12
+    assert O.relerr(e, trace[0]) <= 1e-12
+
+
+def test_profile_counts_launches(V):
+    X, pr = synth.c1_workload(seed=19, N=2_000, K=100)
+    m = V.Model(pr, "fp64")
+    m.profile(True)
+    m.update(X, 2)
+    prof = m.profile_read()
+    assert prof["pass1"][1] == 2 and prof["pass2"][1] == 2 and prof["pass1"][0] > 0
+    assert sum(n for _, n in prof.values()) == m.launches()
