@@ -157,6 +157,32 @@ const char *vbgs_profile_name(int i);
  * out[3] SM count.  Used for the ALU rooflines of the CUDA-core kernels. */
 int vbgs_probe_peaks(int device, double *out);
 
+/* E-step that allocates no memory.  The paper has no counterpart: this is
+ * a deployment variant for callers that cannot call cudaMalloc -- a host
+ * runtime that owns all device memory through its own pool, a process held
+ * to a fixed device-memory budget, or a frame loop that cannot take an
+ * allocation (which may synchronise the device) mid-frame.
+ * Under the context's current posterior q = prior0 (+) S_past it writes the
+ * per-point lse_n (N doubles) and the frame statistics
+ * Delta S = sum_n r_nk [1, x_n, upper(x_n x_n^T)] (K x 28 doubles) into the
+ * caller's DEVICE buffers lse_out and dS_out; points is an N x 6 DEVICE
+ * array.  The context state is not changed (the same values vbgs_update
+ * with one iteration would compute for its E-step).
+ * Scratch memory comes from one static device array of
+ * VBGS_NOALLOC_SCRATCH_BYTES held by every GPU that loads the library until
+ * the process exits; the call fails with VBGS_EINVAL when
+ * 8 N + max(2 N, 28 K) doubles (plus N / 256 block sums) exceed it, e.g.
+ * N = 40,000 points with K = 50,000 components fit.  The array's device
+ * address is looked up by the first call on each device (with that device
+ * current), so make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race; calls on one stream
+ * are ordered.  The points are validated (one stream synchronisation);
+ * results are enqueued on the context's stream without a final sync.
+ * Errors: VBGS_EINVAL (NULL, N < 0, sizes beyond the array, non-finite
+ * points), VBGS_ECUDA. */
+#define VBGS_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
+int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N, double *lse_out, double *dS_out);
+
 /* Message of the last failure on ctx (or of the last failure with no context
  * when ctx is NULL).  Never NULL. */
 const char *vbgs_last_error(const vbgs_ctx *ctx);

@@ -21,6 +21,8 @@
 // accumulation inside a split, FP64 partials and reduction.
 #include "vbgs_internal.cuh"
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 namespace vbgs {
 
@@ -353,4 +355,147 @@ int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
+
+// ---------------------------------------------------------------------------
+// E-step with no allocation (vbgs_estep_noalloc).
+//
+// Some callers cannot call cudaMalloc: a host runtime that owns all device
+// memory through its own pool and forbids side allocations, a process held
+// to a fixed device-memory budget, or a latency-critical loop that cannot
+// afford an allocation (which may synchronise the device) in the middle of
+// a frame.  For them this entry point takes its scratch memory (staged
+// points, split partials, fixed-order sums, flags) from one file-scope
+// device array of VBGS_NOALLOC_SCRATCH_BYTES instead of the context's
+// buffers, and writes its results into buffers the caller passes.
+//
+// The array lives in the library's device image: every GPU that loads the
+// library holds it until the process exits.  Its device address is looked up
+// once per device, by the first call made with that device current.  All
+// calls share the one array and it keeps the last call's contents; calls
+// that overlap on the GPU (different streams, or contexts on other host
+// threads) race on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocDoubles = VBGS_NOALLOC_SCRATCH_BYTES / sizeof(double);
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set-up on the
+// first call per device).  Returns nullptr on failure with *why set.
+double *noalloc_scratch(const char **why)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        *why = "no current CUDA device";
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            *why = "cudaGetSymbolAddress of the scratch array failed";
+            return nullptr;
+        }
+        g_noalloc_addr[dev] = static_cast<double *>(p);
+    }
+    return g_noalloc_addr[dev];
+}
+
+__global__ void k_lse_subtract_psi(double *__restrict__ lse, int64_t N, const double *__restrict__ scal)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) lse[n] -= scal[SC_PSI_AHAT];
+}
+
+int noalloc_fail(vbgs_ctx *ctx, int code, const std::string &msg)
+{
+    ctx->err = msg;
+    return code;
+}
+
+} // namespace
+
 } // namespace vbgs
+
+extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N, double *lse_out,
+                                  double *dS_out)
+{
+    using namespace vbgs;
+    if (!ctx) return VBGS_EINVAL;
+    if (N < 0 || !dS_out || (N > 0 && (!points || !lse_out)))
+        return noalloc_fail(ctx, VBGS_EINVAL, "vbgs_estep_noalloc: need N >= 0 and device points, lse, dS");
+    const cudaStream_t st = ctx->stream;
+    const int K = ctx->K;
+    const char *why = "";
+    double *base = noalloc_scratch(&why);
+    if (!base) return noalloc_fail(ctx, VBGS_ECUDA, std::string("vbgs_estep_noalloc: ") + why);
+    if (N == 0) {
+        if (cudaMemsetAsync(dS_out, 0, sizeof(double) * (size_t)K * 28, st) != cudaSuccess)
+            return noalloc_fail(ctx, VBGS_ECUDA, "vbgs_estep_noalloc: clearing dS failed");
+        return VBGS_OK;
+    }
+    // Scratch layout (doubles): scalars | flags | lse block sums | points N x 8 | split partials.
+    auto round_up = [](size_t v) { return (v + 31) & ~size_t(31); };
+    const size_t o_scal = 0, o_flags = SC_COUNT, o_lsep = 32;
+    const int mb = (int)((N + 255) / 256);
+    const size_t o_X = o_lsep + round_up((size_t)mb + 1);
+    const size_t o_part = o_X + round_up((size_t)N * VBGS_XS);
+    const size_t avail = o_part < kNoAllocDoubles ? kNoAllocDoubles - o_part : 0;
+    if (avail < (size_t)N * 2 || avail < (size_t)K * 28)
+        return noalloc_fail(ctx, VBGS_EINVAL,
+                            "vbgs_estep_noalloc: N = " + std::to_string(N) + ", K = " + std::to_string(K) +
+                            " need more than the " + std::to_string(VBGS_NOALLOC_SCRATCH_BYTES) +
+                            "-byte scratch array (8 N + max(2 N, 28 K) doubles plus block sums)");
+    double *scal = base + o_scal;
+    int *flags = reinterpret_cast<int *>(base + o_flags);
+    double *X = base + o_X;
+    double *part = base + o_part;
+
+    // Stage and validate the points; the flags must start at zero.
+    Prof off;
+    if (cudaMemsetAsync(flags, 0, sizeof(int) * FL_COUNT, st) != cudaSuccess ||
+        launch_stage_points(points, N, X, flags, st, &off) < 0)
+        return noalloc_fail(ctx, VBGS_ECUDA, "vbgs_estep_noalloc: staging failed");
+    int bad = 0;
+    if (cudaMemcpyAsync(&bad, flags + FL_BAD_POINT, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return noalloc_fail(ctx, VBGS_ECUDA, "vbgs_estep_noalloc: reading the staging flag failed");
+    if (bad) return noalloc_fail(ctx, VBGS_EINVAL, "vbgs_estep_noalloc: non-finite point coordinate");
+
+    // The launch plan of the context path, with split counts capped so the
+    // partials fit the array.
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool f64 = ctx->precision == VBGS_FP64;
+    Plan pl = f64 ? make_plan<kPPT64>(N, K, sms) : make_plan<kPPT32>(N, K, sms);
+    const int s1max = (int)std::min<size_t>(avail / ((size_t)N * 2), (size_t)pl.p1_splits);
+    pl.kps = (K + s1max - 1) / s1max;
+    pl.p1_splits = (K + pl.kps - 1) / pl.kps;
+    const int64_t s2max = (int64_t)std::min<size_t>(avail / ((size_t)K * 28), (size_t)pl.p2_splits);
+    pl.nps = (N + s2max - 1) / s2max;
+    pl.p2_splits = (int)((N + pl.nps - 1) / pl.nps);
+
+    double2 *p1 = reinterpret_cast<double2 *>(part);
+    dim3 g1(pl.p1_blocks, pl.p1_splits);
+    if (f64) k_pass1<double, kPPT64><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec, K, pl.kps, p1);
+    else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec32, K, pl.kps, p1);
+    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, lse_out, base + o_lsep);
+    k_sum<<<1, 1024, 0, st>>>(base + o_lsep, mb, scal + SC_SUM_LSE);
+    dim3 g2(pl.p2_tiles, pl.p2_splits);
+    if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part);
+    else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part);
+    k_reduce_splits<<<(K + 127) / 128, 128, 0, st>>>(part, pl.p2_splits, K, f64 ? nullptr : ctx->d_rec32,
+                                                    dS_out);
+    k_lse_subtract_psi<<<mb, 256, 0, st>>>(lse_out, N, ctx->d_scal);
+    if (cudaGetLastError() != cudaSuccess) return noalloc_fail(ctx, VBGS_ECUDA, "vbgs_estep_noalloc: launch failed");
+    ctx->launches = 7;
+    return VBGS_OK;
+}

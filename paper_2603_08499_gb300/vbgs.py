@@ -39,8 +39,9 @@ EXPORTS = [
     "vbgs_init", "vbgs_update", "vbgs_elbo", "vbgs_get_posterior", "vbgs_get_stats",
     "vbgs_set_stats", "vbgs_get_frame_stats", "vbgs_get_lse", "vbgs_last_launch_count",
     "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_name", "vbgs_probe_peaks",
-    "vbgs_last_error", "vbgs_destroy",
+    "vbgs_estep_noalloc", "vbgs_last_error", "vbgs_destroy",
 ]
+NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 PROF_COUNT = 6
 PROF_NAMES = ["pass1", "merge", "pass2", "reduce", "mstep", "misc"]
 
@@ -89,6 +90,7 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
     lib.vbgs_profile_name.argtypes = [C.c_int]
     lib.vbgs_profile_name.restype = C.c_char_p
     lib.vbgs_probe_peaks.argtypes = [C.c_int, _DP]
+    lib.vbgs_estep_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
     return lib
 
 
@@ -217,6 +219,16 @@ def vbgs_probe_peaks(device: int = 0) -> dict:
     _check(lib().vbgs_probe_peaks(device, _dp(out)), None)
     return {"fp64_tflops": float(out[0]), "fp32_tflops": float(out[1]), "mufu_ex2_gops": float(out[2]),
             "sms": int(out[3])}
+
+
+def vbgs_estep_noalloc(ctx, points, lse_out, dS_out) -> None:
+    """E-step into caller-owned device buffers with no allocation by the
+    library (torch CUDA tensors: points N x 6, lse_out N, dS_out K x 28,
+    all float64).  Results are enqueued on the context's stream."""
+    ptr, N, keep = _points_ptr(points)
+    _check(lib().vbgs_estep_noalloc(ctx, ptr, N, C.c_void_p(lse_out.data_ptr() if N else None),
+                                    C.c_void_p(dS_out.data_ptr())), ctx)
+    del keep
 
 
 def vbgs_last_error(ctx=None) -> str:
