@@ -172,11 +172,12 @@ def run_reference(args):
     return 0
 
 
-def timed_stream(V, prior, dev_frames, form, warmup, steps, stream, flush, profile=False, host_frames=None):
+def timed_stream(V, prior, dev_frames, form, warmup, steps, stream, flush, profile=False, host_frames=None,
+                 flags=0):
     """Run warmup + steps frames through a fresh model; per-step device times
     with CUDA events (or host wall time for host inputs)."""
     import torch
-    m = V.Model(prior, form, cuda_stream=stream.cuda_stream)
+    m = V.Model(prior, form, cuda_stream=stream.cuda_stream, flags=flags)
     traces, times, launches = [], [], 0
     pairs = 0
     for t in range(warmup + steps):
@@ -256,7 +257,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    res = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, profile=True)
+    res = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, profile=True, flags=args.flags)
     clk = clocks.stop()
     torch.cuda.synchronize()
     dev_time = sum(res["times"])
@@ -272,7 +273,8 @@ def run_ours(args):
     value = total_pairs / dev_time
 
     # end to end through the same call with pinned host inputs
-    res_e2e = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, host_frames=host)
+    res_e2e = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, host_frames=host,
+                           flags=args.flags)
     e2e_time = sum(res_e2e["times"])
     if ws > 1:
         t = torch.tensor([e2e_time], device="cuda", dtype=torch.float64)
@@ -283,8 +285,9 @@ def run_ours(args):
     h2d = int(np.mean([X.shape[0] * 6 * 8 for X in timed_frames]))
 
     extra = {}
-    if form != "fp64" and rank == 0:
-        ref = timed_stream(V, prior, dev, "fp64", args.warmup, args.steps, stream, flush)
+    if (form != "fp64" or args.flags != V.VBGS_FLAG_PLAIN) and rank == 0:
+        # the plain FP64 form: caller's order, every tile evaluated
+        ref = timed_stream(V, prior, dev, "fp64", args.warmup, args.steps, stream, flush, flags=V.VBGS_FLAG_PLAIN)
         fp64_value = ref["pairs"] / sum(ref["times"])
         errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(res["traces"], ref["traces"])]
         extra["fp64_form"] = {"value": fp64_value, "unit": UNIT, "speedup": value / fp64_value}
@@ -300,7 +303,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_time * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[form], "data": "synthetic",
-            "config": {"workload": WORKLOAD, "K": K_COMP, "iters": ITERS, "form": form,
+            "config": {"workload": WORKLOAD, "K": K_COMP, "iters": ITERS, "form": form, "flags": args.flags,
                        "mean_points_per_frame": n_pts / args.steps,
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas x{ws} (independent streams)"},
@@ -333,6 +336,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", choices=list(DTYPES), default="fp32")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--flags", type=int, default=0,
+                    help="VBGS_FLAG_* bits: 1 = caller's order, 2 = no pass-2 tile skipping (3 = plain)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

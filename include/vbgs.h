@@ -68,9 +68,17 @@ typedef enum {
     VBGS_FP32 = 3
 } vbgs_precision;
 
+/* Option flags.  By default points (per frame) and components (per frame,
+ * by posterior mean) are processed in Morton order, and pass 2 skips every
+ * (point chunk, component tile) whose responsibilities are all below e^-50,
+ * a bound taken from the tile maxima of pass 1; neither changes a result
+ * beyond rounding.  The plain form sets both flags. */
+#define VBGS_FLAG_NO_REORDER 1   /* process in the caller's order */
+#define VBGS_FLAG_NO_SKIP    2   /* evaluate every tile in pass 2 */
+
 typedef struct {
     int precision;        /* vbgs_precision */
-    int reserved0;
+    int flags;            /* VBGS_FLAG_* */
     void *cuda_stream;    /* cudaStream_t to enqueue on; NULL = legacy default stream */
     uint64_t reserved1;
 } vbgs_options;

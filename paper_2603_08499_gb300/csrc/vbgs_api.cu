@@ -117,7 +117,28 @@ int ensure_capacity(vbgs_ctx *ctx, int64_t N)
         if ((rc = dalloc(ctx, &ctx->d_X, (size_t)cap * VBGS_XS))) return rc;
         if ((rc = dalloc(ctx, &ctx->d_lse, (size_t)cap))) return rc;
         if ((rc = dalloc(ctx, &ctx->d_lse_part, (size_t)(cap + 255) / 256 + 1))) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_Xs, (size_t)cap * VBGS_XS))) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_pidx, (size_t)cap))) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_minlse, (size_t)(cap + 255) / 256 + 1))) return rc;
         ctx->ncap = cap;
+    }
+    const int64_t scap = std::max<int64_t>(ctx->ncap, ctx->K);
+    if (scap > ctx->sb.cap) {
+        if ((rc = dalloc(ctx, &ctx->sb.keys_in, (size_t)scap)) || (rc = dalloc(ctx, &ctx->sb.keys_out, (size_t)scap)) ||
+            (rc = dalloc(ctx, &ctx->sb.idx_in, (size_t)scap)))
+            return rc;
+        size_t tb = sort_temp_bytes(scap);
+        unsigned char *t = nullptr;
+        if ((rc = dalloc(ctx, &t, tb))) return rc;
+        if (ctx->sb.temp) cudaFree(ctx->sb.temp);
+        ctx->sb.temp = t;
+        ctx->sb.temp_bytes = tb;
+        ctx->sb.cap = scap;
+    }
+    const size_t tneed = (size_t)((std::max<int64_t>(N, 1) + 255) / 256) * (size_t)((ctx->K + 63) / 64);
+    if (tneed > ctx->tmax_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_tmax, tneed))) return rc;
+        ctx->tmax_cap = tneed;
     }
     size_t need = estep_cuda_core_scratch(std::max<int64_t>(N, 1), ctx->K, ctx->precision);
     if (need > ctx->part_cap) {
@@ -165,11 +186,30 @@ int stage_points(vbgs_ctx *ctx, const double *points, int64_t N)
 
 int run_mstep(vbgs_ctx *ctx, const double *dS)
 {
-    int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_rec, ctx->d_rec32, ctx->d_klk,
+    int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_kinv, ctx->d_rec, ctx->d_rec32, ctx->d_klk,
                          ctx->d_aq, ctx->d_ap, ctx->d_dN, ctx->d_flags, ctx->d_scal, ctx->stream,
                          &ctx->prof);
     if (l < 0) return fail(ctx, VBGS_ECUDA, "posterior update launch failed");
     ctx->launches += l;
+    return VBGS_OK;
+}
+
+// Morton order of the frame's points (sorted staging copy) and of the
+// components by their posterior mean at frame start.
+int order_frame(vbgs_ctx *ctx, int64_t N, bool points)
+{
+    ctx->last_sorted = false;
+    if (ctx->flags & VBGS_FLAG_NO_REORDER) return VBGS_OK;
+    int l = launch_comp_order(ctx->d_m0, ctx->d_Spast, ctx->K, ctx->mp.beta0, ctx->box, ctx->sb, ctx->d_kperm,
+                              ctx->d_kinv, ctx->stream, &ctx->prof);
+    if (l < 0) return fail(ctx, VBGS_ECUDA, "component ordering failed");
+    ctx->launches += 2;
+    if (points && N > 0) {
+        l = launch_point_order(ctx->d_X, N, ctx->box, ctx->sb, ctx->d_Xs, ctx->d_pidx, ctx->stream, &ctx->prof);
+        if (l < 0) return fail(ctx, VBGS_ECUDA, "point ordering failed");
+        ctx->launches += 2;
+        ctx->last_sorted = true;
+    }
     return VBGS_OK;
 }
 
@@ -181,7 +221,7 @@ int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
         return VBGS_OK;
     }
     EstepBuffers B;
-    B.X = ctx->d_X;
+    B.X = ctx->last_sorted ? ctx->d_Xs : ctx->d_X;
     B.N = N;
     B.K = ctx->K;
     B.rec = ctx->d_rec;
@@ -192,6 +232,10 @@ int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
     B.part = ctx->d_part;
     B.part_cap = ctx->part_cap;
     B.dS = ctx->d_dS;
+    B.kperm = ctx->d_kperm;
+    const bool skip = want_stats && !(ctx->flags & VBGS_FLAG_NO_SKIP);
+    B.tmax = skip ? ctx->d_tmax : nullptr;
+    B.minlse = skip ? ctx->d_minlse : nullptr;
     int l = launch_estep_cuda_core(B, ctx->precision, want_stats, ctx->stream, &ctx->prof);
     if (l < 0) return fail(ctx, VBGS_ECUDA, "E-step launch failed (%d): %s", l,
                            cudaGetErrorString(cudaGetLastError()));
@@ -216,7 +260,9 @@ void free_all(vbgs_ctx *ctx)
 {
     void *ptrs[] = {ctx->d_m0, ctx->d_Spast, ctx->d_dS, ctx->d_zero, ctx->d_rec, ctx->d_rec32,
                     ctx->d_klk, ctx->d_aq, ctx->d_ap, ctx->d_dN, ctx->d_scal, ctx->d_elbo,
-                    ctx->d_flags, ctx->d_X, ctx->d_lse, ctx->d_lse_part, ctx->d_part};
+                    ctx->d_flags, ctx->d_X, ctx->d_lse, ctx->d_lse_part, ctx->d_part,
+                    ctx->d_kperm, ctx->d_kinv, ctx->d_pidx, ctx->d_Xs, ctx->d_tmax, ctx->d_minlse,
+                    ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
@@ -254,6 +300,21 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     ctx = new vbgs_ctx();
     ctx->K = K;
     ctx->precision = precision;
+    ctx->flags = opt ? opt->flags : 0;
+    {
+        // Morton box: bounding box of the prior means, padded by 10%.
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int k = 0; k < K; k++)
+            for (int i = 0; i < 3; i++) {
+                lo[i] = std::min(lo[i], prior->m0[(size_t)k * 6 + i]);
+                hi[i] = std::max(hi[i], prior->m0[(size_t)k * 6 + i]);
+            }
+        for (int i = 0; i < 3; i++) {
+            double pad = 0.1 * (hi[i] - lo[i]) + 1e-6;
+            ctx->box.lo[i] = lo[i] - pad;
+            ctx->box.inv_ext[i] = 1.0 / (hi[i] - lo[i] + 2 * pad);
+        }
+    }
     ctx->stream = opt ? (cudaStream_t)opt->cuda_stream : nullptr;
     ctx->mp.alpha0 = prior->alpha0;
     ctx->mp.beta0 = prior->beta0;
@@ -269,7 +330,8 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
         (rc = dalloc(ctx, &ctx->d_rec32, (size_t)K * VBGS_REC)) || (rc = dalloc(ctx, &ctx->d_klk, (size_t)K)) ||
         (rc = dalloc(ctx, &ctx->d_aq, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_ap, (size_t)K)) ||
         (rc = dalloc(ctx, &ctx->d_dN, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_scal, (size_t)SC_COUNT)) ||
-        (rc = dalloc(ctx, &ctx->d_flags, (size_t)FL_COUNT)) || (rc = ensure_elbo(ctx, 64))) {
+        (rc = dalloc(ctx, &ctx->d_flags, (size_t)FL_COUNT)) || (rc = ensure_elbo(ctx, 64)) ||
+        (rc = dalloc(ctx, &ctx->d_kperm, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_kinv, (size_t)K))) {
         g_err = ctx->err;
         free_all(ctx);
         delete ctx;
@@ -295,6 +357,13 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     CU(cudaMemsetAsync(ctx->d_dS, 0, sizeof(double) * KF, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_scal, 0, sizeof(double) * SC_COUNT, ctx->stream));
+    {
+        std::vector<int> ident(K);
+        for (int k = 0; k < K; k++) ident[k] = k;
+        CU(cudaMemcpyAsync(ctx->d_kperm, ident.data(), sizeof(int) * K, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(ctx->d_kinv, ident.data(), sizeof(int) * K, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
     if ((rc = run_mstep(ctx, nullptr))) return init_fail(rc);
     CU(cudaStreamSynchronize(ctx->stream));
 #undef CU
@@ -319,6 +388,7 @@ int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, dou
     if ((rc = ensure_capacity(ctx, N)) || (rc = ensure_elbo(ctx, n_iters))) return rc;
     if ((rc = stage_points(ctx, points, N))) return rc;
     CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    if ((rc = order_frame(ctx, N, true))) return rc;
     // Posterior entering the frame: the effective prior prior0 (+) S_past.
     if ((rc = run_mstep(ctx, nullptr))) return rc;
     for (int it = 0; it < n_iters; it++) {
@@ -348,6 +418,7 @@ int vbgs_elbo(vbgs_ctx *ctx, const double *points, int64_t N, double *elbo_out, 
     if ((rc = ensure_capacity(ctx, N)) || (rc = ensure_elbo(ctx, 1))) return rc;
     if ((rc = stage_points(ctx, points, N))) return rc;
     CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    ctx->last_sorted = false;
     if ((rc = run_mstep(ctx, nullptr))) return rc;
     if ((rc = run_estep(ctx, N, false))) return rc;
     if (launch_elbo(ctx->d_scal, N, ctx->d_elbo, ctx->stream, &ctx->prof) < 0)
@@ -370,7 +441,15 @@ int vbgs_get_lse(vbgs_ctx *ctx, double *lse, int64_t N)
     CU(cudaMemcpyAsync(&psi, ctx->d_scal + SC_PSI_ESTEP, sizeof(double), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    // The device keeps lse without the -psi(sum alpha) shared by every logit.
+    // The device keeps lse without the -psi(sum alpha) shared by every logit,
+    // in processing order.
+    if (ctx->last_sorted) {
+        std::vector<int> pidx((size_t)N);
+        std::vector<double> tmp(lse, lse + N);
+        CU(cudaMemcpyAsync(pidx.data(), ctx->d_pidx, sizeof(int) * N, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        for (int64_t i = 0; i < N; i++) lse[pidx[(size_t)i]] = tmp[(size_t)i];
+    }
     for (int64_t n = 0; n < N; n++) lse[n] -= psi;
     return VBGS_OK;
 }

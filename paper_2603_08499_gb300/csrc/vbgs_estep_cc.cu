@@ -71,16 +71,21 @@ __device__ __forceinline__ T logit(const T *__restrict__ r, const T x[6])
 }
 
 // Pass 1.  grid = (point blocks, K splits).  part[split * N + n] = (max, sum)
-// with max in natural units and sum = sum_k exp(l_k - max).
+// with max in natural units and sum = sum_k exp(l_k - max).  When tmax is
+// given, also the largest logit of every (256-point block, 64-component
+// chunk) in natural units, tmax[block * nkc + chunk]; this needs kps to be a
+// multiple of kChunkK so chunks align across splits.
 template <typename T, int PPT>
 __global__ void __launch_bounds__(kThreads) k_pass1(const double *__restrict__ X, int64_t N,
                                                     const T *__restrict__ rec, int K, int kps,
-                                                    double2 *__restrict__ part)
+                                                    double2 *__restrict__ part, float *__restrict__ tmax)
 {
     __shared__ T srec[kChunkK * 28];
+    __shared__ float sred[kThreads / 32];
     const int split = blockIdx.y;
     const int k0 = split * kps;
     const int k1 = min(K, k0 + kps);
+    const int nkc = (K + kChunkK - 1) / kChunkK;
     T x[PPT][6], mx[PPT], s[PPT];
     int64_t nb = (int64_t)blockIdx.x * kThreads * PPT + threadIdx.x;
 #pragma unroll
@@ -98,17 +103,32 @@ __global__ void __launch_bounds__(kThreads) k_pass1(const double *__restrict__ X
         for (int i = threadIdx.x; i < cnt * 28; i += kThreads)
             srec[i] = rec[(size_t)(kc + i / 28) * VBGS_REC + (i % 28)];
         __syncthreads();
+        T cmax = -INFINITY;
         for (int j = 0; j < cnt; j++) {
             const T *r = srec + j * 28;
 #pragma unroll
             for (int p = 0; p < PPT; p++) {
                 T l = logit<T>(r, x[p]);
+                cmax = l > cmax ? l : cmax;
                 if (l > mx[p]) {
                     s[p] = fma(s[p], Arith<T>::expd(mx[p] - l), T(1));
                     mx[p] = l;
                 } else {
                     s[p] += Arith<T>::expd(l - mx[p]);
                 }
+            }
+        }
+        if (tmax) {
+            float v = (float)((double)cmax / (double)Arith<T>::lse_scale());
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = v;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float w = sred[0];
+#pragma unroll
+                for (int i = 1; i < kThreads / 32; i++) w = fmaxf(w, sred[i]);
+                tmax[(size_t)blockIdx.x * nkc + kc / kChunkK] = w;
             }
         }
     }
@@ -124,9 +144,11 @@ __global__ void __launch_bounds__(kThreads) k_pass1(const double *__restrict__ X
 
 // Merge the K-split partials into lse_n and per-block sums of lse (fixed order).
 __global__ void __launch_bounds__(256) k_merge(const double2 *__restrict__ part, int nsplit, int64_t N,
-                                               double *__restrict__ lse, double *__restrict__ lse_part)
+                                               double *__restrict__ lse, double *__restrict__ lse_part,
+                                               float *__restrict__ minlse)
 {
     __shared__ double sh[8];
+    __shared__ float shm[8];
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
     if (n < N) {
@@ -140,14 +162,20 @@ __global__ void __launch_bounds__(256) k_merge(const double2 *__restrict__ part,
         v = M + log(s);
         lse[n] = v;
     }
+    float vm = n < N ? (float)v : INFINITY;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_down_sync(0xffffffffu, v, o);
+        vm = fminf(vm, __shfl_down_sync(0xffffffffu, vm, o));
+    }
+    if ((threadIdx.x & 31) == 0) { sh[threadIdx.x >> 5] = v; shm[threadIdx.x >> 5] = vm; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += sh[i];
+        float tm = INFINITY;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) { t += sh[i]; tm = fminf(tm, shm[i]); }
         lse_part[blockIdx.x] = t;
+        if (minlse) minlse[blockIdx.x] = tm;
     }
 }
 
@@ -172,11 +200,16 @@ __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ v, int 
 // d = x - a_k about the component's anchor a_k = m_k (the record's mean), so
 // that FP32 accumulation never forms the large, cancelling raw second
 // moments; k_reduce_splits shifts them back to raw moments in FP64.
+// With tmax/minlse (nps a multiple of 256), a 64-point chunk is skipped when
+// the tile's two 64-component chunk maxima minus the min lse of the chunk's
+// 256-point block are below -kSkipNats (uniform across the CTA).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X,
                                                     const double *__restrict__ lse, int64_t N,
                                                     int64_t nps, const T *__restrict__ rec, int K,
-                                                    double *__restrict__ part)
+                                                    double *__restrict__ part,
+                                                    const float *__restrict__ tmax,
+                                                    const float *__restrict__ minlse)
 {
     constexpr bool kAnchored = sizeof(T) == 4;
     __shared__ T spt[kChunkN * 28];   // per point: x[6], lse, upper(x x^T)[21] (FP64 only)
@@ -192,8 +225,16 @@ __global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X
 #pragma unroll
     for (int f = 0; f < 28; f++) acc[f] = T(0);
 
+    const int nkc = (K + kChunkK - 1) / kChunkK;
+    const int c0 = blockIdx.x * (kThreads / kChunkK);
     for (int64_t nc = n0; nc < n1; nc += kChunkN) {
         const int cnt = (int)min((int64_t)kChunkN, n1 - nc);
+        if (tmax) {
+            const int64_t pb = nc / 256;
+            float b = tmax[pb * nkc + c0];
+            if (c0 + 1 < nkc) b = fmaxf(b, tmax[pb * nkc + c0 + 1]);
+            if (b - minlse[pb] < -(float)kSkipNats) continue;
+        }
         __syncthreads();
         for (int p = threadIdx.x; p < cnt; p += kThreads) {
             const double *xp = X + (nc + p) * VBGS_XS;
@@ -246,7 +287,8 @@ __global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X
 // the split sums are moments about a_k and are shifted to raw moments:
 //   S1 = S1' + N a,  S2 = S2' + a S1'^T + S1' a^T + N a a^T   (FP64).
 __global__ void k_reduce_splits(const double *__restrict__ part, int nsplit, int K,
-                                const float *__restrict__ anchor, double *__restrict__ dS)
+                                const float *__restrict__ anchor, const int *__restrict__ kperm,
+                                double *__restrict__ dS)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
@@ -271,8 +313,9 @@ __global__ void k_reduce_splits(const double *__restrict__ part, int nsplit, int
 #pragma unroll
         for (int i = 0; i < 6; i++) s[1 + i] += s[0] * a[i];
     }
+    const size_t out = kperm ? (size_t)kperm[k] : (size_t)k;
 #pragma unroll
-    for (int f = 0; f < 28; f++) dS[(size_t)k * 28 + f] = s[f];
+    for (int f = 0; f < 28; f++) dS[out * 28 + f] = s[f];
 }
 
 struct Plan {
@@ -291,12 +334,14 @@ Plan make_plan(int64_t N, int K, int num_sms)
     int s1 = std::max(1, (target + pl.p1_blocks - 1) / std::max(1, pl.p1_blocks));
     s1 = std::min(s1, std::max(1, K / 16));
     pl.kps = (K + s1 - 1) / s1;
+    pl.kps = (pl.kps + kChunkK - 1) / kChunkK * kChunkK;   // chunk-aligned splits (tile maxima)
     pl.p1_splits = (K + pl.kps - 1) / pl.kps;
     pl.p2_tiles = (K + kThreads - 1) / kThreads;
     int64_t s2 = std::max<int64_t>(1, (target + pl.p2_tiles - 1) / pl.p2_tiles);
     s2 = std::min<int64_t>(s2, std::max<int64_t>(1, N / 64));
     s2 = std::min<int64_t>(s2, 1024);
     pl.nps = (N + s2 - 1) / s2;
+    pl.nps = (pl.nps + 255) / 256 * 256;                   // block-aligned splits (skip bound)
     pl.p2_splits = (int)((N + pl.nps - 1) / pl.nps);
     pl.scratch = std::max((size_t)pl.p1_splits * (size_t)N * 2, (size_t)pl.p2_splits * (size_t)K * 28);
     return pl;
@@ -329,12 +374,13 @@ int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats
     double2 *p1 = reinterpret_cast<double2 *>(B.part);
     dim3 g1(pl.p1_blocks, pl.p1_splits);
     pf->begin(VBGS_PROF_PASS1, st);
-    if (f64) k_pass1<double, kPPT64><<<g1, kThreads, 0, st>>>(B.X, B.N, B.rec, B.K, pl.kps, p1);
-    else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(B.X, B.N, B.rec32, B.K, pl.kps, p1);
+    float *tmax = want_stats ? B.tmax : nullptr;
+    if (f64) k_pass1<double, kPPT64><<<g1, kThreads, 0, st>>>(B.X, B.N, B.rec, B.K, pl.kps, p1, tmax);
+    else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(B.X, B.N, B.rec32, B.K, pl.kps, p1, tmax);
     pf->end(st);
     const int mb = (int)((B.N + 255) / 256);
     pf->begin(VBGS_PROF_MERGE, st);
-    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, B.N, B.lse, B.lse_part);
+    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, B.N, B.lse, B.lse_part, tmax ? B.minlse : nullptr);
     pf->end(st);
     pf->begin(VBGS_PROF_MERGE, st);
     k_sum<<<1, 1024, 0, st>>>(B.lse_part, mb, B.scal + SC_SUM_LSE);
@@ -343,12 +389,14 @@ int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats
     if (want_stats) {
         dim3 g2(pl.p2_tiles, pl.p2_splits);
         pf->begin(VBGS_PROF_PASS2, st);
-        if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec, B.K, B.part);
-        else     k_pass2<float><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec32, B.K, B.part);
+        if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec, B.K, B.part,
+                                                          tmax, B.minlse);
+        else     k_pass2<float><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec32, B.K, B.part,
+                                                         tmax, B.minlse);
         pf->end(st);
         pf->begin(VBGS_PROF_REDUCE, st);
         k_reduce_splits<<<(B.K + 127) / 128, 128, 0, st>>>(B.part, pl.p2_splits, B.K,
-                                                          f64 ? nullptr : B.rec32, B.dS);
+                                                          f64 ? nullptr : B.rec32, B.kperm, B.dS);
         pf->end(st);
         launches += 2;
     }
@@ -485,15 +533,15 @@ extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N
 
     double2 *p1 = reinterpret_cast<double2 *>(part);
     dim3 g1(pl.p1_blocks, pl.p1_splits);
-    if (f64) k_pass1<double, kPPT64><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec, K, pl.kps, p1);
-    else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec32, K, pl.kps, p1);
-    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, lse_out, base + o_lsep);
+    if (f64) k_pass1<double, kPPT64><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec, K, pl.kps, p1, nullptr);
+    else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec32, K, pl.kps, p1, nullptr);
+    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, lse_out, base + o_lsep, nullptr);
     k_sum<<<1, 1024, 0, st>>>(base + o_lsep, mb, scal + SC_SUM_LSE);
     dim3 g2(pl.p2_tiles, pl.p2_splits);
-    if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part);
-    else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part);
+    if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part, nullptr, nullptr);
+    else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part, nullptr, nullptr);
     k_reduce_splits<<<(K + 127) / 128, 128, 0, st>>>(part, pl.p2_splits, K, f64 ? nullptr : ctx->d_rec32,
-                                                    dS_out);
+                                                    ctx->d_kperm, dS_out);
     k_lse_subtract_psi<<<mb, 256, 0, st>>>(lse_out, N, ctx->d_scal);
     if (cudaGetLastError() != cudaSuccess) return noalloc_fail(ctx, VBGS_ECUDA, "vbgs_estep_noalloc: launch failed");
     ctx->launches = 7;

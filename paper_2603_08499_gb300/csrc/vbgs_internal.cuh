@@ -87,6 +87,24 @@ struct MstepParams {
     int K;
 };
 
+// Box of the Morton codes (positions only).
+struct BoxParams {
+    double lo[3], inv_ext[3];
+};
+
+struct SortBuffers {
+    uint32_t *keys_in = nullptr, *keys_out = nullptr;
+    int *idx_in = nullptr;
+    void *temp = nullptr;
+    size_t temp_bytes = 0;
+    int64_t cap = 0;
+};
+
+// Pass 2 skips a (64-point chunk, 128-component tile) when the tile's largest
+// logit minus the smallest lse of the chunk's 256-point block is below this
+// (natural units): every skipped r_nk < e^-50 < 2e-22.
+constexpr double kSkipNats = 50.0;
+
 // Arguments of one E-step (pass 1 + pass 2) over a staged frame.
 struct EstepBuffers {
     const double *X;      // N x 8
@@ -100,13 +118,21 @@ struct EstepBuffers {
     double *part;         // scratch for split partials
     size_t part_cap;      // doubles
     double *dS;           // K x 28
+    const int *kperm;     // position -> component (nullptr: identity)
+    float *tmax;          // pass-1 tile maxima [N/256][K/64] (nullptr: no skipping)
+    float *minlse;        // per 256-point block min of lse
 };
 
 // ---- kernels / launchers (return number of launches, or -1 on error) ----
 int launch_stage_points(const double *src, int64_t N, double *X, int *flags, cudaStream_t st, Prof *pf);
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
-                 double *rec, float *rec32, double *klk, double *aq, double *ap, double *dN,
-                 int *flags, double *scal, cudaStream_t st, Prof *pf);
+                 const int *kinv, double *rec, float *rec32, double *klk, double *aq, double *ap,
+                 double *dN, int *flags, double *scal, cudaStream_t st, Prof *pf);
+size_t sort_temp_bytes(int64_t n);
+int launch_point_order(const double *X, int64_t N, const BoxParams &box, SortBuffers &sb, double *Xs,
+                       int *pidx, cudaStream_t st, Prof *pf);
+int launch_comp_order(const double *m0, const double *Spast, int K, double beta0, const BoxParams &box,
+                      SortBuffers &sb, int *kperm, int *kinv, cudaStream_t st, Prof *pf);
 int launch_commit(double *Spast, const double *dS, int K, const int *flags, cudaStream_t st, Prof *pf);
 int launch_elbo(double *scal, int64_t N, double *elbo_out, cudaStream_t st, Prof *pf);
 
@@ -120,7 +146,15 @@ size_t estep_cuda_core_scratch(int64_t N, int K, int precision);
 struct vbgs_ctx {
     int K = 0, D = 6;
     int precision = VBGS_FP64;
+    int flags = 0;
     cudaStream_t stream = nullptr;
+    vbgs::BoxParams box{};
+    vbgs::SortBuffers sb;
+    int *d_kperm = nullptr, *d_kinv = nullptr, *d_pidx = nullptr;
+    double *d_Xs = nullptr;          // staged points in Morton order
+    float *d_tmax = nullptr, *d_minlse = nullptr;
+    size_t tmax_cap = 0;
+    bool last_sorted = false;
     vbgs::MstepParams mp{};
     std::vector<double> m0_h;
     double *d_m0 = nullptr, *d_Spast = nullptr, *d_dS = nullptr, *d_zero = nullptr;

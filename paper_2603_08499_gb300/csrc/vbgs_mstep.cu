@@ -122,6 +122,7 @@ __device__ void trinv6(const double L[36], double Li[36])
 __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__restrict__ m0,
                                                const double *__restrict__ Spast,
                                                const double *__restrict__ dS,
+                                               const int *__restrict__ kinv,
                                                double *__restrict__ rec, float *__restrict__ rec32,
                                                double *__restrict__ klk, double *__restrict__ aq_out,
                                                double *__restrict__ ap_out, double *__restrict__ dN_out,
@@ -154,8 +155,9 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
 
     // E-step record: quad = nu |L^-1 (x - m)|^2 = |M (x - m)|^2.
     const double sn = sqrt(nq);
-    double *r = rec + (size_t)k * VBGS_REC;
-    float *r32 = rec32 + (size_t)k * VBGS_REC;
+    const size_t pos = kinv ? (size_t)kinv[k] : (size_t)k;   // record position (processing order)
+    double *r = rec + pos * VBGS_REC;
+    float *r32 = rec32 + pos * VBGS_REC;
     const float s2 = 1.2011224087864498f;   // sqrt(log2 e): FP32 record in log2 units
 #pragma unroll
     for (int i = 0; i < 6; i++) { r[i] = mq[i]; r32[i] = (float)mq[i]; }
@@ -279,12 +281,12 @@ __global__ void k_stage(const double *__restrict__ src, int64_t N, double *__res
 } // namespace
 
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
-                 double *rec, float *rec32, double *klk, double *aq, double *ap, double *dN,
-                 int *flags, double *scal, cudaStream_t st, Prof *pf)
+                 const int *kinv, double *rec, float *rec32, double *klk, double *aq, double *ap,
+                 double *dN, int *flags, double *scal, cudaStream_t st, Prof *pf)
 {
     const int K = P.K;
     pf->begin(VBGS_PROF_MSTEP, st);
-    k_mstep<<<(K + 127) / 128, 128, 0, st>>>(P, m0, Spast, dS, rec, rec32, klk, aq, ap, dN, flags);
+    k_mstep<<<(K + 127) / 128, 128, 0, st>>>(P, m0, Spast, dS, kinv, rec, rec32, klk, aq, ap, dN, flags);
     pf->end(st);
     pf->begin(VBGS_PROF_MSTEP, st);
     k_mstep_finalize<<<1, 1024, 0, st>>>(klk, aq, ap, dN, K, scal);

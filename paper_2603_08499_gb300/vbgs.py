@@ -30,6 +30,9 @@ VBGS_FP16X3 = 1
 VBGS_BF16X3 = 2
 VBGS_FP32 = 3
 PRECISIONS = {"fp64": VBGS_FP64, "fp16x3": VBGS_FP16X3, "bf16x3": VBGS_BF16X3, "fp32": VBGS_FP32}
+VBGS_FLAG_NO_REORDER = 1
+VBGS_FLAG_NO_SKIP = 2
+VBGS_FLAG_PLAIN = VBGS_FLAG_NO_REORDER | VBGS_FLAG_NO_SKIP
 
 D = 6
 F = 28
@@ -53,7 +56,7 @@ class VbgsError(RuntimeError):
 
 
 class vbgs_options(C.Structure):
-    _fields_ = [("precision", C.c_int), ("reserved0", C.c_int), ("cuda_stream", C.c_void_p),
+    _fields_ = [("precision", C.c_int), ("flags", C.c_int), ("cuda_stream", C.c_void_p),
                 ("reserved1", C.c_uint64)]
 
 
@@ -140,12 +143,12 @@ def _points_ptr(points):
 # ---- C-named functions ------------------------------------------------------
 
 def vbgs_init(alpha0: float, beta0: float, nu0: float, m0, W0, precision: int = VBGS_FP64,
-              cuda_stream: int | None = None):
+              cuda_stream: int | None = None, flags: int = 0):
     m0a = _host_f64(m0)
     K = m0a.shape[0]
     W0a = _host_f64(W0, (D, D))
     pr = vbgs_prior(alpha0, beta0, nu0, _dp(m0a), _dp(W0a))
-    opt = vbgs_options(int(precision), 0, C.c_void_p(cuda_stream or None), 0)
+    opt = vbgs_options(int(precision), int(flags), C.c_void_p(cuda_stream or None), 0)
     ctx = C.c_void_p()
     _check(lib().vbgs_init(C.byref(ctx), C.byref(pr), K, m0a.shape[1], C.byref(opt)), None)
     return ctx
@@ -243,11 +246,13 @@ def vbgs_destroy(ctx) -> None:
 class Model:
     """One VBGS mixture on the GPU (owns a vbgs_ctx)."""
 
-    def __init__(self, prior: dict, precision: str | int = "fp64", cuda_stream: int | None = None):
+    def __init__(self, prior: dict, precision: str | int = "fp64", cuda_stream: int | None = None,
+                 flags: int = 0):
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.K = int(np.asarray(prior["m0"]).shape[0])
+        self.ctx = None
         self.ctx = vbgs_init(prior["alpha0"], prior["beta0"], prior["nu0"], prior["m0"], prior["W0"],
-                             p, cuda_stream)
+                             p, cuda_stream, flags)
 
     def update(self, points, n_iters: int) -> np.ndarray:
         return vbgs_update(self.ctx, points, n_iters)

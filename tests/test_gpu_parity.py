@@ -29,10 +29,10 @@ def stat_errors(S_gpu, S_ref):
             "S2": O.relerr(S_gpu[:, 7:], S_ref[:, 7:])}
 
 
-def check_frame(V, X, prior, n_iters, form, S_past=None):
+def check_frame(V, X, prior, n_iters, form, S_past=None, flags=0):
     K = prior["m0"].shape[0]
     S_past = np.zeros((K, 28)) if S_past is None else S_past
-    m = V.Model(prior, form)
+    m = V.Model(prior, form, flags=flags)
     if np.any(S_past):
         m.set_stats(S_past)
     trace = m.update(X, n_iters)
@@ -58,11 +58,34 @@ def test_mixture_small_several_tiles_ragged(V, form):
     check_frame(V, X, pr, 6, form)
 
 
-def test_mixture_full_size_fp64(V):
-    """10,000 points, 1,000 components, 10 CAVI iterations (the full plain FP64 workload)."""
+@pytest.mark.parametrize("flags", [0, 3])
+def test_mixture_full_size_fp64(V, flags):
+    """10,000 points, 1,000 components, 10 CAVI iterations (the full plain FP64
+    workload), with Morton order + pass-2 tile skipping (flags 0) and in the
+    caller's order with every tile evaluated (the plain form, flags 3)."""
     X, pr = synth.c1_workload(seed=1, N=10_000, K=1_000)
-    trace, ref = check_frame(V, X, pr, 10, "fp64")
+    trace, ref = check_frame(V, X, pr, 10, "fp64", flags=flags)
     assert np.all(np.diff(trace) >= -1e-9 * abs(trace[-1]))
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32"])
+def test_skip_and_order_change_nothing_beyond_rounding(V, form):
+    room = synth.Room(seed=8)
+    pr = synth.room_prior(2_000, seed=8)
+    X = synth.room_frame(0, seed=8, width=100, height=100, room=room)
+    out = {}
+    for flags in (0, 1, 2, 3):
+        m = V.Model(pr, form, flags=flags)
+        tr = m.update(X, 3)
+        out[flags] = (tr, m.stats(), m.lse(X.shape[0]))
+        m.close()
+    # the FP64 parity bar: rounding differences of another summation order,
+    # amplified over 3 iterations by the raw-moment update on thin surfaces
+    tol = TOL[form]["stat"] if form == "fp64" else 1e-5
+    for f in (1, 2, 3):
+        assert O.relerr(out[f][0], out[0][0]) <= tol
+        assert O.relerr(out[f][1], out[0][1]) <= tol
+        assert O.relerr(out[f][2], out[0][2]) <= tol
 
 
 def test_mixture_full_size_fp32(V):
@@ -160,7 +183,8 @@ def test_invalid_points_leave_state_unchanged(V):
         m.set_stats(np.full((20, 28), np.nan))
 
 
-def test_full_size_room_frame_sampled(V):
+@pytest.mark.parametrize("form", ["fp64", "fp32"])
+def test_full_size_room_frame_sampled(V, form):
     """The benchmark shape (K = 50,000, one 200 x 200 frame, 3 iterations) in
     the launch configuration the benchmark uses: invariants at full size and
     sampled per-point lse checked one by one against the oracle."""
@@ -168,21 +192,22 @@ def test_full_size_room_frame_sampled(V):
     room = synth.Room(seed=2)
     pr = synth.room_prior(50_000, seed=2)
     X = synth.room_frame(0, seed=2, room=room)
-    m = V.Model(pr, "fp64")
+    tol = TOL[form]["lse"] if form == "fp32" else 1e-12
+    m = V.Model(pr, form)
     trace = m.update(torch.from_numpy(X).cuda(), 3)
     dS = m.frame_stats()
     N = X.shape[0]
-    assert abs(dS[:, 0].sum() - N) <= 1e-9 * N
-    assert O.relerr(dS[:, 1:7].sum(0), X.sum(0)) <= 1e-12
-    assert np.all(np.diff(trace) >= -1e-9 * abs(trace[-1]))
+    assert abs(dS[:, 0].sum() - N) <= (1e-9 if form == "fp64" else 1e-4) * N
+    assert O.relerr(dS[:, 1:7].sum(0), X.sum(0)) <= (1e-12 if form == "fp64" else 1e-4)
+    assert np.all(np.diff(trace) >= -(1e-9 if form == "fp64" else 1e-6) * abs(trace[-1]))
     # the ELBO of the first iteration is under the prior: check sampled points
-    m2 = V.Model(pr, "fp64")
+    m2 = V.Model(pr, form)
     e, lse = m2.elbo(X, want_lse=True)
     idx = np.random.default_rng(0).choice(N, 64, replace=False)
     post0 = O.mstep(pr, np.zeros((50_000, 28)))
     lse_ref, _, _ = O.estep_stats(X[idx], post0)
-    assert O.relerr(lse[idx], lse_ref) <= 1e-12
-    assert O.relerr(e, trace[0]) <= 1e-12
+    assert O.relerr(lse[idx], lse_ref) <= tol
+    assert O.relerr(e, trace[0]) <= tol
 
 
 def test_profile_counts_launches(V):
