@@ -108,6 +108,8 @@ int dalloc(vbgs_ctx *ctx, T **p, size_t n)
     return VBGS_OK;
 }
 
+bool is_tc(const vbgs_ctx *ctx) { return ctx->precision == VBGS_FP16X3 || ctx->precision == VBGS_BF16X3; }
+
 // Make the per-frame buffers large enough for N points.
 int ensure_capacity(vbgs_ctx *ctx, int64_t N)
 {
@@ -119,7 +121,7 @@ int ensure_capacity(vbgs_ctx *ctx, int64_t N)
         if ((rc = dalloc(ctx, &ctx->d_lse_part, (size_t)(cap + 255) / 256 + 1))) return rc;
         if ((rc = dalloc(ctx, &ctx->d_Xs, (size_t)cap * VBGS_XS))) return rc;
         if ((rc = dalloc(ctx, &ctx->d_pidx, (size_t)cap))) return rc;
-        if ((rc = dalloc(ctx, &ctx->d_minlse, (size_t)(cap + 255) / 256 + 1))) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_minlse, (size_t)(cap + 31) / 32 + 1))) return rc;
         ctx->ncap = cap;
     }
     const int64_t scap = std::max<int64_t>(ctx->ncap, ctx->K);
@@ -135,12 +137,15 @@ int ensure_capacity(vbgs_ctx *ctx, int64_t N)
         ctx->sb.temp_bytes = tb;
         ctx->sb.cap = scap;
     }
-    const size_t tneed = (size_t)((std::max<int64_t>(N, 1) + 255) / 256) * (size_t)((ctx->K + 63) / 64);
+    const size_t tneed = std::max((size_t)((std::max<int64_t>(N, 1) + 255) / 256) * (size_t)((ctx->K + 63) / 64),
+                                  tc_tmax_floats(std::max<int64_t>(N, 1), ctx->K));
     if (tneed > ctx->tmax_cap) {
         if ((rc = dalloc(ctx, &ctx->d_tmax, tneed))) return rc;
         ctx->tmax_cap = tneed;
     }
-    size_t need = estep_cuda_core_scratch(std::max<int64_t>(N, 1), ctx->K, ctx->precision);
+    size_t need = estep_cuda_core_scratch(std::max<int64_t>(N, 1), ctx->K, is_tc(ctx) ? VBGS_FP32 : ctx->precision);
+    if (is_tc(ctx))   // pass-1 partials of up to 64 K-splits
+        need = std::max(need, (size_t)64 * (size_t)std::max<int64_t>(N, 1) * 2);
     if (need > ctx->part_cap) {
         if ((rc = dalloc(ctx, &ctx->d_part, need))) return rc;
         ctx->part_cap = need;
@@ -186,11 +191,16 @@ int stage_points(vbgs_ctx *ctx, const double *points, int64_t N)
 
 int run_mstep(vbgs_ctx *ctx, const double *dS)
 {
-    int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_kinv, ctx->d_rec, ctx->d_rec32, ctx->d_klk,
-                         ctx->d_aq, ctx->d_ap, ctx->d_dN, ctx->d_flags, ctx->d_scal, ctx->stream,
-                         &ctx->prof);
+    int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_kinv, ctx->d_rec, ctx->d_rec32, ctx->d_pcache,
+                         ctx->d_flags, ctx->d_scal, ctx->stream, &ctx->prof);
     if (l < 0) return fail(ctx, VBGS_ECUDA, "posterior update launch failed");
     ctx->launches += l;
+    if (is_tc(ctx)) {
+        l = launch_coef_tiles(ctx->d_rec, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
+                              ctx->stream, &ctx->prof);
+        if (l < 0) return fail(ctx, VBGS_ECUDA, "coefficient tile launch failed");
+        ctx->launches += l;
+    }
     return VBGS_OK;
 }
 
@@ -236,6 +246,27 @@ int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
     const bool skip = want_stats && !(ctx->flags & VBGS_FLAG_NO_SKIP);
     B.tmax = skip ? ctx->d_tmax : nullptr;
     B.minlse = skip ? ctx->d_minlse : nullptr;
+    if (is_tc(ctx)) {
+        int splits = 1;
+        int l = launch_pass1_tc(B.X, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
+                                reinterpret_cast<double2 *>(ctx->d_part), ctx->part_cap, B.tmax, ctx->d_flags,
+                                ctx->num_sms, &splits, ctx->stream, &ctx->prof);
+        if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        ctx->launches += l;
+        l = launch_lse_merge(reinterpret_cast<double2 *>(ctx->d_part), splits, N, ctx->d_lse, ctx->d_lse_part,
+                             B.tmax ? ctx->d_minlse : nullptr, ctx->d_scal + SC_SUM_LSE, ctx->stream, &ctx->prof);
+        if (l < 0) return fail(ctx, VBGS_ECUDA, "lse merge launch failed");
+        ctx->launches += l;
+        if (want_stats) {
+            l = launch_pass2_tc(B.X, ctx->d_lse, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
+                                B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_part, ctx->part_cap, ctx->d_kperm,
+                                ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->stream, &ctx->prof);
+            if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
+                                   cudaGetErrorString(cudaGetLastError()));
+            ctx->launches += l;
+        }
+        return VBGS_OK;
+    }
     int l = launch_estep_cuda_core(B, ctx->precision, want_stats, ctx->stream, &ctx->prof);
     if (l < 0) return fail(ctx, VBGS_ECUDA, "E-step launch failed (%d): %s", l,
                            cudaGetErrorString(cudaGetLastError()));
@@ -259,10 +290,10 @@ int check_flags(vbgs_ctx *ctx)
 void free_all(vbgs_ctx *ctx)
 {
     void *ptrs[] = {ctx->d_m0, ctx->d_Spast, ctx->d_dS, ctx->d_zero, ctx->d_rec, ctx->d_rec32,
-                    ctx->d_klk, ctx->d_aq, ctx->d_ap, ctx->d_dN, ctx->d_scal, ctx->d_elbo,
+                    ctx->d_pcache, ctx->d_scal, ctx->d_elbo,
                     ctx->d_flags, ctx->d_X, ctx->d_lse, ctx->d_lse_part, ctx->d_part,
                     ctx->d_kperm, ctx->d_kinv, ctx->d_pidx, ctx->d_Xs, ctx->d_tmax, ctx->d_minlse,
-                    ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp};
+                    ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp, ctx->d_tc_tiles, ctx->d_tc_hdr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
@@ -285,8 +316,8 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
         !std::isfinite(prior->alpha0) || !std::isfinite(prior->beta0) || !std::isfinite(prior->nu0))
         return fail(nullptr, VBGS_EINVAL, "need alpha0 > 0, beta0 > 0, nu0 > D - 1");
     int precision = opt ? opt->precision : VBGS_FP64;
-    if (precision != VBGS_FP64 && precision != VBGS_FP32)
-        return fail(nullptr, VBGS_EINVAL, "precision %d is not available in this build", precision);
+    if (precision != VBGS_FP64 && precision != VBGS_FP32 && precision != VBGS_FP16X3 && precision != VBGS_BF16X3)
+        return fail(nullptr, VBGS_EINVAL, "unknown precision %d", precision);
     for (size_t i = 0; i < (size_t)K * 6; i++)
         if (!std::isfinite(prior->m0[i])) return fail(nullptr, VBGS_EINVAL, "non-finite m0");
     double W0[36], W0inv[36];
@@ -301,6 +332,13 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     ctx->K = K;
     ctx->precision = precision;
     ctx->flags = opt ? opt->flags : 0;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+        if (ctx->num_sms <= 0) ctx->num_sms = 152;
+    }
     {
         // Morton box: bounding box of the prior means, padded by 10%.
         double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -327,11 +365,11 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     const size_t KF = (size_t)K * VBGS_F;
     if ((rc = dalloc(ctx, &ctx->d_m0, (size_t)K * 6)) || (rc = dalloc(ctx, &ctx->d_Spast, KF)) ||
         (rc = dalloc(ctx, &ctx->d_dS, KF)) || (rc = dalloc(ctx, &ctx->d_rec, (size_t)K * VBGS_REC)) ||
-        (rc = dalloc(ctx, &ctx->d_rec32, (size_t)K * VBGS_REC)) || (rc = dalloc(ctx, &ctx->d_klk, (size_t)K)) ||
-        (rc = dalloc(ctx, &ctx->d_aq, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_ap, (size_t)K)) ||
-        (rc = dalloc(ctx, &ctx->d_dN, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_scal, (size_t)SC_COUNT)) ||
+        (rc = dalloc(ctx, &ctx->d_rec32, (size_t)K * VBGS_REC)) ||
+        (rc = dalloc(ctx, &ctx->d_pcache, mstep_cache_doubles(K))) || (rc = dalloc(ctx, &ctx->d_scal, (size_t)SC_COUNT)) ||
         (rc = dalloc(ctx, &ctx->d_flags, (size_t)FL_COUNT)) || (rc = ensure_elbo(ctx, 64)) ||
-        (rc = dalloc(ctx, &ctx->d_kperm, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_kinv, (size_t)K))) {
+        (rc = dalloc(ctx, &ctx->d_kperm, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_kinv, (size_t)K)) ||
+        (rc = dalloc(ctx, &ctx->d_tc_tiles, tc_tile_bytes(K))) || (rc = dalloc(ctx, &ctx->d_tc_hdr, tc_hdr_floats(K)))) {
         g_err = ctx->err;
         free_all(ctx);
         delete ctx;

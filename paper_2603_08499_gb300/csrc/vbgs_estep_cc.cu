@@ -148,7 +148,6 @@ __global__ void __launch_bounds__(256) k_merge(const double2 *__restrict__ part,
                                                float *__restrict__ minlse)
 {
     __shared__ double sh[8];
-    __shared__ float shm[8];
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
     if (n < N) {
@@ -168,14 +167,17 @@ __global__ void __launch_bounds__(256) k_merge(const double2 *__restrict__ part,
         v += __shfl_down_sync(0xffffffffu, v, o);
         vm = fminf(vm, __shfl_down_sync(0xffffffffu, vm, o));
     }
-    if ((threadIdx.x & 31) == 0) { sh[threadIdx.x >> 5] = v; shm[threadIdx.x >> 5] = vm; }
+    // minlse per 32 points (one warp), the skip bound's lower bound on lse
+    if ((threadIdx.x & 31) == 0) {
+        sh[threadIdx.x >> 5] = v;
+        const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (minlse && w * 32 < N) minlse[w] = vm;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        float tm = INFINITY;
-        for (int i = 0; i < (int)(blockDim.x >> 5); i++) { t += sh[i]; tm = fminf(tm, shm[i]); }
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += sh[i];
         lse_part[blockIdx.x] = t;
-        if (minlse) minlse[blockIdx.x] = tm;
     }
 }
 
@@ -200,16 +202,18 @@ __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ v, int 
 // d = x - a_k about the component's anchor a_k = m_k (the record's mean), so
 // that FP32 accumulation never forms the large, cancelling raw second
 // moments; k_reduce_splits shifts them back to raw moments in FP64.
-// With tmax/minlse (nps a multiple of 256), a 64-point chunk is skipped when
-// the tile's two 64-component chunk maxima minus the min lse of the chunk's
-// 256-point block are below -kSkipNats (uniform across the CTA).
+// With tile maxima (tmax: largest logit of every (tpb-point block, tkc-
+// component block), nkc column blocks) and per-32-point minima of lse, a
+// 64-point chunk is skipped when the largest of the maxima it touches minus
+// the smallest lse of its points is below -kSkipNats (uniform across the CTA).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X,
                                                     const double *__restrict__ lse, int64_t N,
                                                     int64_t nps, const T *__restrict__ rec, int K,
                                                     double *__restrict__ part,
                                                     const float *__restrict__ tmax,
-                                                    const float *__restrict__ minlse)
+                                                    const float *__restrict__ minlse,
+                                                    int tpb, int tkc)
 {
     constexpr bool kAnchored = sizeof(T) == 4;
     __shared__ T spt[kChunkN * 28];   // per point: x[6], lse, upper(x x^T)[21] (FP64 only)
@@ -225,15 +229,17 @@ __global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X
 #pragma unroll
     for (int f = 0; f < 28; f++) acc[f] = T(0);
 
-    const int nkc = (K + kChunkK - 1) / kChunkK;
-    const int c0 = blockIdx.x * (kThreads / kChunkK);
+    const int nkc = (K + tkc - 1) / (tkc > 0 ? tkc : 1);
+    const int kt0 = blockIdx.x * kThreads;
+    const int c_lo = kt0 / (tkc > 0 ? tkc : 1), c_hi = min(K - 1, kt0 + kThreads - 1) / (tkc > 0 ? tkc : 1);
     for (int64_t nc = n0; nc < n1; nc += kChunkN) {
         const int cnt = (int)min((int64_t)kChunkN, n1 - nc);
         if (tmax) {
-            const int64_t pb = nc / 256;
-            float b = tmax[pb * nkc + c0];
-            if (c0 + 1 < nkc) b = fmaxf(b, tmax[pb * nkc + c0 + 1]);
-            if (b - minlse[pb] < -(float)kSkipNats) continue;
+            float b = -INFINITY, lmin = INFINITY;
+            for (int64_t r = nc / tpb; r <= (nc + cnt - 1) / tpb; r++)
+                for (int c = c_lo; c <= c_hi; c++) b = fmaxf(b, tmax[r * nkc + c]);
+            for (int64_t w = nc / 32; w <= (nc + cnt - 1) / 32; w++) lmin = fminf(lmin, minlse[w]);
+            if (b - lmin < -(float)kSkipNats) continue;
         }
         __syncthreads();
         for (int p = threadIdx.x; p < cnt; p += kThreads) {
@@ -352,6 +358,36 @@ constexpr int kPPT32 = 2;
 
 } // namespace
 
+int launch_lse_merge(const double2 *part, int nsplit, int64_t N, double *lse, double *lse_part, float *minlse,
+                     double *sum_out, cudaStream_t st, Prof *pf)
+{
+    const int mb = (int)((N + 255) / 256);
+    pf->begin(VBGS_PROF_MERGE, st);
+    k_merge<<<mb, 256, 0, st>>>(part, nsplit, N, lse, lse_part, minlse);
+    pf->end(st);
+    pf->begin(VBGS_PROF_MERGE, st);
+    k_sum<<<1, 1024, 0, st>>>(lse_part, mb, sum_out);
+    pf->end(st);
+    return cudaGetLastError() == cudaSuccess ? 2 : -1;
+}
+
+int launch_pass2_fp32(const EstepBuffers &B, int tpb, int tkc, cudaStream_t st, Prof *pf)
+{
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    Plan pl = make_plan<kPPT32>(B.N, B.K, sms);
+    if ((size_t)pl.p2_splits * (size_t)B.K * 28 > B.part_cap) return -2;
+    dim3 g2(pl.p2_tiles, pl.p2_splits);
+    pf->begin(VBGS_PROF_PASS2, st);
+    k_pass2<float><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec32, B.K, B.part, B.tmax, B.minlse, tpb, tkc);
+    pf->end(st);
+    pf->begin(VBGS_PROF_REDUCE, st);
+    k_reduce_splits<<<(B.K + 127) / 128, 128, 0, st>>>(B.part, pl.p2_splits, B.K, B.rec32, B.kperm, B.dS);
+    pf->end(st);
+    return cudaGetLastError() == cudaSuccess ? 2 : -1;
+}
+
 size_t estep_cuda_core_scratch(int64_t N, int K, int precision)
 {
     int sms = 152;
@@ -390,9 +426,9 @@ int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats
         dim3 g2(pl.p2_tiles, pl.p2_splits);
         pf->begin(VBGS_PROF_PASS2, st);
         if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec, B.K, B.part,
-                                                          tmax, B.minlse);
+                                                          tmax, B.minlse, 256, kChunkK);
         else     k_pass2<float><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec32, B.K, B.part,
-                                                         tmax, B.minlse);
+                                                         tmax, B.minlse, 256, kChunkK);
         pf->end(st);
         pf->begin(VBGS_PROF_REDUCE, st);
         k_reduce_splits<<<(B.K + 127) / 128, 128, 0, st>>>(B.part, pl.p2_splits, B.K,
@@ -538,8 +574,8 @@ extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N
     k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, lse_out, base + o_lsep, nullptr);
     k_sum<<<1, 1024, 0, st>>>(base + o_lsep, mb, scal + SC_SUM_LSE);
     dim3 g2(pl.p2_tiles, pl.p2_splits);
-    if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part, nullptr, nullptr);
-    else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part, nullptr, nullptr);
+    if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part, nullptr, nullptr, 1, 1);
+    else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part, nullptr, nullptr, 1, 1);
     k_reduce_splits<<<(K + 127) / 128, 128, 0, st>>>(part, pl.p2_splits, K, f64 ? nullptr : ctx->d_rec32,
                                                     ctx->d_kperm, dS_out);
     k_lse_subtract_psi<<<mb, 256, 0, st>>>(lse_out, N, ctx->d_scal);

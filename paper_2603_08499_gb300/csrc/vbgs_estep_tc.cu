@@ -1,0 +1,1000 @@
+// vbgs_estep_tc.cu -- pass 1 of the E-step on the 5th-generation tensor cores.
+//
+// The expected log-likelihood of compute_elbo_delta (Alg. 1) is a quadratic
+// form in the point, so for a block of components it is one GEMM:
+//   l2_nk = phi(x_n') . C_k,   phi(x') = [1, x', upper(x' x'^T)] (28 -> 32),
+// in log2 units, where x' = (x - o_j) / s_j is the point in the local frame of
+// component tile j (o_j the mean of the tile's component means, s_j their
+// per-axis spread) and C_k holds the constant, linear and quadratic
+// coefficients of component k in that frame.  Local frames keep the terms of
+// the expansion small next to the logit, so the cancellation stays within
+// FP16 hi/lo operands (about 22 bits) and FP32 accumulation:
+//   L = A_hi B_hi + A_hi B_lo + A_lo B_hi     (tcgen05.mma kind::f16, K = 32)
+// with A = features of 128 points (one CTA's rows), B = coefficients of 128
+// components, the 128 x 128 FP32 accumulator in tensor memory (TMEM).
+//
+// CTA = 160 threads.  Warps 0-3 (one thread per point row = TMEM lane) build
+// the A tile of the next component tile in shared memory, then read the
+// finished accumulator with tcgen05.ld and keep the online (max, sum of
+// 2^(l - max)) of their row.  Warp 4 issues the coefficient-tile copies
+// (cp.async.bulk, completion on an mbarrier) and the MMAs (one elected lane),
+// and commits MMA completion to mbarriers.  A and D are double buffered,
+// B has kStagesB stages.  Every wait is bounded: on timeout the kernel sets
+// the context's timeout flag, stops issuing work, waits (bounded) for the
+// copies and MMAs it issued, frees its TMEM and returns.
+//
+// Shared-memory operand layout (K-major, no swizzle): 8 x 8 fp16 core
+// matrices of 128 contiguous bytes; element (row r, feature f) of a 128 x 32
+// tile is at byte (r / 8) * 512 + (f / 8) * 128 + (r % 8) * 16 + (f % 8) * 2,
+// i.e. leading-dimension (K) core-matrix stride 128 B and stride-dimension
+// (8-row group) stride 512 B.  Coefficient tiles are built in global memory
+// in exactly this layout so one bulk copy stages them.
+#include "vbgs_internal.cuh"
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <algorithm>
+
+namespace vbgs {
+
+namespace {
+
+constexpr int kRows = 128;          // points per CTA tile (MMA M)
+constexpr int kCols = 128;          // components per tile (MMA N)
+constexpr int kFeat = 32;           // features (MMA K), 28 used
+constexpr int kStagesB = 4;
+constexpr int kOperandBytes = kRows * kFeat * 2;          // 8 KB (hi or lo)
+constexpr int kTileBytes = 2 * kOperandBytes;             // hi + lo
+constexpr int kThreadsTC = 160;
+constexpr int kTmemCols = 2 * kCols;
+constexpr long long kSpinCycles = 4000000000LL;           // ~2 s at 2 GHz
+
+struct __align__(1024) Smem {
+    unsigned char A[2][kTileBytes];
+    unsigned char B[kStagesB][kTileBytes];
+    unsigned long long bar_bfull[kStagesB];
+    unsigned long long bar_bfree[kStagesB];
+    unsigned long long bar_afull[2];
+    unsigned long long bar_mma[2];
+    unsigned long long bar_dfree[2];
+    unsigned long long bar_final;
+    unsigned int tmem_base;
+};
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(su32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(su32(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Bounded wait on a barrier phase; false on timeout.  A normal wait also
+// gives up as soon as another thread of the grid has timed out; a drain wait
+// (for copies and MMAs this thread issued) only stops at its own limit.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity, int *flags, bool drain = false)
+{
+    if (mbar_try(b, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(b, parity)) return true;
+        if (!drain && *(volatile int *)&flags[FL_TIMEOUT]) return false;
+        if (clock64() - t0 > kSpinCycles) {
+            atomicExch(&flags[FL_TIMEOUT], 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t smem_desc(const void *p)
+{
+    const uint32_t a = su32(p);
+    uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128u >> 4) << 16;   // leading (K) core-matrix stride
+    d |= (uint64_t)(512u >> 4) << 32;   // 8-row group stride
+    d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
+    return d;                           // base offset 0, no swizzle
+}
+
+// kind::f16, FP32 accumulator, A and B K-major, M = 128, N = 128.
+template <bool BF16>
+__host__ __device__ constexpr uint32_t idesc_f16()
+{
+    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((uint32_t)(kCols >> 3) << 17) |
+           ((uint32_t)(kRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+                 "l"(a), "l"(b), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned long long *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                 "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float ex2f(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Byte offset of (row, feature) in a 128 x 32 K-major core-matrix operand.
+__host__ __device__ constexpr int opnd_off(int r, int f) { return (r >> 3) * 512 + (f >> 3) * 128 + (r & 7) * 16 + (f & 7) * 2; }
+
+template <bool BF16> struct H;
+// Scalar conversions (coefficient tiles) and a packed hi/lo split of two
+// floats: hi = round(a, b), lo = round((a, b) - hi), two values per cvt.
+template <> struct H<false> {
+    using T = __half;
+    static __device__ __forceinline__ T from_f(float v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ float to_f(T v) { return __half2float(v); }
+    static __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo)
+    {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+};
+template <> struct H<true> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ T from_f(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float to_f(T v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Coefficient tiles.  One CTA per component tile (128 threads = components at
+// sorted positions).  FP64 throughout, then scaled by 2^-e_j so the largest
+// coefficient of the tile is about 2^14, and split hi/lo.
+// Header (32 floats): o_hi[6], o_lo[6], inv_s[6], outscale (2^e_j), pad.
+// ---------------------------------------------------------------------------
+template <bool BF16>
+__global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ rec, int K,
+                                                    unsigned char *__restrict__ tiles, float *__restrict__ hdr)
+{
+    using HT = typename H<BF16>::T;
+    __shared__ double red[6][4];
+    __shared__ double frame[13];
+    const int t = threadIdx.x, j = blockIdx.x, lane = t & 31, w = t >> 5;
+    const int k = j * kCols + t;
+    const bool valid = k < K;
+    const double *r = rec + (size_t)(valid ? k : K - 1) * VBGS_REC;
+    double m[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) m[i] = r[i];
+    const int nvalid = min(kCols, K - j * kCols);
+    // frame origin: mean of the tile's means
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        double v = valid ? m[i] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[i][w] = v;
+    }
+    __syncthreads();
+    if (t < 6) frame[t] = (red[t][0] + red[t][1] + red[t][2] + red[t][3]) / nvalid;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        double d = valid ? m[i] - frame[i] : 0.0;
+        double v = d * d;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[i][w] = v;
+    }
+    __syncthreads();
+    if (t < 6) {
+        double sd = sqrt((red[t][0] + red[t][1] + red[t][2] + red[t][3]) / nvalid);
+        float inv = (float)(1.0 / fmax(sd, 0.05));
+        float ohi = (float)frame[t];
+        float olo = (float)(frame[t] - (double)ohi);
+        hdr[(size_t)j * 32 + t] = ohi;
+        hdr[(size_t)j * 32 + 6 + t] = olo;
+        hdr[(size_t)j * 32 + 12 + t] = inv;
+        // the frame the coefficients are expressed in is exactly the stored one
+        frame[t] = (double)ohi + (double)olo;
+        frame[6 + t] = 1.0 / (double)inv;
+    }
+    __syncthreads();
+    // Lambda2 = log2(e) M^T M, M packed lower triangular
+    double Mf[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+#pragma unroll
+        for (int q = 0; q < 6; q++) Mf[i][q] = (q <= i) ? r[6 + tri(i, q)] : 0.0;
+    const double L2E = 1.4426950408889634;
+    double Lp[6][6], mp[6];
+#pragma unroll
+    for (int a = 0; a < 6; a++) {
+        mp[a] = (m[a] - frame[a]) / frame[6 + a];
+#pragma unroll
+        for (int b = a; b < 6; b++) {
+            double v = 0.0;
+#pragma unroll
+            for (int l = 0; l < 6; l++) v += Mf[l][a] * Mf[l][b];
+            v *= L2E * frame[6 + a] * frame[6 + b];
+            Lp[a][b] = v;
+            Lp[b][a] = v;
+        }
+    }
+    double coef[kFeat];
+    double quad = 0.0;
+#pragma unroll
+    for (int a = 0; a < 6; a++) {
+        double bl = 0.0;
+#pragma unroll
+        for (int b = 0; b < 6; b++) bl += Lp[a][b] * mp[b];
+        coef[1 + a] = bl;
+        quad += mp[a] * bl;
+    }
+    coef[0] = r[27] * L2E - 0.5 * quad;
+    {
+        int u = 7;
+#pragma unroll
+        for (int a = 0; a < 6; a++)
+#pragma unroll
+            for (int b = a; b < 6; b++, u++) coef[u] = (a == b) ? -0.5 * Lp[a][a] : -Lp[a][b];
+    }
+#pragma unroll
+    for (int f = 28; f < kFeat; f++) coef[f] = 0.0;
+    // tile-wide largest magnitude -> power-of-two scale
+    double mx = 0.0;
+    if (valid)
+#pragma unroll
+        for (int f = 0; f < 28; f++) mx = fmax(mx, fabs(coef[f]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[0][w] = mx;
+    __syncthreads();
+    mx = fmax(fmax(red[0][0], red[0][1]), fmax(red[0][2], red[0][3]));
+    int e = 0;
+    if (mx > 0.0) e = (int)ceil(log2(mx)) - 14;
+    const double sc = ldexp(1.0, -e);
+    if (t == 0) hdr[(size_t)j * 32 + 18] = (float)ldexp(1.0, e);
+    unsigned char *hi = tiles + (size_t)j * kTileBytes;
+    unsigned char *lo = hi + kOperandBytes;
+#pragma unroll
+    for (int f = 0; f < kFeat; f++) {
+        double v = valid ? coef[f] * sc : 0.0;   // padding columns are masked by pass 1
+        HT h = H<BF16>::from_f((float)v);
+        HT l = H<BF16>::from_f((float)(v - (double)H<BF16>::to_f(h)));
+        *reinterpret_cast<HT *>(hi + opnd_off(t, f)) = h;
+        *reinterpret_cast<HT *>(lo + opnd_off(t, f)) = l;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1 on the tensor cores.  grid = (point tiles of 128, K splits).
+// part[split * N + n] = (max in natural units, sum of exp(l - max)).
+// tmax[(point tile * 4 + warp) * ntiles + tile]: largest logit (natural units)
+// of each 32-point row block and 128-component tile.
+// ---------------------------------------------------------------------------
+template <bool BF16>
+__global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__restrict__ X, int64_t N, int K,
+                                                            const unsigned char *__restrict__ tiles,
+                                                            const float *__restrict__ hdr, int ntiles, int tps,
+                                                            double2 *__restrict__ part, float *__restrict__ tmax,
+                                                            int *__restrict__ flags)
+{
+    using HT = typename H<BF16>::T;
+    extern __shared__ unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int split = blockIdx.y;
+    const int j0 = split * tps;
+    const int nt = max(0, min(ntiles, j0 + tps) - j0);
+
+    if (tid == 0) {
+        for (int i = 0; i < kStagesB; i++) { mbar_init(&S.bar_bfull[i], 1); mbar_init(&S.bar_bfree[i], 1); }
+        for (int i = 0; i < 2; i++) { mbar_init(&S.bar_afull[i], 128); mbar_init(&S.bar_mma[i], 1); mbar_init(&S.bar_dfree[i], 128); }
+        mbar_init(&S.bar_final, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp < 4) {
+        // ---------------- feature builders + online log-sum-exp ----------------
+        const int row = warp * 32 + lane;
+        const int64_t n = (int64_t)blockIdx.x * kRows + row;
+        const int64_t nn = n < N ? n : N - 1;
+        float xh[6], xl[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            double v = X[nn * VBGS_XS + i];
+            xh[i] = (float)v;
+            xl[i] = (float)(v - (double)xh[i]);
+        }
+        float mrun = -INFINITY, srun = 0.f;
+        bool ok = true;
+        // frame header of the next tile to build (o_hi, o_lo, 1/s), prefetched one tile ahead
+        float hn[18];
+        auto load_hdr = [&](int jj) {
+            if (jj < nt) {
+                const float4 *h4 = reinterpret_cast<const float4 *>(hdr + (size_t)(j0 + jj) * 32);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const float4 v = h4[q];
+                    hn[4 * q] = v.x; hn[4 * q + 1] = v.y; hn[4 * q + 2] = v.z; hn[4 * q + 3] = v.w;
+                }
+                const float2 v = reinterpret_cast<const float2 *>(hdr + (size_t)(j0 + jj) * 32)[8];
+                hn[16] = v.x; hn[17] = v.y;
+            }
+        };
+        auto build_A = [&](int jj) {
+            float h[18];
+#pragma unroll
+            for (int i = 0; i < 18; i++) h[i] = hn[i];
+            load_hdr(jj + 1);
+            float d[6];
+#pragma unroll
+            for (int i = 0; i < 6; i++) d[i] = ((xh[i] - h[i]) + (xl[i] - h[6 + i])) * h[12 + i];
+            float f[kFeat];
+            f[0] = 1.f;
+#pragma unroll
+            for (int i = 0; i < 6; i++) f[1 + i] = d[i];
+            int u = 7;
+#pragma unroll
+            for (int a = 0; a < 6; a++)
+#pragma unroll
+                for (int b = a; b < 6; b++, u++) f[u] = d[a] * d[b];
+#pragma unroll
+            for (int i = 28; i < kFeat; i++) f[i] = 0.f;
+            unsigned char *Ahi = S.A[jj & 1];
+            unsigned char *Alo = Ahi + kOperandBytes;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) H<BF16>::split2(f[c * 8 + 2 * e], f[c * 8 + 2 * e + 1], hw[e], lw[e]);
+                *reinterpret_cast<uint4 *>(Ahi + opnd_off(row, c * 8)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(Alo + opnd_off(row, c * 8)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+            fence_async_smem();
+            mbar_arrive(&S.bar_afull[jj & 1]);
+        };
+        load_hdr(0);
+        if (nt > 0) build_A(0);
+        for (int jj = 0; jj < nt && ok; jj++) {
+            if (jj + 1 < nt) build_A(jj + 1);
+            const int s = jj & 1;
+            const float scale = hdr[(size_t)(j0 + jj) * 32 + 18];
+            ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_mma[s], (uint32_t)((jj >> 1) & 1), flags));
+            if (!ok) break;
+            fence_after();
+            const int nvalid = min(kCols, K - (j0 + jj) * kCols);   // columns past K are padding
+            float tmx = -INFINITY;
+            const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kCols);
+#pragma unroll 1
+            for (int c = 0; c < kCols; c += 64) {
+                uint32_t v0[32], v1[32];
+                tmem_ld32(tbase + c, v0);
+                tmem_ld32(tbase + c + 32, v1);
+                tmem_wait_ld();
+                if (nvalid < kCols) {
+#pragma unroll
+                    for (int i = 0; i < 32; i++) {
+                        if (c + i >= nvalid) v0[i] = 0xff800000u;        // -inf
+                        if (c + 32 + i >= nvalid) v1[i] = 0xff800000u;
+                    }
+                }
+                // max and sum over 64 values with 8 independent chains each
+                float mx8[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) mx8[q] = fmaxf(__uint_as_float(v0[q]), __uint_as_float(v1[q]));
+#pragma unroll
+                for (int i = 8; i < 32; i++) mx8[i & 7] = fmaxf(mx8[i & 7], fmaxf(__uint_as_float(v0[i]), __uint_as_float(v1[i])));
+                float cm = fmaxf(fmaxf(fmaxf(mx8[0], mx8[1]), fmaxf(mx8[2], mx8[3])),
+                                 fmaxf(fmaxf(mx8[4], mx8[5]), fmaxf(mx8[6], mx8[7])));
+                cm *= scale;
+                tmx = fmaxf(tmx, cm);
+                if (cm > mrun) {
+                    srun *= ex2f(mrun - cm);
+                    mrun = cm;
+                }
+                const float negm = -mrun;
+                float acc[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) acc[q] = 0.f;
+#pragma unroll
+                for (int i = 0; i < 32; i++) {
+                    acc[i & 7] += ex2f(fmaf(__uint_as_float(v0[i]), scale, negm));
+                    acc[(i + 4) & 7] += ex2f(fmaf(__uint_as_float(v1[i]), scale, negm));
+                }
+                srun += ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+            }
+            fence_before();
+            mbar_arrive(&S.bar_dfree[s]);
+            // largest logit of this 32-row block and component tile (natural units)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tmx = fmaxf(tmx, __shfl_xor_sync(0xffffffffu, tmx, o));
+            const int64_t rb = (int64_t)blockIdx.x * 4 + warp;
+            if (lane == 0 && tmax && rb * 32 < N) tmax[rb * ntiles + (j0 + jj)] = tmx * 0.6931471805599453f;
+        }
+        if (n < N) part[(size_t)split * N + n] = make_double2((double)mrun * 0.6931471805599453, (double)srun);
+    } else if (warp == 4 && lane == 0) {
+        // ---------------- copy + MMA issuer ----------------
+        constexpr uint32_t idesc = idesc_f16<BF16>();
+        bool ok = true;
+        int n_loads = 0, n_mma = 0;
+        const int pre = min(nt, kStagesB - 1);
+        for (int jj = 0; jj < pre; jj++) {
+            mbar_expect_tx(&S.bar_bfull[jj], kTileBytes);
+            bulk_g2s(S.B[jj], tiles + (size_t)(j0 + jj) * kTileBytes, kTileBytes, &S.bar_bfull[jj]);
+            n_loads = jj + 1;
+        }
+        for (int jj = 0; jj < nt && ok; jj++) {
+            const int s = jj & 1, sb = jj % kStagesB;
+            ok = mbar_wait(&S.bar_bfull[sb], (uint32_t)((jj / kStagesB) & 1), flags) &&
+                 mbar_wait(&S.bar_afull[s], (uint32_t)((jj >> 1) & 1), flags) &&
+                 (jj < 2 || mbar_wait(&S.bar_dfree[s], (uint32_t)(((jj >> 1) - 1) & 1), flags));
+            if (!ok) break;
+            fence_after();
+            const uint32_t d = tmem + (uint32_t)(s * kCols);
+            const unsigned char *Ahi = S.A[s], *Alo = S.A[s] + kOperandBytes;
+            const unsigned char *Bhi = S.B[sb], *Blo = S.B[sb] + kOperandBytes;
+            // k-steps of 16 features: the descriptor start advances by two core matrices (256 B)
+            mma(d, smem_desc(Ahi), smem_desc(Bhi), idesc, 0u);
+            mma(d, smem_desc(Ahi + 256), smem_desc(Bhi + 256), idesc, 1u);
+            mma(d, smem_desc(Ahi), smem_desc(Blo), idesc, 1u);
+            mma(d, smem_desc(Ahi + 256), smem_desc(Blo + 256), idesc, 1u);
+            mma(d, smem_desc(Alo), smem_desc(Bhi), idesc, 1u);
+            mma(d, smem_desc(Alo + 256), smem_desc(Bhi + 256), idesc, 1u);
+            mma_commit(&S.bar_mma[s]);
+            mma_commit(&S.bar_bfree[sb]);
+            n_mma = jj + 1;
+            // refill the B stage that the previous tile's MMAs read
+            const int nxt = jj + kStagesB - 1;
+            if (nxt < nt) {
+                const int sn = nxt % kStagesB;
+                if (jj >= 1) {
+                    ok = mbar_wait(&S.bar_bfree[sn], (uint32_t)(((jj - 1) / kStagesB) & 1), flags);
+                    if (!ok) break;
+                }
+                mbar_expect_tx(&S.bar_bfull[sn], kTileBytes);
+                bulk_g2s(S.B[sn], tiles + (size_t)(j0 + nxt) * kTileBytes, kTileBytes, &S.bar_bfull[sn]);
+                n_loads = nxt + 1;
+            }
+        }
+        // Drain before the shared memory and TMEM go away: the last phase of
+        // every barrier a copy or a commit of this thread arrives on.
+        for (int sb = 0; sb < kStagesB; sb++) {
+            const int last_load = ((n_loads - 1 - sb) >= 0) ? sb + ((n_loads - 1 - sb) / kStagesB) * kStagesB : -1;
+            if (last_load >= 0) mbar_wait(&S.bar_bfull[sb], (uint32_t)((last_load / kStagesB) & 1), flags, true);
+            const int last_mma = ((n_mma - 1 - sb) >= 0) ? sb + ((n_mma - 1 - sb) / kStagesB) * kStagesB : -1;
+            if (last_mma >= 0) mbar_wait(&S.bar_bfree[sb], (uint32_t)((last_mma / kStagesB) & 1), flags, true);
+        }
+        for (int s = 0; s < 2; s++) {
+            const int last = ((n_mma - 1 - s) >= 0) ? s + ((n_mma - 1 - s) / 2) * 2 : -1;
+            if (last >= 0) mbar_wait(&S.bar_mma[s], (uint32_t)((last >> 1) & 1), flags, true);
+        }
+        // a last commit tracks every MMA this thread issued: TMEM is idle after it
+        if (n_mma > 0) {
+            mma_commit(&S.bar_final);
+            mbar_wait(&S.bar_final, 0u, flags, true);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Pass 2 on the tensor cores: the fused statistics contraction of Eq. 3.
+// grid = (component tiles, N splits), 160 threads.  A CTA keeps its tile's
+// coefficients (the pass-1 tile, A operand) in shared memory and walks the
+// 64-point chunks of its split that the pass-1 bound does not rule out:
+//   MMA1  D1[128 comps x 64 pts]  = C . phi'^T      (3 hi/lo products, K = 32)
+//   epilogue (thread = component row): r = 2^(D1 * scale - lse2_n) -> P hi/lo
+//   MMA2  D2[128 comps x 32 feats]  = P_hi phi'_hi + P_hi phi'_lo + P_lo phi'_hi
+//         (K = 64 points)
+// phi' are the points' features in the tile's frame, so D2 holds the tile-frame
+// moments of one chunk; the epilogue adds each chunk's D2 into FP32 registers
+// (round to nearest) and k_reduce_splits_tile shifts the sums to raw moments
+// in FP64.  One fresh accumulator per chunk keeps the tensor core's FP32
+// accumulation (not round-to-nearest) to 64 points: summed over a whole frame
+// its bias is of the order of the prior scatter W0^-1 of a thin component.  The
+// logits are those of pass 1 (same coefficient tile, same feature arithmetic),
+// so the responsibilities of a point sum to one up to the hi/lo rounding of r.
+// Operands (K-major, no swizzle, core matrices of 8 rows x 16 bytes):
+//   B1 [64 pts  x 32 feats]: LBO 128, SBO 512       (4 KB each for hi, lo)
+//   B2 [32 feats x 64 pts ]: LBO 128, SBO 1024      (4 KB each for hi, lo)
+//   P  [128 comps x 64 pts]: LBO 128, SBO 1024      (16 KB each for hi, lo)
+// TMEM: D1 double buffered at columns 0 / 64, D2 double buffered at 128 / 160.
+// ---------------------------------------------------------------------------
+constexpr int kChunk2 = 64;
+constexpr int kB1Bytes = kChunk2 * kFeat * 2;       // 4 KB
+constexpr int kB2Bytes = kFeat * kChunk2 * 2;       // 4 KB
+constexpr int kPBytes = kCols * kChunk2 * 2;        // 16 KB
+
+struct __align__(128) Smem2 {
+    unsigned char A[kTileBytes];                    // coefficient tile (hi | lo)
+    unsigned char B1[2][2 * kB1Bytes];              // hi | lo
+    unsigned char B2[2][2 * kB2Bytes];              // hi | lo
+    unsigned char P[2][2 * kPBytes];                // hi | lo
+    float lse2[2][kChunk2];
+    unsigned long long bar_a, bar_bfull[2], bar_d1full[2], bar_d1free[2], bar_pfull[2], bar_stfree[2], bar_d2, bar_final;
+    unsigned int tmem_base;
+};
+
+__device__ __forceinline__ uint64_t smem_desc_sbo(const void *p, uint32_t sbo)
+{
+    const uint32_t a = su32(p);
+    uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+template <bool BF16>
+__host__ __device__ constexpr uint32_t idesc_mn(int M, int Ncols)
+{
+    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((uint32_t)(Ncols >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ int b1_off(int pt, int f) { return (pt >> 3) * 512 + (f >> 3) * 128 + (pt & 7) * 16 + (f & 7) * 2; }
+__device__ __forceinline__ int b2_off(int f, int pt) { return (f >> 3) * 1024 + (pt >> 3) * 128 + (f & 7) * 16 + (pt & 7) * 2; }
+__device__ __forceinline__ int p_off(int m, int pt) { return (m >> 3) * 1024 + (pt >> 3) * 128 + (m & 7) * 16 + (pt & 7) * 2; }
+
+// The pass-2 skip bound of a 64-point chunk against tile j (uniform per CTA).
+__device__ __forceinline__ bool chunk_skipped(const float *tmax, const float *minlse, int64_t N, int ntiles, int j,
+                                              int64_t c0)
+{
+    if (!tmax) return false;
+    const int64_t r0 = c0 / 32, r1 = (min(N, c0 + kChunk2) - 1) / 32;
+    float b = -INFINITY, l = INFINITY;
+    for (int64_t r = r0; r <= r1; r++) {
+        b = fmaxf(b, tmax[r * ntiles + j]);
+        l = fminf(l, minlse[r]);
+    }
+    return b - l < -(float)kSkipNats;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__restrict__ X, const double *__restrict__ lse,
+                                                            int64_t N, int K, const unsigned char *__restrict__ tiles,
+                                                            const float *__restrict__ hdr, int ntiles, int64_t cps,
+                                                            const float *__restrict__ tmax,
+                                                            const float *__restrict__ minlse,
+                                                            double *__restrict__ part, int *__restrict__ flags)
+{
+    using HT = typename H<BF16>::T;
+    extern __shared__ unsigned char smem_raw[];
+    Smem2 &S = *reinterpret_cast<Smem2 *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int j = blockIdx.x, split = blockIdx.y;
+    const int64_t nchunks = (N + kChunk2 - 1) / kChunk2;
+    const int64_t cbeg = (int64_t)split * cps, cend = min(nchunks, cbeg + cps);
+
+    if (tid == 0) {
+        mbar_init(&S.bar_a, 1);
+        mbar_init(&S.bar_d2, 1);
+        mbar_init(&S.bar_final, 1);
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&S.bar_bfull[i], 128); mbar_init(&S.bar_d1full[i], 1); mbar_init(&S.bar_d1free[i], 128);
+            mbar_init(&S.bar_pfull[i], 128); mbar_init(&S.bar_stfree[i], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)), "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = S.tmem_base;
+    const float *h = hdr + (size_t)j * 32;
+    const float scale = h[18];
+
+    // next processed chunk at or after c (cend if none)
+    auto next_chunk = [&](int64_t c) {
+        while (c < cend && chunk_skipped(tmax, minlse, N, ntiles, j, c * kChunk2)) c++;
+        return c;
+    };
+
+    if (warp < 4) {
+        // ---------------- builders + responsibilities ----------------
+        float hf[18];
+#pragma unroll
+        for (int i = 0; i < 18; i++) hf[i] = h[i];
+        const int m = tid;                          // component row of the epilogue
+        bool ok = true;
+        auto build = [&](int64_t c, int st) {
+            // threads 0..63 write B1 (point-major), 64..127 write B2 (feature-major); both write lse2
+            const int pt = tid & 63;
+            const int64_t n = c * kChunk2 + pt;
+            const int64_t nn = n < N ? n : N - 1;
+            float d[6];
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                const double v = X[nn * VBGS_XS + i];
+                const float xh = (float)v, xl = (float)(v - (double)xh);
+                d[i] = ((xh - hf[i]) + (xl - hf[6 + i])) * hf[12 + i];
+            }
+            float f[kFeat];
+            f[0] = 1.f;
+#pragma unroll
+            for (int i = 0; i < 6; i++) f[1 + i] = d[i];
+            int u = 7;
+#pragma unroll
+            for (int a = 0; a < 6; a++)
+#pragma unroll
+                for (int b = a; b < 6; b++, u++) f[u] = d[a] * d[b];
+#pragma unroll
+            for (int i = 28; i < kFeat; i++) f[i] = 0.f;
+            uint32_t hw[16], lw[16];
+#pragma unroll
+            for (int e = 0; e < 16; e++) H<BF16>::split2(f[2 * e], f[2 * e + 1], hw[e], lw[e]);
+            if (tid < 64) {
+                unsigned char *bh = S.B1[st], *bl = S.B1[st] + kB1Bytes;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    *reinterpret_cast<uint4 *>(bh + b1_off(pt, 8 * q)) = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+                    *reinterpret_cast<uint4 *>(bl + b1_off(pt, 8 * q)) = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                }
+                S.lse2[st][pt] = n < N ? (float)(lse[n] * 1.4426950408889634) : INFINITY;
+            } else {
+                unsigned char *bh = S.B2[st], *bl = S.B2[st] + kB2Bytes;
+#pragma unroll
+                for (int e = 0; e < 16; e++) {
+                    *reinterpret_cast<unsigned short *>(bh + b2_off(2 * e, pt)) = (unsigned short)(hw[e] & 0xffffu);
+                    *reinterpret_cast<unsigned short *>(bh + b2_off(2 * e + 1, pt)) = (unsigned short)(hw[e] >> 16);
+                    *reinterpret_cast<unsigned short *>(bl + b2_off(2 * e, pt)) = (unsigned short)(lw[e] & 0xffffu);
+                    *reinterpret_cast<unsigned short *>(bl + b2_off(2 * e + 1, pt)) = (unsigned short)(lw[e] >> 16);
+                }
+            }
+            fence_async_smem();
+            mbar_arrive(&S.bar_bfull[st]);
+        };
+        float st[kFeat];
+#pragma unroll
+        for (int i = 0; i < kFeat; i++) st[i] = 0.f;
+        auto add_d2 = [&](int stage) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 128u + (uint32_t)(stage * kFeat), v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < kFeat; i++) st[i] += __uint_as_float(v[i]);
+        };
+        int64_t c = next_chunk(cbeg);
+        int u = 0;
+        if (c < cend) build(c, 0);
+        while (c < cend && ok) {
+            const int s = u & 1;
+            if (u >= 1) {
+                // MMA2(u-1) done: its chunk moments are in D2[(u+1)&1], and the
+                // operand stage (u+1)&1 is free for the next chunk
+                ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_stfree[(u + 1) & 1], (uint32_t)(((u - 1) >> 1) & 1), flags));
+                if (!ok) break;
+                fence_after();
+                add_d2((u + 1) & 1);
+            }
+            const int64_t cn = next_chunk(c + 1);
+            if (cn < cend) build(cn, (u + 1) & 1);
+            ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_d1full[s], (uint32_t)((u >> 1) & 1), flags));
+            if (!ok) break;
+            fence_after();
+            uint32_t v0[32], v1[32];
+            const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kChunk2);
+            tmem_ld32(tb, v0);
+            tmem_ld32(tb + 32, v1);
+            tmem_wait_ld();
+            fence_before();
+            mbar_arrive(&S.bar_d1free[s]);
+            // r = 2^(l2 - lse2) -> FP16, row m of P (P[s] was last read by MMA2(u-2), waited above)
+            unsigned char *prow = S.P[s];
+            const float4 *l4 = reinterpret_cast<const float4 *>(S.lse2[s]);
+#pragma unroll
+            for (int g = 0; g < 8; g++) {
+                const float4 la = l4[2 * g], lb = l4[2 * g + 1];
+                const float lv[8] = {la.x, la.y, la.z, la.w, lb.x, lb.y, lb.z, lb.w};
+                float r[8];
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+                    const int col = g * 8 + e;
+                    const uint32_t raw = col < 32 ? v0[col] : v1[col - 32];
+                    r[e] = ex2f(fmaf(__uint_as_float(raw), scale, -lv[e]));
+                }
+                uint32_t ph[4], pl[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) H<BF16>::split2(r[2 * e], r[2 * e + 1], ph[e], pl[e]);
+                *reinterpret_cast<uint4 *>(prow + p_off(m, g * 8)) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                *reinterpret_cast<uint4 *>(prow + kPBytes + p_off(m, g * 8)) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+            }
+            fence_async_smem();
+            mbar_arrive(&S.bar_pfull[s]);
+            c = cn;
+            u++;
+        }
+        if (ok && u >= 1) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_stfree[(u - 1) & 1], (uint32_t)(((u - 1) >> 1) & 1), flags));
+            if (ok) {
+                fence_after();
+                add_d2((u - 1) & 1);
+            }
+        }
+        const int k = j * kCols + m;
+        if (k < K) {
+            double *dst = part + ((size_t)split * K + k) * 28;
+#pragma unroll
+            for (int i = 0; i < 28; i++) dst[i] = (double)st[i];
+        }
+    } else if (warp == 4 && lane == 0) {
+        // ---------------- copy + MMA issuer ----------------
+        constexpr uint32_t id1 = idesc_mn<BF16>(128, kChunk2);
+        constexpr uint32_t id2 = idesc_mn<BF16>(128, kFeat);
+        bool ok = true;
+        bool a_loaded = false;
+        int n_proc = 0;
+        bool any_mma = false;
+        int64_t c = next_chunk(cbeg);
+        if (c < cend) {
+            mbar_expect_tx(&S.bar_a, kTileBytes);
+            bulk_g2s(S.A, tiles + (size_t)j * kTileBytes, kTileBytes, &S.bar_a);
+            a_loaded = true;
+            ok = mbar_wait(&S.bar_a, 0u, flags);
+        }
+        auto mma1 = [&](int uu) {
+            const int s = uu & 1;
+            const uint32_t d = tmem + (uint32_t)(s * kChunk2);
+            const unsigned char *Ahi = S.A, *Alo = S.A + kOperandBytes;
+            const unsigned char *Bh = S.B1[s], *Bl = S.B1[s] + kB1Bytes;
+            mma(d, smem_desc_sbo(Ahi, 512), smem_desc_sbo(Bh, 512), id1, 0u);
+            mma(d, smem_desc_sbo(Ahi + 256, 512), smem_desc_sbo(Bh + 256, 512), id1, 1u);
+            mma(d, smem_desc_sbo(Ahi, 512), smem_desc_sbo(Bl, 512), id1, 1u);
+            mma(d, smem_desc_sbo(Ahi + 256, 512), smem_desc_sbo(Bl + 256, 512), id1, 1u);
+            mma(d, smem_desc_sbo(Alo, 512), smem_desc_sbo(Bh, 512), id1, 1u);
+            mma(d, smem_desc_sbo(Alo + 256, 512), smem_desc_sbo(Bh + 256, 512), id1, 1u);
+            mma_commit(&S.bar_d1full[s]);
+        };
+        // MMA1 of the first chunk
+        if (ok && c < cend) {
+            ok = mbar_wait(&S.bar_bfull[0], 0u, flags);
+            if (ok) { fence_after(); mma1(0); any_mma = true; }
+        }
+        int u = 0;
+        while (ok && c < cend) {
+            const int s = u & 1;
+            const int64_t cn = next_chunk(c + 1);
+            if (cn < cend) {
+                const int s1 = (u + 1) & 1;
+                ok = mbar_wait(&S.bar_bfull[s1], (uint32_t)(((u + 1) >> 1) & 1), flags) &&
+                     (u + 1 < 2 || mbar_wait(&S.bar_d1free[s1], (uint32_t)((((u + 1) >> 1) - 1) & 1), flags));
+                if (!ok) break;
+                fence_after();
+                mma1(u + 1);
+            }
+            ok = mbar_wait(&S.bar_pfull[s], (uint32_t)((u >> 1) & 1), flags);
+            if (!ok) break;
+            fence_after();
+            const unsigned char *Pp = S.P[s];
+            const unsigned char *Bh = S.B2[s], *Bl = S.B2[s] + kB2Bytes;
+            const uint32_t d2 = tmem + 128u + (uint32_t)(s * kFeat);
+            const unsigned char *Pl = Pp + kPBytes;
+#pragma unroll
+            for (int t = 0; t < kChunk2 / 16; t++) {
+                mma(d2, smem_desc_sbo(Pp + 256 * t, 1024), smem_desc_sbo(Bh + 256 * t, 1024), id2, t > 0 ? 1u : 0u);
+                mma(d2, smem_desc_sbo(Pp + 256 * t, 1024), smem_desc_sbo(Bl + 256 * t, 1024), id2, 1u);
+                mma(d2, smem_desc_sbo(Pl + 256 * t, 1024), smem_desc_sbo(Bh + 256 * t, 1024), id2, 1u);
+            }
+            mma_commit(&S.bar_stfree[s]);
+            n_proc = u + 1;
+            c = cn;
+            u++;
+        }
+        // Drain: last phases of the barriers the copy and the commits arrive on.
+        if (a_loaded) mbar_wait(&S.bar_a, 0u, flags, true);
+        for (int s = 0; s < 2; s++) {
+            const int last = ((n_proc - 1 - s) >= 0) ? s + ((n_proc - 1 - s) / 2) * 2 : -1;
+            if (last >= 0) mbar_wait(&S.bar_stfree[s], (uint32_t)((last >> 1) & 1), flags, true);
+        }
+        if (any_mma) {
+            mma_commit(&S.bar_final);
+            mbar_wait(&S.bar_final, 0u, flags, true);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    }
+}
+
+// dS[kperm[p]] = sum over splits of the tile-frame moments of position p,
+// shifted to raw moments with x = o + s (.) x' (o, s of the position's tile):
+//   S1_i = N o_i + s_i S1'_i,
+//   S2_ij = N o_i o_j + o_i s_j S1'_j + s_i o_j S1'_i + s_i s_j S2'_ij.
+__global__ void k_reduce_splits_tile(const double *__restrict__ part, int nsplit, int K, const float *__restrict__ hdr,
+                                     const int *__restrict__ kperm, double *__restrict__ dS)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= K) return;
+    const size_t n = (size_t)K * 28;
+    double t[28];
+#pragma unroll
+    for (int f = 0; f < 28; f++) t[f] = 0.0;
+    for (int q = 0; q < nsplit; q++) {
+        const double *src = part + (size_t)q * n + (size_t)p * 28;
+#pragma unroll
+        for (int f = 0; f < 28; f++) t[f] += src[f];
+    }
+    const float *h = hdr + (size_t)(p / kCols) * 32;
+    double o[6], sc[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        o[i] = (double)h[i] + (double)h[6 + i];
+        sc[i] = 1.0 / (double)h[12 + i];
+    }
+    double out[28];
+    out[0] = t[0];
+#pragma unroll
+    for (int i = 0; i < 6; i++) out[1 + i] = t[0] * o[i] + sc[i] * t[1 + i];
+    int u = 7;
+#pragma unroll
+    for (int a = 0; a < 6; a++)
+#pragma unroll
+        for (int b = a; b < 6; b++, u++)
+            out[u] = t[0] * o[a] * o[b] + o[a] * sc[b] * t[1 + b] + sc[a] * o[b] * t[1 + a] + sc[a] * sc[b] * t[u];
+    const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
+#pragma unroll
+    for (int f = 0; f < 28; f++) dS[dst * 28 + f] = out[f];
+}
+
+} // namespace
+
+size_t tc_tile_bytes(int K) { return (size_t)((K + kCols - 1) / kCols) * kTileBytes; }
+size_t tc_hdr_floats(int K) { return (size_t)((K + kCols - 1) / kCols) * 32; }
+size_t tc_tmax_floats(int64_t N, int K) { return (size_t)((N + 31) / 32) * (size_t)((K + kCols - 1) / kCols); }
+
+int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, cudaStream_t st, Prof *pf)
+{
+    const int nt = (K + kCols - 1) / kCols;
+    pf->begin(VBGS_PROF_MSTEP, st);
+    if (bf16) k_coef_tiles<true><<<nt, 128, 0, st>>>(rec, K, tiles, hdr);
+    else      k_coef_tiles<false><<<nt, 128, 0, st>>>(rec, K, tiles, hdr);
+    pf->end(st);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+
+int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
+                    const float *hdr, const float *tmax, const float *minlse, double *part, size_t part_cap_doubles,
+                    const int *kperm, double *dS, int *flags, int num_sms, cudaStream_t st, Prof *pf)
+{
+    const int ntiles = (K + kCols - 1) / kCols;
+    const int64_t nchunks = (N + kChunk2 - 1) / kChunk2;
+    int splits = std::max(1, std::min<int>((int)std::min<int64_t>(nchunks, 64), (4 * num_sms + ntiles - 1) / ntiles));
+    while (splits > 1 && (size_t)splits * (size_t)K * 28 > part_cap_doubles) splits--;
+    if ((size_t)K * 28 > part_cap_doubles) return -2;
+    const int64_t cps = (nchunks + splits - 1) / splits;
+    splits = (int)((nchunks + cps - 1) / cps);
+    const size_t smem = sizeof(Smem2) + 128;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[bf16]) {
+        cudaError_t e = bf16 ? cudaFuncSetAttribute(k_pass2_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                             : cudaFuncSetAttribute(k_pass2_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return -1;
+        attr_set[bf16] = true;
+    }
+    dim3 grid(ntiles, splits);
+    pf->begin(VBGS_PROF_PASS2, st);
+    if (bf16) k_pass2_tc<true><<<grid, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, cps, tmax, minlse, part, flags);
+    else      k_pass2_tc<false><<<grid, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, cps, tmax, minlse, part, flags);
+    pf->end(st);
+    pf->begin(VBGS_PROF_REDUCE, st);
+    k_reduce_splits_tile<<<(K + 127) / 128, 128, 0, st>>>(part, splits, K, hdr, kperm, dS);
+    pf->end(st);
+    return cudaGetLastError() == cudaSuccess ? 2 : -1;
+}
+
+int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
+                    double2 *part, size_t part_cap_doubles, float *tmax, int *flags, int num_sms, int *splits_out,
+                    cudaStream_t st, Prof *pf)
+{
+    const int ntiles = (K + kCols - 1) / kCols;
+    const int ptiles = (int)((N + kRows - 1) / kRows);
+    // K-splits: many small CTAs (two resident per SM) that the hardware
+    // scheduler balances, with the number of waves close to an integer so the
+    // last wave is not nearly empty; a mild penalty per split for pipeline fill.
+    int splits = 1;
+    {
+        const double slots = 2.0 * num_sms;
+        double best = -1.0;
+        const int smax = std::max(1, std::min(64, ntiles / 4));
+        for (int sp = 1; sp <= smax; sp++) {
+            const int tp = (ntiles + sp - 1) / sp;
+            const int sreal = (ntiles + tp - 1) / tp;
+            const double waves = ptiles * (double)sreal / slots;
+            const double eff = waves / std::ceil(waves) - 0.004 * sreal;
+            if (eff > best + 1e-9) { best = eff; splits = sreal; }
+        }
+    }
+    while (splits > 1 && (size_t)splits * (size_t)N * 2 > part_cap_doubles) splits--;
+    const int tps = (ntiles + splits - 1) / splits;
+    splits = (ntiles + tps - 1) / tps;
+    *splits_out = splits;
+    const size_t smem = sizeof(Smem) + 1024;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[bf16]) {
+        cudaError_t e = bf16 ? cudaFuncSetAttribute(k_pass1_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                             : cudaFuncSetAttribute(k_pass1_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return -1;
+        attr_set[bf16] = true;
+    }
+    dim3 grid(ptiles, splits);
+    pf->begin(VBGS_PROF_PASS1, st);
+    if (bf16) k_pass1_tc<true><<<grid, kThreadsTC, smem, st>>>(X, N, K, tiles, hdr, ntiles, tps, part, tmax, flags);
+    else      k_pass1_tc<false><<<grid, kThreadsTC, smem, st>>>(X, N, K, tiles, hdr, ntiles, tps, part, tmax, flags);
+    pf->end(st);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+} // namespace vbgs

@@ -9,8 +9,7 @@
 //            triangle row-major, [27] c_k (constant of log rho_nk without
 //            the -psi(sum alpha) term), [28..31] pad
 //   rec32  : K x 32 floats, the same record in FP32, log2 units
-//   klk    : K doubles, per-component KL_NW + Dirichlet terms
-//   aq, ap : K doubles, Dirichlet parameters of posterior and effective prior
+//   pcache : K x 40 doubles, effective-prior terms of the frame (+ block sums)
 //   lse    : N doubles, logsumexp_k of the logits without -psi(sum alpha)
 //   scal   : small FP64 scalars (psi(sum alpha), KL total, sum lse, ...)
 #pragma once
@@ -125,9 +124,13 @@ struct EstepBuffers {
 
 // ---- kernels / launchers (return number of launches, or -1 on error) ----
 int launch_stage_points(const double *src, int64_t N, double *X, int *flags, cudaStream_t st, Prof *pf);
+// Posterior update.  dS == nullptr: the posterior is the effective prior
+// prior0 (+) S_past (frame start), whose per-component terms are cached in
+// `cache` (mstep_cache_doubles(K) doubles) for the KL of later iterations.
+size_t mstep_cache_doubles(int K);
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
-                 const int *kinv, double *rec, float *rec32, double *klk, double *aq, double *ap,
-                 double *dN, int *flags, double *scal, cudaStream_t st, Prof *pf);
+                 const int *kinv, double *rec, float *rec32, double *cache, int *flags, double *scal,
+                 cudaStream_t st, Prof *pf);
 size_t sort_temp_bytes(int64_t n);
 int launch_point_order(const double *X, int64_t N, const BoxParams &box, SortBuffers &sb, double *Xs,
                        int *pidx, cudaStream_t st, Prof *pf);
@@ -140,6 +143,23 @@ int launch_elbo(double *scal, int64_t N, double *elbo_out, cudaStream_t st, Prof
 int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats, cudaStream_t st,
                            Prof *pf);
 size_t estep_cuda_core_scratch(int64_t N, int K, int precision);
+int launch_lse_merge(const double2 *part, int nsplit, int64_t N, double *lse, double *lse_part, float *minlse,
+                     double *sum_out, cudaStream_t st, Prof *pf);
+int launch_pass2_fp32(const EstepBuffers &B, int tpb, int tkc, cudaStream_t st, Prof *pf);
+
+// Tensor-core form (vbgs_estep_tc.cu): coefficient tiles of 128 components
+// (FP16/BF16 hi/lo, 16 KB each, in the MMA's shared-memory layout) with a
+// 32-float frame header each, and pass 1 on tcgen05 with TMEM accumulators.
+size_t tc_tile_bytes(int K);
+size_t tc_hdr_floats(int K);
+size_t tc_tmax_floats(int64_t N, int K);
+int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, cudaStream_t st, Prof *pf);
+int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
+                    const float *hdr, const float *tmax, const float *minlse, double *part, size_t part_cap_doubles,
+                    const int *kperm, double *dS, int *flags, int num_sms, cudaStream_t st, Prof *pf);
+int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
+                    double2 *part, size_t part_cap_doubles, float *tmax, int *flags, int num_sms, int *splits_out,
+                    cudaStream_t st, Prof *pf);
 
 } // namespace vbgs
 
@@ -153,6 +173,9 @@ struct vbgs_ctx {
     int *d_kperm = nullptr, *d_kinv = nullptr, *d_pidx = nullptr;
     double *d_Xs = nullptr;          // staged points in Morton order
     float *d_tmax = nullptr, *d_minlse = nullptr;
+    unsigned char *d_tc_tiles = nullptr;   // tensor-core coefficient tiles
+    float *d_tc_hdr = nullptr;
+    int num_sms = 152;
     size_t tmax_cap = 0;
     bool last_sorted = false;
     vbgs::MstepParams mp{};
@@ -160,7 +183,7 @@ struct vbgs_ctx {
     double *d_m0 = nullptr, *d_Spast = nullptr, *d_dS = nullptr, *d_zero = nullptr;
     double *d_rec = nullptr;
     float *d_rec32 = nullptr;
-    double *d_klk = nullptr, *d_aq = nullptr, *d_ap = nullptr, *d_dN = nullptr;
+    double *d_pcache = nullptr;
     double *d_scal = nullptr, *d_elbo = nullptr;
     int *d_flags = nullptr;
     int elbo_cap = 0;

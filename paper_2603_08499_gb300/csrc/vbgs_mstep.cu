@@ -38,19 +38,34 @@ __device__ double dg_digamma(double x)
     return log(x) - 0.5 / x - p * t - shift;
 }
 
-// Sum over i = 1..6 of f(a + (1 - i)/2).
+// psi_6(a) = sum_{i=0..5} psi(a - i/2): two series evaluations (at a and
+// a - 1/2) and the recurrence psi(x - 1) = psi(x) - 1/(x - 1) for the rest.
 __device__ double mv_digamma6(double a)
 {
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < 6; i++) s += dg_digamma(a - 0.5 * i);
+    for (int h = 0; h < 2; h++) {
+        const double x = a - 0.5 * h;
+        double p = dg_digamma(x);
+        s += p;
+        p -= 1.0 / (x - 1.0); s += p;     // psi(x - 1)
+        p -= 1.0 / (x - 2.0); s += p;     // psi(x - 2)
+    }
     return s;
 }
+// ln Gamma_6(a) = 7.5 ln pi + sum_{i=0..5} lnGamma(a - i/2), with
+// lnGamma(x - 1) = lnGamma(x) - ln(x - 1).
 __device__ double mv_lgamma6(double a)
 {
-    double s = 7.5 * kLnPi;   // D(D-1)/4 ln pi with D = 6
+    double s = 7.5 * kLnPi;
 #pragma unroll
-    for (int i = 0; i < 6; i++) s += lgamma(a - 0.5 * i);
+    for (int h = 0; h < 2; h++) {
+        const double x = a - 0.5 * h;
+        double g = lgamma(x);
+        s += g;
+        g -= log(x - 1.0); s += g;
+        g -= log(x - 2.0); s += g;
+    }
     return s;
 }
 
@@ -119,112 +134,154 @@ __device__ void trinv6(const double L[36], double Li[36])
     }
 }
 
+// Per-component cache of the effective prior p = prior0 (+) S_past, fixed
+// within a frame: alpha, beta, nu, m (6), W^-1 upper (21), ln|W^-1|,
+// ln Gamma_6(nu/2), ln Gamma(alpha).
+constexpr int kPC = 40;
+
+// Block-level fixed-order sums of 4 values (klk, aq, ap, dN) -> part[block].
+__device__ void block_sums4(double v0, double v1, double v2, double v3, double *__restrict__ part)
+{
+    __shared__ double sh[4][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, o);
+        v1 += __shfl_down_sync(0xffffffffu, v1, o);
+        v2 += __shfl_down_sync(0xffffffffu, v2, o);
+        v3 += __shfl_down_sync(0xffffffffu, v3, o);
+    }
+    if (lane == 0) { sh[0][w] = v0; sh[1][w] = v1; sh[2][w] = v2; sh[3][w] = v3; }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        const int q = threadIdx.x;
+        part[(size_t)blockIdx.x * 4 + q] = ((sh[q][0] + sh[q][1]) + (sh[q][2] + sh[q][3]));
+    }
+}
+
+// dS == nullptr: the posterior is the effective prior (frame start): write its
+// E-step record and the prior cache; KL terms are zero.  Otherwise: the
+// posterior prior0 (+) (S_past + dS), its record, and KL against the cache.
 __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__restrict__ m0,
                                                const double *__restrict__ Spast,
                                                const double *__restrict__ dS,
                                                const int *__restrict__ kinv,
                                                double *__restrict__ rec, float *__restrict__ rec32,
-                                               double *__restrict__ klk, double *__restrict__ aq_out,
-                                               double *__restrict__ ap_out, double *__restrict__ dN_out,
+                                               double *__restrict__ pc, double *__restrict__ bpart,
                                                int *__restrict__ flags)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P.K) return;
-    double sp[28], st[28], m0k[6];
+    double kl = 0.0, aq = 0.0, ap = 0.0, dn = 0.0;
+    if (k < P.K) {
+        double st[28], m0k[6];
 #pragma unroll
-    for (int f = 0; f < 28; f++) {
-        sp[f] = Spast[(size_t)k * 28 + f];
-        st[f] = sp[f] + (dS ? dS[(size_t)k * 28 + f] : 0.0);
-    }
+        for (int f = 0; f < 28; f++) st[f] = Spast[(size_t)k * 28 + f] + (dS ? dS[(size_t)k * 28 + f] : 0.0);
 #pragma unroll
-    for (int i = 0; i < 6; i++) m0k[i] = m0[(size_t)k * 6 + i];
+        for (int i = 0; i < 6; i++) m0k[i] = m0[(size_t)k * 6 + i];
+        double bq, nq, mq[6], Aq[36];
+        nw_from_stats(P, m0k, st, aq, bq, nq, mq, Aq);
+        double Lq[36], Li[36];
+        const bool ok = chol6(Aq, Lq);
+        if (!ok) atomicCAS(&flags[FL_NONPD], 0, k + 1);
+        double ldq = 0.0;   // ln|W^-1|
+#pragma unroll
+        for (int i = 0; i < 6; i++) ldq += 2.0 * log(Lq[i * 6 + i]);
+        trinv6(Lq, Li);
 
-    double ap, bp, np, mp[6], Ap[36];
-    double aq, bq, nq, mq[6], Aq[36];
-    nw_from_stats(P, m0k, sp, ap, bp, np, mp, Ap);
-    nw_from_stats(P, m0k, st, aq, bq, nq, mq, Aq);
+        // E-step record: quad = nu |L^-1 (x - m)|^2 = |M (x - m)|^2.
+        const double sn = sqrt(nq);
+        const size_t pos = kinv ? (size_t)kinv[k] : (size_t)k;   // record position (processing order)
+        double *r = rec + pos * VBGS_REC;
+        float *r32 = rec32 + pos * VBGS_REC;
+        const float s2 = 1.2011224087864498f;   // sqrt(log2 e): FP32 record in log2 units
+#pragma unroll
+        for (int i = 0; i < 6; i++) { r[i] = mq[i]; r32[i] = (float)mq[i]; }
+#pragma unroll
+        for (int i = 0; i < 6; i++)
+#pragma unroll
+            for (int j = 0; j <= i; j++) {
+                double v = sn * Li[i * 6 + j];
+                r[6 + tri(i, j)] = v;
+                r32[6 + tri(i, j)] = (float)v * s2;
+            }
+        const double psi_nu = mv_digamma6(0.5 * nq);
+        const double psi_a = dg_digamma(aq);
+        const double elogdet = psi_nu + 6.0 * kLn2 - ldq;
+        const double c = psi_a + 0.5 * elogdet - 3.0 * kLn2Pi - 3.0 / bq;
+        r[27] = c;
+        r32[27] = (float)(c * 1.4426950408889634);
+#pragma unroll
+        for (int i = 28; i < 32; i++) { r[i] = 0.0; r32[i] = 0.f; }
 
-    double Lq[36], Lp[36], Li[36];
-    bool ok = chol6(Aq, Lq);
-    ok = chol6(Ap, Lp) && ok;
-    if (!ok) atomicCAS(&flags[FL_NONPD], 0, k + 1);
-    double ldq = 0.0, ldp = 0.0;   // ln|W^-1|
+        double *cache = pc + (size_t)k * kPC;
+        if (!dS) {
+            cache[0] = aq; cache[1] = bq; cache[2] = nq;
 #pragma unroll
-    for (int i = 0; i < 6; i++) { ldq += 2.0 * log(Lq[i * 6 + i]); ldp += 2.0 * log(Lp[i * 6 + i]); }
-    trinv6(Lq, Li);
-
-    // E-step record: quad = nu |L^-1 (x - m)|^2 = |M (x - m)|^2.
-    const double sn = sqrt(nq);
-    const size_t pos = kinv ? (size_t)kinv[k] : (size_t)k;   // record position (processing order)
-    double *r = rec + pos * VBGS_REC;
-    float *r32 = rec32 + pos * VBGS_REC;
-    const float s2 = 1.2011224087864498f;   // sqrt(log2 e): FP32 record in log2 units
+            for (int i = 0; i < 6; i++) cache[3 + i] = mq[i];
+            int u = 9;
 #pragma unroll
-    for (int i = 0; i < 6; i++) { r[i] = mq[i]; r32[i] = (float)mq[i]; }
+            for (int i = 0; i < 6; i++)
 #pragma unroll
-    for (int i = 0; i < 6; i++)
+                for (int j = i; j < 6; j++, u++) cache[u] = Aq[i * 6 + j];
+            cache[30] = ldq;
+            cache[31] = mv_lgamma6(0.5 * nq);
+            cache[32] = lgamma(aq);
+            ap = aq;
+        } else {
+            // KL(NW_q || NW_p) against the cached effective prior.
+            ap = cache[0];
+            const double bp = cache[1], np = cache[2], ldp = cache[30];
+            double Ap[36];
+            {
+                int u = 9;
 #pragma unroll
-        for (int j = 0; j <= i; j++) {
-            double v = sn * Li[i * 6 + j];
-            r[6 + tri(i, j)] = v;
-            r32[6 + tri(i, j)] = (float)v * s2;
+                for (int i = 0; i < 6; i++)
+#pragma unroll
+                    for (int j = i; j < 6; j++, u++) { Ap[i * 6 + j] = cache[u]; Ap[j * 6 + i] = cache[u]; }
+            }
+            double maha = 0.0;   // (m_q - m_p)^T W_q (m_q - m_p) = |L^-1 (m_q - m_p)|^2
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                double t = 0.0;
+#pragma unroll
+                for (int j = 0; j <= i; j++) t += Li[i * 6 + j] * (mq[j] - cache[3 + j]);
+                maha += t * t;
+            }
+            // tr(W_p^-1 W_q) with W_q = Li^T Li: sum_i (Li Ap Li^T)_ii
+            //   = sum_i sum_{l <= i} (Li Ap)_il Li_il.
+            double tr = 0.0;
+#pragma unroll
+            for (int i = 0; i < 6; i++)
+#pragma unroll
+                for (int l = 0; l <= i; l++) {
+                    double b = 0.0;
+#pragma unroll
+                    for (int j = 0; j <= i; j++) b += Li[i * 6 + j] * Ap[j * 6 + l];
+                    tr += b * Li[i * 6 + l];
+                }
+            kl = 0.5 * (6.0 * bp / bq - 6.0 + bp * nq * maha + 6.0 * log(bq / bp));
+            kl += 0.5 * (nq - np) * psi_nu - 3.0 * nq + 0.5 * nq * tr + 0.5 * np * (ldq - ldp) + cache[31] -
+                  mv_lgamma6(0.5 * nq);
+            // Per-component part of KL(Dir(alpha_q) || Dir(alpha_p)); the psi(sum)
+            // and lnGamma(sum) terms are added after the cross-component sums.
+            kl += -lgamma(aq) + cache[32] + (aq - ap) * psi_a;
+            dn = st[0] - Spast[(size_t)k * 28];
         }
-    const double elogdet = mv_digamma6(0.5 * nq) + 6.0 * kLn2 - ldq;
-    const double c = dg_digamma(aq) + 0.5 * elogdet - 3.0 * kLn2Pi - 3.0 / bq;
-    r[27] = c;
-    r32[27] = (float)(c * 1.4426950408889634);
-#pragma unroll
-    for (int i = 28; i < 32; i++) { r[i] = 0.0; r32[i] = 0.f; }
-
-    // KL(NW_q || NW_p).
-    double d[6];
-#pragma unroll
-    for (int i = 0; i < 6; i++) d[i] = mq[i] - mp[i];
-    double maha = 0.0;   // (m_q - m_p)^T W_q (m_q - m_p) = |L^-1 (m_q - m_p)|^2
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-        double t = 0.0;
-#pragma unroll
-        for (int j = 0; j <= i; j++) t += Li[i * 6 + j] * d[j];
-        maha += t * t;
     }
-    // tr(W_p^-1 W_q) with W_q = Li^T Li: sum_i (Li Ap Li^T)_ii.
-    double tr = 0.0;
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-#pragma unroll
-        for (int l = 0; l < 6; l++) {
-            double b = 0.0;
-#pragma unroll
-            for (int j = 0; j <= i; j++) b += Li[i * 6 + j] * Ap[j * 6 + l];
-            if (l <= i) tr += b * Li[i * 6 + l];
-        }
-    }
-    double kl = 0.5 * (6.0 * bp / bq - 6.0 + bp * nq * maha + 6.0 * log(bq / bp));
-    kl += 0.5 * (nq - np) * mv_digamma6(0.5 * nq) - 3.0 * nq + 0.5 * nq * tr
-        + 0.5 * np * (ldq - ldp) + mv_lgamma6(0.5 * np) - mv_lgamma6(0.5 * nq);
-    // Per-component part of KL(Dir(alpha_q) || Dir(alpha_p)); the psi(sum)
-    // and lnGamma(sum) terms are added after the cross-component sums.
-    kl += -lgamma(aq) + lgamma(ap) + (aq - ap) * dg_digamma(aq);
-    klk[k] = kl;
-    aq_out[k] = aq;
-    ap_out[k] = ap;
-    dN_out[k] = st[0] - sp[0];
+    block_sums4(kl, aq, ap, dn, bpart);
 }
 
-// One block: deterministic fixed-order sums over components, then the
-// Dirichlet terms that need the totals.  scal[SC_PSI_AHAT] = psi(sum alpha_q);
+// One block: fixed-order sums of the per-block partials, then the Dirichlet
+// terms that need the totals.  scal[SC_PSI_AHAT] = psi(sum alpha_q);
 // scal[SC_KL_TOTAL] = sum_k KL_NW,k + KL_Dir.
-__global__ void __launch_bounds__(1024) k_mstep_finalize(const double *__restrict__ klk,
-                                                         const double *__restrict__ aq,
-                                                         const double *__restrict__ ap,
-                                                         const double *__restrict__ dN, int K,
+__global__ void __launch_bounds__(1024) k_mstep_finalize(const double *__restrict__ bpart, int nblocks,
                                                          double *__restrict__ scal)
 {
     __shared__ double sh[4][32];
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        s0 += klk[k]; s1 += aq[k]; s2 += ap[k]; s3 += dN[k];
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        s0 += bpart[(size_t)b * 4]; s1 += bpart[(size_t)b * 4 + 1];
+        s2 += bpart[(size_t)b * 4 + 2]; s3 += bpart[(size_t)b * 4 + 3];
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -280,16 +337,20 @@ __global__ void k_stage(const double *__restrict__ src, int64_t N, double *__res
 
 } // namespace
 
+size_t mstep_cache_doubles(int K) { return (size_t)K * kPC + (size_t)((K + 127) / 128) * 4; }
+
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
-                 const int *kinv, double *rec, float *rec32, double *klk, double *aq, double *ap,
-                 double *dN, int *flags, double *scal, cudaStream_t st, Prof *pf)
+                 const int *kinv, double *rec, float *rec32, double *cache, int *flags, double *scal,
+                 cudaStream_t st, Prof *pf)
 {
     const int K = P.K;
+    const int nb = (K + 127) / 128;
+    double *bpart = cache + (size_t)K * kPC;
     pf->begin(VBGS_PROF_MSTEP, st);
-    k_mstep<<<(K + 127) / 128, 128, 0, st>>>(P, m0, Spast, dS, kinv, rec, rec32, klk, aq, ap, dN, flags);
+    k_mstep<<<nb, 128, 0, st>>>(P, m0, Spast, dS, kinv, rec, rec32, cache, bpart, flags);
     pf->end(st);
     pf->begin(VBGS_PROF_MSTEP, st);
-    k_mstep_finalize<<<1, 1024, 0, st>>>(klk, aq, ap, dN, K, scal);
+    k_mstep_finalize<<<1, 1024, 0, st>>>(bpart, nb, scal);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 2 : -1;
 }

@@ -1,7 +1,9 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
 same seeded inputs.  Tolerances use the paper's relative error (Eq. relerr):
-FP64 form <= 1e-10 on every statistic array and on the ELBO; the FP32 form
-<= 1e-3 per statistic array and <= 1e-4 on the ELBO."""
+FP64 form <= 1e-10 on every statistic array and on the ELBO; the FP32 and
+tensor-core FP16 hi/lo forms <= 1e-3 per statistic array and <= 1e-4 on the
+ELBO (lse_n: 1e-4 for FP32, 1e-3 for FP16 hi/lo, whose logits carry the
+FP32 accumulation error of the expanded quadratic form)."""
 from __future__ import annotations
 
 import numpy as np
@@ -13,7 +15,8 @@ from paper_2603_08499_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": {"stat": 1e-10, "elbo": 1e-10, "lse": 1e-10},
-       "fp32": {"stat": 1e-3, "elbo": 1e-4, "lse": 1e-4}}
+       "fp32": {"stat": 1e-3, "elbo": 1e-4, "lse": 1e-4},
+       "fp16x3": {"stat": 1e-3, "elbo": 1e-4, "lse": 1e-3}}
 
 
 @pytest.fixture(scope="module")
@@ -52,7 +55,7 @@ def check_frame(V, X, prior, n_iters, form, S_past=None, flags=0):
     return trace, e_ref
 
 
-@pytest.mark.parametrize("form", ["fp64", "fp32"])
+@pytest.mark.parametrize("form", ["fp64", "fp32", "fp16x3"])
 def test_mixture_small_several_tiles_ragged(V, form):
     X, pr = synth.c1_workload(seed=11, N=2_345, K=197)
     check_frame(V, X, pr, 6, form)
@@ -88,12 +91,13 @@ def test_skip_and_order_change_nothing_beyond_rounding(V, form):
         assert O.relerr(out[f][2], out[0][2]) <= tol
 
 
-def test_mixture_full_size_fp32(V):
+@pytest.mark.parametrize("form", ["fp32", "fp16x3"])
+def test_mixture_full_size_reduced_precision(V, form):
     X, pr = synth.c1_workload(seed=1, N=10_000, K=1_000)
-    check_frame(V, X, pr, 10, "fp32")
+    check_frame(V, X, pr, 10, form)
 
 
-@pytest.mark.parametrize("form", ["fp64", "fp32"])
+@pytest.mark.parametrize("form", ["fp64", "fp32", "fp16x3"])
 def test_k1_and_tiny_edges(V, form):
     X, pr = synth.c1_workload(seed=12, N=37, K=1)
     check_frame(V, X, pr, 3, form)
@@ -134,8 +138,37 @@ def test_one_iteration_from_given_state(V):
     X0 = synth.room_frame(0, seed=3, width=64, height=64, room=room)
     _, S0, _, _ = O.cavi_frame(X0, pr, np.zeros((600, 28)), 2)
     X1 = synth.room_frame(1, seed=3, width=64, height=64, room=room)
-    for form in ("fp64", "fp32"):
+    for form in ("fp64", "fp32", "fp16x3"):
         check_frame(V, X1, pr, 1, form, S_past=S0)
+
+
+def test_room_one_iteration_full_size_reduced_precision(V):
+    """One iteration from a shared FP64 state after two full room frames
+    (K = 50,000, 200 x 200 frames): the reduced-precision forms against the
+    FP64 form through the same C ABI (the frame-by-frame error)."""
+    import torch
+    room = synth.Room(seed=2)
+    pr = synth.room_prior(50_000, seed=2)
+    frames = [torch.from_numpy(synth.room_frame(t, seed=2, room=room)).cuda() for t in range(3)]
+    ref = V.Model(pr, "fp64")
+    for f in frames[:2]:
+        ref.update(f, 3)
+    S = ref.stats()
+    ref.close()
+    out = {}
+    for form in ("fp64", "fp32", "fp16x3"):
+        m = V.Model(pr, form)
+        m.set_stats(S)
+        e = m.update(frames[2], 1)
+        out[form] = (e, m.frame_stats(), m.lse(frames[2].shape[0]))
+        m.close()
+    for form in ("fp32", "fp16x3"):
+        e, dS, lse = out[form]
+        e0, dS0, lse0 = out["fp64"]
+        assert O.relerr(e, e0) <= TOL[form]["elbo"]
+        for name, err in stat_errors(dS, dS0).items():
+            assert err <= TOL[form]["stat"], (form, name, err)
+        assert O.relerr(lse, lse0) <= TOL[form]["lse"]
 
 
 def test_device_points_equal_host_points(V):
@@ -183,7 +216,7 @@ def test_invalid_points_leave_state_unchanged(V):
         m.set_stats(np.full((20, 28), np.nan))
 
 
-@pytest.mark.parametrize("form", ["fp64", "fp32"])
+@pytest.mark.parametrize("form", ["fp64", "fp32", "fp16x3"])
 def test_full_size_room_frame_sampled(V, form):
     """The benchmark shape (K = 50,000, one 200 x 200 frame, 3 iterations) in
     the launch configuration the benchmark uses: invariants at full size and
@@ -192,14 +225,14 @@ def test_full_size_room_frame_sampled(V, form):
     room = synth.Room(seed=2)
     pr = synth.room_prior(50_000, seed=2)
     X = synth.room_frame(0, seed=2, room=room)
-    tol = TOL[form]["lse"] if form == "fp32" else 1e-12
+    tol = TOL[form]["lse"] if form != "fp64" else 1e-12
     m = V.Model(pr, form)
     trace = m.update(torch.from_numpy(X).cuda(), 3)
     dS = m.frame_stats()
     N = X.shape[0]
-    assert abs(dS[:, 0].sum() - N) <= (1e-9 if form == "fp64" else 1e-4) * N
-    assert O.relerr(dS[:, 1:7].sum(0), X.sum(0)) <= (1e-12 if form == "fp64" else 1e-4)
-    assert np.all(np.diff(trace) >= -(1e-9 if form == "fp64" else 1e-6) * abs(trace[-1]))
+    assert abs(dS[:, 0].sum() - N) <= (1e-9 if form == "fp64" else 1e-3) * N
+    assert O.relerr(dS[:, 1:7].sum(0), X.sum(0)) <= (1e-12 if form == "fp64" else 1e-3)
+    assert np.all(np.diff(trace) >= -(1e-9 if form == "fp64" else 1e-5) * abs(trace[-1]))
     # the ELBO of the first iteration is under the prior: check sampled points
     m2 = V.Model(pr, form)
     e, lse = m2.elbo(X, want_lse=True)
