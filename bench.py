@@ -49,12 +49,26 @@ PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12
 PEAK_FP64_TFLOPS = 1.25
 PEAK_EX2_G = SMS * 16 * SM_MHZ * 1e6 / 1e9
 
-# Algorithmic work per (point, component) pair of each pass:
-# factored logit c - 1/2 |M (x - m)|^2 = 6 sub + 21 FMA + 6 FMA + 1 FMA = 62 flops;
-# pass 1 adds the online max/sum (2 flops) and one exp; pass 2 adds the
-# subtraction of lse (1 flop), one exp and 28 FMAs into the statistics (56).
+# Algorithmic work per (point, component) pair of each pass.
+# CUDA-core forms: factored logit c - 1/2 |M (x - m)|^2 = 6 sub + 21 FMA +
+# 6 FMA + 1 FMA = 62 flops; pass 1 adds the online max/sum (2 flops) and one
+# exp; pass 2 adds the subtraction of lse (1 flop), one exp and 28 FMAs into
+# the statistics (56).  Tensor-core form (MMA flops): logits = 3 hi/lo
+# products x 2 x 32 features = 192; statistics = 3 products x 2 x 32 = 192.
 FLOPS_PASS1 = 64
 FLOPS_PASS2 = 119
+TC_FLOPS_PASS1 = 192
+TC_FLOPS_PASS2 = 384
+
+
+def measured_tensor_peak():
+    """Dense BF16 burst peak from MEASURED_PEAKS.json (FP16 has the same
+    nominal rate), else the profiling fallback."""
+    try:
+        d = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+        return float(d["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16 burst; fp16 nominal ratio 1)"
+    except Exception:
+        return 1900.0, "fallback 1.9 PFLOP/s"
 
 
 def log(*a):
@@ -173,14 +187,17 @@ def run_reference(args):
 
 
 def timed_stream(V, prior, dev_frames, form, warmup, steps, stream, flush, profile=False, host_frames=None,
-                 flags=0):
+                 flags=0, keep_last_state=False):
     """Run warmup + steps frames through a fresh model; per-step device times
     with CUDA events (or host wall time for host inputs)."""
     import torch
     m = V.Model(prior, form, cuda_stream=stream.cuda_stream, flags=flags)
     traces, times, launches = [], [], 0
     pairs = 0
+    state_before_last = None
     for t in range(warmup + steps):
+        if keep_last_state and t == warmup + steps - 1:
+            state_before_last = m.stats()       # outside the timed events
         timed = t >= warmup
         if timed and profile and t == warmup:
             m.profile(True)
@@ -207,28 +224,44 @@ def timed_stream(V, prior, dev_frames, form, warmup, steps, stream, flush, profi
             launches += m.launches()
             pairs += X.shape[0] * K_COMP * ITERS
     prof = m.profile_read() if profile else None
+    prof_pairs = m.profile_pairs() if profile else None
+    final_state = m.stats() if keep_last_state else None
     m.close()
-    return {"times": times, "traces": traces, "launches": launches, "pairs": pairs, "prof": prof}
+    return {"times": times, "traces": traces, "launches": launches, "pairs": pairs, "prof": prof,
+            "prof_pairs": prof_pairs, "state_before_last": state_before_last, "final_state": final_state}
 
 
-def roofline(form, prof, n_points_timed, steps):
-    """Roofline of the dominant kernel from the library's live event timing."""
-    if not prof:
-        return None
-    name = max(("pass1", "pass2"), key=lambda k: prof[k][0])
-    ms, n = prof[name]
-    if n == 0:
-        return None
-    pairs_per_launch = n_points_timed * K_COMP * ITERS / n
-    flops = (FLOPS_PASS1 if name == "pass1" else FLOPS_PASS2) * pairs_per_launch
-    avg_s = ms * 1e-3 / n
-    achieved = flops / avg_s / 1e12
-    peak = PEAK_FP64_TFLOPS if form == "fp64" else PEAK_FP32_TFLOPS
-    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "avg_launch_ms": ms / n, "launches": n,
-            "peak_source": ("nominal GB300 FP64 rate" if form == "fp64"
-                            else "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"),
-            "share_of_step": ms / max(1e-9, sum(v[0] for v in prof.values()))}
+def roofline(form, prof, prof_pairs):
+    """Rooflines of pass 1 and pass 2 from the library's live event timing and
+    work counters; the dominant (longer) one is the headline."""
+    if not prof or not prof_pairs:
+        return None, {}
+    p1_pairs, p2_pairs = prof_pairs
+    tc = form in ("fp16x3", "bf16x3")
+    tpeak, tsrc = measured_tensor_peak()
+    out = {}
+    for name, pairs in (("pass1", p1_pairs), ("pass2", p2_pairs)):
+        ms, n = prof[name]
+        if n == 0 or ms <= 0:
+            continue
+        if tc:
+            flops = (TC_FLOPS_PASS1 if name == "pass1" else TC_FLOPS_PASS2) * pairs
+            bound, peak, src = "tensor", tpeak, tsrc
+        else:
+            flops = (FLOPS_PASS1 if name == "pass1" else FLOPS_PASS2) * pairs
+            bound = "alu"
+            peak = PEAK_FP64_TFLOPS if form == "fp64" else PEAK_FP32_TFLOPS
+            src = "nominal GB300 FP64 rate" if form == "fp64" else "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"
+        achieved = flops / (ms * 1e-3) / 1e12
+        out[name] = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "avg_launch_ms": ms / n, "launches": n,
+                     "pairs_evaluated": pairs, "peak_source": src,
+                     "exp_rate_G_per_s": pairs / (ms * 1e-3) / 1e9,
+                     "share_of_step": ms / max(1e-9, sum(v[0] for v in prof.values()))}
+    if not out:
+        return None, {}
+    head = max(out.values(), key=lambda r: r["avg_launch_ms"] * r["launches"])
+    return head, out
 
 
 def run_ours(args):
@@ -287,15 +320,29 @@ def run_ours(args):
     extra = {}
     if (form != "fp64" or args.flags != V.VBGS_FLAG_PLAIN) and rank == 0:
         # the plain FP64 form: caller's order, every tile evaluated
-        ref = timed_stream(V, prior, dev, "fp64", args.warmup, args.steps, stream, flush, flags=V.VBGS_FLAG_PLAIN)
+        ref = timed_stream(V, prior, dev, "fp64", args.warmup, args.steps, stream, flush, flags=V.VBGS_FLAG_PLAIN,
+                           keep_last_state=True)
         fp64_value = ref["pairs"] / sum(ref["times"])
         errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(res["traces"], ref["traces"])]
         extra["fp64_form"] = {"value": fp64_value, "unit": UNIT, "speedup": value / fp64_value}
         extra["elbo_relerr_vs_fp64"] = max(errs)
+        extra["elbo_relerr_vs_fp64_kind"] = "whole stream (drift after every frame of the run)"
+        # one-frame error: the form from the FP64 stream's state before its last frame
+        S0, S1 = ref["state_before_last"], ref["final_state"]
+        m = V.Model(prior, form, cuda_stream=stream.cuda_stream, flags=args.flags)
+        m.set_stats(S0)
+        tr = m.update(dev[args.warmup + args.steps - 1], ITERS)
+        dS, dS0 = m.stats() - S0, S1 - S0
+        m.close()
+        rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+        extra["one_frame_error_vs_fp64"] = {
+            "elbo": rel(tr, ref["traces"][-1]), "N": rel(dS[:, 0], dS0[:, 0]), "S1": rel(dS[:, 1:7], dS0[:, 1:7]),
+            "S2": rel(dS[:, 7:], dS0[:, 7:]),
+            "what": "last frame, 3 iterations, from the FP64 state before it (Eq. relerr, tau=1e-30)"}
 
     if rank == 0:
         n_pts = sum(X.shape[0] for X in timed_frames)
-        rl = roofline(form, res["prof"], n_pts, args.steps)
+        rl, rl_all = roofline(form, res["prof"], res["prof_pairs"])
         cpu_val, cpu_info = (None, None)
         if not args.no_cpu_baseline:
             cpu_val, cpu_info = cpu_oracle_rate(timed_frames[:2], prior, ITERS, args.cpu_budget)
@@ -311,6 +358,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": ITERS * 8 + 16},
             "gpu_launches": res["launches"],
             "roofline": rl,
+            "roofline_passes": rl_all,
             "clocks": clk,
             "probe_peaks": peaks,
             "kernel_ms": {k: v[0] for k, v in (res["prof"] or {}).items()},
@@ -334,7 +382,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=list(DTYPES), default="fp32")
+    ap.add_argument("--form", choices=list(DTYPES), default="fp16x3")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--flags", type=int, default=0,
                     help="VBGS_FLAG_* bits: 1 = caller's order, 2 = no pass-2 tile skipping (3 = plain)")

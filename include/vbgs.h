@@ -157,6 +157,10 @@ enum {
 };
 int vbgs_profile_enable(vbgs_ctx *ctx, int on);
 int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset);
+/* Work counters of the profiled calls since the last reset: pairs scored by
+ * pass 1 (every point against every component) and pairs pass 2 evaluated
+ * (the ones its skip bound did not rule out).  Synchronises the stream. */
+int vbgs_profile_pairs(vbgs_ctx *ctx, int64_t *pass1_pairs, int64_t *pass2_pairs);
 const char *vbgs_profile_name(int i);
 
 /* Measure this GPU's arithmetic peaks with short probe kernels (a few

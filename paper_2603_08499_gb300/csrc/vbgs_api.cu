@@ -118,7 +118,7 @@ int ensure_capacity(vbgs_ctx *ctx, int64_t N)
         int64_t cap = std::max<int64_t>(N, 1024);
         if ((rc = dalloc(ctx, &ctx->d_X, (size_t)cap * VBGS_XS))) return rc;
         if ((rc = dalloc(ctx, &ctx->d_lse, (size_t)cap))) return rc;
-        if ((rc = dalloc(ctx, &ctx->d_lse_part, (size_t)(cap + 255) / 256 + 1))) return rc;
+        if ((rc = dalloc(ctx, &ctx->d_lse_part, (size_t)(cap + 63) / 64 + 1))) return rc;
         if ((rc = dalloc(ctx, &ctx->d_Xs, (size_t)cap * VBGS_XS))) return rc;
         if ((rc = dalloc(ctx, &ctx->d_pidx, (size_t)cap))) return rc;
         if ((rc = dalloc(ctx, &ctx->d_minlse, (size_t)(cap + 31) / 32 + 1))) return rc;
@@ -142,6 +142,11 @@ int ensure_capacity(vbgs_ctx *ctx, int64_t N)
     if (tneed > ctx->tmax_cap) {
         if ((rc = dalloc(ctx, &ctx->d_tmax, tneed))) return rc;
         ctx->tmax_cap = tneed;
+    }
+    const size_t pneed = tc_plan_ints(std::max<int64_t>(N, 1), ctx->K);
+    if (is_tc(ctx) && pneed > ctx->plan_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_plan, pneed))) return rc;
+        ctx->plan_cap = pneed;
     }
     size_t need = estep_cuda_core_scratch(std::max<int64_t>(N, 1), ctx->K, is_tc(ctx) ? VBGS_FP32 : ctx->precision);
     if (is_tc(ctx))   // pass-1 partials of up to 64 K-splits
@@ -225,6 +230,7 @@ int order_frame(vbgs_ctx *ctx, int64_t N, bool points)
 
 int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
 {
+    if (ctx->prof.on) ctx->prof.pass1_pairs += N * (int64_t)ctx->K;
     if (N == 0) {
         CU(cudaMemsetAsync(ctx->d_scal + SC_SUM_LSE, 0, sizeof(double), ctx->stream));
         if (want_stats) CU(cudaMemsetAsync(ctx->d_dS, 0, sizeof(double) * ctx->K * VBGS_F, ctx->stream));
@@ -259,7 +265,7 @@ int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
         ctx->launches += l;
         if (want_stats) {
             l = launch_pass2_tc(B.X, ctx->d_lse, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
-                                B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_part, ctx->part_cap, ctx->d_kperm,
+                                B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
                                 ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->stream, &ctx->prof);
             if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
                                    cudaGetErrorString(cudaGetLastError()));
@@ -293,11 +299,13 @@ void free_all(vbgs_ctx *ctx)
                     ctx->d_pcache, ctx->d_scal, ctx->d_elbo,
                     ctx->d_flags, ctx->d_X, ctx->d_lse, ctx->d_lse_part, ctx->d_part,
                     ctx->d_kperm, ctx->d_kinv, ctx->d_pidx, ctx->d_Xs, ctx->d_tmax, ctx->d_minlse,
-                    ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp, ctx->d_tc_tiles, ctx->d_tc_hdr};
+                    ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp, ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_plan};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     ctx->prof.pool.clear();
+    if (ctx->prof.d_pairs) cudaFree(ctx->prof.d_pairs);
+    ctx->prof.d_pairs = nullptr;
 }
 
 } // namespace
@@ -563,6 +571,8 @@ int vbgs_profile_enable(vbgs_ctx *ctx, int on)
     if (on && ctx->prof.pool.empty()) {
         ctx->prof.pool.resize(4096);
         for (auto &e : ctx->prof.pool) CU(cudaEventCreate(&e));
+        CU(cudaMalloc(&ctx->prof.d_pairs, sizeof(unsigned long long)));
+        CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, sizeof(unsigned long long), ctx->stream));
     }
     ctx->prof.on = on != 0;
     return VBGS_OK;
@@ -576,6 +586,23 @@ int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset)
         if (launches) launches[i] = ctx->prof.n[i];
         if (reset) { ctx->prof.ms[i] = 0; ctx->prof.n[i] = 0; }
     }
+    if (reset && ctx->prof.d_pairs) {
+        CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, sizeof(unsigned long long), ctx->stream));
+        ctx->prof.pass1_pairs = 0;
+    }
+    return VBGS_OK;
+}
+
+int vbgs_profile_pairs(vbgs_ctx *ctx, int64_t *pass1_pairs, int64_t *pass2_pairs)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    unsigned long long p2 = 0;
+    if (ctx->prof.d_pairs) {
+        CU(cudaMemcpyAsync(&p2, ctx->prof.d_pairs, sizeof p2, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    if (pass1_pairs) *pass1_pairs = ctx->prof.pass1_pairs;
+    if (pass2_pairs) *pass2_pairs = (int64_t)p2;
     return VBGS_OK;
 }
 

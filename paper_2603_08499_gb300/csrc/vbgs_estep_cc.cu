@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X
                                                     double *__restrict__ part,
                                                     const float *__restrict__ tmax,
                                                     const float *__restrict__ minlse,
-                                                    int tpb, int tkc)
+                                                    int tpb, int tkc, unsigned long long *__restrict__ pairs)
 {
     constexpr bool kAnchored = sizeof(T) == 4;
     __shared__ T spt[kChunkN * 28];   // per point: x[6], lse, upper(x x^T)[21] (FP64 only)
@@ -241,6 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X
             for (int64_t w = nc / 32; w <= (nc + cnt - 1) / 32; w++) lmin = fminf(lmin, minlse[w]);
             if (b - lmin < -(float)kSkipNats) continue;
         }
+        if (pairs && threadIdx.x == 0) atomicAdd(pairs, (unsigned long long)cnt * (unsigned long long)min(kThreads, K - kt0));
         __syncthreads();
         for (int p = threadIdx.x; p < cnt; p += kThreads) {
             const double *xp = X + (nc + p) * VBGS_XS;
@@ -361,9 +362,11 @@ constexpr int kPPT32 = 2;
 int launch_lse_merge(const double2 *part, int nsplit, int64_t N, double *lse, double *lse_part, float *minlse,
                      double *sum_out, cudaStream_t st, Prof *pf)
 {
-    const int mb = (int)((N + 255) / 256);
+    // 64-point blocks: the FP64 exp/log of the merge is latency bound, so
+    // spread it over every SM
+    const int mb = (int)((N + 63) / 64);
     pf->begin(VBGS_PROF_MERGE, st);
-    k_merge<<<mb, 256, 0, st>>>(part, nsplit, N, lse, lse_part, minlse);
+    k_merge<<<mb, 64, 0, st>>>(part, nsplit, N, lse, lse_part, minlse);
     pf->end(st);
     pf->begin(VBGS_PROF_MERGE, st);
     k_sum<<<1, 1024, 0, st>>>(lse_part, mb, sum_out);
@@ -380,7 +383,8 @@ int launch_pass2_fp32(const EstepBuffers &B, int tpb, int tkc, cudaStream_t st, 
     if ((size_t)pl.p2_splits * (size_t)B.K * 28 > B.part_cap) return -2;
     dim3 g2(pl.p2_tiles, pl.p2_splits);
     pf->begin(VBGS_PROF_PASS2, st);
-    k_pass2<float><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec32, B.K, B.part, B.tmax, B.minlse, tpb, tkc);
+    k_pass2<float><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec32, B.K, B.part, B.tmax, B.minlse, tpb, tkc,
+                                            pf->on ? pf->d_pairs : nullptr);
     pf->end(st);
     pf->begin(VBGS_PROF_REDUCE, st);
     k_reduce_splits<<<(B.K + 127) / 128, 128, 0, st>>>(B.part, pl.p2_splits, B.K, B.rec32, B.kperm, B.dS);
@@ -414,9 +418,9 @@ int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats
     if (f64) k_pass1<double, kPPT64><<<g1, kThreads, 0, st>>>(B.X, B.N, B.rec, B.K, pl.kps, p1, tmax);
     else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(B.X, B.N, B.rec32, B.K, pl.kps, p1, tmax);
     pf->end(st);
-    const int mb = (int)((B.N + 255) / 256);
+    const int mb = (int)((B.N + 63) / 64);
     pf->begin(VBGS_PROF_MERGE, st);
-    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, B.N, B.lse, B.lse_part, tmax ? B.minlse : nullptr);
+    k_merge<<<mb, 64, 0, st>>>(p1, pl.p1_splits, B.N, B.lse, B.lse_part, tmax ? B.minlse : nullptr);
     pf->end(st);
     pf->begin(VBGS_PROF_MERGE, st);
     k_sum<<<1, 1024, 0, st>>>(B.lse_part, mb, B.scal + SC_SUM_LSE);
@@ -426,9 +430,9 @@ int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats
         dim3 g2(pl.p2_tiles, pl.p2_splits);
         pf->begin(VBGS_PROF_PASS2, st);
         if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec, B.K, B.part,
-                                                          tmax, B.minlse, 256, kChunkK);
+                                                          tmax, B.minlse, 256, kChunkK, pf->on ? pf->d_pairs : nullptr);
         else     k_pass2<float><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec32, B.K, B.part,
-                                                         tmax, B.minlse, 256, kChunkK);
+                                                         tmax, B.minlse, 256, kChunkK, pf->on ? pf->d_pairs : nullptr);
         pf->end(st);
         pf->begin(VBGS_PROF_REDUCE, st);
         k_reduce_splits<<<(B.K + 127) / 128, 128, 0, st>>>(B.part, pl.p2_splits, B.K,
@@ -574,8 +578,8 @@ extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N
     k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, lse_out, base + o_lsep, nullptr);
     k_sum<<<1, 1024, 0, st>>>(base + o_lsep, mb, scal + SC_SUM_LSE);
     dim3 g2(pl.p2_tiles, pl.p2_splits);
-    if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part, nullptr, nullptr, 1, 1);
-    else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part, nullptr, nullptr, 1, 1);
+    if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part, nullptr, nullptr, 1, 1, nullptr);
+    else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part, nullptr, nullptr, 1, 1, nullptr);
     k_reduce_splits<<<(K + 127) / 128, 128, 0, st>>>(part, pl.p2_splits, K, f64 ? nullptr : ctx->d_rec32,
                                                     ctx->d_kperm, dS_out);
     k_lse_subtract_psi<<<mb, 256, 0, st>>>(lse_out, N, ctx->d_scal);

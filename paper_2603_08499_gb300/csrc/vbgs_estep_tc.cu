@@ -615,13 +615,49 @@ __device__ __forceinline__ bool chunk_skipped(const float *tmax, const float *mi
     return b - l < -(float)kSkipNats;
 }
 
+
+// Work list of pass 2: for every component tile, the 64-point chunks the
+// pass-1 bound does not rule out, in increasing order (deterministic).
+// One block per tile; counts[j] and list[j * nchunks + i].
+__global__ void __launch_bounds__(256) k_p2_plan(const float *__restrict__ tmax, const float *__restrict__ minlse,
+                                                 int64_t N, int ntiles, int *__restrict__ counts,
+                                                 int *__restrict__ list)
+{
+    __shared__ int wsum[8];
+    __shared__ int base_sh;
+    const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int64_t nchunks = (N + kChunk2 - 1) / kChunk2;
+    if (t == 0) base_sh = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < nchunks; c0 += 256) {
+        const int64_t c = c0 + t;
+        const bool keep = c < nchunks && !chunk_skipped(tmax, minlse, N, ntiles, j, c * kChunk2);
+        const unsigned b = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wsum[w] = __popc(b);
+        __syncthreads();
+        int off = base_sh;
+        for (int i = 0; i < w; i++) off += wsum[i];
+        off += __popc(b & ((1u << lane) - 1u));
+        if (keep) list[(size_t)j * nchunks + off] = (int)c;
+        __syncthreads();
+        if (t == 0) {
+            int tot = 0;
+            for (int i = 0; i < 8; i++) tot += wsum[i];
+            base_sh += tot;
+        }
+        __syncthreads();
+    }
+    if (t == 0) counts[j] = base_sh;
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__restrict__ X, const double *__restrict__ lse,
                                                             int64_t N, int K, const unsigned char *__restrict__ tiles,
-                                                            const float *__restrict__ hdr, int ntiles, int64_t cps,
-                                                            const float *__restrict__ tmax,
-                                                            const float *__restrict__ minlse,
-                                                            double *__restrict__ part, int *__restrict__ flags)
+                                                            const float *__restrict__ hdr, int ntiles, int nsplit,
+                                                            const int *__restrict__ counts,
+                                                            const int *__restrict__ list,
+                                                            double *__restrict__ part, int *__restrict__ flags,
+                                                            unsigned long long *__restrict__ pairs)
 {
     using HT = typename H<BF16>::T;
     extern __shared__ unsigned char smem_raw[];
@@ -629,7 +665,22 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int j = blockIdx.x, split = blockIdx.y;
     const int64_t nchunks = (N + kChunk2 - 1) / kChunk2;
-    const int64_t cbeg = (int64_t)split * cps, cend = min(nchunks, cbeg + cps);
+    // this CTA's share of the tile's chunk list: entries [ibeg, iend)
+    const int cnt_j = counts ? counts[j] : (int)nchunks;
+    const int per = (cnt_j + nsplit - 1) / nsplit;
+    const int ibeg = min(cnt_j, split * per), iend = min(cnt_j, ibeg + per);
+    if (ibeg >= iend) {
+        // nothing to evaluate: zero moments, no TMEM, no barriers
+        const int k = j * kCols + (int)threadIdx.x;
+        if (threadIdx.x < 128 && k < K) {
+            double *dst = part + ((size_t)split * K + k) * 28;
+            for (int i = 0; i < 28; i++) dst[i] = 0.0;
+        }
+        return;
+    }
+    // list entry i -> chunk index
+    auto chunk_at = [&](int i) -> int64_t { return counts ? (int64_t)list[(size_t)j * nchunks + i] : (int64_t)i; };
+    const int64_t cbeg = ibeg, cend = iend;   // iterate over list positions
 
     if (tid == 0) {
         mbar_init(&S.bar_a, 1);
@@ -653,11 +704,8 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
     const float *h = hdr + (size_t)j * 32;
     const float scale = h[18];
 
-    // next processed chunk at or after c (cend if none)
-    auto next_chunk = [&](int64_t c) {
-        while (c < cend && chunk_skipped(tmax, minlse, N, ntiles, j, c * kChunk2)) c++;
-        return c;
-    };
+    // the list holds only chunks to evaluate: positions advance one by one
+    auto next_chunk = [&](int64_t c) { return c; };
 
     if (warp < 4) {
         // ---------------- builders + responsibilities ----------------
@@ -669,7 +717,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
         auto build = [&](int64_t c, int st) {
             // threads 0..63 write B1 (point-major), 64..127 write B2 (feature-major); both write lse2
             const int pt = tid & 63;
-            const int64_t n = c * kChunk2 + pt;
+            const int64_t n = chunk_at((int)c) * kChunk2 + pt;
             const int64_t nn = n < N ? n : N - 1;
             float d[6];
 #pragma unroll
@@ -859,6 +907,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
             mma_commit(&S.bar_final);
             mbar_wait(&S.bar_final, 0u, flags, true);
         }
+        if (pairs && n_proc > 0) atomicAdd(pairs, (unsigned long long)n_proc * kChunk2 * kCols);
     }
     fence_before();
     __syncthreads();
@@ -925,17 +974,32 @@ int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles,
 }
 
 
-int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
-                    const float *hdr, const float *tmax, const float *minlse, double *part, size_t part_cap_doubles,
-                    const int *kperm, double *dS, int *flags, int num_sms, cudaStream_t st, Prof *pf)
+size_t tc_plan_ints(int64_t N, int K)
 {
+    return (size_t)((K + kCols - 1) / kCols) * (size_t)(1 + (N + kChunk2 - 1) / kChunk2);
+}
+
+int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
+                    const float *hdr, const float *tmax, const float *minlse, int *plan, double *part,
+                    size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, cudaStream_t st,
+                    Prof *pf)
+{
+    unsigned long long *pairs = pf->on ? pf->d_pairs : nullptr;
     const int ntiles = (K + kCols - 1) / kCols;
     const int64_t nchunks = (N + kChunk2 - 1) / kChunk2;
-    int splits = std::max(1, std::min<int>((int)std::min<int64_t>(nchunks, 64), (4 * num_sms + ntiles - 1) / ntiles));
+    // with a work list most tiles hold a handful of chunks: two CTAs per tile
+    // share a long list; without one (no skipping) each CTA takes a range
+    int splits = tmax ? 2 : std::max(1, std::min<int>((int)std::min<int64_t>(nchunks, 64), (4 * num_sms + ntiles - 1) / ntiles));
     while (splits > 1 && (size_t)splits * (size_t)K * 28 > part_cap_doubles) splits--;
     if ((size_t)K * 28 > part_cap_doubles) return -2;
-    const int64_t cps = (nchunks + splits - 1) / splits;
-    splits = (int)((nchunks + cps - 1) / cps);
+    int *counts = nullptr, *list = nullptr;
+    if (tmax) {
+        counts = plan;
+        list = plan + ntiles;
+        pf->begin(VBGS_PROF_PASS2, st);
+        k_p2_plan<<<ntiles, 256, 0, st>>>(tmax, minlse, N, ntiles, counts, list);
+        pf->end(st);
+    }
     const size_t smem = sizeof(Smem2) + 128;
     static bool attr_set[2] = {false, false};
     if (!attr_set[bf16]) {
@@ -946,8 +1010,8 @@ int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool b
     }
     dim3 grid(ntiles, splits);
     pf->begin(VBGS_PROF_PASS2, st);
-    if (bf16) k_pass2_tc<true><<<grid, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, cps, tmax, minlse, part, flags);
-    else      k_pass2_tc<false><<<grid, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, cps, tmax, minlse, part, flags);
+    if (bf16) k_pass2_tc<true><<<grid, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, splits, counts, list, part, flags, pairs);
+    else      k_pass2_tc<false><<<grid, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, splits, counts, list, part, flags, pairs);
     pf->end(st);
     pf->begin(VBGS_PROF_REDUCE, st);
     k_reduce_splits_tile<<<(K + 127) / 128, 128, 0, st>>>(part, splits, K, hdr, kperm, dS);

@@ -53,6 +53,8 @@ struct Prof {
     std::vector<int> cat_of_pair;       // class of event pair i (events 2i, 2i+1)
     double ms[VBGS_PROF_COUNT] = {};
     int64_t n[VBGS_PROF_COUNT] = {};
+    unsigned long long *d_pairs = nullptr;   // device counter: pass-2 pairs evaluated (not skipped)
+    int64_t pass1_pairs = 0;                   // pairs scored by pass 1 (all of them)
     void begin(int cat, cudaStream_t st)
     {
         if (!on || used + 2 > pool.size()) return;
@@ -154,9 +156,11 @@ size_t tc_tile_bytes(int K);
 size_t tc_hdr_floats(int K);
 size_t tc_tmax_floats(int64_t N, int K);
 int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, cudaStream_t st, Prof *pf);
+size_t tc_plan_ints(int64_t N, int K);
 int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
-                    const float *hdr, const float *tmax, const float *minlse, double *part, size_t part_cap_doubles,
-                    const int *kperm, double *dS, int *flags, int num_sms, cudaStream_t st, Prof *pf);
+                    const float *hdr, const float *tmax, const float *minlse, int *plan, double *part,
+                    size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, cudaStream_t st,
+                    Prof *pf);
 int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
                     double2 *part, size_t part_cap_doubles, float *tmax, int *flags, int num_sms, int *splits_out,
                     cudaStream_t st, Prof *pf);
@@ -174,6 +178,8 @@ struct vbgs_ctx {
     double *d_Xs = nullptr;          // staged points in Morton order
     float *d_tmax = nullptr, *d_minlse = nullptr;
     unsigned char *d_tc_tiles = nullptr;   // tensor-core coefficient tiles
+    int *d_plan = nullptr;                 // pass-2 work list (counts + chunk lists per tile)
+    size_t plan_cap = 0;
     float *d_tc_hdr = nullptr;
     int num_sms = 152;
     size_t tmax_cap = 0;

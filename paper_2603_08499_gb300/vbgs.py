@@ -41,7 +41,7 @@ F = 28
 EXPORTS = [
     "vbgs_init", "vbgs_update", "vbgs_elbo", "vbgs_get_posterior", "vbgs_get_stats",
     "vbgs_set_stats", "vbgs_get_frame_stats", "vbgs_get_lse", "vbgs_last_launch_count",
-    "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_name", "vbgs_probe_peaks",
+    "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_pairs", "vbgs_profile_name", "vbgs_probe_peaks",
     "vbgs_estep_noalloc", "vbgs_last_error", "vbgs_destroy",
 ]
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
@@ -90,6 +90,7 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
     lib.vbgs_destroy.restype = None
     lib.vbgs_profile_enable.argtypes = [C.c_void_p, C.c_int]
     lib.vbgs_profile_read.argtypes = [C.c_void_p, _DP, C.POINTER(C.c_int64), C.c_int]
+    lib.vbgs_profile_pairs.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.vbgs_profile_name.argtypes = [C.c_int]
     lib.vbgs_profile_name.restype = C.c_char_p
     lib.vbgs_probe_peaks.argtypes = [C.c_int, _DP]
@@ -217,6 +218,12 @@ def vbgs_profile_read(ctx, reset: bool = False) -> dict:
     return {lib().vbgs_profile_name(i).decode(): (float(ms[i]), int(n[i])) for i in range(PROF_COUNT)}
 
 
+def vbgs_profile_pairs(ctx) -> tuple[int, int]:
+    a, b = C.c_int64(0), C.c_int64(0)
+    _check(lib().vbgs_profile_pairs(ctx, C.byref(a), C.byref(b)), ctx)
+    return int(a.value), int(b.value)
+
+
 def vbgs_probe_peaks(device: int = 0) -> dict:
     out = np.zeros(4)
     _check(lib().vbgs_probe_peaks(device, _dp(out)), None)
@@ -283,6 +290,9 @@ class Model:
 
     def profile_read(self, reset: bool = False) -> dict:
         return vbgs_profile_read(self.ctx, reset)
+
+    def profile_pairs(self) -> tuple[int, int]:
+        return vbgs_profile_pairs(self.ctx)
 
     def close(self) -> None:
         if self.ctx:
