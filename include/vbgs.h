@@ -113,6 +113,28 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
  * VBGS_ECUDA, VBGS_ENOMEM. */
 int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, double *elbo_trace);
 
+/* Many independent scenes at once (each its own context, uneven N and K):
+ * every scene runs the same frame update as vbgs_update(scenes[i],
+ * points[i], N[i], n_iters), all of them as the branches of one CUDA graph
+ * launched once, so small scenes fill the SMs that large ones leave idle.
+ * The graph is cached by (scenes, N, n_iters, tuning) and replayed for later
+ * frames of the same shapes.  Points are host or device arrays as in
+ * vbgs_update; elbo_traces is n_scenes x n_iters (host, may be NULL).  Work
+ * runs on internal streams after each scene's own stream has drained.
+ * Errors as vbgs_update; the message names the scene.  Not thread-safe. */
+int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const double *const *points,
+                        const int64_t *N, int n_iters, double *elbo_traces);
+
+/* Pick the work decomposition of the tensor-core passes (pass-1 K-splits
+ * and pass-2 CTAs per component tile) for this context's K and frames of N
+ * points, by timing 3 x 3 candidates on `points` (one E-step each; the model
+ * state is unchanged).  With cache_path, the choice is read from / appended
+ * to that text file keyed by form, rounded log2 N and K, and SM count.  The
+ * CUDA-core forms have nothing to tune (returns VBGS_OK).  vbgs_get_tuning
+ * reports the current choice (0 = automatic). */
+int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, const char *cache_path);
+int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_splits);
+
 /* ELBO of the points X under the current posterior q = prior0 (+) S_past
  * (the value elbo_trace[0] of a vbgs_update on X would take), without
  * changing the state.  lse_out (N doubles, host, may be NULL) receives the

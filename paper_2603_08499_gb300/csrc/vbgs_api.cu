@@ -14,6 +14,9 @@
 #include <string.h>
 #include <algorithm>
 #include <cstdarg>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 using namespace vbgs;
 
@@ -97,6 +100,7 @@ int dalloc(vbgs_ctx *ctx, T **p, size_t n)
 {
     if (*p) cudaFree(*p);
     *p = nullptr;
+    if (ctx) ctx->alloc_gen++;
     if (n == 0) n = 1;
     cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
     if (e != cudaSuccess) {
@@ -256,7 +260,7 @@ int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
         int splits = 1;
         int l = launch_pass1_tc(B.X, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
                                 reinterpret_cast<double2 *>(ctx->d_part), ctx->part_cap, B.tmax, ctx->d_flags,
-                                ctx->num_sms, &splits, ctx->stream, &ctx->prof);
+                                ctx->num_sms, ctx->tune_p1, &splits, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ctx->launches += l;
         l = launch_lse_merge(reinterpret_cast<double2 *>(ctx->d_part), splits, N, ctx->d_lse, ctx->d_lse_part,
@@ -266,7 +270,7 @@ int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
         if (want_stats) {
             l = launch_pass2_tc(B.X, ctx->d_lse, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
                                 B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
-                                ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->stream, &ctx->prof);
+                                ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->tune_p2, ctx->stream, &ctx->prof);
             if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
                                    cudaGetErrorString(cudaGetLastError()));
             ctx->launches += l;
@@ -293,6 +297,40 @@ int check_flags(vbgs_ctx *ctx)
     return VBGS_OK;
 }
 
+// vbgs_update in three parts: validation, capacity and staging (may
+// synchronise); the asynchronous frame itself (stream-capturable); results.
+int update_prepare(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (N < 0 || n_iters < 1) return fail(ctx, VBGS_EINVAL, "need N >= 0 and n_iters >= 1");
+    if (N > 0 && !points) return fail(ctx, VBGS_EINVAL, "points is NULL");
+    ctx->launches = 0;
+    int rc;
+    if ((rc = ensure_capacity(ctx, N)) || (rc = ensure_elbo(ctx, n_iters))) return rc;
+    return stage_points(ctx, points, N);
+}
+
+int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters)
+{
+    int rc;
+    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    if ((rc = order_frame(ctx, N, true))) return rc;
+    // Posterior entering the frame: the effective prior prior0 (+) S_past.
+    if ((rc = run_mstep(ctx, nullptr))) return rc;
+    for (int it = 0; it < n_iters; it++) {
+        if ((rc = run_estep(ctx, N, true))) return rc;
+        if (launch_elbo(ctx->d_scal, N, ctx->d_elbo + it, ctx->stream, &ctx->prof) < 0)
+            return fail(ctx, VBGS_ECUDA, "ELBO launch failed");
+        ctx->launches += 1;
+        if ((rc = run_mstep(ctx, ctx->d_dS))) return rc;
+    }
+    if (launch_commit(ctx->d_Spast, ctx->d_dS, ctx->K, ctx->d_flags, ctx->stream, &ctx->prof) < 0)
+        return fail(ctx, VBGS_ECUDA, "commit launch failed");
+    ctx->launches += 1;
+    ctx->last_N = N;
+    return VBGS_OK;
+}
+
 void free_all(vbgs_ctx *ctx)
 {
     void *ptrs[] = {ctx->d_m0, ctx->d_Spast, ctx->d_dS, ctx->d_zero, ctx->d_rec, ctx->d_rec32,
@@ -309,6 +347,265 @@ void free_all(vbgs_ctx *ctx)
 }
 
 } // namespace
+
+
+// ---------------------------------------------------------------------------
+// Batched scenes: one CUDA graph, one branch per scene.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> key;
+};
+
+struct BatchRuntime {
+    std::mutex mu;
+    cudaStream_t main = nullptr;
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> ev;
+    cudaEvent_t fork = nullptr;
+    std::vector<GraphEntry> cache;   // most recent first, a few entries
+    int device = -1;
+};
+BatchRuntime g_batch;
+
+int batch_streams(int n)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (g_batch.device != dev) {
+        g_batch.device = dev;
+        g_batch.pool.clear();
+        g_batch.ev.clear();
+        g_batch.cache.clear();
+        g_batch.main = nullptr;
+        g_batch.fork = nullptr;
+    }
+    if (!g_batch.main) {
+        if (cudaStreamCreateWithFlags(&g_batch.main, cudaStreamNonBlocking) != cudaSuccess) return -1;
+        if (cudaEventCreateWithFlags(&g_batch.fork, cudaEventDisableTiming) != cudaSuccess) return -1;
+    }
+    while ((int)g_batch.pool.size() < n) {
+        cudaStream_t st;
+        cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return -1;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return -1;
+        g_batch.pool.push_back(st);
+        g_batch.ev.push_back(e);
+    }
+    return 0;
+}
+
+} // namespace
+
+// Drop cached graphs that reference a context being destroyed.
+void batch_forget(const vbgs_ctx *ctx)
+{
+    std::lock_guard<std::mutex> lock(g_batch.mu);
+    for (size_t c = 0; c < g_batch.cache.size();) {
+        bool hit = false;
+        const auto &k = g_batch.cache[c].key;
+        for (size_t i = 1; i + 3 < k.size() + 1; i += 4)
+            if (k[i] == (int64_t)(uintptr_t)ctx) hit = true;
+        if (hit) {
+            cudaGraphExecDestroy(g_batch.cache[c].exec);
+            g_batch.cache.erase(g_batch.cache.begin() + c);
+        } else {
+            c++;
+        }
+    }
+}
+
+extern "C" int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const double *const *points,
+                                   const int64_t *N, int n_iters, double *elbo_traces)
+{
+    if (!scenes || n_scenes <= 0 || !points || !N || n_iters < 1)
+        return fail(nullptr, VBGS_EINVAL, "vbgs_update_batched: bad arguments");
+    for (int i = 0; i < n_scenes; i++)
+        if (!scenes[i]) return fail(nullptr, VBGS_EINVAL, "vbgs_update_batched: scene %d is NULL", i);
+    std::lock_guard<std::mutex> lock(g_batch.mu);
+    if (batch_streams(n_scenes) || tc_set_attributes())
+        return fail(nullptr, VBGS_ECUDA, "vbgs_update_batched: stream set-up failed");
+    vbgs_ctx *ctx = nullptr;   // for CU() error reporting
+    // Honour work already queued on each scene's own stream, then run every
+    // scene on a stream of the pool for the duration of the call.
+    std::vector<cudaStream_t> own(n_scenes);
+    std::vector<bool> prof_on(n_scenes);
+    for (int i = 0; i < n_scenes; i++) {
+        own[i] = scenes[i]->stream;
+        CU(cudaStreamSynchronize(own[i]));
+        scenes[i]->stream = g_batch.pool[i];
+        prof_on[i] = scenes[i]->prof.on;
+        scenes[i]->prof.on = false;   // no event records inside the graph
+    }
+    auto restore = [&]() {
+        for (int i = 0; i < n_scenes; i++) {
+            scenes[i]->stream = own[i];
+            scenes[i]->prof.on = prof_on[i];
+        }
+    };
+    int rc = VBGS_OK;
+    // 1. validate, size and stage every scene (outside the graph)
+    for (int i = 0; i < n_scenes && rc == VBGS_OK; i++) {
+        rc = update_prepare(scenes[i], points[i], N[i], n_iters);
+        if (rc) g_err = std::string("scene ") + std::to_string(i) + ": " + scenes[i]->err;
+    }
+    if (rc) { restore(); return rc; }
+    for (int i = 0; i < n_scenes; i++) {
+        cudaEventRecord(g_batch.ev[i], g_batch.pool[i]);
+        cudaStreamWaitEvent(g_batch.main, g_batch.ev[i], 0);
+    }
+    // 2. the frames of all scenes as one graph (cached by scene, size and iterations)
+    std::vector<int64_t> key;
+    key.push_back(n_iters);
+    for (int i = 0; i < n_scenes; i++) {
+        key.push_back((int64_t)(uintptr_t)scenes[i]);
+        key.push_back(N[i]);
+        key.push_back(scenes[i]->tune_p1 * 1000 + scenes[i]->tune_p2);
+        key.push_back(scenes[i]->alloc_gen);
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (size_t c = 0; c < g_batch.cache.size(); c++)
+        if (g_batch.cache[c].key == key) {
+            exec = g_batch.cache[c].exec;
+            if (c) std::swap(g_batch.cache[c], g_batch.cache[0]);
+            break;
+        }
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(g_batch.main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            restore();
+            return fail(nullptr, VBGS_ECUDA, "vbgs_update_batched: capture failed to start");
+        }
+        cudaEventRecord(g_batch.fork, g_batch.main);
+        for (int i = 0; i < n_scenes && rc == VBGS_OK; i++) {
+            cudaStreamWaitEvent(g_batch.pool[i], g_batch.fork, 0);
+            rc = update_enqueue(scenes[i], N[i], n_iters);
+            cudaEventRecord(g_batch.ev[i], g_batch.pool[i]);
+            cudaStreamWaitEvent(g_batch.main, g_batch.ev[i], 0);
+        }
+        cudaError_t ce = cudaStreamEndCapture(g_batch.main, &graph);
+        if (rc || ce != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            restore();
+            return rc ? rc : fail(nullptr, VBGS_ECUDA, "vbgs_update_batched: capture failed: %s", cudaGetErrorString(ce));
+        }
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            restore();
+            return fail(nullptr, VBGS_ECUDA, "vbgs_update_batched: instantiate failed: %s", cudaGetErrorString(ce));
+        }
+        GraphEntry e;
+        e.exec = exec;
+        e.key = key;
+        g_batch.cache.insert(g_batch.cache.begin(), e);
+        while (g_batch.cache.size() > 4) {
+            cudaGraphExecDestroy(g_batch.cache.back().exec);
+            g_batch.cache.pop_back();
+        }
+    }
+    if (cudaGraphLaunch(exec, g_batch.main) != cudaSuccess) {
+        restore();
+        return fail(nullptr, VBGS_ECUDA, "vbgs_update_batched: graph launch failed");
+    }
+    // 3. results: ELBO traces and flags of every scene, one synchronisation
+    std::vector<int> fl((size_t)n_scenes * FL_COUNT);
+    for (int i = 0; i < n_scenes; i++) {
+        if (elbo_traces)
+            CU(cudaMemcpyAsync(elbo_traces + (size_t)i * n_iters, scenes[i]->d_elbo, sizeof(double) * n_iters,
+                               cudaMemcpyDeviceToHost, g_batch.main));
+        CU(cudaMemcpyAsync(&fl[(size_t)i * FL_COUNT], scenes[i]->d_flags, sizeof(int) * FL_COUNT,
+                           cudaMemcpyDeviceToHost, g_batch.main));
+    }
+    CU(cudaStreamSynchronize(g_batch.main));
+    restore();
+    for (int i = 0; i < n_scenes; i++) {
+        const int *f = &fl[(size_t)i * FL_COUNT];
+        if (f[FL_NONPD])
+            return fail(scenes[i], VBGS_ENUMERIC, "scene %d: posterior W^-1 of component %d is not positive definite", i,
+                        f[FL_NONPD] - 1);
+        if (f[FL_TIMEOUT]) return fail(scenes[i], VBGS_ETIMEOUT, "scene %d: a bounded device wait gave up", i);
+    }
+    return VBGS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the tensor-core work decomposition.
+// ---------------------------------------------------------------------------
+extern "C" int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, const char *cache_path)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (N <= 0 || !points) return fail(ctx, VBGS_EINVAL, "vbgs_autotune needs points");
+    if (!is_tc(ctx)) return VBGS_OK;   // the CUDA-core forms have nothing to tune
+    // size class: rounded log2 of N and K
+    const int nb = (int)std::lround(std::log2((double)N)), kb = (int)std::lround(std::log2((double)ctx->K));
+    char key[96];
+    snprintf(key, sizeof key, "form%d_N2^%d_K2^%d_sms%d", ctx->precision, nb, kb, ctx->num_sms);
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "r")) {
+            char k2[96];
+            int a, b;
+            while (fscanf(f, "%95s %d %d", k2, &a, &b) == 3)
+                if (!strcmp(k2, key)) {
+                    ctx->tune_p1 = a;
+                    ctx->tune_p2 = b;
+                    fclose(f);
+                    return VBGS_OK;
+                }
+            fclose(f);
+        }
+    }
+    int rc;
+    if ((rc = update_prepare(ctx, points, N, 1))) return rc;
+    if ((rc = order_frame(ctx, N, true)) || (rc = run_mstep(ctx, nullptr))) return rc;
+    const int a0 = tc_pass1_auto_splits(N, ctx->K, ctx->num_sms);
+    const int p1c[3] = {a0, std::max(1, a0 / 2), a0 * 2};
+    const int p2c[3] = {1, 2, 4};
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    const bool pon = ctx->prof.on;
+    ctx->prof.on = false;
+    float best = 1e30f;
+    int b1 = 0, b2 = 0;
+    for (int i = 0; i < 3; i++)
+        for (int jx = 0; jx < 3; jx++) {
+            ctx->tune_p1 = p1c[i];
+            ctx->tune_p2 = p2c[jx];
+            if ((rc = run_estep(ctx, N, true))) break;   // warm-up
+            cudaEventRecord(e0, ctx->stream);
+            if ((rc = run_estep(ctx, N, true))) break;
+            cudaEventRecord(e1, ctx->stream);
+            CU(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; b1 = p1c[i]; b2 = p2c[jx]; }
+        }
+    ctx->prof.on = pon;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    ctx->tune_p1 = b1;
+    ctx->tune_p2 = b2;
+    if ((rc = check_flags(ctx))) return rc;
+    if (cache_path)
+        if (FILE *f = fopen(cache_path, "a")) {
+            fprintf(f, "%s %d %d\n", key, b1, b2);
+            fclose(f);
+        }
+    return VBGS_OK;
+}
+
+int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_splits)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (pass1_splits) *pass1_splits = ctx->tune_p1;
+    if (pass2_splits) *pass2_splits = ctx->tune_p2;
+    return VBGS_OK;
+}
 
 extern "C" {
 
@@ -426,28 +723,9 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
 
 int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, double *elbo_trace)
 {
-    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
-    if (N < 0 || n_iters < 1) return fail(ctx, VBGS_EINVAL, "need N >= 0 and n_iters >= 1");
-    if (N > 0 && !points) return fail(ctx, VBGS_EINVAL, "points is NULL");
-    ctx->launches = 0;
     int rc;
-    if ((rc = ensure_capacity(ctx, N)) || (rc = ensure_elbo(ctx, n_iters))) return rc;
-    if ((rc = stage_points(ctx, points, N))) return rc;
-    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
-    if ((rc = order_frame(ctx, N, true))) return rc;
-    // Posterior entering the frame: the effective prior prior0 (+) S_past.
-    if ((rc = run_mstep(ctx, nullptr))) return rc;
-    for (int it = 0; it < n_iters; it++) {
-        if ((rc = run_estep(ctx, N, true))) return rc;
-        if (launch_elbo(ctx->d_scal, N, ctx->d_elbo + it, ctx->stream, &ctx->prof) < 0)
-            return fail(ctx, VBGS_ECUDA, "ELBO launch failed");
-        ctx->launches += 1;
-        if ((rc = run_mstep(ctx, ctx->d_dS))) return rc;
-    }
-    if (launch_commit(ctx->d_Spast, ctx->d_dS, ctx->K, ctx->d_flags, ctx->stream, &ctx->prof) < 0)
-        return fail(ctx, VBGS_ECUDA, "commit launch failed");
-    ctx->launches += 1;
-    ctx->last_N = N;
+    if ((rc = update_prepare(ctx, points, N, n_iters))) return rc;
+    if ((rc = update_enqueue(ctx, N, n_iters))) return rc;
     if (elbo_trace)
         CU(cudaMemcpyAsync(elbo_trace, ctx->d_elbo, sizeof(double) * n_iters, cudaMemcpyDeviceToHost,
                            ctx->stream));
@@ -621,6 +899,7 @@ const char *vbgs_last_error(const vbgs_ctx *ctx)
 void vbgs_destroy(vbgs_ctx *ctx)
 {
     if (!ctx) return;
+    batch_forget(ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     free_all(ctx);

@@ -981,8 +981,8 @@ size_t tc_plan_ints(int64_t N, int K)
 
 int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const float *tmax, const float *minlse, int *plan, double *part,
-                    size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, cudaStream_t st,
-                    Prof *pf)
+                    size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
+                    cudaStream_t st, Prof *pf)
 {
     unsigned long long *pairs = pf->on ? pf->d_pairs : nullptr;
     const int ntiles = (K + kCols - 1) / kCols;
@@ -990,6 +990,7 @@ int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool b
     // with a work list most tiles hold a handful of chunks: two CTAs per tile
     // share a long list; without one (no skipping) each CTA takes a range
     int splits = tmax ? 2 : std::max(1, std::min<int>((int)std::min<int64_t>(nchunks, 64), (4 * num_sms + ntiles - 1) / ntiles));
+    if (splits_override > 0) splits = std::min<int>(splits_override, (int)std::max<int64_t>(1, nchunks));
     while (splits > 1 && (size_t)splits * (size_t)K * 28 > part_cap_doubles) splits--;
     if ((size_t)K * 28 > part_cap_doubles) return -2;
     int *counts = nullptr, *list = nullptr;
@@ -1001,13 +1002,7 @@ int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool b
         pf->end(st);
     }
     const size_t smem = sizeof(Smem2) + 128;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[bf16]) {
-        cudaError_t e = bf16 ? cudaFuncSetAttribute(k_pass2_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                             : cudaFuncSetAttribute(k_pass2_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return -1;
-        attr_set[bf16] = true;
-    }
+    if (tc_set_attributes()) return -1;
     dim3 grid(ntiles, splits);
     pf->begin(VBGS_PROF_PASS2, st);
     if (bf16) k_pass2_tc<true><<<grid, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, splits, counts, list, part, flags, pairs);
@@ -1019,40 +1014,56 @@ int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool b
     return cudaGetLastError() == cudaSuccess ? 2 : -1;
 }
 
-int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
-                    double2 *part, size_t part_cap_doubles, float *tmax, int *flags, int num_sms, int *splits_out,
-                    cudaStream_t st, Prof *pf)
+// K-splits of pass 1: many small CTAs (two resident per SM) that the hardware
+// scheduler balances, with the number of waves close to an integer so the
+// last wave is not nearly empty; a mild penalty per split for pipeline fill.
+int tc_pass1_auto_splits(int64_t N, int K, int num_sms)
 {
     const int ntiles = (K + kCols - 1) / kCols;
     const int ptiles = (int)((N + kRows - 1) / kRows);
-    // K-splits: many small CTAs (two resident per SM) that the hardware
-    // scheduler balances, with the number of waves close to an integer so the
-    // last wave is not nearly empty; a mild penalty per split for pipeline fill.
     int splits = 1;
-    {
-        const double slots = 2.0 * num_sms;
-        double best = -1.0;
-        const int smax = std::max(1, std::min(64, ntiles / 4));
-        for (int sp = 1; sp <= smax; sp++) {
-            const int tp = (ntiles + sp - 1) / sp;
-            const int sreal = (ntiles + tp - 1) / tp;
-            const double waves = ptiles * (double)sreal / slots;
-            const double eff = waves / std::ceil(waves) - 0.004 * sreal;
-            if (eff > best + 1e-9) { best = eff; splits = sreal; }
-        }
+    const double slots = 2.0 * num_sms;
+    double best = -1.0;
+    const int smax = std::max(1, std::min(64, ntiles / 4));
+    for (int sp = 1; sp <= smax; sp++) {
+        const int tp = (ntiles + sp - 1) / sp;
+        const int sreal = (ntiles + tp - 1) / tp;
+        const double waves = ptiles * (double)sreal / slots;
+        const double eff = waves / std::ceil(waves) - 0.004 * sreal;
+        if (eff > best + 1e-9) { best = eff; splits = sreal; }
     }
+    return splits;
+}
+
+// Shared-memory attributes of the tensor-core kernels (set once, before any
+// stream capture).
+bool g_tc_attr = false;
+int tc_set_attributes()
+{
+    if (g_tc_attr) return 0;
+    const int s1 = (int)(sizeof(Smem) + 1024), s2 = (int)(sizeof(Smem2) + 128);
+    if (cudaFuncSetAttribute(k_pass1_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1) != cudaSuccess ||
+        cudaFuncSetAttribute(k_pass1_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1) != cudaSuccess ||
+        cudaFuncSetAttribute(k_pass2_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2) != cudaSuccess ||
+        cudaFuncSetAttribute(k_pass2_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2) != cudaSuccess)
+        return -1;
+    g_tc_attr = true;
+    return 0;
+}
+
+int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
+                    double2 *part, size_t part_cap_doubles, float *tmax, int *flags, int num_sms, int splits_override,
+                    int *splits_out, cudaStream_t st, Prof *pf)
+{
+    const int ntiles = (K + kCols - 1) / kCols;
+    const int ptiles = (int)((N + kRows - 1) / kRows);
+    int splits = splits_override > 0 ? std::min(splits_override, ntiles) : tc_pass1_auto_splits(N, K, num_sms);
     while (splits > 1 && (size_t)splits * (size_t)N * 2 > part_cap_doubles) splits--;
     const int tps = (ntiles + splits - 1) / splits;
     splits = (ntiles + tps - 1) / tps;
     *splits_out = splits;
     const size_t smem = sizeof(Smem) + 1024;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[bf16]) {
-        cudaError_t e = bf16 ? cudaFuncSetAttribute(k_pass1_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                             : cudaFuncSetAttribute(k_pass1_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return -1;
-        attr_set[bf16] = true;
-    }
+    if (tc_set_attributes()) return -1;
     dim3 grid(ptiles, splits);
     pf->begin(VBGS_PROF_PASS1, st);
     if (bf16) k_pass1_tc<true><<<grid, kThreadsTC, smem, st>>>(X, N, K, tiles, hdr, ntiles, tps, part, tmax, flags);

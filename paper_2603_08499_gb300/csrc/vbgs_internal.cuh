@@ -159,11 +159,13 @@ int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles,
 size_t tc_plan_ints(int64_t N, int K);
 int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const float *tmax, const float *minlse, int *plan, double *part,
-                    size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, cudaStream_t st,
-                    Prof *pf);
-int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
-                    double2 *part, size_t part_cap_doubles, float *tmax, int *flags, int num_sms, int *splits_out,
+                    size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
                     cudaStream_t st, Prof *pf);
+int tc_pass1_auto_splits(int64_t N, int K, int num_sms);
+int tc_set_attributes();
+int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
+                    double2 *part, size_t part_cap_doubles, float *tmax, int *flags, int num_sms, int splits_override,
+                    int *splits_out, cudaStream_t st, Prof *pf);
 
 } // namespace vbgs
 
@@ -182,6 +184,8 @@ struct vbgs_ctx {
     size_t plan_cap = 0;
     float *d_tc_hdr = nullptr;
     int num_sms = 152;
+    int tune_p1 = 0, tune_p2 = 0;          // work decomposition of the tensor-core passes (0 = automatic)
+    int64_t alloc_gen = 0;                 // bumped by every (re)allocation: cached graphs check it
     size_t tmax_cap = 0;
     bool last_sorted = false;
     vbgs::MstepParams mp{};

@@ -42,7 +42,8 @@ EXPORTS = [
     "vbgs_init", "vbgs_update", "vbgs_elbo", "vbgs_get_posterior", "vbgs_get_stats",
     "vbgs_set_stats", "vbgs_get_frame_stats", "vbgs_get_lse", "vbgs_last_launch_count",
     "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_pairs", "vbgs_profile_name", "vbgs_probe_peaks",
-    "vbgs_estep_noalloc", "vbgs_last_error", "vbgs_destroy",
+    "vbgs_estep_noalloc", "vbgs_update_batched", "vbgs_autotune", "vbgs_get_tuning",
+    "vbgs_last_error", "vbgs_destroy",
 ]
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 PROF_COUNT = 6
@@ -95,6 +96,10 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
     lib.vbgs_profile_name.restype = C.c_char_p
     lib.vbgs_probe_peaks.argtypes = [C.c_int, _DP]
     lib.vbgs_estep_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    lib.vbgs_update_batched.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_int64), C.c_int, _DP]
+    lib.vbgs_autotune.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_char_p]
+    lib.vbgs_get_tuning.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     return lib
 
 
@@ -239,6 +244,37 @@ def vbgs_estep_noalloc(ctx, points, lse_out, dS_out) -> None:
     _check(lib().vbgs_estep_noalloc(ctx, ptr, N, C.c_void_p(lse_out.data_ptr() if N else None),
                                     C.c_void_p(dS_out.data_ptr())), ctx)
     del keep
+
+
+def vbgs_update_batched(ctxs, points_list, n_iters: int) -> np.ndarray:
+    """All scenes' frame updates in one graph launch; returns n_scenes x n_iters ELBO traces."""
+    n = len(ctxs)
+    keep, ptrs, Ns = [], [], []
+    for pts in points_list:
+        ptr, N, k = _points_ptr(pts)
+        keep.append(k)
+        ptrs.append(ptr.value)
+        Ns.append(N)
+    arr_ctx = (C.c_void_p * n)(*[c.value for c in ctxs])
+    arr_pts = (C.c_void_p * n)(*ptrs)
+    arr_N = (C.c_int64 * n)(*Ns)
+    traces = np.zeros((n, n_iters))
+    _check(lib().vbgs_update_batched(arr_ctx, n, arr_pts, arr_N, n_iters, _dp(traces)), None)
+    del keep
+    return traces
+
+
+def vbgs_autotune(ctx, points, cache_path: str | None = None) -> tuple[int, int]:
+    ptr, N, keep = _points_ptr(points)
+    _check(lib().vbgs_autotune(ctx, ptr, N, cache_path.encode() if cache_path else None), ctx)
+    del keep
+    return vbgs_get_tuning(ctx)
+
+
+def vbgs_get_tuning(ctx) -> tuple[int, int]:
+    a, b = C.c_int(0), C.c_int(0)
+    _check(lib().vbgs_get_tuning(ctx, C.byref(a), C.byref(b)), ctx)
+    return int(a.value), int(b.value)
 
 
 def vbgs_last_error(ctx=None) -> str:
