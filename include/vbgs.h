@@ -75,6 +75,7 @@ typedef enum {
  * beyond rounding.  The plain form sets both flags. */
 #define VBGS_FLAG_NO_REORDER 1   /* process in the caller's order */
 #define VBGS_FLAG_NO_SKIP    2   /* evaluate every tile in pass 2 */
+#define VBGS_FLAG_PROPOSAL   4   /* learned candidate proposal (see vbgs_proposal_report) */
 
 typedef struct {
     int precision;        /* vbgs_precision */
@@ -134,6 +135,37 @@ int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const double *con
  * reports the current choice (0 = automatic). */
 int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, const char *cache_path);
 int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_splits);
+
+/* Learned proposal (VBGS_FLAG_PROPOSAL at vbgs_init).  A small MLP over the
+ * point (x, y, z, r, g, b), 6 -> 128 -> 128 -> 1024 with ReLU, BF16-rounded
+ * weights and FP32 accumulation, proposes the 4 most likely of 1024
+ * component clusters (k-means of the posterior means, 2 Lloyd iterations
+ * after every posterior update); the E-step scores only their components.
+ * A certified bound of the responsibility mass outside them sends points
+ * above 1e-3 to the exact E-step, as does a seeded 1% audit sample, which
+ * measures the true missed mass; a frame with more than 20% such points runs
+ * exact.  The network is trained on the GPU (forward, backward, Adam lr 1e-3,
+ * minibatches of 4096, one epoch per frame) on the cluster masses of the exact
+ * E-steps of each frame.
+ * vbgs_proposal_report fills out[11]: candidate pairs scored, fallback
+ * points, audit points, audit max and mean missed mass, frame ran exact
+ * (0/1), mean training loss of the last epoch, frames trained, pairs of the
+ * exact E-step, points, clusters added by the certificate (all of the last
+ * iteration of the last frame).
+ * vbgs_proposal_weights reads (get, 149,504 floats) and/or replaces (set)
+ * the FP32 master weights [W1 128x6 | b1 | W2 128x128 | b2 | W3 1024x128 |
+ * b3] (setting resets Adam).  vbgs_proposal_grad runs the network on B <=
+ * 4096 inputs (B x 6, already mapped to [-1, 1]) and returns the top-4
+ * clusters, and with labels (B x 1024) the mean soft cross-entropy and its
+ * gradient (host arrays; no update).  vbgs_proposal_clusters refreshes the
+ * clusters and returns the centroids (1024 x 6) and each component's
+ * cluster (K).  The proposal is host-driven (one synchronisation per
+ * iteration) and is not available in vbgs_update_batched. */
+int vbgs_proposal_report(vbgs_ctx *ctx, double *out);
+int vbgs_proposal_weights(vbgs_ctx *ctx, float *get, const float *set);
+int vbgs_proposal_grad(vbgs_ctx *ctx, const float *inputs, const float *labels, int B, float *loss, float *grad,
+                       int *top);
+int vbgs_proposal_clusters(vbgs_ctx *ctx, float *centroids, int *cluster_of);
 
 /* ELBO of the points X under the current posterior q = prior0 (+) S_past
  * (the value elbo_trace[0] of a vbgs_update on X would take), without

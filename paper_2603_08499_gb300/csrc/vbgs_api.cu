@@ -128,7 +128,7 @@ int ensure_capacity(vbgs_ctx *ctx, int64_t N)
         if ((rc = dalloc(ctx, &ctx->d_minlse, (size_t)(cap + 31) / 32 + 1))) return rc;
         ctx->ncap = cap;
     }
-    const int64_t scap = std::max<int64_t>(ctx->ncap, ctx->K);
+    const int64_t scap = std::max<int64_t>(ctx->prop.on ? ctx->ncap * VBGS_PROP_MAXCAND : ctx->ncap, ctx->K);
     if (scap > ctx->sb.cap) {
         if ((rc = dalloc(ctx, &ctx->sb.keys_in, (size_t)scap)) || (rc = dalloc(ctx, &ctx->sb.keys_out, (size_t)scap)) ||
             (rc = dalloc(ctx, &ctx->sb.idx_in, (size_t)scap)))
@@ -232,7 +232,8 @@ int order_frame(vbgs_ctx *ctx, int64_t N, bool points)
     return VBGS_OK;
 }
 
-int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
+// Full E-step over N staged points X (N x 8) into lse (N) and ctx->d_dS.
+int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool want_stats)
 {
     if (ctx->prof.on) ctx->prof.pass1_pairs += N * (int64_t)ctx->K;
     if (N == 0) {
@@ -241,12 +242,12 @@ int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
         return VBGS_OK;
     }
     EstepBuffers B;
-    B.X = ctx->last_sorted ? ctx->d_Xs : ctx->d_X;
+    B.X = X;
     B.N = N;
     B.K = ctx->K;
     B.rec = ctx->d_rec;
     B.rec32 = ctx->d_rec32;
-    B.lse = ctx->d_lse;
+    B.lse = lse;
     B.lse_part = ctx->d_lse_part;
     B.scal = ctx->d_scal;
     B.part = ctx->d_part;
@@ -263,12 +264,12 @@ int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
                                 ctx->num_sms, ctx->tune_p1, &splits, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ctx->launches += l;
-        l = launch_lse_merge(reinterpret_cast<double2 *>(ctx->d_part), splits, N, ctx->d_lse, ctx->d_lse_part,
+        l = launch_lse_merge(reinterpret_cast<double2 *>(ctx->d_part), splits, N, lse, ctx->d_lse_part,
                              B.tmax ? ctx->d_minlse : nullptr, ctx->d_scal + SC_SUM_LSE, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "lse merge launch failed");
         ctx->launches += l;
         if (want_stats) {
-            l = launch_pass2_tc(B.X, ctx->d_lse, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
+            l = launch_pass2_tc(B.X, lse, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
                                 B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
                                 ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->tune_p2, ctx->stream, &ctx->prof);
             if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
@@ -282,6 +283,291 @@ int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats)
                            cudaGetErrorString(cudaGetLastError()));
     ctx->launches += l;
     return VBGS_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Learned proposal (host side).  Constants of the method: G = 1024 clusters,
+// top-4 proposals, missed-mass threshold 1e-3, 1% audit, a frame with more
+// than 20% fallback points runs exact, 2 Lloyd iterations per refresh, Adam
+// lr 1e-3, minibatches of 4096, one epoch over each frame's labelled points.
+// ---------------------------------------------------------------------------
+constexpr int kPG = VBGS_PROP_CLUSTERS, kPTop = VBGS_PROP_TOP, kMB = 4096, kHid = 128;
+constexpr float kPropThresh = 1e-3f;
+constexpr uint32_t kAuditPerMille = 10;
+constexpr double kExactFrameFrac = 0.2;
+constexpr float kPropLr = 1e-3f;
+constexpr int kPropEpochs = 2;
+constexpr int64_t kPropTrainPoints = 16384;
+constexpr size_t kOffB1 = 128 * 6, kOffW2 = kOffB1 + 128, kOffB2 = kOffW2 + 128 * 128, kOffW3 = kOffB2 + 128,
+                 kOffB3 = kOffW3 + 1024 * 128, kNParam = kOffB3 + 1024;
+
+uint64_t splitmix(uint64_t &s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+float bf16_round(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x;
+    u += 0x7fffu + ((u >> 16) & 1u);
+    u &= 0xffff0000u;
+    float y;
+    memcpy(&y, &u, 4);
+    return y;
+}
+
+int prop_set_weights(vbgs_ctx *ctx, const float *w)
+{
+    std::vector<float> q(kNParam);
+    for (size_t i = 0; i < kNParam; i++) q[i] = bf16_round(w[i]);
+    CU(cudaMemcpyAsync(ctx->prop.w, w, sizeof(float) * kNParam, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->prop.wq, q.data(), sizeof(float) * kNParam, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->prop.am, 0, sizeof(float) * kNParam, ctx->stream));
+    CU(cudaMemsetAsync(ctx->prop.av, 0, sizeof(float) * kNParam, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->prop.step = 0;
+    return VBGS_OK;
+}
+
+int prop_alloc(vbgs_ctx *ctx)
+{
+    PropState &P = ctx->prop;
+    const int K = ctx->K;
+    int rc;
+    if ((rc = dalloc(ctx, &P.cent, (size_t)kPG * 6)) || (rc = dalloc(ctx, &P.kpts, (size_t)K * 6)) ||
+        (rc = dalloc(ctx, &P.cstat, (size_t)kPG * 20)) || (rc = dalloc(ctx, &P.order, (size_t)K)) ||
+        (rc = dalloc(ctx, &P.cstart, (size_t)kPG + 1)) || (rc = dalloc(ctx, &P.skey, (size_t)K)) ||
+        (rc = dalloc(ctx, &P.w, kNParam)) || (rc = dalloc(ctx, &P.wq, kNParam)) || (rc = dalloc(ctx, &P.am, kNParam)) ||
+        (rc = dalloc(ctx, &P.av, kNParam)) || (rc = dalloc(ctx, &P.grad, kNParam)) ||
+        (rc = dalloc(ctx, &P.h1, (size_t)kMB * kHid)) || (rc = dalloc(ctx, &P.h2, (size_t)kMB * kHid)) ||
+        (rc = dalloc(ctx, &P.dh1, (size_t)kMB * kHid)) || (rc = dalloc(ctx, &P.dh2, (size_t)kMB * kHid)) ||
+        (rc = dalloc(ctx, &P.z, (size_t)kMB * kPG)) || (rc = dalloc(ctx, &P.dz, (size_t)kMB * kPG)) ||
+        (rc = dalloc(ctx, &P.loss, 2)) || (rc = dalloc(ctx, &P.counters, 4)) ||
+        (rc = dalloc(ctx, &P.pstart, (size_t)kPG + 1)))
+        return rc;
+    P.nparam = kNParam;
+    // He-uniform initial weights from a fixed seed, zero biases
+    std::vector<float> w(kNParam, 0.f);
+    uint64_t seed = 0x5eedF00Dull;
+    auto fill = [&](size_t off, int fan_out, int fan_in) {
+        const double a = std::sqrt(6.0 / fan_in);
+        for (size_t i = 0; i < (size_t)fan_out * fan_in; i++)
+            w[off + i] = (float)(a * (2.0 * ((splitmix(seed) >> 11) * (1.0 / 9007199254740992.0)) - 1.0));
+    };
+    fill(0, 128, 6);
+    fill(kOffW2, 128, 128);
+    fill(kOffW3, 1024, 128);
+    P.on = true;
+    return prop_set_weights(ctx, w.data());
+}
+
+int prop_ensure_frame(vbgs_ctx *ctx, int64_t N)
+{
+    PropState &P = ctx->prop;
+    int rc;
+    if (N > P.ncap) {
+        const int64_t cap = std::max<int64_t>(N, 1024);
+        if ((rc = dalloc(ctx, &P.top, (size_t)cap * kPTop)) || (rc = dalloc(ctx, &P.exact, (size_t)cap)) ||
+            (rc = dalloc(ctx, &P.erows, (size_t)cap)) || (rc = dalloc(ctx, &P.plist, (size_t)cap * VBGS_PROP_MAXCAND)) ||
+            (rc = dalloc(ctx, &P.cand, (size_t)cap * VBGS_PROP_MAXCAND)) ||
+            (rc = dalloc(ctx, &P.pkey, (size_t)cap * VBGS_PROP_MAXCAND)) || (rc = dalloc(ctx, &P.ekey, (size_t)cap)) ||
+            (rc = dalloc(ctx, &P.lse_c, (size_t)cap)) || (rc = dalloc(ctx, &P.Xe, (size_t)cap * VBGS_XS)) ||
+            (rc = dalloc(ctx, &P.lse_e, (size_t)cap)) || (rc = dalloc(ctx, &P.lsum, (size_t)cap / 256 + 2)) ||
+            (rc = dalloc(ctx, &P.bound, (size_t)cap)) || (rc = dalloc(ctx, &P.audit, (size_t)cap)) ||
+            (rc = dalloc(ctx, &P.Xin, (size_t)std::max<int64_t>(cap, kPropTrainPoints) * 6)) ||
+            (rc = dalloc(ctx, &P.Q, (size_t)kPropTrainPoints * kPG)))
+            return rc;
+        P.ncap = cap;
+        P.lab_cap = cap;
+    }
+    return VBGS_OK;
+}
+
+// k-means of the posterior means (warm start) and the certificate terms.
+int prop_refresh(vbgs_ctx *ctx)
+{
+    PropState &P = ctx->prop;
+    // colour weighted like space in the clustering: scaled by the largest
+    // extent of the position box
+    const float csc = (float)(1.0 / std::min(ctx->box.inv_ext[0], std::min(ctx->box.inv_ext[1], ctx->box.inv_ext[2])));
+    if (!P.centroids_ready) {
+        prop_init_centroids(ctx->d_rec32, ctx->K, csc, P.cent, ctx->stream);
+        P.centroids_ready = true;
+    }
+    if (prop_launch_kmeans(ctx->d_rec32, ctx->K, csc, P.kpts, P.cent, ctx->sb, P.order, P.skey, P.cstart, 2, ctx->stream) ||
+        prop_launch_cluster_stats(ctx->d_rec32, P.order, P.cstart, P.cstat, ctx->stream))
+        return fail(ctx, VBGS_ECUDA, "proposal cluster refresh failed");
+    ctx->launches += 9;
+    return VBGS_OK;
+}
+
+void mlp_forward(vbgs_ctx *ctx, const float *Xin, int B)
+{
+    PropState &P = ctx->prop;
+    const float *q = P.wq;
+    prop_gemm(B, kHid, 6, Xin, 6, 1, q, 1, 6, P.h1, kHid, q + kOffB1, true, false, ctx->stream);
+    prop_gemm(B, kHid, kHid, P.h1, kHid, 1, q + kOffW2, 1, kHid, P.h2, kHid, q + kOffB2, true, false, ctx->stream);
+    prop_gemm(B, kPG, kHid, P.h2, kHid, 1, q + kOffW3, 1, kHid, P.z, kPG, q + kOffB3, false, false, ctx->stream);
+}
+
+// dz (= dLoss/dlogits) -> parameter gradients of the minibatch
+void mlp_backward(vbgs_ctx *ctx, const float *Xin, int B)
+{
+    PropState &P = ctx->prop;
+    const float *q = P.wq;
+    float *g = P.grad;
+    prop_gemm(kPG, kHid, B, P.dz, 1, kPG, P.h2, kHid, 1, g + kOffW3, kHid, nullptr, false, false, ctx->stream);
+    prop_colsum(P.dz, B, kPG, g + kOffB3, ctx->stream);
+    prop_gemm(B, kHid, kPG, P.dz, kPG, 1, q + kOffW3, kHid, 1, P.dh2, kHid, nullptr, false, false, ctx->stream);
+    prop_relu_bwd(P.dh2, P.h2, (size_t)B * kHid, ctx->stream);
+    prop_gemm(kHid, kHid, B, P.dh2, 1, kHid, P.h1, kHid, 1, g + kOffW2, kHid, nullptr, false, false, ctx->stream);
+    prop_colsum(P.dh2, B, kHid, g + kOffB2, ctx->stream);
+    prop_gemm(B, kHid, kHid, P.dh2, kHid, 1, q + kOffW2, kHid, 1, P.dh1, kHid, nullptr, false, false, ctx->stream);
+    prop_relu_bwd(P.dh1, P.h1, (size_t)B * kHid, ctx->stream);
+    prop_gemm(kHid, 6, B, P.dh1, 1, kHid, Xin, 6, 1, g, 6, nullptr, false, false, ctx->stream);
+    prop_colsum(P.dh1, B, kHid, g + kOffB1, ctx->stream);
+}
+
+// Proposal of the frame: top-4 clusters of every (sorted) point.
+int prop_propose(vbgs_ctx *ctx, const double *X, int64_t N)
+{
+    PropState &P = ctx->prop;
+    for (int64_t off = 0; off < N; off += kMB) {
+        const int B = (int)std::min<int64_t>(kMB, N - off);
+        prop_inputs(X + off * VBGS_XS, nullptr, 1, B, ctx->box, P.Xin, ctx->stream);
+        mlp_forward(ctx, P.Xin, B);
+        prop_softmax_top(P.z, B, nullptr, nullptr, P.top + off * kPTop, nullptr, ctx->stream);
+        ctx->launches += 5;
+    }
+    return cudaGetLastError() == cudaSuccess ? VBGS_OK : fail(ctx, VBGS_ECUDA, "proposal inference failed");
+}
+
+// One epoch over the frame's labelled points.
+int prop_train(vbgs_ctx *ctx)
+{
+    PropState &P = ctx->prop;
+    if (P.n_lab <= 0) return VBGS_OK;
+    CU(cudaMemsetAsync(P.loss, 0, sizeof(float) * 2, ctx->stream));
+    for (int epoch = 0; epoch < kPropEpochs; epoch++) {
+        if (epoch == kPropEpochs - 1) CU(cudaMemsetAsync(P.loss, 0, sizeof(float) * 2, ctx->stream));
+        for (int64_t off = 0; off < P.n_lab; off += kMB) {
+            const int B = (int)std::min<int64_t>(kMB, P.n_lab - off);
+            const float *Xin = P.Xin + off * 6;
+            mlp_forward(ctx, Xin, B);
+            prop_softmax_top(P.z, B, P.Q + off * kPG, P.dz, nullptr, P.loss, ctx->stream);
+            mlp_backward(ctx, Xin, B);
+            prop_adam(P.w, P.wq, P.am, P.av, P.grad, kNParam, kPropLr, ++P.step, ctx->stream);
+            ctx->launches += 15;
+        }
+    }
+    P.frames_trained++;
+    P.rep[7] = (double)P.frames_trained;
+    P.rep[6] = -1.0;   // filled by vbgs_proposal_report from the device
+    return cudaGetLastError() == cudaSuccess ? VBGS_OK : fail(ctx, VBGS_ECUDA, "proposal training failed");
+}
+
+// Labels of the exact points of the frame (cluster masses) and their inputs:
+// at most kPropTrainPoints of them, evenly strided over the (Morton-ordered)
+// points so the sample covers the whole frame.
+void prop_label(vbgs_ctx *ctx, const double *X, const double *lse, int64_t n)
+{
+    PropState &P = ctx->prop;
+    const int64_t stride = (n + kPropTrainPoints - 1) / kPropTrainPoints;
+    const int64_t m = stride > 1 ? (n + stride - 1) / stride : n;
+    prop_labels(X, lse, stride > 1 ? stride : 1, m, ctx->d_rec32, P.order, P.cstart, P.cstat, P.Q, ctx->stream);
+    prop_inputs(X, nullptr, stride > 1 ? stride : 1, m, ctx->box, P.Xin, ctx->stream);
+    P.n_lab = m;
+    ctx->launches += 2;
+}
+
+// The E-step of one iteration with the proposal.
+int prop_estep(vbgs_ctx *ctx, int64_t N, bool last_iter)
+{
+    PropState &P = ctx->prop;
+    const double *X = ctx->last_sorted ? ctx->d_Xs : ctx->d_X;
+    int rc;
+    if (P.frame_exact) {
+        if ((rc = run_estep_on(ctx, X, N, ctx->d_lse, true))) return rc;
+        if (last_iter) prop_label(ctx, X, ctx->d_lse, N);
+        return VBGS_OK;
+    }
+    CU(cudaMemsetAsync(P.counters, 0, sizeof(unsigned long long) * 4, ctx->stream));
+    const uint32_t seed = (uint32_t)(P.frame * 0x9E3779B1ull) ^ 0xA5A5A5A5u;
+    if (prop_cand_pass1(X, N, ctx->d_rec32, P.order, P.cstart, P.cstat, P.top, kPropThresh, seed, kAuditPerMille,
+                        P.lse_c, P.bound, P.exact, P.cand, P.counters, ctx->stream))
+        return fail(ctx, VBGS_ECUDA, "candidate pass 1 failed");
+    unsigned long long cnt[4];
+    CU(cudaMemcpyAsync(cnt, P.counters, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const int64_t nfb = (int64_t)cnt[1], nau = (int64_t)cnt[2], ne = nfb + nau;
+    P.rep[10] = (double)cnt[3];
+    P.rep[0] = (double)cnt[0];
+    P.rep[1] = (double)nfb;
+    P.rep[2] = (double)nau;
+    P.rep[9] = (double)N;
+    if ((double)nfb > kExactFrameFrac * (double)N) {
+        // the proposal misses too much on this frame: run it exact
+        P.frame_exact = true;
+        P.rep[5] = 1.0;
+        P.rep[8] = (double)N * ctx->K;
+        if ((rc = run_estep_on(ctx, X, N, ctx->d_lse, true))) return rc;
+        if (last_iter) prop_label(ctx, X, ctx->d_lse, N);
+        return VBGS_OK;
+    }
+    P.rep[5] = 0.0;
+    P.rep[8] = (double)ne * ctx->K;
+    // exact E-step over the fallback and audit points
+    if (prop_exact_rows(P.exact, N, ctx->sb, P.ekey, P.erows, ctx->stream))
+        return fail(ctx, VBGS_ECUDA, "exact-row compaction failed");
+    prop_gather_rows(X, P.erows, ne, P.Xe, ctx->stream);
+    if ((rc = run_estep_on(ctx, P.Xe, ne, P.lse_e, true))) return rc;
+    prop_lse_combine(P.lse_c, P.lse_e, P.erows, ne, P.audit, ctx->stream);
+    // candidate statistics of the proposal points, added to the exact ones
+    if (prop_cand_lists(P.cand, P.exact, N, ctx->sb, P.pkey, P.plist, P.pstart, ctx->stream))
+        return fail(ctx, VBGS_ECUDA, "candidate lists failed");
+    prop_cand_pass2(X, P.lse_c, ctx->d_rec32, P.order, P.cstart, P.pstart, P.plist, ctx->d_kperm, ctx->d_dS,
+                    ctx->stream);
+    // lse of every point and its fixed-order sum
+    CU(cudaMemcpyAsync(ctx->d_lse, P.lse_c, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream));
+    int nparts = 0;
+    prop_sum_lse(P.lse_c, N, P.lsum, &nparts, ctx->stream);
+    prop_sum_final(P.lsum, nparts, ctx->d_scal + SC_SUM_LSE, ctx->stream);
+    ctx->launches += 12;
+    if (last_iter) {
+        prop_label(ctx, P.Xe, P.lse_e, ne);
+        // true missed mass of the audit sample
+        std::vector<int> rows((size_t)ne), ex((size_t)N);
+        std::vector<float> miss((size_t)ne);
+        if (ne > 0) {
+            CU(cudaMemcpyAsync(rows.data(), P.erows, sizeof(int) * ne, cudaMemcpyDeviceToHost, ctx->stream));
+            CU(cudaMemcpyAsync(miss.data(), P.audit, sizeof(float) * ne, cudaMemcpyDeviceToHost, ctx->stream));
+            CU(cudaMemcpyAsync(ex.data(), P.exact, sizeof(int) * N, cudaMemcpyDeviceToHost, ctx->stream));
+            CU(cudaStreamSynchronize(ctx->stream));
+        }
+        double mx = 0.0, sum = 0.0;
+        int64_t na = 0;
+        for (int64_t i = 0; i < ne; i++)
+            if (ex[(size_t)rows[(size_t)i]] == 2) {
+                mx = std::max(mx, (double)miss[(size_t)i]);
+                sum += miss[(size_t)i];
+                na++;
+            }
+        P.rep[3] = mx;
+        P.rep[4] = na ? sum / na : 0.0;
+    }
+    return VBGS_OK;
+}
+
+int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats, bool last_iter = false)
+{
+    if (ctx->prop.on && want_stats && N > 0) return prop_estep(ctx, N, last_iter);
+    return run_estep_on(ctx, ctx->last_sorted ? ctx->d_Xs : ctx->d_X, N, ctx->d_lse, want_stats);
 }
 
 int check_flags(vbgs_ctx *ctx)
@@ -317,17 +603,30 @@ int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters)
     if ((rc = order_frame(ctx, N, true))) return rc;
     // Posterior entering the frame: the effective prior prior0 (+) S_past.
     if ((rc = run_mstep(ctx, nullptr))) return rc;
+    const bool prop = ctx->prop.on && N > 0;
+    if (prop) {
+        ctx->prop.frame_exact = false;
+        ctx->prop.n_lab = 0;
+        if ((rc = prop_ensure_frame(ctx, N)) || (rc = prop_refresh(ctx)) ||
+            (rc = prop_propose(ctx, ctx->last_sorted ? ctx->d_Xs : ctx->d_X, N)))
+            return rc;
+    }
     for (int it = 0; it < n_iters; it++) {
-        if ((rc = run_estep(ctx, N, true))) return rc;
+        if ((rc = run_estep(ctx, N, true, it == n_iters - 1))) return rc;
         if (launch_elbo(ctx->d_scal, N, ctx->d_elbo + it, ctx->stream, &ctx->prof) < 0)
             return fail(ctx, VBGS_ECUDA, "ELBO launch failed");
         ctx->launches += 1;
         if ((rc = run_mstep(ctx, ctx->d_dS))) return rc;
+        if (prop && it + 1 < n_iters && (rc = prop_refresh(ctx))) return rc;
     }
     if (launch_commit(ctx->d_Spast, ctx->d_dS, ctx->K, ctx->d_flags, ctx->stream, &ctx->prof) < 0)
         return fail(ctx, VBGS_ECUDA, "commit launch failed");
     ctx->launches += 1;
     ctx->last_N = N;
+    if (prop) {
+        if ((rc = prop_train(ctx))) return rc;
+        ctx->prop.frame++;
+    }
     return VBGS_OK;
 }
 
@@ -340,6 +639,14 @@ void free_all(vbgs_ctx *ctx)
                     ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp, ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_plan};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    {
+        PropState &P = ctx->prop;
+        void *pp[] = {P.cent, P.kpts, P.cstat, P.order, P.cstart, P.skey, P.w, P.wq, P.am, P.av, P.grad, P.top, P.cand,
+                      P.exact, P.erows, P.plist, P.pstart, P.pkey, P.ekey, P.lse_c, P.Xe, P.lse_e, P.lsum, P.bound,
+                      P.audit, P.counters, P.Xin, P.Q, P.h1, P.h2, P.z, P.dz, P.dh2, P.dh1, P.loss};
+        for (void *p : pp)
+            if (p) cudaFree(p);
+    }
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     ctx->prof.pool.clear();
     if (ctx->prof.d_pairs) cudaFree(ctx->prof.d_pairs);
@@ -422,8 +729,11 @@ extern "C" int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const 
 {
     if (!scenes || n_scenes <= 0 || !points || !N || n_iters < 1)
         return fail(nullptr, VBGS_EINVAL, "vbgs_update_batched: bad arguments");
-    for (int i = 0; i < n_scenes; i++)
+    for (int i = 0; i < n_scenes; i++) {
         if (!scenes[i]) return fail(nullptr, VBGS_EINVAL, "vbgs_update_batched: scene %d is NULL", i);
+        if (scenes[i]->prop.on)
+            return fail(nullptr, VBGS_EINVAL, "vbgs_update_batched: scene %d uses the proposal (host-driven fallback)", i);
+    }
     std::lock_guard<std::mutex> lock(g_batch.mu);
     if (batch_streams(n_scenes) || tc_set_attributes())
         return fail(nullptr, VBGS_ECUDA, "vbgs_update_batched: stream set-up failed");
@@ -539,7 +849,7 @@ extern "C" int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, con
 {
     if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
     if (N <= 0 || !points) return fail(ctx, VBGS_EINVAL, "vbgs_autotune needs points");
-    if (!is_tc(ctx)) return VBGS_OK;   // the CUDA-core forms have nothing to tune
+    if (!is_tc(ctx) || ctx->prop.on) return VBGS_OK;   // nothing to tune
     // size class: rounded log2 of N and K
     const int nb = (int)std::lround(std::log2((double)N)), kb = (int)std::lround(std::log2((double)ctx->K));
     char key[96];
@@ -596,6 +906,78 @@ extern "C" int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, con
             fprintf(f, "%s %d %d\n", key, b1, b2);
             fclose(f);
         }
+    return VBGS_OK;
+}
+
+extern "C" int vbgs_proposal_report(vbgs_ctx *ctx, double *out)
+{
+    if (!ctx || !out) return fail(ctx, VBGS_EINVAL, "vbgs_proposal_report: NULL argument");
+    if (!ctx->prop.on) return fail(ctx, VBGS_EINVAL, "the context has no proposal");
+    float loss = 0.f;
+    CU(cudaMemcpyAsync(&loss, ctx->prop.loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 11; i++) out[i] = ctx->prop.rep[i];
+    out[6] = ctx->prop.n_lab > 0 ? (double)loss / (double)ctx->prop.n_lab : 0.0;
+    return VBGS_OK;
+}
+
+extern "C" int vbgs_proposal_weights(vbgs_ctx *ctx, float *get, const float *set)
+{
+    if (!ctx || !ctx->prop.on) return fail(ctx, VBGS_EINVAL, "the context has no proposal");
+    if (set) {
+        int rc = prop_set_weights(ctx, set);
+        if (rc) return rc;
+    }
+    if (get) {
+        CU(cudaMemcpyAsync(get, ctx->prop.w, sizeof(float) * kNParam, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return VBGS_OK;
+}
+
+extern "C" int vbgs_proposal_grad(vbgs_ctx *ctx, const float *inputs, const float *labels, int B, float *loss,
+                                  float *grad, int *top)
+{
+    if (!ctx || !ctx->prop.on) return fail(ctx, VBGS_EINVAL, "the context has no proposal");
+    if (!inputs || B <= 0 || B > kMB) return fail(ctx, VBGS_EINVAL, "vbgs_proposal_grad: need 1 <= B <= 4096 inputs");
+    PropState &P = ctx->prop;
+    int rc;
+    if ((rc = prop_ensure_frame(ctx, B))) return rc;
+    CU(cudaMemcpyAsync(P.Xin, inputs, sizeof(float) * B * 6, cudaMemcpyHostToDevice, ctx->stream));
+    mlp_forward(ctx, P.Xin, B);
+    if (top) {
+        prop_softmax_top(P.z, B, nullptr, nullptr, P.top, nullptr, ctx->stream);
+        CU(cudaMemcpyAsync(top, P.top, sizeof(int) * B * kPTop, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if (labels) {
+        CU(cudaMemcpyAsync(P.Q, labels, sizeof(float) * B * kPG, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemsetAsync(P.loss, 0, sizeof(float), ctx->stream));
+        prop_softmax_top(P.z, B, P.Q, P.dz, nullptr, P.loss, ctx->stream);
+        mlp_backward(ctx, P.Xin, B);
+        float l = 0.f;
+        CU(cudaMemcpyAsync(&l, P.loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        if (grad) CU(cudaMemcpyAsync(grad, P.grad, sizeof(float) * kNParam, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        if (loss) *loss = l / (float)B;
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return VBGS_OK;
+}
+
+extern "C" int vbgs_proposal_clusters(vbgs_ctx *ctx, float *centroids, int *cluster_of)
+{
+    if (!ctx || !ctx->prop.on) return fail(ctx, VBGS_EINVAL, "the context has no proposal");
+    int rc;
+    if ((rc = prop_refresh(ctx))) return rc;
+    std::vector<int> order(ctx->K), cstart(kPG + 1), kperm(ctx->K);
+    if (centroids) CU(cudaMemcpyAsync(centroids, ctx->prop.cent, sizeof(float) * kPG * 6, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(order.data(), ctx->prop.order, sizeof(int) * ctx->K, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(cstart.data(), ctx->prop.cstart, sizeof(int) * (kPG + 1), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(kperm.data(), ctx->d_kperm, sizeof(int) * ctx->K, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (cluster_of)
+        for (int g = 0; g < kPG; g++)
+            for (int i = cstart[g]; i < cstart[g + 1]; i++) cluster_of[kperm[order[i]]] = g;
     return VBGS_OK;
 }
 
@@ -708,6 +1090,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
         CU(cudaStreamSynchronize(ctx->stream));
     }
     if ((rc = run_mstep(ctx, nullptr))) return init_fail(rc);
+    if ((ctx->flags & VBGS_FLAG_PROPOSAL) && (rc = prop_alloc(ctx))) return init_fail(rc);
     CU(cudaStreamSynchronize(ctx->stream));
 #undef CU
 #define CU(call)                                                                         \

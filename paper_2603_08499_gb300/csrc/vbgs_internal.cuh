@@ -20,6 +20,9 @@
 #include "../../include/vbgs.h"
 
 #define VBGS_REC 32       // doubles (or floats) per E-step record
+#define VBGS_PROP_CLUSTERS 1024   // proposal clusters (k-means of the posterior means)
+#define VBGS_PROP_TOP 4           // clusters proposed per point
+#define VBGS_PROP_MAXCAND 32      // candidate clusters per point after certified expansion
 #define VBGS_XS 8         // doubles per staged point
 
 namespace vbgs {
@@ -167,7 +170,68 @@ int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned
                     double2 *part, size_t part_cap_doubles, float *tmax, int *flags, int num_sms, int splits_override,
                     int *splits_out, cudaStream_t st, Prof *pf);
 
+// Learned proposal (vbgs_proposal.cu).
+int prop_set_attributes();
+int prop_launch_kmeans(const float *rec32, int K, float csc, float *pts, float *cent, SortBuffers &sb, int *order,
+                       unsigned int *skey, int *cstart, int lloyd_iters, cudaStream_t st);
+int prop_launch_cluster_stats(const float *rec32, const int *order, const int *cstart, float *cstat, cudaStream_t st);
+void prop_gemm(int M, int N, int K, const float *A, int sam, int sak, const float *B, int sbk, int sbn, float *C,
+               int ldc, const float *bias, bool relu, bool accumulate, cudaStream_t st);
+void prop_colsum(const float *X, int M, int Nc, float *out, cudaStream_t st);
+void prop_relu_bwd(float *dH, const float *H, size_t n, cudaStream_t st);
+void prop_softmax_top(const float *Z, int B, const float *Q, float *dZ, int *top, float *loss_sum, cudaStream_t st);
+void prop_adam(float *w, float *wq, float *m, float *v, const float *g, size_t n, float lr, int step, cudaStream_t st);
+void prop_inputs(const double *X, const int *rows, int64_t rstride, int64_t n, const BoxParams &box, float *out,
+                 cudaStream_t st);
+int prop_cand_pass1(const double *X, int64_t N, const float *rec32, const int *order, const int *cstart,
+                    const float *cstat, const int *top, float thresh, uint32_t seed, uint32_t audit_per_mille,
+                    double *lse_c, float *bound, int *exact, int *cand, unsigned long long *counters, cudaStream_t st);
+void prop_gather_rows(const double *X, const int *rows, int64_t n, double *Xe, cudaStream_t st);
+int prop_cand_lists(const int *cand, const int *exact, int64_t N, SortBuffers &sb, unsigned int *skey, int *plist,
+                    int *pstart, cudaStream_t st);
+void prop_cand_pass2(const double *X, const double *lse_c, const float *rec32, const int *order, const int *cstart,
+                     const int *pstart, const int *plist, const int *kperm, double *dS, cudaStream_t st);
+void prop_labels(const double *Xe, const double *lse_e, int64_t rstride, int64_t ne, const float *rec32,
+                 const int *order, const int *cstart, const float *cstat, float *Q, cudaStream_t st);
+void prop_lse_combine(double *lse_c, const double *lse_e, const int *erows, int64_t ne, float *audit_missed,
+                      cudaStream_t st);
+void prop_sum_lse(const double *v, int64_t n, double *part, int *nparts, cudaStream_t st);
+void prop_add(double *a, const double *b, size_t n, cudaStream_t st);
+void prop_init_centroids(const float *rec32, int K, float csc, float *cent, cudaStream_t st);
+void prop_sum_final(const double *part, int n, double *out, cudaStream_t st);
+int prop_exact_rows(const int *exact, int64_t N, SortBuffers &sb, unsigned int *skey, int *erows, cudaStream_t st);
+
 } // namespace vbgs
+
+// State of the learned proposal of a context (VBGS_FLAG_PROPOSAL).
+struct PropState {
+    bool on = false;
+    bool centroids_ready = false;
+    // clusters (k-means of the posterior means, at record positions)
+    float *cent = nullptr, *kpts = nullptr, *cstat = nullptr;
+    int *order = nullptr, *cstart = nullptr;
+    unsigned int *skey = nullptr;
+    // network: [W1 128x6 | b1 128 | W2 128x128 | b2 128 | W3 1024x128 | b3 1024]
+    size_t nparam = 0;
+    float *w = nullptr, *wq = nullptr, *am = nullptr, *av = nullptr, *grad = nullptr;
+    int step = 0;
+    int64_t frames_trained = 0;
+    // per frame
+    int64_t ncap = 0;
+    int *top = nullptr, *cand = nullptr, *exact = nullptr, *erows = nullptr, *plist = nullptr, *pstart = nullptr;
+    unsigned int *pkey = nullptr, *ekey = nullptr;
+    double *lse_c = nullptr, *Xe = nullptr, *lse_e = nullptr, *lsum = nullptr;
+    float *bound = nullptr, *audit = nullptr;
+    unsigned long long *counters = nullptr;   // [0] candidate pairs, [1] fallback, [2] audit
+    bool frame_exact = false;
+    uint64_t frame = 0;
+    // training set of the current frame and minibatch buffers
+    int64_t lab_cap = 0, n_lab = 0;
+    float *Xin = nullptr, *Q = nullptr;
+    float *h1 = nullptr, *h2 = nullptr, *z = nullptr, *dz = nullptr, *dh2 = nullptr, *dh1 = nullptr, *loss = nullptr;
+    // report of the last frame
+    double rep[11] = {};
+};
 
 struct vbgs_ctx {
     int K = 0, D = 6;
@@ -204,5 +268,6 @@ struct vbgs_ctx {
     int64_t last_N = 0;
     int64_t launches = 0;
     vbgs::Prof prof;
+    PropState prop;
     std::string err;
 };

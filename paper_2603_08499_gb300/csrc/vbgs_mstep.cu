@@ -69,6 +69,24 @@ __device__ double mv_lgamma6(double a)
     return s;
 }
 
+// Largest eigenvalue of a symmetric 3x3 matrix (a00, a01, a02, a11, a12,
+// a22) by the trigonometric solution of its characteristic cubic (Smith 1961):
+// q = tr/3, p = sqrt(tr((A - qI)^2)/6), r = det((A - qI)/p)/2,
+// lambda_max = q + 2 p cos(acos(r)/3).
+__device__ double sym3_max_eig(double a00, double a01, double a02, double a11, double a12, double a22)
+{
+    const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    if (p1 == 0.0) return fmax(a00, fmax(a11, a22));
+    const double q = (a00 + a11 + a22) / 3.0;
+    const double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    const double p = sqrt((b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1) / 6.0);
+    const double ip = 1.0 / p;
+    const double c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+    const double r = 0.5 * (c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02));
+    const double phi = acos(fmin(1.0, fmax(-1.0, r))) / 3.0;
+    return q + 2.0 * p * cos(phi);
+}
+
 // Posterior parameters from prior and statistics; A is the full symmetric W^-1.
 __device__ void nw_from_stats(const MstepParams &P, const double *m0, const double *s,
                               double &alpha, double &beta, double &nu, double m[6], double A[36])
@@ -212,6 +230,20 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
         r32[27] = (float)(c * 1.4426950408889634);
 #pragma unroll
         for (int i = 28; i < 32; i++) { r[i] = 0.0; r32[i] = 0.f; }
+        // For the proposal certificate: lower bounds (log2 units) of the
+        // smallest eigenvalue of the marginal precision of the position block
+        // and of the colour block.  Minimising (x - m)^T nu W (x - m) over the
+        // colour part leaves the position part's quadratic form in the inverse
+        // of its covariance block (W^-1)_pp / nu, whose smallest eigenvalue is
+        // nu / lambda_max((W^-1)_pp); same for colour.
+        // (exact largest eigenvalue of each 3 x 3 block, shrunk by 1e-6 so
+        // that rounding keeps the bound below the true smallest eigenvalue)
+        const double lpp = sym3_max_eig(Aq[0], Aq[1], Aq[2], Aq[7], Aq[8], Aq[14]);
+        const double lcc = sym3_max_eig(Aq[21], Aq[22], Aq[23], Aq[28], Aq[29], Aq[35]);
+        r32[28] = (float)(1.4426950408889634 * (1.0 - 1e-6) * nq / lpp);
+        r32[29] = (float)(1.4426950408889634 * (1.0 - 1e-6) * nq / lcc);
+        // and of the full precision: lambda_min(nu W) >= nu / tr(W^-1)
+        r32[30] = (float)(1.4426950408889634 * nq / (Aq[0] + Aq[7] + Aq[14] + Aq[21] + Aq[28] + Aq[35]));
 
         double *cache = pc + (size_t)k * kPC;
         if (!dS) {

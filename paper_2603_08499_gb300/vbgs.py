@@ -33,6 +33,11 @@ PRECISIONS = {"fp64": VBGS_FP64, "fp16x3": VBGS_FP16X3, "bf16x3": VBGS_BF16X3, "
 VBGS_FLAG_NO_REORDER = 1
 VBGS_FLAG_NO_SKIP = 2
 VBGS_FLAG_PLAIN = VBGS_FLAG_NO_REORDER | VBGS_FLAG_NO_SKIP
+VBGS_FLAG_PROPOSAL = 4
+PROP_CLUSTERS = 1024
+PROP_NPARAM = 128 * 6 + 128 + 128 * 128 + 128 + 1024 * 128 + 1024
+PROP_REPORT = ["cand_pairs", "fallback", "audit", "audit_max_missed", "audit_mean_missed", "frame_exact",
+               "train_loss", "frames_trained", "exact_pairs", "points", "added_clusters"]
 
 D = 6
 F = 28
@@ -43,6 +48,7 @@ EXPORTS = [
     "vbgs_set_stats", "vbgs_get_frame_stats", "vbgs_get_lse", "vbgs_last_launch_count",
     "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_pairs", "vbgs_profile_name", "vbgs_probe_peaks",
     "vbgs_estep_noalloc", "vbgs_update_batched", "vbgs_autotune", "vbgs_get_tuning",
+    "vbgs_proposal_report", "vbgs_proposal_weights", "vbgs_proposal_grad", "vbgs_proposal_clusters",
     "vbgs_last_error", "vbgs_destroy",
 ]
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
@@ -100,6 +106,11 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
                                         C.POINTER(C.c_int64), C.c_int, _DP]
     lib.vbgs_autotune.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_char_p]
     lib.vbgs_get_tuning.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    _FP = C.POINTER(C.c_float)
+    lib.vbgs_proposal_report.argtypes = [C.c_void_p, _DP]
+    lib.vbgs_proposal_weights.argtypes = [C.c_void_p, _FP, _FP]
+    lib.vbgs_proposal_grad.argtypes = [C.c_void_p, _FP, _FP, C.c_int, _FP, _FP, C.POINTER(C.c_int)]
+    lib.vbgs_proposal_clusters.argtypes = [C.c_void_p, _FP, C.POINTER(C.c_int)]
     return lib
 
 
@@ -275,6 +286,43 @@ def vbgs_get_tuning(ctx) -> tuple[int, int]:
     a, b = C.c_int(0), C.c_int(0)
     _check(lib().vbgs_get_tuning(ctx, C.byref(a), C.byref(b)), ctx)
     return int(a.value), int(b.value)
+
+
+def _fp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def vbgs_proposal_report(ctx) -> dict:
+    out = np.zeros(11)
+    _check(lib().vbgs_proposal_report(ctx, _dp(out)), ctx)
+    return dict(zip(PROP_REPORT, out.tolist()))
+
+
+def vbgs_proposal_weights(ctx, set_to=None) -> np.ndarray:
+    get = np.zeros(PROP_NPARAM, dtype=np.float32)
+    st = None if set_to is None else np.ascontiguousarray(set_to, dtype=np.float32)
+    _check(lib().vbgs_proposal_weights(ctx, _fp(get), _fp(st)), ctx)
+    return get
+
+
+def vbgs_proposal_grad(ctx, inputs, labels=None):
+    """(loss, grad, top) of the network on B inputs (B x 6 in [-1, 1]) and labels (B x 1024)."""
+    x = np.ascontiguousarray(inputs, dtype=np.float32)
+    B = x.shape[0]
+    q = None if labels is None else np.ascontiguousarray(labels, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.zeros(PROP_NPARAM, dtype=np.float32)
+    top = np.zeros((B, 4), dtype=np.int32)
+    _check(lib().vbgs_proposal_grad(ctx, _fp(x), _fp(q), B, _fp(loss), _fp(grad),
+                                    top.ctypes.data_as(C.POINTER(C.c_int))), ctx)
+    return float(loss[0]), grad, top
+
+
+def vbgs_proposal_clusters(ctx, K: int):
+    cent = np.zeros((PROP_CLUSTERS, 6), dtype=np.float32)
+    cl = np.zeros(K, dtype=np.int32)
+    _check(lib().vbgs_proposal_clusters(ctx, _fp(cent), cl.ctypes.data_as(C.POINTER(C.c_int))), ctx)
+    return cent, cl
 
 
 def vbgs_last_error(ctx=None) -> str:

@@ -301,3 +301,73 @@ def test_elbo_entry_matches_update_trace():
     _, S1, _, _ = O.cavi_frame(X[:250], pr, np.zeros((20, 28)), 3)
     e, _, _, _ = O.cavi_frame(X[250:], pr, S1, 2)
     assert O.elbo(X[250:], pr, S1) == pytest.approx(e[0], rel=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# proposal network oracle (FP64): the backward pass against central finite
+# differences of the forward pass, and closed forms of the loss
+
+
+def _mlp_case(seed=0, B=6):
+    from oracle import mlp as M
+    rng = np.random.default_rng(seed)
+    theta = np.concatenate([rng.normal(0, 1 / np.sqrt(s[-1]) if len(s) == 2 else 0.1, int(np.prod(s))).ravel()
+                            for s in M.SHAPES])
+    x = rng.uniform(-1, 1, (B, 6))
+    q = rng.dirichlet(np.full(1024, 0.05), size=B)
+    return M, theta, x, q
+
+
+def test_mlp_gradient_matches_central_differences():
+    M, theta, x, q = _mlp_case()
+    g = M.grad(theta, x, q)
+    rng = np.random.default_rng(1)
+    # a coordinate sample from every parameter block plus one random direction
+    sizes = [int(np.prod(s)) for s in M.SHAPES]
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    coords = np.concatenate([s + rng.choice(n, min(n, 40), replace=False) for s, n in zip(starts, sizes)])
+    eps = 1e-6
+    h1, h2, _ = M.forward(theta, x)
+    # keep the sample away from ReLU kinks: no pre-activation within the step
+    assert np.min(np.abs(h1[h1 > 0])) > 1e-4 and np.min(np.abs(h2[h2 > 0])) > 1e-4
+    for i in coords:
+        e = np.zeros_like(theta)
+        e[i] = eps
+        fd = (M.loss(theta + e, x, q) - M.loss(theta - e, x, q)) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9, (i, fd, g[i])
+    v = rng.normal(size=theta.shape)
+    v /= np.linalg.norm(v)
+    fd = (M.loss(theta + eps * v, x, q) - M.loss(theta - eps * v, x, q)) / (2 * eps)
+    assert abs(fd - g @ v) <= 1e-6 * abs(g @ v)
+
+
+def test_mlp_loss_closed_forms():
+    M, theta, x, q = _mlp_case(seed=2)
+    # zero output layer: uniform softmax, loss = ln 1024 for any normalised q
+    z0 = theta.copy()
+    off = sum(int(np.prod(s)) for s in M.SHAPES[:4])
+    z0[off:] = 0.0
+    assert abs(M.loss(z0, x, q) - np.log(1024.0)) <= 1e-12
+    # the output-bias gradient is the mean of softmax - q, which sums to 0
+    g = M.grad(theta, x, q)
+    assert abs(g[-1024:].sum()) <= 1e-12
+    # loss >= entropy of q (Gibbs), equality only at softmax = q
+    ent = -(q * np.log(np.where(q > 0, q, 1.0))).sum() / x.shape[0]
+    assert M.loss(theta, x, q) >= ent
+
+
+def test_top4_and_nearest_centroid_tie_rules():
+    from oracle import mlp as M
+    z = np.array([[1.0, 3.0, 3.0, 0.0, 3.0, 2.0, 3.0]])
+    assert list(M.top4(z)[0]) == [1, 2, 4, 6]
+    rng = np.random.default_rng(3)
+    z = rng.integers(0, 5, (50, 40)).astype(float)
+    t = M.top4(z)
+    for row, sel in zip(z, t):
+        # brute force: the 4 smallest (-value, index) pairs
+        ref = sorted(range(len(row)), key=lambda j: (-row[j], j))[:4]
+        assert list(sel) == ref
+    c = np.array([[0.0, 0, 0, 0, 0, 0], [2.0, 0, 0, 0, 0, 0], [1.0, 0, 0, 0, 0, 0]])
+    p = np.array([[0.5, 0, 0, 0, 0, 0], [1.5, 0, 0, 0, 0, 0], [3.0, 0, 0, 0, 0, 0]])
+    a, _ = M.nearest_centroid(p, c)
+    assert list(a) == [0, 1, 1]
