@@ -159,13 +159,20 @@ int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_splits);
  * clusters, and with labels (B x 1024) the mean soft cross-entropy and its
  * gradient (host arrays; no update).  vbgs_proposal_clusters refreshes the
  * clusters and returns the centroids (1024 x 6) and each component's
- * cluster (K).  The proposal is host-driven (one synchronisation per
- * iteration) and is not available in vbgs_update_batched. */
+ * cluster (K).  vbgs_proposal_bounds evaluates the certificate of the
+ * current posterior (prior (+) accumulated statistics) at N host points
+ * (N x 6): ub[n * 1024 + g] (host, N x 1024) is an upper bound, in log2
+ * units, of log2 sum_{k in cluster g} exp(l_nk), with l_nk the natural-unit
+ * logit of Eq. 1's E-step; cluster_of (K, nullable) receives each
+ * component's cluster.  It refreshes the clusters once, like the start of a
+ * frame.  The proposal is host-driven (one synchronisation per iteration)
+ * and is not available in vbgs_update_batched. */
 int vbgs_proposal_report(vbgs_ctx *ctx, double *out);
 int vbgs_proposal_weights(vbgs_ctx *ctx, float *get, const float *set);
 int vbgs_proposal_grad(vbgs_ctx *ctx, const float *inputs, const float *labels, int B, float *loss, float *grad,
                        int *top);
 int vbgs_proposal_clusters(vbgs_ctx *ctx, float *centroids, int *cluster_of);
+int vbgs_proposal_bounds(vbgs_ctx *ctx, const double *points, int64_t N, float *ub, int *cluster_of);
 
 /* ELBO of the points X under the current posterior q = prior0 (+) S_past
  * (the value elbo_trace[0] of a vbgs_update on X would take), without

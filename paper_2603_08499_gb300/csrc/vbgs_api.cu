@@ -341,7 +341,8 @@ int prop_alloc(vbgs_ctx *ctx)
     const int K = ctx->K;
     int rc;
     if ((rc = dalloc(ctx, &P.cent, (size_t)kPG * 6)) || (rc = dalloc(ctx, &P.kpts, (size_t)K * 6)) ||
-        (rc = dalloc(ctx, &P.cstat, (size_t)kPG * 20)) || (rc = dalloc(ctx, &P.order, (size_t)K)) ||
+        (rc = dalloc(ctx, &P.cpar, prop_cpar_floats())) ||
+        (rc = dalloc(ctx, &P.cscr, prop_cscr_doubles())) || (rc = dalloc(ctx, &P.mscr, prop_mscr_floats(K))) || (rc = dalloc(ctx, &P.order, (size_t)K)) ||
         (rc = dalloc(ctx, &P.cstart, (size_t)kPG + 1)) || (rc = dalloc(ctx, &P.skey, (size_t)K)) ||
         (rc = dalloc(ctx, &P.w, kNParam)) || (rc = dalloc(ctx, &P.wq, kNParam)) || (rc = dalloc(ctx, &P.am, kNParam)) ||
         (rc = dalloc(ctx, &P.av, kNParam)) || (rc = dalloc(ctx, &P.grad, kNParam)) ||
@@ -349,7 +350,8 @@ int prop_alloc(vbgs_ctx *ctx)
         (rc = dalloc(ctx, &P.dh1, (size_t)kMB * kHid)) || (rc = dalloc(ctx, &P.dh2, (size_t)kMB * kHid)) ||
         (rc = dalloc(ctx, &P.z, (size_t)kMB * kPG)) || (rc = dalloc(ctx, &P.dz, (size_t)kMB * kPG)) ||
         (rc = dalloc(ctx, &P.loss, 2)) || (rc = dalloc(ctx, &P.counters, 4)) ||
-        (rc = dalloc(ctx, &P.pstart, (size_t)kPG + 1)))
+        (rc = dalloc(ctx, &P.pstart, (size_t)kPG + 1)) || (rc = dalloc(ctx, &P.item_start, (size_t)kPG + 1)) ||
+        (rc = dalloc(ctx, &P.fbase, (size_t)kPG + 1)))
         return rc;
     P.nparam = kNParam;
     // He-uniform initial weights from a fixed seed, zero biases
@@ -379,7 +381,7 @@ int prop_ensure_frame(vbgs_ctx *ctx, int64_t N)
             (rc = dalloc(ctx, &P.pkey, (size_t)cap * VBGS_PROP_MAXCAND)) || (rc = dalloc(ctx, &P.ekey, (size_t)cap)) ||
             (rc = dalloc(ctx, &P.lse_c, (size_t)cap)) || (rc = dalloc(ctx, &P.Xe, (size_t)cap * VBGS_XS)) ||
             (rc = dalloc(ctx, &P.lse_e, (size_t)cap)) || (rc = dalloc(ctx, &P.lsum, (size_t)cap / 256 + 2)) ||
-            (rc = dalloc(ctx, &P.bound, (size_t)cap)) || (rc = dalloc(ctx, &P.audit, (size_t)cap)) ||
+            (rc = dalloc(ctx, &P.bound, (size_t)cap)) || (rc = dalloc(ctx, &P.ub, (size_t)cap * kPG)) || (rc = dalloc(ctx, &P.audit, (size_t)cap)) ||
             (rc = dalloc(ctx, &P.Xin, (size_t)std::max<int64_t>(cap, kPropTrainPoints) * 6)) ||
             (rc = dalloc(ctx, &P.Q, (size_t)kPropTrainPoints * kPG)))
             return rc;
@@ -389,21 +391,31 @@ int prop_ensure_frame(vbgs_ctx *ctx, int64_t N)
     return VBGS_OK;
 }
 
-// k-means of the posterior means (warm start) and the certificate terms.
-int prop_refresh(vbgs_ctx *ctx)
+// k-means of the posterior means (warm start) and the certificate tables of
+// the current posterior; with_frame: the posterior includes the frame's
+// statistics dS (weights of the cluster metrics).
+int prop_refresh(vbgs_ctx *ctx, bool with_frame)
 {
     PropState &P = ctx->prop;
-    // colour weighted like space in the clustering: scaled by the largest
-    // extent of the position box
-    const float csc = (float)(1.0 / std::min(ctx->box.inv_ext[0], std::min(ctx->box.inv_ext[1], ctx->box.inv_ext[2])));
+    // colour weighted against position in the clustering: scaled by a fifth
+    // of the largest extent of the position box
+    const double ext = 1.0 / std::min(ctx->box.inv_ext[0], std::min(ctx->box.inv_ext[1], ctx->box.inv_ext[2]));
+    const float csc = (float)(0.2 * ext);
+    double xmax = 1.0;
+    for (int q = 0; q < 3; q++)
+        xmax = std::max(xmax, std::max(std::fabs(ctx->box.lo[q]), std::fabs(ctx->box.lo[q] + 1.0 / ctx->box.inv_ext[q])));
+    if (!ctx->sb.temp || ctx->sb.cap < ctx->K || !ctx->d_rec || !ctx->d_rec32)
+        return fail(ctx, VBGS_ECUDA, "proposal refresh before the buffers exist");
     if (!P.centroids_ready) {
         prop_init_centroids(ctx->d_rec32, ctx->K, csc, P.cent, ctx->stream);
         P.centroids_ready = true;
     }
     if (prop_launch_kmeans(ctx->d_rec32, ctx->K, csc, P.kpts, P.cent, ctx->sb, P.order, P.skey, P.cstart, 2, ctx->stream) ||
-        prop_launch_cluster_stats(ctx->d_rec32, P.order, P.cstart, P.cstat, ctx->stream))
+        prop_launch_certificate(ctx->d_rec, ctx->d_rec32, P.order, P.skey, P.cstart, ctx->K, ctx->d_Spast,
+                                with_frame ? ctx->d_dS : nullptr, ctx->d_kperm, (float)(4.0 * xmax), P.cpar, P.cscr,
+                                P.mscr, ctx->stream))
         return fail(ctx, VBGS_ECUDA, "proposal cluster refresh failed");
-    ctx->launches += 9;
+    ctx->launches += 11;
     return VBGS_OK;
 }
 
@@ -474,14 +486,15 @@ int prop_train(vbgs_ctx *ctx)
 
 // Labels of the exact points of the frame (cluster masses) and their inputs:
 // at most kPropTrainPoints of them, evenly strided over the (Morton-ordered)
-// points so the sample covers the whole frame.
-void prop_label(vbgs_ctx *ctx, const double *X, const double *lse, int64_t n)
+// points so the sample covers the whole frame.  rows: frame index of each
+// point when X holds gathered points (null: X is the frame).
+void prop_label(vbgs_ctx *ctx, const double *X, const double *lse, int64_t n, const int *rows)
 {
     PropState &P = ctx->prop;
-    const int64_t stride = (n + kPropTrainPoints - 1) / kPropTrainPoints;
-    const int64_t m = stride > 1 ? (n + stride - 1) / stride : n;
-    prop_labels(X, lse, stride > 1 ? stride : 1, m, ctx->d_rec32, P.order, P.cstart, P.cstat, P.Q, ctx->stream);
-    prop_inputs(X, nullptr, stride > 1 ? stride : 1, m, ctx->box, P.Xin, ctx->stream);
+    const int64_t stride = std::max<int64_t>((n + kPropTrainPoints - 1) / kPropTrainPoints, 1);
+    const int64_t m = (n + stride - 1) / stride;
+    prop_labels(X, lse, rows, stride, m, ctx->d_rec32, P.order, P.cstart, P.ub, P.Q, ctx->stream);
+    prop_inputs(X, nullptr, stride, m, ctx->box, P.Xin, ctx->stream);
     P.n_lab = m;
     ctx->launches += 2;
 }
@@ -494,12 +507,18 @@ int prop_estep(vbgs_ctx *ctx, int64_t N, bool last_iter)
     int rc;
     if (P.frame_exact) {
         if ((rc = run_estep_on(ctx, X, N, ctx->d_lse, true))) return rc;
-        if (last_iter) prop_label(ctx, X, ctx->d_lse, N);
+        if (last_iter) {
+            prop_bounds(X, N, P.cpar, P.ub, ctx->stream);
+            prop_label(ctx, X, ctx->d_lse, N, nullptr);
+            ctx->launches += 1;
+        }
         return VBGS_OK;
     }
+    prop_bounds(X, N, P.cpar, P.ub, ctx->stream);
+    ctx->launches += 1;
     CU(cudaMemsetAsync(P.counters, 0, sizeof(unsigned long long) * 4, ctx->stream));
     const uint32_t seed = (uint32_t)(P.frame * 0x9E3779B1ull) ^ 0xA5A5A5A5u;
-    if (prop_cand_pass1(X, N, ctx->d_rec32, P.order, P.cstart, P.cstat, P.top, kPropThresh, seed, kAuditPerMille,
+    if (prop_cand_pass1(X, N, ctx->d_rec32, P.order, P.cstart, P.ub, P.top, kPropThresh, seed, kAuditPerMille,
                         P.lse_c, P.bound, P.exact, P.cand, P.counters, ctx->stream))
         return fail(ctx, VBGS_ECUDA, "candidate pass 1 failed");
     unsigned long long cnt[4];
@@ -517,7 +536,7 @@ int prop_estep(vbgs_ctx *ctx, int64_t N, bool last_iter)
         P.rep[5] = 1.0;
         P.rep[8] = (double)N * ctx->K;
         if ((rc = run_estep_on(ctx, X, N, ctx->d_lse, true))) return rc;
-        if (last_iter) prop_label(ctx, X, ctx->d_lse, N);
+        if (last_iter) prop_label(ctx, X, ctx->d_lse, N, nullptr);
         return VBGS_OK;
     }
     P.rep[5] = 0.0;
@@ -527,20 +546,37 @@ int prop_estep(vbgs_ctx *ctx, int64_t N, bool last_iter)
         return fail(ctx, VBGS_ECUDA, "exact-row compaction failed");
     prop_gather_rows(X, P.erows, ne, P.Xe, ctx->stream);
     if ((rc = run_estep_on(ctx, P.Xe, ne, P.lse_e, true))) return rc;
-    prop_lse_combine(P.lse_c, P.lse_e, P.erows, ne, P.audit, ctx->stream);
+    const size_t aneed = prop_audit_floats(ne, ctx->K);
+    if (aneed > P.apart_cap) {
+        if ((rc = dalloc(ctx, &P.apart, aneed))) return rc;
+        P.apart_cap = aneed;
+    }
+    prop_audit(X, P.erows, ne, P.exact, P.lse_c, ctx->d_rec32, ctx->K, P.apart, P.audit, ctx->stream);
+    prop_lse_combine(P.lse_c, P.lse_e, P.erows, ne, ctx->stream);
     // candidate statistics of the proposal points, added to the exact ones
-    if (prop_cand_lists(P.cand, P.exact, N, ctx->sb, P.pkey, P.plist, P.pstart, ctx->stream))
+    if (prop_cand_lists(P.cand, P.exact, N, ctx->sb, P.pkey, P.plist, P.pstart, ctx->stream) ||
+        prop_cand_items(P.pstart, P.cstart, P.item_start, P.fbase, ctx->stream))
         return fail(ctx, VBGS_ECUDA, "candidate lists failed");
-    prop_cand_pass2(X, P.lse_c, ctx->d_rec32, P.order, P.cstart, P.pstart, P.plist, ctx->d_kperm, ctx->d_dS,
-                    ctx->stream);
+    int n_items = 0;
+    long long n_part = 0;
+    CU(cudaMemcpyAsync(&n_items, P.item_start + kPG, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(&n_part, P.fbase + kPG, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const size_t pneed = (size_t)n_part * VBGS_F;
+    if (pneed > P.part2_cap) {
+        if ((rc = dalloc(ctx, &P.part2, pneed + pneed / 4))) return rc;
+        P.part2_cap = pneed + pneed / 4;
+    }
+    prop_cand_pass2(X, P.lse_c, ctx->d_rec32, P.order, P.cstart, P.skey, ctx->K, P.pstart, P.plist, P.item_start,
+                    P.fbase, n_items, P.part2, ctx->d_kperm, ctx->d_dS, ctx->stream);
     // lse of every point and its fixed-order sum
     CU(cudaMemcpyAsync(ctx->d_lse, P.lse_c, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream));
     int nparts = 0;
     prop_sum_lse(P.lse_c, N, P.lsum, &nparts, ctx->stream);
     prop_sum_final(P.lsum, nparts, ctx->d_scal + SC_SUM_LSE, ctx->stream);
-    ctx->launches += 12;
+    ctx->launches += 15;
     if (last_iter) {
-        prop_label(ctx, P.Xe, P.lse_e, ne);
+        prop_label(ctx, P.Xe, P.lse_e, ne, P.erows);
         // true missed mass of the audit sample
         std::vector<int> rows((size_t)ne), ex((size_t)N);
         std::vector<float> miss((size_t)ne);
@@ -607,7 +643,7 @@ int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters)
     if (prop) {
         ctx->prop.frame_exact = false;
         ctx->prop.n_lab = 0;
-        if ((rc = prop_ensure_frame(ctx, N)) || (rc = prop_refresh(ctx)) ||
+        if ((rc = prop_ensure_frame(ctx, N)) || (rc = prop_refresh(ctx, false)) ||
             (rc = prop_propose(ctx, ctx->last_sorted ? ctx->d_Xs : ctx->d_X, N)))
             return rc;
     }
@@ -617,7 +653,7 @@ int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters)
             return fail(ctx, VBGS_ECUDA, "ELBO launch failed");
         ctx->launches += 1;
         if ((rc = run_mstep(ctx, ctx->d_dS))) return rc;
-        if (prop && it + 1 < n_iters && (rc = prop_refresh(ctx))) return rc;
+        if (prop && it + 1 < n_iters && (rc = prop_refresh(ctx, true))) return rc;
     }
     if (launch_commit(ctx->d_Spast, ctx->d_dS, ctx->K, ctx->d_flags, ctx->stream, &ctx->prof) < 0)
         return fail(ctx, VBGS_ECUDA, "commit launch failed");
@@ -641,9 +677,10 @@ void free_all(vbgs_ctx *ctx)
         if (p) cudaFree(p);
     {
         PropState &P = ctx->prop;
-        void *pp[] = {P.cent, P.kpts, P.cstat, P.order, P.cstart, P.skey, P.w, P.wq, P.am, P.av, P.grad, P.top, P.cand,
+        void *pp[] = {P.cent, P.kpts, P.cpar, P.cscr, P.mscr, P.ub, P.order, P.cstart, P.skey, P.w, P.wq, P.am, P.av, P.grad, P.top, P.cand,
                       P.exact, P.erows, P.plist, P.pstart, P.pkey, P.ekey, P.lse_c, P.Xe, P.lse_e, P.lsum, P.bound,
-                      P.audit, P.counters, P.Xin, P.Q, P.h1, P.h2, P.z, P.dz, P.dh2, P.dh1, P.loss};
+                      P.audit, P.counters, P.Xin, P.Q, P.h1, P.h2, P.z, P.dz, P.dh2, P.dh1, P.loss,
+                      P.item_start, P.fbase, P.part2, P.apart};
         for (void *p : pp)
             if (p) cudaFree(p);
     }
@@ -968,7 +1005,10 @@ extern "C" int vbgs_proposal_clusters(vbgs_ctx *ctx, float *centroids, int *clus
 {
     if (!ctx || !ctx->prop.on) return fail(ctx, VBGS_EINVAL, "the context has no proposal");
     int rc;
-    if ((rc = prop_refresh(ctx))) return rc;
+    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    if ((rc = ensure_capacity(ctx, 0)) || (rc = order_frame(ctx, 0, false)) || (rc = run_mstep(ctx, nullptr)) ||
+        (rc = prop_refresh(ctx, false)))
+        return rc;
     std::vector<int> order(ctx->K), cstart(kPG + 1), kperm(ctx->K);
     if (centroids) CU(cudaMemcpyAsync(centroids, ctx->prop.cent, sizeof(float) * kPG * 6, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaMemcpyAsync(order.data(), ctx->prop.order, sizeof(int) * ctx->K, cudaMemcpyDeviceToHost, ctx->stream));
@@ -979,6 +1019,33 @@ extern "C" int vbgs_proposal_clusters(vbgs_ctx *ctx, float *centroids, int *clus
         for (int g = 0; g < kPG; g++)
             for (int i = cstart[g]; i < cstart[g + 1]; i++) cluster_of[kperm[order[i]]] = g;
     return VBGS_OK;
+}
+
+extern "C" int vbgs_proposal_bounds(vbgs_ctx *ctx, const double *points, int64_t N, float *ub, int *cluster_of)
+{
+    if (!ctx || !ctx->prop.on) return fail(ctx, VBGS_EINVAL, "the context has no proposal");
+    if (N < 0 || (N > 0 && (!points || !ub))) return fail(ctx, VBGS_EINVAL, "vbgs_proposal_bounds: bad arguments");
+    PropState &P = ctx->prop;
+    int rc;
+    if ((rc = ensure_capacity(ctx, N)) || (rc = prop_ensure_frame(ctx, std::max<int64_t>(N, 1))) ||
+        (rc = stage_points(ctx, points, N)))
+        return rc;
+    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    if ((rc = order_frame(ctx, 0, false)) || (rc = run_mstep(ctx, nullptr)) || (rc = prop_refresh(ctx, false)))
+        return rc;
+    prop_bounds(ctx->d_X, N, P.cpar, P.ub, ctx->stream);
+    if (N > 0)
+        CU(cudaMemcpyAsync(ub, P.ub, sizeof(float) * (size_t)N * kPG, cudaMemcpyDeviceToHost, ctx->stream));
+    if (cluster_of) {
+        std::vector<int> order(ctx->K), cstart(kPG + 1), kperm(ctx->K);
+        CU(cudaMemcpyAsync(order.data(), P.order, sizeof(int) * ctx->K, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaMemcpyAsync(cstart.data(), P.cstart, sizeof(int) * (kPG + 1), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaMemcpyAsync(kperm.data(), ctx->d_kperm, sizeof(int) * ctx->K, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        for (int g = 0; g < kPG; g++)
+            for (int i = cstart[g]; i < cstart[g + 1]; i++) cluster_of[kperm[order[i]]] = g;
+    }
+    return check_flags(ctx);
 }
 
 int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_splits)

@@ -171,10 +171,15 @@ int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned
                     int *splits_out, cudaStream_t st, Prof *pf);
 
 // Learned proposal (vbgs_proposal.cu).
-int prop_set_attributes();
 int prop_launch_kmeans(const float *rec32, int K, float csc, float *pts, float *cent, SortBuffers &sb, int *order,
                        unsigned int *skey, int *cstart, int lloyd_iters, cudaStream_t st);
-int prop_launch_cluster_stats(const float *rec32, const int *order, const int *cstart, float *cstat, cudaStream_t st);
+int prop_launch_certificate(const double *rec, const float *rec32, const int *order, const unsigned int *skey,
+                            const int *cstart, int K, const double *Spast, const double *dS, const int *kperm,
+                            float xmax, float *cpar, double *cscr, float *mscr, cudaStream_t st);
+void prop_bounds(const double *X, int64_t N, const float *cpar, float *UB, cudaStream_t st);
+size_t prop_cpar_floats();
+size_t prop_cscr_doubles();
+size_t prop_mscr_floats(int K);
 void prop_gemm(int M, int N, int K, const float *A, int sam, int sak, const float *B, int sbk, int sbn, float *C,
                int ldc, const float *bias, bool relu, bool accumulate, cudaStream_t st);
 void prop_colsum(const float *X, int M, int Nc, float *out, cudaStream_t st);
@@ -184,17 +189,21 @@ void prop_adam(float *w, float *wq, float *m, float *v, const float *g, size_t n
 void prop_inputs(const double *X, const int *rows, int64_t rstride, int64_t n, const BoxParams &box, float *out,
                  cudaStream_t st);
 int prop_cand_pass1(const double *X, int64_t N, const float *rec32, const int *order, const int *cstart,
-                    const float *cstat, const int *top, float thresh, uint32_t seed, uint32_t audit_per_mille,
+                    const float *UB, const int *top, float thresh, uint32_t seed, uint32_t audit_per_mille,
                     double *lse_c, float *bound, int *exact, int *cand, unsigned long long *counters, cudaStream_t st);
 void prop_gather_rows(const double *X, const int *rows, int64_t n, double *Xe, cudaStream_t st);
 int prop_cand_lists(const int *cand, const int *exact, int64_t N, SortBuffers &sb, unsigned int *skey, int *plist,
                     int *pstart, cudaStream_t st);
+int prop_cand_items(const int *pstart, const int *cstart, int *item_start, long long *fbase, cudaStream_t st);
 void prop_cand_pass2(const double *X, const double *lse_c, const float *rec32, const int *order, const int *cstart,
-                     const int *pstart, const int *plist, const int *kperm, double *dS, cudaStream_t st);
-void prop_labels(const double *Xe, const double *lse_e, int64_t rstride, int64_t ne, const float *rec32,
-                 const int *order, const int *cstart, const float *cstat, float *Q, cudaStream_t st);
-void prop_lse_combine(double *lse_c, const double *lse_e, const int *erows, int64_t ne, float *audit_missed,
-                      cudaStream_t st);
+                     const unsigned int *skey, int K, const int *pstart, const int *plist, const int *item_start,
+                     const long long *fbase, int n_items, float *part, const int *kperm, double *dS, cudaStream_t st);
+void prop_labels(const double *Xe, const double *lse_e, const int *rows, int64_t rstride, int64_t ne,
+                 const float *rec32, const int *order, const int *cstart, const float *UB, float *Q, cudaStream_t st);
+size_t prop_audit_floats(int64_t ne, int K);
+void prop_audit(const double *X, const int *erows, int64_t ne, const int *exact, const double *lse_c,
+                const float *rec32, int K, float *scratch, float *audit_missed, cudaStream_t st);
+void prop_lse_combine(double *lse_c, const double *lse_e, const int *erows, int64_t ne, cudaStream_t st);
 void prop_sum_lse(const double *v, int64_t n, double *part, int *nparts, cudaStream_t st);
 void prop_add(double *a, const double *b, size_t n, cudaStream_t st);
 void prop_init_centroids(const float *rec32, int K, float csc, float *cent, cudaStream_t st);
@@ -208,7 +217,16 @@ struct PropState {
     bool on = false;
     bool centroids_ready = false;
     // clusters (k-means of the posterior means, at record positions)
-    float *cent = nullptr, *kpts = nullptr, *cstat = nullptr;
+    float *cent = nullptr, *kpts = nullptr;
+    // certificate: per-cluster centre, metric and bound tables; FP64 scratch
+    // of the cluster metrics; per-member bound terms; bounds of the frame
+    float *cpar = nullptr, *mscr = nullptr, *ub = nullptr;
+    double *cscr = nullptr;
+    // candidate pass-2 work items and partials; audit partials
+    int *item_start = nullptr;
+    long long *fbase = nullptr;
+    float *part2 = nullptr, *apart = nullptr;
+    size_t part2_cap = 0, apart_cap = 0;
     int *order = nullptr, *cstart = nullptr;
     unsigned int *skey = nullptr;
     // network: [W1 128x6 | b1 128 | W2 128x128 | b2 128 | W3 1024x128 | b3 1024]

@@ -4,18 +4,19 @@
 // negligible.  A small MLP over the point (x, y, z, r, g, b) proposes the 4
 // most likely of G = 1024 component clusters (k-means of the posterior means,
 // refreshed after every posterior update); the E-step then scores only the
-// components of those clusters.  A certificate bounds, per point, the mass the
-// other clusters can hold:
-//   for a cluster g with constant cmax_g = max_k c_k, precision lower bound
-//   lmin_g = min_k nu_k / tr(W_k^-1) <= lambda_min(nu_k W_k) and bounding box
-//   of the means bbox_g, every logit of g is <= cmax_g - lmin_g/2 d^2(x, bbox_g),
-//   so the missed mass is <= sum_{g not proposed} |g| 2^(ub_g - lse2_cand).
-// Points whose bound exceeds 1e-3 (and a seeded 1% audit sample) run the exact
-// E-step over all components; the audit also measures the true missed mass.
+// components of those clusters.  A certificate bounds, per point and cluster,
+// the mass sum_{k in g} exp(l_nk) (tables of per-member bounds, below); the
+// candidate pass adds the cluster with the largest bound while the bound mass
+// of the other clusters exceeds 1e-3 of the candidates' mass, up to 32
+// clusters.  Points still above 1e-3 (and a seeded 1% audit sample) run the
+// exact E-step over all components; the audit also scores all components in
+// the candidates' FP32 arithmetic to measure the true missed mass.
 // The MLP is trained on the GPU by the kernels below (forward, backward, Adam)
 // on the cluster masses q_ng = sum_{k in g} r_nk of the exact E-steps.
 //
-// All logits here are in log2 units (FP32 records: c and M scaled by log2 e).
+// All logits here are in log2 units (FP32 records: c and M scaled by log2 e),
+// and, like every E-step logit of the library, without the -psi(sum alpha)
+// term shared by all components (it cancels in every ratio used here).
 #include "vbgs_internal.cuh"
 #include <cub/device/device_radix_sort.cuh>
 #include <algorithm>
@@ -50,24 +51,6 @@ __device__ __forceinline__ float logit32(const float *__restrict__ r, const floa
         q = fmaf(y, y, q);
     }
     return fmaf(-0.5f, q, r[27]);
-}
-
-// Certificate terms of a cluster (kCS floats): [0] cmax, [1] lp, [2..7] box
-// low, [8..13] box high, [14] size, [15] lc, [16] la; log2 units.
-constexpr int kCS = 20;
-
-// Upper bound of every logit of a cluster at point x.
-__device__ __forceinline__ float cluster_ub(const float *__restrict__ c, const float x[6])
-{
-    float dp = 0.f, dc = 0.f;
-#pragma unroll
-    for (int q = 0; q < 3; q++) {
-        const float o = fmaxf(fmaxf(c[2 + q] - x[q], x[q] - c[8 + q]), 0.f);
-        dp = fmaf(o, o, dp);
-        const float oc = fmaxf(fmaxf(c[5 + q] - x[3 + q], x[3 + q] - c[11 + q]), 0.f);
-        dc = fmaf(oc, oc, dc);
-    }
-    return c[0] - 0.5f * fmaxf(fmaxf(c[1] * dp, c[15] * dc), c[16] * (dp + dc));
 }
 
 // ---------------------------------------------------------------- k-means ----
@@ -141,47 +124,358 @@ __global__ void __launch_bounds__(128) k_centroids(const float *__restrict__ pts
     if (t < 6 && e > b) cent[g * 6 + t] = ((sh[t][0] + sh[t][1]) + (sh[t][2] + sh[t][3])) / (float)(e - b);
 }
 
-// Certificate terms of every cluster (layout of cluster_ub).  The FP32
-// record holds the per-component bounds lp at [28], lc at [29], la at [30].
-__global__ void __launch_bounds__(128) k_cluster_stats(const float *__restrict__ rec32,
-                                                       const int *__restrict__ order, const int *__restrict__ cstart,
-                                                       float *__restrict__ cstat)
+// ------------------------------------------------------- certificate -----
+// The logit of component k is l_k(x) = c_k - 1/2 (x - m_k)^T Lam_k (x - m_k).
+// Four lower bounds of the quadratic form, each a scale times a squared norm:
+//   metric:   mu_k |L^T (x - m_k)|^2 with P = L L^T the cluster's metric and
+//             mu_k = lambda_min(L^-1 Lam_k L^-T);
+//   position: lp_k |x_p - m_p|^2 (lp_k: smallest eigenvalue of the position
+//             block's Schur complement, i.e. of the marginal precision);
+//   colour:   lc_k |x_c - m_c|^2;
+//   joint:    la_k |x - m|^2 (la_k = lambda_min(Lam_k)).
+// With the triangle inequality |x - m_k| >= |x - o| - |m_k - o| in the same
+// norm around the cluster centre o, every kind q gives
+//   sum_{k in g} exp(l_k(x)) <= T_q(d_q) = sum_k exp(c_k - 1/2 mu_qk (d_q - r_qk)_+^2),
+// d_q the distance of x to o and r_qk that of m_k; T_q does not increase
+// with d_q.  Each T_q is tabulated (log2 units) at kTJ - 1 grid points and
+// at d_last = r_max + sqrt(2 span / mu_min); beyond d_last the tail
+//   T_q(d) <= T_q(d_last) - 1/2 mu_min (d - d_last)(d + d_last - 2 r_max)
+// holds because every term decays at least that fast once d >= r_max.  The
+// bound of a cluster at x is the smallest of the four table look-ups.
+constexpr int kTJ = 16;                   // table points per kind
+constexpr int kKind = 4;                  // metric, position, colour, joint
+constexpr int kKS = kTJ + 5;              // T[kTJ], 1/h, d_last, tail slope, r_max, eps
+constexpr int kCP = 28 + kKind * kKS;     // [0..5] centre, [6..26] L (lower), [27] metric valid
+constexpr int kMS = 9;                    // per member: c (log2), mu[4], r[4]
+constexpr int kCScr = 28;                 // per cluster FP64: centre, L, valid
+constexpr double kSpanNats = 30.0;
+static_assert(kCP % 4 == 0, "cluster records are staged as float4");
+
+// Upper bound of the largest eigenvalue of a symmetric positive definite 6 x 6
+// matrix (lower triangle, tri order): with B = S / tr(S),
+// lambda_max(B)^8 <= |B^8|_F, which overestimates by at most 6^(1/16).
+__device__ double lmax_bound6(const double *S)
 {
-    __shared__ float sh[16][4];
+    double B[36], C[36];
+    double t = 0.0;
+    for (int i = 0; i < 6; i++) t += S[tri(i, i)];
+    if (!(t > 0.0)) return INFINITY;
+    const double it = 1.0 / t;
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j <= i; j++) B[i * 6 + j] = B[j * 6 + i] = S[tri(i, j)] * it;
+    for (int rep = 0; rep < 3; rep++) {   // B <- B^2, three times: B^8
+        for (int i = 0; i < 6; i++)
+            for (int j = 0; j <= i; j++) {
+                double v = 0.0;
+                for (int l = 0; l < 6; l++) v = fma(B[i * 6 + l], B[l * 6 + j], v);
+                C[i * 6 + j] = C[j * 6 + i] = v;
+            }
+        for (int i = 0; i < 36; i++) B[i] = C[i];
+    }
+    double f = 0.0;
+    for (int i = 0; i < 36; i++) f = fma(B[i], B[i], f);
+    return t * pow(sqrt(f), 0.125) * (1.0 + 1e-9);
+}
+
+// Cluster centre and metric: o = mean of the member means, P = the average
+// member precision weighted by N_k + 1e-3, L = chol(P) rounded to FP32.
+__global__ void __launch_bounds__(64) k_cluster_metric(const double *__restrict__ rec, const int *__restrict__ order,
+                                                       const int *__restrict__ cstart,
+                                                       const double *__restrict__ Spast,
+                                                       const double *__restrict__ dS, const int *__restrict__ kperm,
+                                                       float *__restrict__ cpar, double *__restrict__ cscr)
+{
+    __shared__ double sh[28][2];
     const int g = blockIdx.x, t = threadIdx.x;
     const int b = cstart[g], e = cstart[g + 1];
-    float cm = -INFINITY, lm = INFINITY, lc = INFINITY, la = INFINITY, lo[6], hi[6];
+    double acc[28];
 #pragma unroll
-    for (int q = 0; q < 6; q++) { lo[q] = INFINITY; hi[q] = -INFINITY; }
-    for (int i = b + t; i < e; i += blockDim.x) {
-        const float *r = rec32 + (size_t)order[i] * VBGS_REC;
-        cm = fmaxf(cm, r[27]);
-        lm = fminf(lm, r[28]);
-        lc = fminf(lc, r[29]);
-        la = fminf(la, r[30]);
+    for (int q = 0; q < 28; q++) acc[q] = 0.0;
+    for (int i = b + t; i < e; i += 64) {
+        const int p = order[i];
+        const double *r = rec + (size_t)p * VBGS_REC;
+        const int k = kperm[p];
+        const double w = Spast[(size_t)k * VBGS_F] + (dS ? dS[(size_t)k * VBGS_F] : 0.0) + 1e-3;
 #pragma unroll
-        for (int q = 0; q < 6; q++) { lo[q] = fminf(lo[q], r[q]); hi[q] = fmaxf(hi[q], r[q]); }
+        for (int q = 0; q < 6; q++) acc[q] += r[q];
+        // Lam = M^T M with M lower triangular (tri order at r + 6)
+#pragma unroll
+        for (int a = 0; a < 6; a++)
+#pragma unroll
+            for (int c = 0; c <= a; c++) {
+                double v = 0.0;
+#pragma unroll
+                for (int l = a; l < 6; l++) v = fma(r[6 + tri(l, a)], r[6 + tri(l, c)], v);
+                acc[6 + tri(a, c)] = fma(w, v, acc[6 + tri(a, c)]);
+            }
+        acc[27] += w;
     }
-    float v[16] = {cm, lm, lo[0], lo[1], lo[2], lo[3], lo[4], lo[5], hi[0], hi[1], hi[2], hi[3], hi[4], hi[5], lc, la};
 #pragma unroll
-    for (int q = 0; q < 16; q++) {
-        float x = v[q];
-        const bool mx = (q == 0) || (q >= 8 && q < 14);
+    for (int q = 0; q < 28; q++) {
+        double v = acc[q];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float y = __shfl_xor_sync(0xffffffffu, x, o);
-            x = mx ? fmaxf(x, y) : fminf(x, y);
-        }
-        if ((t & 31) == 0) sh[q][t >> 5] = x;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((t & 31) == 0) sh[q][t >> 5] = v;
     }
     __syncthreads();
-    if (t < 16) {
-        const bool mx = (t == 0) || (t >= 8 && t < 14);
-        float x = sh[t][0];
-        for (int w = 1; w < 4; w++) x = mx ? fmaxf(x, sh[t][w]) : fminf(x, sh[t][w]);
-        cstat[g * kCS + (t < 14 ? t : t + 1)] = x;   // lc -> [15], la -> [16]
+    if (t != 0) return;
+    float *cp = cpar + (size_t)g * kCP;
+    double *cs = cscr + (size_t)g * kCScr;
+    const int n = e - b;
+    double L[21];
+    bool ok = n > 0;
+    double o[6];
+    for (int q = 0; q < 6; q++) o[q] = n > 0 ? (sh[q][0] + sh[q][1]) / n : 0.0;
+    if (ok) {
+        const double iw = 1.0 / (sh[27][0] + sh[27][1]);
+        for (int q = 0; q < 21; q++) L[q] = (sh[6 + q][0] + sh[6 + q][1]) * iw;
+        // in-place Cholesky of P (lower, tri order)
+        for (int j = 0; j < 6 && ok; j++) {
+            double d = L[tri(j, j)];
+            for (int l = 0; l < j; l++) d -= L[tri(j, l)] * L[tri(j, l)];
+            if (!(d > 0.0)) { ok = false; break; }
+            d = sqrt(d);
+            L[tri(j, j)] = d;
+            for (int i = j + 1; i < 6; i++) {
+                double v = L[tri(i, j)];
+                for (int l = 0; l < j; l++) v -= L[tri(i, l)] * L[tri(j, l)];
+                L[tri(i, j)] = v / d;
+            }
+        }
     }
-    if (t == 16) cstat[g * kCS + 14] = (float)(e - b);
+    for (int q = 0; q < 6; q++) {
+        const float of = (float)o[q];
+        cp[q] = of;
+        cs[q] = (double)of;
+    }
+    for (int q = 0; q < 21; q++) {
+        const float lf = ok ? (float)L[q] : 0.f;
+        cp[6 + q] = lf;
+        cs[6 + q] = (double)lf;
+    }
+    cp[27] = ok ? 1.f : 0.f;
+    cs[27] = ok ? 1.0 : 0.0;
+}
+
+__device__ __forceinline__ float f_up(double v)
+{
+    float f = (float)v;
+    if ((double)f < v) f = nextafterf(f, INFINITY);
+    return f;
+}
+__device__ __forceinline__ float f_down(double v)
+{
+    float f = (float)v;
+    if ((double)f > v) f = nextafterf(f, -INFINITY);
+    return f;
+}
+
+// Per member (sorted position i): constant (log2, rounded up), the four
+// scales mu (rounded down) and the four radii r (rounded up).
+__global__ void __launch_bounds__(128) k_cluster_members(const double *__restrict__ rec,
+                                                         const float *__restrict__ rec32,
+                                                         const int *__restrict__ order,
+                                                         const unsigned int *__restrict__ skey, int K,
+                                                         const double *__restrict__ cscr, float *__restrict__ mscr)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    const int p = order[i];
+    const int g = (int)skey[i];
+    const double *r = rec + (size_t)p * VBGS_REC;
+    const double *cs = cscr + (size_t)g * kCScr;
+    double M[21], Mi[21];
+    for (int q = 0; q < 21; q++) M[q] = r[6 + q];
+    // inverse of the lower-triangular M
+    for (int j = 0; j < 6; j++) {
+        Mi[tri(j, j)] = 1.0 / M[tri(j, j)];
+        for (int a = j + 1; a < 6; a++) {
+            double v = 0.0;
+            for (int l = j; l < a; l++) v = fma(M[tri(a, l)], Mi[tri(l, j)], v);
+            Mi[tri(a, j)] = -v / M[tri(a, a)];
+        }
+    }
+    // covariance Sigma = Lam^-1 = Mi Mi^T
+    double Sg[21];
+    for (int a = 0; a < 6; a++)
+        for (int c = 0; c <= a; c++) {
+            double v = 0.0;
+            for (int l = 0; l <= c; l++) v = fma(Mi[tri(a, l)], Mi[tri(c, l)], v);
+            Sg[tri(a, c)] = v;
+        }
+    const double la = 1.0 / lmax_bound6(Sg);
+    // metric kind: lambda_min(L^-1 Lam L^-T) = 1 / lambda_max(L^T Sigma L)
+    double mu_m = 0.0;
+    const double *L = cs + 6;
+    if (cs[27] != 0.0) {
+        double Z[36];   // Sigma L
+        for (int a = 0; a < 6; a++)
+            for (int c = 0; c < 6; c++) {
+                double v = 0.0;
+                for (int l = c; l < 6; l++) v = fma(Sg[a >= l ? tri(a, l) : tri(l, a)], L[tri(l, c)], v);
+                Z[a * 6 + c] = v;
+            }
+        double A[21];   // L^T Sigma L
+        for (int a = 0; a < 6; a++)
+            for (int c = 0; c <= a; c++) {
+                double v = 0.0;
+                for (int l = a; l < 6; l++) v = fma(L[tri(l, a)], Z[l * 6 + c], v);
+                A[tri(a, c)] = v;
+            }
+        mu_m = 1.0 / lmax_bound6(A);
+    }
+    const double lp = (double)rec32[(size_t)p * VBGS_REC + 28] * 0.6931471805599453 * (1.0 - 1e-6);
+    const double lc = (double)rec32[(size_t)p * VBGS_REC + 29] * 0.6931471805599453 * (1.0 - 1e-6);
+    double dx[6], rp = 0.0, rc = 0.0, rm = 0.0;
+    for (int q = 0; q < 6; q++) dx[q] = r[q] - cs[q];
+    for (int q = 0; q < 3; q++) { rp = fma(dx[q], dx[q], rp); rc = fma(dx[3 + q], dx[3 + q], rc); }
+    for (int c = 0; c < 6; c++) {
+        double y = 0.0;
+        for (int a = c; a < 6; a++) y = fma(L[tri(a, c)], dx[a], y);
+        rm = fma(y, y, rm);
+    }
+    float *ms = mscr + (size_t)i * kMS;
+    ms[0] = f_up(r[27] * 1.4426950408889634);
+    ms[1] = f_down(fmax(mu_m * (1.0 - 1e-9), 0.0));
+    ms[2] = f_down(fmax(lp, 0.0));
+    ms[3] = f_down(fmax(lc, 0.0));
+    ms[4] = f_down(fmax(la * (1.0 - 1e-9), 0.0));
+    ms[5] = f_up(sqrt(rm) * (1.0 + 1e-12));
+    ms[6] = f_up(sqrt(rp) * (1.0 + 1e-12));
+    ms[7] = f_up(sqrt(rc) * (1.0 + 1e-12));
+    ms[8] = f_up(sqrt(rp + rc) * (1.0 + 1e-12));
+}
+
+// The tables: one block per cluster, thread (q, j) = (kind, table point).
+__global__ void __launch_bounds__(64) k_cluster_tables(const float *__restrict__ mscr, const int *__restrict__ cstart,
+                                                       float xmax, float *__restrict__ cpar)
+{
+    const int g = blockIdx.x, t = threadIdx.x, q = t >> 4, j = t & 15;
+    const int b = cstart[g], e = cstart[g + 1];
+    float *cp = cpar + (size_t)g * kCP;
+    float *tq = cp + 28 + q * kKS;
+    if (e == b) {
+        tq[j] = -INFINITY;
+        if (j == 0) { tq[kTJ] = 0.f; tq[kTJ + 1] = INFINITY; tq[kTJ + 2] = 0.f; tq[kTJ + 3] = 0.f; tq[kTJ + 4] = 0.f; }
+        return;
+    }
+    float rmax = 0.f, mumin = INFINITY;
+    for (int i = b + j; i < e; i += kTJ) {
+        rmax = fmaxf(rmax, mscr[(size_t)i * kMS + 5 + q]);
+        mumin = fminf(mumin, mscr[(size_t)i * kMS + 1 + q]);
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        mumin = fminf(mumin, __shfl_xor_sync(0xffffffffu, mumin, o));
+    }
+    float dl = INFINITY, inv_h = 0.f;
+    double hd = 0.0;
+    if (mumin > 0.f) {
+        dl = f_down((double)rmax + sqrt(2.0 * kSpanNats / (double)mumin));
+        inv_h = f_down((double)(kTJ - 1) / (double)dl);
+        hd = 1.0 / (double)inv_h;
+    }
+    const float dj = (j < kTJ - 1) ? f_down((double)j * hd) : (mumin > 0.f ? dl : 0.f);
+    const float hmu = 0.72134752044448170f;   // log2(e) / 2
+    float mx = -INFINITY;
+    for (int i = b; i < e; i++) {
+        const float *ms = mscr + (size_t)i * kMS;
+        const float dd = fmaxf(dj - ms[5 + q], 0.f);
+        mx = fmaxf(mx, ms[0] - hmu * ms[1 + q] * dd * dd);
+    }
+    float s = 0.f;
+    for (int i = b; i < e; i++) {
+        const float *ms = mscr + (size_t)i * kMS;
+        const float dd = fmaxf(dj - ms[5 + q], 0.f);
+        s += exp2f(ms[0] - hmu * ms[1 + q] * dd * dd - mx);
+    }
+    // FP32 rounding of the terms and of the sum: a margin of 1e-3 + 1e-6 |T|
+    const float T = mx + log2f(s);
+    tq[j] = T + 1e-3f + 1e-6f * fabsf(T);
+    if (j == 0) {
+        float lf = 1.f;
+        if (q == 0) {
+            float f2 = 0.f;
+            for (int a = 0; a < 21; a++) f2 = fmaf(cp[6 + a], cp[6 + a], f2);
+            lf = sqrtf(f2);
+        }
+        tq[kTJ] = inv_h;
+        tq[kTJ + 1] = dl;
+        tq[kTJ + 2] = hmu * mumin * (1.f - 1e-6f);
+        tq[kTJ + 3] = rmax;
+        // rounding of the point, the centre and the distance in FP32
+        tq[kTJ + 4] = 1e-6f * (rmax + (mumin > 0.f ? dl : 0.f)) + 1e-6f * lf * xmax;
+    }
+}
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Table look-up of one kind at distance d (log2 units).  The 1e-5 relative
+// shrink of d covers the error of the approximate square roots.
+__device__ __forceinline__ float table_bound(const float *__restrict__ tq, float d)
+{
+    d = fmaxf(fmaf(d, 1.f - 1e-5f, -tq[kTJ + 4]), 0.f);
+    const float dl = tq[kTJ + 1];
+    if (d >= dl) return tq[kTJ - 1] - tq[kTJ + 2] * (d - dl) * (d + dl - 2.f * tq[kTJ + 3]);
+    const int j = min((int)(d * tq[kTJ] * 0.999999f), kTJ - 2);
+    return tq[j];
+}
+
+// Bound of every cluster at every point: UB[n][g] (log2 units), one thread
+// per point, clusters staged through shared memory kBC at a time; blockIdx.y
+// selects one of kBG groups of clusters (more CTAs in flight).
+constexpr int kBC = 16;
+constexpr int kBG = 4;
+__global__ void __launch_bounds__(128) k_bounds(const double *__restrict__ X, int64_t N,
+                                                const float *__restrict__ cpar, float *__restrict__ UB)
+{
+    __shared__ __align__(16) float sp[kBC * kCP];
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = n < N;
+    float x[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) x[i] = live ? (float)X[n * VBGS_XS + i] : 0.f;
+    const int gb = blockIdx.y * (kG / kBG), ge = gb + kG / kBG;
+    for (int g0 = gb; g0 < ge; g0 += kBC) {
+        __syncthreads();
+        const float4 *src = reinterpret_cast<const float4 *>(cpar + (size_t)g0 * kCP);
+        for (int i = threadIdx.x; i < kBC * kCP / 4; i += blockDim.x) reinterpret_cast<float4 *>(sp)[i] = src[i];
+        __syncthreads();
+        float out[kBC];
+#pragma unroll
+        for (int c = 0; c < kBC; c++) {
+            const float *cp = sp + c * kCP;
+            float dx[6];
+#pragma unroll
+            for (int i = 0; i < 6; i++) dx[i] = x[i] - cp[i];
+            const float dp2 = fmaf(dx[0], dx[0], fmaf(dx[1], dx[1], dx[2] * dx[2]));
+            const float dc2 = fmaf(dx[3], dx[3], fmaf(dx[4], dx[4], dx[5] * dx[5]));
+            float dm2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < 6; a++) {
+                float y = 0.f;
+#pragma unroll
+                for (int l = a; l < 6; l++) y = fmaf(cp[6 + tri(l, a)], dx[l], y);
+                dm2 = fmaf(y, y, dm2);
+            }
+            const float b0 = table_bound(cp + 28, sqrt_approx(dm2));
+            const float b1 = table_bound(cp + 28 + kKS, sqrt_approx(dp2));
+            const float b2 = table_bound(cp + 28 + 2 * kKS, sqrt_approx(dc2));
+            const float b3 = table_bound(cp + 28 + 3 * kKS, sqrt_approx(dp2 + dc2));
+            out[c] = fminf(fminf(b0, b1), fminf(b2, b3));
+        }
+        if (live) {
+            float4 *dst = reinterpret_cast<float4 *>(UB + n * kG + g0);
+#pragma unroll
+            for (int c = 0; c < kBC / 4; c++) dst[c] = make_float4(out[4 * c], out[4 * c + 1], out[4 * c + 2], out[4 * c + 3]);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ MLP -----
@@ -399,87 +693,66 @@ __device__ __forceinline__ float warp_max(float v)
 
 __global__ void __launch_bounds__(256) k_cand_pass1(const double *__restrict__ X, int64_t N,
                                                     const float *__restrict__ rec32, const int *__restrict__ order,
-                                                    const int *__restrict__ cstart, const float *__restrict__ cstat,
+                                                    const int *__restrict__ cstart, const float *__restrict__ UB,
                                                     const int *__restrict__ top, float thresh, uint32_t audit_seed,
                                                     uint32_t audit_per_mille, double *__restrict__ lse_c,
                                                     float *__restrict__ bound, int *__restrict__ exact,
                                                     int *__restrict__ cand, unsigned long long *__restrict__ counters)
 {
-    extern __shared__ float scs[];   // kG x kCS cluster certificate terms (80 KB)
-    for (int i = threadIdx.x; i < kG * kCS; i += blockDim.x) scs[i] = cstat[i];
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (n >= N) return;
     float x[6];
 #pragma unroll
     for (int i = 0; i < 6; i++) x[i] = (float)X[n * VBGS_XS + i];
-    // lane l owns the membership bits of clusters 32 l .. 32 l + 31
+    // lane l holds the bounds and the membership bits of clusters 32 j + l
+    float u[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) u[j] = UB[n * kG + j * 32 + lane];
     uint32_t mine = 0u;
     int nc = 0;
     float mx = -INFINITY, s = 0.f;
     unsigned long long pairs = 0;
     for (int t = 0; t < kTop; t++) {
         const int g = top[n * kTop + t];
-        if ((g >> 5) == lane) mine |= 1u << (g & 31);
+        if ((g & 31) == lane) mine |= 1u << (g >> 5);
         if (lane == 0) cand[n * kMaxCand + nc] = g;
         nc++;
         pairs += (unsigned long long)(cstart[g + 1] - cstart[g]);
         warp_score_cluster(rec32, order, cstart[g], cstart[g + 1], x, lane, mx, s);
     }
-    // bound term of the non-candidate clusters of this lane
-    auto lane_terms = [&](float l2, float &sum, float &best) {
-        sum = 0.f;
-        best = 0.f;
-        for (int j = 0; j < 32; j++) {
-            const int g = lane * 32 + j;
-            if (mine & (1u << j)) continue;
-            const float *c = scs + g * kCS;
-            if (c[14] == 0.f) continue;
-            const float b = c[14] * ex2a(fminf(cluster_ub(c, x) - l2, 64.f));
-            sum += b;
-            best = fmaxf(best, b);
-        }
-    };
+    // Greedy expansion: while the bound mass of the non-candidate clusters,
+    // relative to the candidates' lse, exceeds the threshold, add the cluster
+    // with the largest bound (ties to the lower index) and score it exactly.
     float mm = 0.f;
-    for (int round = 0; round < 8; round++) {
+    for (;;) {
         const float l2 = warp_l2(mx, s);
-        float ls, lb;
-        lane_terms(l2, ls, lb);
-        mm = warp_sum(ls);
-        const float best = warp_max(lb);
-        if (mm <= thresh || nc == kMaxCand) break;
-        // add every cluster whose term is within 4x of the largest, in index
-        // order, up to the free slots
-        const float tau = fmaxf(0.25f * best, thresh * (1.f / 64.f));
-        uint32_t add = 0u;
+        float ls = 0.f, lb = -INFINITY;
+        int lj = -1;
+#pragma unroll
         for (int j = 0; j < 32; j++) {
-            const int g = lane * 32 + j;
             if (mine & (1u << j)) continue;
-            const float *c = scs + g * kCS;
-            if (c[14] == 0.f) continue;
-            if (c[14] * ex2a(fminf(cluster_ub(c, x) - l2, 64.f)) >= tau) add |= 1u << j;
+            ls += ex2a(fminf(u[j] - l2, 64.f));
+            if (u[j] > lb) { lb = u[j]; lj = j; }
         }
-        for (int l = 0; l < 32 && nc < kMaxCand; l++) {
-            uint32_t a = __shfl_sync(0xffffffffu, add, l);
-            while (a && nc < kMaxCand) {
-                const int j = __ffs(a) - 1;
-                a &= a - 1;
-                const int g = l * 32 + j;
-                if (lane == l) mine |= 1u << j;
-                if (lane == 0) cand[n * kMaxCand + nc] = g;
-                nc++;
-                pairs += (unsigned long long)(cstart[g + 1] - cstart[g]);
-                warp_score_cluster(rec32, order, cstart[g], cstart[g + 1], x, lane, mx, s);
-            }
+        mm = warp_sum(ls);
+        if (mm <= thresh || nc == kMaxCand) break;
+        int bg = lj >= 0 ? lj * 32 + lane : 0x7fffffff;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, lb, o);
+            const int og = __shfl_xor_sync(0xffffffffu, bg, o);
+            if (ov > lb || (ov == lb && og < bg)) { lb = ov; bg = og; }
         }
+        if (bg == 0x7fffffff || lb == -INFINITY) break;   // every remaining cluster is empty
+        const int g = bg;
+        if (lane == (g & 31)) mine |= 1u << (g >> 5);
+        if (lane == 0) cand[n * kMaxCand + nc] = g;
+        nc++;
+        pairs += (unsigned long long)(cstart[g + 1] - cstart[g]);
+        warp_score_cluster(rec32, order, cstart[g], cstart[g + 1], x, lane, mx, s);
     }
     const float l2 = warp_l2(mx, s);
-    {
-        float ls, lb;
-        lane_terms(l2, ls, lb);
-        mm = warp_sum(ls);
-    }
     if (lane == 0) {
         for (int i = nc; i < kMaxCand; i++) cand[n * kMaxCand + i] = -1;
         bound[n] = mm;
@@ -519,70 +792,145 @@ __global__ void k_cand_keys(const int *__restrict__ cand, const int *__restrict_
     val[i] = (int)n;
 }
 
-// Candidate pass 2: one CTA per cluster, one thread per member component;
-// the cluster's proposal points stream through shared memory and each thread
-// accumulates r [1, d, upper(d d^T)] about its component's mean (FP32), then
-// writes the moments shifted to raw (FP64) at the component's position.
-__global__ void __launch_bounds__(128) k_cand_pass2(const double *__restrict__ X, const double *__restrict__ lse_c,
-                                                    const float *__restrict__ rec32, const int *__restrict__ order,
-                                                    const int *__restrict__ cstart, const int *__restrict__ pstart,
-                                                    const int *__restrict__ plist, const int *__restrict__ kperm,
-                                                    double *__restrict__ dS)
+// Candidate pass 2.  Work items are (cluster, chunk of up to kPB of the
+// cluster's proposal points); item_start[g] and the partial base fbase[g]
+// come from one scan over the clusters.  An item's CTA stages its points in
+// shared memory; each thread owns a member component and accumulates
+// r [1, d, upper(d d^T)] about the component's mean (FP32) over the chunk,
+// written as the item's partial.  A second kernel sums a member's partials
+// in item order (FP64, deterministic), shifts them to raw moments and adds
+// them to the component's frame statistics.
+constexpr int kPB = 128;
+
+__global__ void __launch_bounds__(1024) k_items(const int *__restrict__ pstart, const int *__restrict__ cstart,
+                                                int *__restrict__ item_start, long long *__restrict__ fbase)
 {
-    __shared__ float sp[64][8];
-    const int g = blockIdx.x;
-    const int b = cstart[g], e = cstart[g + 1];
-    const int pb = pstart[g], pe = pstart[g + 1];
-    for (int m0 = b; m0 < e; m0 += blockDim.x) {
-        const int mi = m0 + threadIdx.x;
-        const bool valid = mi < e;
-        const int pos = valid ? order[mi] : order[b];
+    __shared__ long long sa[kG], sb[kG];
+    const int g = threadIdx.x;
+    const int cnt = pstart[g + 1] - pstart[g];
+    const int S = cstart[g + 1] - cstart[g];
+    const long long items = S > 0 ? (cnt + kPB - 1) / kPB : 0;
+    sa[g] = items;
+    sb[g] = items * S;
+    __syncthreads();
+    // inclusive Hillis-Steele scans of both columns
+    for (int o = 1; o < kG; o <<= 1) {
+        const long long a = g >= o ? sa[g - o] : 0, b = g >= o ? sb[g - o] : 0;
+        __syncthreads();
+        sa[g] += a;
+        sb[g] += b;
+        __syncthreads();
+    }
+    item_start[g + 1] = (int)sa[g];
+    fbase[g + 1] = sb[g];
+    if (g == 0) { item_start[0] = 0; fbase[0] = 0; }
+}
+
+__global__ void __launch_bounds__(64) k_cand_pass2(const double *__restrict__ X, const double *__restrict__ lse_c,
+                                                   const float *__restrict__ rec32, const int *__restrict__ order,
+                                                   const int *__restrict__ cstart, const int *__restrict__ pstart,
+                                                   const int *__restrict__ plist, const int *__restrict__ item_start,
+                                                   const long long *__restrict__ fbase, float *__restrict__ part)
+{
+    __shared__ float sp[kPB][8];
+    __shared__ int sg;
+    const int item = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = kG;   // largest g with item_start[g] <= item
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (item_start[mid] <= item) lo = mid; else hi = mid;
+        }
+        sg = lo;
+    }
+    __syncthreads();
+    const int g = sg;
+    const int c = item - item_start[g];
+    const int b = cstart[g], S = cstart[g + 1] - b;
+    const int p0 = pstart[g] + c * kPB, cnt = min(kPB, pstart[g + 1] - p0);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int n = plist[p0 + t];
+#pragma unroll
+        for (int q = 0; q < 6; q++) sp[t][q] = (float)X[(int64_t)n * VBGS_XS + q];
+        sp[t][6] = (float)(lse_c[n] * 1.4426950408889634);
+    }
+    __syncthreads();
+    for (int m0 = 0; m0 < S; m0 += blockDim.x) {
+        const int ml = m0 + threadIdx.x;
+        if (ml >= S) break;
+        const int pos = order[b + ml];
         float r[28];
 #pragma unroll
         for (int i = 0; i < 28; i++) r[i] = rec32[(size_t)pos * VBGS_REC + i];
         float acc[28];
 #pragma unroll
         for (int f = 0; f < 28; f++) acc[f] = 0.f;
-        for (int p0 = pb; p0 < pe; p0 += 64) {
-            const int cnt = min(64, pe - p0);
-            __syncthreads();
-            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-                const int n = plist[p0 + t];
+        for (int t = 0; t < cnt; t++) {
+            float x[6];
 #pragma unroll
-                for (int q = 0; q < 6; q++) sp[t][q] = (float)X[(int64_t)n * VBGS_XS + q];
-                sp[t][6] = (float)(lse_c[n] * 1.4426950408889634);
-            }
-            __syncthreads();
-            for (int t = 0; t < cnt; t++) {
-                float x[6];
+            for (int q = 0; q < 6; q++) x[q] = sp[t][q];
+            const float w = ex2a(logit32(r, x) - sp[t][6]);
+            acc[0] += w;
+            float d[6], wd[6];
 #pragma unroll
-                for (int q = 0; q < 6; q++) x[q] = sp[t][q];
-                const float w = ex2a(logit32(r, x) - sp[t][6]);
-                acc[0] += w;
-                float d[6], wd[6];
-#pragma unroll
-                for (int q = 0; q < 6; q++) { d[q] = x[q] - r[q]; wd[q] = w * d[q]; acc[1 + q] += wd[q]; }
-                int u = 7;
-#pragma unroll
-                for (int i = 0; i < 6; i++)
-#pragma unroll
-                    for (int j = i; j < 6; j++, u++) acc[u] = fmaf(wd[i], d[j], acc[u]);
-            }
-        }
-        if (valid) {
-            double s[28], a[6];
-#pragma unroll
-            for (int f = 0; f < 28; f++) s[f] = (double)acc[f];
-#pragma unroll
-            for (int i = 0; i < 6; i++) a[i] = (double)r[i];
+            for (int q = 0; q < 6; q++) { d[q] = x[q] - r[q]; wd[q] = w * d[q]; acc[1 + q] += wd[q]; }
             int u = 7;
 #pragma unroll
             for (int i = 0; i < 6; i++)
 #pragma unroll
-                for (int j = i; j < 6; j++, u++) s[u] += a[i] * s[1 + j] + s[1 + i] * a[j] + s[0] * a[i] * a[j];
+                for (int j = i; j < 6; j++, u++) acc[u] = fmaf(wd[i], d[j], acc[u]);
+        }
+        float *dst = part + (fbase[g] + (long long)c * S + ml) * VBGS_F;
 #pragma unroll
-            for (int i = 0; i < 6; i++) s[1 + i] += s[0] * a[i];
-            double *dst = dS + (size_t)kperm[pos] * 28;
+        for (int f = 0; f < 28; f++) dst[f] = acc[f];
+    }
+}
+
+// One CTA per cluster: lane = member (32 at a time), warp w sums the items
+// c = w, w + 4, ... in order; the four warp sums are added in warp order.
+__global__ void __launch_bounds__(128) k_cand_reduce(const float *__restrict__ part, const float *__restrict__ rec32,
+                                                     const int *__restrict__ order, const int *__restrict__ cstart,
+                                                     const int *__restrict__ item_start,
+                                                     const long long *__restrict__ fbase,
+                                                     const int *__restrict__ kperm, double *__restrict__ dS)
+{
+    __shared__ double sh[3][32][29];
+    const int g = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int b = cstart[g], S = cstart[g + 1] - b;
+    const int items = item_start[g + 1] - item_start[g];
+    if (items == 0) return;
+    for (int m0 = 0; m0 < S; m0 += 32) {
+        const int ml = m0 + lane;
+        const bool v = ml < S;
+        double s[28];
+#pragma unroll
+        for (int f = 0; f < 28; f++) s[f] = 0.0;
+        if (v)
+            for (int c = w; c < items; c += 4) {
+                const float *src = part + (fbase[g] + (long long)c * S + ml) * VBGS_F;
+#pragma unroll
+                for (int f = 0; f < 28; f++) s[f] += (double)src[f];
+            }
+        __syncthreads();
+        if (w > 0)
+#pragma unroll
+            for (int f = 0; f < 28; f++) sh[w - 1][lane][f] = s[f];
+        __syncthreads();
+        if (w == 0 && v) {
+#pragma unroll
+            for (int f = 0; f < 28; f++) s[f] += sh[0][lane][f] + sh[1][lane][f] + sh[2][lane][f];
+            const int pos = order[b + ml];
+            double a[6];
+#pragma unroll
+            for (int q = 0; q < 6; q++) a[q] = (double)rec32[(size_t)pos * VBGS_REC + q];
+            int u = 7;
+#pragma unroll
+            for (int q = 0; q < 6; q++)
+#pragma unroll
+                for (int j = q; j < 6; j++, u++) s[u] += a[q] * s[1 + j] + s[1 + q] * a[j] + s[0] * a[q] * a[j];
+#pragma unroll
+            for (int q = 0; q < 6; q++) s[1 + q] += s[0] * a[q];
+            double *dst = dS + (size_t)kperm[pos] * VBGS_F;
 #pragma unroll
             for (int f = 0; f < 28; f++) dst[f] += s[f];
         }
@@ -600,12 +948,14 @@ __global__ void k_list_bounds(const unsigned int *__restrict__ skey, int64_t n, 
 }
 
 // Labels of the exact points: q_ng = sum_{k in g} 2^(l_nk - lse2_n), over the
-// clusters the certificate does not rule out (bound mass >= 2^-40).  One warp
+// clusters whose certificate bound is not below 2^-40 of the point's mass
+// (UB row of the point's frame index: rows[i] when the points were gathered).  One warp
 // per point: lanes test the clusters, then share the scoring of each kept one.
 __global__ void __launch_bounds__(256) k_labels(const double *__restrict__ Xe, const double *__restrict__ lse_e,
-                                                int64_t rstride, int64_t ne, const float *__restrict__ rec32,
-                                                const int *__restrict__ order, const int *__restrict__ cstart,
-                                                const float *__restrict__ cstat, float *__restrict__ Q)
+                                                const int *__restrict__ rows, int64_t rstride, int64_t ne,
+                                                const float *__restrict__ rec32, const int *__restrict__ order,
+                                                const int *__restrict__ cstart, const float *__restrict__ UB,
+                                                float *__restrict__ Q)
 {
     const int lane = threadIdx.x & 31;
     const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -615,10 +965,10 @@ __global__ void __launch_bounds__(256) k_labels(const double *__restrict__ Xe, c
     for (int i = 0; i < 6; i++) x[i] = (float)Xe[n * rstride * VBGS_XS + i];
     const float l2 = (float)(lse_e[n * rstride] * 1.4426950408889634);
     float *q = Q + n * kG;
+    const float *ub = UB + (int64_t)(rows ? rows[n * rstride] : n * rstride) * kG;
     for (int g0 = 0; g0 < kG; g0 += 32) {
         const int g = g0 + lane;
-        const float *c = cstat + g * kCS;
-        const bool keep = c[14] > 0.f && cluster_ub(c, x) - l2 > -40.f;
+        const bool keep = ub[g] - l2 > -40.f;
         if (!keep) q[g] = 0.f;
         uint32_t kb = __ballot_sync(0xffffffffu, keep);
         while (kb) {
@@ -637,15 +987,83 @@ __global__ void __launch_bounds__(256) k_labels(const double *__restrict__ Xe, c
 // lse of the frame: proposal points keep the candidate lse, exact points the
 // exact one; fixed-order block sums.
 __global__ void __launch_bounds__(256) k_lse_combine(double *__restrict__ lse_c, const double *__restrict__ lse_e,
+                                                     const int *__restrict__ erows, int64_t ne)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    lse_c[erows[i]] = lse_e[i];
+}
+
+// True missed mass of the proposal on the audit points: every component
+// scored in the candidates' FP32 arithmetic, 1 - 2^(lse2_cand - lse2_all).
+// Blocks of (kAP exact rows) x (256 components) write per-row partial
+// (max, sum) pairs; the final kernel merges them in component-chunk order.
+// Rows that are fallbacks (not audits) report 0.
+constexpr int kAP = 32;
+__global__ void __launch_bounds__(256) k_audit_part(const double *__restrict__ X, const int *__restrict__ erows,
+                                                    int64_t ne, const int *__restrict__ exact,
+                                                    const float *__restrict__ rec32, int K, float2 *__restrict__ part)
+{
+    __shared__ float xs[kAP][6];
+    __shared__ int live[kAP];
+    __shared__ float2 wp[kAP][8];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int64_t i0 = (int64_t)blockIdx.x * kAP;
+    if (t < kAP) {
+        const int64_t i = i0 + t;
+        const bool ok = i < ne && exact[erows[i]] == 2;
+        live[t] = ok;
+#pragma unroll
+        for (int q = 0; q < 6; q++) xs[t][q] = ok ? (float)X[(int64_t)erows[i] * VBGS_XS + q] : 0.f;
+    }
+    __syncthreads();
+    const int k = blockIdx.y * 256 + t;
+    const bool kv = k < K;
+    float r[28];
+#pragma unroll
+    for (int q = 0; q < 28; q++) r[q] = kv ? rec32[(size_t)k * VBGS_REC + q] : 0.f;
+    for (int p = 0; p < kAP; p++) {
+        if (!live[p]) continue;
+        float x[6];
+#pragma unroll
+        for (int q = 0; q < 6; q++) x[q] = xs[p][q];
+        const float l = kv ? logit32(r, x) : -INFINITY;
+        const float m = warp_max(l);
+        const float e = (m == -INFINITY) ? 0.f : warp_sum(ex2a(l - m));
+        if (lane == 0) wp[p][w] = make_float2(m, e);
+    }
+    __syncthreads();
+    if (t < kAP) {
+        float2 out = make_float2(-INFINITY, 0.f);
+        if (live[t]) {
+            float m = -INFINITY;
+            for (int q = 0; q < 8; q++) m = fmaxf(m, wp[t][q].x);
+            float sum = 0.f;
+            if (m != -INFINITY)
+                for (int q = 0; q < 8; q++) sum += wp[t][q].y * ex2a(wp[t][q].x - m);
+            out = make_float2(m, sum);
+        }
+        if (i0 + t < ne) part[(i0 + t) * gridDim.y + blockIdx.y] = out;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_audit_final(const float2 *__restrict__ part, int nch,
                                                      const int *__restrict__ erows, int64_t ne,
+                                                     const int *__restrict__ exact, const double *__restrict__ lse_c,
                                                      float *__restrict__ audit_missed)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
     const int n = erows[i];
-    // true missed mass of the proposal on this point: 1 - exp(lse_cand - lse)
-    audit_missed[i] = (float)(-expm1(lse_c[n] - lse_e[i]));
-    lse_c[n] = lse_e[i];
+    if (exact[n] != 2) { audit_missed[i] = 0.f; return; }
+    float m = -INFINITY;
+    for (int c = 0; c < nch; c++) m = fmaxf(m, part[i * nch + c].x);
+    double s = 0.0;
+    for (int c = 0; c < nch; c++)
+        if (part[i * nch + c].x != -INFINITY) s += (double)part[i * nch + c].y * (double)ex2a(part[i * nch + c].x - m);
+    const double l2 = (double)m + log2(s);
+    const double d = lse_c[n] * 1.4426950408889634 - l2;
+    audit_missed[i] = (float)fmax(0.0, -expm1(d * 0.6931471805599453));
 }
 
 __global__ void __launch_bounds__(256) k_sum_lse(const double *__restrict__ v, int64_t n, double *__restrict__ part)
@@ -673,17 +1091,6 @@ __global__ void k_add(double *__restrict__ a, const double *__restrict__ b, size
 } // namespace
 
 // ------------------------------------------------------------ launchers -----
-bool g_prop_attr = false;
-int prop_set_attributes()
-{
-    if (g_prop_attr) return 0;
-    if (cudaFuncSetAttribute(k_cand_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, kG * kCS * (int)sizeof(float)) !=
-        cudaSuccess)
-        return -1;
-    g_prop_attr = true;
-    return 0;
-}
-
 int prop_launch_kmeans(const float *rec32, int K, float csc, float *pts, float *cent, SortBuffers &sb, int *order,
                        unsigned int *skey, int *cstart, int lloyd_iters, cudaStream_t st)
 {
@@ -700,11 +1107,24 @@ int prop_launch_kmeans(const float *rec32, int K, float csc, float *pts, float *
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int prop_launch_cluster_stats(const float *rec32, const int *order, const int *cstart, float *cstat, cudaStream_t st)
+int prop_launch_certificate(const double *rec, const float *rec32, const int *order, const unsigned int *skey,
+                            const int *cstart, int K, const double *Spast, const double *dS, const int *kperm,
+                            float xmax, float *cpar, double *cscr, float *mscr, cudaStream_t st)
 {
-    k_cluster_stats<<<kG, 128, 0, st>>>(rec32, order, cstart, cstat);
+    k_cluster_metric<<<kG, 64, 0, st>>>(rec, order, cstart, Spast, dS, kperm, cpar, cscr);
+    k_cluster_members<<<(K + 127) / 128, 128, 0, st>>>(rec, rec32, order, skey, K, cscr, mscr);
+    k_cluster_tables<<<kG, 64, 0, st>>>(mscr, cstart, xmax, cpar);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
+
+void prop_bounds(const double *X, int64_t N, const float *cpar, float *UB, cudaStream_t st)
+{
+    if (N > 0) k_bounds<<<dim3((unsigned)((N + 127) / 128), kBG), 128, 0, st>>>(X, N, cpar, UB);
+}
+
+size_t prop_cpar_floats() { return (size_t)kG * kCP; }
+size_t prop_cscr_doubles() { return (size_t)kG * kCScr; }
+size_t prop_mscr_floats(int K) { return (size_t)K * kMS; }
 
 void prop_gemm(int M, int N, int K, const float *A, int sam, int sak, const float *B, int sbk, int sbn, float *C,
                int ldc, const float *bias, bool relu, bool accumulate, cudaStream_t st)
@@ -742,14 +1162,12 @@ void prop_inputs(const double *X, const int *rows, int64_t rstride, int64_t n, c
 }
 
 int prop_cand_pass1(const double *X, int64_t N, const float *rec32, const int *order, const int *cstart,
-                    const float *cstat, const int *top, float thresh, uint32_t seed, uint32_t audit_per_mille,
+                    const float *UB, const int *top, float thresh, uint32_t seed, uint32_t audit_per_mille,
                     double *lse_c, float *bound, int *exact, int *cand, unsigned long long *counters, cudaStream_t st)
 {
-    const size_t smem = (size_t)kG * kCS * sizeof(float);
-    if (prop_set_attributes()) return -1;
-    k_cand_pass1<<<(unsigned)((N * 32 + 255) / 256), 256, smem, st>>>(X, N, rec32, order, cstart, cstat, top, thresh,
-                                                                      seed, audit_per_mille, lse_c, bound, exact, cand,
-                                                                      counters);
+    k_cand_pass1<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(X, N, rec32, order, cstart, UB, top, thresh, seed,
+                                                                   audit_per_mille, lse_c, bound, exact, cand,
+                                                                   counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -771,24 +1189,46 @@ int prop_cand_lists(const int *cand, const int *exact, int64_t N, SortBuffers &s
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-void prop_cand_pass2(const double *X, const double *lse_c, const float *rec32, const int *order, const int *cstart,
-                     const int *pstart, const int *plist, const int *kperm, double *dS, cudaStream_t st)
+int prop_cand_items(const int *pstart, const int *cstart, int *item_start, long long *fbase, cudaStream_t st)
 {
-    k_cand_pass2<<<kG, 128, 0, st>>>(X, lse_c, rec32, order, cstart, pstart, plist, kperm, dS);
+    k_items<<<1, kG, 0, st>>>(pstart, cstart, item_start, fbase);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-void prop_labels(const double *Xe, const double *lse_e, int64_t rstride, int64_t ne, const float *rec32,
-                 const int *order, const int *cstart, const float *cstat, float *Q, cudaStream_t st)
+void prop_cand_pass2(const double *X, const double *lse_c, const float *rec32, const int *order, const int *cstart,
+                     const unsigned int *skey, int K, const int *pstart, const int *plist, const int *item_start,
+                     const long long *fbase, int n_items, float *part, const int *kperm, double *dS, cudaStream_t st)
+{
+    if (n_items > 0)
+        k_cand_pass2<<<(unsigned)n_items, 64, 0, st>>>(X, lse_c, rec32, order, cstart, pstart, plist, item_start,
+                                                        fbase, part);
+    k_cand_reduce<<<kG, 128, 0, st>>>(part, rec32, order, cstart, item_start, fbase, kperm, dS);
+}
+
+void prop_labels(const double *Xe, const double *lse_e, const int *rows, int64_t rstride, int64_t ne,
+                 const float *rec32, const int *order, const int *cstart, const float *UB, float *Q, cudaStream_t st)
 {
     if (ne > 0)
-        k_labels<<<(unsigned)((ne * 32 + 255) / 256), 256, 0, st>>>(Xe, lse_e, rstride, ne, rec32, order, cstart,
-                                                                     cstat, Q);
+        k_labels<<<(unsigned)((ne * 32 + 255) / 256), 256, 0, st>>>(Xe, lse_e, rows, rstride, ne, rec32, order,
+                                                                     cstart, UB, Q);
 }
 
-void prop_lse_combine(double *lse_c, const double *lse_e, const int *erows, int64_t ne, float *audit_missed,
-                      cudaStream_t st)
+size_t prop_audit_floats(int64_t ne, int K) { return (size_t)std::max<int64_t>(ne, 1) * ((K + 255) / 256) * 2; }
+
+void prop_audit(const double *X, const int *erows, int64_t ne, const int *exact, const double *lse_c,
+                const float *rec32, int K, float *scratch, float *audit_missed, cudaStream_t st)
 {
-    if (ne > 0) k_lse_combine<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(lse_c, lse_e, erows, ne, audit_missed);
+    if (ne <= 0) return;
+    const int nch = (K + 255) / 256;
+    float2 *part = reinterpret_cast<float2 *>(scratch);
+    k_audit_part<<<dim3((unsigned)((ne + kAP - 1) / kAP), (unsigned)nch), 256, 0, st>>>(X, erows, ne, exact, rec32,
+                                                                                          K, part);
+    k_audit_final<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(part, nch, erows, ne, exact, lse_c, audit_missed);
+}
+
+void prop_lse_combine(double *lse_c, const double *lse_e, const int *erows, int64_t ne, cudaStream_t st)
+{
+    if (ne > 0) k_lse_combine<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(lse_c, lse_e, erows, ne);
 }
 
 void prop_sum_lse(const double *v, int64_t n, double *part, int *nparts, cudaStream_t st)

@@ -49,7 +49,7 @@ EXPORTS = [
     "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_pairs", "vbgs_profile_name", "vbgs_probe_peaks",
     "vbgs_estep_noalloc", "vbgs_update_batched", "vbgs_autotune", "vbgs_get_tuning",
     "vbgs_proposal_report", "vbgs_proposal_weights", "vbgs_proposal_grad", "vbgs_proposal_clusters",
-    "vbgs_last_error", "vbgs_destroy",
+    "vbgs_proposal_bounds", "vbgs_last_error", "vbgs_destroy",
 ]
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 PROF_COUNT = 6
@@ -111,6 +111,7 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
     lib.vbgs_proposal_weights.argtypes = [C.c_void_p, _FP, _FP]
     lib.vbgs_proposal_grad.argtypes = [C.c_void_p, _FP, _FP, C.c_int, _FP, _FP, C.POINTER(C.c_int)]
     lib.vbgs_proposal_clusters.argtypes = [C.c_void_p, _FP, C.POINTER(C.c_int)]
+    lib.vbgs_proposal_bounds.argtypes = [C.c_void_p, _DP, C.c_int64, _FP, C.POINTER(C.c_int)]
     return lib
 
 
@@ -323,6 +324,16 @@ def vbgs_proposal_clusters(ctx, K: int):
     cl = np.zeros(K, dtype=np.int32)
     _check(lib().vbgs_proposal_clusters(ctx, _fp(cent), cl.ctypes.data_as(C.POINTER(C.c_int))), ctx)
     return cent, cl
+
+
+def vbgs_proposal_bounds(ctx, points, K: int):
+    """Certificate bounds (log2 units, N x 1024) of the current posterior at
+    host points (N x 6) and each component's cluster (K)."""
+    x = np.ascontiguousarray(np.asarray(points, dtype=np.float64)[:, :6])
+    ub = np.zeros((x.shape[0], PROP_CLUSTERS), dtype=np.float32)
+    cl = np.zeros(K, dtype=np.int32)
+    _check(lib().vbgs_proposal_bounds(ctx, _dp(x), x.shape[0], _fp(ub), cl.ctypes.data_as(C.POINTER(C.c_int))), ctx)
+    return ub, cl
 
 
 def vbgs_last_error(ctx=None) -> str:
