@@ -316,6 +316,111 @@ def run_batched(args):
     return 0
 
 
+K_PROP = 200_000
+PROP_WORKLOAD = ("continual RGB-D room stream (seed 5): 200x200 frames, K=200,000 components, 3 CAVI iterations "
+                 "per frame, learned proposal (1,024 k-means clusters, MLP top-4, certificate 1e-3, 1% audit)")
+
+
+def proposal_measure(V, form, n_warm, n_steps, stream, flush, log_frames=False):
+    """The learned-proposal form against the full E-step (the ablation "with
+    MLP vs without") on the same frames: updates/s counted as the exact-
+    equivalent N*K*iters, the proposal's fallback / audit / candidate-pair
+    report per frame, and the one-frame error of the last frame from the full
+    form's state before it."""
+    import torch
+    from paper_2603_08499_gb300 import synth
+    prior = synth.room_prior(K_PROP, seed=5)
+    frames = make_frames(n_warm + n_steps, seed=5)
+    dev = [torch.from_numpy(X).cuda() for X in frames]
+    out = {}
+    for name, flags in (("proposal", V.VBGS_FLAG_PROPOSAL), ("full", 0)):
+        m = V.Model(prior, form, cuda_stream=stream.cuda_stream, flags=flags)
+        times, pairs, reps, traces = [], 0, [], []
+        for t, X in enumerate(dev):
+            if t == len(dev) - 1:
+                state_before_last = m.stats()
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            tr = m.update(X, ITERS)
+            e1.record(stream)
+            e1.synchronize()
+            if t >= n_warm:
+                times.append(e0.elapsed_time(e1) * 1e-3)
+                pairs += X.shape[0] * K_PROP * ITERS
+                traces.append(tr)
+                if flags:
+                    reps.append(V.vbgs_proposal_report(m.ctx))
+        out[name] = {"value": pairs / sum(times), "ms_per_frame": 1e3 * sum(times) / len(times), "reps": reps,
+                     "state_before_last": state_before_last, "final": m.stats(), "traces": traces,
+                     "model": m if flags else None}
+        if not flags:
+            m.close()
+    # one-frame error: the trained proposal model from the full form's state
+    mp = out["proposal"]["model"]
+    S0, S1 = out["full"]["state_before_last"], out["full"]["final"]
+    mp.set_stats(S0)
+    tr = mp.update(dev[-1], ITERS)
+    dS, dS0 = mp.stats() - S0, S1 - S0
+    mp.close()
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+    reps = out["proposal"]["reps"]
+    n_pts = sum(r["points"] for r in reps)
+    res = {
+        "workload": PROP_WORKLOAD, "form": form, "frames_timed": n_steps, "frames_warm": n_warm,
+        "value": out["proposal"]["value"], "unit": UNIT + " (exact-equivalent N*K*iters)",
+        "ms_per_frame": out["proposal"]["ms_per_frame"],
+        "full_estep_value": out["full"]["value"], "full_estep_ms_per_frame": out["full"]["ms_per_frame"],
+        "speedup_vs_full_estep": out["proposal"]["value"] / out["full"]["value"],
+        "frames_run_exact": int(sum(r["frame_exact"] for r in reps)),
+        "fallback_fraction": float(sum(r["fallback"] for r in reps) / max(n_pts, 1)),
+        "audit_points": int(sum(r["audit"] for r in reps)),
+        "audit_max_missed_mass": float(max(r["audit_max_missed"] for r in reps)),
+        "candidate_pair_fraction_first_iteration": float(
+            sum(r["cand_pairs"] for r in reps if not r["frame_exact"]) /
+            max(sum(r["points"] for r in reps if not r["frame_exact"]) * K_PROP, 1)),
+        "clusters_added_per_point": float(sum(r["added_clusters"] for r in reps if not r["frame_exact"]) /
+                                          max(sum(r["points"] for r in reps if not r["frame_exact"]), 1)),
+        "train_loss_last": reps[-1]["train_loss"], "frames_trained": int(reps[-1]["frames_trained"]),
+        "one_frame_error_vs_full_estep": {
+            "elbo": rel(tr, out["full"]["traces"][-1]), "N": rel(dS[:, 0], dS0[:, 0]),
+            "S1": rel(dS[:, 1:7], dS0[:, 1:7]), "S2": rel(dS[:, 7:], dS0[:, 7:]),
+            "what": "last frame, 3 iterations, proposal model from the full form's state before it"},
+        "whole_stream_elbo_drift_vs_full_estep": max(
+            rel(a, b) for a, b in zip(out["proposal"]["traces"], out["full"]["traces"])),
+    }
+    if log_frames:
+        for t, r in enumerate(reps):
+            log(f"proposal frame {t}: exact={int(r['frame_exact'])} fallback={int(r['fallback'])} "
+                f"audit={int(r['audit'])} audit_max={r['audit_max_missed']:.2e} cand_pairs={r['cand_pairs']:.3e} "
+                f"loss={r['train_loss']:.3f}")
+    return res
+
+
+def run_proposal(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as G
+    G.build()
+    from paper_2603_08499_gb300 import vbgs as V
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = proposal_measure(V, args.form, args.warmup, args.steps, stream, flush, log_frames=True)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_frame"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPES[args.form], "data": "synthetic",
+            "config": {"workload": PROP_WORKLOAD, "K": K_PROP, "iters": ITERS, "form": args.form,
+                       "l2": "flushed between steps (256 MB write outside the timed events)"},
+            "proposal": res, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -392,6 +497,12 @@ def run_ours(args):
             "S2": rel(dS[:, 7:], dS0[:, 7:]),
             "what": "last frame, 3 iterations, from the FP64 state before it (Eq. relerr, tau=1e-30)"}
 
+    if rank == 0 and not args.no_proposal:
+        try:
+            extra["proposal"] = proposal_measure(V, form, 3, 12, stream, flush)
+        except Exception as exc:   # reported, never fatal to the headline line
+            extra["proposal"] = {"error": f"{type(exc).__name__}: {exc}"}
+
     if rank == 0:
         n_pts = sum(X.shape[0] for X in timed_frames)
         rl, rl_all = roofline(form, res["prof"], res["prof_pairs"])
@@ -436,7 +547,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", choices=list(DTYPES), default="fp16x3")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["room", "batched"], default="room")
+    ap.add_argument("--workload", choices=["room", "batched", "proposal"], default="room")
+    ap.add_argument("--no-proposal", action="store_true", help="skip the proposal measurement of the default run")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--flags", type=int, default=0,
                     help="VBGS_FLAG_* bits: 1 = caller's order, 2 = no pass-2 tile skipping (3 = plain)")
@@ -449,6 +561,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "proposal":
+        return run_proposal(args)
     return run_ours(args)
 
 

@@ -200,7 +200,7 @@ int stage_points(vbgs_ctx *ctx, const double *points, int64_t N)
 
 int run_mstep(vbgs_ctx *ctx, const double *dS)
 {
-    int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_kinv, ctx->d_rec, ctx->d_rec32, ctx->d_pcache,
+    int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_kperm, ctx->d_rec, ctx->d_rec32, ctx->d_pcache,
                          ctx->d_flags, ctx->d_scal, ctx->stream, &ctx->prof);
     if (l < 0) return fail(ctx, VBGS_ECUDA, "posterior update launch failed");
     ctx->launches += l;
@@ -299,6 +299,7 @@ constexpr double kExactFrameFrac = 0.2;
 constexpr float kPropLr = 1e-3f;
 constexpr int kPropEpochs = 2;
 constexpr int64_t kPropTrainPoints = 16384;
+constexpr int kPropRounds = 6;   // candidate rounds: the top 4, then up to 8 clusters per round; the last adds none
 constexpr size_t kOffB1 = 128 * 6, kOffW2 = kOffB1 + 128, kOffB2 = kOffW2 + 128 * 128, kOffW3 = kOffB2 + 128,
                  kOffB3 = kOffW3 + 1024 * 128, kNParam = kOffB3 + 1024;
 
@@ -349,7 +350,7 @@ int prop_alloc(vbgs_ctx *ctx)
         (rc = dalloc(ctx, &P.h1, (size_t)kMB * kHid)) || (rc = dalloc(ctx, &P.h2, (size_t)kMB * kHid)) ||
         (rc = dalloc(ctx, &P.dh1, (size_t)kMB * kHid)) || (rc = dalloc(ctx, &P.dh2, (size_t)kMB * kHid)) ||
         (rc = dalloc(ctx, &P.z, (size_t)kMB * kPG)) || (rc = dalloc(ctx, &P.dz, (size_t)kMB * kPG)) ||
-        (rc = dalloc(ctx, &P.loss, 2)) || (rc = dalloc(ctx, &P.counters, 4)) ||
+        (rc = dalloc(ctx, &P.loss, 2)) || (rc = dalloc(ctx, &P.counters, 8)) ||
         (rc = dalloc(ctx, &P.pstart, (size_t)kPG + 1)) || (rc = dalloc(ctx, &P.item_start, (size_t)kPG + 1)) ||
         (rc = dalloc(ctx, &P.fbase, (size_t)kPG + 1)))
         return rc;
@@ -381,7 +382,9 @@ int prop_ensure_frame(vbgs_ctx *ctx, int64_t N)
             (rc = dalloc(ctx, &P.pkey, (size_t)cap * VBGS_PROP_MAXCAND)) || (rc = dalloc(ctx, &P.ekey, (size_t)cap)) ||
             (rc = dalloc(ctx, &P.lse_c, (size_t)cap)) || (rc = dalloc(ctx, &P.Xe, (size_t)cap * VBGS_XS)) ||
             (rc = dalloc(ctx, &P.lse_e, (size_t)cap)) || (rc = dalloc(ctx, &P.lsum, (size_t)cap / 256 + 2)) ||
-            (rc = dalloc(ctx, &P.bound, (size_t)cap)) || (rc = dalloc(ctx, &P.ub, (size_t)cap * kPG)) || (rc = dalloc(ctx, &P.audit, (size_t)cap)) ||
+            (rc = dalloc(ctx, &P.bound, (size_t)cap)) || (rc = dalloc(ctx, &P.ub, (size_t)cap * kPG)) ||
+            (rc = dalloc(ctx, &P.ncand, (size_t)cap)) || (rc = dalloc(ctx, &P.pend, (size_t)cap)) ||
+            (rc = dalloc(ctx, &P.run, (size_t)cap)) || (rc = dalloc(ctx, &P.cpart, (size_t)cap * VBGS_PROP_MAXCAND)) || (rc = dalloc(ctx, &P.audit, (size_t)cap)) ||
             (rc = dalloc(ctx, &P.Xin, (size_t)std::max<int64_t>(cap, kPropTrainPoints) * 6)) ||
             (rc = dalloc(ctx, &P.Q, (size_t)kPropTrainPoints * kPG)))
             return rc;
@@ -516,11 +519,32 @@ int prop_estep(vbgs_ctx *ctx, int64_t N, bool last_iter)
     }
     prop_bounds(X, N, P.cpar, P.ub, ctx->stream);
     ctx->launches += 1;
-    CU(cudaMemsetAsync(P.counters, 0, sizeof(unsigned long long) * 4, ctx->stream));
+    CU(cudaMemsetAsync(P.counters, 0, sizeof(unsigned long long) * 8, ctx->stream));
     const uint32_t seed = (uint32_t)(P.frame * 0x9E3779B1ull) ^ 0xA5A5A5A5u;
-    if (prop_cand_pass1(X, N, ctx->d_rec32, P.order, P.cstart, P.ub, P.top, kPropThresh, seed, kAuditPerMille,
-                        P.lse_c, P.bound, P.exact, P.cand, P.counters, ctx->stream))
-        return fail(ctx, VBGS_ECUDA, "candidate pass 1 failed");
+    // candidate rounds: score the pending candidates cluster-major, then
+    // merge and select the next clusters by the certificate
+    prop_cand_init(P.top, N, P.cand, P.ncand, P.pend, P.run, P.cpart, ctx->stream);
+    ctx->launches += 1;
+    for (int round = 0; round < kPropRounds; round++) {
+        if (prop_pend_lists(P.cand, P.ncand, P.pend, N, ctx->sb, P.pkey, P.plist, P.pstart, ctx->stream) ||
+            prop_cand_items(P.pstart, P.cstart, false, P.item_start, P.fbase, ctx->stream))
+            return fail(ctx, VBGS_ECUDA, "candidate lists failed");
+        int n_items = 0;
+        CU(cudaMemcpyAsync(&n_items, P.item_start + kPG, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        prop_cand_score(X, ctx->d_rec32, P.order, P.cstart, P.pstart, P.plist, P.item_start, n_items, P.cpart,
+                        ctx->stream);
+        CU(cudaMemsetAsync(P.counters + 4, 0, sizeof(unsigned long long), ctx->stream));
+        prop_cand_select(P.ub, N, P.cstart, kPropThresh, round == kPropRounds - 1, seed, kAuditPerMille, P.cand,
+                         P.ncand, P.pend, P.run, P.cpart, P.lse_c, P.bound, P.exact, P.counters, ctx->stream);
+        ctx->launches += 7;
+        unsigned long long added = 0;
+        CU(cudaMemcpyAsync(&added, P.counters + 4, sizeof added, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        if (!added) break;
+    }
+    prop_cand_count(P.exact, P.ncand, P.cand, P.cstart, N, P.counters, ctx->stream);
+    ctx->launches += 1;
     unsigned long long cnt[4];
     CU(cudaMemcpyAsync(cnt, P.counters, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -551,11 +575,12 @@ int prop_estep(vbgs_ctx *ctx, int64_t N, bool last_iter)
         if ((rc = dalloc(ctx, &P.apart, aneed))) return rc;
         P.apart_cap = aneed;
     }
-    prop_audit(X, P.erows, ne, P.exact, P.lse_c, ctx->d_rec32, ctx->K, P.apart, P.audit, ctx->stream);
+    if (last_iter)   // the report's true missed mass (the last iteration's)
+        prop_audit(X, P.erows, ne, P.exact, P.lse_c, ctx->d_rec32, ctx->K, P.apart, P.audit, ctx->stream);
     prop_lse_combine(P.lse_c, P.lse_e, P.erows, ne, ctx->stream);
     // candidate statistics of the proposal points, added to the exact ones
     if (prop_cand_lists(P.cand, P.exact, N, ctx->sb, P.pkey, P.plist, P.pstart, ctx->stream) ||
-        prop_cand_items(P.pstart, P.cstart, P.item_start, P.fbase, ctx->stream))
+        prop_cand_items(P.pstart, P.cstart, true, P.item_start, P.fbase, ctx->stream))
         return fail(ctx, VBGS_ECUDA, "candidate lists failed");
     int n_items = 0;
     long long n_part = 0;
@@ -680,7 +705,7 @@ void free_all(vbgs_ctx *ctx)
         void *pp[] = {P.cent, P.kpts, P.cpar, P.cscr, P.mscr, P.ub, P.order, P.cstart, P.skey, P.w, P.wq, P.am, P.av, P.grad, P.top, P.cand,
                       P.exact, P.erows, P.plist, P.pstart, P.pkey, P.ekey, P.lse_c, P.Xe, P.lse_e, P.lsum, P.bound,
                       P.audit, P.counters, P.Xin, P.Q, P.h1, P.h2, P.z, P.dz, P.dh2, P.dh1, P.loss,
-                      P.item_start, P.fbase, P.part2, P.apart};
+                      P.item_start, P.fbase, P.part2, P.apart, P.ncand, P.pend, P.run, P.cpart};
         for (void *p : pp)
             if (p) cudaFree(p);
     }
@@ -1112,6 +1137,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     ctx->mp.beta0 = prior->beta0;
     ctx->mp.nu0 = prior->nu0;
     ctx->mp.K = K;
+    ctx->mp.want_bounds = (ctx->flags & VBGS_FLAG_PROPOSAL) ? 1 : 0;
     for (int i = 0; i < 36; i++) ctx->mp.W0inv[i] = W0inv[i];
     ctx->m0_h.assign(prior->m0, prior->m0 + (size_t)K * 6);
 
@@ -1147,6 +1173,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     CU(cudaMemcpyAsync(ctx->d_m0, prior->m0, sizeof(double) * K * 6, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_Spast, 0, sizeof(double) * KF, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_dS, 0, sizeof(double) * KF, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_pcache, 0, sizeof(double) * mstep_cache_doubles(K), ctx->stream));
     CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_scal, 0, sizeof(double) * SC_COUNT, ctx->stream));
     {

@@ -89,6 +89,7 @@ struct MstepParams {
     double alpha0, beta0, nu0;
     double W0inv[36];
     int K;
+    int want_bounds;   // write the eigenvalue bounds of the proposal certificate (record floats 28-30)
 };
 
 // Box of the Morton codes (positions only).
@@ -134,7 +135,7 @@ int launch_stage_points(const double *src, int64_t N, double *X, int *flags, cud
 // `cache` (mstep_cache_doubles(K) doubles) for the KL of later iterations.
 size_t mstep_cache_doubles(int K);
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
-                 const int *kinv, double *rec, float *rec32, double *cache, int *flags, double *scal,
+                 const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
                  cudaStream_t st, Prof *pf);
 size_t sort_temp_bytes(int64_t n);
 int launch_point_order(const double *X, int64_t N, const BoxParams &box, SortBuffers &sb, double *Xs,
@@ -188,13 +189,22 @@ void prop_softmax_top(const float *Z, int B, const float *Q, float *dZ, int *top
 void prop_adam(float *w, float *wq, float *m, float *v, const float *g, size_t n, float lr, int step, cudaStream_t st);
 void prop_inputs(const double *X, const int *rows, int64_t rstride, int64_t n, const BoxParams &box, float *out,
                  cudaStream_t st);
-int prop_cand_pass1(const double *X, int64_t N, const float *rec32, const int *order, const int *cstart,
-                    const float *UB, const int *top, float thresh, uint32_t seed, uint32_t audit_per_mille,
-                    double *lse_c, float *bound, int *exact, int *cand, unsigned long long *counters, cudaStream_t st);
+void prop_cand_init(const int *top, int64_t N, int *cand, int *ncand, int *pend, float2 *run, float2 *part,
+                    cudaStream_t st);
+int prop_pend_lists(const int *cand, const int *ncand, const int *pend, int64_t N, SortBuffers &sb,
+                    unsigned int *skey, int *plist, int *pstart, cudaStream_t st);
+void prop_cand_score(const double *X, const float *rec32, const int *order, const int *cstart, const int *pstart,
+                     const int *plist, const int *item_start, int n_items, float2 *part, cudaStream_t st);
+void prop_cand_select(const float *UB, int64_t N, const int *cstart, float thresh, bool final_round, uint32_t seed,
+                      uint32_t audit_per_mille, int *cand, int *ncand, int *pend, float2 *run, float2 *part,
+                      double *lse_c, float *bound, int *exact, unsigned long long *counters, cudaStream_t st);
+void prop_cand_count(const int *exact, const int *ncand, const int *cand, const int *cstart, int64_t N,
+                     unsigned long long *counters, cudaStream_t st);
 void prop_gather_rows(const double *X, const int *rows, int64_t n, double *Xe, cudaStream_t st);
 int prop_cand_lists(const int *cand, const int *exact, int64_t N, SortBuffers &sb, unsigned int *skey, int *plist,
                     int *pstart, cudaStream_t st);
-int prop_cand_items(const int *pstart, const int *cstart, int *item_start, long long *fbase, cudaStream_t st);
+int prop_cand_items(const int *pstart, const int *cstart, bool pass2, int *item_start, long long *fbase,
+                    cudaStream_t st);
 void prop_cand_pass2(const double *X, const double *lse_c, const float *rec32, const int *order, const int *cstart,
                      const unsigned int *skey, int K, const int *pstart, const int *plist, const int *item_start,
                      const long long *fbase, int n_items, float *part, const int *kperm, double *dS, cudaStream_t st);
@@ -240,7 +250,9 @@ struct PropState {
     unsigned int *pkey = nullptr, *ekey = nullptr;
     double *lse_c = nullptr, *Xe = nullptr, *lse_e = nullptr, *lsum = nullptr;
     float *bound = nullptr, *audit = nullptr;
-    unsigned long long *counters = nullptr;   // [0] candidate pairs, [1] fallback, [2] audit
+    unsigned long long *counters = nullptr;   // [0] candidate pairs, [1] fallback, [2] audit, [3] added, [4] added in a round
+    int *ncand = nullptr, *pend = nullptr;    // candidate count and first unscored slot per point
+    float2 *run = nullptr, *cpart = nullptr;  // running (max, sum) per point; per-slot partials
     bool frame_exact = false;
     uint64_t frame = 0;
     // training set of the current frame and minibatch buffers

@@ -26,45 +26,45 @@ constexpr double kLnPi = 1.1447298858494001741;
 // asymptotic expansion ln x - 1/(2x) - sum_k B_2k / (2k x^2k) through B_16.
 __device__ double dg_digamma(double x)
 {
-    double shift = 0.0;
-    while (x < 10.0) { shift += 1.0 / x; x += 1.0; }
-    const double t = 1.0 / (x * x);
+    // shift = sum 1/(x + i) accumulated as one fraction num/den; one division
+    // gives both shift and 1/x
+    double num = 0.0, den = 1.0;
+    while (x < 10.0) { num = fma(num, x, den); den *= x; x += 1.0; }
+    const double r = 1.0 / (den * x);
+    const double shift = num * x * r, ix = den * r;
+    const double t = ix * ix;
     // B2/2, B4/4, ..., B16/16
     const double c1 = 1.0 / 12.0, c2 = -1.0 / 120.0, c3 = 1.0 / 252.0, c4 = -1.0 / 240.0;
     const double c5 = 1.0 / 132.0, c6 = -691.0 / 32760.0, c7 = 1.0 / 12.0, c8 = -3617.0 / 8160.0;
     double p = c8;
     p = fma(p, t, c7); p = fma(p, t, c6); p = fma(p, t, c5); p = fma(p, t, c4);
     p = fma(p, t, c3); p = fma(p, t, c2); p = fma(p, t, c1);
-    return log(x) - 0.5 / x - p * t - shift;
+    return log(x) - 0.5 * ix - p * t - shift;
 }
 
-// psi_6(a) = sum_{i=0..5} psi(a - i/2): two series evaluations (at a and
-// a - 1/2) and the recurrence psi(x - 1) = psi(x) - 1/(x - 1) for the rest.
+// psi_6(a) = sum_{i=0..5} psi(a - i/2): two series evaluations (at x = a and
+// x = a - 1/2) and the recurrence psi(x - 1) = psi(x) - 1/(x - 1), i.e.
+// psi(x) + psi(x-1) + psi(x-2) = 3 psi(x) - (3x - 5) / ((x - 1)(x - 2)).
 __device__ double mv_digamma6(double a)
 {
     double s = 0.0;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const double x = a - 0.5 * h;
-        double p = dg_digamma(x);
-        s += p;
-        p -= 1.0 / (x - 1.0); s += p;     // psi(x - 1)
-        p -= 1.0 / (x - 2.0); s += p;     // psi(x - 2)
+        s += 3.0 * dg_digamma(x) - (3.0 * x - 5.0) / ((x - 1.0) * (x - 2.0));
     }
     return s;
 }
 // ln Gamma_6(a) = 7.5 ln pi + sum_{i=0..5} lnGamma(a - i/2), with
-// lnGamma(x - 1) = lnGamma(x) - ln(x - 1).
+// lnGamma(x - 1) = lnGamma(x) - ln(x - 1): per half-step x,
+// 3 lnGamma(x) - ln((x - 1)^2 (x - 2)).
 __device__ double mv_lgamma6(double a)
 {
     double s = 7.5 * kLnPi;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const double x = a - 0.5 * h;
-        double g = lgamma(x);
-        s += g;
-        g -= log(x - 1.0); s += g;
-        g -= log(x - 2.0); s += g;
+        s += 3.0 * lgamma(x) - log((x - 1.0) * (x - 1.0) * (x - 2.0));
     }
     return s;
 }
@@ -72,19 +72,20 @@ __device__ double mv_lgamma6(double a)
 // Largest eigenvalue of a symmetric 3x3 matrix (a00, a01, a02, a11, a12,
 // a22) by the trigonometric solution of its characteristic cubic (Smith 1961):
 // q = tr/3, p = sqrt(tr((A - qI)^2)/6), r = det((A - qI)/p)/2,
-// lambda_max = q + 2 p cos(acos(r)/3).
-__device__ double sym3_max_eig(double a00, double a01, double a02, double a11, double a12, double a22)
+// lambda_max = q + 2 p cos(acos(r)/3).  In FP32: the result is within a few
+// 1e-6 of |A| >= lambda_max; callers inflate it by 1e-4.
+__device__ float sym3_max_eig(float a00, float a01, float a02, float a11, float a12, float a22)
 {
-    const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
-    if (p1 == 0.0) return fmax(a00, fmax(a11, a22));
-    const double q = (a00 + a11 + a22) / 3.0;
-    const double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
-    const double p = sqrt((b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1) / 6.0);
-    const double ip = 1.0 / p;
-    const double c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
-    const double r = 0.5 * (c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02));
-    const double phi = acos(fmin(1.0, fmax(-1.0, r))) / 3.0;
-    return q + 2.0 * p * cos(phi);
+    const float p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    if (p1 == 0.f) return fmaxf(a00, fmaxf(a11, a22));
+    const float q = (a00 + a11 + a22) * (1.f / 3.f);
+    const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    const float p = sqrtf((b00 * b00 + b11 * b11 + b22 * b22 + 2.f * p1) * (1.f / 6.f));
+    const float ip = 1.f / p;
+    const float c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+    const float r = 0.5f * (c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02));
+    const float phi = acosf(fminf(1.f, fmaxf(-1.f, r))) * (1.f / 3.f);
+    return q + 2.f * p * cosf(phi);
 }
 
 // Posterior parameters from prior and statistics; A is the full symmetric W^-1.
@@ -95,8 +96,9 @@ __device__ void nw_from_stats(const MstepParams &P, const double *m0, const doub
     alpha = P.alpha0 + N;
     beta = P.beta0 + N;
     nu = P.nu0 + N;
+    const double ib = 1.0 / beta;
 #pragma unroll
-    for (int i = 0; i < 6; i++) m[i] = (P.beta0 * m0[i] + s[1 + i]) / beta;
+    for (int i = 0; i < 6; i++) m[i] = (P.beta0 * m0[i] + s[1 + i]) * ib;
 #pragma unroll
     for (int i = 0; i < 6; i++)
 #pragma unroll
@@ -120,9 +122,10 @@ __device__ bool chol6(const double A[36], double L[36])
 #pragma unroll
         for (int k = 0; k < j; k++) d -= L[j * 6 + k] * L[j * 6 + k];
         ok = ok && (d > 0.0);
-        d = sqrt(fmax(d, 1e-300));
+        d = fmax(d, 1e-300);
+        const double inv = rsqrt(d);
+        d *= inv;
         L[j * 6 + j] = d;
-        const double inv = 1.0 / d;
 #pragma unroll
         for (int i = j + 1; i < 6; i++) {
             double t = A[i * 6 + j];
@@ -140,14 +143,15 @@ __device__ void trinv6(const double L[36], double Li[36])
 #pragma unroll
     for (int i = 0; i < 36; i++) Li[i] = 0.0;
 #pragma unroll
+    for (int c = 0; c < 6; c++) Li[c * 6 + c] = 1.0 / L[c * 6 + c];
+#pragma unroll
     for (int c = 0; c < 6; c++) {
-        Li[c * 6 + c] = 1.0 / L[c * 6 + c];
 #pragma unroll
         for (int i = c + 1; i < 6; i++) {
             double t = 0.0;
 #pragma unroll
             for (int k = c; k < i; k++) t += L[i * 6 + k] * Li[k * 6 + c];
-            Li[i * 6 + c] = -t / L[i * 6 + i];
+            Li[i * 6 + c] = -t * Li[i * 6 + i];
         }
     }
 }
@@ -180,17 +184,32 @@ __device__ void block_sums4(double v0, double v1, double v2, double v3, double *
 // dS == nullptr: the posterior is the effective prior (frame start): write its
 // E-step record and the prior cache; KL terms are zero.  Otherwise: the
 // posterior prior0 (+) (S_past + dS), its record, and KL against the cache.
+//
+// Threads run over record positions p (component k = kperm[p]), so that
+// spatial neighbours share a warp.  A component whose frame statistics are
+// all exactly zero has q = p bit for bit: when its record already holds p
+// (flag cache[33], set by the frame-start call and by any call that wrote p),
+// nothing is recomputed and its KL term is exactly zero.
 __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__restrict__ m0,
                                                const double *__restrict__ Spast,
                                                const double *__restrict__ dS,
-                                               const int *__restrict__ kinv,
+                                               const int *__restrict__ kperm,
                                                double *__restrict__ rec, float *__restrict__ rec32,
                                                double *__restrict__ pc, double *__restrict__ bpart,
                                                int *__restrict__ flags)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pos = blockIdx.x * blockDim.x + threadIdx.x;
     double kl = 0.0, aq = 0.0, ap = 0.0, dn = 0.0;
-    if (k < P.K) {
+    const int k = pos < P.K ? (kperm ? kperm[pos] : pos) : 0;
+    bool zero = false;
+    if (pos < P.K && dS) {
+        zero = true;
+#pragma unroll
+        for (int f = 0; f < 28; f++) zero = zero && (dS[(size_t)k * 28 + f] == 0.0);
+        zero = zero && (pc[(size_t)k * kPC + 33] != 0.0);
+        if (zero) { aq = ap = pc[(size_t)k * kPC]; }
+    }
+    if (pos < P.K && !zero) {
         double st[28], m0k[6];
 #pragma unroll
         for (int f = 0; f < 28; f++) st[f] = Spast[(size_t)k * 28 + f] + (dS ? dS[(size_t)k * 28 + f] : 0.0);
@@ -201,16 +220,16 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
         double Lq[36], Li[36];
         const bool ok = chol6(Aq, Lq);
         if (!ok) atomicCAS(&flags[FL_NONPD], 0, k + 1);
-        double ldq = 0.0;   // ln|W^-1|
+        double dprod = 1.0;   // ln|W^-1| = 2 ln prod_i L_ii
 #pragma unroll
-        for (int i = 0; i < 6; i++) ldq += 2.0 * log(Lq[i * 6 + i]);
+        for (int i = 0; i < 6; i++) dprod *= Lq[i * 6 + i];
+        const double ldq = 2.0 * log(dprod);
         trinv6(Lq, Li);
 
         // E-step record: quad = nu |L^-1 (x - m)|^2 = |M (x - m)|^2.
         const double sn = sqrt(nq);
-        const size_t pos = kinv ? (size_t)kinv[k] : (size_t)k;   // record position (processing order)
-        double *r = rec + pos * VBGS_REC;
-        float *r32 = rec32 + pos * VBGS_REC;
+        double *r = rec + (size_t)pos * VBGS_REC;
+        float *r32 = rec32 + (size_t)pos * VBGS_REC;
         const float s2 = 1.2011224087864498f;   // sqrt(log2 e): FP32 record in log2 units
 #pragma unroll
         for (int i = 0; i < 6; i++) { r[i] = mq[i]; r32[i] = (float)mq[i]; }
@@ -230,20 +249,25 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
         r32[27] = (float)(c * 1.4426950408889634);
 #pragma unroll
         for (int i = 28; i < 32; i++) { r[i] = 0.0; r32[i] = 0.f; }
-        // For the proposal certificate: lower bounds (log2 units) of the
-        // smallest eigenvalue of the marginal precision of the position block
-        // and of the colour block.  Minimising (x - m)^T nu W (x - m) over the
-        // colour part leaves the position part's quadratic form in the inverse
-        // of its covariance block (W^-1)_pp / nu, whose smallest eigenvalue is
-        // nu / lambda_max((W^-1)_pp); same for colour.
-        // (exact largest eigenvalue of each 3 x 3 block, shrunk by 1e-6 so
-        // that rounding keeps the bound below the true smallest eigenvalue)
-        const double lpp = sym3_max_eig(Aq[0], Aq[1], Aq[2], Aq[7], Aq[8], Aq[14]);
-        const double lcc = sym3_max_eig(Aq[21], Aq[22], Aq[23], Aq[28], Aq[29], Aq[35]);
-        r32[28] = (float)(1.4426950408889634 * (1.0 - 1e-6) * nq / lpp);
-        r32[29] = (float)(1.4426950408889634 * (1.0 - 1e-6) * nq / lcc);
-        // and of the full precision: lambda_min(nu W) >= nu / tr(W^-1)
-        r32[30] = (float)(1.4426950408889634 * nq / (Aq[0] + Aq[7] + Aq[14] + Aq[21] + Aq[28] + Aq[35]));
+        if (P.want_bounds) {
+            // For the proposal certificate: lower bounds (log2 units) of the
+            // smallest eigenvalue of the marginal precision of the position
+            // block and of the colour block.  Minimising (x - m)^T nu W (x - m)
+            // over the colour part leaves the position part's quadratic form
+            // in the inverse of its covariance block (W^-1)_pp / nu, whose
+            // smallest eigenvalue is nu / lambda_max((W^-1)_pp); same for
+            // colour.  (largest eigenvalue of each 3 x 3 block in FP32,
+            // inflated by 1e-4 so the bound stays below the exact one)
+            const float lpp = sym3_max_eig((float)Aq[0], (float)Aq[1], (float)Aq[2], (float)Aq[7], (float)Aq[8],
+                                           (float)Aq[14]);
+            const float lcc = sym3_max_eig((float)Aq[21], (float)Aq[22], (float)Aq[23], (float)Aq[28],
+                                           (float)Aq[29], (float)Aq[35]);
+            r32[28] = (float)(1.4426950408889634 * (1.0 - 1e-6) * nq / ((double)lpp * (1.0 + 1e-4)));
+            r32[29] = (float)(1.4426950408889634 * (1.0 - 1e-6) * nq / ((double)lcc * (1.0 + 1e-4)));
+            // and of the full precision: lambda_min(nu W) >= nu / tr(W^-1)
+            r32[30] = (float)(1.4426950408889634 * (1.0 - 1e-6) * nq /
+                              (Aq[0] + Aq[7] + Aq[14] + Aq[21] + Aq[28] + Aq[35]));
+        }
 
         double *cache = pc + (size_t)k * kPC;
         if (!dS) {
@@ -258,8 +282,15 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
             cache[30] = ldq;
             cache[31] = mv_lgamma6(0.5 * nq);
             cache[32] = lgamma(aq);
+            cache[33] = 1.0;   // the record holds the effective prior
             ap = aq;
         } else {
+            // the record now holds the prior again only if this frame's
+            // statistics of the component are all zero
+            bool z = true;
+#pragma unroll
+            for (int f = 0; f < 28; f++) z = z && (dS[(size_t)k * 28 + f] == 0.0);
+            cache[33] = z ? 1.0 : 0.0;
             // KL(NW_q || NW_p) against the cached effective prior.
             ap = cache[0];
             const double bp = cache[1], np = cache[2], ldp = cache[30];
@@ -279,17 +310,17 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
                 for (int j = 0; j <= i; j++) t += Li[i * 6 + j] * (mq[j] - cache[3 + j]);
                 maha += t * t;
             }
-            // tr(W_p^-1 W_q) with W_q = Li^T Li: sum_i (Li Ap Li^T)_ii
-            //   = sum_i sum_{l <= i} (Li Ap)_il Li_il.
+            // tr(W_p^-1 W_q) = sum_ij (W_p^-1)_ij (W_q)_ij with W_q = Li^T Li,
+            // (W_q)_ij = sum_{l >= max(i, j)} Li_li Li_lj.
             double tr = 0.0;
 #pragma unroll
             for (int i = 0; i < 6; i++)
 #pragma unroll
-                for (int l = 0; l <= i; l++) {
-                    double b = 0.0;
+                for (int j = 0; j <= i; j++) {
+                    double w = 0.0;
 #pragma unroll
-                    for (int j = 0; j <= i; j++) b += Li[i * 6 + j] * Ap[j * 6 + l];
-                    tr += b * Li[i * 6 + l];
+                    for (int l = i; l < 6; l++) w += Li[l * 6 + i] * Li[l * 6 + j];
+                    tr += (i == j ? 1.0 : 2.0) * Ap[i * 6 + j] * w;
                 }
             kl = 0.5 * (6.0 * bp / bq - 6.0 + bp * nq * maha + 6.0 * log(bq / bp));
             kl += 0.5 * (nq - np) * psi_nu - 3.0 * nq + 0.5 * nq * tr + 0.5 * np * (ldq - ldp) + cache[31] -
@@ -372,14 +403,14 @@ __global__ void k_stage(const double *__restrict__ src, int64_t N, double *__res
 size_t mstep_cache_doubles(int K) { return (size_t)K * kPC + (size_t)((K + 127) / 128) * 4; }
 
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
-                 const int *kinv, double *rec, float *rec32, double *cache, int *flags, double *scal,
+                 const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
                  cudaStream_t st, Prof *pf)
 {
     const int K = P.K;
     const int nb = (K + 127) / 128;
     double *bpart = cache + (size_t)K * kPC;
     pf->begin(VBGS_PROF_MSTEP, st);
-    k_mstep<<<nb, 128, 0, st>>>(P, m0, Spast, dS, kinv, rec, rec32, cache, bpart, flags);
+    k_mstep<<<nb, 128, 0, st>>>(P, m0, Spast, dS, kperm, rec, rec32, cache, bpart, flags);
     pf->end(st);
     pf->begin(VBGS_PROF_MSTEP, st);
     k_mstep_finalize<<<1, 1024, 0, st>>>(bpart, nb, scal);

@@ -153,28 +153,41 @@ static_assert(kCP % 4 == 0, "cluster records are staged as float4");
 
 // Upper bound of the largest eigenvalue of a symmetric positive definite 6 x 6
 // matrix (lower triangle, tri order): with B = S / tr(S),
-// lambda_max(B)^8 <= |B^8|_F, which overestimates by at most 6^(1/16).
+// lambda_max(B)^8 <= |B^8|_F, which overestimates by at most 6^(1/16).  The
+// three squarings run in FP32: B is positive semi-definite with |B| <= 1, so
+// each rounded product is within a relative 6 * 6 * 2^-24 of the exact one in
+// norm, the rounding of |B^8|_F stays below 2e-5 relative and its eighth root
+// below 3e-6; the result is inflated by 1e-4.
 __device__ double lmax_bound6(const double *S)
 {
-    double B[36], C[36];
     double t = 0.0;
     for (int i = 0; i < 6; i++) t += S[tri(i, i)];
     if (!(t > 0.0)) return INFINITY;
     const double it = 1.0 / t;
-    for (int i = 0; i < 6; i++)
-        for (int j = 0; j <= i; j++) B[i * 6 + j] = B[j * 6 + i] = S[tri(i, j)] * it;
+    float B[21], C[21];
+#pragma unroll
+    for (int q = 0; q < 21; q++) B[q] = (float)(S[q] * it);
+#pragma unroll
     for (int rep = 0; rep < 3; rep++) {   // B <- B^2, three times: B^8
+#pragma unroll
         for (int i = 0; i < 6; i++)
+#pragma unroll
             for (int j = 0; j <= i; j++) {
-                double v = 0.0;
-                for (int l = 0; l < 6; l++) v = fma(B[i * 6 + l], B[l * 6 + j], v);
-                C[i * 6 + j] = C[j * 6 + i] = v;
+                float v = 0.f;
+#pragma unroll
+                for (int l = 0; l < 6; l++)
+                    v = fmaf(B[i >= l ? tri(i, l) : tri(l, i)], B[l >= j ? tri(l, j) : tri(j, l)], v);
+                C[tri(i, j)] = v;
             }
-        for (int i = 0; i < 36; i++) B[i] = C[i];
+#pragma unroll
+        for (int q = 0; q < 21; q++) B[q] = C[q];
     }
     double f = 0.0;
-    for (int i = 0; i < 36; i++) f = fma(B[i], B[i], f);
-    return t * pow(sqrt(f), 0.125) * (1.0 + 1e-9);
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+#pragma unroll
+        for (int j = 0; j <= i; j++) f += (i == j ? 1.0 : 2.0) * (double)B[tri(i, j)] * (double)B[tri(i, j)];
+    return t * pow(sqrt(f), 0.125) * (1.0 + 1e-4);
 }
 
 // Cluster centre and metric: o = mean of the member means, P = the average
@@ -653,31 +666,6 @@ __global__ void k_mlp_inputs(const double *__restrict__ X, const int *__restrict
 // kMaxCand clusters.  exact[n] = 1 (bound still above the
 // threshold: the point takes the exact E-step), 2 (seeded audit sample), 0.
 // cand[n * kMaxCand + i]: candidate clusters, -1 padded.
-// One warp per point.  Lanes split the members of a cluster when scoring it
-// and split the clusters when evaluating the bound; (max, sum) pairs and the
-// bound are combined across the warp.
-__device__ __forceinline__ void warp_score_cluster(const float *__restrict__ rec32, const int *__restrict__ order,
-                                                   int b, int e, const float x[6], int lane, float &mx, float &s)
-{
-    for (int i = b + lane; i < e; i += 32) {
-        const float l = logit32(rec32 + (size_t)order[i] * VBGS_REC, x);
-        if (l > mx) { s = s * ex2a(mx - l) + 1.f; mx = l; }
-        else s += ex2a(l - mx);
-    }
-}
-
-__device__ __forceinline__ float warp_l2(float mx, float s)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float om = __shfl_xor_sync(0xffffffffu, mx, o), os = __shfl_xor_sync(0xffffffffu, s, o);
-        const float m = fmaxf(mx, om);
-        s = (m == -INFINITY) ? 0.f : s * ex2a(mx - m) + os * ex2a(om - m);
-        mx = m;
-    }
-    return mx + __log2f(s);
-}
-
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -691,82 +679,216 @@ __device__ __forceinline__ float warp_max(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_cand_pass1(const double *__restrict__ X, int64_t N,
-                                                    const float *__restrict__ rec32, const int *__restrict__ order,
-                                                    const int *__restrict__ cstart, const float *__restrict__ UB,
-                                                    const int *__restrict__ top, float thresh, uint32_t audit_seed,
-                                                    uint32_t audit_per_mille, double *__restrict__ lse_c,
-                                                    float *__restrict__ bound, int *__restrict__ exact,
-                                                    int *__restrict__ cand, unsigned long long *__restrict__ counters)
+// Candidate pass 1, in rounds.  Per point: the candidate clusters
+// cand[n][0 .. nc), of which slots [pend, nc) are not scored yet, and the
+// running (max, sum) of 2^logit over the scored candidates (log2 units).
+// A round scores the pending (cluster, point) pairs cluster-major (k_cand_score:
+// a CTA per (cluster, chunk of points), the cluster's member records in
+// shared memory, a thread per point) into per-slot partials, then k_cand_select
+// (a warp per point) merges them in slot order and evaluates the certificate:
+// while the bound mass of the other clusters exceeds thresh times the
+// candidates' mass, it adds the clusters with the largest bounds (up to
+// kAddMax per round, no more than the bound says are needed), which the next
+// round scores.  The last round's select writes the lse, the bound and the
+// point's status (0 proposal, 1 fallback, 2 seeded audit).
+constexpr int kAddMax = 8;
+constexpr int kPB = 128;   // points per work item of the cluster-major kernels
+
+__global__ void __launch_bounds__(256) k_cand_init(const int *__restrict__ top, int64_t N, int *__restrict__ cand,
+                                                   int *__restrict__ ncand, int *__restrict__ pend,
+                                                   float2 *__restrict__ run, float2 *__restrict__ part)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    for (int t = 0; t < kMaxCand; t++) {
+        cand[n * kMaxCand + t] = t < kTop ? top[n * kTop + t] : -1;
+        part[n * kMaxCand + t] = make_float2(-INFINITY, 0.f);
+    }
+    ncand[n] = kTop;
+    pend[n] = 0;
+    run[n] = make_float2(-INFINITY, 0.f);
+}
+
+// (cluster, point * 32 + slot) keys of the pending candidate slots (at most
+// kAddMax per point: the top 4, or one round's additions).
+__global__ void k_pend_keys(const int *__restrict__ cand, const int *__restrict__ ncand,
+                            const int *__restrict__ pend, int64_t N, unsigned int *__restrict__ key,
+                            int *__restrict__ val)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * kAddMax) return;
+    const int64_t n = i / kAddMax;
+    const int t = pend[n] + (int)(i % kAddMax);
+    const bool p = t < ncand[n];
+    key[i] = p ? (unsigned int)cand[n * kMaxCand + t] : (unsigned int)kG;
+    val[i] = (int)(n * kMaxCand + (p ? t : 0));
+}
+
+constexpr int kSM = 256;   // member records staged per pass of k_cand_score
+__global__ void __launch_bounds__(kPB) k_cand_score(const double *__restrict__ X, const float *__restrict__ rec32,
+                                                    const int *__restrict__ order, const int *__restrict__ cstart,
+                                                    const int *__restrict__ pstart, const int *__restrict__ plist,
+                                                    const int *__restrict__ item_start, float2 *__restrict__ part)
+{
+    __shared__ __align__(16) float sr[kSM * 28];
+    __shared__ int sg;
+    const int item = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = kG;   // largest g with item_start[g] <= item
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (item_start[mid] <= item) lo = mid; else hi = mid;
+        }
+        sg = lo;
+    }
+    __syncthreads();
+    const int g = sg;
+    const int c = item - item_start[g];
+    const int b = cstart[g], S = cstart[g + 1] - b;
+    const int p0 = pstart[g] + c * kPB, cnt = min(kPB, pstart[g + 1] - p0);
+    const int t = threadIdx.x;
+    const bool live = t < cnt;
+    const int v = live ? plist[p0 + t] : 0;
+    float x[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) x[q] = live ? (float)X[(int64_t)(v / kMaxCand) * VBGS_XS + q] : 0.f;
+    float mx = -INFINITY, sum = 0.f;
+    for (int m0 = 0; m0 < S; m0 += kSM) {
+        const int ms = min(kSM, S - m0);
+        __syncthreads();
+        for (int i = t; i < ms * 28; i += blockDim.x) {
+            const int mm = i / 28, f = i - mm * 28;
+            sr[i] = rec32[(size_t)order[b + m0 + mm] * VBGS_REC + f];
+        }
+        __syncthreads();
+        if (live)
+            for (int mm = 0; mm < ms; mm++) {
+                const float l = logit32(sr + mm * 28, x);
+                if (l > mx) { sum = sum * ex2a(mx - l) + 1.f; mx = l; }
+                else sum += ex2a(l - mx);
+            }
+    }
+    if (live) part[v] = make_float2(mx, sum);
+}
+
+__global__ void __launch_bounds__(256) k_cand_select(const float *__restrict__ UB, int64_t N,
+                                                     const int *__restrict__ cstart, float thresh, int final_round,
+                                                     uint32_t audit_seed, uint32_t audit_per_mille,
+                                                     int *__restrict__ cand, int *__restrict__ ncand,
+                                                     int *__restrict__ pend, float2 *__restrict__ run,
+                                                     float2 *__restrict__ part, double *__restrict__ lse_c,
+                                                     float *__restrict__ bound, int *__restrict__ exact,
+                                                     unsigned long long *__restrict__ counters)
 {
     const int lane = threadIdx.x & 31;
     const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (n >= N) return;
-    float x[6];
-#pragma unroll
-    for (int i = 0; i < 6; i++) x[i] = (float)X[n * VBGS_XS + i];
-    // lane l holds the bounds and the membership bits of clusters 32 j + l
+    int nc = ncand[n];
+    const int p = pend[n];
+    // candidate membership: lane l holds clusters 32 j + l
+    const int my = lane < nc ? cand[n * kMaxCand + lane] : -1;
+    uint32_t mine = 0u;
+    for (int t = 0; t < nc; t++) {
+        const int g = __shfl_sync(0xffffffffu, my, t);
+        if ((g & 31) == lane) mine |= 1u << (g >> 5);
+    }
+    // merge the new partials in slot order
+    float2 r = run[n];
+    float mx = r.x, s = r.y;
+    const float2 pp = (lane >= p && lane < nc) ? part[n * kMaxCand + lane] : make_float2(-INFINITY, 0.f);
+    for (int t = p; t < nc; t++) {
+        const float pm = __shfl_sync(0xffffffffu, pp.x, t), ps = __shfl_sync(0xffffffffu, pp.y, t);
+        if (pm == -INFINITY) continue;
+        if (pm > mx) { s = s * ex2a(mx - pm) + ps; mx = pm; }
+        else s += ps * ex2a(pm - mx);
+    }
+    const float l2 = (mx == -INFINITY) ? -INFINITY : mx + __log2f(s);
     float u[32];
 #pragma unroll
     for (int j = 0; j < 32; j++) u[j] = UB[n * kG + j * 32 + lane];
-    uint32_t mine = 0u;
-    int nc = 0;
-    float mx = -INFINITY, s = 0.f;
-    unsigned long long pairs = 0;
-    for (int t = 0; t < kTop; t++) {
-        const int g = top[n * kTop + t];
-        if ((g & 31) == lane) mine |= 1u << (g >> 5);
-        if (lane == 0) cand[n * kMaxCand + nc] = g;
-        nc++;
-        pairs += (unsigned long long)(cstart[g + 1] - cstart[g]);
-        warp_score_cluster(rec32, order, cstart[g], cstart[g + 1], x, lane, mx, s);
-    }
-    // Greedy expansion: while the bound mass of the non-candidate clusters,
-    // relative to the candidates' lse, exceeds the threshold, add the cluster
-    // with the largest bound (ties to the lower index) and score it exactly.
-    float mm = 0.f;
-    for (;;) {
-        const float l2 = warp_l2(mx, s);
-        float ls = 0.f, lb = -INFINITY;
-        int lj = -1;
+    float ls = 0.f;
 #pragma unroll
-        for (int j = 0; j < 32; j++) {
-            if (mine & (1u << j)) continue;
-            ls += ex2a(fminf(u[j] - l2, 64.f));
-            if (u[j] > lb) { lb = u[j]; lj = j; }
-        }
-        mm = warp_sum(ls);
-        if (mm <= thresh || nc == kMaxCand) break;
-        int bg = lj >= 0 ? lj * 32 + lane : 0x7fffffff;
+    for (int j = 0; j < 32; j++)
+        if (!(mine & (1u << j))) ls += ex2a(fminf(u[j] - l2, 64.f));
+    float mm = warp_sum(ls);
+    int added = 0;
+    unsigned long long new_pairs = 0;
+    if (!final_round) {
+        // add the largest-bound clusters while the remaining mass exceeds the
+        // threshold (each pick removes its term), at most kAddMax per round
+        float rest = mm;
+        while (rest > thresh && nc < kMaxCand && added < kAddMax) {
+            float lb = -INFINITY;
+            int lj = -1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, lb, o);
-            const int og = __shfl_xor_sync(0xffffffffu, bg, o);
-            if (ov > lb || (ov == lb && og < bg)) { lb = ov; bg = og; }
+            for (int j = 0; j < 32; j++)
+                if (!(mine & (1u << j)) && u[j] > lb) { lb = u[j]; lj = j; }
+            int bg = lj >= 0 ? lj * 32 + lane : 0x7fffffff;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, lb, o);
+                const int og = __shfl_xor_sync(0xffffffffu, bg, o);
+                if (ov > lb || (ov == lb && og < bg)) { lb = ov; bg = og; }
+            }
+            if (bg == 0x7fffffff || lb == -INFINITY) break;
+            if (lane == (bg & 31)) mine |= 1u << (bg >> 5);
+            if (lane == 0) {
+                cand[n * kMaxCand + nc] = bg;
+                part[n * kMaxCand + nc] = make_float2(-INFINITY, 0.f);
+            }
+            rest -= ex2a(fminf(lb - l2, 64.f));
+            new_pairs += (unsigned long long)(cstart[bg + 1] - cstart[bg]);
+            nc++;
+            added++;
         }
-        if (bg == 0x7fffffff || lb == -INFINITY) break;   // every remaining cluster is empty
-        const int g = bg;
-        if (lane == (g & 31)) mine |= 1u << (g >> 5);
-        if (lane == 0) cand[n * kMaxCand + nc] = g;
-        nc++;
-        pairs += (unsigned long long)(cstart[g + 1] - cstart[g]);
-        warp_score_cluster(rec32, order, cstart[g], cstart[g + 1], x, lane, mx, s);
     }
-    const float l2 = warp_l2(mx, s);
     if (lane == 0) {
-        for (int i = nc; i < kMaxCand; i++) cand[n * kMaxCand + i] = -1;
+        run[n] = make_float2(mx, s);
+        pend[n] = ncand[n];
+        ncand[n] = nc;
         bound[n] = mm;
-        // seeded audit sample: a hash of (seed, point index)
-        uint32_t h = audit_seed ^ (uint32_t)(n * 0x9E3779B9u);
-        h ^= h >> 16; h *= 0x7feb352du; h ^= h >> 15; h *= 0x846ca68bu; h ^= h >> 16;
-        const bool audit = (h % 1000u) < audit_per_mille;
-        const int ex = !(mm <= thresh) ? 1 : (audit ? 2 : 0);
-        exact[n] = ex;
         lse_c[n] = (double)l2 * 0.6931471805599453;   // natural units
-        atomicAdd(&counters[0], pairs);
-        if (ex == 1) atomicAdd(&counters[1], 1ull);
-        if (ex == 2) atomicAdd(&counters[2], 1ull);
-        atomicAdd(&counters[3], (unsigned long long)(nc - kTop));
+        if (added) atomicAdd(&counters[4], (unsigned long long)added);
+        atomicAdd(&counters[0], new_pairs);
+        if (!added) {
+            // seeded audit sample: a hash of (seed, point index)
+            uint32_t h = audit_seed ^ (uint32_t)(n * 0x9E3779B9u);
+            h ^= h >> 16; h *= 0x7feb352du; h ^= h >> 15; h *= 0x846ca68bu; h ^= h >> 16;
+            const bool audit = (h % 1000u) < audit_per_mille;
+            exact[n] = !(mm <= thresh) ? 1 : (audit ? 2 : 0);
+        }
+    }
+}
+
+// Final counts of the candidate pass: fallback / audit points, clusters
+// added beyond the proposal's top 4, and the scored pairs of the top 4.
+__global__ void __launch_bounds__(256) k_cand_count(const int *__restrict__ exact, const int *__restrict__ ncand,
+                                                    const int *__restrict__ cand, const int *__restrict__ cstart,
+                                                    int64_t N, unsigned long long *__restrict__ counters)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long fb = 0, au = 0, ad = 0, pr = 0;
+    if (n < N) {
+        fb = exact[n] == 1;
+        au = exact[n] == 2;
+        ad = (unsigned long long)(ncand[n] - kTop);
+        for (int t = 0; t < kTop; t++) {
+            const int g = cand[n * kMaxCand + t];
+            pr += (unsigned long long)(cstart[g + 1] - cstart[g]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fb += __shfl_xor_sync(0xffffffffu, fb, o);
+        au += __shfl_xor_sync(0xffffffffu, au, o);
+        ad += __shfl_xor_sync(0xffffffffu, ad, o);
+        pr += __shfl_xor_sync(0xffffffffu, pr, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&counters[1], fb);
+        atomicAdd(&counters[2], au);
+        atomicAdd(&counters[3], ad);
+        atomicAdd(&counters[0], pr);
     }
 }
 
@@ -792,7 +914,7 @@ __global__ void k_cand_keys(const int *__restrict__ cand, const int *__restrict_
     val[i] = (int)n;
 }
 
-// Candidate pass 2.  Work items are (cluster, chunk of up to kPB of the
+// Candidate pass 2.  Work items are (cluster, chunk of up to kPB2 of the
 // cluster's proposal points); item_start[g] and the partial base fbase[g]
 // come from one scan over the clusters.  An item's CTA stages its points in
 // shared memory; each thread owns a member component and accumulates
@@ -800,16 +922,15 @@ __global__ void k_cand_keys(const int *__restrict__ cand, const int *__restrict_
 // written as the item's partial.  A second kernel sums a member's partials
 // in item order (FP64, deterministic), shifts them to raw moments and adds
 // them to the component's frame statistics.
-constexpr int kPB = 128;
-
 __global__ void __launch_bounds__(1024) k_items(const int *__restrict__ pstart, const int *__restrict__ cstart,
-                                                int *__restrict__ item_start, long long *__restrict__ fbase)
+                                                int chunk, int *__restrict__ item_start,
+                                                long long *__restrict__ fbase)
 {
     __shared__ long long sa[kG], sb[kG];
     const int g = threadIdx.x;
     const int cnt = pstart[g + 1] - pstart[g];
     const int S = cstart[g + 1] - cstart[g];
-    const long long items = S > 0 ? (cnt + kPB - 1) / kPB : 0;
+    const long long items = S > 0 ? (cnt + chunk - 1) / chunk : 0;
     sa[g] = items;
     sb[g] = items * S;
     __syncthreads();
@@ -826,13 +947,15 @@ __global__ void __launch_bounds__(1024) k_items(const int *__restrict__ pstart, 
     if (g == 0) { item_start[0] = 0; fbase[0] = 0; }
 }
 
+constexpr int kPB2 = 512;   // points per work item of candidate pass 2
+
 __global__ void __launch_bounds__(64) k_cand_pass2(const double *__restrict__ X, const double *__restrict__ lse_c,
                                                    const float *__restrict__ rec32, const int *__restrict__ order,
                                                    const int *__restrict__ cstart, const int *__restrict__ pstart,
                                                    const int *__restrict__ plist, const int *__restrict__ item_start,
                                                    const long long *__restrict__ fbase, float *__restrict__ part)
 {
-    __shared__ float sp[kPB][8];
+    __shared__ float sp[kPB2][8];
     __shared__ int sg;
     const int item = blockIdx.x;
     if (threadIdx.x == 0) {
@@ -847,7 +970,7 @@ __global__ void __launch_bounds__(64) k_cand_pass2(const double *__restrict__ X,
     const int g = sg;
     const int c = item - item_start[g];
     const int b = cstart[g], S = cstart[g + 1] - b;
-    const int p0 = pstart[g] + c * kPB, cnt = min(kPB, pstart[g + 1] - p0);
+    const int p0 = pstart[g] + c * kPB2, cnt = min(kPB2, pstart[g + 1] - p0);
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         const int n = plist[p0 + t];
 #pragma unroll
@@ -1161,14 +1284,46 @@ void prop_inputs(const double *X, const int *rows, int64_t rstride, int64_t n, c
     if (n > 0) k_mlp_inputs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, rows, rstride, n, box, out);
 }
 
-int prop_cand_pass1(const double *X, int64_t N, const float *rec32, const int *order, const int *cstart,
-                    const float *UB, const int *top, float thresh, uint32_t seed, uint32_t audit_per_mille,
-                    double *lse_c, float *bound, int *exact, int *cand, unsigned long long *counters, cudaStream_t st)
+void prop_cand_init(const int *top, int64_t N, int *cand, int *ncand, int *pend, float2 *run, float2 *part,
+                    cudaStream_t st)
 {
-    k_cand_pass1<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(X, N, rec32, order, cstart, UB, top, thresh, seed,
-                                                                   audit_per_mille, lse_c, bound, exact, cand,
-                                                                   counters);
+    if (N > 0) k_cand_init<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(top, N, cand, ncand, pend, run, part);
+}
+
+int prop_pend_lists(const int *cand, const int *ncand, const int *pend, int64_t N, SortBuffers &sb,
+                    unsigned int *skey, int *plist, int *pstart, cudaStream_t st)
+{
+    const int64_t n = N * kAddMax;
+    k_pend_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, ncand, pend, N, sb.keys_in, sb.idx_in);
+    size_t bytes = sb.temp_bytes;
+    if (cub::DeviceRadixSort::SortPairs(sb.temp, bytes, sb.keys_in, skey, sb.idx_in, plist, (int)n, 0, 11, st) !=
+        cudaSuccess)
+        return -1;
+    k_list_bounds<<<(unsigned)((n + 256) / 256), 256, 0, st>>>(skey, n, pstart);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+void prop_cand_score(const double *X, const float *rec32, const int *order, const int *cstart, const int *pstart,
+                     const int *plist, const int *item_start, int n_items, float2 *part, cudaStream_t st)
+{
+    if (n_items > 0)
+        k_cand_score<<<(unsigned)n_items, kPB, 0, st>>>(X, rec32, order, cstart, pstart, plist, item_start, part);
+}
+
+void prop_cand_select(const float *UB, int64_t N, const int *cstart, float thresh, bool final_round, uint32_t seed,
+                      uint32_t audit_per_mille, int *cand, int *ncand, int *pend, float2 *run, float2 *part,
+                      double *lse_c, float *bound, int *exact, unsigned long long *counters, cudaStream_t st)
+{
+    if (N > 0)
+        k_cand_select<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(UB, N, cstart, thresh, final_round ? 1 : 0,
+                                                                          seed, audit_per_mille, cand, ncand, pend,
+                                                                          run, part, lse_c, bound, exact, counters);
+}
+
+void prop_cand_count(const int *exact, const int *ncand, const int *cand, const int *cstart, int64_t N,
+                     unsigned long long *counters, cudaStream_t st)
+{
+    if (N > 0) k_cand_count<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(exact, ncand, cand, cstart, N, counters);
 }
 
 void prop_gather_rows(const double *X, const int *rows, int64_t n, double *Xe, cudaStream_t st)
@@ -1189,9 +1344,10 @@ int prop_cand_lists(const int *cand, const int *exact, int64_t N, SortBuffers &s
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int prop_cand_items(const int *pstart, const int *cstart, int *item_start, long long *fbase, cudaStream_t st)
+int prop_cand_items(const int *pstart, const int *cstart, bool pass2, int *item_start, long long *fbase,
+                    cudaStream_t st)
 {
-    k_items<<<1, kG, 0, st>>>(pstart, cstart, item_start, fbase);
+    k_items<<<1, kG, 0, st>>>(pstart, cstart, pass2 ? kPB2 : kPB, item_start, fbase);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
