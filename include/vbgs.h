@@ -127,14 +127,16 @@ int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const double *con
                         const int64_t *N, int n_iters, double *elbo_traces);
 
 /* Pick the work decomposition of the tensor-core passes (pass-1 K-splits
- * and pass-2 CTAs per component tile) for this context's K and frames of N
+ * and the least number of 64-point chunks per pass-2 work item; pass 2 cuts
+ * every component tile's list of unskipped chunks into such items, one CTA
+ * each) for this context's K and frames of N
  * points, by timing 3 x 3 candidates on `points` (one E-step each; the model
  * state is unchanged).  With cache_path, the choice is read from / appended
  * to that text file keyed by form, rounded log2 N and K, and SM count.  The
  * CUDA-core forms have nothing to tune (returns VBGS_OK).  vbgs_get_tuning
  * reports the current choice (0 = automatic). */
 int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, const char *cache_path);
-int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_splits);
+int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_chunks);
 
 /* Learned proposal (VBGS_FLAG_PROPOSAL at vbgs_init).  A small MLP over the
  * point (x, y, z, r, g, b), 6 -> 128 -> 128 -> 1024 with ReLU, BF16-rounded

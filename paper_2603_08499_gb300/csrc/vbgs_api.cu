@@ -153,8 +153,8 @@ int ensure_capacity(vbgs_ctx *ctx, int64_t N)
         ctx->plan_cap = pneed;
     }
     size_t need = estep_cuda_core_scratch(std::max<int64_t>(N, 1), ctx->K, is_tc(ctx) ? VBGS_FP32 : ctx->precision);
-    if (is_tc(ctx))   // pass-1 partials of up to 64 K-splits
-        need = std::max(need, (size_t)64 * (size_t)std::max<int64_t>(N, 1) * 2);
+    if (is_tc(ctx))   // pass-1 partials of up to 64 K-splits; pass-2 item partials
+        need = std::max(need, std::max((size_t)64 * (size_t)std::max<int64_t>(N, 1) * 2, tc_pass2_part_doubles(ctx->K)));
     if (need > ctx->part_cap) {
         if ((rc = dalloc(ctx, &ctx->d_part, need))) return rc;
         ctx->part_cap = need;
@@ -935,7 +935,7 @@ extern "C" int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, con
     if ((rc = order_frame(ctx, N, true)) || (rc = run_mstep(ctx, nullptr))) return rc;
     const int a0 = tc_pass1_auto_splits(N, ctx->K, ctx->num_sms);
     const int p1c[3] = {a0, std::max(1, a0 / 2), a0 * 2};
-    const int p2c[3] = {1, 2, 4};
+    const int p2c[3] = {2, 4, 8};   // pass 2: least chunks per work item
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));

@@ -650,12 +650,78 @@ __global__ void __launch_bounds__(256) k_p2_plan(const float *__restrict__ tmax,
     if (t == 0) counts[j] = base_sh;
 }
 
+// Work items of pass 2: every tile's chunk list cut into items of at most C
+// consecutive entries, with C >= cmin chosen so that the items fit the
+// partial buffer (tcap items of 128 x 28 moments): sum_j ceil(n_j / C) <=
+// total / C + ntiles <= tcap.  item_start[j] is the first item of tile j
+// (exclusive scan); items are in tile order.  One block.
+constexpr int kItemCap = 2048;
+__global__ void __launch_bounds__(1024) k_p2_items(const int *__restrict__ counts, int ntiles, int64_t nchunks,
+                                                   int cmin, int tcap, int *__restrict__ item_start,
+                                                   int *__restrict__ item_tile, int *__restrict__ item_lo,
+                                                   int *__restrict__ item_hi, int *__restrict__ nitems)
+{
+    __shared__ long long red[32];
+    __shared__ int scan[1024];
+    __shared__ int carry_sh, C_sh;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    auto cnt = [&](int j) -> int { return counts ? counts[j] : (int)nchunks; };
+    long long tot = 0;
+    for (int j = t; j < ntiles; j += 1024) tot += cnt(j);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) red[w] = tot;
+    __syncthreads();
+    if (t == 0) {
+        long long s = 0;
+        for (int i = 0; i < 32; i++) s += red[i];
+        const long long room = tcap > ntiles ? tcap - ntiles : 1;
+        C_sh = (int)max((long long)cmin, (s + room - 1) / room);
+        carry_sh = 0;
+    }
+    __syncthreads();
+    const int C = C_sh;
+    for (int j0 = 0; j0 < ntiles; j0 += 1024) {
+        const int j = j0 + t;
+        const int nj = j < ntiles ? (cnt(j) + C - 1) / C : 0;
+        scan[t] = nj;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {   // inclusive Hillis-Steele scan
+            const int v = t >= o ? scan[t - o] : 0;
+            __syncthreads();
+            scan[t] += v;
+            __syncthreads();
+        }
+        const int start = carry_sh + scan[t] - nj;
+        if (j < ntiles) {
+            item_start[j] = start;
+            const int c = cnt(j);
+            for (int i = 0; i < nj; i++) {
+                item_tile[start + i] = j;
+                item_lo[start + i] = i * C;
+                item_hi[start + i] = min(c, (i + 1) * C);
+            }
+        }
+        __syncthreads();
+        if (t == 1023) carry_sh += scan[1023];
+        __syncthreads();
+    }
+    if (t == 0) {
+        item_start[ntiles] = carry_sh;
+        *nitems = carry_sh;
+    }
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__restrict__ X, const double *__restrict__ lse,
                                                             int64_t N, int K, const unsigned char *__restrict__ tiles,
-                                                            const float *__restrict__ hdr, int ntiles, int nsplit,
+                                                            const float *__restrict__ hdr, int ntiles,
                                                             const int *__restrict__ counts,
                                                             const int *__restrict__ list,
+                                                            const int *__restrict__ item_tile,
+                                                            const int *__restrict__ item_lo,
+                                                            const int *__restrict__ item_hi,
+                                                            const int *__restrict__ nitems,
                                                             double *__restrict__ part, int *__restrict__ flags,
                                                             unsigned long long *__restrict__ pairs)
 {
@@ -663,21 +729,13 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
     extern __shared__ unsigned char smem_raw[];
     Smem2 &S = *reinterpret_cast<Smem2 *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int j = blockIdx.x, split = blockIdx.y;
+    // this CTA's work item: list entries [ibeg, iend) of tile j (never empty);
+    // CTAs beyond the item count leave before any TMEM or barrier
+    const int item = blockIdx.x;
+    if (item >= *nitems) return;
+    const int j = item_tile[item];
     const int64_t nchunks = (N + kChunk2 - 1) / kChunk2;
-    // this CTA's share of the tile's chunk list: entries [ibeg, iend)
-    const int cnt_j = counts ? counts[j] : (int)nchunks;
-    const int per = (cnt_j + nsplit - 1) / nsplit;
-    const int ibeg = min(cnt_j, split * per), iend = min(cnt_j, ibeg + per);
-    if (ibeg >= iend) {
-        // nothing to evaluate: zero moments, no TMEM, no barriers
-        const int k = j * kCols + (int)threadIdx.x;
-        if (threadIdx.x < 128 && k < K) {
-            double *dst = part + ((size_t)split * K + k) * 28;
-            for (int i = 0; i < 28; i++) dst[i] = 0.0;
-        }
-        return;
-    }
+    const int ibeg = item_lo[item], iend = item_hi[item];
     // list entry i -> chunk index
     auto chunk_at = [&](int i) -> int64_t { return counts ? (int64_t)list[(size_t)j * nchunks + i] : (int64_t)i; };
     const int64_t cbeg = ibeg, cend = iend;   // iterate over list positions
@@ -830,7 +888,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
         }
         const int k = j * kCols + m;
         if (k < K) {
-            double *dst = part + ((size_t)split * K + k) * 28;
+            double *dst = part + ((size_t)item * kCols + m) * 28;
 #pragma unroll
             for (int i = 0; i < 28; i++) dst[i] = (double)st[i];
         }
@@ -917,25 +975,40 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
     }
 }
 
-// dS[kperm[p]] = sum over splits of the tile-frame moments of position p,
-// shifted to raw moments with x = o + s (.) x' (o, s of the position's tile):
+// dS[kperm[p]] = sum over the items of p's tile (in item order) of the
+// tile-frame moments of position p, shifted to raw moments with
+// x = o + s (.) x' (o, s of the position's tile):
 //   S1_i = N o_i + s_i S1'_i,
 //   S2_ij = N o_i o_j + o_i s_j S1'_j + s_i o_j S1'_i + s_i s_j S2'_ij.
-__global__ void k_reduce_splits_tile(const double *__restrict__ part, int nsplit, int K, const float *__restrict__ hdr,
-                                     const int *__restrict__ kperm, double *__restrict__ dS)
+// One CTA per (tile, 32 positions): warp w sums the items q = w, w + 4, ...
+// of the tile in order; the 4 warp sums are added in warp order.
+__global__ void __launch_bounds__(128) k_reduce_items(const double *__restrict__ part,
+                                                      const int *__restrict__ item_start, int K,
+                                                      const float *__restrict__ hdr, const int *__restrict__ kperm,
+                                                      double *__restrict__ dS)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= K) return;
-    const size_t n = (size_t)K * 28;
+    __shared__ double sh[3][32][29];
+    const int j = blockIdx.x >> 2, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int m = (blockIdx.x & 3) * 32 + lane;
+    const int p = j * kCols + m;
     double t[28];
 #pragma unroll
     for (int f = 0; f < 28; f++) t[f] = 0.0;
-    for (int q = 0; q < nsplit; q++) {
-        const double *src = part + (size_t)q * n + (size_t)p * 28;
+    if (p < K)
+        for (int q = item_start[j] + w; q < item_start[j + 1]; q += 4) {
+            const double *src = part + ((size_t)q * kCols + m) * 28;
 #pragma unroll
-        for (int f = 0; f < 28; f++) t[f] += src[f];
-    }
-    const float *h = hdr + (size_t)(p / kCols) * 32;
+            for (int f = 0; f < 28; f++) t[f] += src[f];
+        }
+    if (w > 0)
+#pragma unroll
+        for (int f = 0; f < 28; f++) sh[w - 1][lane][f] = t[f];
+    __syncthreads();
+    if (w != 0 || p >= K) return;
+    for (int q = 0; q < 3; q++)
+#pragma unroll
+        for (int f = 0; f < 28; f++) t[f] += sh[q][lane][f];
+    const float *h = hdr + (size_t)j * 32;
     double o[6], sc[6];
 #pragma unroll
     for (int i = 0; i < 6; i++) {
@@ -974,9 +1047,14 @@ int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles,
 }
 
 
+// Item capacity of pass 2: at least two items per tile.
+int tc_item_cap(int K) { return std::max(kItemCap, 2 * ((K + kCols - 1) / kCols)); }
+size_t tc_pass2_part_doubles(int K) { return (size_t)tc_item_cap(K) * kCols * 28; }
+
 size_t tc_plan_ints(int64_t N, int K)
 {
-    return (size_t)((K + kCols - 1) / kCols) * (size_t)(1 + (N + kChunk2 - 1) / kChunk2);
+    const size_t nt = (size_t)((K + kCols - 1) / kCols);
+    return nt * (size_t)(1 + (N + kChunk2 - 1) / kChunk2) + (nt + 1) + 3 * (size_t)tc_item_cap(K) + 1;
 }
 
 int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
@@ -987,31 +1065,36 @@ int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool b
     unsigned long long *pairs = pf->on ? pf->d_pairs : nullptr;
     const int ntiles = (K + kCols - 1) / kCols;
     const int64_t nchunks = (N + kChunk2 - 1) / kChunk2;
-    // with a work list most tiles hold a handful of chunks: two CTAs per tile
-    // share a long list; without one (no skipping) each CTA takes a range
-    int splits = tmax ? 2 : std::max(1, std::min<int>((int)std::min<int64_t>(nchunks, 64), (4 * num_sms + ntiles - 1) / ntiles));
-    if (splits_override > 0) splits = std::min<int>(splits_override, (int)std::max<int64_t>(1, nchunks));
-    while (splits > 1 && (size_t)splits * (size_t)K * 28 > part_cap_doubles) splits--;
-    if ((size_t)K * 28 > part_cap_doubles) return -2;
-    int *counts = nullptr, *list = nullptr;
-    if (tmax) {
-        counts = plan;
-        list = plan + ntiles;
-        pf->begin(VBGS_PROF_PASS2, st);
-        k_p2_plan<<<ntiles, 256, 0, st>>>(tmax, minlse, N, ntiles, counts, list);
-        pf->end(st);
-    }
+    // balanced work items: chunks of each tile's list, at least cmin per item
+    // (4 unless tuned), as many items as the partial buffer holds (at most
+    // kItemCap); one CTA per item slot
+    const int cmin = splits_override > 0 ? splits_override : 4;
+    const int icap = tc_item_cap(K);
+    const int tcap = (int)std::min<size_t>((size_t)icap, part_cap_doubles / ((size_t)kCols * 28));
+    if (tcap < ntiles + 1) return -2;
+    int *counts = plan, *list = plan + ntiles;
+    int *item_start = list + (size_t)ntiles * nchunks;
+    int *item_tile = item_start + ntiles + 1, *item_lo = item_tile + icap, *item_hi = item_lo + icap;
+    int *nitems = item_hi + icap;
+    pf->begin(VBGS_PROF_PASS2, st);
+    if (tmax) k_p2_plan<<<ntiles, 256, 0, st>>>(tmax, minlse, N, ntiles, counts, list);
+    k_p2_items<<<1, 1024, 0, st>>>(tmax ? counts : nullptr, ntiles, nchunks, cmin, tcap, item_start, item_tile,
+                                   item_lo, item_hi, nitems);
+    pf->end(st);
     const size_t smem = sizeof(Smem2) + 128;
     if (tc_set_attributes()) return -1;
-    dim3 grid(ntiles, splits);
     pf->begin(VBGS_PROF_PASS2, st);
-    if (bf16) k_pass2_tc<true><<<grid, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, splits, counts, list, part, flags, pairs);
-    else      k_pass2_tc<false><<<grid, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, splits, counts, list, part, flags, pairs);
+    if (bf16)
+        k_pass2_tc<true><<<tcap, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
+                                                         list, item_tile, item_lo, item_hi, nitems, part, flags, pairs);
+    else
+        k_pass2_tc<false><<<tcap, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
+                                                          list, item_tile, item_lo, item_hi, nitems, part, flags, pairs);
     pf->end(st);
     pf->begin(VBGS_PROF_REDUCE, st);
-    k_reduce_splits_tile<<<(K + 127) / 128, 128, 0, st>>>(part, splits, K, hdr, kperm, dS);
+    k_reduce_items<<<ntiles * 4, 128, 0, st>>>(part, item_start, K, hdr, kperm, dS);
     pf->end(st);
-    return cudaGetLastError() == cudaSuccess ? 2 : -1;
+    return cudaGetLastError() == cudaSuccess ? (tmax ? 4 : 3) : -1;
 }
 
 // K-splits of pass 1: many small CTAs (two resident per SM) that the hardware

@@ -161,6 +161,7 @@ size_t tc_hdr_floats(int K);
 size_t tc_tmax_floats(int64_t N, int K);
 int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, cudaStream_t st, Prof *pf);
 size_t tc_plan_ints(int64_t N, int K);
+size_t tc_pass2_part_doubles(int K);
 int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
