@@ -126,17 +126,18 @@ int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, dou
 int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const double *const *points,
                         const int64_t *N, int n_iters, double *elbo_traces);
 
-/* Pick the work decomposition of the tensor-core passes (pass-1 K-splits
- * and the least number of 64-point chunks per pass-2 work item; pass 2 cuts
- * every component tile's list of unskipped chunks into such items, one CTA
- * each) for this context's K and frames of N
+/* Pick the work decomposition of the tensor-core passes (the least number
+ * of component tiles per pass-1 work item and of 64-point chunks per pass-2
+ * work item; both passes cut their lists of tile pairs not ruled out by the
+ * skip bounds into such items, one CTA each) for this context's K and frames
+ * of N
  * points, by timing 3 x 3 candidates on `points` (one E-step each; the model
  * state is unchanged).  With cache_path, the choice is read from / appended
  * to that text file keyed by form, rounded log2 N and K, and SM count.  The
  * CUDA-core forms have nothing to tune (returns VBGS_OK).  vbgs_get_tuning
  * reports the current choice (0 = automatic). */
 int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, const char *cache_path);
-int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_chunks);
+int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_tiles, int *pass2_chunks);
 
 /* Learned proposal (VBGS_FLAG_PROPOSAL at vbgs_init).  A small MLP over the
  * point (x, y, z, r, g, b), 6 -> 128 -> 128 -> 1024 with ReLU, BF16-rounded
@@ -221,8 +222,10 @@ enum {
 int vbgs_profile_enable(vbgs_ctx *ctx, int on);
 int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset);
 /* Work counters of the profiled calls since the last reset: pairs scored by
- * pass 1 (every point against every component) and pairs pass 2 evaluated
- * (the ones its skip bound did not rule out).  Synchronises the stream. */
+ * pass 1 (every pair in the CUDA-core forms; in the tensor-core forms the
+ * pairs of the component tiles its certified bound did not rule out) and
+ * pairs pass 2 evaluated (the ones its skip bound did not rule out).
+ * Synchronises the stream. */
 int vbgs_profile_pairs(vbgs_ctx *ctx, int64_t *pass1_pairs, int64_t *pass2_pairs);
 const char *vbgs_profile_name(int i);
 

@@ -152,6 +152,13 @@ int ensure_capacity(vbgs_ctx *ctx, int64_t N)
         if ((rc = dalloc(ctx, &ctx->d_plan, pneed))) return rc;
         ctx->plan_cap = pneed;
     }
+    const size_t p1need = tc_p1plan_ints(std::max<int64_t>(N, 1), ctx->K);
+    if (is_tc(ctx) && p1need > ctx->p1plan_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_p1plan, p1need)) ||
+            (rc = dalloc(ctx, &ctx->d_p1ub, tc_p1ub_floats(std::max<int64_t>(N, 1), ctx->K))))
+            return rc;
+        ctx->p1plan_cap = p1need;
+    }
     size_t need = estep_cuda_core_scratch(std::max<int64_t>(N, 1), ctx->K, is_tc(ctx) ? VBGS_FP32 : ctx->precision);
     if (is_tc(ctx))   // pass-1 partials of up to 64 K-splits; pass-2 item partials
         need = std::max(need, std::max((size_t)64 * (size_t)std::max<int64_t>(N, 1) * 2, tc_pass2_part_doubles(ctx->K)));
@@ -235,7 +242,7 @@ int order_frame(vbgs_ctx *ctx, int64_t N, bool points)
 // Full E-step over N staged points X (N x 8) into lse (N) and ctx->d_dS.
 int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool want_stats)
 {
-    if (ctx->prof.on) ctx->prof.pass1_pairs += N * (int64_t)ctx->K;
+    if (ctx->prof.on && !is_tc(ctx)) ctx->prof.pass1_pairs += N * (int64_t)ctx->K;   // tensor-core pass 1 counts on the device
     if (N == 0) {
         CU(cudaMemsetAsync(ctx->d_scal + SC_SUM_LSE, 0, sizeof(double), ctx->stream));
         if (want_stats) CU(cudaMemsetAsync(ctx->d_dS, 0, sizeof(double) * ctx->K * VBGS_F, ctx->stream));
@@ -258,19 +265,20 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
     B.tmax = skip ? ctx->d_tmax : nullptr;
     B.minlse = skip ? ctx->d_minlse : nullptr;
     if (is_tc(ctx)) {
-        int splits = 1;
+        const int *item_start = nullptr;
         int l = launch_pass1_tc(B.X, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
-                                reinterpret_cast<double2 *>(ctx->d_part), ctx->part_cap, B.tmax, ctx->d_flags,
-                                ctx->num_sms, ctx->tune_p1, &splits, ctx->stream, &ctx->prof);
+                                ctx->d_rec32, reinterpret_cast<double2 *>(ctx->d_part), ctx->part_cap, B.tmax,
+                                ctx->d_p1plan, ctx->d_p1ub, ctx->d_flags, ctx->num_sms, ctx->tune_p1, &item_start,
+                                ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ctx->launches += l;
-        l = launch_lse_merge(reinterpret_cast<double2 *>(ctx->d_part), splits, N, lse, ctx->d_lse_part,
+        l = launch_lse_merge(reinterpret_cast<double2 *>(ctx->d_part), 0, N, item_start, lse, ctx->d_lse_part,
                              B.tmax ? ctx->d_minlse : nullptr, ctx->d_scal + SC_SUM_LSE, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "lse merge launch failed");
         ctx->launches += l;
         if (want_stats) {
             l = launch_pass2_tc(B.X, lse, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
-                                B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
+                                ctx->d_rec, B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
                                 ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->tune_p2, ctx->stream, &ctx->prof);
             if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
                                    cudaGetErrorString(cudaGetLastError()));
@@ -697,7 +705,8 @@ void free_all(vbgs_ctx *ctx)
                     ctx->d_pcache, ctx->d_scal, ctx->d_elbo,
                     ctx->d_flags, ctx->d_X, ctx->d_lse, ctx->d_lse_part, ctx->d_part,
                     ctx->d_kperm, ctx->d_kinv, ctx->d_pidx, ctx->d_Xs, ctx->d_tmax, ctx->d_minlse,
-                    ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp, ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_plan};
+                    ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp, ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_plan,
+                    ctx->d_p1plan, ctx->d_p1ub};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     {
@@ -933,8 +942,7 @@ extern "C" int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, con
     int rc;
     if ((rc = update_prepare(ctx, points, N, 1))) return rc;
     if ((rc = order_frame(ctx, N, true)) || (rc = run_mstep(ctx, nullptr))) return rc;
-    const int a0 = tc_pass1_auto_splits(N, ctx->K, ctx->num_sms);
-    const int p1c[3] = {a0, std::max(1, a0 / 2), a0 * 2};
+    const int p1c[3] = {2, 4, 8};   // pass 1: least component tiles per work item
     const int p2c[3] = {2, 4, 8};   // pass 2: least chunks per work item
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
@@ -1137,7 +1145,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     ctx->mp.beta0 = prior->beta0;
     ctx->mp.nu0 = prior->nu0;
     ctx->mp.K = K;
-    ctx->mp.want_bounds = (ctx->flags & VBGS_FLAG_PROPOSAL) ? 1 : 0;
+    ctx->mp.want_bounds = 1;   // eigenvalue bounds: pass-1 tile lists and the proposal certificate
     for (int i = 0; i < 36; i++) ctx->mp.W0inv[i] = W0inv[i];
     ctx->m0_h.assign(prior->m0, prior->m0 + (size_t)K * 6);
 
@@ -1326,8 +1334,8 @@ int vbgs_profile_enable(vbgs_ctx *ctx, int on)
     if (on && ctx->prof.pool.empty()) {
         ctx->prof.pool.resize(4096);
         for (auto &e : ctx->prof.pool) CU(cudaEventCreate(&e));
-        CU(cudaMalloc(&ctx->prof.d_pairs, sizeof(unsigned long long)));
-        CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, sizeof(unsigned long long), ctx->stream));
+        CU(cudaMalloc(&ctx->prof.d_pairs, 2 * sizeof(unsigned long long)));
+        CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, 2 * sizeof(unsigned long long), ctx->stream));
     }
     ctx->prof.on = on != 0;
     return VBGS_OK;
@@ -1342,7 +1350,7 @@ int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset)
         if (reset) { ctx->prof.ms[i] = 0; ctx->prof.n[i] = 0; }
     }
     if (reset && ctx->prof.d_pairs) {
-        CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, sizeof(unsigned long long), ctx->stream));
+        CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, 2 * sizeof(unsigned long long), ctx->stream));
         ctx->prof.pass1_pairs = 0;
     }
     return VBGS_OK;
@@ -1351,13 +1359,13 @@ int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset)
 int vbgs_profile_pairs(vbgs_ctx *ctx, int64_t *pass1_pairs, int64_t *pass2_pairs)
 {
     if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
-    unsigned long long p2 = 0;
+    unsigned long long p[2] = {0, 0};
     if (ctx->prof.d_pairs) {
-        CU(cudaMemcpyAsync(&p2, ctx->prof.d_pairs, sizeof p2, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaMemcpyAsync(p, ctx->prof.d_pairs, sizeof p, cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
     }
-    if (pass1_pairs) *pass1_pairs = ctx->prof.pass1_pairs;
-    if (pass2_pairs) *pass2_pairs = (int64_t)p2;
+    if (pass1_pairs) *pass1_pairs = ctx->prof.pass1_pairs + (int64_t)p[1];
+    if (pass2_pairs) *pass2_pairs = (int64_t)p[0];
     return VBGS_OK;
 }
 

@@ -143,19 +143,30 @@ __global__ void __launch_bounds__(kThreads) k_pass1(const double *__restrict__ X
 }
 
 // Merge the K-split partials into lse_n and per-block sums of lse (fixed order).
+// Without item_start the partials are split-major, part[j * N + n]; with it
+// they are per work item of 128 points, part[q * 128 + n % 128] for the items
+// q = item_start[n / 128] .. item_start[n / 128 + 1] - 1 of the point's tile.
 __global__ void __launch_bounds__(256) k_merge(const double2 *__restrict__ part, int nsplit, int64_t N,
-                                               double *__restrict__ lse, double *__restrict__ lse_part,
-                                               float *__restrict__ minlse)
+                                               const int *__restrict__ item_start, double *__restrict__ lse,
+                                               double *__restrict__ lse_part, float *__restrict__ minlse)
 {
     __shared__ double sh[8];
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
     if (n < N) {
+        size_t base = (size_t)n, stride = (size_t)N;
+        int cnt = nsplit;
+        if (item_start) {
+            const int64_t P = n >> 7;
+            base = (size_t)item_start[P] * 128 + (size_t)(n & 127);
+            stride = 128;
+            cnt = item_start[P + 1] - item_start[P];
+        }
         double M = -INFINITY;
-        for (int j = 0; j < nsplit; j++) M = fmax(M, part[(size_t)j * N + n].x);
+        for (int j = 0; j < cnt; j++) M = fmax(M, part[base + (size_t)j * stride].x);
         double s = 0.0;
-        for (int j = 0; j < nsplit; j++) {
-            double2 p = part[(size_t)j * N + n];
+        for (int j = 0; j < cnt; j++) {
+            double2 p = part[base + (size_t)j * stride];
             if (p.y > 0.0) s += p.y * exp(p.x - M);
         }
         v = M + log(s);
@@ -359,14 +370,14 @@ constexpr int kPPT32 = 2;
 
 } // namespace
 
-int launch_lse_merge(const double2 *part, int nsplit, int64_t N, double *lse, double *lse_part, float *minlse,
-                     double *sum_out, cudaStream_t st, Prof *pf)
+int launch_lse_merge(const double2 *part, int nsplit, int64_t N, const int *item_start, double *lse,
+                     double *lse_part, float *minlse, double *sum_out, cudaStream_t st, Prof *pf)
 {
     // 64-point blocks: the FP64 exp/log of the merge is latency bound, so
     // spread it over every SM
     const int mb = (int)((N + 63) / 64);
     pf->begin(VBGS_PROF_MERGE, st);
-    k_merge<<<mb, 64, 0, st>>>(part, nsplit, N, lse, lse_part, minlse);
+    k_merge<<<mb, 64, 0, st>>>(part, nsplit, N, item_start, lse, lse_part, minlse);
     pf->end(st);
     pf->begin(VBGS_PROF_MERGE, st);
     k_sum<<<1, 1024, 0, st>>>(lse_part, mb, sum_out);
@@ -420,7 +431,7 @@ int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats
     pf->end(st);
     const int mb = (int)((B.N + 63) / 64);
     pf->begin(VBGS_PROF_MERGE, st);
-    k_merge<<<mb, 64, 0, st>>>(p1, pl.p1_splits, B.N, B.lse, B.lse_part, tmax ? B.minlse : nullptr);
+    k_merge<<<mb, 64, 0, st>>>(p1, pl.p1_splits, B.N, nullptr, B.lse, B.lse_part, tmax ? B.minlse : nullptr);
     pf->end(st);
     pf->begin(VBGS_PROF_MERGE, st);
     k_sum<<<1, 1024, 0, st>>>(B.lse_part, mb, B.scal + SC_SUM_LSE);
@@ -575,7 +586,7 @@ extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N
     dim3 g1(pl.p1_blocks, pl.p1_splits);
     if (f64) k_pass1<double, kPPT64><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec, K, pl.kps, p1, nullptr);
     else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec32, K, pl.kps, p1, nullptr);
-    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, lse_out, base + o_lsep, nullptr);
+    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, nullptr, lse_out, base + o_lsep, nullptr);
     k_sum<<<1, 1024, 0, st>>>(base + o_lsep, mb, scal + SC_SUM_LSE);
     dim3 g2(pl.p2_tiles, pl.p2_splits);
     if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part, nullptr, nullptr, 1, 1, nullptr);

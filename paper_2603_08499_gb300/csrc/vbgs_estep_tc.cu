@@ -216,16 +216,28 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
 #pragma unroll
     for (int i = 0; i < 6; i++) m[i] = r[i];
     const int nvalid = min(kCols, K - j * kCols);
-    // frame origin: mean of the tile's means
+    // frame origin: precision-weighted mean of the tile's means (weight
+    // tr(nu W) = |M|_F^2), so the tightest components sit near the origin
+    double wk = 0.0;
+    if (valid)
+#pragma unroll
+        for (int q = 0; q < 21; q++) wk += r[6 + q] * r[6 + q];
+    __shared__ double wred[4];
+    {
+        double v = wk;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) wred[w] = v;
+    }
 #pragma unroll
     for (int i = 0; i < 6; i++) {
-        double v = valid ? m[i] : 0.0;
+        double v = valid ? wk * m[i] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[i][w] = v;
     }
     __syncthreads();
-    if (t < 6) frame[t] = (red[t][0] + red[t][1] + red[t][2] + red[t][3]) / nvalid;
+    if (t < 6) frame[t] = (red[t][0] + red[t][1] + red[t][2] + red[t][3]) / (wred[0] + wred[1] + wred[2] + wred[3]);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < 6; i++) {
@@ -325,17 +337,29 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
 template <bool BF16>
 __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__restrict__ X, int64_t N, int K,
                                                             const unsigned char *__restrict__ tiles,
-                                                            const float *__restrict__ hdr, int ntiles, int tps,
+                                                            const float *__restrict__ hdr, int ntiles,
+                                                            const int *__restrict__ list,
+                                                            const int *__restrict__ item_tile,
+                                                            const int *__restrict__ item_lo,
+                                                            const int *__restrict__ item_hi,
+                                                            const int *__restrict__ nitems,
                                                             double2 *__restrict__ part, float *__restrict__ tmax,
-                                                            int *__restrict__ flags)
+                                                            int *__restrict__ flags,
+                                                            unsigned long long *__restrict__ pairs)
 {
     using HT = typename H<BF16>::T;
     extern __shared__ unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int split = blockIdx.y;
-    const int j0 = split * tps;
-    const int nt = max(0, min(ntiles, j0 + tps) - j0);
+    // this CTA's work item: point tile P, entries [lo, hi) of its component-tile
+    // list (all tiles in order without a list); slots beyond the item count
+    // leave before any TMEM or barrier
+    const int item = blockIdx.x;
+    if (item >= *nitems) return;
+    const int P = item_tile[item];
+    const int lo = item_lo[item];
+    const int nt = item_hi[item] - lo;
+    auto tile_at = [&](int jj) -> int { return list ? list[(size_t)P * ntiles + lo + jj] : lo + jj; };
 
     if (tid == 0) {
         for (int i = 0; i < kStagesB; i++) { mbar_init(&S.bar_bfull[i], 1); mbar_init(&S.bar_bfree[i], 1); }
@@ -357,7 +381,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__rest
     if (warp < 4) {
         // ---------------- feature builders + online log-sum-exp ----------------
         const int row = warp * 32 + lane;
-        const int64_t n = (int64_t)blockIdx.x * kRows + row;
+        const int64_t n = (int64_t)P * kRows + row;
         const int64_t nn = n < N ? n : N - 1;
         float xh[6], xl[6];
 #pragma unroll
@@ -372,13 +396,13 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__rest
         float hn[18];
         auto load_hdr = [&](int jj) {
             if (jj < nt) {
-                const float4 *h4 = reinterpret_cast<const float4 *>(hdr + (size_t)(j0 + jj) * 32);
+                const float4 *h4 = reinterpret_cast<const float4 *>(hdr + (size_t)tile_at(jj) * 32);
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const float4 v = h4[q];
                     hn[4 * q] = v.x; hn[4 * q + 1] = v.y; hn[4 * q + 2] = v.z; hn[4 * q + 3] = v.w;
                 }
-                const float2 v = reinterpret_cast<const float2 *>(hdr + (size_t)(j0 + jj) * 32)[8];
+                const float2 v = reinterpret_cast<const float2 *>(hdr + (size_t)tile_at(jj) * 32)[8];
                 hn[16] = v.x; hn[17] = v.y;
             }
         };
@@ -419,11 +443,12 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__rest
         for (int jj = 0; jj < nt && ok; jj++) {
             if (jj + 1 < nt) build_A(jj + 1);
             const int s = jj & 1;
-            const float scale = hdr[(size_t)(j0 + jj) * 32 + 18];
+            const int tj = tile_at(jj);
+            const float scale = hdr[(size_t)tj * 32 + 18];
             ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_mma[s], (uint32_t)((jj >> 1) & 1), flags));
             if (!ok) break;
             fence_after();
-            const int nvalid = min(kCols, K - (j0 + jj) * kCols);   // columns past K are padding
+            const int nvalid = min(kCols, K - tj * kCols);   // columns past K are padding
             float tmx = -INFINITY;
             const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kCols);
 #pragma unroll 1
@@ -469,10 +494,15 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__rest
             // largest logit of this 32-row block and component tile (natural units)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tmx = fmaxf(tmx, __shfl_xor_sync(0xffffffffu, tmx, o));
-            const int64_t rb = (int64_t)blockIdx.x * 4 + warp;
-            if (lane == 0 && tmax && rb * 32 < N) tmax[rb * ntiles + (j0 + jj)] = tmx * 0.6931471805599453f;
+            const int64_t rb = (int64_t)P * 4 + warp;
+            if (lane == 0 && tmax && rb * 32 < N) tmax[rb * ntiles + tj] = tmx * 0.6931471805599453f;
         }
-        if (n < N) part[(size_t)split * N + n] = make_double2((double)mrun * 0.6931471805599453, (double)srun);
+        if (n < N) part[(size_t)item * kRows + row] = make_double2((double)mrun * 0.6931471805599453, (double)srun);
+        if (pairs && tid == 0) {
+            unsigned long long cols = 0;
+            for (int jj = 0; jj < nt; jj++) cols += (unsigned long long)min(kCols, K - tile_at(jj) * kCols);
+            atomicAdd(pairs, cols * (unsigned long long)min((int64_t)kRows, N - (int64_t)P * kRows));
+        }
     } else if (warp == 4 && lane == 0) {
         // ---------------- copy + MMA issuer ----------------
         constexpr uint32_t idesc = idesc_f16<BF16>();
@@ -481,7 +511,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__rest
         const int pre = min(nt, kStagesB - 1);
         for (int jj = 0; jj < pre; jj++) {
             mbar_expect_tx(&S.bar_bfull[jj], kTileBytes);
-            bulk_g2s(S.B[jj], tiles + (size_t)(j0 + jj) * kTileBytes, kTileBytes, &S.bar_bfull[jj]);
+            bulk_g2s(S.B[jj], tiles + (size_t)tile_at(jj) * kTileBytes, kTileBytes, &S.bar_bfull[jj]);
             n_loads = jj + 1;
         }
         for (int jj = 0; jj < nt && ok; jj++) {
@@ -513,7 +543,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__rest
                     if (!ok) break;
                 }
                 mbar_expect_tx(&S.bar_bfull[sn], kTileBytes);
-                bulk_g2s(S.B[sn], tiles + (size_t)(j0 + nxt) * kTileBytes, kTileBytes, &S.bar_bfull[sn]);
+                bulk_g2s(S.B[sn], tiles + (size_t)tile_at(nxt) * kTileBytes, kTileBytes, &S.bar_bfull[sn]);
                 n_loads = nxt + 1;
             }
         }
@@ -543,6 +573,183 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__rest
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Pass-1 tile lists.  For a point tile P (128 Morton-consecutive points, box
+// B_P) and a component k, every logit is bounded by the smallest-eigenvalue
+// bounds of the record (log2 units, floats 28-30: position Schur complement,
+// colour Schur complement, full precision):
+//   l_k(x) <= c_k - 1/2 max(lp d_p^2, lc d_c^2, la (d_p^2 + d_c^2)),
+// with d_p, d_c the distances of m_k to the position and colour boxes of P.
+// ub(P, j) is the largest over the components of tile j.  A lower bound of
+// every point's lse: the exact FP32 lse over the single tile with the largest
+// ub (the log-sum over a subset), less 1 + 1e-5 |lse| for its rounding.
+// Tiles with ub(P, j) < LB_P - 50 nats hold only pairs with r < e^-50 and are
+// not evaluated.  One CTA per point tile, thread = point.
+// ---------------------------------------------------------------------------
+constexpr float kSkipLog2 = 72.13475204444817f;   // 50 nats in log2 units
+
+__device__ __forceinline__ float logit32_rec(const float *__restrict__ r, const float x[6])
+{
+    float d[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) d[i] = x[i] - r[i];
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        float y = 0.f;
+#pragma unroll
+        for (int jx = 0; jx <= i; jx++) y = fmaf(r[6 + tri(i, jx)], d[jx], y);
+        q = fmaf(y, y, q);
+    }
+    return fmaf(-0.5f, q, r[27]);
+}
+
+// Bounding box (lo[6], hi[6]) of each point tile.
+__global__ void __launch_bounds__(128) k_p1_boxes(const double *__restrict__ X, int64_t N, float *__restrict__ boxes)
+{
+    __shared__ float sbox[2][6][4];
+    const int P = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int64_t n = (int64_t)P * kRows + t;
+    const int64_t nn = n < N ? n : (int64_t)P * kRows;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        float a = (float)X[nn * VBGS_XS + i], b = a;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if (lane == 0) { sbox[0][i][w] = a; sbox[1][i][w] = b; }
+    }
+    __syncthreads();
+    if (t < 6) {
+        boxes[(size_t)P * 12 + t] = fminf(fminf(sbox[0][t][0], sbox[0][t][1]), fminf(sbox[0][t][2], sbox[0][t][3]));
+        boxes[(size_t)P * 12 + 6 + t] = fmaxf(fmaxf(sbox[1][t][0], sbox[1][t][1]), fmaxf(sbox[1][t][2], sbox[1][t][3]));
+    }
+}
+
+// ub[P][j] for every point tile, one CTA per component tile j (thread =
+// component); point-tile boxes staged through shared memory 128 at a time.
+__global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, int ptiles, int K, int ntiles,
+                                               const float *__restrict__ rec32, float *__restrict__ ub)
+{
+    __shared__ float sb[kRows][12];
+    __shared__ float wm[kRows][4];
+    const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int k = j * kCols + t;
+    const bool valid = k < K;
+    float m[6], c2 = -INFINITY, lp = 0.f, lc = 0.f, la = 0.f;
+    const float *r = rec32 + (size_t)(valid ? k : 0) * VBGS_REC;
+#pragma unroll
+    for (int i = 0; i < 6; i++) m[i] = r[i];
+    if (valid) { c2 = r[27]; lp = r[28]; lc = r[29]; la = r[30]; }
+    for (int p0 = 0; p0 < ptiles; p0 += kRows) {
+        const int np = min(kRows, ptiles - p0);
+        __syncthreads();
+        for (int i = t; i < np * 12; i += kRows) sb[i / 12][i % 12] = boxes[(size_t)p0 * 12 + i];
+        __syncthreads();
+        for (int q = 0; q < np; q++) {
+            float dp = 0.f, dc = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const float o = fmaxf(fmaxf(sb[q][i] - m[i], m[i] - sb[q][6 + i]), 0.f);
+                dp = fmaf(o, o, dp);
+                const float oc = fmaxf(fmaxf(sb[q][3 + i] - m[3 + i], m[3 + i] - sb[q][9 + i]), 0.f);
+                dc = fmaf(oc, oc, dc);
+            }
+            float v = valid ? c2 - 0.5f * fmaxf(fmaxf(lp * dp, lc * dc), la * (dp + dc)) : -INFINITY;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) wm[q][w] = v;
+        }
+        __syncthreads();
+        if (t < np) ub[(size_t)(p0 + t) * ntiles + j] = fmaxf(fmaxf(wm[t][0], wm[t][1]), fmaxf(wm[t][2], wm[t][3]));
+    }
+}
+
+// Per point tile: the seed tile (largest ub, ties to the lower index), the
+// lower bound LB of every point's lse from its exact FP32 log-sum, and the
+// list of tiles with ub >= LB - 50 nats, in increasing order.
+__global__ void __launch_bounds__(128) k_p1_lists(const double *__restrict__ X, int64_t N, int K, int ntiles,
+                                                  const float *__restrict__ rec32, const float *__restrict__ ub,
+                                                  int *__restrict__ list, int *__restrict__ counts)
+{
+    __shared__ float sr[kCols * 28];
+    __shared__ float red[4];
+    __shared__ int redi[4];
+    __shared__ int wsum[4];
+    __shared__ int base_sh;
+    const int P = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const float *u = ub + (size_t)P * ntiles;
+    float bv = -INFINITY;
+    int bj = 0x7fffffff;
+    for (int j = t; j < ntiles; j += kRows)
+        if (u[j] > bv) { bv = u[j]; bj = j; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ov > bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; }
+    }
+    if (lane == 0) { red[w] = bv; redi[w] = bj; }
+    __syncthreads();
+    int js;
+    {
+        float v = -INFINITY;
+        int jx = 0x7fffffff;
+        for (int q = 0; q < 4; q++)
+            if (red[q] > v || (red[q] == v && redi[q] < jx)) { v = red[q]; jx = redi[q]; }
+        js = jx == 0x7fffffff ? 0 : jx;
+    }
+    const int ks = js * kCols, ns = min(kCols, K - ks);
+    for (int i = t; i < ns * 28; i += kRows) {
+        const int mm = i / 28, f = i - mm * 28;
+        sr[i] = rec32[(size_t)(ks + mm) * VBGS_REC + f];
+    }
+    const int64_t n = (int64_t)P * kRows + t;
+    const bool live = n < N;
+    float x[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) x[i] = (float)X[(live ? n : (int64_t)P * kRows) * VBGS_XS + i];
+    __syncthreads();
+    float mx = -INFINITY, sm = 0.f;
+    for (int mm = 0; mm < ns; mm++) {
+        const float l = logit32_rec(sr + mm * 28, x);
+        if (l > mx) { sm = sm * exp2f(mx - l) + 1.f; mx = l; }
+        else sm += exp2f(l - mx);
+    }
+    float lb = mx + log2f(sm);
+    lb = live ? lb - (1.f + 1e-5f * fabsf(lb)) : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lb = fminf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+    __syncthreads();
+    if (lane == 0) red[w] = lb;
+    if (t == 0) base_sh = 0;
+    __syncthreads();
+    const float LB = fminf(fminf(red[0], red[1]), fminf(red[2], red[3]));
+    for (int j0 = 0; j0 < ntiles; j0 += kRows) {
+        const int j = j0 + t;
+        const bool keep = j < ntiles && u[j] >= LB - kSkipLog2;
+        const unsigned bb = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wsum[w] = __popc(bb);
+        __syncthreads();
+        int off = base_sh;
+        for (int i = 0; i < w; i++) off += wsum[i];
+        off += __popc(bb & ((1u << lane) - 1u));
+        if (keep) list[(size_t)P * ntiles + off] = j;
+        __syncthreads();
+        if (t == 0) base_sh += wsum[0] + wsum[1] + wsum[2] + wsum[3];
+        __syncthreads();
+    }
+    if (t == 0) counts[P] = base_sh;
+}
+
+__global__ void k_fill_neg_inf(float *__restrict__ a, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = -INFINITY;
+}
 
 // ---------------------------------------------------------------------------
 // Pass 2 on the tensor cores: the fused statistics contraction of Eq. 3.
@@ -722,6 +929,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
                                                             const int *__restrict__ item_lo,
                                                             const int *__restrict__ item_hi,
                                                             const int *__restrict__ nitems,
+                                                            const double *__restrict__ rec,
                                                             double *__restrict__ part, int *__restrict__ flags,
                                                             unsigned long long *__restrict__ pairs)
 {
@@ -775,14 +983,22 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
         auto build = [&](int64_t c, int st) {
             // threads 0..63 write B1 (point-major), 64..127 write B2 (feature-major); both write lse2
             const int pt = tid & 63;
-            const int64_t n = chunk_at((int)c) * kChunk2 + pt;
+            const int64_t c0 = chunk_at((int)c) * kChunk2;
+            const int64_t n = c0 + pt;
             const int64_t nn = n < N ? n : N - 1;
             float d[6];
+            if (tid < 64) {
+                // logits: the tile's frame, like the coefficients
 #pragma unroll
-            for (int i = 0; i < 6; i++) {
-                const double v = X[nn * VBGS_XS + i];
-                const float xh = (float)v, xl = (float)(v - (double)xh);
-                d[i] = ((xh - hf[i]) + (xl - hf[6 + i])) * hf[12 + i];
+                for (int i = 0; i < 6; i++) {
+                    const double v = X[nn * VBGS_XS + i];
+                    const float xh = (float)v, xl = (float)(v - (double)xh);
+                    d[i] = ((xh - hf[i]) + (xl - hf[6 + i])) * hf[12 + i];
+                }
+            } else {
+                // statistics: the chunk's frame, origin at its first point
+#pragma unroll
+                for (int i = 0; i < 6; i++) d[i] = (float)(X[nn * VBGS_XS + i] - X[c0 * VBGS_XS + i]) * hf[12 + i];
             }
             float f[kFeat];
             f[0] = 1.f;
@@ -819,19 +1035,46 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
             fence_async_smem();
             mbar_arrive(&S.bar_bfull[st]);
         };
-        float st[kFeat];
+        // Statistics of component row m about its own mean m_k (FP32), from
+        // each chunk's moments about the chunk origin o_c (first point),
+        // delta = o_c - m_k, per-axis scale s of the features:
+        //   S1 += s S1' + N' delta,
+        //   S2_ab += s_a s_b S2'_ab + delta_a s_b S1'_b + s_a S1'_a delta_b + N' delta_a delta_b.
+        float st[28];
 #pragma unroll
-        for (int i = 0; i < kFeat; i++) st[i] = 0.f;
+        for (int i = 0; i < 28; i++) st[i] = 0.f;
+        float sc[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) sc[i] = 1.f / hf[12 + i];
+        const int kcomp = j * kCols + m;
+        const double *mrec = rec + (size_t)(kcomp < K ? kcomp : K - 1) * VBGS_REC;
+        int64_t stagepos[2] = {0, 0};
         auto add_d2 = [&](int stage) {
             uint32_t v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 128u + (uint32_t)(stage * kFeat), v);
             tmem_wait_ld();
+            const int64_t c0 = chunk_at((int)stagepos[stage]) * kChunk2;
+            float dl[6], s1[6];
 #pragma unroll
-            for (int i = 0; i < kFeat; i++) st[i] += __uint_as_float(v[i]);
+            for (int i = 0; i < 6; i++) dl[i] = (float)(X[c0 * VBGS_XS + i] - mrec[i]);
+            const float nn = __uint_as_float(v[0]);
+            st[0] += nn;
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                s1[i] = sc[i] * __uint_as_float(v[1 + i]);
+                st[1 + i] += fmaf(nn, dl[i], s1[i]);
+            }
+            int u = 7;
+#pragma unroll
+            for (int a = 0; a < 6; a++)
+#pragma unroll
+                for (int b = a; b < 6; b++, u++)
+                    st[u] += fmaf(sc[a] * sc[b], __uint_as_float(v[u]),
+                                  fmaf(dl[a], s1[b], fmaf(s1[a], dl[b], nn * dl[a] * dl[b])));
         };
         int64_t c = next_chunk(cbeg);
         int u = 0;
-        if (c < cend) build(c, 0);
+        if (c < cend) { build(c, 0); stagepos[0] = c; }
         while (c < cend && ok) {
             const int s = u & 1;
             if (u >= 1) {
@@ -843,7 +1086,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
                 add_d2((u + 1) & 1);
             }
             const int64_t cn = next_chunk(c + 1);
-            if (cn < cend) build(cn, (u + 1) & 1);
+            if (cn < cend) { build(cn, (u + 1) & 1); stagepos[(u + 1) & 1] = cn; }
             ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_d1full[s], (uint32_t)((u >> 1) & 1), flags));
             if (!ok) break;
             fence_after();
@@ -976,15 +1219,13 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
 }
 
 // dS[kperm[p]] = sum over the items of p's tile (in item order) of the
-// tile-frame moments of position p, shifted to raw moments with
-// x = o + s (.) x' (o, s of the position's tile):
-//   S1_i = N o_i + s_i S1'_i,
-//   S2_ij = N o_i o_j + o_i s_j S1'_j + s_i o_j S1'_i + s_i s_j S2'_ij.
+// moments of position p about its component's mean m (FP64 record), shifted
+// to raw moments: S1 = S1' + N m, S2 = S2' + m S1'^T + S1' m^T + N m m^T.
 // One CTA per (tile, 32 positions): warp w sums the items q = w, w + 4, ...
 // of the tile in order; the 4 warp sums are added in warp order.
 __global__ void __launch_bounds__(128) k_reduce_items(const double *__restrict__ part,
                                                       const int *__restrict__ item_start, int K,
-                                                      const float *__restrict__ hdr, const int *__restrict__ kperm,
+                                                      const double *__restrict__ rec, const int *__restrict__ kperm,
                                                       double *__restrict__ dS)
 {
     __shared__ double sh[3][32][29];
@@ -1008,23 +1249,18 @@ __global__ void __launch_bounds__(128) k_reduce_items(const double *__restrict__
     for (int q = 0; q < 3; q++)
 #pragma unroll
         for (int f = 0; f < 28; f++) t[f] += sh[q][lane][f];
-    const float *h = hdr + (size_t)j * 32;
-    double o[6], sc[6];
+    double mk[6];
 #pragma unroll
-    for (int i = 0; i < 6; i++) {
-        o[i] = (double)h[i] + (double)h[6 + i];
-        sc[i] = 1.0 / (double)h[12 + i];
-    }
+    for (int i = 0; i < 6; i++) mk[i] = rec[(size_t)p * VBGS_REC + i];
     double out[28];
     out[0] = t[0];
 #pragma unroll
-    for (int i = 0; i < 6; i++) out[1 + i] = t[0] * o[i] + sc[i] * t[1 + i];
+    for (int i = 0; i < 6; i++) out[1 + i] = t[1 + i] + t[0] * mk[i];
     int u = 7;
 #pragma unroll
     for (int a = 0; a < 6; a++)
 #pragma unroll
-        for (int b = a; b < 6; b++, u++)
-            out[u] = t[0] * o[a] * o[b] + o[a] * sc[b] * t[1 + b] + sc[a] * o[b] * t[1 + a] + sc[a] * sc[b] * t[u];
+        for (int b = a; b < 6; b++, u++) out[u] = t[u] + mk[a] * t[1 + b] + t[1 + a] * mk[b] + t[0] * mk[a] * mk[b];
     const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
 #pragma unroll
     for (int f = 0; f < 28; f++) dS[dst * 28 + f] = out[f];
@@ -1058,7 +1294,7 @@ size_t tc_plan_ints(int64_t N, int K)
 }
 
 int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
-                    const float *hdr, const float *tmax, const float *minlse, int *plan, double *part,
+                    const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
                     cudaStream_t st, Prof *pf)
 {
@@ -1086,13 +1322,15 @@ int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool b
     pf->begin(VBGS_PROF_PASS2, st);
     if (bf16)
         k_pass2_tc<true><<<tcap, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
-                                                         list, item_tile, item_lo, item_hi, nitems, part, flags, pairs);
+                                                         list, item_tile, item_lo, item_hi, nitems, rec, part, flags,
+                                                         pairs);
     else
         k_pass2_tc<false><<<tcap, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
-                                                          list, item_tile, item_lo, item_hi, nitems, part, flags, pairs);
+                                                          list, item_tile, item_lo, item_hi, nitems, rec, part, flags,
+                                                         pairs);
     pf->end(st);
     pf->begin(VBGS_PROF_REDUCE, st);
-    k_reduce_items<<<ntiles * 4, 128, 0, st>>>(part, item_start, K, hdr, kperm, dS);
+    k_reduce_items<<<ntiles * 4, 128, 0, st>>>(part, item_start, K, rec, kperm, dS);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? (tmax ? 4 : 3) : -1;
 }
@@ -1134,25 +1372,70 @@ int tc_set_attributes()
     return 0;
 }
 
+// Pass-1 work items: at most kItemCap1 + point tiles, so item partials of
+// 128 (max, sum) pairs fit next to the other scratch.
+constexpr int kItemCap1 = 2048;
+size_t tc_p1plan_ints(int64_t N, int K)
+{
+    const size_t pt = (size_t)((N + kRows - 1) / kRows), nt = (size_t)((K + kCols - 1) / kCols);
+    return pt * nt + pt + (pt + 1) + 3 * (kItemCap1 + pt) + 1;
+}
+size_t tc_p1ub_floats(int64_t N, int K)
+{
+    const size_t pt = (size_t)((N + kRows - 1) / kRows);
+    return pt * (size_t)((K + kCols - 1) / kCols) + 12 * pt;   // ub, then the point-tile boxes
+}
+
 int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
-                    double2 *part, size_t part_cap_doubles, float *tmax, int *flags, int num_sms, int splits_override,
-                    int *splits_out, cudaStream_t st, Prof *pf)
+                    const float *rec32, double2 *part, size_t part_cap_doubles, float *tmax, int *p1plan,
+                    float *p1ub, int *flags, int num_sms, int tiles_per_item, const int **item_start_out,
+                    cudaStream_t st, Prof *pf)
 {
     const int ntiles = (K + kCols - 1) / kCols;
     const int ptiles = (int)((N + kRows - 1) / kRows);
-    int splits = splits_override > 0 ? std::min(splits_override, ntiles) : tc_pass1_auto_splits(N, K, num_sms);
-    while (splits > 1 && (size_t)splits * (size_t)N * 2 > part_cap_doubles) splits--;
-    const int tps = (ntiles + splits - 1) / splits;
-    splits = (ntiles + tps - 1) / tps;
-    *splits_out = splits;
+    unsigned long long *pairs1 = pf->on ? pf->d_pairs + 1 : nullptr;
+    const int icap = (int)std::min<size_t>((size_t)kItemCap1 + ptiles, part_cap_doubles / (2 * (size_t)kRows));
+    if (icap < ptiles + 1) return -2;
+    int *list = p1plan, *counts = list + (size_t)ptiles * ntiles;
+    int *item_start = counts + ptiles, *item_tile = item_start + ptiles + 1;
+    int *item_lo = item_tile + icap, *item_hi = item_lo + icap, *nitems = item_hi + icap;
+    // least tiles per item: tuned, or the K-split decomposition when every
+    // tile is evaluated; with skipping, at least 4 (items then follow the
+    // lists' total so the grid keeps several waves)
+    int tmin = tiles_per_item;
+    if (tmin <= 0) {
+        if (tmax) tmin = 4;
+        else {
+            const int splits = tc_pass1_auto_splits(N, K, num_sms);
+            tmin = (ntiles + splits - 1) / splits;
+        }
+    }
+    const int target = tmax ? std::min(icap, std::max(ptiles + 1, 8 * num_sms)) : icap;
+    pf->begin(VBGS_PROF_PASS1, st);
+    if (tmax) {
+        const size_t nt = tc_tmax_floats(N, K);
+        float *boxes = p1ub + (size_t)ptiles * ntiles;
+        k_fill_neg_inf<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(tmax, nt);
+        k_p1_boxes<<<ptiles, kRows, 0, st>>>(X, N, boxes);
+        k_p1_ub<<<ntiles, kCols, 0, st>>>(boxes, ptiles, K, ntiles, rec32, p1ub);
+        k_p1_lists<<<ptiles, kRows, 0, st>>>(X, N, K, ntiles, rec32, p1ub, list, counts);
+    }
+    k_p2_items<<<1, 1024, 0, st>>>(tmax ? counts : nullptr, ptiles, ntiles, tmin, target, item_start, item_tile,
+                                   item_lo, item_hi, nitems);
+    pf->end(st);
     const size_t smem = sizeof(Smem) + 1024;
     if (tc_set_attributes()) return -1;
-    dim3 grid(ptiles, splits);
     pf->begin(VBGS_PROF_PASS1, st);
-    if (bf16) k_pass1_tc<true><<<grid, kThreadsTC, smem, st>>>(X, N, K, tiles, hdr, ntiles, tps, part, tmax, flags);
-    else      k_pass1_tc<false><<<grid, kThreadsTC, smem, st>>>(X, N, K, tiles, hdr, ntiles, tps, part, tmax, flags);
+    const int *lst = tmax ? list : nullptr;
+    if (bf16)
+        k_pass1_tc<true><<<target, kThreadsTC, smem, st>>>(X, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
+                                                           item_hi, nitems, part, tmax, flags, pairs1);
+    else
+        k_pass1_tc<false><<<target, kThreadsTC, smem, st>>>(X, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
+                                                            item_hi, nitems, part, tmax, flags, pairs1);
     pf->end(st);
-    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+    *item_start_out = item_start;
+    return cudaGetLastError() == cudaSuccess ? (tmax ? 6 : 2) : -1;
 }
 
 } // namespace vbgs

@@ -56,8 +56,8 @@ struct Prof {
     std::vector<int> cat_of_pair;       // class of event pair i (events 2i, 2i+1)
     double ms[VBGS_PROF_COUNT] = {};
     int64_t n[VBGS_PROF_COUNT] = {};
-    unsigned long long *d_pairs = nullptr;   // device counter: pass-2 pairs evaluated (not skipped)
-    int64_t pass1_pairs = 0;                   // pairs scored by pass 1 (all of them)
+    unsigned long long *d_pairs = nullptr;   // device counters: [0] pass-2 pairs evaluated, [1] tensor-core pass-1 pairs evaluated
+    int64_t pass1_pairs = 0;                   // pairs scored by the CUDA-core pass 1 (all of them)
     void begin(int cat, cudaStream_t st)
     {
         if (!on || used + 2 > pool.size()) return;
@@ -149,8 +149,8 @@ int launch_elbo(double *scal, int64_t N, double *elbo_out, cudaStream_t st, Prof
 int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats, cudaStream_t st,
                            Prof *pf);
 size_t estep_cuda_core_scratch(int64_t N, int K, int precision);
-int launch_lse_merge(const double2 *part, int nsplit, int64_t N, double *lse, double *lse_part, float *minlse,
-                     double *sum_out, cudaStream_t st, Prof *pf);
+int launch_lse_merge(const double2 *part, int nsplit, int64_t N, const int *item_start, double *lse,
+                     double *lse_part, float *minlse, double *sum_out, cudaStream_t st, Prof *pf);
 int launch_pass2_fp32(const EstepBuffers &B, int tpb, int tkc, cudaStream_t st, Prof *pf);
 
 // Tensor-core form (vbgs_estep_tc.cu): coefficient tiles of 128 components
@@ -162,15 +162,23 @@ size_t tc_tmax_floats(int64_t N, int K);
 int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, cudaStream_t st, Prof *pf);
 size_t tc_plan_ints(int64_t N, int K);
 size_t tc_pass2_part_doubles(int K);
+size_t tc_p1plan_ints(int64_t N, int K);
+size_t tc_p1ub_floats(int64_t N, int K);
 int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
-                    const float *hdr, const float *tmax, const float *minlse, int *plan, double *part,
+                    const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
                     cudaStream_t st, Prof *pf);
 int tc_pass1_auto_splits(int64_t N, int K, int num_sms);
 int tc_set_attributes();
+// Pass 1 on the tensor cores over balanced work items (point tile, list of
+// component tiles).  With tmax (skipping on): the component tiles whose
+// certified logit bound over the point tile is within 50 nats of a lower bound
+// of every point's lse; tmax of the other tiles is -inf.  item_start_out: the
+// item table the lse merge reads.
 int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
-                    double2 *part, size_t part_cap_doubles, float *tmax, int *flags, int num_sms, int splits_override,
-                    int *splits_out, cudaStream_t st, Prof *pf);
+                    const float *rec32, double2 *part, size_t part_cap_doubles, float *tmax, int *p1plan,
+                    float *p1ub, int *flags, int num_sms, int tiles_per_item, const int **item_start_out,
+                    cudaStream_t st, Prof *pf);
 
 // Learned proposal (vbgs_proposal.cu).
 int prop_launch_kmeans(const float *rec32, int K, float csc, float *pts, float *cent, SortBuffers &sb, int *order,
@@ -277,6 +285,9 @@ struct vbgs_ctx {
     unsigned char *d_tc_tiles = nullptr;   // tensor-core coefficient tiles
     int *d_plan = nullptr;                 // pass-2 work list (counts + chunk lists per tile)
     size_t plan_cap = 0;
+    int *d_p1plan = nullptr;               // pass-1 tile lists and work items
+    float *d_p1ub = nullptr;               // pass-1 logit bounds per (point tile, component tile)
+    size_t p1plan_cap = 0;
     float *d_tc_hdr = nullptr;
     int num_sms = 152;
     int tune_p1 = 0, tune_p2 = 0;          // work decomposition of the tensor-core passes (0 = automatic)
