@@ -205,11 +205,26 @@ int stage_points(vbgs_ctx *ctx, const double *points, int64_t N)
     return VBGS_OK;
 }
 
+// The M-step's KL terms run on ctx->side; the main stream waits for them
+// before anything reads their sums (the ELBO) or rewrites their inputs (the
+// next M-step), and before a call returns.
+int join_side(vbgs_ctx *ctx)
+{
+    if (!ctx->side_pending) return VBGS_OK;
+    const cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+    if (e != cudaSuccess) return fail(ctx, VBGS_ECUDA, "stream join failed: %s", cudaGetErrorString(e));
+    ctx->side_pending = false;
+    return VBGS_OK;
+}
+
 int run_mstep(vbgs_ctx *ctx, const double *dS)
 {
+    int rc;
+    if ((rc = join_side(ctx))) return rc;
     int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_kperm, ctx->d_rec, ctx->d_rec32, ctx->d_pcache,
-                         ctx->d_flags, ctx->d_scal, ctx->stream, &ctx->prof);
+                         ctx->d_flags, ctx->d_scal, ctx->stream, ctx->side, ctx->ev_fork, ctx->ev_join, &ctx->prof);
     if (l < 0) return fail(ctx, VBGS_ECUDA, "posterior update launch failed");
+    ctx->side_pending = true;
     ctx->launches += l;
     if (is_tc(ctx)) {
         l = launch_coef_tiles(ctx->d_rec, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
@@ -661,7 +676,8 @@ int update_prepare(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters)
     if (N > 0 && !points) return fail(ctx, VBGS_EINVAL, "points is NULL");
     ctx->launches = 0;
     int rc;
-    if ((rc = ensure_capacity(ctx, N)) || (rc = ensure_elbo(ctx, n_iters))) return rc;
+    // outside any stream capture: finish the M-step work of earlier calls
+    if ((rc = join_side(ctx)) || (rc = ensure_capacity(ctx, N)) || (rc = ensure_elbo(ctx, n_iters))) return rc;
     return stage_points(ctx, points, N);
 }
 
@@ -682,6 +698,7 @@ int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters)
     }
     for (int it = 0; it < n_iters; it++) {
         if ((rc = run_estep(ctx, N, true, it == n_iters - 1))) return rc;
+        if ((rc = join_side(ctx))) return rc;
         if (launch_elbo(ctx->d_scal, N, ctx->d_elbo + it, ctx->stream, &ctx->prof) < 0)
             return fail(ctx, VBGS_ECUDA, "ELBO launch failed");
         ctx->launches += 1;
@@ -696,7 +713,7 @@ int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters)
         if ((rc = prop_train(ctx))) return rc;
         ctx->prop.frame++;
     }
-    return VBGS_OK;
+    return join_side(ctx);
 }
 
 void free_all(vbgs_ctx *ctx)
@@ -718,6 +735,12 @@ void free_all(vbgs_ctx *ctx)
         for (void *p : pp)
             if (p) cudaFree(p);
     }
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    ctx->ev_fork = ctx->ev_join = nullptr;
+    ctx->side = nullptr;
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     ctx->prof.pool.clear();
     if (ctx->prof.d_pairs) cudaFree(ctx->prof.d_pairs);
@@ -1141,6 +1164,17 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
         }
     }
     ctx->stream = opt ? (cudaStream_t)opt->cuda_stream : nullptr;
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        fail(ctx, VBGS_ECUDA, "stream or event creation failed");
+        g_err = ctx->err;
+        free_all(ctx);
+        delete ctx;
+        return VBGS_ECUDA;
+    }
+
     ctx->mp.alpha0 = prior->alpha0;
     ctx->mp.beta0 = prior->beta0;
     ctx->mp.nu0 = prior->nu0;
@@ -1191,7 +1225,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
         CU(cudaMemcpyAsync(ctx->d_kinv, ident.data(), sizeof(int) * K, cudaMemcpyHostToDevice, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
     }
-    if ((rc = run_mstep(ctx, nullptr))) return init_fail(rc);
+    if ((rc = run_mstep(ctx, nullptr)) || (rc = join_side(ctx))) return init_fail(rc);
     if ((ctx->flags & VBGS_FLAG_PROPOSAL) && (rc = prop_alloc(ctx))) return init_fail(rc);
     CU(cudaStreamSynchronize(ctx->stream));
 #undef CU
@@ -1230,6 +1264,7 @@ int vbgs_elbo(vbgs_ctx *ctx, const double *points, int64_t N, double *elbo_out, 
     ctx->last_sorted = false;
     if ((rc = run_mstep(ctx, nullptr))) return rc;
     if ((rc = run_estep(ctx, N, false))) return rc;
+    if ((rc = join_side(ctx))) return rc;
     if (launch_elbo(ctx->d_scal, N, ctx->d_elbo, ctx->stream, &ctx->prof) < 0)
         return fail(ctx, VBGS_ECUDA, "ELBO launch failed");
     ctx->launches += 1;

@@ -134,9 +134,11 @@ int launch_stage_points(const double *src, int64_t N, double *X, int *flags, cud
 // prior0 (+) S_past (frame start), whose per-component terms are cached in
 // `cache` (mstep_cache_doubles(K) doubles) for the KL of later iterations.
 size_t mstep_cache_doubles(int K);
+// The record kernel runs on st; the KL terms and their sums (scal) on side,
+// after ev_fork; ev_join completes them (wait on it before reading scal).
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
                  const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
-                 cudaStream_t st, Prof *pf);
+                 cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, Prof *pf);
 size_t sort_temp_bytes(int64_t n);
 int launch_point_order(const double *X, int64_t N, const BoxParams &box, SortBuffers &sb, double *Xs,
                        int *pidx, cudaStream_t st, Prof *pf);
@@ -277,6 +279,9 @@ struct vbgs_ctx {
     int precision = VBGS_FP64;
     int flags = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;               // KL terms of the M-step, beside the next E-step
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool side_pending = false;                 // KL work launched on side and not yet joined
     vbgs::BoxParams box{};
     vbgs::SortBuffers sb;
     int *d_kperm = nullptr, *d_kinv = nullptr, *d_pidx = nullptr;

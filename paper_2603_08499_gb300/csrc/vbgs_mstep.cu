@@ -190,27 +190,39 @@ __device__ void block_sums4(double v0, double v1, double v2, double v3, double *
 // all exactly zero has q = p bit for bit: when its record already holds p
 // (flag cache[33], set by the frame-start call and by any call that wrote p),
 // nothing is recomputed and its KL term is exactly zero.
+//
+// The record (the next E-step's input) is this kernel's job; the KL terms of
+// the ELBO are k_mstep_kl's, which runs on a second stream beside the next
+// E-step: for every recomputed component this kernel leaves in kls[k] (kKS
+// doubles) m_q (6), L^-1 of W_q^-1 = L L^T (21, packed lower), alpha_q,
+// beta_q, nu_q, ln|W_q^-1|, psi_6(nu_q/2), psi(alpha_q), a flag (1:
+// recomputed, 0: q = p) and the frame count Delta N_k.
+constexpr int kKS = 36;
+
 __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__restrict__ m0,
                                                const double *__restrict__ Spast,
                                                const double *__restrict__ dS,
                                                const int *__restrict__ kperm,
                                                double *__restrict__ rec, float *__restrict__ rec32,
-                                               double *__restrict__ pc, double *__restrict__ bpart,
+                                               double *__restrict__ pc, double *__restrict__ kls,
                                                int *__restrict__ flags)
 {
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-    double kl = 0.0, aq = 0.0, ap = 0.0, dn = 0.0;
-    const int k = pos < P.K ? (kperm ? kperm[pos] : pos) : 0;
-    bool zero = false;
-    if (pos < P.K && dS) {
-        zero = true;
+    if (pos >= P.K) return;
+    const int k = kperm ? kperm[pos] : pos;
+    double *ks = kls + (size_t)k * kKS;
+    if (dS) {
+        bool zero = true;
 #pragma unroll
         for (int f = 0; f < 28; f++) zero = zero && (dS[(size_t)k * 28 + f] == 0.0);
-        zero = zero && (pc[(size_t)k * kPC + 33] != 0.0);
-        if (zero) { aq = ap = pc[(size_t)k * kPC]; }
+        if (zero && pc[(size_t)k * kPC + 33] != 0.0) {
+            ks[33] = 0.0;
+            ks[34] = 0.0;
+            return;
+        }
     }
-    if (pos < P.K && !zero) {
-        double st[28], m0k[6];
+    {
+        double st[28], m0k[6], aq;
 #pragma unroll
         for (int f = 0; f < 28; f++) st[f] = Spast[(size_t)k * 28 + f] + (dS ? dS[(size_t)k * 28 + f] : 0.0);
 #pragma unroll
@@ -250,14 +262,15 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
 #pragma unroll
         for (int i = 28; i < 32; i++) { r[i] = 0.0; r32[i] = 0.f; }
         if (P.want_bounds) {
-            // For the proposal certificate: lower bounds (log2 units) of the
-            // smallest eigenvalue of the marginal precision of the position
-            // block and of the colour block.  Minimising (x - m)^T nu W (x - m)
-            // over the colour part leaves the position part's quadratic form
-            // in the inverse of its covariance block (W^-1)_pp / nu, whose
-            // smallest eigenvalue is nu / lambda_max((W^-1)_pp); same for
-            // colour.  (largest eigenvalue of each 3 x 3 block in FP32,
-            // inflated by 1e-4 so the bound stays below the exact one)
+            // Lower bounds (log2 units) of the smallest eigenvalue of the
+            // marginal precision of the position block and of the colour
+            // block, for the tile-skip bounds of pass 1 and the proposal
+            // certificate.  Minimising (x - m)^T nu W (x - m) over the colour
+            // part leaves the position part's quadratic form in the inverse
+            // of its covariance block (W^-1)_pp / nu, whose smallest
+            // eigenvalue is nu / lambda_max((W^-1)_pp); same for colour.
+            // (largest eigenvalue of each 3 x 3 block in FP32, inflated by
+            // 1e-4 so the bound stays below the exact one)
             const float lpp = sym3_max_eig((float)Aq[0], (float)Aq[1], (float)Aq[2], (float)Aq[7], (float)Aq[8],
                                            (float)Aq[14]);
             const float lcc = sym3_max_eig((float)Aq[21], (float)Aq[22], (float)Aq[23], (float)Aq[28],
@@ -280,47 +293,71 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
 #pragma unroll
                 for (int j = i; j < 6; j++, u++) cache[u] = Aq[i * 6 + j];
             cache[30] = ldq;
-            cache[31] = mv_lgamma6(0.5 * nq);
-            cache[32] = lgamma(aq);
             cache[33] = 1.0;   // the record holds the effective prior
-            ap = aq;
         } else {
-            // the record now holds the prior again only if this frame's
+            // the record holds the prior again only if this frame's
             // statistics of the component are all zero
             bool z = true;
 #pragma unroll
             for (int f = 0; f < 28; f++) z = z && (dS[(size_t)k * 28 + f] == 0.0);
             cache[33] = z ? 1.0 : 0.0;
-            // KL(NW_q || NW_p) against the cached effective prior.
-            ap = cache[0];
+#pragma unroll
+            for (int i = 0; i < 6; i++) ks[i] = mq[i];
+#pragma unroll
+            for (int i = 0; i < 6; i++)
+#pragma unroll
+                for (int j = 0; j <= i; j++) ks[6 + tri(i, j)] = Li[i * 6 + j];
+            ks[27] = aq; ks[28] = bq; ks[29] = nq; ks[30] = ldq; ks[31] = psi_nu; ks[32] = psi_a;
+            ks[33] = 1.0;
+            ks[34] = st[0] - Spast[(size_t)k * 28];
+        }
+    }
+}
+
+// KL terms of the posterior that k_mstep just wrote (second stream).  Frame
+// start (dS == nullptr): the lnGamma terms of the effective prior's cache,
+// KL = 0.  Otherwise KL(NW_q || NW_p) + the per-component Dirichlet part from
+// kls and the cache.  Block sums of (KL, alpha_q, alpha_p, Delta N) in
+// position order.
+__global__ void __launch_bounds__(128) k_mstep_kl(MstepParams P, bool frame_start, const int *__restrict__ kperm,
+                                                  double *__restrict__ pc, const double *__restrict__ kls,
+                                                  double *__restrict__ bpart)
+{
+    const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    double kl = 0.0, aq = 0.0, ap = 0.0, dn = 0.0;
+    if (pos < P.K) {
+        const int k = kperm ? kperm[pos] : pos;
+        double *cache = pc + (size_t)k * kPC;
+        const double *ks = kls + (size_t)k * kKS;
+        ap = cache[0];
+        aq = ap;
+        if (frame_start) {
+            cache[31] = mv_lgamma6(0.5 * cache[2]);
+            cache[32] = lgamma(ap);
+        } else if (ks[33] != 0.0) {
+            aq = ks[27];
+            const double bq = ks[28], nq = ks[29], ldq = ks[30], psi_nu = ks[31], psi_a = ks[32];
             const double bp = cache[1], np = cache[2], ldp = cache[30];
-            double Ap[36];
-            {
-                int u = 9;
-#pragma unroll
-                for (int i = 0; i < 6; i++)
-#pragma unroll
-                    for (int j = i; j < 6; j++, u++) { Ap[i * 6 + j] = cache[u]; Ap[j * 6 + i] = cache[u]; }
-            }
             double maha = 0.0;   // (m_q - m_p)^T W_q (m_q - m_p) = |L^-1 (m_q - m_p)|^2
 #pragma unroll
             for (int i = 0; i < 6; i++) {
                 double t = 0.0;
 #pragma unroll
-                for (int j = 0; j <= i; j++) t += Li[i * 6 + j] * (mq[j] - cache[3 + j]);
+                for (int j = 0; j <= i; j++) t += ks[6 + tri(i, j)] * (ks[j] - cache[3 + j]);
                 maha += t * t;
             }
             // tr(W_p^-1 W_q) = sum_ij (W_p^-1)_ij (W_q)_ij with W_q = Li^T Li,
-            // (W_q)_ij = sum_{l >= max(i, j)} Li_li Li_lj.
+            // (W_q)_ij = sum_{l >= max(i, j)} Li_li Li_lj (W_p^-1 upper in the cache).
             double tr = 0.0;
+            int u = 9;
 #pragma unroll
             for (int i = 0; i < 6; i++)
 #pragma unroll
-                for (int j = 0; j <= i; j++) {
+                for (int j = i; j < 6; j++, u++) {
                     double w = 0.0;
 #pragma unroll
-                    for (int l = i; l < 6; l++) w += Li[l * 6 + i] * Li[l * 6 + j];
-                    tr += (i == j ? 1.0 : 2.0) * Ap[i * 6 + j] * w;
+                    for (int l = j; l < 6; l++) w += ks[6 + tri(l, i)] * ks[6 + tri(l, j)];
+                    tr += (i == j ? 1.0 : 2.0) * cache[u] * w;
                 }
             kl = 0.5 * (6.0 * bp / bq - 6.0 + bp * nq * maha + 6.0 * log(bq / bp));
             kl += 0.5 * (nq - np) * psi_nu - 3.0 * nq + 0.5 * nq * tr + 0.5 * np * (ldq - ldp) + cache[31] -
@@ -328,7 +365,7 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
             // Per-component part of KL(Dir(alpha_q) || Dir(alpha_p)); the psi(sum)
             // and lnGamma(sum) terms are added after the cross-component sums.
             kl += -lgamma(aq) + cache[32] + (aq - ap) * psi_a;
-            dn = st[0] - Spast[(size_t)k * 28];
+            dn = ks[34];
         }
     }
     block_sums4(kl, aq, ap, dn, bpart);
@@ -400,22 +437,32 @@ __global__ void k_stage(const double *__restrict__ src, int64_t N, double *__res
 
 } // namespace
 
-size_t mstep_cache_doubles(int K) { return (size_t)K * kPC + (size_t)((K + 127) / 128) * 4; }
+size_t mstep_cache_doubles(int K)
+{
+    return (size_t)K * kPC + (size_t)((K + 127) / 128) * 4 + (size_t)K * kKS;   // cache, block sums, KL inputs
+}
 
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
                  const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
-                 cudaStream_t st, Prof *pf)
+                 cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, Prof *pf)
 {
     const int K = P.K;
     const int nb = (K + 127) / 128;
     double *bpart = cache + (size_t)K * kPC;
+    double *kls = bpart + (size_t)nb * 4;
     pf->begin(VBGS_PROF_MSTEP, st);
-    k_mstep<<<nb, 128, 0, st>>>(P, m0, Spast, dS, kperm, rec, rec32, cache, bpart, flags);
+    k_mstep<<<nb, 128, 0, st>>>(P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags);
     pf->end(st);
-    pf->begin(VBGS_PROF_MSTEP, st);
-    k_mstep_finalize<<<1, 1024, 0, st>>>(bpart, nb, scal);
-    pf->end(st);
-    return cudaGetLastError() == cudaSuccess ? 2 : -1;
+    // KL terms and their sums beside the next E-step
+    if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return -1;
+    pf->begin(VBGS_PROF_MSTEP, side);
+    k_mstep_kl<<<nb, 128, 0, side>>>(P, dS == nullptr, kperm, cache, kls, bpart);
+    pf->end(side);
+    pf->begin(VBGS_PROF_MSTEP, side);
+    k_mstep_finalize<<<1, 1024, 0, side>>>(bpart, nb, scal);
+    pf->end(side);
+    if (cudaEventRecord(ev_join, side) != cudaSuccess) return -1;
+    return cudaGetLastError() == cudaSuccess ? 3 : -1;
 }
 
 int launch_commit(double *Spast, const double *dS, int K, const int *flags, cudaStream_t st, Prof *pf)
