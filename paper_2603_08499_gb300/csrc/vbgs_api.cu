@@ -222,13 +222,14 @@ int run_mstep(vbgs_ctx *ctx, const double *dS)
     int rc;
     if ((rc = join_side(ctx))) return rc;
     int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_kperm, ctx->d_rec, ctx->d_rec32, ctx->d_pcache,
-                         ctx->d_flags, ctx->d_scal, ctx->stream, ctx->side, ctx->ev_fork, ctx->ev_join, &ctx->prof);
+                         ctx->d_flags, ctx->d_scal, is_tc(ctx) ? ctx->d_tile_dirty : nullptr, ctx->stream, ctx->side,
+                         ctx->ev_fork, ctx->ev_join, &ctx->prof);
     if (l < 0) return fail(ctx, VBGS_ECUDA, "posterior update launch failed");
     ctx->side_pending = true;
     ctx->launches += l;
     if (is_tc(ctx)) {
         l = launch_coef_tiles(ctx->d_rec, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
-                              ctx->stream, &ctx->prof);
+                              ctx->d_tile_dirty, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "coefficient tile launch failed");
         ctx->launches += l;
     }
@@ -723,7 +724,7 @@ void free_all(vbgs_ctx *ctx)
                     ctx->d_flags, ctx->d_X, ctx->d_lse, ctx->d_lse_part, ctx->d_part,
                     ctx->d_kperm, ctx->d_kinv, ctx->d_pidx, ctx->d_Xs, ctx->d_tmax, ctx->d_minlse,
                     ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp, ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_plan,
-                    ctx->d_p1plan, ctx->d_p1ub};
+                    ctx->d_p1plan, ctx->d_p1ub, ctx->d_tile_dirty};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     {
@@ -1191,7 +1192,8 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
         (rc = dalloc(ctx, &ctx->d_pcache, mstep_cache_doubles(K))) || (rc = dalloc(ctx, &ctx->d_scal, (size_t)SC_COUNT)) ||
         (rc = dalloc(ctx, &ctx->d_flags, (size_t)FL_COUNT)) || (rc = ensure_elbo(ctx, 64)) ||
         (rc = dalloc(ctx, &ctx->d_kperm, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_kinv, (size_t)K)) ||
-        (rc = dalloc(ctx, &ctx->d_tc_tiles, tc_tile_bytes(K))) || (rc = dalloc(ctx, &ctx->d_tc_hdr, tc_hdr_floats(K)))) {
+        (rc = dalloc(ctx, &ctx->d_tc_tiles, tc_tile_bytes(K))) || (rc = dalloc(ctx, &ctx->d_tc_hdr, tc_hdr_floats(K))) ||
+        (rc = dalloc(ctx, &ctx->d_tile_dirty, (size_t)(K + 127) / 128))) {
         g_err = ctx->err;
         free_all(ctx);
         delete ctx;
@@ -1216,6 +1218,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     CU(cudaMemsetAsync(ctx->d_Spast, 0, sizeof(double) * KF, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_dS, 0, sizeof(double) * KF, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_pcache, 0, sizeof(double) * mstep_cache_doubles(K), ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_tile_dirty, 0, sizeof(int) * ((K + 127) / 128), ctx->stream));
     CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_scal, 0, sizeof(double) * SC_COUNT, ctx->stream));
     {

@@ -203,12 +203,19 @@ template <> struct H<true> {
 // ---------------------------------------------------------------------------
 template <bool BF16>
 __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ rec, int K,
-                                                    unsigned char *__restrict__ tiles, float *__restrict__ hdr)
+                                                    unsigned char *__restrict__ tiles, float *__restrict__ hdr,
+                                                    int *__restrict__ dirty)
 {
     using HT = typename H<BF16>::T;
     __shared__ double red[6][4];
     __shared__ double frame[13];
     const int t = threadIdx.x, j = blockIdx.x, lane = t & 31, w = t >> 5;
+    // a tile whose records were not rewritten since its last build is current
+    if (dirty) {
+        if (dirty[j] == 0) return;
+        __syncthreads();
+        if (t == 0) dirty[j] = 0;
+    }
     const int k = j * kCols + t;
     const bool valid = k < K;
     const double *r = rec + (size_t)(valid ? k : K - 1) * VBGS_REC;
@@ -629,42 +636,40 @@ __global__ void __launch_bounds__(128) k_p1_boxes(const double *__restrict__ X, 
     }
 }
 
-// ub[P][j] for every point tile, one CTA per component tile j (thread =
-// component); point-tile boxes staged through shared memory 128 at a time.
+// ub[P][j] for every point tile: one CTA per component tile j, the tile's
+// bound terms (m, c, lp, lc, la) in shared memory, one thread per point tile.
 __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, int ptiles, int K, int ntiles,
                                                const float *__restrict__ rec32, float *__restrict__ ub)
 {
-    __shared__ float sb[kRows][12];
-    __shared__ float wm[kRows][4];
-    const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    __shared__ float sc[kCols][10];
+    const int j = blockIdx.x, t = threadIdx.x;
     const int k = j * kCols + t;
-    const bool valid = k < K;
-    float m[6], c2 = -INFINITY, lp = 0.f, lc = 0.f, la = 0.f;
-    const float *r = rec32 + (size_t)(valid ? k : 0) * VBGS_REC;
+    const int nv = min(kCols, K - j * kCols);
+    {
+        const float *r = rec32 + (size_t)(k < K ? k : 0) * VBGS_REC;
 #pragma unroll
-    for (int i = 0; i < 6; i++) m[i] = r[i];
-    if (valid) { c2 = r[27]; lp = r[28]; lc = r[29]; la = r[30]; }
-    for (int p0 = 0; p0 < ptiles; p0 += kRows) {
-        const int np = min(kRows, ptiles - p0);
-        __syncthreads();
-        for (int i = t; i < np * 12; i += kRows) sb[i / 12][i % 12] = boxes[(size_t)p0 * 12 + i];
-        __syncthreads();
-        for (int q = 0; q < np; q++) {
+        for (int i = 0; i < 6; i++) sc[t][i] = r[i];
+        sc[t][6] = r[27]; sc[t][7] = r[28]; sc[t][8] = r[29]; sc[t][9] = r[30];
+    }
+    __syncthreads();
+    for (int P = t; P < ptiles; P += kCols) {
+        float lo[6], hi[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) { lo[i] = boxes[(size_t)P * 12 + i]; hi[i] = boxes[(size_t)P * 12 + 6 + i]; }
+        float b = -INFINITY;
+        for (int q = 0; q < nv; q++) {
+            const float *c = sc[q];
             float dp = 0.f, dc = 0.f;
 #pragma unroll
             for (int i = 0; i < 3; i++) {
-                const float o = fmaxf(fmaxf(sb[q][i] - m[i], m[i] - sb[q][6 + i]), 0.f);
+                const float o = fmaxf(fmaxf(lo[i] - c[i], c[i] - hi[i]), 0.f);
                 dp = fmaf(o, o, dp);
-                const float oc = fmaxf(fmaxf(sb[q][3 + i] - m[3 + i], m[3 + i] - sb[q][9 + i]), 0.f);
+                const float oc = fmaxf(fmaxf(lo[3 + i] - c[3 + i], c[3 + i] - hi[3 + i]), 0.f);
                 dc = fmaf(oc, oc, dc);
             }
-            float v = valid ? c2 - 0.5f * fmaxf(fmaxf(lp * dp, lc * dc), la * (dp + dc)) : -INFINITY;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-            if (lane == 0) wm[q][w] = v;
+            b = fmaxf(b, c[6] - 0.5f * fmaxf(fmaxf(c[7] * dp, c[8] * dc), c[9] * (dp + dc)));
         }
-        __syncthreads();
-        if (t < np) ub[(size_t)(p0 + t) * ntiles + j] = fmaxf(fmaxf(wm[t][0], wm[t][1]), fmaxf(wm[t][2], wm[t][3]));
+        ub[(size_t)P * ntiles + j] = b;
     }
 }
 
@@ -1272,12 +1277,13 @@ size_t tc_tile_bytes(int K) { return (size_t)((K + kCols - 1) / kCols) * kTileBy
 size_t tc_hdr_floats(int K) { return (size_t)((K + kCols - 1) / kCols) * 32; }
 size_t tc_tmax_floats(int64_t N, int K) { return (size_t)((N + 31) / 32) * (size_t)((K + kCols - 1) / kCols); }
 
-int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, cudaStream_t st, Prof *pf)
+int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, int *dirty,
+                      cudaStream_t st, Prof *pf)
 {
     const int nt = (K + kCols - 1) / kCols;
     pf->begin(VBGS_PROF_MSTEP, st);
-    if (bf16) k_coef_tiles<true><<<nt, 128, 0, st>>>(rec, K, tiles, hdr);
-    else      k_coef_tiles<false><<<nt, 128, 0, st>>>(rec, K, tiles, hdr);
+    if (bf16) k_coef_tiles<true><<<nt, 128, 0, st>>>(rec, K, tiles, hdr, dirty);
+    else      k_coef_tiles<false><<<nt, 128, 0, st>>>(rec, K, tiles, hdr, dirty);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }

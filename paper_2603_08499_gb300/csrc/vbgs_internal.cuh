@@ -138,7 +138,8 @@ size_t mstep_cache_doubles(int K);
 // after ev_fork; ev_join completes them (wait on it before reading scal).
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
                  const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
-                 cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, Prof *pf);
+                 int *tile_dirty, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
+                 Prof *pf);
 size_t sort_temp_bytes(int64_t n);
 int launch_point_order(const double *X, int64_t N, const BoxParams &box, SortBuffers &sb, double *Xs,
                        int *pidx, cudaStream_t st, Prof *pf);
@@ -161,7 +162,8 @@ int launch_pass2_fp32(const EstepBuffers &B, int tpb, int tkc, cudaStream_t st, 
 size_t tc_tile_bytes(int K);
 size_t tc_hdr_floats(int K);
 size_t tc_tmax_floats(int64_t N, int K);
-int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, cudaStream_t st, Prof *pf);
+int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, int *dirty,
+                      cudaStream_t st, Prof *pf);
 size_t tc_plan_ints(int64_t N, int K);
 size_t tc_pass2_part_doubles(int K);
 size_t tc_p1plan_ints(int64_t N, int K);
@@ -294,6 +296,7 @@ struct vbgs_ctx {
     float *d_p1ub = nullptr;               // pass-1 logit bounds per (point tile, component tile)
     size_t p1plan_cap = 0;
     float *d_tc_hdr = nullptr;
+    int *d_tile_dirty = nullptr;           // per 128-position tile: a record changed since its last coefficient build
     int num_sms = 152;
     int tune_p1 = 0, tune_p2 = 0;          // work decomposition of the tensor-core passes (0 = automatic)
     int64_t alloc_gen = 0;                 // bumped by every (re)allocation: cached graphs check it

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
                                                const int *__restrict__ kperm,
                                                double *__restrict__ rec, float *__restrict__ rec32,
                                                double *__restrict__ pc, double *__restrict__ kls,
-                                               int *__restrict__ flags)
+                                               int *__restrict__ flags, int *__restrict__ tile_dirty)
 {
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= P.K) return;
@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__re
         trinv6(Lq, Li);
 
         // E-step record: quad = nu |L^-1 (x - m)|^2 = |M (x - m)|^2.
+        if (tile_dirty) tile_dirty[pos >> 7] = 1;   // its tensor-core tile must be rebuilt
         const double sn = sqrt(nq);
         double *r = rec + (size_t)pos * VBGS_REC;
         float *r32 = rec32 + (size_t)pos * VBGS_REC;
@@ -444,14 +445,15 @@ size_t mstep_cache_doubles(int K)
 
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
                  const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
-                 cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, Prof *pf)
+                 int *tile_dirty, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
+                 Prof *pf)
 {
     const int K = P.K;
     const int nb = (K + 127) / 128;
     double *bpart = cache + (size_t)K * kPC;
     double *kls = bpart + (size_t)nb * 4;
     pf->begin(VBGS_PROF_MSTEP, st);
-    k_mstep<<<nb, 128, 0, st>>>(P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags);
+    k_mstep<<<nb, 128, 0, st>>>(P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags, tile_dirty);
     pf->end(st);
     // KL terms and their sums beside the next E-step
     if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return -1;
