@@ -197,11 +197,15 @@ def run_reference(args):
 
 
 def timed_stream(V, prior, dev_frames, form, warmup, steps, stream, flush, profile=False, host_frames=None,
-                 flags=0, keep_last_state=False):
+                 flags=0, keep_last_state=False, tuning=None):
     """Run warmup + steps frames through a fresh model; per-step device times
-    with CUDA events (or host wall time for host inputs)."""
+    with CUDA events (or host wall time for host inputs).  tuning: the
+    tensor-core work decomposition (pass-1 tiles, pass-2 chunks per item) to
+    apply, as vbgs_autotune picked it."""
     import torch
     m = V.Model(prior, form, cuda_stream=stream.cuda_stream, flags=flags)
+    if tuning:
+        V.vbgs_set_tuning(m.ctx, *tuning)
     traces, times, launches = [], [], 0
     pairs = 0
     state_before_last = None
@@ -464,12 +468,21 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     peaks = V.vbgs_probe_peaks(lrank) if rank == 0 else None
 
+    tuning = None
+    if args.autotune and form in ("fp16x3", "bf16x3"):
+        # pick the work decomposition on the first frame (not timed)
+        mt = V.Model(prior, form, cuda_stream=stream.cuda_stream, flags=args.flags)
+        V.vbgs_autotune(mt.ctx, dev[0], None)
+        tuning = V.vbgs_get_tuning(mt.ctx)
+        mt.close()
+
     clocks = ClockSampler(lrank)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    res = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, profile=True, flags=args.flags)
+    res = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, profile=True, flags=args.flags,
+                       tuning=tuning)
     clk = clocks.stop()
     torch.cuda.synchronize()
     dev_time = sum(res["times"])
@@ -486,7 +499,7 @@ def run_ours(args):
 
     # end to end through the same call with pinned host inputs
     res_e2e = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, host_frames=host,
-                           flags=args.flags)
+                           flags=args.flags, tuning=tuning)
     e2e_time = sum(res_e2e["times"])
     if ws > 1:
         t = torch.tensor([e2e_time], device="cuda", dtype=torch.float64)
@@ -536,6 +549,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": dev_time * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[form], "data": "synthetic",
             "config": {"workload": WORKLOAD, "K": K_COMP, "iters": ITERS, "form": form, "flags": args.flags,
+                       "tuning": list(tuning) if tuning else "automatic",
                        "mean_points_per_frame": n_pts / args.steps,
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas x{ws} (independent streams)"},

@@ -131,13 +131,17 @@ int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const double *con
  * work item; both passes cut their lists of tile pairs not ruled out by the
  * skip bounds into such items, one CTA each) for this context's K and frames
  * of N
- * points, by timing 3 x 3 candidates on `points` (one E-step each; the model
+ * points, by timing 4 x 4 candidates on `points` (one E-step each; the model
  * state is unchanged).  With cache_path, the choice is read from / appended
  * to that text file keyed by form, rounded log2 N and K, and SM count.  The
  * CUDA-core forms have nothing to tune (returns VBGS_OK).  vbgs_get_tuning
  * reports the current choice (0 = automatic). */
 int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, const char *cache_path);
 int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_tiles, int *pass2_chunks);
+/* Set the decomposition directly (0 = automatic), e.g. a choice
+ * vbgs_autotune made on another context of the same sizes.  Errors:
+ * VBGS_EINVAL (NULL ctx, negative values). */
+int vbgs_set_tuning(vbgs_ctx *ctx, int pass1_tiles, int pass2_chunks);
 
 /* Learned proposal (VBGS_FLAG_PROPOSAL at vbgs_init).  A small MLP over the
  * point (x, y, z, r, g, b), 6 -> 128 -> 128 -> 1024 with ReLU, BF16-rounded

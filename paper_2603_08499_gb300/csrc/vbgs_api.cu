@@ -283,13 +283,13 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
     if (is_tc(ctx)) {
         const int *item_start = nullptr;
         int l = launch_pass1_tc(B.X, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
-                                ctx->d_rec32, reinterpret_cast<double2 *>(ctx->d_part), ctx->part_cap, B.tmax,
+                                ctx->d_rec32, ctx->d_part, ctx->part_cap, B.tmax,
                                 ctx->d_p1plan, ctx->d_p1ub, ctx->d_flags, ctx->num_sms, ctx->tune_p1, &item_start,
                                 ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ctx->launches += l;
-        l = launch_lse_merge(reinterpret_cast<double2 *>(ctx->d_part), 0, N, item_start, lse, ctx->d_lse_part,
-                             B.tmax ? ctx->d_minlse : nullptr, ctx->d_scal + SC_SUM_LSE, ctx->stream, &ctx->prof);
+        l = launch_lse_merge_tc(ctx->d_part, N, item_start, lse, ctx->d_lse_part, B.tmax ? ctx->d_minlse : nullptr,
+                                ctx->d_scal + SC_SUM_LSE, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "lse merge launch failed");
         ctx->launches += l;
         if (want_stats) {
@@ -966,8 +966,8 @@ extern "C" int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, con
     int rc;
     if ((rc = update_prepare(ctx, points, N, 1))) return rc;
     if ((rc = order_frame(ctx, N, true)) || (rc = run_mstep(ctx, nullptr))) return rc;
-    const int p1c[3] = {2, 4, 8};   // pass 1: least component tiles per work item
-    const int p2c[3] = {2, 4, 8};   // pass 2: least chunks per work item
+    const int p1c[4] = {2, 4, 8, 16};   // pass 1: least component tiles per work item
+    const int p2c[4] = {2, 4, 8, 16};   // pass 2: least chunks per work item
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
@@ -975,8 +975,8 @@ extern "C" int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, con
     ctx->prof.on = false;
     float best = 1e30f;
     int b1 = 0, b2 = 0;
-    for (int i = 0; i < 3; i++)
-        for (int jx = 0; jx < 3; jx++) {
+    for (int i = 0; i < 4; i++)
+        for (int jx = 0; jx < 4; jx++) {
             ctx->tune_p1 = p1c[i];
             ctx->tune_p2 = p2c[jx];
             if ((rc = run_estep(ctx, N, true))) break;   // warm-up
@@ -1103,6 +1103,15 @@ extern "C" int vbgs_proposal_bounds(vbgs_ctx *ctx, const double *points, int64_t
             for (int i = cstart[g]; i < cstart[g + 1]; i++) cluster_of[kperm[order[i]]] = g;
     }
     return check_flags(ctx);
+}
+
+extern "C" int vbgs_set_tuning(vbgs_ctx *ctx, int pass1_tiles, int pass2_chunks)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (pass1_tiles < 0 || pass2_chunks < 0) return fail(ctx, VBGS_EINVAL, "vbgs_set_tuning: negative value");
+    ctx->tune_p1 = pass1_tiles;
+    ctx->tune_p2 = pass2_chunks;
+    return VBGS_OK;
 }
 
 int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_splits)

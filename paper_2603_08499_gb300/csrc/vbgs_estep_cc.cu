@@ -370,6 +370,14 @@ constexpr int kPPT32 = 2;
 
 } // namespace
 
+int launch_block_sum(const double *part, int n, double *sum_out, cudaStream_t st, Prof *pf)
+{
+    pf->begin(VBGS_PROF_MERGE, st);
+    k_sum<<<1, 1024, 0, st>>>(part, n, sum_out);
+    pf->end(st);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
 int launch_lse_merge(const double2 *part, int nsplit, int64_t N, const int *item_start, double *lse,
                      double *lse_part, float *minlse, double *sum_out, cudaStream_t st, Prof *pf)
 {

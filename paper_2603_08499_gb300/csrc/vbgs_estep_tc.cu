@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
 }
 
 // ---------------------------------------------------------------------------
-// Pass 1 on the tensor cores.  grid = (point tiles of 128, K splits).
-// part[split * N + n] = (max in natural units, sum of exp(l - max)).
+// Pass 1 on the tensor cores.  grid = work items (point tile, component
+// tiles).  part[item * 128 + row] = (max in log2 units, sum of 2^(l - max)).
 // tmax[(point tile * 4 + warp) * ntiles + tile]: largest logit (natural units)
 // of each 32-point row block and 128-component tile.
 // ---------------------------------------------------------------------------
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__rest
                                                             const int *__restrict__ item_lo,
                                                             const int *__restrict__ item_hi,
                                                             const int *__restrict__ nitems,
-                                                            double2 *__restrict__ part, float *__restrict__ tmax,
+                                                            float2 *__restrict__ part, float *__restrict__ tmax,
                                                             int *__restrict__ flags,
                                                             unsigned long long *__restrict__ pairs)
 {
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__rest
             const int64_t rb = (int64_t)P * 4 + warp;
             if (lane == 0 && tmax && rb * 32 < N) tmax[rb * ntiles + tj] = tmx * 0.6931471805599453f;
         }
-        if (n < N) part[(size_t)item * kRows + row] = make_double2((double)mrun * 0.6931471805599453, (double)srun);
+        if (n < N) part[(size_t)item * kRows + row] = make_float2(mrun, srun);   // log2 units
         if (pairs && tid == 0) {
             unsigned long long cols = 0;
             for (int jj = 0; jj < nt; jj++) cols += (unsigned long long)min(kCols, K - tile_at(jj) * kCols);
@@ -718,13 +718,15 @@ __global__ void __launch_bounds__(128) k_p1_lists(const double *__restrict__ X, 
 #pragma unroll
     for (int i = 0; i < 6; i++) x[i] = (float)X[(live ? n : (int64_t)P * kRows) * VBGS_XS + i];
     __syncthreads();
+    // (approximate ex2 / lg2: relative errors of a few 2^-22, far inside the
+    // 1 + 1e-5 |lse| margin below)
     float mx = -INFINITY, sm = 0.f;
     for (int mm = 0; mm < ns; mm++) {
         const float l = logit32_rec(sr + mm * 28, x);
-        if (l > mx) { sm = sm * exp2f(mx - l) + 1.f; mx = l; }
-        else sm += exp2f(l - mx);
+        if (l > mx) { sm = sm * ex2f(mx - l) + 1.f; mx = l; }
+        else sm += ex2f(l - mx);
     }
-    float lb = mx + log2f(sm);
+    float lb = mx + __log2f(sm);
     lb = live ? lb - (1.f + 1e-5f * fabsf(lb)) : INFINITY;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lb = fminf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
@@ -935,7 +937,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
                                                             const int *__restrict__ item_hi,
                                                             const int *__restrict__ nitems,
                                                             const double *__restrict__ rec,
-                                                            double *__restrict__ part, int *__restrict__ flags,
+                                                            float *__restrict__ part, int *__restrict__ flags,
                                                             unsigned long long *__restrict__ pairs)
 {
     using HT = typename H<BF16>::T;
@@ -1136,9 +1138,9 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
         }
         const int k = j * kCols + m;
         if (k < K) {
-            double *dst = part + ((size_t)item * kCols + m) * 28;
+            float4 *dst = reinterpret_cast<float4 *>(part + ((size_t)item * kCols + m) * 28);
 #pragma unroll
-            for (int i = 0; i < 28; i++) dst[i] = (double)st[i];
+            for (int i = 0; i < 7; i++) dst[i] = make_float4(st[4 * i], st[4 * i + 1], st[4 * i + 2], st[4 * i + 3]);
         }
     } else if (warp == 4 && lane == 0) {
         // ---------------- copy + MMA issuer ----------------
@@ -1228,7 +1230,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
 // to raw moments: S1 = S1' + N m, S2 = S2' + m S1'^T + S1' m^T + N m m^T.
 // One CTA per (tile, 32 positions): warp w sums the items q = w, w + 4, ...
 // of the tile in order; the 4 warp sums are added in warp order.
-__global__ void __launch_bounds__(128) k_reduce_items(const double *__restrict__ part,
+__global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ part,
                                                       const int *__restrict__ item_start, int K,
                                                       const double *__restrict__ rec, const int *__restrict__ kperm,
                                                       double *__restrict__ dS)
@@ -1242,9 +1244,12 @@ __global__ void __launch_bounds__(128) k_reduce_items(const double *__restrict__
     for (int f = 0; f < 28; f++) t[f] = 0.0;
     if (p < K)
         for (int q = item_start[j] + w; q < item_start[j + 1]; q += 4) {
-            const double *src = part + ((size_t)q * kCols + m) * 28;
+            const float4 *src = reinterpret_cast<const float4 *>(part + ((size_t)q * kCols + m) * 28);
 #pragma unroll
-            for (int f = 0; f < 28; f++) t[f] += src[f];
+            for (int f = 0; f < 7; f++) {
+                const float4 v = src[f];
+                t[4 * f] += (double)v.x; t[4 * f + 1] += (double)v.y; t[4 * f + 2] += (double)v.z; t[4 * f + 3] += (double)v.w;
+            }
         }
     if (w > 0)
 #pragma unroll
@@ -1325,18 +1330,19 @@ int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool b
     pf->end(st);
     const size_t smem = sizeof(Smem2) + 128;
     if (tc_set_attributes()) return -1;
+    float *fpart = reinterpret_cast<float *>(part);   // item partials: FP32 register sums
     pf->begin(VBGS_PROF_PASS2, st);
     if (bf16)
         k_pass2_tc<true><<<tcap, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
-                                                         list, item_tile, item_lo, item_hi, nitems, rec, part, flags,
+                                                         list, item_tile, item_lo, item_hi, nitems, rec, fpart, flags,
                                                          pairs);
     else
         k_pass2_tc<false><<<tcap, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
-                                                          list, item_tile, item_lo, item_hi, nitems, rec, part, flags,
+                                                          list, item_tile, item_lo, item_hi, nitems, rec, fpart, flags,
                                                          pairs);
     pf->end(st);
     pf->begin(VBGS_PROF_REDUCE, st);
-    k_reduce_items<<<ntiles * 4, 128, 0, st>>>(part, item_start, K, rec, kperm, dS);
+    k_reduce_items<<<ntiles * 4, 128, 0, st>>>(fpart, item_start, K, rec, kperm, dS);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? (tmax ? 4 : 3) : -1;
 }
@@ -1378,6 +1384,45 @@ int tc_set_attributes()
     return 0;
 }
 
+// lse_n from the item partials of its point tile (FP32, log2 units: the
+// partials carry the tensor-core pass's FP32 sums), natural-unit lse in FP64,
+// the smallest lse per 32 points and per-block FP64 sums of lse.
+__global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part, const int *__restrict__ item_start,
+                                                 int64_t N, double *__restrict__ lse, double *__restrict__ lse_part,
+                                                 float *__restrict__ minlse)
+{
+    __shared__ double sh[2];
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (n < N) {
+        const int64_t P = n >> 7;
+        const size_t row = (size_t)(n & 127);
+        const int q0 = item_start[P], q1 = item_start[P + 1];
+        float M = -INFINITY;
+        for (int q = q0; q < q1; q++) M = fmaxf(M, part[(size_t)q * kRows + row].x);
+        float sm = 0.f;
+        for (int q = q0; q < q1; q++) {
+            const float2 p = part[(size_t)q * kRows + row];
+            if (p.y > 0.f) sm += p.y * ex2f(p.x - M);
+        }
+        v = (double)(M + __log2f(sm)) * 0.6931471805599453;
+        lse[n] = v;
+    }
+    float vm = n < N ? (float)v : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_down_sync(0xffffffffu, v, o);
+        vm = fminf(vm, __shfl_down_sync(0xffffffffu, vm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[threadIdx.x >> 5] = v;
+        const int64_t w = (int64_t)blockIdx.x * 2 + (threadIdx.x >> 5);
+        if (minlse && w * 32 < N) minlse[w] = vm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) lse_part[blockIdx.x] = sh[0] + sh[1];
+}
+
 // Pass-1 work items: at most kItemCap1 + point tiles, so item partials of
 // 128 (max, sum) pairs fit next to the other scratch.
 constexpr int kItemCap1 = 2048;
@@ -1393,10 +1438,11 @@ size_t tc_p1ub_floats(int64_t N, int K)
 }
 
 int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
-                    const float *rec32, double2 *part, size_t part_cap_doubles, float *tmax, int *p1plan,
+                    const float *rec32, double *part_buf, size_t part_cap_doubles, float *tmax, int *p1plan,
                     float *p1ub, int *flags, int num_sms, int tiles_per_item, const int **item_start_out,
                     cudaStream_t st, Prof *pf)
 {
+    float2 *part = reinterpret_cast<float2 *>(part_buf);
     const int ntiles = (K + kCols - 1) / kCols;
     const int ptiles = (int)((N + kRows - 1) / kRows);
     unsigned long long *pairs1 = pf->on ? pf->d_pairs + 1 : nullptr;
@@ -1442,6 +1488,16 @@ int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned
     pf->end(st);
     *item_start_out = item_start;
     return cudaGetLastError() == cudaSuccess ? (tmax ? 6 : 2) : -1;
+}
+
+int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, double *lse_part,
+                        float *minlse, double *sum_out, cudaStream_t st, Prof *pf)
+{
+    const int mb = (int)((N + 63) / 64);
+    pf->begin(VBGS_PROF_MERGE, st);
+    k_merge_tc<<<mb, 64, 0, st>>>(reinterpret_cast<const float2 *>(part_buf), item_start, N, lse, lse_part, minlse);
+    pf->end(st);
+    return launch_block_sum(lse_part, mb, sum_out, st, pf) < 0 ? -1 : 2;
 }
 
 } // namespace vbgs

@@ -180,9 +180,13 @@ int tc_set_attributes();
 // of every point's lse; tmax of the other tiles is -inf.  item_start_out: the
 // item table the lse merge reads.
 int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
-                    const float *rec32, double2 *part, size_t part_cap_doubles, float *tmax, int *p1plan,
+                    const float *rec32, double *part_buf, size_t part_cap_doubles, float *tmax, int *p1plan,
                     float *p1ub, int *flags, int num_sms, int tiles_per_item, const int **item_start_out,
                     cudaStream_t st, Prof *pf);
+// lse from pass 1's FP32 item partials, minlse per 32 points, sum of lse.
+int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, double *lse_part,
+                        float *minlse, double *sum_out, cudaStream_t st, Prof *pf);
+int launch_block_sum(const double *part, int n, double *sum_out, cudaStream_t st, Prof *pf);
 
 // Learned proposal (vbgs_proposal.cu).
 int prop_launch_kmeans(const float *rec32, int K, float csc, float *pts, float *cent, SortBuffers &sb, int *order,

@@ -47,7 +47,7 @@ EXPORTS = [
     "vbgs_init", "vbgs_update", "vbgs_elbo", "vbgs_get_posterior", "vbgs_get_stats",
     "vbgs_set_stats", "vbgs_get_frame_stats", "vbgs_get_lse", "vbgs_last_launch_count",
     "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_pairs", "vbgs_profile_name", "vbgs_probe_peaks",
-    "vbgs_estep_noalloc", "vbgs_update_batched", "vbgs_autotune", "vbgs_get_tuning",
+    "vbgs_estep_noalloc", "vbgs_update_batched", "vbgs_autotune", "vbgs_get_tuning", "vbgs_set_tuning",
     "vbgs_proposal_report", "vbgs_proposal_weights", "vbgs_proposal_grad", "vbgs_proposal_clusters",
     "vbgs_proposal_bounds", "vbgs_last_error", "vbgs_destroy",
 ]
@@ -106,6 +106,7 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
                                         C.POINTER(C.c_int64), C.c_int, _DP]
     lib.vbgs_autotune.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_char_p]
     lib.vbgs_get_tuning.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.vbgs_set_tuning.argtypes = [C.c_void_p, C.c_int, C.c_int]
     _FP = C.POINTER(C.c_float)
     lib.vbgs_proposal_report.argtypes = [C.c_void_p, _DP]
     lib.vbgs_proposal_weights.argtypes = [C.c_void_p, _FP, _FP]
@@ -281,6 +282,10 @@ def vbgs_autotune(ctx, points, cache_path: str | None = None) -> tuple[int, int]
     _check(lib().vbgs_autotune(ctx, ptr, N, cache_path.encode() if cache_path else None), ctx)
     del keep
     return vbgs_get_tuning(ctx)
+
+
+def vbgs_set_tuning(ctx, pass1_tiles: int, pass2_chunks: int) -> None:
+    _check(lib().vbgs_set_tuning(ctx, int(pass1_tiles), int(pass2_chunks)), ctx)
 
 
 def vbgs_get_tuning(ctx) -> tuple[int, int]:
