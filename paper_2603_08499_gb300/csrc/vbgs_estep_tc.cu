@@ -1235,20 +1235,32 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
                                                       const double *__restrict__ rec, const int *__restrict__ kperm,
                                                       double *__restrict__ dS)
 {
-    __shared__ double sh[3][32][29];
+    __shared__ float sh[3][32][29];
     const int j = blockIdx.x >> 2, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int m = (blockIdx.x & 3) * 32 + lane;
     const int p = j * kCols + m;
-    double t[28];
+    const int q0 = item_start[j], q1 = item_start[j + 1];
+    if (q0 == q1) {
+        // no pair of this tile was evaluated: zero statistics
+        if (w == 0 && p < K) {
+            const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
 #pragma unroll
-    for (int f = 0; f < 28; f++) t[f] = 0.0;
+            for (int f = 0; f < 28; f++) dS[dst * 28 + f] = 0.0;
+        }
+        return;
+    }
+    // the item partials are FP32 sums: add them in FP32 (a few terms), then
+    // shift to raw moments in FP64
+    float t[28];
+#pragma unroll
+    for (int f = 0; f < 28; f++) t[f] = 0.f;
     if (p < K)
-        for (int q = item_start[j] + w; q < item_start[j + 1]; q += 4) {
+        for (int q = q0 + w; q < q1; q += 4) {
             const float4 *src = reinterpret_cast<const float4 *>(part + ((size_t)q * kCols + m) * 28);
 #pragma unroll
             for (int f = 0; f < 7; f++) {
                 const float4 v = src[f];
-                t[4 * f] += (double)v.x; t[4 * f + 1] += (double)v.y; t[4 * f + 2] += (double)v.z; t[4 * f + 3] += (double)v.w;
+                t[4 * f] += v.x; t[4 * f + 1] += v.y; t[4 * f + 2] += v.z; t[4 * f + 3] += v.w;
             }
         }
     if (w > 0)
@@ -1256,21 +1268,21 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
         for (int f = 0; f < 28; f++) sh[w - 1][lane][f] = t[f];
     __syncthreads();
     if (w != 0 || p >= K) return;
-    for (int q = 0; q < 3; q++)
+    double d[28];
 #pragma unroll
-        for (int f = 0; f < 28; f++) t[f] += sh[q][lane][f];
+    for (int f = 0; f < 28; f++) d[f] = (double)t[f] + ((double)sh[0][lane][f] + (double)sh[1][lane][f] + (double)sh[2][lane][f]);
     double mk[6];
 #pragma unroll
     for (int i = 0; i < 6; i++) mk[i] = rec[(size_t)p * VBGS_REC + i];
     double out[28];
-    out[0] = t[0];
+    out[0] = d[0];
 #pragma unroll
-    for (int i = 0; i < 6; i++) out[1 + i] = t[1 + i] + t[0] * mk[i];
+    for (int i = 0; i < 6; i++) out[1 + i] = d[1 + i] + d[0] * mk[i];
     int u = 7;
 #pragma unroll
     for (int a = 0; a < 6; a++)
 #pragma unroll
-        for (int b = a; b < 6; b++, u++) out[u] = t[u] + mk[a] * t[1 + b] + t[1 + a] * mk[b] + t[0] * mk[a] * mk[b];
+        for (int b = a; b < 6; b++, u++) out[u] = d[u] + mk[a] * d[1 + b] + d[1 + a] * mk[b] + d[0] * mk[a] * mk[b];
     const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
 #pragma unroll
     for (int f = 0; f < 28; f++) dS[dst * 28 + f] = out[f];
