@@ -221,7 +221,8 @@ enum {
     VBGS_PROF_REDUCE = 3,  /* FP64 cross-split statistic reduction */
     VBGS_PROF_MSTEP = 4,   /* FP64 posterior update, KL terms, records */
     VBGS_PROF_MISC = 5,    /* staging, ELBO, commit */
-    VBGS_PROF_COUNT = 6
+    VBGS_PROF_PLAN = 6,    /* tensor-core work lists: tile bounds, skip lists, work items */
+    VBGS_PROF_COUNT = 7
 };
 int vbgs_profile_enable(vbgs_ctx *ctx, int on);
 int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset);

@@ -1335,7 +1335,7 @@ int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool b
     int *item_start = list + (size_t)ntiles * nchunks;
     int *item_tile = item_start + ntiles + 1, *item_lo = item_tile + icap, *item_hi = item_lo + icap;
     int *nitems = item_hi + icap;
-    pf->begin(VBGS_PROF_PASS2, st);
+    pf->begin(VBGS_PROF_PLAN, st);
     if (tmax) k_p2_plan<<<ntiles, 256, 0, st>>>(tmax, minlse, N, ntiles, counts, list);
     k_p2_items<<<1, 1024, 0, st>>>(tmax ? counts : nullptr, ntiles, nchunks, cmin, tcap, item_start, item_tile,
                                    item_lo, item_hi, nitems);
@@ -1475,7 +1475,7 @@ int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned
         }
     }
     const int target = tmax ? std::min(icap, std::max(ptiles + 1, 8 * num_sms)) : icap;
-    pf->begin(VBGS_PROF_PASS1, st);
+    pf->begin(VBGS_PROF_PLAN, st);
     if (tmax) {
         const size_t nt = tc_tmax_floats(N, K);
         float *boxes = p1ub + (size_t)ptiles * ntiles;

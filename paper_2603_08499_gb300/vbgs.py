@@ -52,8 +52,8 @@ EXPORTS = [
     "vbgs_proposal_bounds", "vbgs_last_error", "vbgs_destroy",
 ]
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
-PROF_COUNT = 6
-PROF_NAMES = ["pass1", "merge", "pass2", "reduce", "mstep", "misc"]
+PROF_COUNT = 7
+PROF_NAMES = ["pass1", "merge", "pass2", "reduce", "mstep", "misc", "plan"]
 
 
 class VbgsError(RuntimeError):
