@@ -152,6 +152,11 @@ int ensure_capacity(vbgs_ctx *ctx, int64_t N)
         if ((rc = dalloc(ctx, &ctx->d_plan, pneed))) return rc;
         ctx->plan_cap = pneed;
     }
+    if (is_tc(ctx) && ctx->ncap > ctx->xhl_cap) {
+        if ((rc = dalloc(ctx, &ctx->d_Xhl, (size_t)ctx->ncap * 16)) || (rc = dalloc(ctx, &ctx->d_lse2f, (size_t)ctx->ncap)))
+            return rc;
+        ctx->xhl_cap = ctx->ncap;
+    }
     const size_t p1need = tc_p1plan_ints(std::max<int64_t>(N, 1), ctx->K);
     if (is_tc(ctx) && p1need > ctx->p1plan_cap) {
         if ((rc = dalloc(ctx, &ctx->d_p1plan, p1need)) ||
@@ -282,18 +287,18 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
     B.minlse = skip ? ctx->d_minlse : nullptr;
     if (is_tc(ctx)) {
         const int *item_start = nullptr;
-        int l = launch_pass1_tc(B.X, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
-                                ctx->d_rec32, ctx->d_part, ctx->part_cap, B.tmax,
+        int l = launch_pass1_tc(B.X, ctx->d_Xhl, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles,
+                                ctx->d_tc_hdr, ctx->d_rec32, ctx->d_part, ctx->part_cap, B.tmax,
                                 ctx->d_p1plan, ctx->d_p1ub, ctx->d_flags, ctx->num_sms, ctx->tune_p1, &item_start,
                                 ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ctx->launches += l;
-        l = launch_lse_merge_tc(ctx->d_part, N, item_start, lse, ctx->d_lse_part, B.tmax ? ctx->d_minlse : nullptr,
-                                ctx->d_scal + SC_SUM_LSE, ctx->stream, &ctx->prof);
+        l = launch_lse_merge_tc(ctx->d_part, N, item_start, lse, ctx->d_lse2f, ctx->d_lse_part,
+                                B.tmax ? ctx->d_minlse : nullptr, ctx->d_scal + SC_SUM_LSE, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "lse merge launch failed");
         ctx->launches += l;
         if (want_stats) {
-            l = launch_pass2_tc(B.X, lse, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
+            l = launch_pass2_tc(ctx->d_Xhl, ctx->d_lse2f, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
                                 ctx->d_rec, B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
                                 ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->tune_p2, ctx->stream, &ctx->prof);
             if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
@@ -724,7 +729,7 @@ void free_all(vbgs_ctx *ctx)
                     ctx->d_flags, ctx->d_X, ctx->d_lse, ctx->d_lse_part, ctx->d_part,
                     ctx->d_kperm, ctx->d_kinv, ctx->d_pidx, ctx->d_Xs, ctx->d_tmax, ctx->d_minlse,
                     ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp, ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_plan,
-                    ctx->d_p1plan, ctx->d_p1ub, ctx->d_tile_dirty};
+                    ctx->d_p1plan, ctx->d_p1ub, ctx->d_tile_dirty, ctx->d_Xhl, ctx->d_lse2f};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     {

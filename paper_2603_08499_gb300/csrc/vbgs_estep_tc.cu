@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
 // of each 32-point row block and 128-component tile.
 // ---------------------------------------------------------------------------
 template <bool BF16>
-__global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__restrict__ X, int64_t N, int K,
+__global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restrict__ Xhl, int64_t N, int K,
                                                             const unsigned char *__restrict__ tiles,
                                                             const float *__restrict__ hdr, int ntiles,
                                                             const int *__restrict__ list,
@@ -393,9 +393,8 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const double *__rest
         float xh[6], xl[6];
 #pragma unroll
         for (int i = 0; i < 6; i++) {
-            double v = X[nn * VBGS_XS + i];
-            xh[i] = (float)v;
-            xl[i] = (float)(v - (double)xh[i]);
+            xh[i] = Xhl[nn * 16 + i];
+            xl[i] = Xhl[nn * 16 + 8 + i];
         }
         float mrun = -INFINITY, srun = 0.f;
         bool ok = true;
@@ -927,7 +926,7 @@ __global__ void __launch_bounds__(1024) k_p2_items(const int *__restrict__ count
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__restrict__ X, const double *__restrict__ lse,
+__global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restrict__ Xhl, const float *__restrict__ lse2f,
                                                             int64_t N, int K, const unsigned char *__restrict__ tiles,
                                                             const float *__restrict__ hdr, int ntiles,
                                                             const int *__restrict__ counts,
@@ -994,18 +993,16 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
             const int64_t n = c0 + pt;
             const int64_t nn = n < N ? n : N - 1;
             float d[6];
+            const float *xp = Xhl + nn * 16;
             if (tid < 64) {
                 // logits: the tile's frame, like the coefficients
 #pragma unroll
-                for (int i = 0; i < 6; i++) {
-                    const double v = X[nn * VBGS_XS + i];
-                    const float xh = (float)v, xl = (float)(v - (double)xh);
-                    d[i] = ((xh - hf[i]) + (xl - hf[6 + i])) * hf[12 + i];
-                }
+                for (int i = 0; i < 6; i++) d[i] = ((xp[i] - hf[i]) + (xp[8 + i] - hf[6 + i])) * hf[12 + i];
             } else {
                 // statistics: the chunk's frame, origin at its first point
+                const float *xo = Xhl + c0 * 16;
 #pragma unroll
-                for (int i = 0; i < 6; i++) d[i] = (float)(X[nn * VBGS_XS + i] - X[c0 * VBGS_XS + i]) * hf[12 + i];
+                for (int i = 0; i < 6; i++) d[i] = ((xp[i] - xo[i]) + (xp[8 + i] - xo[8 + i])) * hf[12 + i];
             }
             float f[kFeat];
             f[0] = 1.f;
@@ -1028,7 +1025,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
                     *reinterpret_cast<uint4 *>(bh + b1_off(pt, 8 * q)) = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
                     *reinterpret_cast<uint4 *>(bl + b1_off(pt, 8 * q)) = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
                 }
-                S.lse2[st][pt] = n < N ? (float)(lse[n] * 1.4426950408889634) : INFINITY;
+                S.lse2[st][pt] = n < N ? lse2f[n] : INFINITY;
             } else {
                 unsigned char *bh = S.B2[st], *bl = S.B2[st] + kB2Bytes;
 #pragma unroll
@@ -1054,7 +1051,16 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
 #pragma unroll
         for (int i = 0; i < 6; i++) sc[i] = 1.f / hf[12 + i];
         const int kcomp = j * kCols + m;
-        const double *mrec = rec + (size_t)(kcomp < K ? kcomp : K - 1) * VBGS_REC;
+        float mh[6], ml[6];   // the component's mean as an FP32 hi/lo pair
+        {
+            const double *mrec = rec + (size_t)(kcomp < K ? kcomp : K - 1) * VBGS_REC;
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                const double v = mrec[i];
+                mh[i] = (float)v;
+                ml[i] = (float)(v - (double)mh[i]);
+            }
+        }
         int64_t stagepos[2] = {0, 0};
         auto add_d2 = [&](int stage) {
             uint32_t v[32];
@@ -1063,7 +1069,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const double *__rest
             const int64_t c0 = chunk_at((int)stagepos[stage]) * kChunk2;
             float dl[6], s1[6];
 #pragma unroll
-            for (int i = 0; i < 6; i++) dl[i] = (float)(X[c0 * VBGS_XS + i] - mrec[i]);
+            for (int i = 0; i < 6; i++) dl[i] = (Xhl[c0 * 16 + i] - mh[i]) + (Xhl[c0 * 16 + 8 + i] - ml[i]);
             const float nn = __uint_as_float(v[0]);
             st[0] += nn;
 #pragma unroll
@@ -1316,7 +1322,7 @@ size_t tc_plan_ints(int64_t N, int K)
     return nt * (size_t)(1 + (N + kChunk2 - 1) / kChunk2) + (nt + 1) + 3 * (size_t)tc_item_cap(K) + 1;
 }
 
-int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
+int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
                     cudaStream_t st, Prof *pf)
@@ -1345,11 +1351,11 @@ int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool b
     float *fpart = reinterpret_cast<float *>(part);   // item partials: FP32 register sums
     pf->begin(VBGS_PROF_PASS2, st);
     if (bf16)
-        k_pass2_tc<true><<<tcap, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
+        k_pass2_tc<true><<<tcap, kThreadsTC, smem, st>>>(Xhl, lse2f, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
                                                          list, item_tile, item_lo, item_hi, nitems, rec, fpart, flags,
                                                          pairs);
     else
-        k_pass2_tc<false><<<tcap, kThreadsTC, smem, st>>>(X, lse, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
+        k_pass2_tc<false><<<tcap, kThreadsTC, smem, st>>>(Xhl, lse2f, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
                                                           list, item_tile, item_lo, item_hi, nitems, rec, fpart, flags,
                                                          pairs);
     pf->end(st);
@@ -1396,12 +1402,31 @@ int tc_set_attributes()
     return 0;
 }
 
+// Points as FP32 hi/lo pairs, 16 floats per point (hi at 0-5, lo at 8-13):
+// the tensor-core builders then form differences in FP32 double-float
+// arithmetic instead of FP64.
+__global__ void k_split_points(const double *__restrict__ X, int64_t N, float *__restrict__ Xhl)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * 8) return;
+    const int64_t n = i >> 3;
+    const int q = (int)(i & 7);
+    float hi = 0.f, lo = 0.f;
+    if (q < 6) {
+        const double v = X[n * VBGS_XS + q];
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    }
+    Xhl[n * 16 + q] = hi;
+    Xhl[n * 16 + 8 + q] = lo;
+}
+
 // lse_n from the item partials of its point tile (FP32, log2 units: the
 // partials carry the tensor-core pass's FP32 sums), natural-unit lse in FP64,
 // the smallest lse per 32 points and per-block FP64 sums of lse.
 __global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part, const int *__restrict__ item_start,
-                                                 int64_t N, double *__restrict__ lse, double *__restrict__ lse_part,
-                                                 float *__restrict__ minlse)
+                                                 int64_t N, double *__restrict__ lse, float *__restrict__ lse2f,
+                                                 double *__restrict__ lse_part, float *__restrict__ minlse)
 {
     __shared__ double sh[2];
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1417,8 +1442,10 @@ __global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part
             const float2 p = part[(size_t)q * kRows + row];
             if (p.y > 0.f) sm += p.y * ex2f(p.x - M);
         }
-        v = (double)(M + __log2f(sm)) * 0.6931471805599453;
+        const float l2 = M + __log2f(sm);
+        v = (double)l2 * 0.6931471805599453;
         lse[n] = v;
+        lse2f[n] = l2;
     }
     float vm = n < N ? (float)v : INFINITY;
 #pragma unroll
@@ -1449,12 +1476,17 @@ size_t tc_p1ub_floats(int64_t N, int K)
     return pt * (size_t)((K + kCols - 1) / kCols) + 12 * pt;   // ub, then the point-tile boxes
 }
 
-int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
-                    const float *rec32, double *part_buf, size_t part_cap_doubles, float *tmax, int *p1plan,
-                    float *p1ub, int *flags, int num_sms, int tiles_per_item, const int **item_start_out,
-                    cudaStream_t st, Prof *pf)
+int launch_pass1_tc(const double *X, float *Xhl, int64_t N, int K, bool bf16, const unsigned char *tiles,
+                    const float *hdr, const float *rec32, double *part_buf, size_t part_cap_doubles, float *tmax,
+                    int *p1plan, float *p1ub, int *flags, int num_sms, int tiles_per_item,
+                    const int **item_start_out, cudaStream_t st, Prof *pf)
 {
     float2 *part = reinterpret_cast<float2 *>(part_buf);
+    if (N > 0) {
+        pf->begin(VBGS_PROF_PLAN, st);
+        k_split_points<<<(unsigned)((N * 8 + 255) / 256), 256, 0, st>>>(X, N, Xhl);
+        pf->end(st);
+    }
     const int ntiles = (K + kCols - 1) / kCols;
     const int ptiles = (int)((N + kRows - 1) / kRows);
     unsigned long long *pairs1 = pf->on ? pf->d_pairs + 1 : nullptr;
@@ -1492,22 +1524,23 @@ int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned
     pf->begin(VBGS_PROF_PASS1, st);
     const int *lst = tmax ? list : nullptr;
     if (bf16)
-        k_pass1_tc<true><<<target, kThreadsTC, smem, st>>>(X, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
+        k_pass1_tc<true><<<target, kThreadsTC, smem, st>>>(Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
                                                            item_hi, nitems, part, tmax, flags, pairs1);
     else
-        k_pass1_tc<false><<<target, kThreadsTC, smem, st>>>(X, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
+        k_pass1_tc<false><<<target, kThreadsTC, smem, st>>>(Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
                                                             item_hi, nitems, part, tmax, flags, pairs1);
     pf->end(st);
     *item_start_out = item_start;
-    return cudaGetLastError() == cudaSuccess ? (tmax ? 6 : 2) : -1;
+    return cudaGetLastError() == cudaSuccess ? (tmax ? 6 : 2) + (N > 0 ? 1 : 0) : -1;
 }
 
-int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, double *lse_part,
-                        float *minlse, double *sum_out, cudaStream_t st, Prof *pf)
+int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
+                        double *lse_part, float *minlse, double *sum_out, cudaStream_t st, Prof *pf)
 {
     const int mb = (int)((N + 63) / 64);
     pf->begin(VBGS_PROF_MERGE, st);
-    k_merge_tc<<<mb, 64, 0, st>>>(reinterpret_cast<const float2 *>(part_buf), item_start, N, lse, lse_part, minlse);
+    k_merge_tc<<<mb, 64, 0, st>>>(reinterpret_cast<const float2 *>(part_buf), item_start, N, lse, lse2f, lse_part,
+                                  minlse);
     pf->end(st);
     return launch_block_sum(lse_part, mb, sum_out, st, pf) < 0 ? -1 : 2;
 }

@@ -168,7 +168,7 @@ size_t tc_plan_ints(int64_t N, int K);
 size_t tc_pass2_part_doubles(int K);
 size_t tc_p1plan_ints(int64_t N, int K);
 size_t tc_p1ub_floats(int64_t N, int K);
-int launch_pass2_tc(const double *X, const double *lse, int64_t N, int K, bool bf16, const unsigned char *tiles,
+int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
                     cudaStream_t st, Prof *pf);
@@ -179,13 +179,13 @@ int tc_set_attributes();
 // certified logit bound over the point tile is within 50 nats of a lower bound
 // of every point's lse; tmax of the other tiles is -inf.  item_start_out: the
 // item table the lse merge reads.
-int launch_pass1_tc(const double *X, int64_t N, int K, bool bf16, const unsigned char *tiles, const float *hdr,
-                    const float *rec32, double *part_buf, size_t part_cap_doubles, float *tmax, int *p1plan,
-                    float *p1ub, int *flags, int num_sms, int tiles_per_item, const int **item_start_out,
-                    cudaStream_t st, Prof *pf);
+int launch_pass1_tc(const double *X, float *Xhl, int64_t N, int K, bool bf16, const unsigned char *tiles,
+                    const float *hdr, const float *rec32, double *part_buf, size_t part_cap_doubles, float *tmax,
+                    int *p1plan, float *p1ub, int *flags, int num_sms, int tiles_per_item,
+                    const int **item_start_out, cudaStream_t st, Prof *pf);
 // lse from pass 1's FP32 item partials, minlse per 32 points, sum of lse.
-int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, double *lse_part,
-                        float *minlse, double *sum_out, cudaStream_t st, Prof *pf);
+int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
+                        double *lse_part, float *minlse, double *sum_out, cudaStream_t st, Prof *pf);
 int launch_block_sum(const double *part, int n, double *sum_out, cudaStream_t st, Prof *pf);
 
 // Learned proposal (vbgs_proposal.cu).
@@ -298,6 +298,9 @@ struct vbgs_ctx {
     size_t plan_cap = 0;
     int *d_p1plan = nullptr;               // pass-1 tile lists and work items
     float *d_p1ub = nullptr;               // pass-1 logit bounds per (point tile, component tile)
+    float *d_Xhl = nullptr;                // points as FP32 hi/lo pairs (tensor-core builders)
+    float *d_lse2f = nullptr;              // lse in log2 units, FP32 (tensor-core pass 2)
+    int64_t xhl_cap = 0;
     size_t p1plan_cap = 0;
     float *d_tc_hdr = nullptr;
     int *d_tile_dirty = nullptr;           // per 128-position tile: a record changed since its last coefficient build

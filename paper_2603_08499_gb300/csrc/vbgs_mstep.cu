@@ -199,7 +199,7 @@ __device__ void block_sums4(double v0, double v1, double v2, double v3, double *
 // recomputed, 0: q = p) and the frame count Delta N_k.
 constexpr int kKS = 36;
 
-__global__ void __launch_bounds__(128) k_mstep(MstepParams P, const double *__restrict__ m0,
+__global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__restrict__ m0,
                                                const double *__restrict__ Spast,
                                                const double *__restrict__ dS,
                                                const int *__restrict__ kperm,
@@ -453,7 +453,9 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
     double *bpart = cache + (size_t)K * kPC;
     double *kls = bpart + (size_t)nb * 4;
     pf->begin(VBGS_PROF_MSTEP, st);
-    k_mstep<<<nb, 128, 0, st>>>(P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags, tile_dirty);
+    // 64 threads a block: the per-component work is long and uneven (skipped
+    // components return at once), so smaller blocks spread it over more SMs
+    k_mstep<<<(K + 63) / 64, 64, 0, st>>>(P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags, tile_dirty);
     pf->end(st);
     // KL terms and their sums beside the next E-step
     if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return -1;
