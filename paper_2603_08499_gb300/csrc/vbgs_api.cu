@@ -233,8 +233,8 @@ int run_mstep(vbgs_ctx *ctx, const double *dS)
     ctx->side_pending = true;
     ctx->launches += l;
     if (is_tc(ctx)) {
-        l = launch_coef_tiles(ctx->d_rec, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
-                              ctx->d_tile_dirty, ctx->stream, &ctx->prof);
+        l = launch_coef_tiles(ctx->d_rec, ctx->d_rec32, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles,
+                              ctx->d_tc_hdr, ctx->d_tile_dirty, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "coefficient tile launch failed");
         ctx->launches += l;
     }

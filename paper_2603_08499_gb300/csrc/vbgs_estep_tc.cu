@@ -162,6 +162,45 @@ __device__ __forceinline__ float ex2f(float x)
     return y;
 }
 
+// Double-float arithmetic: a value as an unevaluated FP32 sum h + l (about
+// 48 significant bits), on the FP32 pipe.  Error-free transformations of
+// Knuth (two-sum), Dekker (fast two-sum) and the FMA product.
+struct dfl {
+    float h, l;
+};
+__device__ __forceinline__ dfl df_fast_sum(float a, float b)   // |a| >= |b|
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_two_sum(float a, float b)
+{
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y)
+{
+    const dfl s = df_two_sum(x.h, y.h);
+    return df_fast_sum(s.h, s.l + (x.l + y.l));
+}
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y)
+{
+    const float p = __fmul_rn(x.h, y.h);   // never contracted into a later add
+    const float e = fmaf(x.h, y.l, fmaf(x.l, y.h, fmaf(x.h, y.h, -p)));
+    return df_fast_sum(p, e);
+}
+__device__ __forceinline__ dfl df_mulf(dfl x, float f)
+{
+    const float p = __fmul_rn(x.h, f);
+    return df_fast_sum(p, fmaf(x.l, f, fmaf(x.h, f, -p)));
+}
+// FP64 -> double-float
+__device__ __forceinline__ dfl df_from(double v)
+{
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
 // Byte offset of (row, feature) in a 128 x 32 K-major core-matrix operand.
 __host__ __device__ constexpr int opnd_off(int r, int f) { return (r >> 3) * 512 + (f >> 3) * 128 + (r & 7) * 16 + (f & 7) * 2; }
 
@@ -197,18 +236,37 @@ template <> struct H<true> {
 
 // ---------------------------------------------------------------------------
 // Coefficient tiles.  One CTA per component tile (128 threads = components at
-// sorted positions).  FP64 throughout, then scaled by 2^-e_j so the largest
-// coefficient of the tile is about 2^14, and split hi/lo.
-// Header (32 floats): o_hi[6], o_lo[6], inv_s[6], outscale (2^e_j), pad.
+// sorted positions).  In the tile's frame y = (x - o) * inv_s the log2 logit
+// is c' - (y - mu)^T P (y - mu) / 2 with P = S Lambda2 S (S = diag(1/inv_s),
+// Lambda2 = log2(e) nu W) and mu = (m - o) * inv_s, expanded as
+// coef0 + coef1 . y + sum_{a<=b} C_ab y_a y_b and scaled by 2^-e_j (largest
+// coefficient of the tile about 2^14) before the hi/lo split.
+//
+// Double-float arithmetic (FP32 pairs) instead of FP64, whose rate on this
+// part is 1/64 of FP32: P from the record's M as FP32 pairs; then coef1 and
+// coef0 from the matrix that the stored hi/lo pairs of C represent (Pr), so
+// the three parts expand one quadratic form centred exactly at mu and no
+// error grows with |mu|.  FP64 only to split the record's FP64 values.
+// Header (32 floats): o_hi[6], o_lo[6] (zero), inv_s[6], outscale (2^e_j), pad.
 // ---------------------------------------------------------------------------
 template <bool BF16>
-__global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ rec, int K,
-                                                    unsigned char *__restrict__ tiles, float *__restrict__ hdr,
-                                                    int *__restrict__ dirty)
+__device__ __forceinline__ void split_store(dfl v, unsigned char *hi, unsigned char *lo, int off, float &rep)
 {
     using HT = typename H<BF16>::T;
-    __shared__ double red[6][4];
-    __shared__ double frame[13];
+    const HT h = H<BF16>::from_f(v.h);
+    const HT l = H<BF16>::from_f((v.h - H<BF16>::to_f(h)) + v.l);
+    *reinterpret_cast<HT *>(hi + off) = h;
+    *reinterpret_cast<HT *>(lo + off) = l;
+    rep = H<BF16>::to_f(h) + H<BF16>::to_f(l);
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ rec, const float *__restrict__ rec32,
+                                                    int K, unsigned char *__restrict__ tiles,
+                                                    float *__restrict__ hdr, int *__restrict__ dirty)
+{
+    __shared__ float red[7][4];
+    __shared__ float frame[12];   // origin o (6), inv_s (6)
     const int t = threadIdx.x, j = blockIdx.x, lane = t & 31, w = t >> 5;
     // a tile whose records were not rewritten since its last build is current
     if (dirty) {
@@ -218,120 +276,144 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
     }
     const int k = j * kCols + t;
     const bool valid = k < K;
-    const double *r = rec + (size_t)(valid ? k : K - 1) * VBGS_REC;
-    double m[6];
+    const size_t rk = (size_t)(valid ? k : K - 1) * VBGS_REC;
+    const float *r32 = rec32 + rk;
+    const double *r = rec + rk;
+    float mf[6];
+    dfl M[21];   // sqrt(log2 e) * M: FP32 record value plus its FP64 remainder
 #pragma unroll
-    for (int i = 0; i < 6; i++) m[i] = r[i];
+    for (int i = 0; i < 6; i++) mf[i] = r32[i];
+#pragma unroll
+    for (int q = 0; q < 21; q++) {
+        const float h = r32[6 + q];
+        M[q] = {h, (float)(r[6 + q] * 1.2011224087864498 - (double)h)};
+    }
     const int nvalid = min(kCols, K - j * kCols);
     // frame origin: precision-weighted mean of the tile's means (weight
-    // tr(nu W) = |M|_F^2), so the tightest components sit near the origin
-    double wk = 0.0;
+    // tr(nu W), proportional to |M|_F^2), so the tightest components sit
+    // near the origin; any origin is exact, it only has to be stored
+    float wk = 0.f;
     if (valid)
 #pragma unroll
-        for (int q = 0; q < 21; q++) wk += r[6 + q] * r[6 + q];
-    __shared__ double wred[4];
-    {
-        double v = wk;
+        for (int q = 0; q < 21; q++) wk = fmaf(M[q].h, M[q].h, wk);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) wred[w] = v;
-    }
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-        double v = valid ? wk * m[i] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[i][w] = v;
-    }
-    __syncthreads();
-    if (t < 6) frame[t] = (red[t][0] + red[t][1] + red[t][2] + red[t][3]) / (wred[0] + wred[1] + wred[2] + wred[3]);
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-        double d = valid ? m[i] - frame[i] : 0.0;
-        double v = d * d;
+    for (int i = 0; i < 7; i++) {
+        float v = i < 6 ? wk * mf[i] : wk;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[i][w] = v;
     }
     __syncthreads();
     if (t < 6) {
-        double sd = sqrt((red[t][0] + red[t][1] + red[t][2] + red[t][3]) / nvalid);
-        float inv = (float)(1.0 / fmax(sd, 0.05));
-        float ohi = (float)frame[t];
-        float olo = (float)(frame[t] - (double)ohi);
-        hdr[(size_t)j * 32 + t] = ohi;
-        hdr[(size_t)j * 32 + 6 + t] = olo;
-        hdr[(size_t)j * 32 + 12 + t] = inv;
-        // the frame the coefficients are expressed in is exactly the stored one
-        frame[t] = (double)ohi + (double)olo;
-        frame[6 + t] = 1.0 / (double)inv;
+        const float tw = (red[6][0] + red[6][1]) + (red[6][2] + red[6][3]);
+        frame[t] = ((red[t][0] + red[t][1]) + (red[t][2] + red[t][3])) / tw;
     }
     __syncthreads();
-    // Lambda2 = log2(e) M^T M, M packed lower triangular
-    double Mf[6][6];
 #pragma unroll
-    for (int i = 0; i < 6; i++)
+    for (int i = 0; i < 6; i++) {
+        const float d = valid ? mf[i] - frame[i] : 0.f;
+        float v = d * d;
 #pragma unroll
-        for (int q = 0; q < 6; q++) Mf[i][q] = (q <= i) ? r[6 + tri(i, q)] : 0.0;
-    const double L2E = 1.4426950408889634;
-    double Lp[6][6], mp[6];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[i][w] = v;
+    }
+    __syncthreads();
+    if (t < 6) {
+        const float sd = sqrtf(((red[t][0] + red[t][1]) + (red[t][2] + red[t][3])) / (float)nvalid);
+        const float inv = 1.f / fmaxf(sd, 0.05f);
+        hdr[(size_t)j * 32 + t] = frame[t];
+        hdr[(size_t)j * 32 + 6 + t] = 0.f;
+        hdr[(size_t)j * 32 + 12 + t] = inv;
+        frame[6 + t] = inv;
+    }
+    __syncthreads();
+    float o[6], inv[6], sa[6];
 #pragma unroll
-    for (int a = 0; a < 6; a++) {
-        mp[a] = (m[a] - frame[a]) / frame[6 + a];
+    for (int i = 0; i < 6; i++) {
+        o[i] = frame[i];
+        inv[i] = frame[6 + i];
+        sa[i] = 1.f / inv[i];   // its rounding rescales the frame axis: exact for the form
+    }
+    // P = S M^T M S (M packed lower triangular: M_la != 0 for l >= a)
+    dfl P[21];
+#pragma unroll
+    for (int a = 0; a < 6; a++)
 #pragma unroll
         for (int b = a; b < 6; b++) {
-            double v = 0.0;
+            dfl v = df_mul(M[tri(b, a)], M[tri(b, b)]);
 #pragma unroll
-            for (int l = 0; l < 6; l++) v += Mf[l][a] * Mf[l][b];
-            v *= L2E * frame[6 + a] * frame[6 + b];
-            Lp[a][b] = v;
-            Lp[b][a] = v;
+            for (int l = b + 1; l < 6; l++) v = df_add(v, df_mul(M[tri(l, a)], M[tri(l, b)]));
+            P[tri(b, a)] = df_mulf(df_mulf(v, sa[a]), sa[b]);
         }
-    }
-    double coef[kFeat];
-    double quad = 0.0;
+    // mu = (m - o) * inv_s
+    dfl mu[6];
 #pragma unroll
-    for (int a = 0; a < 6; a++) {
-        double bl = 0.0;
+    for (int a = 0; a < 6; a++) mu[a] = df_mulf(df_from(r[a] - (double)o[a]), inv[a]);
+    // tile-wide largest coefficient (estimate) -> power-of-two scale
+    float mx = 0.f;
+    if (valid) {
+        float c0 = 0.f;
 #pragma unroll
-        for (int b = 0; b < 6; b++) bl += Lp[a][b] * mp[b];
-        coef[1 + a] = bl;
-        quad += mp[a] * bl;
+        for (int a = 0; a < 6; a++) {
+            float bl = 0.f;
+#pragma unroll
+            for (int b = 0; b < 6; b++) bl = fmaf(P[a >= b ? tri(a, b) : tri(b, a)].h, mu[b].h, bl);
+            mx = fmaxf(mx, fabsf(bl));
+            c0 = fmaf(mu[a].h, bl, c0);
+        }
+        mx = fmaxf(mx, fabsf(r32[27] - 0.5f * c0));
+#pragma unroll
+        for (int q = 0; q < 21; q++) mx = fmaxf(mx, fabsf(P[q].h));
     }
-    coef[0] = r[27] * L2E - 0.5 * quad;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) red[0][w] = mx;
+    __syncthreads();
+    mx = fmaxf(fmaxf(red[0][0], red[0][1]), fmaxf(red[0][2], red[0][3]));
+    int e = 0;
+    if (mx > 0.f) e = ilogbf(mx) + 1 - 14;   // 2^(e+13) <= mx < 2^(e+14)
+    const float sc = ldexpf(1.f, -e), isc = ldexpf(1.f, e);
+    if (t == 0) hdr[(size_t)j * 32 + 18] = isc;
+    unsigned char *hi = tiles + (size_t)j * kTileBytes;
+    unsigned char *lo = hi + kOperandBytes;
+    // quadratic part: C_aa = -P_aa / 2, C_ab = -P_ab (a < b), scaled by a
+    // power of two (exact), split; Pr: the matrix the stored pairs represent
+    float Pr[21];
     {
         int u = 7;
 #pragma unroll
         for (int a = 0; a < 6; a++)
 #pragma unroll
-            for (int b = a; b < 6; b++, u++) coef[u] = (a == b) ? -0.5 * Lp[a][a] : -Lp[a][b];
+            for (int b = a; b < 6; b++, u++) {
+                const float f = valid ? (a == b ? -0.5f : -1.f) * sc : 0.f;
+                const dfl pv = P[tri(b, a)];
+                float rep;
+                split_store<BF16>({pv.h * f, pv.l * f}, hi, lo, opnd_off(t, u), rep);
+                Pr[tri(b, a)] = (a == b ? -2.f : -1.f) * isc * rep;
+            }
     }
 #pragma unroll
-    for (int f = 28; f < kFeat; f++) coef[f] = 0.0;
-    // tile-wide largest magnitude -> power-of-two scale
-    double mx = 0.0;
-    if (valid)
+    for (int f = 28; f < kFeat; f++) {
+        float rep;
+        split_store<BF16>({0.f, 0.f}, hi, lo, opnd_off(t, f), rep);
+    }
+    // linear and constant parts: coef1 = Pr mu, coef0 = c' - mu . Pr mu / 2
+    dfl quad = {0.f, 0.f};
 #pragma unroll
-        for (int f = 0; f < 28; f++) mx = fmax(mx, fabs(coef[f]));
+    for (int a = 0; a < 6; a++) {
+        dfl bl = df_mulf(mu[0], Pr[tri(a, 0)]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) red[0][w] = mx;
-    __syncthreads();
-    mx = fmax(fmax(red[0][0], red[0][1]), fmax(red[0][2], red[0][3]));
-    int e = 0;
-    if (mx > 0.0) e = (int)ceil(log2(mx)) - 14;
-    const double sc = ldexp(1.0, -e);
-    if (t == 0) hdr[(size_t)j * 32 + 18] = (float)ldexp(1.0, e);
-    unsigned char *hi = tiles + (size_t)j * kTileBytes;
-    unsigned char *lo = hi + kOperandBytes;
-#pragma unroll
-    for (int f = 0; f < kFeat; f++) {
-        double v = valid ? coef[f] * sc : 0.0;   // padding columns are masked by pass 1
-        HT h = H<BF16>::from_f((float)v);
-        HT l = H<BF16>::from_f((float)(v - (double)H<BF16>::to_f(h)));
-        *reinterpret_cast<HT *>(hi + opnd_off(t, f)) = h;
-        *reinterpret_cast<HT *>(lo + opnd_off(t, f)) = l;
+        for (int b = 1; b < 6; b++) bl = df_add(bl, df_mulf(mu[b], Pr[a >= b ? tri(a, b) : tri(b, a)]));
+        quad = df_add(quad, df_mul(mu[a], bl));
+        const float f = valid ? sc : 0.f;   // padding columns are masked by pass 1
+        float rep;
+        split_store<BF16>({bl.h * f, bl.l * f}, hi, lo, opnd_off(t, 1 + a), rep);
+    }
+    const dfl c0 = df_add(df_from(r[27] * 1.4426950408889634), {-0.5f * quad.h, -0.5f * quad.l});
+    {
+        const float f = valid ? sc : 0.f;
+        float rep;
+        split_store<BF16>({c0.h * f, c0.l * f}, hi, lo, opnd_off(t, 0), rep);
     }
 }
 
@@ -1061,12 +1143,12 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
                 ml[i] = (float)(v - (double)mh[i]);
             }
         }
-        int64_t stagepos[2] = {0, 0};
+        int64_t stagepos0 = 0, stagepos1 = 0;   // chunk held by each operand stage
         auto add_d2 = [&](int stage) {
             uint32_t v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 128u + (uint32_t)(stage * kFeat), v);
             tmem_wait_ld();
-            const int64_t c0 = chunk_at((int)stagepos[stage]) * kChunk2;
+            const int64_t c0 = chunk_at((int)(stage ? stagepos1 : stagepos0)) * kChunk2;
             float dl[6], s1[6];
 #pragma unroll
             for (int i = 0; i < 6; i++) dl[i] = (Xhl[c0 * 16 + i] - mh[i]) + (Xhl[c0 * 16 + 8 + i] - ml[i]);
@@ -1087,7 +1169,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
         };
         int64_t c = next_chunk(cbeg);
         int u = 0;
-        if (c < cend) { build(c, 0); stagepos[0] = c; }
+        if (c < cend) { build(c, 0); stagepos0 = c; }
         while (c < cend && ok) {
             const int s = u & 1;
             if (u >= 1) {
@@ -1099,7 +1181,10 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
                 add_d2((u + 1) & 1);
             }
             const int64_t cn = next_chunk(c + 1);
-            if (cn < cend) { build(cn, (u + 1) & 1); stagepos[(u + 1) & 1] = cn; }
+            if (cn < cend) {
+                build(cn, (u + 1) & 1);
+                if ((u + 1) & 1) stagepos1 = cn; else stagepos0 = cn;
+            }
             ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_d1full[s], (uint32_t)((u >> 1) & 1), flags));
             if (!ok) break;
             fence_after();
@@ -1300,13 +1385,14 @@ size_t tc_tile_bytes(int K) { return (size_t)((K + kCols - 1) / kCols) * kTileBy
 size_t tc_hdr_floats(int K) { return (size_t)((K + kCols - 1) / kCols) * 32; }
 size_t tc_tmax_floats(int64_t N, int K) { return (size_t)((N + 31) / 32) * (size_t)((K + kCols - 1) / kCols); }
 
-int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, int *dirty,
+int launch_coef_tiles(const double *rec, const float *rec32, int K, bool bf16, unsigned char *tiles, float *hdr,
+                      int *dirty,
                       cudaStream_t st, Prof *pf)
 {
     const int nt = (K + kCols - 1) / kCols;
     pf->begin(VBGS_PROF_MSTEP, st);
-    if (bf16) k_coef_tiles<true><<<nt, 128, 0, st>>>(rec, K, tiles, hdr, dirty);
-    else      k_coef_tiles<false><<<nt, 128, 0, st>>>(rec, K, tiles, hdr, dirty);
+    if (bf16) k_coef_tiles<true><<<nt, 128, 0, st>>>(rec, rec32, K, tiles, hdr, dirty);
+    else      k_coef_tiles<false><<<nt, 128, 0, st>>>(rec, rec32, K, tiles, hdr, dirty);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }

@@ -162,8 +162,8 @@ int launch_pass2_fp32(const EstepBuffers &B, int tpb, int tkc, cudaStream_t st, 
 size_t tc_tile_bytes(int K);
 size_t tc_hdr_floats(int K);
 size_t tc_tmax_floats(int64_t N, int K);
-int launch_coef_tiles(const double *rec, int K, bool bf16, unsigned char *tiles, float *hdr, int *dirty,
-                      cudaStream_t st, Prof *pf);
+int launch_coef_tiles(const double *rec, const float *rec32, int K, bool bf16, unsigned char *tiles, float *hdr,
+                      int *dirty, cudaStream_t st, Prof *pf);
 size_t tc_plan_ints(int64_t N, int K);
 size_t tc_pass2_part_doubles(int K);
 size_t tc_p1plan_ints(int64_t N, int K);

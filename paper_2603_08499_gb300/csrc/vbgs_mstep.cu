@@ -88,9 +88,11 @@ __device__ float sym3_max_eig(float a00, float a01, float a02, float a11, float 
     return q + 2.f * p * cosf(phi);
 }
 
-// Posterior parameters from prior and statistics; A is the full symmetric W^-1.
-__device__ void nw_from_stats(const MstepParams &P, const double *m0, const double *s,
-                              double &alpha, double &beta, double &nu, double m[6], double A[36])
+// Posterior parameters from prior and statistics; A is W^-1, packed lower
+// triangular (A[tri(i, j)], j <= i).  Packed storage keeps the 6 x 6
+// matrices of one thread in registers.
+__device__ __forceinline__ void nw_from_stats(const MstepParams &P, const double *m0, const double *s,
+                              double &alpha, double &beta, double &nu, double m[6], double A[21])
 {
     const double N = s[0];
     alpha = P.alpha0 + N;
@@ -102,56 +104,58 @@ __device__ void nw_from_stats(const MstepParams &P, const double *m0, const doub
 #pragma unroll
     for (int i = 0; i < 6; i++)
 #pragma unroll
-        for (int j = i; j < 6; j++) {
-            double v = P.W0inv[i * 6 + j] + s[upper_index(i, j)]
-                     + P.beta0 * m0[i] * m0[j] - beta * m[i] * m[j];
-            A[i * 6 + j] = v;
-            A[j * 6 + i] = v;
-        }
+        for (int j = i; j < 6; j++)
+            A[tri(j, i)] = P.W0inv[i * 6 + j] + s[upper_index(i, j)] + P.beta0 * m0[i] * m0[j] - beta * m[i] * m[j];
 }
 
-// In-register Cholesky A = L L^T (L lower, full 6x6 storage); false if not PD.
-__device__ bool chol6(const double A[36], double L[36])
+// One column of the in-register Cholesky A = L L^T (both packed lower
+// triangular); a template so the compiler unrolls every loop and keeps A and
+// L in registers.
+template <int J>
+__device__ __forceinline__ void chol6_col(const double A[21], double L[21], bool &ok)
+{
+    double d = A[tri(J, J)];
+#pragma unroll
+    for (int k = 0; k < J; k++) d -= L[tri(J, k)] * L[tri(J, k)];
+    ok = ok && (d > 0.0);
+    d = fmax(d, 1e-300);
+    const double inv = rsqrt(d);
+    L[tri(J, J)] = d * inv;
+#pragma unroll
+    for (int i = J + 1; i < 6; i++) {
+        double t = A[tri(i, J)];
+#pragma unroll
+        for (int k = 0; k < J; k++) t -= L[tri(i, k)] * L[tri(J, k)];
+        L[tri(i, J)] = t * inv;
+    }
+}
+
+// A = L L^T; false if A is not positive definite.
+__device__ __forceinline__ bool chol6(const double A[21], double L[21])
 {
     bool ok = true;
-#pragma unroll
-    for (int i = 0; i < 36; i++) L[i] = 0.0;
-#pragma unroll
-    for (int j = 0; j < 6; j++) {
-        double d = A[j * 6 + j];
-#pragma unroll
-        for (int k = 0; k < j; k++) d -= L[j * 6 + k] * L[j * 6 + k];
-        ok = ok && (d > 0.0);
-        d = fmax(d, 1e-300);
-        const double inv = rsqrt(d);
-        d *= inv;
-        L[j * 6 + j] = d;
-#pragma unroll
-        for (int i = j + 1; i < 6; i++) {
-            double t = A[i * 6 + j];
-#pragma unroll
-            for (int k = 0; k < j; k++) t -= L[i * 6 + k] * L[j * 6 + k];
-            L[i * 6 + j] = t * inv;
-        }
-    }
+    chol6_col<0>(A, L, ok);
+    chol6_col<1>(A, L, ok);
+    chol6_col<2>(A, L, ok);
+    chol6_col<3>(A, L, ok);
+    chol6_col<4>(A, L, ok);
+    chol6_col<5>(A, L, ok);
     return ok;
 }
 
-// Inverse of a lower-triangular 6x6 matrix (result lower triangular).
-__device__ void trinv6(const double L[36], double Li[36])
+// Inverse of a lower-triangular 6x6 matrix, both packed.
+__device__ __forceinline__ void trinv6(const double L[21], double Li[21])
 {
 #pragma unroll
-    for (int i = 0; i < 36; i++) Li[i] = 0.0;
-#pragma unroll
-    for (int c = 0; c < 6; c++) Li[c * 6 + c] = 1.0 / L[c * 6 + c];
+    for (int c = 0; c < 6; c++) Li[tri(c, c)] = 1.0 / L[tri(c, c)];
 #pragma unroll
     for (int c = 0; c < 6; c++) {
 #pragma unroll
         for (int i = c + 1; i < 6; i++) {
             double t = 0.0;
 #pragma unroll
-            for (int k = c; k < i; k++) t += L[i * 6 + k] * Li[k * 6 + c];
-            Li[i * 6 + c] = -t * Li[i * 6 + i];
+            for (int k = c; k < i; k++) t += L[tri(i, k)] * Li[tri(k, c)];
+            Li[tri(i, c)] = -t * Li[tri(i, i)];
         }
     }
 }
@@ -211,10 +215,14 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
     if (pos >= P.K) return;
     const int k = kperm ? kperm[pos] : pos;
     double *ks = kls + (size_t)k * kKS;
+    // all 28 frame statistics exactly zero (either sign): integer test of
+    // the bit patterns, off the FP64 pipe
+    bool zero = false;
     if (dS) {
-        bool zero = true;
+        unsigned long long bits = 0;
 #pragma unroll
-        for (int f = 0; f < 28; f++) zero = zero && (dS[(size_t)k * 28 + f] == 0.0);
+        for (int f = 0; f < 28; f++) bits |= (unsigned long long)__double_as_longlong(dS[(size_t)k * 28 + f]);
+        zero = (bits << 1) == 0;
         if (zero && pc[(size_t)k * kPC + 33] != 0.0) {
             ks[33] = 0.0;
             ks[34] = 0.0;
@@ -227,14 +235,14 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
         for (int f = 0; f < 28; f++) st[f] = Spast[(size_t)k * 28 + f] + (dS ? dS[(size_t)k * 28 + f] : 0.0);
 #pragma unroll
         for (int i = 0; i < 6; i++) m0k[i] = m0[(size_t)k * 6 + i];
-        double bq, nq, mq[6], Aq[36];
+        double bq, nq, mq[6], Aq[21];
         nw_from_stats(P, m0k, st, aq, bq, nq, mq, Aq);
-        double Lq[36], Li[36];
+        double Lq[21], Li[21];
         const bool ok = chol6(Aq, Lq);
         if (!ok) atomicCAS(&flags[FL_NONPD], 0, k + 1);
         double dprod = 1.0;   // ln|W^-1| = 2 ln prod_i L_ii
 #pragma unroll
-        for (int i = 0; i < 6; i++) dprod *= Lq[i * 6 + i];
+        for (int i = 0; i < 6; i++) dprod *= Lq[tri(i, i)];
         const double ldq = 2.0 * log(dprod);
         trinv6(Lq, Li);
 
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
         for (int i = 0; i < 6; i++)
 #pragma unroll
             for (int j = 0; j <= i; j++) {
-                double v = sn * Li[i * 6 + j];
+                double v = sn * Li[tri(i, j)];
                 r[6 + tri(i, j)] = v;
                 r32[6 + tri(i, j)] = (float)v * s2;
             }
@@ -272,15 +280,17 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
             // eigenvalue is nu / lambda_max((W^-1)_pp); same for colour.
             // (largest eigenvalue of each 3 x 3 block in FP32, inflated by
             // 1e-4 so the bound stays below the exact one)
-            const float lpp = sym3_max_eig((float)Aq[0], (float)Aq[1], (float)Aq[2], (float)Aq[7], (float)Aq[8],
-                                           (float)Aq[14]);
-            const float lcc = sym3_max_eig((float)Aq[21], (float)Aq[22], (float)Aq[23], (float)Aq[28],
-                                           (float)Aq[29], (float)Aq[35]);
-            r32[28] = (float)(1.4426950408889634 * (1.0 - 1e-6) * nq / ((double)lpp * (1.0 + 1e-4)));
-            r32[29] = (float)(1.4426950408889634 * (1.0 - 1e-6) * nq / ((double)lcc * (1.0 + 1e-4)));
+            // The rest in FP32: a few roundings of 2^-24 each, covered by
+            // the 1e-5 deflation.
+            const float a0 = (float)Aq[tri(0, 0)], a7 = (float)Aq[tri(1, 1)], a14 = (float)Aq[tri(2, 2)];
+            const float a21 = (float)Aq[tri(3, 3)], a28 = (float)Aq[tri(4, 4)], a35 = (float)Aq[tri(5, 5)];
+            const float lpp = sym3_max_eig(a0, (float)Aq[tri(1, 0)], (float)Aq[tri(2, 0)], a7, (float)Aq[tri(2, 1)], a14);
+            const float lcc = sym3_max_eig(a21, (float)Aq[tri(4, 3)], (float)Aq[tri(5, 3)], a28, (float)Aq[tri(5, 4)], a35);
+            const float num = 1.44269504f * (1.f - 1e-5f) * (float)nq;
+            r32[28] = num / (lpp * (1.f + 1e-4f));
+            r32[29] = num / (lcc * (1.f + 1e-4f));
             // and of the full precision: lambda_min(nu W) >= nu / tr(W^-1)
-            r32[30] = (float)(1.4426950408889634 * (1.0 - 1e-6) * nq /
-                              (Aq[0] + Aq[7] + Aq[14] + Aq[21] + Aq[28] + Aq[35]));
+            r32[30] = num / ((a0 + a7) + (a14 + a21) + (a28 + a35));
         }
 
         double *cache = pc + (size_t)k * kPC;
@@ -292,22 +302,19 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
 #pragma unroll
             for (int i = 0; i < 6; i++)
 #pragma unroll
-                for (int j = i; j < 6; j++, u++) cache[u] = Aq[i * 6 + j];
+                for (int j = i; j < 6; j++, u++) cache[u] = Aq[tri(j, i)];
             cache[30] = ldq;
             cache[33] = 1.0;   // the record holds the effective prior
         } else {
             // the record holds the prior again only if this frame's
             // statistics of the component are all zero
-            bool z = true;
-#pragma unroll
-            for (int f = 0; f < 28; f++) z = z && (dS[(size_t)k * 28 + f] == 0.0);
-            cache[33] = z ? 1.0 : 0.0;
+            cache[33] = zero ? 1.0 : 0.0;
 #pragma unroll
             for (int i = 0; i < 6; i++) ks[i] = mq[i];
 #pragma unroll
             for (int i = 0; i < 6; i++)
 #pragma unroll
-                for (int j = 0; j <= i; j++) ks[6 + tri(i, j)] = Li[i * 6 + j];
+                for (int j = 0; j <= i; j++) ks[6 + tri(i, j)] = Li[tri(i, j)];
             ks[27] = aq; ks[28] = bq; ks[29] = nq; ks[30] = ldq; ks[31] = psi_nu; ks[32] = psi_a;
             ks[33] = 1.0;
             ks[34] = st[0] - Spast[(size_t)k * 28];
