@@ -261,7 +261,7 @@ int order_frame(vbgs_ctx *ctx, int64_t N, bool points)
 }
 
 // Full E-step over N staged points X (N x 8) into lse (N) and ctx->d_dS.
-int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool want_stats)
+int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool want_stats, bool same_points = false)
 {
     if (ctx->prof.on && !is_tc(ctx)) ctx->prof.pass1_pairs += N * (int64_t)ctx->K;   // tensor-core pass 1 counts on the device
     if (N == 0) {
@@ -287,8 +287,8 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
     B.minlse = skip ? ctx->d_minlse : nullptr;
     if (is_tc(ctx)) {
         const int *item_start = nullptr;
-        int l = launch_pass1_tc(B.X, ctx->d_Xhl, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles,
-                                ctx->d_tc_hdr, ctx->d_rec32, ctx->d_part, ctx->part_cap, B.tmax,
+        int l = launch_pass1_tc(B.X, ctx->d_Xhl, same_points, N, ctx->K, ctx->precision == VBGS_BF16X3,
+                                ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_rec32, ctx->d_part, ctx->part_cap, B.tmax,
                                 ctx->d_p1plan, ctx->d_p1ub, ctx->d_flags, ctx->num_sms, ctx->tune_p1, &item_start,
                                 ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -654,10 +654,12 @@ int prop_estep(vbgs_ctx *ctx, int64_t N, bool last_iter)
     return VBGS_OK;
 }
 
-int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats, bool last_iter = false)
+// same_points: the points are those of the previous E-step of this frame
+// (their FP32 split and tile boxes are current).
+int run_estep(vbgs_ctx *ctx, int64_t N, bool want_stats, bool last_iter = false, bool same_points = false)
 {
     if (ctx->prop.on && want_stats && N > 0) return prop_estep(ctx, N, last_iter);
-    return run_estep_on(ctx, ctx->last_sorted ? ctx->d_Xs : ctx->d_X, N, ctx->d_lse, want_stats);
+    return run_estep_on(ctx, ctx->last_sorted ? ctx->d_Xs : ctx->d_X, N, ctx->d_lse, want_stats, same_points);
 }
 
 int check_flags(vbgs_ctx *ctx)
@@ -703,7 +705,7 @@ int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters)
             return rc;
     }
     for (int it = 0; it < n_iters; it++) {
-        if ((rc = run_estep(ctx, N, true, it == n_iters - 1))) return rc;
+        if ((rc = run_estep(ctx, N, true, it == n_iters - 1, it > 0))) return rc;
         if ((rc = join_side(ctx))) return rc;
         if (launch_elbo(ctx->d_scal, N, ctx->d_elbo + it, ctx->stream, &ctx->prof) < 0)
             return fail(ctx, VBGS_ECUDA, "ELBO launch failed");

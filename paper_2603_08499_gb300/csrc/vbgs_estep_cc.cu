@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(256) k_merge(const double2 *__restrict__ part,
 
 __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ v, int n, double *__restrict__ out)
 {
+    pdl_wait();
     __shared__ double sh[32];
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
@@ -373,7 +374,7 @@ constexpr int kPPT32 = 2;
 int launch_block_sum(const double *part, int n, double *sum_out, cudaStream_t st, Prof *pf)
 {
     pf->begin(VBGS_PROF_MERGE, st);
-    k_sum<<<1, 1024, 0, st>>>(part, n, sum_out);
+    launch_pdl(k_sum, 1, 1024, 0, st, part, n, sum_out);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
@@ -388,7 +389,7 @@ int launch_lse_merge(const double2 *part, int nsplit, int64_t N, const int *item
     k_merge<<<mb, 64, 0, st>>>(part, nsplit, N, item_start, lse, lse_part, minlse);
     pf->end(st);
     pf->begin(VBGS_PROF_MERGE, st);
-    k_sum<<<1, 1024, 0, st>>>(lse_part, mb, sum_out);
+    launch_pdl(k_sum, 1, 1024, 0, st, lse_part, mb, sum_out);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 2 : -1;
 }
@@ -442,7 +443,7 @@ int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats
     k_merge<<<mb, 64, 0, st>>>(p1, pl.p1_splits, B.N, nullptr, B.lse, B.lse_part, tmax ? B.minlse : nullptr);
     pf->end(st);
     pf->begin(VBGS_PROF_MERGE, st);
-    k_sum<<<1, 1024, 0, st>>>(B.lse_part, mb, B.scal + SC_SUM_LSE);
+    launch_pdl(k_sum, 1, 1024, 0, st, B.lse_part, mb, B.scal + SC_SUM_LSE);
     pf->end(st);
     launches += 3;
     if (want_stats) {
@@ -595,7 +596,7 @@ extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N
     if (f64) k_pass1<double, kPPT64><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec, K, pl.kps, p1, nullptr);
     else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec32, K, pl.kps, p1, nullptr);
     k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, nullptr, lse_out, base + o_lsep, nullptr);
-    k_sum<<<1, 1024, 0, st>>>(base + o_lsep, mb, scal + SC_SUM_LSE);
+    launch_pdl(k_sum, 1, 1024, 0, st, base + o_lsep, mb, scal + SC_SUM_LSE);
     dim3 g2(pl.p2_tiles, pl.p2_splits);
     if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part, nullptr, nullptr, 1, 1, nullptr);
     else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part, nullptr, nullptr, 1, 1, nullptr);

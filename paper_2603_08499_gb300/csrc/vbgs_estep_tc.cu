@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
                                                     int K, unsigned char *__restrict__ tiles,
                                                     float *__restrict__ hdr, int *__restrict__ dirty)
 {
+    pdl_wait();
     __shared__ float red[7][4];
     __shared__ float frame[12];   // origin o (6), inv_s (6)
     const int t = threadIdx.x, j = blockIdx.x, lane = t & 31, w = t >> 5;
@@ -436,6 +437,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restr
                                                             int *__restrict__ flags,
                                                             unsigned long long *__restrict__ pairs)
 {
+    pdl_wait();
     using HT = typename H<BF16>::T;
     extern __shared__ unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -696,6 +698,7 @@ __device__ __forceinline__ float logit32_rec(const float *__restrict__ r, const 
 // Bounding box (lo[6], hi[6]) of each point tile.
 __global__ void __launch_bounds__(128) k_p1_boxes(const double *__restrict__ X, int64_t N, float *__restrict__ boxes)
 {
+    pdl_wait();
     __shared__ float sbox[2][6][4];
     const int P = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int64_t n = (int64_t)P * kRows + t;
@@ -722,6 +725,7 @@ __global__ void __launch_bounds__(128) k_p1_boxes(const double *__restrict__ X, 
 __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, int ptiles, int K, int ntiles,
                                                const float *__restrict__ rec32, float *__restrict__ ub)
 {
+    pdl_wait();
     __shared__ float sc[kCols][10];
     const int j = blockIdx.x, t = threadIdx.x;
     const int k = j * kCols + t;
@@ -761,6 +765,7 @@ __global__ void __launch_bounds__(128) k_p1_lists(const double *__restrict__ X, 
                                                   const float *__restrict__ rec32, const float *__restrict__ ub,
                                                   int *__restrict__ list, int *__restrict__ counts)
 {
+    pdl_wait();
     __shared__ float sr[kCols * 28];
     __shared__ float red[4];
     __shared__ int redi[4];
@@ -835,6 +840,7 @@ __global__ void __launch_bounds__(128) k_p1_lists(const double *__restrict__ X, 
 
 __global__ void k_fill_neg_inf(float *__restrict__ a, size_t n)
 {
+    pdl_wait();
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = -INFINITY;
 }
@@ -918,6 +924,7 @@ __global__ void __launch_bounds__(256) k_p2_plan(const float *__restrict__ tmax,
                                                  int64_t N, int ntiles, int *__restrict__ counts,
                                                  int *__restrict__ list)
 {
+    pdl_wait();
     __shared__ int wsum[8];
     __shared__ int base_sh;
     const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -956,6 +963,7 @@ __global__ void __launch_bounds__(1024) k_p2_items(const int *__restrict__ count
                                                    int *__restrict__ item_tile, int *__restrict__ item_lo,
                                                    int *__restrict__ item_hi, int *__restrict__ nitems)
 {
+    pdl_wait();
     __shared__ long long red[32];
     __shared__ int scan[1024];
     __shared__ int carry_sh, C_sh;
@@ -1021,6 +1029,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
                                                             float *__restrict__ part, int *__restrict__ flags,
                                                             unsigned long long *__restrict__ pairs)
 {
+    pdl_wait();
     using HT = typename H<BF16>::T;
     extern __shared__ unsigned char smem_raw[];
     Smem2 &S = *reinterpret_cast<Smem2 *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -1326,6 +1335,7 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
                                                       const double *__restrict__ rec, const int *__restrict__ kperm,
                                                       double *__restrict__ dS)
 {
+    pdl_wait();
     __shared__ float sh[3][32][29];
     const int j = blockIdx.x >> 2, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int m = (blockIdx.x & 3) * 32 + lane;
@@ -1391,8 +1401,8 @@ int launch_coef_tiles(const double *rec, const float *rec32, int K, bool bf16, u
 {
     const int nt = (K + kCols - 1) / kCols;
     pf->begin(VBGS_PROF_MSTEP, st);
-    if (bf16) k_coef_tiles<true><<<nt, 128, 0, st>>>(rec, rec32, K, tiles, hdr, dirty);
-    else      k_coef_tiles<false><<<nt, 128, 0, st>>>(rec, rec32, K, tiles, hdr, dirty);
+    if (bf16) launch_pdl(k_coef_tiles<true>, nt, 128, 0, st, rec, rec32, K, tiles, hdr, dirty);
+    else      launch_pdl(k_coef_tiles<false>, nt, 128, 0, st, rec, rec32, K, tiles, hdr, dirty);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
@@ -1428,8 +1438,8 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
     int *item_tile = item_start + ntiles + 1, *item_lo = item_tile + icap, *item_hi = item_lo + icap;
     int *nitems = item_hi + icap;
     pf->begin(VBGS_PROF_PLAN, st);
-    if (tmax) k_p2_plan<<<ntiles, 256, 0, st>>>(tmax, minlse, N, ntiles, counts, list);
-    k_p2_items<<<1, 1024, 0, st>>>(tmax ? counts : nullptr, ntiles, nchunks, cmin, tcap, item_start, item_tile,
+    if (tmax) launch_pdl(k_p2_plan, ntiles, 256, 0, st, tmax, minlse, N, ntiles, counts, list);
+    launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ntiles, nchunks, cmin, tcap, item_start, item_tile,
                                    item_lo, item_hi, nitems);
     pf->end(st);
     const size_t smem = sizeof(Smem2) + 128;
@@ -1437,16 +1447,16 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
     float *fpart = reinterpret_cast<float *>(part);   // item partials: FP32 register sums
     pf->begin(VBGS_PROF_PASS2, st);
     if (bf16)
-        k_pass2_tc<true><<<tcap, kThreadsTC, smem, st>>>(Xhl, lse2f, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
+        launch_pdl(k_pass2_tc<true>, tcap, kThreadsTC, smem, st, Xhl, lse2f, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
                                                          list, item_tile, item_lo, item_hi, nitems, rec, fpart, flags,
                                                          pairs);
     else
-        k_pass2_tc<false><<<tcap, kThreadsTC, smem, st>>>(Xhl, lse2f, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
+        launch_pdl(k_pass2_tc<false>, tcap, kThreadsTC, smem, st, Xhl, lse2f, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
                                                           list, item_tile, item_lo, item_hi, nitems, rec, fpart, flags,
                                                          pairs);
     pf->end(st);
     pf->begin(VBGS_PROF_REDUCE, st);
-    k_reduce_items<<<ntiles * 4, 128, 0, st>>>(fpart, item_start, K, rec, kperm, dS);
+    launch_pdl(k_reduce_items, ntiles * 4, 128, 0, st, fpart, item_start, K, rec, kperm, dS);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? (tmax ? 4 : 3) : -1;
 }
@@ -1493,6 +1503,7 @@ int tc_set_attributes()
 // arithmetic instead of FP64.
 __global__ void k_split_points(const double *__restrict__ X, int64_t N, float *__restrict__ Xhl)
 {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * 8) return;
     const int64_t n = i >> 3;
@@ -1514,6 +1525,7 @@ __global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part
                                                  int64_t N, double *__restrict__ lse, float *__restrict__ lse2f,
                                                  double *__restrict__ lse_part, float *__restrict__ minlse)
 {
+    pdl_wait();
     __shared__ double sh[2];
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
@@ -1562,15 +1574,17 @@ size_t tc_p1ub_floats(int64_t N, int K)
     return pt * (size_t)((K + kCols - 1) / kCols) + 12 * pt;   // ub, then the point-tile boxes
 }
 
-int launch_pass1_tc(const double *X, float *Xhl, int64_t N, int K, bool bf16, const unsigned char *tiles,
-                    const float *hdr, const float *rec32, double *part_buf, size_t part_cap_doubles, float *tmax,
-                    int *p1plan, float *p1ub, int *flags, int num_sms, int tiles_per_item,
-                    const int **item_start_out, cudaStream_t st, Prof *pf)
+int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, int K, bool bf16,
+                    const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
+                    size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
+                    int tiles_per_item, const int **item_start_out, cudaStream_t st, Prof *pf)
 {
     float2 *part = reinterpret_cast<float2 *>(part_buf);
-    if (N > 0) {
+    int launches = 0;
+    if (N > 0 && !same_points) {
+        launches++;
         pf->begin(VBGS_PROF_PLAN, st);
-        k_split_points<<<(unsigned)((N * 8 + 255) / 256), 256, 0, st>>>(X, N, Xhl);
+        launch_pdl(k_split_points, (unsigned)((N * 8 + 255) / 256), 256, 0, st, X, N, Xhl);
         pf->end(st);
     }
     const int ntiles = (K + kCols - 1) / kCols;
@@ -1597,12 +1611,15 @@ int launch_pass1_tc(const double *X, float *Xhl, int64_t N, int K, bool bf16, co
     if (tmax) {
         const size_t nt = tc_tmax_floats(N, K);
         float *boxes = p1ub + (size_t)ptiles * ntiles;
-        k_fill_neg_inf<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(tmax, nt);
-        k_p1_boxes<<<ptiles, kRows, 0, st>>>(X, N, boxes);
-        k_p1_ub<<<ntiles, kCols, 0, st>>>(boxes, ptiles, K, ntiles, rec32, p1ub);
-        k_p1_lists<<<ptiles, kRows, 0, st>>>(X, N, K, ntiles, rec32, p1ub, list, counts);
+        launch_pdl(k_fill_neg_inf, (unsigned)((nt + 255) / 256), 256, 0, st, tmax, nt);
+        if (!same_points) {   // the boxes of the previous E-step's points are current
+            launch_pdl(k_p1_boxes, ptiles, kRows, 0, st, X, N, boxes);
+            launches++;
+        }
+        launch_pdl(k_p1_ub, ntiles, kCols, 0, st, boxes, ptiles, K, ntiles, rec32, p1ub);
+        launch_pdl(k_p1_lists, ptiles, kRows, 0, st, X, N, K, ntiles, rec32, p1ub, list, counts);
     }
-    k_p2_items<<<1, 1024, 0, st>>>(tmax ? counts : nullptr, ptiles, ntiles, tmin, target, item_start, item_tile,
+    launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ptiles, ntiles, tmin, target, item_start, item_tile,
                                    item_lo, item_hi, nitems);
     pf->end(st);
     const size_t smem = sizeof(Smem) + 1024;
@@ -1610,14 +1627,14 @@ int launch_pass1_tc(const double *X, float *Xhl, int64_t N, int K, bool bf16, co
     pf->begin(VBGS_PROF_PASS1, st);
     const int *lst = tmax ? list : nullptr;
     if (bf16)
-        k_pass1_tc<true><<<target, kThreadsTC, smem, st>>>(Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
+        launch_pdl(k_pass1_tc<true>, target, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
                                                            item_hi, nitems, part, tmax, flags, pairs1);
     else
-        k_pass1_tc<false><<<target, kThreadsTC, smem, st>>>(Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
+        launch_pdl(k_pass1_tc<false>, target, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
                                                             item_hi, nitems, part, tmax, flags, pairs1);
     pf->end(st);
     *item_start_out = item_start;
-    return cudaGetLastError() == cudaSuccess ? (tmax ? 6 : 2) + (N > 0 ? 1 : 0) : -1;
+    return cudaGetLastError() == cudaSuccess ? launches + (tmax ? 5 : 2) : -1;
 }
 
 int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
@@ -1625,7 +1642,7 @@ int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start
 {
     const int mb = (int)((N + 63) / 64);
     pf->begin(VBGS_PROF_MERGE, st);
-    k_merge_tc<<<mb, 64, 0, st>>>(reinterpret_cast<const float2 *>(part_buf), item_start, N, lse, lse2f, lse_part,
+    launch_pdl(k_merge_tc, mb, 64, 0, st, reinterpret_cast<const float2 *>(part_buf), item_start, N, lse, lse2f, lse_part,
                                   minlse);
     pf->end(st);
     return launch_block_sum(lse_part, mb, sum_out, st, pf) < 0 ? -1 : 2;

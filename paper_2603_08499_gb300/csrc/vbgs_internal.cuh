@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 #include "../../include/vbgs.h"
 
@@ -26,6 +27,33 @@
 #define VBGS_XS 8         // doubles per staged point
 
 namespace vbgs {
+
+// Programmatic dependent launch.  A kernel launched with launch_pdl is set up
+// while the kernel before it in the stream finishes (its CTAs exiting are the
+// trigger), which hides most of the launch latency between dependent kernels.
+// It calls pdl_wait() as its first statement: that returns once every earlier
+// grid of the stream has completed and its writes are visible (a no-op for a
+// kernel launched without the attribute).  An explicit early trigger
+// (griddepcontrol.launch_dependents at kernel start) measured slower on the
+// K = 50,000 room stream: 3.29e12 against 3.74e12 pair updates/s.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Offsets into the packed lower triangle of a 6x6 matrix, row-major i >= j.
 __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
@@ -177,12 +205,14 @@ int tc_set_attributes();
 // Pass 1 on the tensor cores over balanced work items (point tile, list of
 // component tiles).  With tmax (skipping on): the component tiles whose
 // certified logit bound over the point tile is within 50 nats of a lower bound
-// of every point's lse; tmax of the other tiles is -inf.  item_start_out: the
+// of every point's lse; tmax of the other tiles is -inf.  same_points: X and N
+// are the previous call's (its FP32 split Xhl and point-tile boxes are
+// reused).  item_start_out: the
 // item table the lse merge reads.
-int launch_pass1_tc(const double *X, float *Xhl, int64_t N, int K, bool bf16, const unsigned char *tiles,
-                    const float *hdr, const float *rec32, double *part_buf, size_t part_cap_doubles, float *tmax,
-                    int *p1plan, float *p1ub, int *flags, int num_sms, int tiles_per_item,
-                    const int **item_start_out, cudaStream_t st, Prof *pf);
+int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, int K, bool bf16,
+                    const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
+                    size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
+                    int tiles_per_item, const int **item_start_out, cudaStream_t st, Prof *pf);
 // lse from pass 1's FP32 item partials, minlse per 32 points, sum of lse.
 int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
                         double *lse_part, float *minlse, double *sum_out, cudaStream_t st, Prof *pf);

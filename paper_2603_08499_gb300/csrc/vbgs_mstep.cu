@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
                                                double *__restrict__ pc, double *__restrict__ kls,
                                                int *__restrict__ flags, int *__restrict__ tile_dirty)
 {
+    pdl_wait();
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= P.K) return;
     const int k = kperm ? kperm[pos] : pos;
@@ -385,6 +386,7 @@ __global__ void __launch_bounds__(128) k_mstep_kl(MstepParams P, bool frame_star
 __global__ void __launch_bounds__(1024) k_mstep_finalize(const double *__restrict__ bpart, int nblocks,
                                                          double *__restrict__ scal)
 {
+    pdl_wait();
     __shared__ double sh[4][32];
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
@@ -415,12 +417,14 @@ __global__ void __launch_bounds__(1024) k_mstep_finalize(const double *__restric
 __global__ void k_commit(double *__restrict__ Spast, const double *__restrict__ dS, size_t n,
                          const int *__restrict__ flags)
 {
+    pdl_wait();
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && flags[FL_NONPD] == 0 && flags[FL_BAD_POINT] == 0) Spast[i] += dS[i];
 }
 
 __global__ void k_elbo(double *__restrict__ scal, double N, double *__restrict__ out)
 {
+    pdl_wait();
     *out = scal[SC_SUM_LSE] - N * scal[SC_PSI_AHAT] - scal[SC_KL_TOTAL];
     scal[SC_PSI_ESTEP] = scal[SC_PSI_AHAT];
 }
@@ -429,6 +433,7 @@ __global__ void k_elbo(double *__restrict__ scal, double N, double *__restrict__
 __global__ void k_stage(const double *__restrict__ src, int64_t N, double *__restrict__ X,
                         int *__restrict__ flags)
 {
+    pdl_wait();
     int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     bool bad = false;
@@ -462,7 +467,7 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
     pf->begin(VBGS_PROF_MSTEP, st);
     // 64 threads a block: the per-component work is long and uneven (skipped
     // components return at once), so smaller blocks spread it over more SMs
-    k_mstep<<<(K + 63) / 64, 64, 0, st>>>(P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags, tile_dirty);
+    launch_pdl(k_mstep, (K + 63) / 64, 64, 0, st, P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags, tile_dirty);
     pf->end(st);
     // KL terms and their sums beside the next E-step
     if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return -1;
@@ -470,7 +475,7 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
     k_mstep_kl<<<nb, 128, 0, side>>>(P, dS == nullptr, kperm, cache, kls, bpart);
     pf->end(side);
     pf->begin(VBGS_PROF_MSTEP, side);
-    k_mstep_finalize<<<1, 1024, 0, side>>>(bpart, nb, scal);
+    launch_pdl(k_mstep_finalize, 1, 1024, 0, side, bpart, nb, scal);
     pf->end(side);
     if (cudaEventRecord(ev_join, side) != cudaSuccess) return -1;
     return cudaGetLastError() == cudaSuccess ? 3 : -1;
@@ -480,7 +485,7 @@ int launch_commit(double *Spast, const double *dS, int K, const int *flags, cuda
 {
     size_t n = (size_t)K * 28;
     pf->begin(VBGS_PROF_MISC, st);
-    k_commit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Spast, dS, n, flags);
+    launch_pdl(k_commit, (unsigned)((n + 255) / 256), 256, 0, st, Spast, dS, n, flags);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
@@ -488,7 +493,7 @@ int launch_commit(double *Spast, const double *dS, int K, const int *flags, cuda
 int launch_elbo(double *scal, int64_t N, double *elbo_out, cudaStream_t st, Prof *pf)
 {
     pf->begin(VBGS_PROF_MISC, st);
-    k_elbo<<<1, 1, 0, st>>>(scal, (double)N, elbo_out);
+    launch_pdl(k_elbo, 1, 1, 0, st, scal, (double)N, elbo_out);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
@@ -497,7 +502,7 @@ int launch_stage_points(const double *src, int64_t N, double *X, int *flags, cud
 {
     if (N <= 0) return 0;
     pf->begin(VBGS_PROF_MISC, st);
-    k_stage<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(src, N, X, flags);
+    launch_pdl(k_stage, (unsigned)((N + 255) / 256), 256, 0, st, src, N, X, flags);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }

@@ -43,6 +43,7 @@ __device__ __forceinline__ uint32_t morton3(const BoxParams &b, double x, double
 __global__ void k_point_codes(const double *__restrict__ X, int64_t N, BoxParams b, uint32_t *__restrict__ keys,
                               int *__restrict__ idx)
 {
+    pdl_wait();
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const double *x = X + n * VBGS_XS;
@@ -54,6 +55,7 @@ __global__ void k_point_codes(const double *__restrict__ X, int64_t N, BoxParams
 __global__ void k_comp_codes(const double *__restrict__ m0, const double *__restrict__ Spast, int K,
                              double beta0, BoxParams b, uint32_t *__restrict__ keys, int *__restrict__ idx)
 {
+    pdl_wait();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     const double *s = Spast + (size_t)k * 28;
@@ -68,6 +70,7 @@ __global__ void k_comp_codes(const double *__restrict__ m0, const double *__rest
 __global__ void k_gather_points(const double *__restrict__ X, const int *__restrict__ pidx, int64_t N,
                                 double *__restrict__ Xs)
 {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * 4) return;
     const int64_t n = i >> 2, q = i & 3;   // 4 x 16-byte pieces of a 64-byte row
@@ -77,6 +80,7 @@ __global__ void k_gather_points(const double *__restrict__ X, const int *__restr
 
 __global__ void k_invert(const int *__restrict__ kperm, int K, int *__restrict__ kinv)
 {
+    pdl_wait();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < K) kinv[kperm[p]] = p;
 }
@@ -96,14 +100,14 @@ int launch_point_order(const double *X, int64_t N, const BoxParams &box, SortBuf
 {
     if (N <= 0) return 0;
     pf->begin(VBGS_PROF_MISC, st);
-    k_point_codes<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(X, N, box, sb.keys_in, sb.idx_in);
+    launch_pdl(k_point_codes, (unsigned)((N + 255) / 256), 256, 0, st, X, N, box, sb.keys_in, sb.idx_in);
     pf->end(st);
     size_t bytes = sb.temp_bytes;
     if (cub::DeviceRadixSort::SortPairs(sb.temp, bytes, sb.keys_in, sb.keys_out, sb.idx_in, pidx, (int)N, 0, 30,
                                         st) != cudaSuccess)
         return -1;
     pf->begin(VBGS_PROF_MISC, st);
-    k_gather_points<<<(unsigned)((N * 4 + 255) / 256), 256, 0, st>>>(X, pidx, N, Xs);
+    launch_pdl(k_gather_points, (unsigned)((N * 4 + 255) / 256), 256, 0, st, X, pidx, N, Xs);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 4 : -1;
 }
@@ -112,14 +116,14 @@ int launch_comp_order(const double *m0, const double *Spast, int K, double beta0
                       SortBuffers &sb, int *kperm, int *kinv, cudaStream_t st, Prof *pf)
 {
     pf->begin(VBGS_PROF_MISC, st);
-    k_comp_codes<<<(K + 255) / 256, 256, 0, st>>>(m0, Spast, K, beta0, box, sb.keys_in, sb.idx_in);
+    launch_pdl(k_comp_codes, (K + 255) / 256, 256, 0, st, m0, Spast, K, beta0, box, sb.keys_in, sb.idx_in);
     pf->end(st);
     size_t bytes = sb.temp_bytes;
     if (cub::DeviceRadixSort::SortPairs(sb.temp, bytes, sb.keys_in, sb.keys_out, sb.idx_in, kperm, K, 0, 30, st) !=
         cudaSuccess)
         return -1;
     pf->begin(VBGS_PROF_MISC, st);
-    k_invert<<<(K + 255) / 256, 256, 0, st>>>(kperm, K, kinv);
+    launch_pdl(k_invert, (K + 255) / 256, 256, 0, st, kperm, K, kinv);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 4 : -1;
 }
