@@ -720,13 +720,14 @@ __global__ void __launch_bounds__(128) k_p1_boxes(const double *__restrict__ X, 
     }
 }
 
-// ub[P][j] for every point tile: one CTA per component tile j, the tile's
-// bound terms (m, c, lp, lc, la) in shared memory, one thread per point tile.
+// ub[P][j] for every point tile: a CTA per (component tile j, 128 point
+// tiles), the tile's bound terms (m, c, lp, lc, la; 16-byte aligned rows for
+// vector loads) in shared memory, one thread per point tile.
 __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, int ptiles, int K, int ntiles,
                                                const float *__restrict__ rec32, float *__restrict__ ub)
 {
     pdl_wait();
-    __shared__ float sc[kCols][10];
+    __shared__ __align__(16) float sc[kCols][12];
     const int j = blockIdx.x, t = threadIdx.x;
     const int k = j * kCols + t;
     const int nv = min(kCols, K - j * kCols);
@@ -737,13 +738,17 @@ __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, 
         sc[t][6] = r[27]; sc[t][7] = r[28]; sc[t][8] = r[29]; sc[t][9] = r[30];
     }
     __syncthreads();
-    for (int P = t; P < ptiles; P += kCols) {
+    const int P = blockIdx.y * kCols + t;
+    if (P < ptiles) {
         float lo[6], hi[6];
 #pragma unroll
         for (int i = 0; i < 6; i++) { lo[i] = boxes[(size_t)P * 12 + i]; hi[i] = boxes[(size_t)P * 12 + 6 + i]; }
         float b = -INFINITY;
         for (int q = 0; q < nv; q++) {
-            const float *c = sc[q];
+            const float4 c0 = *reinterpret_cast<const float4 *>(&sc[q][0]);
+            const float4 c1 = *reinterpret_cast<const float4 *>(&sc[q][4]);
+            const float4 c2 = *reinterpret_cast<const float4 *>(&sc[q][8]);
+            const float c[10] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y};
             float dp = 0.f, dc = 0.f;
 #pragma unroll
             for (int i = 0; i < 3; i++) {
@@ -760,22 +765,27 @@ __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, 
 
 // Per point tile: the seed tile (largest ub, ties to the lower index), the
 // lower bound LB of every point's lse from its exact FP32 log-sum, and the
-// list of tiles with ub >= LB - 50 nats, in increasing order.
-__global__ void __launch_bounds__(128) k_p1_lists(const double *__restrict__ X, int64_t N, int K, int ntiles,
-                                                  const float *__restrict__ rec32, const float *__restrict__ ub,
-                                                  int *__restrict__ list, int *__restrict__ counts)
+// list of tiles with ub >= LB - 50 nats, in increasing order.  256 threads:
+// two per point, each over half of the seed tile's components.
+constexpr int kListThreads = 256;
+__global__ void __launch_bounds__(kListThreads) k_p1_lists(const double *__restrict__ X, int64_t N, int K,
+                                                           int ntiles, const float *__restrict__ rec32,
+                                                           const float *__restrict__ ub, int *__restrict__ list,
+                                                           int *__restrict__ counts)
 {
     pdl_wait();
+    constexpr int kW = kListThreads / 32;
     __shared__ float sr[kCols * 28];
-    __shared__ float red[4];
-    __shared__ int redi[4];
-    __shared__ int wsum[4];
+    __shared__ float red[kW];
+    __shared__ int redi[kW];
+    __shared__ int wsum[kW];
+    __shared__ float hm[kRows], hs[kRows];
     __shared__ int base_sh;
     const int P = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const float *u = ub + (size_t)P * ntiles;
     float bv = -INFINITY;
     int bj = 0x7fffffff;
-    for (int j = t; j < ntiles; j += kRows)
+    for (int j = t; j < ntiles; j += kListThreads)
         if (u[j] > bv) { bv = u[j]; bj = j; }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -789,16 +799,17 @@ __global__ void __launch_bounds__(128) k_p1_lists(const double *__restrict__ X, 
     {
         float v = -INFINITY;
         int jx = 0x7fffffff;
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < kW; q++)
             if (red[q] > v || (red[q] == v && redi[q] < jx)) { v = red[q]; jx = redi[q]; }
         js = jx == 0x7fffffff ? 0 : jx;
     }
     const int ks = js * kCols, ns = min(kCols, K - ks);
-    for (int i = t; i < ns * 28; i += kRows) {
+    for (int i = t; i < ns * 28; i += kListThreads) {
         const int mm = i / 28, f = i - mm * 28;
         sr[i] = rec32[(size_t)(ks + mm) * VBGS_REC + f];
     }
-    const int64_t n = (int64_t)P * kRows + t;
+    const int pt = t & (kRows - 1), half = t / kRows;
+    const int64_t n = (int64_t)P * kRows + pt;
     const bool live = n < N;
     float x[6];
 #pragma unroll
@@ -807,21 +818,30 @@ __global__ void __launch_bounds__(128) k_p1_lists(const double *__restrict__ X, 
     // (approximate ex2 / lg2: relative errors of a few 2^-22, far inside the
     // 1 + 1e-5 |lse| margin below)
     float mx = -INFINITY, sm = 0.f;
-    for (int mm = 0; mm < ns; mm++) {
+    const int m_end = half ? ns : min(ns, kCols / 2);
+    for (int mm = half * (kCols / 2); mm < m_end; mm++) {
         const float l = logit32_rec(sr + mm * 28, x);
         if (l > mx) { sm = sm * ex2f(mx - l) + 1.f; mx = l; }
         else sm += ex2f(l - mx);
     }
-    float lb = mx + __log2f(sm);
-    lb = live ? lb - (1.f + 1e-5f * fabsf(lb)) : INFINITY;
+    if (half) { hm[pt] = mx; hs[pt] = sm; }
+    __syncthreads();
+    float lb = INFINITY;
+    if (!half) {
+        const float m1 = hm[pt], s1 = hs[pt];
+        if (m1 > mx) { sm = sm * ex2f(mx - m1) + s1; mx = m1; }
+        else if (m1 > -INFINITY) sm += s1 * ex2f(m1 - mx);
+        lb = mx + __log2f(sm);
+        lb = live ? lb - (1.f + 1e-5f * fabsf(lb)) : INFINITY;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lb = fminf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
-    __syncthreads();
     if (lane == 0) red[w] = lb;
     if (t == 0) base_sh = 0;
     __syncthreads();
-    const float LB = fminf(fminf(red[0], red[1]), fminf(red[2], red[3]));
-    for (int j0 = 0; j0 < ntiles; j0 += kRows) {
+    float LB = red[0];
+    for (int q = 1; q < kW; q++) LB = fminf(LB, red[q]);
+    for (int j0 = 0; j0 < ntiles; j0 += kListThreads) {
         const int j = j0 + t;
         const bool keep = j < ntiles && u[j] >= LB - kSkipLog2;
         const unsigned bb = __ballot_sync(0xffffffffu, keep);
@@ -832,7 +852,11 @@ __global__ void __launch_bounds__(128) k_p1_lists(const double *__restrict__ X, 
         off += __popc(bb & ((1u << lane) - 1u));
         if (keep) list[(size_t)P * ntiles + off] = j;
         __syncthreads();
-        if (t == 0) base_sh += wsum[0] + wsum[1] + wsum[2] + wsum[3];
+        if (t == 0) {
+            int tot = 0;
+            for (int i = 0; i < kW; i++) tot += wsum[i];
+            base_sh += tot;
+        }
         __syncthreads();
     }
     if (t == 0) counts[P] = base_sh;
@@ -1616,8 +1640,9 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
             launch_pdl(k_p1_boxes, ptiles, kRows, 0, st, X, N, boxes);
             launches++;
         }
-        launch_pdl(k_p1_ub, ntiles, kCols, 0, st, boxes, ptiles, K, ntiles, rec32, p1ub);
-        launch_pdl(k_p1_lists, ptiles, kRows, 0, st, X, N, K, ntiles, rec32, p1ub, list, counts);
+        launch_pdl(k_p1_ub, dim3(ntiles, (ptiles + kCols - 1) / kCols), kCols, 0, st, boxes, ptiles, K, ntiles,
+                   rec32, p1ub);
+        launch_pdl(k_p1_lists, ptiles, kListThreads, 0, st, X, N, K, ntiles, rec32, p1ub, list, counts);
     }
     launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ptiles, ntiles, tmin, target, item_start, item_tile,
                                    item_lo, item_hi, nitems);
