@@ -222,16 +222,51 @@ int join_side(vbgs_ctx *ctx)
     return VBGS_OK;
 }
 
-int run_mstep(vbgs_ctx *ctx, const double *dS)
+// dS == nullptr: the posterior entering a frame, prior0 (+) S_past.
+// write_next: also write the next frame's effective-prior cache (the last
+// iteration of a frame).
+int run_mstep(vbgs_ctx *ctx, const double *dS, bool write_next = false)
 {
     int rc;
     if ((rc = join_side(ctx))) return rc;
+    if (!dS) ctx->next_prior_ready = false;
     int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_kperm, ctx->d_rec, ctx->d_rec32, ctx->d_pcache,
-                         ctx->d_flags, ctx->d_scal, is_tc(ctx) ? ctx->d_tile_dirty : nullptr, ctx->stream, ctx->side,
-                         ctx->ev_fork, ctx->ev_join, &ctx->prof);
+                         ctx->d_flags, ctx->d_scal, is_tc(ctx) ? ctx->d_tile_dirty : nullptr,
+                         write_next ? ctx->d_pcache_next : nullptr, ctx->stream, ctx->side, ctx->ev_fork, ctx->ev_join,
+                         &ctx->prof);
     if (l < 0) return fail(ctx, VBGS_ECUDA, "posterior update launch failed");
     ctx->side_pending = true;
     ctx->launches += l;
+    if (is_tc(ctx)) {
+        l = launch_coef_tiles(ctx->d_rec, ctx->d_rec32, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles,
+                              ctx->d_tc_hdr, ctx->d_tile_dirty, ctx->stream, &ctx->prof);
+        if (l < 0) return fail(ctx, VBGS_ECUDA, "coefficient tile launch failed");
+        ctx->launches += l;
+    }
+    return VBGS_OK;
+}
+
+// The posterior entering a frame when the previous frame's last M-step left
+// it ready (next_prior_ready): the commit made S_past bitwise the statistics
+// that M-step used, so its posterior is this frame's effective prior and the
+// records already hold it.  Move the records to the new component order
+// (kinv_old: the positions before it), take the prior cache, KL = 0; the
+// psi(sum alpha) of that M-step stays (equal up to the order of the sum).
+int frame_start_from_next(vbgs_ctx *ctx, bool moved, const int *kinv_old)
+{
+    int l;
+    if (moved) {
+        l = launch_move_records(ctx->d_kperm, kinv_old, ctx->K, ctx->d_rec, ctx->d_rec32, ctx->d_rec_alt,
+                                ctx->d_rec32_alt, ctx->stream, &ctx->prof);
+        if (l < 0) return fail(ctx, VBGS_ECUDA, "record move launch failed");
+        ctx->launches += l;
+        std::swap(ctx->d_rec, ctx->d_rec_alt);
+        std::swap(ctx->d_rec32, ctx->d_rec32_alt);
+        if (is_tc(ctx)) CU(cudaMemsetAsync(ctx->d_tile_dirty, 0x01, sizeof(int) * ((ctx->K + 127) / 128), ctx->stream));
+    }
+    CU(cudaMemcpyAsync(ctx->d_pcache, ctx->d_pcache_next, sizeof(double) * mstep_prior_cache_doubles(ctx->K),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_scal + SC_KL_TOTAL, 0, sizeof(double), ctx->stream));
     if (is_tc(ctx)) {
         l = launch_coef_tiles(ctx->d_rec, ctx->d_rec32, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles,
                               ctx->d_tc_hdr, ctx->d_tile_dirty, ctx->stream, &ctx->prof);
@@ -689,13 +724,20 @@ int update_prepare(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters)
     return stage_points(ctx, points, N);
 }
 
-int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters)
+int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters, bool carry_prior)
 {
     int rc;
     CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    const bool from_next = carry_prior && ctx->next_prior_ready;
+    const bool reorder = !(ctx->flags & VBGS_FLAG_NO_REORDER);
+    ctx->next_prior_ready = false;
+    ctx->next_written = false;
+    if (from_next && reorder) std::swap(ctx->d_kinv, ctx->d_kinv_alt);   // keep the old inverse order
     if ((rc = order_frame(ctx, N, true))) return rc;
     // Posterior entering the frame: the effective prior prior0 (+) S_past.
-    if ((rc = run_mstep(ctx, nullptr))) return rc;
+    if (from_next) {
+        if ((rc = frame_start_from_next(ctx, reorder, ctx->d_kinv_alt))) return rc;
+    } else if ((rc = run_mstep(ctx, nullptr))) return rc;
     const bool prop = ctx->prop.on && N > 0;
     if (prop) {
         ctx->prop.frame_exact = false;
@@ -710,7 +752,9 @@ int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters)
         if (launch_elbo(ctx->d_scal, N, ctx->d_elbo + it, ctx->stream, &ctx->prof) < 0)
             return fail(ctx, VBGS_ECUDA, "ELBO launch failed");
         ctx->launches += 1;
-        if ((rc = run_mstep(ctx, ctx->d_dS))) return rc;
+        const bool last = it + 1 == n_iters;
+        if ((rc = run_mstep(ctx, ctx->d_dS, carry_prior && last))) return rc;
+        if (carry_prior && last) ctx->next_written = true;
         if (prop && it + 1 < n_iters && (rc = prop_refresh(ctx, true))) return rc;
     }
     if (launch_commit(ctx->d_Spast, ctx->d_dS, ctx->K, ctx->d_flags, ctx->stream, &ctx->prof) < 0)
@@ -731,7 +775,8 @@ void free_all(vbgs_ctx *ctx)
                     ctx->d_flags, ctx->d_X, ctx->d_lse, ctx->d_lse_part, ctx->d_part,
                     ctx->d_kperm, ctx->d_kinv, ctx->d_pidx, ctx->d_Xs, ctx->d_tmax, ctx->d_minlse,
                     ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp, ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_plan,
-                    ctx->d_p1plan, ctx->d_p1ub, ctx->d_tile_dirty, ctx->d_Xhl, ctx->d_lse2f};
+                    ctx->d_p1plan, ctx->d_p1ub, ctx->d_tile_dirty, ctx->d_Xhl, ctx->d_lse2f,
+                    ctx->d_pcache_next, ctx->d_rec_alt, ctx->d_rec32_alt, ctx->d_kinv_alt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     {
@@ -893,7 +938,7 @@ extern "C" int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const 
         cudaEventRecord(g_batch.fork, g_batch.main);
         for (int i = 0; i < n_scenes && rc == VBGS_OK; i++) {
             cudaStreamWaitEvent(g_batch.pool[i], g_batch.fork, 0);
-            rc = update_enqueue(scenes[i], N[i], n_iters);
+            rc = update_enqueue(scenes[i], N[i], n_iters, false);   // graphs replay: no carried prior
             cudaEventRecord(g_batch.ev[i], g_batch.pool[i]);
             cudaStreamWaitEvent(g_batch.main, g_batch.ev[i], 0);
         }
@@ -1209,7 +1254,10 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
         (rc = dalloc(ctx, &ctx->d_flags, (size_t)FL_COUNT)) || (rc = ensure_elbo(ctx, 64)) ||
         (rc = dalloc(ctx, &ctx->d_kperm, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_kinv, (size_t)K)) ||
         (rc = dalloc(ctx, &ctx->d_tc_tiles, tc_tile_bytes(K))) || (rc = dalloc(ctx, &ctx->d_tc_hdr, tc_hdr_floats(K))) ||
-        (rc = dalloc(ctx, &ctx->d_tile_dirty, (size_t)(K + 127) / 128))) {
+        (rc = dalloc(ctx, &ctx->d_tile_dirty, (size_t)(K + 127) / 128)) ||
+        (rc = dalloc(ctx, &ctx->d_pcache_next, mstep_prior_cache_doubles(K))) ||
+        (rc = dalloc(ctx, &ctx->d_rec_alt, (size_t)K * VBGS_REC)) ||
+        (rc = dalloc(ctx, &ctx->d_rec32_alt, (size_t)K * VBGS_REC)) || (rc = dalloc(ctx, &ctx->d_kinv_alt, (size_t)K))) {
         g_err = ctx->err;
         free_all(ctx);
         delete ctx;
@@ -1263,11 +1311,13 @@ int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, dou
 {
     int rc;
     if ((rc = update_prepare(ctx, points, N, n_iters))) return rc;
-    if ((rc = update_enqueue(ctx, N, n_iters))) return rc;
+    if ((rc = update_enqueue(ctx, N, n_iters, true))) return rc;
     if (elbo_trace)
         CU(cudaMemcpyAsync(elbo_trace, ctx->d_elbo, sizeof(double) * n_iters, cudaMemcpyDeviceToHost,
                            ctx->stream));
-    return check_flags(ctx);
+    if ((rc = check_flags(ctx))) return rc;
+    ctx->next_prior_ready = ctx->next_written;   // the commit ran: the carried prior is exact
+    return VBGS_OK;
 }
 
 int vbgs_elbo(vbgs_ctx *ctx, const double *points, int64_t N, double *elbo_out, double *lse_out)

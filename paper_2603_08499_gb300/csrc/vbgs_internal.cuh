@@ -164,10 +164,16 @@ int launch_stage_points(const double *src, int64_t N, double *X, int *flags, cud
 size_t mstep_cache_doubles(int K);
 // The record kernel runs on st; the KL terms and their sums (scal) on side,
 // after ev_fork; ev_join completes them (wait on it before reading scal).
+// cache_next (nullable, used only with dS): also write each component's
+// posterior q as an effective-prior cache entry; after the commit it is the
+// next frame's effective prior bit for bit (the last iteration of a frame).
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
                  const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
-                 int *tile_dirty, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
-                 Prof *pf);
+                 int *tile_dirty, double *cache_next, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork,
+                 cudaEvent_t ev_join, Prof *pf);
+int launch_move_records(const int *kperm, const int *kinv_old, int K, const double *rec, const float *rec32,
+                        double *rec_dst, float *rec32_dst, cudaStream_t st, Prof *pf);
+size_t mstep_prior_cache_doubles(int K);
 size_t sort_temp_bytes(int64_t n);
 int launch_point_order(const double *X, int64_t N, const BoxParams &box, SortBuffers &sb, double *Xs,
                        int *pidx, cudaStream_t st, Prof *pf);
@@ -318,6 +324,15 @@ struct vbgs_ctx {
     cudaStream_t side = nullptr;               // KL terms of the M-step, beside the next E-step
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool side_pending = false;                 // KL work launched on side and not yet joined
+    // The last M-step of the previous frame wrote d_pcache_next and the
+    // commit made it the effective prior of the next frame bit for bit; the
+    // records hold the same posterior (at the positions of d_kinv).
+    bool next_prior_ready = false;
+    bool next_written = false;                 // this frame's last M-step wrote d_pcache_next
+    double *d_pcache_next = nullptr;           // K x 40: the next frame's effective-prior cache
+    double *d_rec_alt = nullptr;               // record buffers for a new component order
+    float *d_rec32_alt = nullptr;
+    int *d_kinv_alt = nullptr;
     vbgs::BoxParams box{};
     vbgs::SortBuffers sb;
     int *d_kperm = nullptr, *d_kinv = nullptr, *d_pidx = nullptr;

@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
                                                const int *__restrict__ kperm,
                                                double *__restrict__ rec, float *__restrict__ rec32,
                                                double *__restrict__ pc, double *__restrict__ kls,
-                                               int *__restrict__ flags, int *__restrict__ tile_dirty)
+                                               int *__restrict__ flags, int *__restrict__ tile_dirty,
+                                               double *__restrict__ pcq)
 {
     pdl_wait();
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
@@ -227,6 +228,9 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
         if (zero && pc[(size_t)k * kPC + 33] != 0.0) {
             ks[33] = 0.0;
             ks[34] = 0.0;
+            if (pcq)   // q = p: the next frame's prior is this one's
+#pragma unroll
+                for (int f = 0; f < 34; f++) pcq[(size_t)k * kPC + f] = pc[(size_t)k * kPC + f];
             return;
         }
     }
@@ -319,6 +323,22 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
             ks[27] = aq; ks[28] = bq; ks[29] = nq; ks[30] = ldq; ks[31] = psi_nu; ks[32] = psi_a;
             ks[33] = 1.0;
             ks[34] = st[0] - Spast[(size_t)k * 28];
+            if (pcq) {
+                // After the commit S_past + Delta S is bitwise the st above,
+                // so q is the next frame's effective prior: its cache entry
+                // (the lnGamma terms come from k_mstep_kl).
+                double *cq = pcq + (size_t)k * kPC;
+                cq[0] = aq; cq[1] = bq; cq[2] = nq;
+#pragma unroll
+                for (int i = 0; i < 6; i++) cq[3 + i] = mq[i];
+                int u = 9;
+#pragma unroll
+                for (int i = 0; i < 6; i++)
+#pragma unroll
+                    for (int j = i; j < 6; j++, u++) cq[u] = Aq[tri(j, i)];
+                cq[30] = ldq;
+                cq[33] = 1.0;
+            }
         }
     }
 }
@@ -330,7 +350,7 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
 // position order.
 __global__ void __launch_bounds__(128) k_mstep_kl(MstepParams P, bool frame_start, const int *__restrict__ kperm,
                                                   double *__restrict__ pc, const double *__restrict__ kls,
-                                                  double *__restrict__ bpart)
+                                                  double *__restrict__ bpart, double *__restrict__ pcq)
 {
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
     double kl = 0.0, aq = 0.0, ap = 0.0, dn = 0.0;
@@ -368,12 +388,16 @@ __global__ void __launch_bounds__(128) k_mstep_kl(MstepParams P, bool frame_star
                     for (int l = j; l < 6; l++) w += ks[6 + tri(l, i)] * ks[6 + tri(l, j)];
                     tr += (i == j ? 1.0 : 2.0) * cache[u] * w;
                 }
+            const double lg6q = mv_lgamma6(0.5 * nq), lgaq = lgamma(aq);
             kl = 0.5 * (6.0 * bp / bq - 6.0 + bp * nq * maha + 6.0 * log(bq / bp));
-            kl += 0.5 * (nq - np) * psi_nu - 3.0 * nq + 0.5 * nq * tr + 0.5 * np * (ldq - ldp) + cache[31] -
-                  mv_lgamma6(0.5 * nq);
+            kl += 0.5 * (nq - np) * psi_nu - 3.0 * nq + 0.5 * nq * tr + 0.5 * np * (ldq - ldp) + cache[31] - lg6q;
             // Per-component part of KL(Dir(alpha_q) || Dir(alpha_p)); the psi(sum)
             // and lnGamma(sum) terms are added after the cross-component sums.
-            kl += -lgamma(aq) + cache[32] + (aq - ap) * psi_a;
+            kl += -lgaq + cache[32] + (aq - ap) * psi_a;
+            if (pcq) {   // the lnGamma terms of the next frame's prior
+                pcq[(size_t)k * kPC + 31] = lg6q;
+                pcq[(size_t)k * kPC + 32] = lgaq;
+            }
             dn = ks[34];
         }
     }
@@ -450,6 +474,8 @@ __global__ void k_stage(const double *__restrict__ src, int64_t N, double *__res
 
 } // namespace
 
+size_t mstep_prior_cache_doubles(int K) { return (size_t)K * kPC; }
+
 size_t mstep_cache_doubles(int K)
 {
     return (size_t)K * kPC + (size_t)((K + 127) / 128) * 4 + (size_t)K * kKS;   // cache, block sums, KL inputs
@@ -457,9 +483,10 @@ size_t mstep_cache_doubles(int K)
 
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
                  const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
-                 int *tile_dirty, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
-                 Prof *pf)
+                 int *tile_dirty, double *cache_next, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork,
+                 cudaEvent_t ev_join, Prof *pf)
 {
+    if (!dS) cache_next = nullptr;
     const int K = P.K;
     const int nb = (K + 127) / 128;
     double *bpart = cache + (size_t)K * kPC;
@@ -467,18 +494,46 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
     pf->begin(VBGS_PROF_MSTEP, st);
     // 64 threads a block: the per-component work is long and uneven (skipped
     // components return at once), so smaller blocks spread it over more SMs
-    launch_pdl(k_mstep, (K + 63) / 64, 64, 0, st, P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags, tile_dirty);
+    launch_pdl(k_mstep, (K + 63) / 64, 64, 0, st, P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags, tile_dirty,
+               cache_next);
     pf->end(st);
     // KL terms and their sums beside the next E-step
     if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return -1;
     pf->begin(VBGS_PROF_MSTEP, side);
-    k_mstep_kl<<<nb, 128, 0, side>>>(P, dS == nullptr, kperm, cache, kls, bpart);
+    k_mstep_kl<<<nb, 128, 0, side>>>(P, dS == nullptr, kperm, cache, kls, bpart, cache_next);
     pf->end(side);
     pf->begin(VBGS_PROF_MSTEP, side);
     launch_pdl(k_mstep_finalize, 1, 1024, 0, side, bpart, nb, scal);
     pf->end(side);
     if (cudaEventRecord(ev_join, side) != cudaSuccess) return -1;
     return cudaGetLastError() == cudaSuccess ? 3 : -1;
+}
+
+// Records to the positions of a new component order: dst[p] = src[kinv_old[kperm[p]]].
+__global__ void k_move_records(const int *__restrict__ kperm, const int *__restrict__ kinv_old, int K,
+                               const double *__restrict__ rec, const float *__restrict__ rec32,
+                               double *__restrict__ rec_dst, float *__restrict__ rec32_dst)
+{
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)K * 16) return;
+    const int p = (int)(i >> 4), q = (int)(i & 15);   // 16-byte pieces: 16 of the FP64 record, 8 of the FP32
+    const int po = kinv_old[kperm[p]];
+    reinterpret_cast<double2 *>(rec_dst + (size_t)p * VBGS_REC)[q] =
+        reinterpret_cast<const double2 *>(rec + (size_t)po * VBGS_REC)[q];
+    if (q < 8)
+        reinterpret_cast<float4 *>(rec32_dst + (size_t)p * VBGS_REC)[q] =
+            reinterpret_cast<const float4 *>(rec32 + (size_t)po * VBGS_REC)[q];
+}
+
+int launch_move_records(const int *kperm, const int *kinv_old, int K, const double *rec, const float *rec32,
+                        double *rec_dst, float *rec32_dst, cudaStream_t st, Prof *pf)
+{
+    pf->begin(VBGS_PROF_MSTEP, st);
+    launch_pdl(k_move_records, (unsigned)(((int64_t)K * 16 + 255) / 256), 256, 0, st, kperm, kinv_old, K, rec, rec32,
+               rec_dst, rec32_dst);
+    pf->end(st);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_commit(double *Spast, const double *dS, int K, const int *flags, cudaStream_t st, Prof *pf)

@@ -131,6 +131,28 @@ def test_streaming_frames_match_oracle(V):
     m.close()
 
 
+@pytest.mark.parametrize("form", ["fp64", "fp16x3"])
+def test_carried_prior_equals_recomputed(V, form):
+    """A frame after a completed frame starts from the posterior its last
+    M-step wrote (moved to the new component order); a context whose state is
+    reset through set_stats before every frame recomputes it from S_past.  The
+    two streams agree to rounding (only the order of the sum of the alpha_k
+    inside psi differs)."""
+    room = synth.Room(seed=7)
+    pr = synth.room_prior(2_000, seed=7)
+    a, b = V.Model(pr, form), V.Model(pr, form)
+    for t in range(4):
+        X = synth.room_frame(t, seed=7, width=64, height=64, room=room)
+        ta = a.update(X, 2)
+        b.set_stats(b.stats())
+        tb = b.update(X, 2)
+        assert O.relerr(ta, tb) <= 1e-12, (t, ta, tb)
+        for name, e in stat_errors(a.stats(), b.stats()).items():
+            assert e <= 1e-12, (t, name, e)
+    a.close()
+    b.close()
+
+
 def test_one_iteration_from_given_state(V):
     """One iteration from a shared FP64 state (set_stats) on a room frame."""
     room = synth.Room(seed=3)
