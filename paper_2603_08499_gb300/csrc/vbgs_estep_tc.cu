@@ -902,8 +902,9 @@ struct __align__(128) Smem2 {
     unsigned char B1[2][2 * kB1Bytes];              // hi | lo
     unsigned char B2[2][2 * kB2Bytes];              // hi | lo
     unsigned char P[2][2 * kPBytes];                // hi | lo
-    float lse2[2][kChunk2];
-    unsigned long long bar_a, bar_bfull[2], bar_d1full[2], bar_d1free[2], bar_pfull[2], bar_stfree[2], bar_d2, bar_final;
+    float lse2[3][kChunk2];                         // three stages: a lagging warp may still read the last one
+    unsigned long long bar_a, bar_b1full[2], bar_b2full[2], bar_d1full[2], bar_d1free[2], bar_pfull[2], bar_stfree[2],
+        bar_d2, bar_final;
     unsigned int tmem_base;
 };
 
@@ -1074,7 +1075,8 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
         mbar_init(&S.bar_d2, 1);
         mbar_init(&S.bar_final, 1);
         for (int i = 0; i < 2; i++) {
-            mbar_init(&S.bar_bfull[i], 128); mbar_init(&S.bar_d1full[i], 1); mbar_init(&S.bar_d1free[i], 128);
+            mbar_init(&S.bar_b1full[i], 64); mbar_init(&S.bar_b2full[i], 64);
+            mbar_init(&S.bar_d1full[i], 1); mbar_init(&S.bar_d1free[i], 128);
             mbar_init(&S.bar_pfull[i], 128); mbar_init(&S.bar_stfree[i], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1101,8 +1103,9 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
         for (int i = 0; i < 18; i++) hf[i] = h[i];
         const int m = tid;                          // component row of the epilogue
         bool ok = true;
-        auto build = [&](int64_t c, int st) {
-            // threads 0..63 write B1 (point-major), 64..127 write B2 (feature-major); both write lse2
+        auto build = [&](int64_t c, int st, int sl) {
+            // threads 0..63 write B1 (point-major) and lse2, 64..127 write B2
+            // (feature-major); each half arrives on its own barrier
             const int pt = tid & 63;
             const int64_t c0 = chunk_at((int)c) * kChunk2;
             const int64_t n = c0 + pt;
@@ -1140,7 +1143,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
                     *reinterpret_cast<uint4 *>(bh + b1_off(pt, 8 * q)) = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
                     *reinterpret_cast<uint4 *>(bl + b1_off(pt, 8 * q)) = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
                 }
-                S.lse2[st][pt] = n < N ? lse2f[n] : INFINITY;
+                S.lse2[sl][pt] = n < N ? lse2f[n] : INFINITY;
             } else {
                 unsigned char *bh = S.B2[st], *bl = S.B2[st] + kB2Bytes;
 #pragma unroll
@@ -1152,7 +1155,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
                 }
             }
             fence_async_smem();
-            mbar_arrive(&S.bar_bfull[st]);
+            mbar_arrive(tid < 64 ? &S.bar_b1full[st] : &S.bar_b2full[st]);
         };
         // Statistics of component row m about its own mean m_k (FP32), from
         // each chunk's moments about the chunk origin o_c (first point),
@@ -1200,24 +1203,17 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
                     st[u] += fmaf(sc[a] * sc[b], __uint_as_float(v[u]),
                                   fmaf(dl[a], s1[b], fmaf(s1[a], dl[b], nn * dl[a] * dl[b])));
         };
-        int64_t c = next_chunk(cbeg);
-        int u = 0;
-        if (c < cend) { build(c, 0); stagepos0 = c; }
-        while (c < cend && ok) {
-            const int s = u & 1;
-            if (u >= 1) {
-                // MMA2(u-1) done: its chunk moments are in D2[(u+1)&1], and the
-                // operand stage (u+1)&1 is free for the next chunk
-                ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_stfree[(u + 1) & 1], (uint32_t)(((u - 1) >> 1) & 1), flags));
-                if (!ok) break;
-                fence_after();
-                add_d2((u + 1) & 1);
-            }
-            const int64_t cn = next_chunk(c + 1);
-            if (cn < cend) {
-                build(cn, (u + 1) & 1);
-                if ((u + 1) & 1) stagepos1 = cn; else stagepos0 = cn;
-            }
+        // Chunk u: (a) B1 and lse2 of chunk u+1 (threads 0..63); (b) the
+        // responsibilities of chunk u from MMA1(u); (c) once MMA2(u-1) is done,
+        // the statistics of chunk u-1 from D2 and B2 of chunk u+1 (threads
+        // 64..127, its stage was MMA2(u-1)'s).  MMA2(u-1) thus runs while (b)
+        // computes, instead of the epilogue waiting for it.
+        const int64_t nc = cend - cbeg;
+        if (nc > 0) { build(cbeg, 0, 0); stagepos0 = cbeg; }
+        for (int64_t u = 0; u < nc && ok; u++) {
+            const int s = (int)(u & 1);
+            const int64_t cn = cbeg + u + 1;
+            if (cn < cend && tid < 64) build(cn, s ^ 1, (int)((u + 1) % 3));
             ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_d1full[s], (uint32_t)((u >> 1) & 1), flags));
             if (!ok) break;
             fence_after();
@@ -1228,9 +1224,10 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
             tmem_wait_ld();
             fence_before();
             mbar_arrive(&S.bar_d1free[s]);
-            // r = 2^(l2 - lse2) -> FP16, row m of P (P[s] was last read by MMA2(u-2), waited above)
+            // r = 2^(l2 - lse2) -> FP16, row m of P (P[s] was last read by
+            // MMA2(u-2), waited for in the previous chunk's step (c))
             unsigned char *prow = S.P[s];
-            const float4 *l4 = reinterpret_cast<const float4 *>(S.lse2[s]);
+            const float4 *l4 = reinterpret_cast<const float4 *>(S.lse2[u % 3]);
 #pragma unroll
             for (int g = 0; g < 8; g++) {
                 const float4 la = l4[2 * g], lb = l4[2 * g + 1];
@@ -1250,14 +1247,25 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
             }
             fence_async_smem();
             mbar_arrive(&S.bar_pfull[s]);
-            c = cn;
-            u++;
+            if (u >= 1) {
+                // MMA2(u-1) done: chunk u-1's moments are in D2[s^1], and
+                // the B2 stage s^1 is free for chunk u+1
+                ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_stfree[s ^ 1], (uint32_t)(((u - 1) >> 1) & 1), flags));
+                if (!ok) break;
+                fence_after();
+                add_d2(s ^ 1);
+            }
+            if (cn < cend) {
+                if (tid >= 64) build(cn, s ^ 1, (int)((u + 1) % 3));
+                if (s) stagepos0 = cn; else stagepos1 = cn;
+            }
         }
-        if (ok && u >= 1) {
-            ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_stfree[(u - 1) & 1], (uint32_t)(((u - 1) >> 1) & 1), flags));
+        if (ok && nc >= 1) {
+            const int sl = (int)((nc - 1) & 1);
+            ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_stfree[sl], (uint32_t)(((nc - 1) >> 1) & 1), flags));
             if (ok) {
                 fence_after();
-                add_d2((u - 1) & 1);
+                add_d2(sl);
             }
         }
         const int k = j * kCols + m;
@@ -1296,7 +1304,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
         };
         // MMA1 of the first chunk
         if (ok && c < cend) {
-            ok = mbar_wait(&S.bar_bfull[0], 0u, flags);
+            ok = mbar_wait(&S.bar_b1full[0], 0u, flags);
             if (ok) { fence_after(); mma1(0); any_mma = true; }
         }
         int u = 0;
@@ -1305,13 +1313,14 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
             const int64_t cn = next_chunk(c + 1);
             if (cn < cend) {
                 const int s1 = (u + 1) & 1;
-                ok = mbar_wait(&S.bar_bfull[s1], (uint32_t)(((u + 1) >> 1) & 1), flags) &&
+                ok = mbar_wait(&S.bar_b1full[s1], (uint32_t)(((u + 1) >> 1) & 1), flags) &&
                      (u + 1 < 2 || mbar_wait(&S.bar_d1free[s1], (uint32_t)((((u + 1) >> 1) - 1) & 1), flags));
                 if (!ok) break;
                 fence_after();
                 mma1(u + 1);
             }
-            ok = mbar_wait(&S.bar_pfull[s], (uint32_t)((u >> 1) & 1), flags);
+            ok = mbar_wait(&S.bar_pfull[s], (uint32_t)((u >> 1) & 1), flags) &&
+                 mbar_wait(&S.bar_b2full[s], (uint32_t)((u >> 1) & 1), flags);
             if (!ok) break;
             fence_after();
             const unsigned char *Pp = S.P[s];

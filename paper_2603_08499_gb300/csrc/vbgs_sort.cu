@@ -5,7 +5,10 @@
 // spatially coherent order: 30-bit Morton codes of the position (x, y, z)
 // inside a fixed box, sorted with CUB's radix sort.  Neighbouring points and
 // components then share tiles, which is what lets pass 2 skip tiles whose
-// responsibilities are all negligible.
+// responsibilities are all negligible.  Only the top 16 bits of the codes
+// are sorted (two radix passes instead of four): cells of 1/40 of the box per
+// axis, far smaller than the region of a 128-wide tile; the sort is stable,
+// so inside a cell the input order stays.
 //   points:      pidx[i] = original index of the i-th point in Morton order
 //   components:  kperm[p] = original index of the component at position p,
 //                kinv[k] = position of component k; positions are ordered
@@ -16,6 +19,8 @@
 namespace vbgs {
 
 namespace {
+
+constexpr int kSortLo = 14;   // lowest code bit sorted
 
 __device__ __forceinline__ uint32_t spread10(uint32_t v)
 {
@@ -103,7 +108,7 @@ int launch_point_order(const double *X, int64_t N, const BoxParams &box, SortBuf
     launch_pdl(k_point_codes, (unsigned)((N + 255) / 256), 256, 0, st, X, N, box, sb.keys_in, sb.idx_in);
     pf->end(st);
     size_t bytes = sb.temp_bytes;
-    if (cub::DeviceRadixSort::SortPairs(sb.temp, bytes, sb.keys_in, sb.keys_out, sb.idx_in, pidx, (int)N, 0, 30,
+    if (cub::DeviceRadixSort::SortPairs(sb.temp, bytes, sb.keys_in, sb.keys_out, sb.idx_in, pidx, (int)N, kSortLo, 30,
                                         st) != cudaSuccess)
         return -1;
     pf->begin(VBGS_PROF_MISC, st);
@@ -119,7 +124,7 @@ int launch_comp_order(const double *m0, const double *Spast, int K, double beta0
     launch_pdl(k_comp_codes, (K + 255) / 256, 256, 0, st, m0, Spast, K, beta0, box, sb.keys_in, sb.idx_in);
     pf->end(st);
     size_t bytes = sb.temp_bytes;
-    if (cub::DeviceRadixSort::SortPairs(sb.temp, bytes, sb.keys_in, sb.keys_out, sb.idx_in, kperm, K, 0, 30, st) !=
+    if (cub::DeviceRadixSort::SortPairs(sb.temp, bytes, sb.keys_in, sb.keys_out, sb.idx_in, kperm, K, kSortLo, 30, st) !=
         cudaSuccess)
         return -1;
     pf->begin(VBGS_PROF_MISC, st);
