@@ -1098,29 +1098,38 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
 
     if (warp < 4) {
         // ---------------- builders + responsibilities ----------------
-        float hf[18];
-#pragma unroll
-        for (int i = 0; i < 18; i++) hf[i] = h[i];
+        const float *hf = h;   // tile frame (header), read where used (uniform, cached)
         const int m = tid;                          // component row of the epilogue
         bool ok = true;
-        auto build = [&](int64_t c, int st, int sl) {
+        // The next chunk's inputs, loaded one chunk ahead of their use: this
+        // thread's point (FP32 hi/lo) and, for threads 0..63, its lse2.  The
+        // chunk origin (its first point, which thread 0 loads too) is read
+        // where it is used.
+        float nx[12], nl = INFINITY;
+        int64_t nc0 = 0;
+        auto load_next = [&](int64_t c) {
+            nc0 = chunk_at((int)c) * kChunk2;
+            const int64_t n = nc0 + (tid & 63);
+            const float4 *xp = reinterpret_cast<const float4 *>(Xhl + (n < N ? n : N - 1) * 16);
+            const float4 p0 = xp[0], p1 = xp[1], p2 = xp[2], p3 = xp[3];
+            nx[0] = p0.x; nx[1] = p0.y; nx[2] = p0.z; nx[3] = p0.w; nx[4] = p1.x; nx[5] = p1.y;
+            nx[6] = p2.x; nx[7] = p2.y; nx[8] = p2.z; nx[9] = p2.w; nx[10] = p3.x; nx[11] = p3.y;
+            if (tid < 64) nl = n < N ? lse2f[n] : INFINITY;
+        };
+        auto build = [&](int st, int sl) {
             // threads 0..63 write B1 (point-major) and lse2, 64..127 write B2
             // (feature-major); each half arrives on its own barrier
             const int pt = tid & 63;
-            const int64_t c0 = chunk_at((int)c) * kChunk2;
-            const int64_t n = c0 + pt;
-            const int64_t nn = n < N ? n : N - 1;
             float d[6];
-            const float *xp = Xhl + nn * 16;
             if (tid < 64) {
                 // logits: the tile's frame, like the coefficients
 #pragma unroll
-                for (int i = 0; i < 6; i++) d[i] = ((xp[i] - hf[i]) + (xp[8 + i] - hf[6 + i])) * hf[12 + i];
+                for (int i = 0; i < 6; i++) d[i] = ((nx[i] - hf[i]) + (nx[6 + i] - hf[6 + i])) * hf[12 + i];
             } else {
                 // statistics: the chunk's frame, origin at its first point
-                const float *xo = Xhl + c0 * 16;
+                const float *xo = Xhl + nc0 * 16;
 #pragma unroll
-                for (int i = 0; i < 6; i++) d[i] = ((xp[i] - xo[i]) + (xp[8 + i] - xo[8 + i])) * hf[12 + i];
+                for (int i = 0; i < 6; i++) d[i] = ((nx[i] - xo[i]) + (nx[6 + i] - xo[8 + i])) * hf[12 + i];
             }
             float f[kFeat];
             f[0] = 1.f;
@@ -1143,7 +1152,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
                     *reinterpret_cast<uint4 *>(bh + b1_off(pt, 8 * q)) = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
                     *reinterpret_cast<uint4 *>(bl + b1_off(pt, 8 * q)) = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
                 }
-                S.lse2[sl][pt] = n < N ? lse2f[n] : INFINITY;
+                S.lse2[sl][pt] = nl;
             } else {
                 unsigned char *bh = S.B2[st], *bl = S.B2[st] + kB2Bytes;
 #pragma unroll
@@ -1179,15 +1188,15 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
                 ml[i] = (float)(v - (double)mh[i]);
             }
         }
-        int64_t stagepos0 = 0, stagepos1 = 0;   // chunk held by each operand stage
+        int64_t org0 = 0, org1 = 0;   // origin (first point) of the chunk in each stage
         auto add_d2 = [&](int stage) {
             uint32_t v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 128u + (uint32_t)(stage * kFeat), v);
             tmem_wait_ld();
-            const int64_t c0 = chunk_at((int)(stage ? stagepos1 : stagepos0)) * kChunk2;
+            const float *xo = Xhl + (stage ? org1 : org0) * 16;
             float dl[6], s1[6];
 #pragma unroll
-            for (int i = 0; i < 6; i++) dl[i] = (Xhl[c0 * 16 + i] - mh[i]) + (Xhl[c0 * 16 + 8 + i] - ml[i]);
+            for (int i = 0; i < 6; i++) dl[i] = (xo[i] - mh[i]) + (xo[8 + i] - ml[i]);
             const float nn = __uint_as_float(v[0]);
             st[0] += nn;
 #pragma unroll
@@ -1209,11 +1218,16 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
         // 64..127, its stage was MMA2(u-1)'s).  MMA2(u-1) thus runs while (b)
         // computes, instead of the epilogue waiting for it.
         const int64_t nc = cend - cbeg;
-        if (nc > 0) { build(cbeg, 0, 0); stagepos0 = cbeg; }
+        if (nc > 0) {
+            load_next(cbeg);
+            build(0, 0);
+            org0 = nc0;
+            if (nc > 1) load_next(cbeg + 1);
+        }
         for (int64_t u = 0; u < nc && ok; u++) {
             const int s = (int)(u & 1);
             const int64_t cn = cbeg + u + 1;
-            if (cn < cend && tid < 64) build(cn, s ^ 1, (int)((u + 1) % 3));
+            if (cn < cend && tid < 64) build(s ^ 1, (int)((u + 1) % 3));
             ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_d1full[s], (uint32_t)((u >> 1) & 1), flags));
             if (!ok) break;
             fence_after();
@@ -1256,8 +1270,9 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
                 add_d2(s ^ 1);
             }
             if (cn < cend) {
-                if (tid >= 64) build(cn, s ^ 1, (int)((u + 1) % 3));
-                if (s) stagepos0 = cn; else stagepos1 = cn;
+                if (tid >= 64) build(s ^ 1, (int)((u + 1) % 3));
+                if (s) org0 = nc0; else org1 = nc0;
+                if (cn + 1 < cend) load_next(cn + 1);
             }
         }
         if (ok && nc >= 1) {
