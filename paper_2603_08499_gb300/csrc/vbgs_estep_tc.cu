@@ -1107,8 +1107,12 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
         // where it is used.
         float nx[12], nl = INFINITY;
         int64_t nc0 = 0;
+        // list entry of the chunk after the one load_next(c) is called for,
+        // read one call ahead
+        int64_t c0_ahead = cbeg < cend ? chunk_at((int)cbeg) * kChunk2 : 0;
         auto load_next = [&](int64_t c) {
-            nc0 = chunk_at((int)c) * kChunk2;
+            nc0 = c0_ahead;
+            if (c + 1 < cend) c0_ahead = chunk_at((int)(c + 1)) * kChunk2;
             const int64_t n = nc0 + (tid & 63);
             const float4 *xp = reinterpret_cast<const float4 *>(Xhl + (n < N ? n : N - 1) * 16);
             const float4 p0 = xp[0], p1 = xp[1], p2 = xp[2], p3 = xp[3];
