@@ -722,20 +722,78 @@ __global__ void __launch_bounds__(128) k_p1_boxes(const double *__restrict__ X, 
 
 // ub[P][j] for every point tile: a CTA per (component tile j, 128 point
 // tiles), the tile's bound terms (m, c, lp, lc, la; 16-byte aligned rows for
-// vector loads) in shared memory, one thread per point tile.
+// vector loads) in shared memory, one thread per point tile.  Branch and
+// bound for the maximum: each group of 32 components has a summary (box of
+// its means, largest c, smallest lp, lc, la) whose bound dominates every
+// member's (each step is monotone, also in FP32); a group whose summary bound
+// does not exceed the maximum found so far cannot raise it and is skipped.
+// The result equals the maximum over all components.
+__device__ __forceinline__ float p1_bound(const float *c, const float lo[6], const float hi[6])
+{
+    float dp = 0.f, dc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float o = fmaxf(fmaxf(lo[i] - c[i], c[i] - hi[i]), 0.f);
+        dp = fmaf(o, o, dp);
+        const float oc = fmaxf(fmaxf(lo[3 + i] - c[3 + i], c[3 + i] - hi[3 + i]), 0.f);
+        dc = fmaf(oc, oc, dc);
+    }
+    return c[6] - 0.5f * fmaxf(fmaxf(c[7] * dp, c[8] * dc), c[9] * (dp + dc));
+}
+// the same for a group summary g: means box (lo g[0..5], hi g[6..11]), g[12..15] = cmax, lpmin, lcmin, lamin
+__device__ __forceinline__ float p1_group_bound(const float *g, const float lo[6], const float hi[6])
+{
+    float dp = 0.f, dc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float o = fmaxf(fmaxf(lo[i] - g[6 + i], g[i] - hi[i]), 0.f);
+        dp = fmaf(o, o, dp);
+        const float oc = fmaxf(fmaxf(lo[3 + i] - g[9 + i], g[3 + i] - hi[3 + i]), 0.f);
+        dc = fmaf(oc, oc, dc);
+    }
+    return g[12] - 0.5f * fmaxf(fmaxf(g[13] * dp, g[14] * dc), g[15] * (dp + dc));
+}
+
 __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, int ptiles, int K, int ntiles,
                                                const float *__restrict__ rec32, float *__restrict__ ub)
 {
     pdl_wait();
     __shared__ __align__(16) float sc[kCols][12];
-    const int j = blockIdx.x, t = threadIdx.x;
+    __shared__ float sg[kCols / 32][16];
+    const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int k = j * kCols + t;
     const int nv = min(kCols, K - j * kCols);
     {
         const float *r = rec32 + (size_t)(k < K ? k : 0) * VBGS_REC;
+        float v[16];
 #pragma unroll
         for (int i = 0; i < 6; i++) sc[t][i] = r[i];
         sc[t][6] = r[27]; sc[t][7] = r[28]; sc[t][8] = r[29]; sc[t][9] = r[30];
+        // group summary over the valid components of this warp's 32
+        const bool valid = t < nv;
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            v[i] = valid ? r[i] : INFINITY;
+            v[6 + i] = valid ? r[i] : -INFINITY;
+        }
+        v[12] = valid ? r[27] : -INFINITY;
+#pragma unroll
+        for (int i = 0; i < 3; i++) v[13 + i] = valid ? r[28 + i] : INFINITY;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const bool mx = i >= 6 && i <= 12;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, v[i], o);
+                v[i] = mx ? fmaxf(v[i], ov) : fminf(v[i], ov);
+            }
+        }
+        if (lane < 16) {
+            float x = v[0];
+#pragma unroll
+            for (int i = 1; i < 16; i++) x = lane == i ? v[i] : x;
+            sg[w][lane] = x;
+        }
     }
     __syncthreads();
     const int P = blockIdx.y * kCols + t;
@@ -743,21 +801,30 @@ __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, 
         float lo[6], hi[6];
 #pragma unroll
         for (int i = 0; i < 6; i++) { lo[i] = boxes[(size_t)P * 12 + i]; hi[i] = boxes[(size_t)P * 12 + 6 + i]; }
-        float b = -INFINITY;
-        for (int q = 0; q < nv; q++) {
-            const float4 c0 = *reinterpret_cast<const float4 *>(&sc[q][0]);
-            const float4 c1 = *reinterpret_cast<const float4 *>(&sc[q][4]);
-            const float4 c2 = *reinterpret_cast<const float4 *>(&sc[q][8]);
-            const float c[10] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y};
-            float dp = 0.f, dc = 0.f;
+        static_assert(kCols / 32 == 4, "four component groups per tile");
+        float gb[4];
+        int g0 = 0;
+        float gbest = -INFINITY;
 #pragma unroll
-            for (int i = 0; i < 3; i++) {
-                const float o = fmaxf(fmaxf(lo[i] - c[i], c[i] - hi[i]), 0.f);
-                dp = fmaf(o, o, dp);
-                const float oc = fmaxf(fmaxf(lo[3 + i] - c[3 + i], c[3 + i] - hi[3 + i]), 0.f);
-                dc = fmaf(oc, oc, dc);
+        for (int g = 0; g < 4; g++) {
+            gb[g] = p1_group_bound(sg[g], lo, hi);
+            if (gb[g] > gbest) { gbest = gb[g]; g0 = g; }
+        }
+        float b = -INFINITY;
+        // the group with the largest summary bound first, then the others
+#pragma unroll
+        for (int gi = 0; gi < kCols / 32; gi++) {
+            const int g = gi == 0 ? g0 : (gi <= g0 ? gi - 1 : gi);
+            const float bg = g == 0 ? gb[0] : g == 1 ? gb[1] : g == 2 ? gb[2] : gb[3];   // no local-memory index
+            if (!(bg > b)) continue;
+            const int q1 = min(nv, g * 32 + 32);
+            for (int q = g * 32; q < q1; q++) {
+                const float4 c0 = *reinterpret_cast<const float4 *>(&sc[q][0]);
+                const float4 c1 = *reinterpret_cast<const float4 *>(&sc[q][4]);
+                const float4 c2 = *reinterpret_cast<const float4 *>(&sc[q][8]);
+                const float c[10] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y};
+                b = fmaxf(b, p1_bound(c, lo, hi));
             }
-            b = fmaxf(b, c[6] - 0.5f * fmaxf(fmaxf(c[7] * dp, c[8] * dc), c[9] * (dp + dc)));
         }
         ub[(size_t)P * ntiles + j] = b;
     }
