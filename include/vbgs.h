@@ -110,8 +110,11 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
  * doubles, host, may be NULL) receives the ELBO of the posterior entering
  * each iteration, against the effective prior prior0 (+) S_past.  N may be 0.
  * Errors: VBGS_EINVAL (NULL ctx/points with N > 0, N < 0, n_iters < 1,
- * non-finite coordinates; the state is left unchanged), VBGS_ENUMERIC,
- * VBGS_ECUDA, VBGS_ENOMEM. */
+ * non-finite coordinates; the state is left unchanged: S_past and the
+ * posterior.  Device-resident points are checked while the frame runs, so
+ * after such an error the per-call results -- elbo_trace, vbgs_get_lse,
+ * vbgs_get_frame_stats -- are undefined), VBGS_ENUMERIC, VBGS_ECUDA,
+ * VBGS_ENOMEM. */
 int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, double *elbo_trace);
 
 /* Many independent scenes at once (each its own context, uneven N and K):

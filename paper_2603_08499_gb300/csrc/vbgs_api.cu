@@ -184,8 +184,13 @@ int ensure_elbo(vbgs_ctx *ctx, int n)
     return VBGS_OK;
 }
 
-// Stage N points (host or device) into d_X and validate them.
-int stage_points(vbgs_ctx *ctx, const double *points, int64_t N)
+// Stage N points (host or device) into d_X and validate them.  defer_check
+// (device points): the staging kernel sets the bad-point flag and the frame
+// runs on; the commit of S_past skips on that flag and check_flags reports
+// it, so the statistics stay unchanged without a synchronisation here.  Every
+// kernel of a frame is bounded whatever the values (indices come from counts
+// and lists, never from coordinates).
+int stage_points(vbgs_ctx *ctx, const double *points, int64_t N, bool defer_check = false)
 {
     if (N == 0) return VBGS_OK;
     if (is_device_pointer(points)) {
@@ -193,6 +198,7 @@ int stage_points(vbgs_ctx *ctx, const double *points, int64_t N)
         int l = launch_stage_points(points, N, ctx->d_X, ctx->d_flags, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "point staging launch failed");
         ctx->launches += l;
+        if (defer_check) return VBGS_OK;
         int bad = 0;
         CU(cudaMemcpyAsync(&bad, ctx->d_flags + FL_BAD_POINT, sizeof(int), cudaMemcpyDeviceToHost,
                            ctx->stream));
@@ -703,6 +709,7 @@ int check_flags(vbgs_ctx *ctx)
     CU(cudaMemcpyAsync(fl, ctx->d_flags, sizeof fl, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->prof.collect();
+    if (fl[FL_BAD_POINT]) return fail(ctx, VBGS_EINVAL, "non-finite point coordinate");
     if (fl[FL_NONPD])
         return fail(ctx, VBGS_ENUMERIC, "posterior W^-1 of component %d is not positive definite",
                     fl[FL_NONPD] - 1);
@@ -712,7 +719,7 @@ int check_flags(vbgs_ctx *ctx)
 
 // vbgs_update in three parts: validation, capacity and staging (may
 // synchronise); the asynchronous frame itself (stream-capturable); results.
-int update_prepare(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters)
+int update_prepare(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, bool defer_check = false)
 {
     if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
     if (N < 0 || n_iters < 1) return fail(ctx, VBGS_EINVAL, "need N >= 0 and n_iters >= 1");
@@ -721,13 +728,13 @@ int update_prepare(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters)
     int rc;
     // outside any stream capture: finish the M-step work of earlier calls
     if ((rc = join_side(ctx)) || (rc = ensure_capacity(ctx, N)) || (rc = ensure_elbo(ctx, n_iters))) return rc;
-    return stage_points(ctx, points, N);
+    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));   // this frame's flags
+    return stage_points(ctx, points, N, defer_check);
 }
 
 int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters, bool carry_prior)
 {
     int rc;
-    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
     const bool from_next = carry_prior && ctx->next_prior_ready;
     const bool reorder = !(ctx->flags & VBGS_FLAG_NO_REORDER);
     ctx->next_prior_ready = false;
@@ -1310,7 +1317,9 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
 int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, double *elbo_trace)
 {
     int rc;
-    if ((rc = update_prepare(ctx, points, N, n_iters))) return rc;
+    // device points are checked during the frame (the proposal's training
+    // must not see them, so it checks first)
+    if ((rc = update_prepare(ctx, points, N, n_iters, ctx && !ctx->prop.on))) return rc;
     if ((rc = update_enqueue(ctx, N, n_iters, true))) return rc;
     if (elbo_trace)
         CU(cudaMemcpyAsync(elbo_trace, ctx->d_elbo, sizeof(double) * n_iters, cudaMemcpyDeviceToHost,
