@@ -270,8 +270,9 @@ int frame_start_from_next(vbgs_ctx *ctx, bool moved, const int *kinv_old)
         std::swap(ctx->d_rec32, ctx->d_rec32_alt);
         if (is_tc(ctx)) CU(cudaMemsetAsync(ctx->d_tile_dirty, 0x01, sizeof(int) * ((ctx->K + 127) / 128), ctx->stream));
     }
-    CU(cudaMemcpyAsync(ctx->d_pcache, ctx->d_pcache_next, sizeof(double) * mstep_prior_cache_doubles(ctx->K),
-                       cudaMemcpyDeviceToDevice, ctx->stream));
+    l = launch_apply_next(ctx->K, ctx->d_pcache_next, ctx->d_pcache, ctx->stream, &ctx->prof);
+    if (l < 0) return fail(ctx, VBGS_ECUDA, "prior cache launch failed");
+    ctx->launches += l;
     CU(cudaMemsetAsync(ctx->d_scal + SC_KL_TOTAL, 0, sizeof(double), ctx->stream));
     if (is_tc(ctx)) {
         l = launch_coef_tiles(ctx->d_rec, ctx->d_rec32, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles,

@@ -164,9 +164,11 @@ int launch_stage_points(const double *src, int64_t N, double *X, int *flags, cud
 size_t mstep_cache_doubles(int K);
 // The record kernel runs on st; the KL terms and their sums (scal) on side,
 // after ev_fork; ev_join completes them (wait on it before reading scal).
-// cache_next (nullable, used only with dS): also write each component's
-// posterior q as an effective-prior cache entry; after the commit it is the
-// next frame's effective prior bit for bit (the last iteration of a frame).
+// cache_next (nullable, used only with dS): also write the posterior q of
+// every recomputed component as an effective-prior cache entry (one slot per
+// recomputed component, with its index); after the commit they are the next
+// frame's effective prior bit for bit (the last iteration of a frame), the
+// other components keep q = p.
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
                  const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
                  int *tile_dirty, double *cache_next, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork,
@@ -174,6 +176,9 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
 int launch_move_records(const int *kperm, const int *kinv_old, int K, const double *rec, const float *rec32,
                         double *rec_dst, float *rec32_dst, cudaStream_t st, Prof *pf);
 size_t mstep_prior_cache_doubles(int K);
+// cache: the prior cache of the frame's previous M-steps; slots: the next
+// frame's prior of each component the last M-step recomputed.
+int launch_apply_next(int K, const double *slots, double *cache, cudaStream_t st, Prof *pf);
 size_t sort_temp_bytes(int64_t n);
 int launch_point_order(const double *X, int64_t N, const BoxParams &box, SortBuffers &sb, double *Xs,
                        int *pidx, cudaStream_t st, Prof *pf);

@@ -203,37 +203,31 @@ __device__ void block_sums4(double v0, double v1, double v2, double v3, double *
 // recomputed, 0: q = p) and the frame count Delta N_k.
 constexpr int kKS = 36;
 
-__global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__restrict__ m0,
-                                               const double *__restrict__ Spast,
-                                               const double *__restrict__ dS,
-                                               const int *__restrict__ kperm,
-                                               double *__restrict__ rec, float *__restrict__ rec32,
-                                               double *__restrict__ pc, double *__restrict__ kls,
-                                               int *__restrict__ flags, int *__restrict__ tile_dirty,
-                                               double *__restrict__ pcq)
+// all 28 frame statistics of component k exactly zero (either sign): an
+// integer test of the bit patterns, off the FP64 pipe
+__device__ __forceinline__ bool stats_zero(const double *__restrict__ dS, int k)
 {
-    pdl_wait();
-    const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= P.K) return;
-    const int k = kperm ? kperm[pos] : pos;
-    double *ks = kls + (size_t)k * kKS;
-    // all 28 frame statistics exactly zero (either sign): integer test of
-    // the bit patterns, off the FP64 pipe
-    bool zero = false;
-    if (dS) {
-        unsigned long long bits = 0;
+    const longlong2 *v = reinterpret_cast<const longlong2 *>(dS + (size_t)k * 28);   // 224-byte rows
+    unsigned long long bits = 0;
 #pragma unroll
-        for (int f = 0; f < 28; f++) bits |= (unsigned long long)__double_as_longlong(dS[(size_t)k * 28 + f]);
-        zero = (bits << 1) == 0;
-        if (zero && pc[(size_t)k * kPC + 33] != 0.0) {
-            ks[33] = 0.0;
-            ks[34] = 0.0;
-            if (pcq)   // q = p: the next frame's prior is this one's
-#pragma unroll
-                for (int f = 0; f < 34; f++) pcq[(size_t)k * kPC + f] = pc[(size_t)k * kPC + f];
-            return;
-        }
+    for (int f = 0; f < 14; f++) {
+        const longlong2 w = v[f];
+        bits |= (unsigned long long)w.x | (unsigned long long)w.y;
     }
+    return (bits << 1) == 0;
+}
+
+// The posterior of component k (record position pos), one thread: record,
+// prior cache (dS == nullptr) or KL hand-off (dS), and the next frame's
+// prior into the slot cq (nullable).
+__device__ __forceinline__ void mstep_thread(const MstepParams &P, const double *__restrict__ m0,
+                                             const double *__restrict__ Spast, const double *__restrict__ dS,
+                                             int pos, int k, bool zero, double *__restrict__ rec,
+                                             float *__restrict__ rec32, double *__restrict__ pc,
+                                             double *__restrict__ kls, int *__restrict__ flags,
+                                             int *__restrict__ tile_dirty, double *__restrict__ cq)
+{
+    double *ks = kls + (size_t)k * kKS;
     {
         double st[28], m0k[6], aq;
 #pragma unroll
@@ -323,11 +317,11 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
             ks[27] = aq; ks[28] = bq; ks[29] = nq; ks[30] = ldq; ks[31] = psi_nu; ks[32] = psi_a;
             ks[33] = 1.0;
             ks[34] = st[0] - Spast[(size_t)k * 28];
-            if (pcq) {
+            if (cq) {
                 // After the commit S_past + Delta S is bitwise the st above,
                 // so q is the next frame's effective prior: its cache entry
-                // (the lnGamma terms come from k_mstep_kl).
-                double *cq = pcq + (size_t)k * kPC;
+                // (the lnGamma terms come from k_mstep_kl) and k.
+                cq[34] = (double)k;
                 cq[0] = aq; cq[1] = bq; cq[2] = nq;
 #pragma unroll
                 for (int i = 0; i < 6; i++) cq[3 + i] = mq[i];
@@ -340,6 +334,279 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
                 cq[33] = 1.0;
             }
         }
+    }
+}
+
+__global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__restrict__ m0,
+                                               const double *__restrict__ Spast,
+                                               const double *__restrict__ dS,
+                                               const int *__restrict__ kperm,
+                                               double *__restrict__ rec, float *__restrict__ rec32,
+                                               double *__restrict__ pc, double *__restrict__ kls,
+                                               int *__restrict__ flags, int *__restrict__ tile_dirty,
+                                               double *__restrict__ pcq)
+{
+    pdl_wait();
+    const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= P.K) return;
+    const int k = kperm ? kperm[pos] : pos;
+    bool zero = false;
+    if (dS) {
+        zero = stats_zero(dS, k);
+        if (zero && pc[(size_t)k * kPC + 33] != 0.0) {
+            double *ks = kls + (size_t)k * kKS;
+            ks[33] = 0.0;
+            ks[34] = 0.0;
+            return;
+        }
+    }
+    mstep_thread(P, m0, Spast, dS, pos, k, zero, rec, rec32, pc, kls, flags, tile_dirty, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// M-step of an iteration (dS given).  Few components change in a frame (a few
+// hundred of 50,000 on the room stream), and an FP64 instruction occupies a
+// warp's SM sub-partition for 64 cycles whatever its active lanes, so a
+// thread-per-component kernel is bound by the latency of one component's
+// serial FP64 chain.  k_mstep_scan compacts the components to recompute into
+// a list (the others only hand over q = p); k_mstep_list then computes each
+// five listed components with a warp, six lanes each over the rows of its
+// 6 x 6 matrices (about 300 FP64 instructions per warp instead of 650 for
+// one chain), or, for long lists, one thread per component as k_mstep does.  Every entry is formed by the
+// same operations in the same order as in mstep_thread.
+// ---------------------------------------------------------------------------
+constexpr int kListWarpMax = 5 * 1216;   // longest list computed five components to a warp (2 warps per SM sub-partition)
+
+__global__ void __launch_bounds__(128) k_mstep_scan(int K, const double *__restrict__ dS, const int *__restrict__ kperm,
+                                                    const double *__restrict__ pc, double *__restrict__ kls,
+                                                    int *__restrict__ list, int *__restrict__ count)
+{
+    pdl_wait();
+    const int pos = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    bool act = false;
+    if (pos < K) {
+        const int k = kperm ? kperm[pos] : pos;
+        act = !(stats_zero(dS, k) && pc[(size_t)k * kPC + 33] != 0.0);
+        if (!act) {   // q = p (also the next frame's prior: its cache entry stays)
+            double *ks = kls + (size_t)k * kKS;
+            ks[33] = 0.0;
+            ks[34] = 0.0;
+        }
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, act);
+    if (b) {
+        const int leader = __ffs(b) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(count, __popc(b));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (act) list[base + __popc(b & ((1u << lane) - 1u))] = pos;
+    }
+}
+
+// a ? x : y as a 64-bit bit select the compiler keeps in registers (a chain
+// of ternaries over an array is otherwise turned into a local-memory lookup)
+__device__ __forceinline__ double sel64(bool a, double x, double y)
+{
+    unsigned long long r;
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\tselp.b64 %0, %1, %2, p;\n\t}"
+        : "=l"(r)
+        : "l"(__double_as_longlong(x)), "l"(__double_as_longlong(y)), "r"((unsigned)a));
+    return __longlong_as_double((long long)r);
+}
+
+// Listed components, five to a warp: lanes 6g..6g+5 hold rows r = 0..5 of
+// component g's matrices (lanes 30, 31 idle).  w0r[j] = W0^-1 at
+// (min(r, j), max(r, j)), as nw_from_stats reads it.  The inverse L^-1 is kept
+// by distance from the diagonal (Lid[s] = (L^-1)[r][r - s]) so that every
+// register index stays a compile-time constant.
+__device__ __forceinline__ void mstep_group(const MstepParams &P, const double w0r[6], int r, int gb, bool gv,
+                                            const double *__restrict__ m0, const double *__restrict__ Spast,
+                                            const double *__restrict__ dS, int pos, int k, double *__restrict__ rec,
+                                            float *__restrict__ rec32, double *__restrict__ pc,
+                                            double *__restrict__ kls, int *__restrict__ flags,
+                                            int *__restrict__ tile_dirty, double *__restrict__ cq)
+{
+    constexpr unsigned F = 0xffffffffu;
+    auto row = [&](double v, int rr) { return __shfl_sync(F, v, (gb + rr) & 31); };
+    const double *Sk = Spast + (size_t)k * 28, *dk = dS + (size_t)k * 28;
+    // posterior parameters (nw_from_stats, entry by entry)
+    const double st0 = Sk[0] + dk[0];
+    const double aq = P.alpha0 + st0, bq = P.beta0 + st0, nq = P.nu0 + st0;
+    const double ib = 1.0 / bq;
+    const double m0r = m0[(size_t)k * 6 + r];
+    const double mr = (P.beta0 * m0r + (Sk[1 + r] + dk[1 + r])) * ib;
+    double A[6];   // row r of W_q^-1
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        const double mj = row(mr, j), m0j = row(m0r, j);
+        const bool lo = r <= j;   // (r, j) is an upper entry (i = r) or a lower one (i = j)
+        const int u = lo ? upper_index(r, j) : upper_index(j, r);
+        const double mi_ = lo ? mr : mj, mj_ = lo ? mj : mr, m0i_ = lo ? m0r : m0j, m0j_ = lo ? m0j : m0r;
+        A[j] = w0r[j] + (Sk[u] + dk[u]) + P.beta0 * m0i_ * m0j_ - bq * mi_ * mj_;
+    }
+    // Cholesky by columns (chol6_col's operations and order); row r in Lr
+    double Lr[6];
+    bool ok = true;
+#pragma unroll
+    for (int J = 0; J < 6; J++) {
+        double t = A[J];
+#pragma unroll
+        for (int kk = 0; kk < J; kk++) t -= Lr[kk] * row(Lr[kk], J);
+        const double dv = row(t, J);
+        ok = ok && (dv > 0.0);
+        const double d = fmax(dv, 1e-300);
+        const double inv = rsqrt(d);
+        Lr[J] = (r >= J) ? ((r == J) ? d : t) * inv : 0.0;
+    }
+    if (gv && r == 0 && !ok) atomicCAS(&flags[FL_NONPD], 0, k + 1);
+    double dprod = 1.0;   // ln|W^-1| = 2 ln prod_i L_ii
+#pragma unroll
+    for (int i = 0; i < 6; i++) dprod *= row(Lr[i], i);
+    const double ldq = 2.0 * log(dprod);
+    // L^-1 (trinv6's operations and order), by distance from the diagonal
+    double Ld[6], Lid[6];
+#pragma unroll
+    for (int sd = 0; sd < 6; sd++) {
+        double v = 0.0;
+#pragma unroll
+        for (int kk = 0; kk < 6; kk++) v = sel64(kk == r - sd, Lr[kk], v);
+        Ld[sd] = v;
+        Lid[sd] = 0.0;
+    }
+    Lid[0] = 1.0 / Ld[0];
+#pragma unroll
+    for (int d = 1; d < 6; d++) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < d; q++) {
+            // entry (r, r - d): L[r][k] (own, k = r - d + q) times (L^-1)[k][r - d] (row k, distance q)
+            const int src = r - d + q;
+            t += Ld[d - q] * __shfl_sync(F, Lid[q], (gb + (src > 0 ? src : 0)) & 31);
+        }
+        if (r >= d) Lid[d] = -t * Lid[0];
+    }
+    // psi(alpha_q) on row 0, the two halves of psi_6(nu_q / 2) on rows 1, 2
+    const double xd = r == 1 ? 0.5 * nq - 0.5 * 0 : r == 2 ? 0.5 * nq - 0.5 * 1 : aq;
+    const double yd = dg_digamma(xd);
+    const double term = r == 0 ? yd : 3.0 * yd - (3.0 * xd - 5.0) / ((xd - 1.0) * (xd - 2.0));
+    const double psi_a = row(term, 0);
+    double psi_nu = 0.0;
+    psi_nu += row(term, 1);
+    psi_nu += row(term, 2);
+    const double elogdet = psi_nu + 6.0 * kLn2 - ldq;
+    const double c = psi_a + 0.5 * elogdet - 3.0 * kLn2Pi - 3.0 / bq;
+    // eigenvalue bounds: position block on row 0, colour block on row 1
+    const double p00 = row(A[0], 0), p01 = row(A[0], 1), p02 = row(A[0], 2);
+    const double p11 = row(A[1], 1), p12 = row(A[1], 2), p22 = row(A[2], 2);
+    const double c00 = row(A[3], 3), c01 = row(A[3], 4), c02 = row(A[3], 5);
+    const double c11 = row(A[4], 4), c12 = row(A[4], 5), c22 = row(A[5], 5);
+    const bool colr = r == 1;
+    const float eig = sym3_max_eig((float)(colr ? c00 : p00), (float)(colr ? c01 : p01), (float)(colr ? c02 : p02),
+                                   (float)(colr ? c11 : p11), (float)(colr ? c12 : p12), (float)(colr ? c22 : p22));
+    const float lpp = (float)__shfl_sync(F, eig, gb & 31), lcc = (float)__shfl_sync(F, eig, (gb + 1) & 31);
+    const float trw = ((float)p00 + (float)p11) + ((float)p22 + (float)c00) + ((float)c11 + (float)c22);
+    if (!gv) return;
+    // E-step record
+    const double sn = sqrt(nq);
+    double *rr = rec + (size_t)pos * VBGS_REC;
+    float *r32 = rec32 + (size_t)pos * VBGS_REC;
+    const float s2f = 1.2011224087864498f;   // sqrt(log2 e): FP32 record in log2 units
+    rr[r] = mr;
+    r32[r] = (float)mr;
+    double *ks = kls + (size_t)k * kKS;
+    ks[r] = mr;
+#pragma unroll
+    for (int sd = 0; sd < 6; sd++)
+        if (sd <= r) {
+            const int e = tri(r, r - sd);
+            const double v = sn * Lid[sd];
+            rr[6 + e] = v;
+            r32[6 + e] = (float)v * s2f;
+            ks[6 + e] = Lid[sd];
+        }
+    if (r == 0) {
+        if (tile_dirty) tile_dirty[pos >> 7] = 1;
+        rr[27] = c;
+        r32[27] = (float)(c * 1.4426950408889634);
+#pragma unroll
+        for (int i = 28; i < 32; i++) { rr[i] = 0.0; r32[i] = 0.f; }
+        if (P.want_bounds) {
+            const float num = 1.44269504f * (1.f - 1e-5f) * (float)nq;
+            r32[28] = num / (lpp * (1.f + 1e-4f));
+            r32[29] = num / (lcc * (1.f + 1e-4f));
+            r32[30] = num / trw;
+        }
+        // KL hand-off and the "record holds the prior" flag
+        pc[(size_t)k * kPC + 33] = stats_zero(dS, k) ? 1.0 : 0.0;
+        ks[27] = aq; ks[28] = bq; ks[29] = nq; ks[30] = ldq; ks[31] = psi_nu; ks[32] = psi_a;
+        ks[33] = 1.0;
+        ks[34] = st0 - Sk[0];
+    }
+    if (cq) {   // the next frame's prior (lnGamma terms from k_mstep_kl) and k
+        if (r == 0) { cq[0] = aq; cq[1] = bq; cq[2] = nq; cq[30] = ldq; cq[33] = 1.0; cq[34] = (double)k; }
+        cq[3 + r] = mr;
+#pragma unroll
+        for (int j = 0; j < 6; j++)
+            if (j >= r) cq[9 + upper_index(r, j) - 7] = A[j];
+    }
+}
+
+// pcq (nullable): slot e of the list receives the next frame's prior of
+// entry e's component (ks[35] = e tells k_mstep_kl where its lnGamma terms go).
+__global__ void __launch_bounds__(128) k_mstep_list(MstepParams P, const double *__restrict__ m0,
+                                                    const double *__restrict__ Spast, const double *__restrict__ dS,
+                                                    const int *__restrict__ kperm, const int *__restrict__ list,
+                                                    const int *__restrict__ count, double *__restrict__ rec,
+                                                    float *__restrict__ rec32, double *__restrict__ pc,
+                                                    double *__restrict__ kls, int *__restrict__ flags,
+                                                    int *__restrict__ tile_dirty, double *__restrict__ pcq)
+{
+    pdl_wait();
+    const int n = *count;
+    if (n <= kListWarpMax) {
+        const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+        if (gw * 5 >= n) return;   // warp-uniform
+        const int lane = threadIdx.x & 31, g = lane / 6, r = lane - 6 * (lane / 6);
+        const int rr = g < 5 ? r : 0;
+        double w0r[6];   // W0^-1 at (min(rr, j), max(rr, j)), selected without indexing the parameter array
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            const int idx = rr <= j ? rr * 6 + j : j * 6 + rr;
+            double w = 0.0;
+#pragma unroll
+            for (int q = 0; q < 36; q++) w = sel64(q == idx, P.W0inv[q], w);
+            w0r[j] = w;
+        }
+        for (int e0 = gw * 5; e0 < n; e0 += nw * 5) {
+            const int e = e0 + g;
+            const bool gv = g < 5 && e < n;
+            const int pos = list[gv ? e : e0];
+            const int k = kperm ? kperm[pos] : pos;
+            if (gv && r == 0) kls[(size_t)k * kKS + 35] = (double)e;
+            mstep_group(P, w0r, rr, 6 * g, gv, m0, Spast, dS, pos, k, rec, rec32, pc, kls, flags, tile_dirty,
+                        pcq ? pcq + (size_t)e * kPC : nullptr);
+        }
+    } else {
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+            const int pos = list[e];
+            const int k = kperm ? kperm[pos] : pos;
+            kls[(size_t)k * kKS + 35] = (double)e;
+            mstep_thread(P, m0, Spast, dS, pos, k, stats_zero(dS, k), rec, rec32, pc, kls, flags, tile_dirty,
+                         pcq ? pcq + (size_t)e * kPC : nullptr);
+        }
+    }
+}
+
+// The next frame's prior from the slots of the previous frame's last
+// M-step: pc[k] = slot for each listed component (the others kept q = p).
+__global__ void k_apply_next(const int *__restrict__ count, const double *__restrict__ slots, double *__restrict__ pc)
+{
+    pdl_wait();
+    const int n = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * 34; i += gridDim.x * blockDim.x) {
+        const int e = i / 34, f = i - e * 34;
+        const int k = (int)slots[(size_t)e * kPC + 34];
+        pc[(size_t)k * kPC + f] = slots[(size_t)e * kPC + f];
     }
 }
 
@@ -394,9 +661,10 @@ __global__ void __launch_bounds__(128) k_mstep_kl(MstepParams P, bool frame_star
             // Per-component part of KL(Dir(alpha_q) || Dir(alpha_p)); the psi(sum)
             // and lnGamma(sum) terms are added after the cross-component sums.
             kl += -lgaq + cache[32] + (aq - ap) * psi_a;
-            if (pcq) {   // the lnGamma terms of the next frame's prior
-                pcq[(size_t)k * kPC + 31] = lg6q;
-                pcq[(size_t)k * kPC + 32] = lgaq;
+            if (pcq) {   // the lnGamma terms of the next frame's prior, in its slot
+                const size_t e = (size_t)ks[35];
+                pcq[e * kPC + 31] = lg6q;
+                pcq[e * kPC + 32] = lgaq;
             }
             dn = ks[34];
         }
@@ -478,7 +746,8 @@ size_t mstep_prior_cache_doubles(int K) { return (size_t)K * kPC; }
 
 size_t mstep_cache_doubles(int K)
 {
-    return (size_t)K * kPC + (size_t)((K + 127) / 128) * 4 + (size_t)K * kKS;   // cache, block sums, KL inputs
+    // cache, block sums, KL inputs, then the list of components to recompute (K + 1 ints)
+    return (size_t)K * kPC + (size_t)((K + 127) / 128) * 4 + (size_t)K * kKS + (size_t)(K + 2) / 2;
 }
 
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
@@ -491,12 +760,26 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
     const int nb = (K + 127) / 128;
     double *bpart = cache + (size_t)K * kPC;
     double *kls = bpart + (size_t)nb * 4;
-    pf->begin(VBGS_PROF_MSTEP, st);
-    // 64 threads a block: the per-component work is long and uneven (skipped
-    // components return at once), so smaller blocks spread it over more SMs
-    launch_pdl(k_mstep, (K + 63) / 64, 64, 0, st, P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags, tile_dirty,
-               cache_next);
-    pf->end(st);
+    int launches = 3;
+    if (!dS) {
+        pf->begin(VBGS_PROF_MSTEP, st);
+        // 64 threads a block: the per-component work is long, so smaller
+        // blocks spread it over more SMs
+        launch_pdl(k_mstep, (K + 63) / 64, 64, 0, st, P, m0, Spast, dS, kperm, rec, rec32, cache, kls, flags,
+                   tile_dirty, cache_next);
+        pf->end(st);
+    } else {
+        int *list = reinterpret_cast<int *>(kls + (size_t)K * kKS), *count = list + K;
+        if (cudaMemsetAsync(count, 0, sizeof(int), st) != cudaSuccess) return -1;
+        pf->begin(VBGS_PROF_MSTEP, st);
+        launch_pdl(k_mstep_scan, (K + 127) / 128, 128, 0, st, K, dS, kperm, cache, kls, list, count);
+        pf->end(st);
+        pf->begin(VBGS_PROF_MSTEP, st);
+        launch_pdl(k_mstep_list, kListWarpMax / 5 / 4, 128, 0, st, P, m0, Spast, dS, kperm, list, count, rec, rec32,
+                   cache, kls, flags, tile_dirty, cache_next);
+        pf->end(st);
+        launches = 4;
+    }
     // KL terms and their sums beside the next E-step
     if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return -1;
     pf->begin(VBGS_PROF_MSTEP, side);
@@ -506,7 +789,7 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
     launch_pdl(k_mstep_finalize, 1, 1024, 0, side, bpart, nb, scal);
     pf->end(side);
     if (cudaEventRecord(ev_join, side) != cudaSuccess) return -1;
-    return cudaGetLastError() == cudaSuccess ? 3 : -1;
+    return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
 // Records to the positions of a new component order: dst[p] = src[kinv_old[kperm[p]]].
@@ -524,6 +807,16 @@ __global__ void k_move_records(const int *__restrict__ kperm, const int *__restr
     if (q < 8)
         reinterpret_cast<float4 *>(rec32_dst + (size_t)p * VBGS_REC)[q] =
             reinterpret_cast<const float4 *>(rec32 + (size_t)po * VBGS_REC)[q];
+}
+
+int launch_apply_next(int K, const double *slots, double *cache, cudaStream_t st, Prof *pf)
+{
+    const int nb = (K + 127) / 128;
+    const int *count = reinterpret_cast<const int *>(cache + (size_t)K * kPC + (size_t)nb * 4 + (size_t)K * kKS) + K;
+    pf->begin(VBGS_PROF_MSTEP, st);
+    launch_pdl(k_apply_next, 152 * 4, 256, 0, st, count, slots, cache);
+    pf->end(st);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_move_records(const int *kperm, const int *kinv_old, int K, const double *rec, const float *rec32,
