@@ -111,9 +111,9 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
  * each iteration, against the effective prior prior0 (+) S_past.  N may be 0.
  * Errors: VBGS_EINVAL (NULL ctx/points with N > 0, N < 0, n_iters < 1,
  * non-finite coordinates; the state is left unchanged: S_past and the
- * posterior.  Device-resident points are checked while the frame runs, so
- * after such an error the per-call results -- elbo_trace, vbgs_get_lse,
- * vbgs_get_frame_stats -- are undefined), VBGS_ENUMERIC, VBGS_ECUDA,
+ * posterior.  Without the learned proposal the points are checked while
+ * the frame runs, so after such an error the per-call results -- elbo_trace,
+ * vbgs_get_lse, vbgs_get_frame_stats -- are undefined), VBGS_ENUMERIC, VBGS_ECUDA,
  * VBGS_ENOMEM. */
 int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, double *elbo_trace);
 
@@ -214,7 +214,9 @@ int64_t vbgs_last_launch_count(const vbgs_ctx *ctx);
 /* Per-kernel device timing.  When enabled, the library records a CUDA event
  * pair around every kernel it launches on the context's stream and, at the
  * end of each call that synchronises, adds the elapsed times per kernel
- * class.  vbgs_profile_read copies VBGS_PROF_COUNT totals (milliseconds and
+ * class.  on: 0 off, 1 every class, otherwise a mask of the classes to time
+ * (VBGS_PROF_ONLY(c) | ...): each pair of events serialises its kernel with
+ * its neighbours, so timing one class perturbs the rest least.  vbgs_profile_read copies VBGS_PROF_COUNT totals (milliseconds and
  * launch counts) into caller arrays (either may be NULL) and optionally
  * resets them.  vbgs_profile_name(i) names class i. */
 enum {
@@ -227,6 +229,7 @@ enum {
     VBGS_PROF_PLAN = 6,    /* tensor-core work lists: tile bounds, skip lists, work items */
     VBGS_PROF_COUNT = 7
 };
+#define VBGS_PROF_ONLY(c) (1 << ((c) + 1))
 int vbgs_profile_enable(vbgs_ctx *ctx, int on);
 int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset);
 /* Work counters of the profiled calls since the last reset: pairs scored by

@@ -184,10 +184,11 @@ int ensure_elbo(vbgs_ctx *ctx, int n)
     return VBGS_OK;
 }
 
-// Stage N points (host or device) into d_X and validate them.  defer_check
-// (device points): the staging kernel sets the bad-point flag and the frame
-// runs on; the commit of S_past skips on that flag and check_flags reports
-// it, so the statistics stay unchanged without a synchronisation here.  Every
+// Stage N points (host or device) into d_X and validate them.  defer_check:
+// the points go to the device as they are, the staging kernel sets the
+// bad-point flag and the frame runs on; the commit of S_past skips on that
+// flag and check_flags reports it, so the statistics stay unchanged without
+// a synchronisation or a host pass over the points here.  Every
 // kernel of a frame is bounded whatever the values (indices come from counts
 // and lists, never from coordinates).
 int stage_points(vbgs_ctx *ctx, const double *points, int64_t N, bool defer_check = false)
@@ -205,6 +206,14 @@ int stage_points(vbgs_ctx *ctx, const double *points, int64_t N, bool defer_chec
         CU(cudaStreamSynchronize(ctx->stream));
         ctx->prof.collect();
         if (bad) return fail(ctx, VBGS_EINVAL, "non-finite point coordinate");
+    } else if (defer_check) {
+        // one contiguous copy into scratch (the Morton-sorted buffer, written
+        // later in the frame), then the staging kernel checks and pads
+        CU(cudaMemcpyAsync(ctx->d_Xs, points, sizeof(double) * 6 * (size_t)N, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+        int l = launch_stage_points(ctx->d_Xs, N, ctx->d_X, ctx->d_flags, ctx->stream, &ctx->prof);
+        if (l < 0) return fail(ctx, VBGS_ECUDA, "point staging launch failed");
+        ctx->launches += l;
     } else {
         for (int64_t i = 0; i < N * 6; i++)
             if (!std::isfinite(points[i]))
@@ -1318,8 +1327,8 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
 int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, double *elbo_trace)
 {
     int rc;
-    // device points are checked during the frame (the proposal's training
-    // must not see them, so it checks first)
+    // points are checked during the frame (the proposal's training must not
+    // see bad ones, so with the proposal they are checked first)
     if ((rc = update_prepare(ctx, points, N, n_iters, ctx && !ctx->prop.on))) return rc;
     if ((rc = update_enqueue(ctx, N, n_iters, true))) return rc;
     if (elbo_trace)
@@ -1452,6 +1461,7 @@ int vbgs_profile_enable(vbgs_ctx *ctx, int on)
         CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, 2 * sizeof(unsigned long long), ctx->stream));
     }
     ctx->prof.on = on != 0;
+    ctx->prof.mask = on == 1 ? ~0u : (unsigned)on >> 1;
     return VBGS_OK;
 }
 

@@ -79,6 +79,7 @@ enum FlagSlot {
 // begin()/end() around each kernel; collect() runs after a stream sync.
 struct Prof {
     bool on = false;
+    unsigned mask = ~0u;                // classes timed (bit c)
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
     std::vector<int> cat_of_pair;       // class of event pair i (events 2i, 2i+1)
@@ -88,7 +89,7 @@ struct Prof {
     int64_t pass1_pairs = 0;                   // pairs scored by the CUDA-core pass 1 (all of them)
     void begin(int cat, cudaStream_t st)
     {
-        if (!on || used + 2 > pool.size()) return;
+        if (!on || !((mask >> cat) & 1u) || used + 2 > pool.size()) return;
         cudaEventRecord(pool[used], st);
         cat_of_pair.push_back(cat);
     }

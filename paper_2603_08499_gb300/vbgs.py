@@ -225,7 +225,15 @@ def vbgs_last_launch_count(ctx) -> int:
     return int(lib().vbgs_last_launch_count(ctx))
 
 
-def vbgs_profile_enable(ctx, on: bool = True) -> None:
+def prof_only(*classes: int) -> int:
+    """vbgs_profile_enable's mask that times only the given classes."""
+    m = 0
+    for c in classes:
+        m |= 1 << (int(c) + 1)
+    return m
+
+
+def vbgs_profile_enable(ctx, on: bool | int = True) -> None:
     _check(lib().vbgs_profile_enable(ctx, int(on)), ctx)
 
 
@@ -385,7 +393,7 @@ class Model:
     def launches(self) -> int:
         return vbgs_last_launch_count(self.ctx)
 
-    def profile(self, on: bool = True) -> None:
+    def profile(self, on: bool | int = True) -> None:
         vbgs_profile_enable(self.ctx, on)
 
     def profile_read(self, reset: bool = False) -> dict:
