@@ -254,7 +254,7 @@ int run_mstep(vbgs_ctx *ctx, const double *dS, bool write_next = false)
     ctx->launches += l;
     if (is_tc(ctx)) {
         l = launch_coef_tiles(ctx->d_rec, ctx->d_rec32, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles,
-                              ctx->d_tc_hdr, ctx->d_tile_dirty, ctx->stream, &ctx->prof);
+                              ctx->d_tc_hdr, ctx->d_tile_dirty, ++ctx->coef_epoch, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "coefficient tile launch failed");
         ctx->launches += l;
     }
@@ -285,7 +285,7 @@ int frame_start_from_next(vbgs_ctx *ctx, bool moved, const int *kinv_old)
     CU(cudaMemsetAsync(ctx->d_scal + SC_KL_TOTAL, 0, sizeof(double), ctx->stream));
     if (is_tc(ctx)) {
         l = launch_coef_tiles(ctx->d_rec, ctx->d_rec32, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles,
-                              ctx->d_tc_hdr, ctx->d_tile_dirty, ctx->stream, &ctx->prof);
+                              ctx->d_tc_hdr, ctx->d_tile_dirty, ++ctx->coef_epoch, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "coefficient tile launch failed");
         ctx->launches += l;
     }
@@ -340,8 +340,10 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
         const int *item_start = nullptr;
         int l = launch_pass1_tc(B.X, ctx->d_Xhl, same_points, N, ctx->K, ctx->precision == VBGS_BF16X3,
                                 ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_rec32, ctx->d_part, ctx->part_cap, B.tmax,
-                                ctx->d_p1plan, ctx->d_p1ub, ctx->d_flags, ctx->num_sms, ctx->tune_p1, &item_start,
-                                ctx->stream, &ctx->prof);
+                                ctx->d_p1plan, ctx->d_p1ub, ctx->d_flags, ctx->num_sms, ctx->tune_p1,
+                                ctx->d_tile_dirty + (ctx->K + 127) / 128, ctx->plan_epoch, &item_start, ctx->stream,
+                                &ctx->prof);
+        ctx->plan_epoch = ctx->coef_epoch;
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ctx->launches += l;
         l = launch_lse_merge_tc(ctx->d_part, N, item_start, lse, ctx->d_lse2f, ctx->d_lse_part,
@@ -1271,7 +1273,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
         (rc = dalloc(ctx, &ctx->d_flags, (size_t)FL_COUNT)) || (rc = ensure_elbo(ctx, 64)) ||
         (rc = dalloc(ctx, &ctx->d_kperm, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_kinv, (size_t)K)) ||
         (rc = dalloc(ctx, &ctx->d_tc_tiles, tc_tile_bytes(K))) || (rc = dalloc(ctx, &ctx->d_tc_hdr, tc_hdr_floats(K))) ||
-        (rc = dalloc(ctx, &ctx->d_tile_dirty, (size_t)(K + 127) / 128)) ||
+        (rc = dalloc(ctx, &ctx->d_tile_dirty, 2 * (size_t)((K + 127) / 128))) ||
         (rc = dalloc(ctx, &ctx->d_pcache_next, mstep_prior_cache_doubles(K))) ||
         (rc = dalloc(ctx, &ctx->d_rec_alt, (size_t)K * VBGS_REC)) ||
         (rc = dalloc(ctx, &ctx->d_rec32_alt, (size_t)K * VBGS_REC)) || (rc = dalloc(ctx, &ctx->d_kinv_alt, (size_t)K))) {
@@ -1299,7 +1301,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     CU(cudaMemsetAsync(ctx->d_Spast, 0, sizeof(double) * KF, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_dS, 0, sizeof(double) * KF, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_pcache, 0, sizeof(double) * mstep_cache_doubles(K), ctx->stream));
-    CU(cudaMemsetAsync(ctx->d_tile_dirty, 0, sizeof(int) * ((K + 127) / 128), ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_tile_dirty, 0, 2 * sizeof(int) * ((K + 127) / 128), ctx->stream));
     CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_scal, 0, sizeof(double) * SC_COUNT, ctx->stream));
     {

@@ -263,17 +263,21 @@ __device__ __forceinline__ void split_store(dfl v, unsigned char *hi, unsigned c
 template <bool BF16>
 __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ rec, const float *__restrict__ rec32,
                                                     int K, unsigned char *__restrict__ tiles,
-                                                    float *__restrict__ hdr, int *__restrict__ dirty)
+                                                    float *__restrict__ hdr, int *__restrict__ dirty, int epoch)
 {
     pdl_wait();
     __shared__ float red[7][4];
     __shared__ float frame[12];   // origin o (6), inv_s (6)
     const int t = threadIdx.x, j = blockIdx.x, lane = t & 31, w = t >> 5;
-    // a tile whose records were not rewritten since its last build is current
+    // a tile whose records were not rewritten since its last build is current;
+    // dirty[ntiles + j]: the epoch of the tile's last build
     if (dirty) {
         if (dirty[j] == 0) return;
         __syncthreads();
-        if (t == 0) dirty[j] = 0;
+        if (t == 0) {
+            dirty[j] = 0;
+            dirty[gridDim.x + j] = epoch;
+        }
     }
     const int k = j * kCols + t;
     const bool valid = k < K;
@@ -754,10 +758,14 @@ __device__ __forceinline__ float p1_group_bound(const float *g, const float lo[6
     return g[12] - 0.5f * fmaxf(fmaxf(g[13] * dp, g[14] * dc), g[15] * (dp + dc));
 }
 
+// tile_epoch (nullable): bounds of tiles not rebuilt since epoch `since`
+// (the last plan for the same points) are current and kept.
 __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, int ptiles, int K, int ntiles,
-                                               const float *__restrict__ rec32, float *__restrict__ ub)
+                                               const float *__restrict__ rec32, float *__restrict__ ub,
+                                               const int *__restrict__ tile_epoch, int since)
 {
     pdl_wait();
+    if (tile_epoch && tile_epoch[blockIdx.x] <= since) return;
     __shared__ __align__(16) float sc[kCols][12];
     __shared__ float sg[kCols / 32][16];
     const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -835,10 +843,13 @@ __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, 
 // list of tiles with ub >= LB - 50 nats, in increasing order.  256 threads:
 // two per point, each over half of the seed tile's components.
 constexpr int kListThreads = 256;
+// lbc[P] = (LB, seed) of the last plan; with tile_epoch, reused when the
+// seed is the same tile and was not rebuilt since epoch `since`.
 __global__ void __launch_bounds__(kListThreads) k_p1_lists(const double *__restrict__ X, int64_t N, int K,
                                                            int ntiles, const float *__restrict__ rec32,
                                                            const float *__restrict__ ub, int *__restrict__ list,
-                                                           int *__restrict__ counts)
+                                                           int *__restrict__ counts, float2 *__restrict__ lbc,
+                                                           const int *__restrict__ tile_epoch, int since)
 {
     pdl_wait();
     constexpr int kW = kListThreads / 32;
@@ -870,44 +881,55 @@ __global__ void __launch_bounds__(kListThreads) k_p1_lists(const double *__restr
             if (red[q] > v || (red[q] == v && redi[q] < jx)) { v = red[q]; jx = redi[q]; }
         js = jx == 0x7fffffff ? 0 : jx;
     }
-    const int ks = js * kCols, ns = min(kCols, K - ks);
-    for (int i = t; i < ns * 28; i += kListThreads) {
-        const int mm = i / 28, f = i - mm * 28;
-        sr[i] = rec32[(size_t)(ks + mm) * VBGS_REC + f];
-    }
-    const int pt = t & (kRows - 1), half = t / kRows;
-    const int64_t n = (int64_t)P * kRows + pt;
-    const bool live = n < N;
-    float x[6];
+    const float2 prev = lbc[P];
+    const bool reuse = tile_epoch && (int)prev.y == js && tile_epoch[js] <= since;   // uniform
+    float LB;
+    if (reuse) {
+        LB = prev.x;
+        if (t == 0) base_sh = 0;
+        __syncthreads();
+    } else {
+        const int ks = js * kCols, ns = min(kCols, K - ks);
+        for (int i = t; i < ns * 28; i += kListThreads) {
+            const int mm = i / 28, f = i - mm * 28;
+            sr[i] = rec32[(size_t)(ks + mm) * VBGS_REC + f];
+        }
+        const int pt = t & (kRows - 1), half = t / kRows;
+        const int64_t n = (int64_t)P * kRows + pt;
+        const bool live = n < N;
+        float x[6];
 #pragma unroll
-    for (int i = 0; i < 6; i++) x[i] = (float)X[(live ? n : (int64_t)P * kRows) * VBGS_XS + i];
-    __syncthreads();
-    // (approximate ex2 / lg2: relative errors of a few 2^-22, far inside the
-    // 1 + 1e-5 |lse| margin below)
-    float mx = -INFINITY, sm = 0.f;
-    const int m_end = half ? ns : min(ns, kCols / 2);
-    for (int mm = half * (kCols / 2); mm < m_end; mm++) {
-        const float l = logit32_rec(sr + mm * 28, x);
-        if (l > mx) { sm = sm * ex2f(mx - l) + 1.f; mx = l; }
-        else sm += ex2f(l - mx);
-    }
-    if (half) { hm[pt] = mx; hs[pt] = sm; }
-    __syncthreads();
-    float lb = INFINITY;
-    if (!half) {
-        const float m1 = hm[pt], s1 = hs[pt];
-        if (m1 > mx) { sm = sm * ex2f(mx - m1) + s1; mx = m1; }
-        else if (m1 > -INFINITY) sm += s1 * ex2f(m1 - mx);
-        lb = mx + __log2f(sm);
-        lb = live ? lb - (1.f + 1e-5f * fabsf(lb)) : INFINITY;
-    }
+        for (int i = 0; i < 6; i++) x[i] = (float)X[(live ? n : (int64_t)P * kRows) * VBGS_XS + i];
+        __syncthreads();
+        // (approximate ex2 / lg2: relative errors of a few 2^-22, far inside the
+        // 1 + 1e-5 |lse| margin below)
+        float mx = -INFINITY, sm = 0.f;
+        const int m_end = half ? ns : min(ns, kCols / 2);
+        for (int mm = half * (kCols / 2); mm < m_end; mm++) {
+            const float l = logit32_rec(sr + mm * 28, x);
+            if (l > mx) { sm = sm * ex2f(mx - l) + 1.f; mx = l; }
+            else sm += ex2f(l - mx);
+        }
+        if (half) { hm[pt] = mx; hs[pt] = sm; }
+        __syncthreads();
+        float lb = INFINITY;
+        if (!half) {
+            const float m1 = hm[pt], s1 = hs[pt];
+            if (m1 > mx) { sm = sm * ex2f(mx - m1) + s1; mx = m1; }
+            else if (m1 > -INFINITY) sm += s1 * ex2f(m1 - mx);
+            lb = mx + __log2f(sm);
+            lb = live ? lb - (1.f + 1e-5f * fabsf(lb)) : INFINITY;
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lb = fminf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
-    if (lane == 0) red[w] = lb;
-    if (t == 0) base_sh = 0;
-    __syncthreads();
-    float LB = red[0];
-    for (int q = 1; q < kW; q++) LB = fminf(LB, red[q]);
+        for (int o = 16; o > 0; o >>= 1) lb = fminf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+        if (lane == 0) red[w] = lb;
+        if (t == 0) base_sh = 0;
+        __syncthreads();
+        LB = red[0];
+        for (int q = 1; q < kW; q++) LB = fminf(LB, red[q]);
+        if (t == 0) lbc[P] = make_float2(LB, (float)js);
+    }
+
     for (int j0 = 0; j0 < ntiles; j0 += kListThreads) {
         const int j = j0 + t;
         const bool keep = j < ntiles && u[j] >= LB - kSkipLog2;
@@ -1515,13 +1537,12 @@ size_t tc_hdr_floats(int K) { return (size_t)((K + kCols - 1) / kCols) * 32; }
 size_t tc_tmax_floats(int64_t N, int K) { return (size_t)((N + 31) / 32) * (size_t)((K + kCols - 1) / kCols); }
 
 int launch_coef_tiles(const double *rec, const float *rec32, int K, bool bf16, unsigned char *tiles, float *hdr,
-                      int *dirty,
-                      cudaStream_t st, Prof *pf)
+                      int *dirty, int epoch, cudaStream_t st, Prof *pf)
 {
     const int nt = (K + kCols - 1) / kCols;
     pf->begin(VBGS_PROF_MSTEP, st);
-    if (bf16) launch_pdl(k_coef_tiles<true>, nt, 128, 0, st, rec, rec32, K, tiles, hdr, dirty);
-    else      launch_pdl(k_coef_tiles<false>, nt, 128, 0, st, rec, rec32, K, tiles, hdr, dirty);
+    if (bf16) launch_pdl(k_coef_tiles<true>, nt, 128, 0, st, rec, rec32, K, tiles, hdr, dirty, epoch);
+    else      launch_pdl(k_coef_tiles<false>, nt, 128, 0, st, rec, rec32, K, tiles, hdr, dirty, epoch);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
@@ -1690,13 +1711,15 @@ size_t tc_p1plan_ints(int64_t N, int K)
 size_t tc_p1ub_floats(int64_t N, int K)
 {
     const size_t pt = (size_t)((N + kRows - 1) / kRows);
-    return pt * (size_t)((K + kCols - 1) / kCols) + 12 * pt;   // ub, then the point-tile boxes
+    // ub, the point-tile boxes, then (LB, seed) per tile at an even offset (float2)
+    return pt * (size_t)((K + kCols - 1) / kCols) + 14 * pt + 2;
 }
 
 int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, int K, bool bf16,
                     const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
                     size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
-                    int tiles_per_item, const int **item_start_out, cudaStream_t st, Prof *pf)
+                    int tiles_per_item, const int *tile_epoch, int since, const int **item_start_out,
+                    cudaStream_t st, Prof *pf)
 {
     float2 *part = reinterpret_cast<float2 *>(part_buf);
     int launches = 0;
@@ -1735,9 +1758,15 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
             launch_pdl(k_p1_boxes, ptiles, kRows, 0, st, X, N, boxes);
             launches++;
         }
+        // bounds of the tiles rebuilt since the last plan of these points
+        const int *te = same_points ? tile_epoch : nullptr;
+        // (float2: 8-byte aligned, so an even float offset)
+        const size_t lbc_off = ((size_t)ptiles * ntiles + 12 * (size_t)ptiles + 1) & ~(size_t)1;
+        float2 *lbc = reinterpret_cast<float2 *>(p1ub + lbc_off);
         launch_pdl(k_p1_ub, dim3(ntiles, (ptiles + kCols - 1) / kCols), kCols, 0, st, boxes, ptiles, K, ntiles,
-                   rec32, p1ub);
-        launch_pdl(k_p1_lists, ptiles, kListThreads, 0, st, X, N, K, ntiles, rec32, p1ub, list, counts);
+                   rec32, p1ub, te, since);
+        launch_pdl(k_p1_lists, ptiles, kListThreads, 0, st, X, N, K, ntiles, rec32, p1ub, list, counts, lbc, te,
+                   since);
     }
     launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ptiles, ntiles, tmin, target, item_start, item_tile,
                                    item_lo, item_hi, nitems);

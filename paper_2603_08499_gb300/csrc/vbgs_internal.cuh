@@ -202,8 +202,10 @@ int launch_pass2_fp32(const EstepBuffers &B, int tpb, int tkc, cudaStream_t st, 
 size_t tc_tile_bytes(int K);
 size_t tc_hdr_floats(int K);
 size_t tc_tmax_floats(int64_t N, int K);
+// dirty: ntiles flags (records rewritten since the tile's last build), then
+// the epoch of each tile's last build (set to `epoch` for the tiles built).
 int launch_coef_tiles(const double *rec, const float *rec32, int K, bool bf16, unsigned char *tiles, float *hdr,
-                      int *dirty, cudaStream_t st, Prof *pf);
+                      int *dirty, int epoch, cudaStream_t st, Prof *pf);
 size_t tc_plan_ints(int64_t N, int K);
 size_t tc_pass2_part_doubles(int K);
 size_t tc_p1plan_ints(int64_t N, int K);
@@ -219,12 +221,15 @@ int tc_set_attributes();
 // certified logit bound over the point tile is within 50 nats of a lower bound
 // of every point's lse; tmax of the other tiles is -inf.  same_points: X and N
 // are the previous call's (its FP32 split Xhl and point-tile boxes are
-// reused).  item_start_out: the
+// reused; tile_epoch / since: only the bounds of tiles built after epoch
+// `since` are recomputed, and a point tile's lse lower bound is kept while
+// its seed tile is unchanged).  item_start_out: the
 // item table the lse merge reads.
 int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, int K, bool bf16,
                     const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
                     size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
-                    int tiles_per_item, const int **item_start_out, cudaStream_t st, Prof *pf);
+                    int tiles_per_item, const int *tile_epoch, int since, const int **item_start_out,
+                    cudaStream_t st, Prof *pf);
 // lse from pass 1's FP32 item partials, minlse per 32 points, sum of lse.
 int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
                         double *lse_part, float *minlse, double *sum_out, cudaStream_t st, Prof *pf);
@@ -354,7 +359,9 @@ struct vbgs_ctx {
     int64_t xhl_cap = 0;
     size_t p1plan_cap = 0;
     float *d_tc_hdr = nullptr;
-    int *d_tile_dirty = nullptr;           // per 128-position tile: a record changed since its last coefficient build
+    int *d_tile_dirty = nullptr;           // per 128-position tile: a record changed since its last coefficient build; then the epoch of each tile's last build
+    int coef_epoch = 0;                    // coefficient-tile builds so far
+    int plan_epoch = 0;                    // coef_epoch at the last pass-1 plan
     int num_sms = 152;
     int tune_p1 = 0, tune_p2 = 0;          // work decomposition of the tensor-core passes (0 = automatic)
     int64_t alloc_gen = 0;                 // bumped by every (re)allocation: cached graphs check it
