@@ -353,7 +353,8 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
         if (want_stats) {
             l = launch_pass2_tc(ctx->d_Xhl, ctx->d_lse2f, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
                                 ctx->d_rec, B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
-                                ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->tune_p2, ctx->stream, &ctx->prof);
+                                ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->tune_p2,
+                                ctx->d_tile_dirty + 2 * ((ctx->K + 127) / 128), same_points, ctx->stream, &ctx->prof);
             if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
                                    cudaGetErrorString(cudaGetLastError()));
             ctx->launches += l;
@@ -1273,7 +1274,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
         (rc = dalloc(ctx, &ctx->d_flags, (size_t)FL_COUNT)) || (rc = ensure_elbo(ctx, 64)) ||
         (rc = dalloc(ctx, &ctx->d_kperm, (size_t)K)) || (rc = dalloc(ctx, &ctx->d_kinv, (size_t)K)) ||
         (rc = dalloc(ctx, &ctx->d_tc_tiles, tc_tile_bytes(K))) || (rc = dalloc(ctx, &ctx->d_tc_hdr, tc_hdr_floats(K))) ||
-        (rc = dalloc(ctx, &ctx->d_tile_dirty, 2 * (size_t)((K + 127) / 128))) ||
+        (rc = dalloc(ctx, &ctx->d_tile_dirty, 6 * (size_t)((K + 127) / 128))) ||
         (rc = dalloc(ctx, &ctx->d_pcache_next, mstep_prior_cache_doubles(K))) ||
         (rc = dalloc(ctx, &ctx->d_rec_alt, (size_t)K * VBGS_REC)) ||
         (rc = dalloc(ctx, &ctx->d_rec32_alt, (size_t)K * VBGS_REC)) || (rc = dalloc(ctx, &ctx->d_kinv_alt, (size_t)K))) {
@@ -1301,7 +1302,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     CU(cudaMemsetAsync(ctx->d_Spast, 0, sizeof(double) * KF, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_dS, 0, sizeof(double) * KF, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_pcache, 0, sizeof(double) * mstep_cache_doubles(K), ctx->stream));
-    CU(cudaMemsetAsync(ctx->d_tile_dirty, 0, 2 * sizeof(int) * ((K + 127) / 128), ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_tile_dirty, 0, 6 * sizeof(int) * ((K + 127) / 128), ctx->stream));
     CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_scal, 0, sizeof(double) * SC_COUNT, ctx->stream));
     {

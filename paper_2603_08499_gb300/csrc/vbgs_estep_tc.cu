@@ -1471,10 +1471,13 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
 // to raw moments: S1 = S1' + N m, S2 = S2' + m S1'^T + S1' m^T + N m m^T.
 // One CTA per (tile, 32 positions): warp w sums the items q = w, w + 4, ...
 // of the tile in order; the 4 warp sums are added in warp order.
+// nz (nullable): per block, whether its rows of dS were last written nonzero;
+// with skip_zero, a block without items whose rows are already zero writes
+// nothing (iterations after the first of a frame: same points and order).
 __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ part,
                                                       const int *__restrict__ item_start, int K,
                                                       const double *__restrict__ rec, const int *__restrict__ kperm,
-                                                      double *__restrict__ dS)
+                                                      double *__restrict__ dS, int *__restrict__ nz, bool skip_zero)
 {
     pdl_wait();
     __shared__ float sh[3][32][29];
@@ -1484,13 +1487,17 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
     const int q0 = item_start[j], q1 = item_start[j + 1];
     if (q0 == q1) {
         // no pair of this tile was evaluated: zero statistics
+        if (skip_zero && nz[blockIdx.x] == 0) return;
         if (w == 0 && p < K) {
             const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
+            double2 *o = reinterpret_cast<double2 *>(dS + dst * 28);   // 224-byte rows
 #pragma unroll
-            for (int f = 0; f < 28; f++) dS[dst * 28 + f] = 0.0;
+            for (int f = 0; f < 14; f++) o[f] = make_double2(0.0, 0.0);
         }
+        if (nz && threadIdx.x == 0) nz[blockIdx.x] = 0;
         return;
     }
+    if (nz && threadIdx.x == 0) nz[blockIdx.x] = 1;
     // the item partials are FP32 sums: add them in FP32 (a few terms), then
     // shift to raw moments in FP64
     float t[28];
@@ -1526,8 +1533,9 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
 #pragma unroll
         for (int b = a; b < 6; b++, u++) out[u] = d[u] + mk[a] * d[1 + b] + d[1 + a] * mk[b] + d[0] * mk[a] * mk[b];
     const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
+    double2 *o = reinterpret_cast<double2 *>(dS + dst * 28);
 #pragma unroll
-    for (int f = 0; f < 28; f++) dS[dst * 28 + f] = out[f];
+    for (int f = 0; f < 14; f++) o[f] = make_double2(out[2 * f], out[2 * f + 1]);
 }
 
 } // namespace
@@ -1561,7 +1569,7 @@ size_t tc_plan_ints(int64_t N, int K)
 int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
-                    cudaStream_t st, Prof *pf)
+                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf)
 {
     unsigned long long *pairs = pf->on ? pf->d_pairs : nullptr;
     const int ntiles = (K + kCols - 1) / kCols;
@@ -1596,7 +1604,7 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
                                                          pairs);
     pf->end(st);
     pf->begin(VBGS_PROF_REDUCE, st);
-    launch_pdl(k_reduce_items, ntiles * 4, 128, 0, st, fpart, item_start, K, rec, kperm, dS);
+    launch_pdl(k_reduce_items, ntiles * 4, 128, 0, st, fpart, item_start, K, rec, kperm, dS, nz, skip_zero && nz);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? (tmax ? 4 : 3) : -1;
 }

@@ -213,7 +213,7 @@ size_t tc_p1ub_floats(int64_t N, int K);
 int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
-                    cudaStream_t st, Prof *pf);
+                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf);
 int tc_pass1_auto_splits(int64_t N, int K, int num_sms);
 int tc_set_attributes();
 // Pass 1 on the tensor cores over balanced work items (point tile, list of
@@ -359,7 +359,10 @@ struct vbgs_ctx {
     int64_t xhl_cap = 0;
     size_t p1plan_cap = 0;
     float *d_tc_hdr = nullptr;
-    int *d_tile_dirty = nullptr;           // per 128-position tile: a record changed since its last coefficient build; then the epoch of each tile's last build
+    // per 128-position tile: a record changed since its last coefficient
+    // build; the epoch of the tile's last build; then per quarter tile
+    // whether its rows of dS were last written nonzero (tensor-core reduce)
+    int *d_tile_dirty = nullptr;
     int coef_epoch = 0;                    // coefficient-tile builds so far
     int plan_epoch = 0;                    // coef_epoch at the last pass-1 plan
     int num_sms = 152;
