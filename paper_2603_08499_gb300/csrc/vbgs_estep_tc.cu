@@ -200,6 +200,23 @@ __device__ __forceinline__ dfl df_from(double v)
     const float h = (float)v;
     return {h, (float)(v - (double)h)};
 }
+// The same split from the bit pattern, without FP64 instructions: h = v with
+// its significand cut to 24 bits (exact in FP32), l = the remaining 29 bits
+// rounded to FP32, for |v| in [2^-74, 2^127]; other values take df_from.
+__device__ __forceinline__ dfl df_from_bits(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex < 949 || ex > 1150) return df_from(v);
+    const unsigned sgn = (unsigned)(b >> 63) << 31;
+    const float h = __uint_as_float(sgn | ((unsigned)(ex - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    const float scale = __uint_as_float((unsigned)(ex - 1075 + 127) << 23);   // 2^(ex - 1075), a normal float
+    const float l = __uint2float_rn((unsigned)(b & 0x1fffffffu)) * scale;
+    return {h, sgn ? -l : l};
+}
+// sqrt(log2 e) and log2 e as double-float pairs
+constexpr float kS2h = 1.2011224031448364f, kS2l = 5.641613398665868e-09f;
+constexpr float kL2Eh = 1.4426950216293335f, kL2El = 1.925963033500011e-08f;
 
 // Byte offset of (row, feature) in a 128 x 32 K-major core-matrix operand.
 __host__ __device__ constexpr int opnd_off(int r, int f) { return (r >> 3) * 512 + (f >> 3) * 128 + (r & 7) * 16 + (f & 7) * 2; }
@@ -246,7 +263,8 @@ template <> struct H<true> {
 // part is 1/64 of FP32: P from the record's M as FP32 pairs; then coef1 and
 // coef0 from the matrix that the stored hi/lo pairs of C represent (Pr), so
 // the three parts expand one quadratic form centred exactly at mu and no
-// error grows with |mu|.  FP64 only to split the record's FP64 values.
+// error grows with |mu|.  The record's FP64 values are split into pairs from
+// their bit patterns, so the kernel issues no FP64 instruction.
 // Header (32 floats): o_hi[6], o_lo[6] (zero), inv_s[6], outscale (2^e_j), pad.
 // ---------------------------------------------------------------------------
 template <bool BF16>
@@ -285,14 +303,11 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
     const float *r32 = rec32 + rk;
     const double *r = rec + rk;
     float mf[6];
-    dfl M[21];   // sqrt(log2 e) * M: FP32 record value plus its FP64 remainder
+    dfl M[21];   // sqrt(log2 e) * M from the FP64 record, in double-float
 #pragma unroll
     for (int i = 0; i < 6; i++) mf[i] = r32[i];
 #pragma unroll
-    for (int q = 0; q < 21; q++) {
-        const float h = r32[6 + q];
-        M[q] = {h, (float)(r[6 + q] * 1.2011224087864498 - (double)h)};
-    }
+    for (int q = 0; q < 21; q++) M[q] = df_mul(df_from_bits(r[6 + q]), {kS2h, kS2l});
     const int nvalid = min(kCols, K - j * kCols);
     // frame origin: precision-weighted mean of the tile's means (weight
     // tr(nu W), proportional to |M|_F^2), so the tightest components sit
@@ -353,7 +368,7 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
     // mu = (m - o) * inv_s
     dfl mu[6];
 #pragma unroll
-    for (int a = 0; a < 6; a++) mu[a] = df_mulf(df_from(r[a] - (double)o[a]), inv[a]);
+    for (int a = 0; a < 6; a++) mu[a] = df_mulf(df_add(df_from_bits(r[a]), {-o[a], 0.f}), inv[a]);
     // tile-wide largest coefficient (estimate) -> power-of-two scale
     float mx = 0.f;
     if (valid) {
@@ -414,7 +429,7 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
         float rep;
         split_store<BF16>({bl.h * f, bl.l * f}, hi, lo, opnd_off(t, 1 + a), rep);
     }
-    const dfl c0 = df_add(df_from(r[27] * 1.4426950408889634), {-0.5f * quad.h, -0.5f * quad.l});
+    const dfl c0 = df_add(df_mul(df_from_bits(r[27]), {kL2Eh, kL2El}), {-0.5f * quad.h, -0.5f * quad.l});
     {
         const float f = valid ? sc : 0.f;
         float rep;
