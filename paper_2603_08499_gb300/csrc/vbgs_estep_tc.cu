@@ -864,9 +864,16 @@ __global__ void __launch_bounds__(kListThreads) k_p1_lists(const double *__restr
                                                            int ntiles, const float *__restrict__ rec32,
                                                            const float *__restrict__ ub, int *__restrict__ list,
                                                            int *__restrict__ counts, float2 *__restrict__ lbc,
-                                                           const int *__restrict__ tile_epoch, int since)
+                                                           const int *__restrict__ tile_epoch, int since,
+                                                           float *__restrict__ tmax)
 {
     pdl_wait();
+    // the pass-1 tile maxima of this point tile's four 32-row blocks start at
+    // -inf (pass 1 writes the evaluated tiles)
+    for (int i = threadIdx.x; i < 4 * ntiles; i += kListThreads) {
+        const int64_t rb = (int64_t)blockIdx.x * 4 + i / ntiles;
+        if (rb * 32 < N) tmax[rb * ntiles + i % ntiles] = -INFINITY;
+    }
     constexpr int kW = kListThreads / 32;
     __shared__ float sr[kCols * 28];
     __shared__ float red[kW];
@@ -966,12 +973,6 @@ __global__ void __launch_bounds__(kListThreads) k_p1_lists(const double *__restr
     if (t == 0) counts[P] = base_sh;
 }
 
-__global__ void k_fill_neg_inf(float *__restrict__ a, size_t n)
-{
-    pdl_wait();
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = -INFINITY;
-}
 
 // ---------------------------------------------------------------------------
 // Pass 2 on the tensor cores: the fused statistics contraction of Eq. 3.
@@ -1774,9 +1775,7 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
     const int target = tmax ? std::min(icap, std::max(ptiles + 1, 8 * num_sms)) : icap;
     pf->begin(VBGS_PROF_PLAN, st);
     if (tmax) {
-        const size_t nt = tc_tmax_floats(N, K);
         float *boxes = p1ub + (size_t)ptiles * ntiles;
-        launch_pdl(k_fill_neg_inf, (unsigned)((nt + 255) / 256), 256, 0, st, tmax, nt);
         if (!same_points) {   // the boxes of the previous E-step's points are current
             launch_pdl(k_p1_boxes, ptiles, kRows, 0, st, X, N, boxes);
             launches++;
@@ -1789,7 +1788,7 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
         launch_pdl(k_p1_ub, dim3(ntiles, (ptiles + kCols - 1) / kCols), kCols, 0, st, boxes, ptiles, K, ntiles,
                    rec32, p1ub, te, since);
         launch_pdl(k_p1_lists, ptiles, kListThreads, 0, st, X, N, K, ntiles, rec32, p1ub, list, counts, lbc, te,
-                   since);
+                   since, tmax);
     }
     launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ptiles, ntiles, tmin, target, item_start, item_tile,
                                    item_lo, item_hi, nitems);
@@ -1806,7 +1805,7 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
                                                             item_hi, nitems, part, tmax, flags, pairs1);
     pf->end(st);
     *item_start_out = item_start;
-    return cudaGetLastError() == cudaSuccess ? launches + (tmax ? 5 : 2) : -1;
+    return cudaGetLastError() == cudaSuccess ? launches + (tmax ? 4 : 2) : -1;
 }
 
 int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
@@ -1815,7 +1814,7 @@ int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start
     const int mb = (int)((N + 63) / 64);
     pf->begin(VBGS_PROF_MERGE, st);
     launch_pdl(k_merge_tc, mb, 64, 0, st, reinterpret_cast<const float2 *>(part_buf), item_start, N, lse, lse2f, lse_part,
-                                  minlse);
+               minlse);
     pf->end(st);
     return launch_block_sum(lse_part, mb, sum_out, st, pf) < 0 ? -1 : 2;
 }
