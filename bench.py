@@ -61,7 +61,7 @@ PEAK_EX2_G = SMS * 32 * SM_MHZ * 1e6 / 1e9
 # MMA work (3 hi/lo products: 192 flops per pair in pass 1, 384 in pass 2)
 # is reported beside it as the tensor-pipe view; the CUDA-core forms'
 # factored logit is 62 flops (+2 for the online sum) in pass 1 and 119 in
-# pass 2 (see DESIGN.md).
+# pass 2.
 ALG_FLOPS_PASS1 = 56
 ALG_FLOPS_PASS2 = 112
 FLOPS_PASS1 = 64

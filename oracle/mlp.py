@@ -10,7 +10,7 @@ weights, out x in).  Pinned in tests/test_oracle_pins.py by central finite
 differences, so the backward pass is checked against the forward pass, not
 against itself.  Also the k-means assignment rule (nearest centroid, ties
 to the lower index) and the top-4 rule (largest logits, ties to the lower
-index) used to judge the GPU's integer decisions.
+index) against which the GPU's integer decisions are checked.
 """
 from __future__ import annotations
 
