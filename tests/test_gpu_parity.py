@@ -71,6 +71,25 @@ def test_mixture_full_size_fp64(V, flags):
     assert np.all(np.diff(trace) >= -1e-9 * abs(trace[-1]))
 
 
+@pytest.mark.parametrize("form", ["fp64", "fp16x3"])
+def test_many_changed_components(V, form):
+    """8,000 components of which nearly all receive responsibility from
+    12,000 points: the M-step's list of changed components is longer than the
+    warp-per-five-components limit (6,080), so the per-thread list path runs;
+    two frames, so the second starts from the carried prior."""
+    X, pr = synth.c1_workload(seed=23, N=12_000, K=8_000)
+    m = V.Model(pr, form)
+    S = np.zeros((8_000, 28))
+    tol = TOL[form]
+    for t, Xt in enumerate((X[:6_000], X[6_000:])):
+        trace = m.update(Xt, 2)
+        e_ref, S, _, _ = O.cavi_frame(Xt, pr, S, 2)
+        assert O.relerr(trace, e_ref) <= tol["elbo"], (t, trace, e_ref)
+        for name, e in stat_errors(m.stats(), S).items():
+            assert e <= tol["stat"], (t, name, e)
+    m.close()
+
+
 @pytest.mark.parametrize("form", ["fp64", "fp32"])
 def test_skip_and_order_change_nothing_beyond_rounding(V, form):
     room = synth.Room(seed=8)
