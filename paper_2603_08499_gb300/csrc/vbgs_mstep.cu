@@ -196,11 +196,12 @@ __device__ void block_sums4(double v0, double v1, double v2, double v3, double *
 // nothing is recomputed and its KL term is exactly zero.
 //
 // The record (the next E-step's input) is this kernel's job; the KL terms of
-// the ELBO are k_mstep_kl's, which runs on a second stream beside the next
-// E-step: for every recomputed component this kernel leaves in kls[k] (kKS
-// doubles) m_q (6), L^-1 of W_q^-1 = L L^T (21, packed lower), alpha_q,
+// the ELBO are k_mstep_kl_list's, which runs on a second stream beside the
+// next E-step: for every recomputed component this kernel leaves in kls[k]
+// (kKS doubles) m_q (6), L^-1 of W_q^-1 = L L^T (21, packed lower), alpha_q,
 // beta_q, nu_q, ln|W_q^-1|, psi_6(nu_q/2), psi(alpha_q), a flag (1:
-// recomputed, 0: q = p) and the frame count Delta N_k.
+// recomputed, 0: q = p) and the frame count Delta N_k; k_mstep_kl_list adds
+// the component's KL term as the last double.
 constexpr int kKS = 36;
 
 // all 28 frame statistics of component k exactly zero (either sign): an
@@ -320,7 +321,7 @@ __device__ __forceinline__ void mstep_thread(const MstepParams &P, const double 
             if (cq) {
                 // After the commit S_past + Delta S is bitwise the st above,
                 // so q is the next frame's effective prior: its cache entry
-                // (the lnGamma terms come from k_mstep_kl) and k.
+                // (the lnGamma terms come from k_mstep_kl_list) and k.
                 cq[34] = (double)k;
                 cq[0] = aq; cq[1] = bq; cq[2] = nq;
 #pragma unroll
@@ -542,7 +543,7 @@ __device__ __forceinline__ void mstep_group(const MstepParams &P, const double w
         ks[33] = 1.0;
         ks[34] = st0 - Sk[0];
     }
-    if (cq) {   // the next frame's prior (lnGamma terms from k_mstep_kl) and k
+    if (cq) {   // the next frame's prior (lnGamma terms from k_mstep_kl_list) and k
         if (r == 0) { cq[0] = aq; cq[1] = bq; cq[2] = nq; cq[30] = ldq; cq[33] = 1.0; cq[34] = (double)k; }
         cq[3 + r] = mr;
 #pragma unroll
@@ -552,7 +553,7 @@ __device__ __forceinline__ void mstep_group(const MstepParams &P, const double w
 }
 
 // pcq (nullable): slot e of the list receives the next frame's prior of
-// entry e's component (ks[35] = e tells k_mstep_kl where its lnGamma terms go).
+// entry e's component (k_mstep_kl_list adds its lnGamma terms).
 __global__ void __launch_bounds__(128) k_mstep_list(MstepParams P, const double *__restrict__ m0,
                                                     const double *__restrict__ Spast, const double *__restrict__ dS,
                                                     const int *__restrict__ kperm, const int *__restrict__ list,
@@ -582,7 +583,6 @@ __global__ void __launch_bounds__(128) k_mstep_list(MstepParams P, const double 
             const bool gv = g < 5 && e < n;
             const int pos = list[gv ? e : e0];
             const int k = kperm ? kperm[pos] : pos;
-            if (gv && r == 0) kls[(size_t)k * kKS + 35] = (double)e;
             mstep_group(P, w0r, rr, 6 * g, gv, m0, Spast, dS, pos, k, rec, rec32, pc, kls, flags, tile_dirty,
                         pcq ? pcq + (size_t)e * kPC : nullptr);
         }
@@ -590,7 +590,6 @@ __global__ void __launch_bounds__(128) k_mstep_list(MstepParams P, const double 
         for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
             const int pos = list[e];
             const int k = kperm ? kperm[pos] : pos;
-            kls[(size_t)k * kKS + 35] = (double)e;
             mstep_thread(P, m0, Spast, dS, pos, k, stats_zero(dS, k), rec, rec32, pc, kls, flags, tile_dirty,
                          pcq ? pcq + (size_t)e * kPC : nullptr);
         }
@@ -610,76 +609,137 @@ __global__ void k_apply_next(const int *__restrict__ count, const double *__rest
     }
 }
 
-// KL terms of the posterior that k_mstep just wrote (second stream).  Frame
-// start (dS == nullptr): the lnGamma terms of the effective prior's cache,
-// KL = 0.  Otherwise KL(NW_q || NW_p) + the per-component Dirichlet part from
-// kls and the cache.  Block sums of (KL, alpha_q, alpha_p, Delta N) in
+// Frame start (second stream): the lnGamma terms of the effective prior's
+// cache; q = p, so KL = 0.  Block sums of (0, alpha_p, alpha_p, 0) in
 // position order.
-__global__ void __launch_bounds__(128) k_mstep_kl(MstepParams P, bool frame_start, const int *__restrict__ kperm,
-                                                  double *__restrict__ pc, const double *__restrict__ kls,
-                                                  double *__restrict__ bpart, double *__restrict__ pcq)
+__global__ void __launch_bounds__(128) k_mstep_kl_prior(int K, const int *__restrict__ kperm, double *__restrict__ pc,
+                                                        double *__restrict__ bpart)
 {
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    double a = 0.0;
+    if (pos < K) {
+        double *cache = pc + (size_t)(kperm ? kperm[pos] : pos) * kPC;
+        a = cache[0];
+        cache[31] = mv_lgamma6(0.5 * cache[2]);
+        cache[32] = lgamma(a);
+    }
+    block_sums4(0.0, a, a, 0.0, bpart);
+}
+
+constexpr int kKlBlocks = 304;   // 1,216 warps: a list of up to 4,864 components in one pass
+
+// KL(NW_q || NW_p) plus the per-component part of KL(Dir(alpha_q) ||
+// Dir(alpha_p)) of every listed component (second stream, beside the next
+// E-step), from kls and the cache; the psi(sum) and lnGamma(sum) terms of the
+// Dirichlet part are added after the cross-component sums.  Eight lanes to a
+// component, four components to a warp: lanes r = 0..5 take row r of
+// |L^-1 (m_q - m_p)|^2 and of tr(W_p^-1 W_q); lanes 0, 1 and 2 take one
+// lnGamma and one log each (the two half-steps of ln Gamma_6(nu_q / 2), then
+// ln Gamma(alpha_q) beside ln(beta_q / beta_p)).  An FP64 instruction costs a
+// warp the same whatever its active lanes, so spreading the terms over lanes
+// shortens the chain each warp issues.  Leaves the KL term in ks[35] and the
+// next frame's lnGamma terms in slot e of pcq (nullable).
+__global__ void __launch_bounds__(128) k_mstep_kl_list(const int *__restrict__ kperm, const int *__restrict__ list,
+                                                       const int *__restrict__ count, const double *__restrict__ pc,
+                                                       double *__restrict__ kls, double *__restrict__ pcq)
+{
+    const int n = *count;
+    const unsigned F = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = lane >> 3, r = lane & 7, gb = lane & ~7;
+    const int rr = r < 6 ? r : 5;   // lanes 6, 7 repeat row 5 and are left out of the sums
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int e0 = gw * 4; e0 < n; e0 += nw * 4) {   // warp-uniform
+        const int e = e0 + g;
+        const bool gv = e < n;   // an empty group repeats entry e0 and writes nothing
+        const int pos = list[gv ? e : e0];
+        const double *cache = pc + (size_t)(kperm ? kperm[pos] : pos) * kPC;
+        double *ks = kls + (size_t)(kperm ? kperm[pos] : pos) * kKS;
+        const double *Li = ks + 6;   // L^-1, packed lower
+        double d[6];
+#pragma unroll
+        for (int j = 0; j < 6; j++) d[j] = ks[j] - cache[3 + j];
+        // row rr of L^-1 (m_q - m_p)
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < 6; j++)
+            if (j <= rr) t += Li[tri(rr, j)] * d[j];
+        // row rr of sum_ij (W_p^-1)_ij (W_q)_ij, W_q = L^-T L^-1:
+        // (W_q)_ij = sum_{l >= max(i, j)} (L^-1)_li (L^-1)_lj, W_p^-1 upper in the cache
+        double tr = 0.0;
+#pragma unroll
+        for (int j = 0; j < 6; j++)
+            if (j >= rr) {
+                double w = 0.0;
+#pragma unroll
+                for (int l = j; l < 6; l++) w += Li[tri(l, rr)] * Li[tri(l, j)];
+                tr += (rr == j ? 1.0 : 2.0) * cache[2 + upper_index(rr, j)] * w;
+            }
+        double maha = r < 6 ? t * t : 0.0;
+        tr = r < 6 ? tr : 0.0;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            maha += __shfl_xor_sync(F, maha, o);
+            tr += __shfl_xor_sync(F, tr, o);
+        }
+        const double aq = ks[27], bq = ks[28], nq = ks[29], ldq = ks[30], psi_nu = ks[31], psi_a = ks[32];
+        const double ap = cache[0], bp = cache[1], np = cache[2], ldp = cache[30];
+        const double x = 0.5 * nq - 0.5 * (r & 1);
+        const double y = r < 2 ? x : r == 2 ? aq : 2.0;
+        const double z = r < 2 ? (x - 1.0) * (x - 1.0) * (x - 2.0) : r == 2 ? bq / bp : 1.0;
+        const double lg = lgamma(y), lz = log(z);
+        const double lg0 = __shfl_sync(F, lg, gb), lz0 = __shfl_sync(F, lz, gb);
+        const double lg1 = __shfl_sync(F, lg, gb + 1), lz1 = __shfl_sync(F, lz, gb + 1);
+        const double lgaq = __shfl_sync(F, lg, gb + 2), lbq = __shfl_sync(F, lz, gb + 2);
+        double lg6q = 7.5 * kLnPi;   // ln Gamma_6(nu_q / 2), as mv_lgamma6 sums it
+        lg6q += 3.0 * lg0 - lz0;
+        lg6q += 3.0 * lg1 - lz1;
+        double kl = 0.5 * (6.0 * bp / bq - 6.0 + bp * nq * maha + 6.0 * lbq);
+        kl += 0.5 * (nq - np) * psi_nu - 3.0 * nq + 0.5 * nq * tr + 0.5 * np * (ldq - ldp) + cache[31] - lg6q;
+        kl += -lgaq + cache[32] + (aq - ap) * psi_a;
+        if (gv && r == 0 && ks[33] != 0.0) {
+            ks[35] = kl;
+            if (pcq) {
+                pcq[(size_t)e * kPC + 31] = lg6q;
+                pcq[(size_t)e * kPC + 32] = lgaq;
+            }
+        }
+    }
+}
+
+// Block sums of (KL, alpha_q, alpha_p, Delta N) in position order: the
+// listed components' terms from kls, alpha_q = alpha_p and no KL elsewhere.
+__global__ void __launch_bounds__(128) k_mstep_kl_sum(int K, const int *__restrict__ kperm,
+                                                      const double *__restrict__ pc, const double *__restrict__ kls,
+                                                      double *__restrict__ bpart)
+{
+    pdl_wait();
+    const int pos = blockIdx.x * blockDim.x + threadIdx.x;
     double kl = 0.0, aq = 0.0, ap = 0.0, dn = 0.0;
-    if (pos < P.K) {
+    if (pos < K) {
         const int k = kperm ? kperm[pos] : pos;
-        double *cache = pc + (size_t)k * kPC;
         const double *ks = kls + (size_t)k * kKS;
-        ap = cache[0];
+        ap = pc[(size_t)k * kPC];
         aq = ap;
-        if (frame_start) {
-            cache[31] = mv_lgamma6(0.5 * cache[2]);
-            cache[32] = lgamma(ap);
-        } else if (ks[33] != 0.0) {
+        if (ks[33] != 0.0) {
+            kl = ks[35];
             aq = ks[27];
-            const double bq = ks[28], nq = ks[29], ldq = ks[30], psi_nu = ks[31], psi_a = ks[32];
-            const double bp = cache[1], np = cache[2], ldp = cache[30];
-            double maha = 0.0;   // (m_q - m_p)^T W_q (m_q - m_p) = |L^-1 (m_q - m_p)|^2
-#pragma unroll
-            for (int i = 0; i < 6; i++) {
-                double t = 0.0;
-#pragma unroll
-                for (int j = 0; j <= i; j++) t += ks[6 + tri(i, j)] * (ks[j] - cache[3 + j]);
-                maha += t * t;
-            }
-            // tr(W_p^-1 W_q) = sum_ij (W_p^-1)_ij (W_q)_ij with W_q = Li^T Li,
-            // (W_q)_ij = sum_{l >= max(i, j)} Li_li Li_lj (W_p^-1 upper in the cache).
-            double tr = 0.0;
-            int u = 9;
-#pragma unroll
-            for (int i = 0; i < 6; i++)
-#pragma unroll
-                for (int j = i; j < 6; j++, u++) {
-                    double w = 0.0;
-#pragma unroll
-                    for (int l = j; l < 6; l++) w += ks[6 + tri(l, i)] * ks[6 + tri(l, j)];
-                    tr += (i == j ? 1.0 : 2.0) * cache[u] * w;
-                }
-            const double lg6q = mv_lgamma6(0.5 * nq), lgaq = lgamma(aq);
-            kl = 0.5 * (6.0 * bp / bq - 6.0 + bp * nq * maha + 6.0 * log(bq / bp));
-            kl += 0.5 * (nq - np) * psi_nu - 3.0 * nq + 0.5 * nq * tr + 0.5 * np * (ldq - ldp) + cache[31] - lg6q;
-            // Per-component part of KL(Dir(alpha_q) || Dir(alpha_p)); the psi(sum)
-            // and lnGamma(sum) terms are added after the cross-component sums.
-            kl += -lgaq + cache[32] + (aq - ap) * psi_a;
-            if (pcq) {   // the lnGamma terms of the next frame's prior, in its slot
-                const size_t e = (size_t)ks[35];
-                pcq[e * kPC + 31] = lg6q;
-                pcq[e * kPC + 32] = lgaq;
-            }
             dn = ks[34];
         }
     }
     block_sums4(kl, aq, ap, dn, bpart);
 }
 
-// One block: fixed-order sums of the per-block partials, then the Dirichlet
-// terms that need the totals.  scal[SC_PSI_AHAT] = psi(sum alpha_q);
+// One block of four warps: fixed-order sums of the per-block partials, then
+// the Dirichlet terms that need the totals, psi(sum alpha_q), lnGamma(sum
+// alpha_q) and lnGamma(sum alpha_p) each on its own warp (so on its own SM
+// sub-partition, side by side).  scal[SC_PSI_AHAT] = psi(sum alpha_q);
 // scal[SC_KL_TOTAL] = sum_k KL_NW,k + KL_Dir.
-__global__ void __launch_bounds__(1024) k_mstep_finalize(const double *__restrict__ bpart, int nblocks,
-                                                         double *__restrict__ scal)
+__global__ void __launch_bounds__(128) k_mstep_finalize(const double *__restrict__ bpart, int nblocks,
+                                                        double *__restrict__ scal)
 {
     pdl_wait();
-    __shared__ double sh[4][32];
+    __shared__ double sh[4][4];
+    __shared__ double tf[3];
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
         s0 += bpart[(size_t)b * 4]; s1 += bpart[(size_t)b * 4 + 1];
@@ -695,13 +755,20 @@ __global__ void __launch_bounds__(1024) k_mstep_finalize(const double *__restric
     }
     if (lane == 0) { sh[0][w] = s0; sh[1][w] = s1; sh[2][w] = s2; sh[3][w] = s3; }
     __syncthreads();
+    const double t1 = (sh[1][0] + sh[1][1]) + (sh[1][2] + sh[1][3]);
+    const double t2 = (sh[2][0] + sh[2][1]) + (sh[2][2] + sh[2][3]);
+    if (lane == 0) {   // warp-uniform branches
+        if (w == 0) tf[0] = dg_digamma(t1);
+        else if (w == 1) tf[1] = lgamma(t1);
+        else if (w == 2) tf[2] = lgamma(t2);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
-        const int nw = blockDim.x >> 5;
-        for (int i = 0; i < nw; i++) { t0 += sh[0][i]; t1 += sh[1][i]; t2 += sh[2][i]; t3 += sh[3][i]; }
-        const double psi = dg_digamma(t1);
+        const double t0 = (sh[0][0] + sh[0][1]) + (sh[0][2] + sh[0][3]);
+        const double t3 = (sh[3][0] + sh[3][1]) + (sh[3][2] + sh[3][3]);
+        const double psi = tf[0];
         scal[SC_PSI_AHAT] = psi;
-        scal[SC_KL_TOTAL] = t0 + lgamma(t1) - lgamma(t2) - psi * t3;
+        scal[SC_KL_TOTAL] = t0 + tf[1] - tf[2] - psi * t3;
     }
 }
 
@@ -782,11 +849,22 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
     }
     // KL terms and their sums beside the next E-step
     if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return -1;
+    if (!dS) {
+        pf->begin(VBGS_PROF_MSTEP, side);
+        k_mstep_kl_prior<<<nb, 128, 0, side>>>(K, kperm, cache, bpart);
+        pf->end(side);
+    } else {
+        const int *list = reinterpret_cast<const int *>(kls + (size_t)K * kKS), *count = list + K;
+        pf->begin(VBGS_PROF_MSTEP, side);
+        k_mstep_kl_list<<<kKlBlocks, 128, 0, side>>>(kperm, list, count, cache, kls, cache_next);
+        pf->end(side);
+        pf->begin(VBGS_PROF_MSTEP, side);
+        launch_pdl(k_mstep_kl_sum, nb, 128, 0, side, K, kperm, (const double *)cache, (const double *)kls, bpart);
+        pf->end(side);
+        launches++;
+    }
     pf->begin(VBGS_PROF_MSTEP, side);
-    k_mstep_kl<<<nb, 128, 0, side>>>(P, dS == nullptr, kperm, cache, kls, bpart, cache_next);
-    pf->end(side);
-    pf->begin(VBGS_PROF_MSTEP, side);
-    launch_pdl(k_mstep_finalize, 1, 1024, 0, side, bpart, nb, scal);
+    launch_pdl(k_mstep_finalize, 1, 128, 0, side, (const double *)bpart, nb, scal);
     pf->end(side);
     if (cudaEventRecord(ev_join, side) != cudaSuccess) return -1;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
