@@ -53,3 +53,21 @@ def test_no_plain_launch_of_pdl_kernels():
             plain = re.findall(r"\b" + name + r"(?:<[^<>]*>)?<<<", text)
             if fname in ("vbgs_estep_tc.cu", "vbgs_mstep.cu", "vbgs_sort.cu"):
                 assert not plain, (fname, name)
+
+
+def test_pass1_traffic_digest(tmp_path):
+    """The benchmark reports pass 1's DRAM traffic from an ncu capture only
+    while the kernel's source digest matches the captured one; the digest is
+    found (a renamed or moved kernel would silently turn the figure off) and
+    differs when the kernel's text changes."""
+    import bench
+    path = CSRC / "vbgs_estep_tc.cu"
+    d = bench.kernel_digest("k_pass1_tc", path)
+    assert d is not None and len(d) == 40
+    src = path.read_text()
+    body = _kernel_body(src, "k_pass1_tc")
+    edited = src.replace(body, body.replace("pdl_wait();", "pdl_wait(); ", 1), 1)
+    tmp = tmp_path / "edited.cu"
+    tmp.write_text(edited)
+    assert bench.kernel_digest("k_pass1_tc", tmp) != d
+    assert bench.pass1_traffic("bf16x3") is None
