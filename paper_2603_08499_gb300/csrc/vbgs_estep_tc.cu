@@ -202,13 +202,18 @@ __device__ __forceinline__ dfl df_from(double v)
 }
 // The same split from the bit pattern, without FP64 instructions: h = v with
 // its significand cut to 24 bits (exact in FP32), l = the remaining 29 bits
-// rounded to FP32, for |v| in [2^-74, 2^127]; other values take df_from.
+// rounded to FP32, for |v| in [2^-74, 2^127]; zeros and FP64 subnormals give
+// (+-0, +0): df_from's pair for a zero, and for a subnormal (which rounds to
+// zero in FP32) the same up to the sign of a zero; other values take
+// df_from.  Zeros are common: a component no data has reached keeps the
+// prior's diagonal precision, 15 of its 21 Cholesky entries exactly zero.
 __device__ __forceinline__ dfl df_from_bits(double v)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int ex = (int)((b >> 52) & 0x7ff);
-    if (ex < 949 || ex > 1150) return df_from(v);
     const unsigned sgn = (unsigned)(b >> 63) << 31;
+    if (ex == 0) return {__uint_as_float(sgn), 0.f};
+    if (ex < 949 || ex > 1150) return df_from(v);
     const float h = __uint_as_float(sgn | ((unsigned)(ex - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
     const float scale = __uint_as_float((unsigned)(ex - 1075 + 127) << 23);   // 2^(ex - 1075), a normal float
     const float l = __uint2float_rn((unsigned)(b & 0x1fffffffu)) * scale;
