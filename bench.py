@@ -328,6 +328,40 @@ def roofline(form, prof, prof_pairs, probe=None, step_ms=None):
     return head, out
 
 
+def reassign_measure(V, prior, frames, form, warm, stream, flags=0, tuning=None, n=500, calls=5):
+    """reassign of Alg. 1 at the stream's shape: after `warm` frames, the
+    next frame's n points sampled toward low per-point ELBO (Gumbel-top-n,
+    tau = 1) and the n least-used components (random tie keys).  Host wall
+    time of the whole call (per-point ELBO pass, key and sort kernels, prior
+    update, read-back of the picks), median of `calls` calls; beside it the
+    same frame's vbgs_elbo, the E-step share of the call."""
+    import torch
+    m = V.Model(prior, form, cuda_stream=stream.cuda_stream, flags=flags)
+    if tuning:
+        V.vbgs_set_tuning(m.ctx, *tuning)
+    for t in range(warm):
+        m.update(frames[t], ITERS)
+    X = frames[warm]
+    rng = np.random.default_rng(2026)
+    g = rng.gumbel(size=X.shape[0])
+    v = rng.random(K_COMP)
+    t_re, t_el = [], []
+    for _ in range(calls + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.reassign(X, n, g, 1.0, v)
+        t_re.append(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.elbo(X)
+        t_el.append(time.perf_counter() - t0)
+    m.close()
+    return {"ms": statistics.median(t_re[1:]) * 1e3, "elbo_ms": statistics.median(t_el[1:]) * 1e3,
+            "n": n, "points": int(X.shape[0]), "K": K_COMP,
+            "what": "host wall time of vbgs_reassign (median of 5 calls after one untimed) and of vbgs_elbo on "
+                    "the same frame"}
+
+
 def run_batched(args):
     """64 uneven scenes (N log-uniform 5,000-160,000, K log-uniform
     1,000-50,000, mixture-points generator, 5 CAVI iterations each) updated
@@ -594,6 +628,10 @@ def run_ours(args):
                           tuning=tuning)
         breakdown = {k: v[0] / nb for k, v in (bd["prof"] or {}).items()}
         _, rl_all = roofline(form, bd["prof"], bd["prof_pairs"], peaks, sum(bd["times"]) * 1e3)
+        try:
+            extra["reassign"] = reassign_measure(V, prior, dev, form, args.warmup, stream, args.flags, tuning)
+        except Exception as exc:   # reported, never fatal to the headline line
+            extra["reassign"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         n_pts = sum(X.shape[0] for X in timed_frames)
         rl, _ = roofline(form, res["prof"], res["prof_pairs"], peaks, dev_time * 1e3)

@@ -190,6 +190,33 @@ int vbgs_proposal_bounds(vbgs_ctx *ctx, const double *points, int64_t N, float *
  * per-point terms lse_n, the per-point ELBO that `reassign` ranks on. */
 int vbgs_elbo(vbgs_ctx *ctx, const double *points, int64_t N, double *elbo_out, double *lse_out);
 
+/* reassign (Alg. 1, the step before fit in every frame; Sec. 2.1.2): the
+ * per-point ELBO term lse_n of the frame's N points (host or device, N x 6)
+ * under the current posterior prior0 (+) S_past, n points sampled toward low
+ * ELBO, the n least-used components, and the prior means m0 (position and
+ * colour) of those components set to the sampled points.  Nothing else of
+ * the prior and nothing of S_past changes; the next vbgs_update starts from
+ * the new prior.
+ *   Points: the n largest keys g_n - lse_n / tau, ties to the lower index.
+ *     gumbel (host, N finite doubles) holds standard Gumbel variates the
+ *     caller draws (-ln(-ln u), u uniform on (0, 1)); the n largest keys are
+ *     then a sample without replacement with probability proportional to
+ *     exp(-lse_n / tau) (Gumbel-top-k).  tau > 0, natural log units.
+ *   Components: ascending count N_k of S_past; ties by comp_key (host, K
+ *     finite doubles, ascending; NULL: none), then by the lower index.
+ *     Components no data has reached (N_k = 0) all tie, so a random
+ *     comp_key picks among them at random.
+ *   The i-th sampled point (by key rank) becomes the mean of the i-th picked
+ *   component.  picked_points (n int64) and picked_comps (n ints), host,
+ *   nullable, receive the choices in that order; vbgs_get_lse afterwards
+ *   returns the lse_n ranked on.
+ * n = 0 changes nothing.  Errors: VBGS_EINVAL (NULL points or gumbel with
+ * n > 0, n < 0, n > min(N, K), tau not > 0, a non-finite point, gumbel or
+ * comp_key value), VBGS_ENUMERIC, VBGS_ECUDA; on error the prior is
+ * unchanged. */
+int vbgs_reassign(vbgs_ctx *ctx, const double *points, int64_t N, int n, double tau, const double *gumbel,
+                  const double *comp_key, int64_t *picked_points, int *picked_comps);
+
 /* Posterior q = prior0 (+) S_past, host arrays allocated by the caller:
  * alpha, beta, nu (K), m (K x D), Winv (K x D x D, full symmetric W^-1).
  * Any pointer may be NULL to skip it. */

@@ -184,6 +184,29 @@ int ensure_elbo(vbgs_ctx *ctx, int n)
     return VBGS_OK;
 }
 
+// Buffers of vbgs_reassign for up to n points or components.
+int ensure_reassign(vbgs_ctx *ctx, int64_t n)
+{
+    ReassignBuffers &r = ctx->ra;
+    if (n <= r.cap) return VBGS_OK;
+    const int64_t cap = std::max<int64_t>(n, 1024);
+    int rc;
+    if ((rc = dalloc(ctx, &r.k_in, (size_t)cap)) || (rc = dalloc(ctx, &r.k_out, (size_t)cap)) ||
+        (rc = dalloc(ctx, &r.i_in, (size_t)cap)) || (rc = dalloc(ctx, &r.i_out, (size_t)cap)) ||
+        (rc = dalloc(ctx, &r.pts, (size_t)cap)) || (rc = dalloc(ctx, &r.comps, (size_t)cap)) ||
+        (rc = dalloc(ctx, &r.picks, (size_t)cap * 2)) || (rc = dalloc(ctx, &r.g, (size_t)cap)) ||
+        (rc = dalloc(ctx, &r.v, (size_t)cap)) || (rc = dalloc(ctx, &r.rows, (size_t)cap * 6)))
+        return rc;
+    unsigned char *t = nullptr;
+    const size_t tb = reassign_temp_bytes(cap);
+    if ((rc = dalloc(ctx, &t, tb))) return rc;
+    if (r.temp) cudaFree(r.temp);
+    r.temp = t;
+    r.temp_bytes = tb;
+    r.cap = cap;
+    return VBGS_OK;
+}
+
 // Stage N points (host or device) into d_X and validate them.  defer_check:
 // the points go to the device as they are, the staging kernel sets the
 // bad-point flag and the frame runs on; the commit of S_past skips on that
@@ -796,7 +819,9 @@ void free_all(vbgs_ctx *ctx)
                     ctx->d_kperm, ctx->d_kinv, ctx->d_pidx, ctx->d_Xs, ctx->d_tmax, ctx->d_minlse,
                     ctx->sb.keys_in, ctx->sb.keys_out, ctx->sb.idx_in, ctx->sb.temp, ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_plan,
                     ctx->d_p1plan, ctx->d_p1ub, ctx->d_tile_dirty, ctx->d_Xhl, ctx->d_lse2f,
-                    ctx->d_pcache_next, ctx->d_rec_alt, ctx->d_rec32_alt, ctx->d_kinv_alt};
+                    ctx->d_pcache_next, ctx->d_rec_alt, ctx->d_rec32_alt, ctx->d_kinv_alt,
+                    ctx->ra.k_in, ctx->ra.k_out, ctx->ra.i_in, ctx->ra.i_out, ctx->ra.pts, ctx->ra.comps,
+                    ctx->ra.picks, ctx->ra.g, ctx->ra.v, ctx->ra.rows, ctx->ra.temp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     {
@@ -1363,6 +1388,70 @@ int vbgs_elbo(vbgs_ctx *ctx, const double *points, int64_t N, double *elbo_out, 
     CU(cudaMemcpyAsync(elbo_out, ctx->d_elbo, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if ((rc = check_flags(ctx))) return rc;
     if (lse_out && N > 0) return vbgs_get_lse(ctx, lse_out, N);
+    return VBGS_OK;
+}
+
+int vbgs_reassign(vbgs_ctx *ctx, const double *points, int64_t N, int n, double tau, const double *gumbel,
+                  const double *comp_key, int64_t *picked_points, int *picked_comps)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    const int K = ctx->K;
+    if (n < 0 || N < 0 || n > N || n > K) return fail(ctx, VBGS_EINVAL, "need 0 <= n <= min(N, K)");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(ctx, VBGS_EINVAL, "tau must be finite and > 0");
+    if (n == 0) return VBGS_OK;
+    if (!points || !gumbel) return fail(ctx, VBGS_EINVAL, "points and gumbel are required");
+    for (int64_t i = 0; i < N; i++)
+        if (!std::isfinite(gumbel[i])) return fail(ctx, VBGS_EINVAL, "non-finite gumbel value at %lld", (long long)i);
+    if (comp_key)
+        for (int k = 0; k < K; k++)
+            if (!std::isfinite(comp_key[k])) return fail(ctx, VBGS_EINVAL, "non-finite comp_key value at %d", k);
+    ctx->launches = 0;
+    int rc;
+    // the per-point ELBO term under the current posterior, as vbgs_elbo
+    if ((rc = ensure_capacity(ctx, N)) || (rc = ensure_elbo(ctx, 1)) ||
+        (rc = ensure_reassign(ctx, std::max<int64_t>(N, K))))
+        return rc;
+    if ((rc = stage_points(ctx, points, N))) return rc;
+    CU(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * FL_COUNT, ctx->stream));
+    ctx->last_sorted = false;
+    if ((rc = run_mstep(ctx, nullptr))) return rc;
+    if ((rc = run_estep(ctx, N, false))) return rc;
+    if ((rc = join_side(ctx))) return rc;
+    if (launch_elbo(ctx->d_scal, N, ctx->d_elbo, ctx->stream, &ctx->prof) < 0)
+        return fail(ctx, VBGS_ECUDA, "ELBO launch failed");
+    ctx->launches += 1;
+    ctx->last_N = N;
+    if ((rc = check_flags(ctx))) return rc;   // before the prior changes
+    ReassignBuffers &rb = ctx->ra;
+    CU(cudaMemcpyAsync(rb.g, gumbel, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, ctx->stream));
+    if (comp_key) CU(cudaMemcpyAsync(rb.v, comp_key, sizeof(double) * (size_t)K, cudaMemcpyHostToDevice, ctx->stream));
+    ReassignArgs a;
+    a.lse = ctx->d_lse;   // the E-step above ran on d_X, in caller order
+    a.psi = ctx->d_scal + SC_PSI_ESTEP;
+    a.X = ctx->d_X;
+    a.S = ctx->d_Spast;
+    a.m0 = ctx->d_m0;
+    a.N = N;
+    a.K = K;
+    a.n = n;
+    a.inv_tau = 1.0 / tau;
+    a.have_v = comp_key != nullptr;
+    const int l = launch_reassign(a, rb, ctx->stream);
+    if (l < 0) return fail(ctx, VBGS_ECUDA, "reassign launch failed");
+    ctx->launches += l;
+    std::vector<int> picks((size_t)n * 2);
+    std::vector<double> rows((size_t)n * 6);
+    CU(cudaMemcpyAsync(picks.data(), rb.picks, sizeof(int) * picks.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(rows.data(), rb.rows, sizeof(double) * rows.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    // the host copy of the prior means follows the device's
+    for (int i = 0; i < n; i++)
+        for (int d = 0; d < 6; d++) ctx->m0_h[(size_t)picks[(size_t)n + i] * 6 + d] = rows[(size_t)i * 6 + d];
+    if (picked_points)
+        for (int i = 0; i < n; i++) picked_points[i] = picks[i];
+    if (picked_comps)
+        for (int i = 0; i < n; i++) picked_comps[i] = picks[(size_t)n + i];
+    ctx->next_prior_ready = false;   // the next frame starts from the new prior
     return VBGS_OK;
 }
 

@@ -134,6 +134,33 @@ struct SortBuffers {
     int64_t cap = 0;
 };
 
+// reassign (vbgs_reassign.cu): 64-bit sort keys and indices for up to cap
+// points or components, the caller's Gumbel variates (g) and component tie
+// keys (v), the sorted points and components, and the picks for the host
+// (rows: n x 6 point coordinates; picks: n points, then n components).
+struct ReassignBuffers {
+    unsigned long long *k_in = nullptr, *k_out = nullptr;
+    int *i_in = nullptr, *i_out = nullptr, *pts = nullptr, *comps = nullptr, *picks = nullptr;
+    double *g = nullptr, *v = nullptr, *rows = nullptr;
+    void *temp = nullptr;
+    size_t temp_bytes = 0;
+    int64_t cap = 0;
+};
+struct ReassignArgs {
+    const double *lse = nullptr;   // caller order, without -psi
+    const double *psi = nullptr;   // device scalar: psi(sum alpha) of the E-step
+    const double *X = nullptr;     // staged points, caller order, N x 8
+    const double *S = nullptr;     // S_past, K x 28
+    double *m0 = nullptr;          // prior means, K x 6 (updated)
+    int64_t N = 0;
+    int K = 0, n = 0;
+    double inv_tau = 1.0;
+    bool have_v = false;
+};
+size_t reassign_temp_bytes(int64_t n);
+// Returns the kernel launches issued, or -1.
+int launch_reassign(const ReassignArgs &a, ReassignBuffers &rb, cudaStream_t st);
+
 // Pass 2 skips a (64-point chunk, 128-component tile) when the tile's largest
 // logit minus the smallest lse of the chunk's 256-point block is below this
 // (natural units): every skipped r_nk < e^-50 < 2e-22.
@@ -346,6 +373,7 @@ struct vbgs_ctx {
     int *d_kinv_alt = nullptr;
     vbgs::BoxParams box{};
     vbgs::SortBuffers sb;
+    vbgs::ReassignBuffers ra;
     int *d_kperm = nullptr, *d_kinv = nullptr, *d_pidx = nullptr;
     double *d_Xs = nullptr;          // staged points in Morton order
     float *d_tmax = nullptr, *d_minlse = nullptr;

@@ -49,7 +49,7 @@ EXPORTS = [
     "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_pairs", "vbgs_profile_name", "vbgs_probe_peaks",
     "vbgs_estep_noalloc", "vbgs_update_batched", "vbgs_autotune", "vbgs_get_tuning", "vbgs_set_tuning",
     "vbgs_proposal_report", "vbgs_proposal_weights", "vbgs_proposal_grad", "vbgs_proposal_clusters",
-    "vbgs_proposal_bounds", "vbgs_last_error", "vbgs_destroy",
+    "vbgs_proposal_bounds", "vbgs_reassign", "vbgs_last_error", "vbgs_destroy",
 ]
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 PROF_COUNT = 7
@@ -84,6 +84,8 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
                               C.POINTER(vbgs_options)]
     lib.vbgs_update.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, _DP]
     lib.vbgs_elbo.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, _DP, _DP]
+    lib.vbgs_reassign.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double, _DP, _DP,
+                                  C.POINTER(C.c_int64), C.POINTER(C.c_int)]
     lib.vbgs_get_posterior.argtypes = [C.c_void_p, _DP, _DP, _DP, _DP, _DP]
     lib.vbgs_get_stats.argtypes = [C.c_void_p, _DP]
     lib.vbgs_set_stats.argtypes = [C.c_void_p, _DP]
@@ -188,6 +190,24 @@ def vbgs_elbo(ctx, points, want_lse: bool = False):
     _check(lib().vbgs_elbo(ctx, ptr, N, _dp(out), _dp(lse) if want_lse else None), ctx)
     del keep
     return (float(out[0]), lse[:N]) if want_lse else float(out[0])
+
+
+def vbgs_reassign(ctx, points, n: int, gumbel, tau: float = 1.0, comp_key=None):
+    """reassign (Alg. 1): returns (picked points, picked components), host
+    int arrays in rank order; the prior means of the components are now the
+    points'.  gumbel: N standard Gumbel variates; comp_key: K tie keys or None."""
+    ptr, N, keep = _points_ptr(points)
+    g = _host_f64(gumbel).ravel()
+    if g.size != N:
+        raise ValueError(f"gumbel needs {N} values, got {g.size}")
+    v = None if comp_key is None else _host_f64(comp_key).ravel()
+    pts = np.zeros(max(n, 1), dtype=np.int64)
+    comps = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().vbgs_reassign(ctx, ptr, N, int(n), float(tau), _dp(g), None if v is None else _dp(v),
+                               pts.ctypes.data_as(C.POINTER(C.c_int64)), comps.ctypes.data_as(C.POINTER(C.c_int))),
+           ctx)
+    del keep
+    return pts[:n], comps[:n]
 
 
 def vbgs_get_posterior(ctx, K: int) -> dict:
@@ -374,6 +394,11 @@ class Model:
 
     def elbo(self, points, want_lse: bool = False):
         return vbgs_elbo(self.ctx, points, want_lse)
+
+    def reassign(self, points, n: int, gumbel, tau: float = 1.0, comp_key=None):
+        if comp_key is not None and np.asarray(comp_key).size != self.K:
+            raise ValueError(f"comp_key needs {self.K} values")
+        return vbgs_reassign(self.ctx, points, n, gumbel, tau, comp_key)
 
     def posterior(self) -> dict:
         return vbgs_get_posterior(self.ctx, self.K)
