@@ -162,6 +162,37 @@ __device__ __forceinline__ float ex2f(float x)
     return y;
 }
 
+// Paired FP32 arithmetic of sm_100 and later (two lanes of a 64-bit register,
+// each rounded to nearest like the scalar instruction) and the three-input
+// maximum: fewer instructions per logit in the pass-1 reduction, with the
+// results of the scalar forms.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // Double-float arithmetic: a value as an unevaluated FP32 sum h + l (about
 // 48 significant bits), on the FP32 pipe.  Error-free transformations of
 // Knuth (two-sum), Dekker (fast two-sum) and the FMA product.
@@ -578,30 +609,38 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restr
                         if (c + 32 + i >= nvalid) v1[i] = 0xff800000u;
                     }
                 }
-                // max and sum over 64 values with 8 independent chains each
+                // max and sum over 64 values with 8 independent chains each;
+                // three-input maxima, and the scaled exponent arguments and
+                // the accumulators taken two at a time (each accumulator adds
+                // the same values in the same order as one at a time)
+                auto vf = [&](const uint32_t (&v)[32], int i) { return __uint_as_float(v[i]); };
                 float mx8[8];
 #pragma unroll
-                for (int q = 0; q < 8; q++) mx8[q] = fmaxf(__uint_as_float(v0[q]), __uint_as_float(v1[q]));
-#pragma unroll
-                for (int i = 8; i < 32; i++) mx8[i & 7] = fmaxf(mx8[i & 7], fmaxf(__uint_as_float(v0[i]), __uint_as_float(v1[i])));
-                float cm = fmaxf(fmaxf(fmaxf(mx8[0], mx8[1]), fmaxf(mx8[2], mx8[3])),
-                                 fmaxf(fmaxf(mx8[4], mx8[5]), fmaxf(mx8[6], mx8[7])));
+                for (int q = 0; q < 8; q++) {
+                    float m = fmax3(vf(v0, q), vf(v1, q), vf(v0, q + 8));
+                    m = fmax3(m, vf(v1, q + 8), vf(v0, q + 16));
+                    m = fmax3(m, vf(v1, q + 16), vf(v0, q + 24));
+                    mx8[q] = fmaxf(m, vf(v1, q + 24));
+                }
+                float cm = fmax3(fmax3(mx8[0], mx8[1], mx8[2]), fmax3(mx8[3], mx8[4], mx8[5]), fmaxf(mx8[6], mx8[7]));
                 cm *= scale;
                 tmx = fmaxf(tmx, cm);
                 if (cm > mrun) {
                     srun *= ex2f(mrun - cm);
                     mrun = cm;
                 }
-                const float negm = -mrun;
-                float acc[8];
+                const float2 sc2 = make_float2(scale, scale), nm2 = make_float2(-mrun, -mrun);
+                float2 acc[4];   // acc[q] = (chain 2q, chain 2q + 1)
 #pragma unroll
-                for (int q = 0; q < 8; q++) acc[q] = 0.f;
+                for (int q = 0; q < 4; q++) acc[q] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    acc[i & 7] += ex2f(fmaf(__uint_as_float(v0[i]), scale, negm));
-                    acc[(i + 4) & 7] += ex2f(fmaf(__uint_as_float(v1[i]), scale, negm));
+                for (int i = 0; i < 32; i += 2) {
+                    const float2 a = ffma2(make_float2(vf(v0, i), vf(v0, i + 1)), sc2, nm2);
+                    const float2 b = ffma2(make_float2(vf(v1, i), vf(v1, i + 1)), sc2, nm2);
+                    acc[(i & 7) >> 1] = fadd2(acc[(i & 7) >> 1], make_float2(ex2f(a.x), ex2f(a.y)));
+                    acc[((i + 4) & 7) >> 1] = fadd2(acc[((i + 4) & 7) >> 1], make_float2(ex2f(b.x), ex2f(b.y)));
                 }
-                srun += ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+                srun += ((acc[0].x + acc[0].y) + (acc[1].x + acc[1].y)) + ((acc[2].x + acc[2].y) + (acc[3].x + acc[3].y));
             }
             fence_before();
             mbar_arrive(&S.bar_dfree[s]);
