@@ -1397,6 +1397,7 @@ int vbgs_reassign(vbgs_ctx *ctx, const double *points, int64_t N, int n, double 
     if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
     const int K = ctx->K;
     if (n < 0 || N < 0 || n > N || n > K) return fail(ctx, VBGS_EINVAL, "need 0 <= n <= min(N, K)");
+    if (N > (int64_t)INT_MAX) return fail(ctx, VBGS_EINVAL, "reassign takes at most %d points", INT_MAX);
     if (!(tau > 0.0) || !std::isfinite(tau)) return fail(ctx, VBGS_EINVAL, "tau must be finite and > 0");
     if (n == 0) return VBGS_OK;
     if (!points || !gumbel) return fail(ctx, VBGS_EINVAL, "points and gumbel are required");

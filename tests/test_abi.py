@@ -84,6 +84,7 @@ def test_null_context_calls_fail_cleanly(L):
     assert lib.vbgs_update(None, None, 0, 1, None) == L.VBGS_EINVAL
     assert lib.vbgs_elbo(None, None, 0, None, None) == L.VBGS_EINVAL
     assert lib.vbgs_get_stats(None, None) == L.VBGS_EINVAL
+    assert lib.vbgs_reassign(None, None, 0, 0, 1.0, None, None, None, None) == L.VBGS_EINVAL
     lib.vbgs_destroy(None)
     assert lib.vbgs_profile_name(2) == b"pass2"
 
