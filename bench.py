@@ -93,6 +93,21 @@ def dist_info():
     return ws, rank, lrank
 
 
+def job_totals(time_s: float, units: float, ws: int, device: str = "cuda"):
+    """Whole-job figures of a replicas-only run of ws ranks: the slowest
+    rank's time (the job ends when it does) and the units all ranks
+    processed.  One process returns its own figures without a collective."""
+    if ws <= 1:
+        return float(time_s), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(time_s)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
 
@@ -560,16 +575,7 @@ def run_ours(args):
                        profile=V.prof_only(0), flags=args.flags, tuning=tuning)
     clk = clocks.stop()
     torch.cuda.synchronize()
-    dev_time = sum(res["times"])
-    if ws > 1:
-        t = torch.tensor([dev_time], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_time = float(t.item())
-        p = torch.tensor([res["pairs"]], device="cuda", dtype=torch.float64)
-        dist.all_reduce(p)
-        total_pairs = float(p.item())
-    else:
-        total_pairs = float(res["pairs"])
+    dev_time, total_pairs = job_totals(sum(res["times"]), res["pairs"], ws)
     value = total_pairs / dev_time
 
     # end to end through the same call with pinned host inputs: host wall
@@ -580,11 +586,7 @@ def run_ours(args):
     for _ in range(E2E_REPEATS):
         res_e2e = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, host_frames=host,
                                flags=args.flags, tuning=tuning)
-        e2e_time = sum(res_e2e["times"])
-        if ws > 1:
-            t = torch.tensor([e2e_time], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_time = float(t.item())
+        e2e_time, _ = job_totals(sum(res_e2e["times"]), 0.0, ws)
         e2e_runs.append(total_pairs / e2e_time)
     e2e_value = statistics.median(e2e_runs)
     timed_frames = frames[args.warmup:]
