@@ -76,6 +76,17 @@ typedef enum {
 #define VBGS_FLAG_NO_REORDER 1   /* process in the caller's order */
 #define VBGS_FLAG_NO_SKIP    2   /* evaluate every tile in pass 2 */
 #define VBGS_FLAG_PROPOSAL   4   /* learned candidate proposal (see vbgs_proposal_report) */
+#define VBGS_FLAG_SPLIT      8   /* the split model of Fig. 3 (below) */
+
+/* The split model (VBGS_FLAG_SPLIT; Sec. 2.1.2, Fig. 3): each component has
+ * a spatial Gaussian over (x, y, z) and a colour Gaussian over (r, g, b), each
+ * with its own Normal-Wishart prior and posterior, and one Dirichlet over the
+ * weights; log rho_nk is E[ln pi_k] plus the two blocks' expected
+ * log-likelihoods.  The blocks share alpha0, beta0, nu0 (nu0 > 2) and m0;
+ * their prior scales are the diagonal 3 x 3 blocks of W0.  The statistics keep
+ * the layout above (the position-colour cross moments are accumulated and not
+ * used), every W^-1 is block diagonal, and the ELBO's KL is the Dirichlet term
+ * plus both blocks' Normal-Wishart terms. */
 
 typedef struct {
     int precision;        /* vbgs_precision */
@@ -99,8 +110,8 @@ typedef struct vbgs_ctx vbgs_ctx;
 /* Create a context for K components of dimension D (must be 6) with the given
  * prior; opt may be NULL (FP64 form, default stream).  The accumulated
  * statistics S_past start at zero, so the model starts at the prior.
- * Errors: VBGS_EINVAL (bad sizes, NULL, nu0 <= D-1, beta0 <= 0, alpha0 <= 0,
- * W0 not SPD, non-finite m0), VBGS_ENOMEM, VBGS_ECUDA. */
+ * Errors: VBGS_EINVAL (bad sizes, NULL, nu0 <= D-1 (split model: nu0 <= 2),
+ * beta0 <= 0, alpha0 <= 0, W0 not SPD, non-finite m0), VBGS_ENOMEM, VBGS_ECUDA. */
 int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_options *opt);
 
 /* Process one frame X_t (Alg. 1 `fit`): n_iters CAVI iterations over the N

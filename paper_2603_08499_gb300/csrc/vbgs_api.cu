@@ -1229,9 +1229,12 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     if (!prior || !prior->m0 || !prior->W0) return fail(nullptr, VBGS_EINVAL, "prior, m0 or W0 is NULL");
     if (D != VBGS_D) return fail(nullptr, VBGS_EINVAL, "D must be 6 (got %d)", D);
     if (K <= 0) return fail(nullptr, VBGS_EINVAL, "K must be positive (got %d)", K);
-    if (!(prior->alpha0 > 0) || !(prior->beta0 > 0) || !(prior->nu0 > D - 1) ||
+    const bool split = opt && (opt->flags & VBGS_FLAG_SPLIT);
+    const int dof_min = split ? 2 : D - 1;   // nu0 > (dimension of a Wishart block) - 1
+    if (!(prior->alpha0 > 0) || !(prior->beta0 > 0) || !(prior->nu0 > dof_min) ||
         !std::isfinite(prior->alpha0) || !std::isfinite(prior->beta0) || !std::isfinite(prior->nu0))
-        return fail(nullptr, VBGS_EINVAL, "need alpha0 > 0, beta0 > 0, nu0 > D - 1");
+        return fail(nullptr, VBGS_EINVAL, split ? "need alpha0 > 0, beta0 > 0, nu0 > 2 (split model)"
+                                                : "need alpha0 > 0, beta0 > 0, nu0 > D - 1");
     int precision = opt ? opt->precision : VBGS_FP64;
     if (precision != VBGS_FP64 && precision != VBGS_FP32 && precision != VBGS_FP16X3 && precision != VBGS_BF16X3)
         return fail(nullptr, VBGS_EINVAL, "unknown precision %d", precision);
@@ -1244,6 +1247,14 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
             if (!std::isfinite(W0[i * 6 + j]) || W0[i * 6 + j] != W0[j * 6 + i])
                 return fail(nullptr, VBGS_EINVAL, "W0 must be finite and symmetric");
     if (!host_spd_inverse6(W0, W0inv)) return fail(nullptr, VBGS_EINVAL, "W0 is not positive definite");
+    if (split) {
+        // the blocks' prior scales are W0's diagonal blocks: invert them alone
+        // (the inverse of the block-diagonal matrix is block diagonal, zeros exact)
+        double Wb[36];
+        for (int i = 0; i < 6; i++)
+            for (int j = 0; j < 6; j++) Wb[i * 6 + j] = ((i < 3) == (j < 3)) ? W0[i * 6 + j] : 0.0;
+        if (!host_spd_inverse6(Wb, W0inv)) return fail(nullptr, VBGS_EINVAL, "W0's diagonal blocks are not SPD");
+    }
 
     ctx = new vbgs_ctx();
     ctx->K = K;
@@ -1288,6 +1299,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     ctx->mp.K = K;
     ctx->mp.want_bounds = 1;   // eigenvalue bounds: pass-1 tile lists and the proposal certificate
     for (int i = 0; i < 36; i++) ctx->mp.W0inv[i] = W0inv[i];
+    ctx->mp.split = split ? 1 : 0;
     ctx->m0_h.assign(prior->m0, prior->m0 + (size_t)K * 6);
 
     int rc = VBGS_OK;
@@ -1534,7 +1546,9 @@ int vbgs_get_posterior(vbgs_ctx *ctx, double *alpha, double *beta, double *m, do
         if (Winv)
             for (int i = 0; i < 6; i++)
                 for (int j = i; j < 6; j++) {
-                    double v = P.W0inv[i * 6 + j] + s[upper_index(i, j)] + P.beta0 * m0[i] * m0[j] - b * mk[i] * mk[j];
+                    double v = (P.split && i < 3 && j >= 3)
+                                   ? 0.0
+                                   : P.W0inv[i * 6 + j] + s[upper_index(i, j)] + P.beta0 * m0[i] * m0[j] - b * mk[i] * mk[j];
                     Winv[(size_t)k * 36 + i * 6 + j] = v;
                     Winv[(size_t)k * 36 + j * 6 + i] = v;
                 }

@@ -119,6 +119,7 @@ struct MstepParams {
     double W0inv[36];
     int K;
     int want_bounds;   // write the eigenvalue bounds of the proposal certificate (record floats 28-30)
+    int split;         // the split model: W^-1 block diagonal (position, colour), 3-D Wishart terms per block
 };
 
 // Box of the Morton codes (positions only).

@@ -69,6 +69,24 @@ __device__ double mv_lgamma6(double a)
     return s;
 }
 
+// The split model's two 3-D blocks with the same nu: 2 psi_3(a) and
+// 2 ln Gamma_3(a), psi_3(a) = psi(a) + psi(a - 1/2) + psi(a - 1) with
+// psi(a - 1) = psi(a) - 1/(a - 1), ln Gamma_3(a) = 1.5 ln pi + lnGamma(a) +
+// lnGamma(a - 1/2) + lnGamma(a - 1) with lnGamma(a - 1) = lnGamma(a) - ln(a - 1).
+__device__ double mv_digamma_split(double a)
+{
+    double s = 4.0 * dg_digamma(a) - 2.0 / (a - 1.0);
+    s += 2.0 * dg_digamma(a - 0.5);
+    return s;
+}
+__device__ double mv_lgamma_split(double a)
+{
+    double s = 3.0 * kLnPi;
+    s += 4.0 * lgamma(a) - 2.0 * log(a - 1.0);
+    s += 2.0 * lgamma(a - 0.5);
+    return s;
+}
+
 // Largest eigenvalue of a symmetric 3x3 matrix (a00, a01, a02, a11, a12,
 // a22) by the trigonometric solution of its characteristic cubic (Smith 1961):
 // q = tr/3, p = sqrt(tr((A - qI)^2)/6), r = det((A - qI)/p)/2,
@@ -105,7 +123,9 @@ __device__ __forceinline__ void nw_from_stats(const MstepParams &P, const double
     for (int i = 0; i < 6; i++)
 #pragma unroll
         for (int j = i; j < 6; j++)
-            A[tri(j, i)] = P.W0inv[i * 6 + j] + s[upper_index(i, j)] + P.beta0 * m0[i] * m0[j] - beta * m[i] * m[j];
+            A[tri(j, i)] = (P.split && i < 3 && j >= 3)   // split model: no position-colour block
+                               ? 0.0
+                               : P.W0inv[i * 6 + j] + s[upper_index(i, j)] + P.beta0 * m0[i] * m0[j] - beta * m[i] * m[j];
 }
 
 // One column of the in-register Cholesky A = L L^T (both packed lower
@@ -262,7 +282,7 @@ __device__ __forceinline__ void mstep_thread(const MstepParams &P, const double 
                 r[6 + tri(i, j)] = v;
                 r32[6 + tri(i, j)] = (float)v * s2;
             }
-        const double psi_nu = mv_digamma6(0.5 * nq);
+        const double psi_nu = P.split ? mv_digamma_split(0.5 * nq) : mv_digamma6(0.5 * nq);
         const double psi_a = dg_digamma(aq);
         const double elogdet = psi_nu + 6.0 * kLn2 - ldq;
         const double c = psi_a + 0.5 * elogdet - 3.0 * kLn2Pi - 3.0 / bq;
@@ -443,7 +463,7 @@ __device__ __forceinline__ void mstep_group(const MstepParams &P, const double w
         const bool lo = r <= j;   // (r, j) is an upper entry (i = r) or a lower one (i = j)
         const int u = lo ? upper_index(r, j) : upper_index(j, r);
         const double mi_ = lo ? mr : mj, mj_ = lo ? mj : mr, m0i_ = lo ? m0r : m0j, m0j_ = lo ? m0j : m0r;
-        A[j] = w0r[j] + (Sk[u] + dk[u]) + P.beta0 * m0i_ * m0j_ - bq * mi_ * mj_;
+        A[j] = (P.split && ((r < 3) != (j < 3))) ? 0.0 : w0r[j] + (Sk[u] + dk[u]) + P.beta0 * m0i_ * m0j_ - bq * mi_ * mj_;
     }
     // Cholesky by columns (chol6_col's operations and order); row r in Lr
     double Lr[6];
@@ -489,7 +509,10 @@ __device__ __forceinline__ void mstep_group(const MstepParams &P, const double w
     // psi(alpha_q) on row 0, the two halves of psi_6(nu_q / 2) on rows 1, 2
     const double xd = r == 1 ? 0.5 * nq - 0.5 * 0 : r == 2 ? 0.5 * nq - 0.5 * 1 : aq;
     const double yd = dg_digamma(xd);
-    const double term = r == 0 ? yd : 3.0 * yd - (3.0 * xd - 5.0) / ((xd - 1.0) * (xd - 2.0));
+    const double term = r == 0    ? yd
+                        : !P.split ? 3.0 * yd - (3.0 * xd - 5.0) / ((xd - 1.0) * (xd - 2.0))
+                        : r == 1   ? 4.0 * yd - 2.0 / (xd - 1.0)   // mv_digamma_split's two parts
+                                   : 2.0 * yd;
     const double psi_a = row(term, 0);
     double psi_nu = 0.0;
     psi_nu += row(term, 1);
@@ -612,15 +635,15 @@ __global__ void k_apply_next(const int *__restrict__ count, const double *__rest
 // Frame start (second stream): the lnGamma terms of the effective prior's
 // cache; q = p, so KL = 0.  Block sums of (0, alpha_p, alpha_p, 0) in
 // position order.
-__global__ void __launch_bounds__(128) k_mstep_kl_prior(int K, const int *__restrict__ kperm, double *__restrict__ pc,
-                                                        double *__restrict__ bpart)
+__global__ void __launch_bounds__(128) k_mstep_kl_prior(int K, bool split, const int *__restrict__ kperm,
+                                                        double *__restrict__ pc, double *__restrict__ bpart)
 {
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
     double a = 0.0;
     if (pos < K) {
         double *cache = pc + (size_t)(kperm ? kperm[pos] : pos) * kPC;
         a = cache[0];
-        cache[31] = mv_lgamma6(0.5 * cache[2]);
+        cache[31] = split ? mv_lgamma_split(0.5 * cache[2]) : mv_lgamma6(0.5 * cache[2]);
         cache[32] = lgamma(a);
     }
     block_sums4(0.0, a, a, 0.0, bpart);
@@ -638,8 +661,11 @@ constexpr int kKlBlocks = 304;   // 1,216 warps: a list of up to 4,864 component
 // ln Gamma(alpha_q) beside ln(beta_q / beta_p)).  An FP64 instruction costs a
 // warp the same whatever its active lanes, so spreading the terms over lanes
 // shortens the chain each warp issues.  Leaves the KL term in ks[35] and the
-// next frame's lnGamma terms in slot e of pcq (nullable).
-__global__ void __launch_bounds__(128) k_mstep_kl_list(const int *__restrict__ kperm, const int *__restrict__ list,
+// next frame's lnGamma terms in slot e of pcq (nullable).  Split model: the
+// two blocks share beta and nu and their matrices are block diagonal, so the
+// sum of their two Normal-Wishart KL terms is this form with 2 psi_3 and
+// 2 ln Gamma_3 in place of psi_6 and ln Gamma_6.
+__global__ void __launch_bounds__(128) k_mstep_kl_list(bool split, const int *__restrict__ kperm, const int *__restrict__ list,
                                                        const int *__restrict__ count, const double *__restrict__ pc,
                                                        double *__restrict__ kls, double *__restrict__ pcq)
 {
@@ -685,14 +711,22 @@ __global__ void __launch_bounds__(128) k_mstep_kl_list(const int *__restrict__ k
         const double ap = cache[0], bp = cache[1], np = cache[2], ldp = cache[30];
         const double x = 0.5 * nq - 0.5 * (r & 1);
         const double y = r < 2 ? x : r == 2 ? aq : 2.0;
-        const double z = r < 2 ? (x - 1.0) * (x - 1.0) * (x - 2.0) : r == 2 ? bq / bp : 1.0;
+        const double z = r < 2 ? (split ? (r == 0 ? x - 1.0 : 1.0) : (x - 1.0) * (x - 1.0) * (x - 2.0))
+                         : r == 2 ? bq / bp : 1.0;
         const double lg = lgamma(y), lz = log(z);
         const double lg0 = __shfl_sync(F, lg, gb), lz0 = __shfl_sync(F, lz, gb);
         const double lg1 = __shfl_sync(F, lg, gb + 1), lz1 = __shfl_sync(F, lz, gb + 1);
         const double lgaq = __shfl_sync(F, lg, gb + 2), lbq = __shfl_sync(F, lz, gb + 2);
-        double lg6q = 7.5 * kLnPi;   // ln Gamma_6(nu_q / 2), as mv_lgamma6 sums it
-        lg6q += 3.0 * lg0 - lz0;
-        lg6q += 3.0 * lg1 - lz1;
+        double lg6q;   // ln Gamma_6(nu_q / 2) as mv_lgamma6 sums it (split model: mv_lgamma_split)
+        if (split) {
+            lg6q = 3.0 * kLnPi;
+            lg6q += 4.0 * lg0 - 2.0 * lz0;
+            lg6q += 2.0 * lg1;
+        } else {
+            lg6q = 7.5 * kLnPi;
+            lg6q += 3.0 * lg0 - lz0;
+            lg6q += 3.0 * lg1 - lz1;
+        }
         double kl = 0.5 * (6.0 * bp / bq - 6.0 + bp * nq * maha + 6.0 * lbq);
         kl += 0.5 * (nq - np) * psi_nu - 3.0 * nq + 0.5 * nq * tr + 0.5 * np * (ldq - ldp) + cache[31] - lg6q;
         kl += -lgaq + cache[32] + (aq - ap) * psi_a;
@@ -851,12 +885,12 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
     if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return -1;
     if (!dS) {
         pf->begin(VBGS_PROF_MSTEP, side);
-        k_mstep_kl_prior<<<nb, 128, 0, side>>>(K, kperm, cache, bpart);
+        k_mstep_kl_prior<<<nb, 128, 0, side>>>(K, P.split != 0, kperm, cache, bpart);
         pf->end(side);
     } else {
         const int *list = reinterpret_cast<const int *>(kls + (size_t)K * kKS), *count = list + K;
         pf->begin(VBGS_PROF_MSTEP, side);
-        k_mstep_kl_list<<<kKlBlocks, 128, 0, side>>>(kperm, list, count, cache, kls, cache_next);
+        k_mstep_kl_list<<<kKlBlocks, 128, 0, side>>>(P.split != 0, kperm, list, count, cache, kls, cache_next);
         pf->end(side);
         pf->begin(VBGS_PROF_MSTEP, side);
         launch_pdl(k_mstep_kl_sum, nb, 128, 0, side, K, kperm, (const double *)cache, (const double *)kls, bpart);

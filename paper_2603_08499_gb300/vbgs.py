@@ -34,6 +34,7 @@ VBGS_FLAG_NO_REORDER = 1
 VBGS_FLAG_NO_SKIP = 2
 VBGS_FLAG_PLAIN = VBGS_FLAG_NO_REORDER | VBGS_FLAG_NO_SKIP
 VBGS_FLAG_PROPOSAL = 4
+VBGS_FLAG_SPLIT = 8
 PROP_CLUSTERS = 1024
 PROP_NPARAM = 128 * 6 + 128 + 128 * 128 + 128 + 1024 * 128 + 1024
 PROP_REPORT = ["cand_pairs", "fallback", "audit", "audit_max_missed", "audit_mean_missed", "frame_exact",
