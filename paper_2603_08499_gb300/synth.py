@@ -167,6 +167,27 @@ def room_frame(t: int, seed: int = 2, width: int = 200, height: int = 200, fov_d
     return np.ascontiguousarray(np.concatenate([pts, c], axis=1))
 
 
+def room_view(t: int, seed: int = 2, width: int = 200, height: int = 200, fov_deg: float = 60.0,
+              dmin: float = 0.5, dmax: float = 5.0, room: Room | None = None) -> dict:
+    """The pinhole view of pose t of the seeded room stream as an image (the
+    ground truth of a held-out view): camera centre o, camera-to-world
+    rotation Rwc, focal length f (pixels), the colour image (height x width x
+    3 in [0, 1], no noise; 0 where nothing lies within [dmin, dmax]) and its
+    hit mask.  Pixel (u, v) looks along Rwc ((u + 1/2 - width/2) / f,
+    (v + 1/2 - height/2) / f, 1), as in room_frame."""
+    room = room or Room(seed)
+    rng = np.random.default_rng([seed, t])
+    o, Rwc = camera_pose(rng)
+    f = (width / 2.0) / math.tan(math.radians(fov_deg) / 2.0)
+    u, v = np.meshgrid(np.arange(width) + 0.5, np.arange(height) + 0.5)
+    dirs_cam = np.stack([(u.ravel() - width / 2.0) / f, (v.ravel() - height / 2.0) / f, np.ones(u.size)], axis=1)
+    tt, col = room.cast(o, dirs_cam @ Rwc.T)
+    hit = np.isfinite(tt) & (tt >= dmin) & (tt <= dmax)
+    img = np.where(hit[:, None], col, 0.0).reshape(height, width, 3)
+    return {"o": o, "Rwc": Rwc, "f": f, "width": width, "height": height, "image": img,
+            "mask": hit.reshape(height, width)}
+
+
 def room_prior(K: int, seed: int = 2, **kw) -> dict:
     """Prior for the room stream: m0 uniform in the room box x [0, 1]^3."""
     return nw_prior(K, seed=seed + 1000, lo=tuple(ROOM_LO) + (0, 0, 0), hi=tuple(ROOM_HI) + (1, 1, 1), **kw)
