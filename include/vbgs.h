@@ -107,7 +107,8 @@ typedef struct {
 
 typedef struct vbgs_ctx vbgs_ctx;
 
-/* Create a context for K components of dimension D (must be 6) with the given
+/* Create a context (Sec. 2.1.2: the model of Fig. 3 under its conjugate prior;
+ * Alg. 1 starts from S = 0) for K components of dimension D (must be 6) with the given
  * prior; opt may be NULL (FP64 form, default stream).  The accumulated
  * statistics S_past start at zero, so the model starts at the prior.
  * Errors: VBGS_EINVAL (bad sizes, NULL, nu0 <= D-1 (split model: nu0 <= 2),
@@ -128,7 +129,8 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
  * VBGS_ENOMEM. */
 int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, double *elbo_trace);
 
-/* Many independent scenes at once (each its own context, uneven N and K):
+/* Alg. 1 `fit` for many independent scenes at once (running them in one launch
+ * has no paper counterpart; each scene is its own context, uneven N and K):
  * every scene runs the same frame update as vbgs_update(scenes[i],
  * points[i], N[i], n_iters), all of them as the branches of one CUDA graph
  * launched once, so small scenes fill the SMs that large ones leave idle.
@@ -140,7 +142,8 @@ int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, dou
 int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const double *const *points,
                         const int64_t *N, int n_iters, double *elbo_traces);
 
-/* Pick the work decomposition of the tensor-core passes (the least number
+/* No paper counterpart (a tuning aid of this library).  Pick the work
+ * decomposition of the tensor-core passes (the least number
  * of component tiles per pass-1 work item and of 64-point chunks per pass-2
  * work item; both passes cut their lists of tile pairs not ruled out by the
  * skip bounds into such items, one CTA each) for this context's K and frames
@@ -152,7 +155,7 @@ int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const double *con
  * reports the current choice (0 = automatic). */
 int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, const char *cache_path);
 int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_tiles, int *pass2_chunks);
-/* Set the decomposition directly (0 = automatic), e.g. a choice
+/* No paper counterpart.  Set the decomposition directly (0 = automatic), e.g. a choice
  * vbgs_autotune made on another context of the same sizes.  Errors:
  * VBGS_EINVAL (NULL ctx, negative values). */
 int vbgs_set_tuning(vbgs_ctx *ctx, int pass1_tiles, int pass2_chunks);
@@ -195,7 +198,8 @@ int vbgs_proposal_grad(vbgs_ctx *ctx, const float *inputs, const float *labels, 
 int vbgs_proposal_clusters(vbgs_ctx *ctx, float *centroids, int *cluster_of);
 int vbgs_proposal_bounds(vbgs_ctx *ctx, const double *points, int64_t N, float *ub, int *cluster_of);
 
-/* ELBO of the points X under the current posterior q = prior0 (+) S_past
+/* Alg. 1 `compute_elbo_delta` and the ELBO of Sec. 2.1.2's model: the ELBO
+ * of the points X under the current posterior q = prior0 (+) S_past
  * (the value elbo_trace[0] of a vbgs_update on X would take), without
  * changing the state.  lse_out (N doubles, host, may be NULL) receives the
  * per-point terms lse_n, the per-point ELBO that `reassign` ranks on. */
@@ -228,28 +232,32 @@ int vbgs_elbo(vbgs_ctx *ctx, const double *points, int64_t N, double *elbo_out, 
 int vbgs_reassign(vbgs_ctx *ctx, const double *points, int64_t N, int n, double tau, const double *gumbel,
                   const double *comp_key, int64_t *picked_points, int *picked_comps);
 
-/* Posterior q = prior0 (+) S_past, host arrays allocated by the caller:
+/* Alg. 1 `update_from_statistics`: the posterior q = prior0 (+) S_past, host
+ * arrays allocated by the caller:
  * alpha, beta, nu (K), m (K x D), Winv (K x D x D, full symmetric W^-1).
  * Any pointer may be NULL to skip it. */
 int vbgs_get_posterior(vbgs_ctx *ctx, double *alpha, double *beta, double *m,
                        double *Winv, double *nu);
 
-/* Accumulated statistics S_past (K x F, host). */
+/* Alg. 1's statistics buffer S: the accumulated statistics S_past (K x F, host). */
 int vbgs_get_stats(vbgs_ctx *ctx, double *S);
 
-/* Replace S_past (K x F, host), e.g. to resume a stream or to evaluate one
+/* Alg. 1's statistics buffer S: replace S_past (K x F, host), e.g. to resume a stream or to evaluate one
  * iteration from a given state.  Errors: VBGS_EINVAL on non-finite input. */
 int vbgs_set_stats(vbgs_ctx *ctx, const double *S);
 
-/* Statistics Delta S (K x F) of the last iteration of the last vbgs_update,
- * and its per-point lse_n (N_last doubles). */
+/* Eq. 3's statistics Delta S (K x F) of the last iteration of the last
+ * vbgs_update, and its per-point lse_n (N_last doubles) of Alg. 1's
+ * `compute_elbo_delta`. */
 int vbgs_get_frame_stats(vbgs_ctx *ctx, double *dS);
 int vbgs_get_lse(vbgs_ctx *ctx, double *lse, int64_t N);
 
-/* Kernel launches issued by the last vbgs_update / vbgs_elbo call. */
+/* No paper counterpart: kernel launches issued by the last vbgs_update /
+ * vbgs_elbo call. */
 int64_t vbgs_last_launch_count(const vbgs_ctx *ctx);
 
-/* Per-kernel device timing.  When enabled, the library records a CUDA event
+/* No paper counterpart (measurement).  Per-kernel device timing.  When
+ * enabled, the library records a CUDA event
  * pair around every kernel it launches on the context's stream and, at the
  * end of each call that synchronises, adds the elapsed times per kernel
  * class.  on: 0 off, 1 every class, otherwise a mask of the classes to time
@@ -268,9 +276,12 @@ enum {
     VBGS_PROF_COUNT = 7
 };
 #define VBGS_PROF_ONLY(c) (1 << ((c) + 1))
+/* No paper counterpart (measurement): switch the timing described above on
+ * or off, and read or reset its totals. */
 int vbgs_profile_enable(vbgs_ctx *ctx, int on);
 int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset);
-/* Work counters of the profiled calls since the last reset: pairs scored by
+/* No paper counterpart (measurement).  Work counters of the profiled calls
+ * since the last reset: pairs scored by
  * pass 1 (every pair in the CUDA-core forms; in the tensor-core forms the
  * pairs of the component tiles its certified bound did not rule out) and
  * pairs pass 2 evaluated (the ones its skip bound did not rule out).
@@ -278,7 +289,8 @@ int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset);
 int vbgs_profile_pairs(vbgs_ctx *ctx, int64_t *pass1_pairs, int64_t *pass2_pairs);
 const char *vbgs_profile_name(int i);
 
-/* Measure this GPU's arithmetic peaks with short probe kernels (a few
+/* No paper counterpart (measurement).  Measure this GPU's arithmetic peaks
+ * with short probe kernels (a few
  * milliseconds each, device `device`): out[0] FP64 FMA TFLOP/s, out[1] FP32
  * FMA TFLOP/s, out[2] MUFU ex2.approx.f32 results per second (1e9 units),
  * out[3] SM count.  Used for the ALU rooflines of the CUDA-core kernels. */
@@ -310,11 +322,11 @@ int vbgs_probe_peaks(int device, double *out);
 #define VBGS_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
 int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N, double *lse_out, double *dS_out);
 
-/* Message of the last failure on ctx (or of the last failure with no context
+/* No paper counterpart.  Message of the last failure on ctx (or of the last failure with no context
  * when ctx is NULL).  Never NULL. */
 const char *vbgs_last_error(const vbgs_ctx *ctx);
 
-/* Free every device and host resource of ctx (NULL is a no-op). */
+/* No paper counterpart.  Free every device and host resource of ctx (NULL is a no-op). */
 void vbgs_destroy(vbgs_ctx *ctx);
 
 #ifdef __cplusplus

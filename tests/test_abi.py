@@ -100,3 +100,22 @@ def test_valid_init_without_gpu_reports_cuda_error(L):
     with pytest.raises(L.VbgsError) as e:
         L.Model(_prior())
     assert e.value.code in (L.VBGS_ECUDA, L.VBGS_ENOMEM)
+
+
+def test_every_declaration_cites_its_passage_or_says_it_has_none():
+    """Each entry point of include/vbgs.h is documented by the comment block
+    above it (shared by consecutive declarations), which names the passage
+    of the paper that defines the operation (Alg., Eq., Sec., Fig.) or states
+    that it has no paper counterpart."""
+    import re
+    src = (Path(__file__).resolve().parent.parent / "include" / "vbgs.h").read_text()
+    decl = re.finditer(r"^(?:int|int64_t|void|const char \*)\s*\*?\s*(vbgs_\w+)\s*\(", src, re.M)
+    missing = []
+    for m in decl:
+        head = src[:m.start()]
+        end = head.rfind("*/")
+        comment = head[head.rfind("/*", 0, end):end]
+        if not re.search(r"Alg\. ?\d|Eq\. ?\d|Sec\. ?\d|Fig\. ?\d|[Nn]o paper counterpart|paper has no counterpart",
+                         comment):
+            missing.append(m.group(1))
+    assert not missing, missing
