@@ -119,3 +119,11 @@ def test_every_declaration_cites_its_passage_or_says_it_has_none():
                          comment):
             missing.append(m.group(1))
     assert not missing, missing
+
+
+def test_reassign_binding_checks_sizes_before_the_library(L):
+    """The binding rejects a Gumbel array whose length is not the point count
+    before it reaches the library (no context or GPU needed)."""
+    with pytest.raises(ValueError):
+        L.vbgs_reassign(None, np.zeros((5, 6)), 2, np.zeros(4))
+    assert L.VBGS_FLAG_SPLIT == 8
