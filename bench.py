@@ -40,6 +40,7 @@ K_COMP = 50_000
 ITERS = 3
 WORKLOAD = ("continual RGB-D room stream: 200x200 frames (<=40,000 lifted points, depth 0.5-5 m), "
             "K=50,000 NW/Dirichlet components, 3 CAVI iterations per frame, no replay")
+SPLIT_NOTE = "; split model (spatial and colour Normal-Wishart blocks per component, Fig. 3)"
 DTYPES = {"fp64": "f64", "fp32": "f32", "fp16x3": "f16x3 (fp32 acc)", "bf16x3": "bf16x3 (fp32 acc)"}
 
 # Peaks for the ALU rooflines, derived from unit counts and the maximum SM
@@ -593,9 +594,10 @@ def run_ours(args):
     h2d = int(np.mean([X.shape[0] * 6 * 8 for X in timed_frames]))
 
     extra = {}
-    if (form != "fp64" or args.flags != V.VBGS_FLAG_PLAIN) and rank == 0:
+    plain = V.VBGS_FLAG_PLAIN | (args.flags & V.VBGS_FLAG_SPLIT)   # the same model, every pair in FP64
+    if (form != "fp64" or args.flags != plain) and rank == 0:
         # the plain FP64 form: caller's order, every tile evaluated
-        ref = timed_stream(V, prior, dev, "fp64", args.warmup, args.steps, stream, flush, flags=V.VBGS_FLAG_PLAIN,
+        ref = timed_stream(V, prior, dev, "fp64", args.warmup, args.steps, stream, flush, flags=plain,
                            keep_last_state=True)
         fp64_value = ref["pairs"] / sum(ref["times"])
         errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(res["traces"], ref["traces"])]
@@ -644,7 +646,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_time * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[form], "data": "synthetic",
-            "config": {"workload": WORKLOAD, "K": K_COMP, "iters": ITERS, "form": form, "flags": args.flags,
+            "config": {"workload": WORKLOAD + (SPLIT_NOTE if args.flags & V.VBGS_FLAG_SPLIT else ""), "K": K_COMP,
+                       "iters": ITERS, "form": form, "flags": args.flags,
                        "tuning": list(tuning) if tuning else "automatic",
                        "mean_points_per_frame": n_pts / args.steps,
                        "l2": "flushed between steps (256 MB write outside the timed events)",
@@ -685,10 +688,14 @@ def main():
     ap.add_argument("--workload", choices=["room", "batched", "proposal"], default="room")
     ap.add_argument("--no-proposal", action="store_true", help="skip the proposal measurement of the default run")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--split", action="store_true",
+                    help="the split model of Fig. 3 (spatial and colour Normal-Wishart blocks; VBGS_FLAG_SPLIT)")
     ap.add_argument("--flags", type=int, default=0,
                     help="VBGS_FLAG_* bits: 1 = caller's order, 2 = no pass-2 tile skipping (3 = plain)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.split:
+        args.flags |= 8   # VBGS_FLAG_SPLIT
     if args.warmup < 3:
         log("warmup raised to 3")
         args.warmup = 3
