@@ -44,6 +44,8 @@ extern "C" {
 #define VBGS_ECUDA    -3   /* a CUDA runtime call failed */
 #define VBGS_ENUMERIC -4   /* a posterior W^-1 is not positive definite (component in message) */
 #define VBGS_ETIMEOUT -5   /* a bounded device-side wait gave up */
+#define VBGS_ECHECK   -6   /* a consistency check of the frame's results failed (options.checks) */
+#define VBGS_EIO      -7   /* a state file could not be written or read, or is not a valid state */
 
 /* Statistics per component, F = 1 + D + D(D+1)/2 = 28 doubles for D = 6:
  * [0] N_k, [1..6] S1 = sum r x, [7..27] S2 = sum r x x^T upper triangle,
@@ -88,11 +90,27 @@ typedef enum {
  * used), every W^-1 is block diagonal, and the ELBO's KL is the Dirichlet term
  * plus both blocks' Normal-Wishart terms. */
 
+/* Options of a context (vbgs_init, vbgs_load_state).  A zero-filled struct
+ * is the FP64 form on the legacy default stream with every default.
+ *   checks: 1 = after every frame, run the consistency checks of the frame's
+ *     results on the device (every count, moment and lse_n finite and the
+ *     counts non-negative; sum_k Delta N_k = N and sum_k Delta S1_k =
+ *     sum_n x_n within the form's tolerance: 1e-9 relative for FP64, 1e-3
+ *     otherwise); a failed check returns VBGS_ECHECK and, like every failed
+ *     frame, leaves S_past unchanged.  0 = off.
+ *   autotune_cache: tensor-core forms only; non-NULL = before the first frame
+ *     of each size class (rounded log2 N) pick the work decomposition with
+ *     vbgs_autotune on that frame's points, read from / appended to this
+ *     text file; NULL = the automatic decomposition.  The path is copied.
+ *   seed: seed of the library's own random draws (the proposal network's
+ *     initial weights and its audit sample); 0 = the library's default. */
 typedef struct {
     int precision;        /* vbgs_precision */
     int flags;            /* VBGS_FLAG_* */
     void *cuda_stream;    /* cudaStream_t to enqueue on; NULL = legacy default stream */
-    uint64_t reserved1;
+    int checks;
+    const char *autotune_cache;
+    uint64_t seed;
 } vbgs_options;
 
 /* Prior of every component (Sec. 2.1.2): Dirichlet(alpha0) weights and
@@ -198,6 +216,21 @@ int vbgs_proposal_grad(vbgs_ctx *ctx, const float *inputs, const float *labels, 
 int vbgs_proposal_clusters(vbgs_ctx *ctx, float *centroids, int *cluster_of);
 int vbgs_proposal_bounds(vbgs_ctx *ctx, const double *points, int64_t N, float *ub, int *cluster_of);
 
+/* No paper counterpart: the clustering step of the learned proposal on
+ * caller data.  K points (K x 6 floats, host), G = 1024 centroids (1024 x 6
+ * floats, host, in/out: the warm start, replaced by the result), lloyd_iters
+ * rounds of Lloyd's algorithm -- each point to its nearest centroid (squared
+ * Euclidean distance in FP32, ties to the lower centroid index), then each
+ * centroid to the mean of its members (an empty cluster keeps its centroid)
+ * -- and cluster_of (K ints, host, may be NULL) receives the nearest-centroid
+ * assignment under the returned centroids.  These are the kernels the
+ * proposal runs on the posterior means after every posterior update (with
+ * lloyd_iters = 2).  Temporary device memory is allocated and freed; the
+ * call synchronises.  Errors: VBGS_EINVAL (K < 0, NULL, lloyd_iters outside
+ * 0..64, non-finite values), VBGS_ENOMEM, VBGS_ECUDA (message from
+ * vbgs_last_error(NULL)). */
+int vbgs_kmeans(const float *points, int K, float *centroids, int lloyd_iters, int *cluster_of);
+
 /* Alg. 1 `compute_elbo_delta` and the ELBO of Sec. 2.1.2's model: the ELBO
  * of the points X under the current posterior q = prior0 (+) S_past
  * (the value elbo_trace[0] of a vbgs_update on X would take), without
@@ -245,6 +278,39 @@ int vbgs_get_stats(vbgs_ctx *ctx, double *S);
 /* Alg. 1's statistics buffer S: replace S_past (K x F, host), e.g. to resume a stream or to evaluate one
  * iteration from a given state.  Errors: VBGS_EINVAL on non-finite input. */
 int vbgs_set_stats(vbgs_ctx *ctx, const double *S);
+
+/* Alg. 1's continual state (Sec. 2.1.2: the model M and the statistics
+ * buffer S carried from frame to frame) to and from a file.  vbgs_save_state
+ * writes everything that determines the context's later results: the prior
+ * (alpha0, beta0, nu0, W0 and the current m0, including means `reassign`
+ * changed), S_past, the form and flags, the work decomposition, the
+ * posterior the last frame's M-step carried into the next frame (records,
+ * effective-prior cache, component order, coefficient tiles), and with the
+ * learned proposal its network (FP32 master weights, their BF16 copies, the
+ * Adam moments and step), the clusters' centroids and the frame counter of
+ * its audit sample.  vbgs_load_state creates a new context from such a file
+ * (*out, destroy with vbgs_destroy): continuing a stream through it gives
+ * the same results, bit for bit, as continuing the saved context.  The form,
+ * flags and seed are the saved ones; from opt (may be NULL) only
+ * cuda_stream, checks and autotune_cache are taken.  The file is a
+ * little-endian binary image with a 64-bit FNV-1a checksum, written to
+ * path.tmp and renamed over path; it holds ~1.3 kB per component (plus
+ * ~2.4 MB with the proposal).  Both calls synchronise the stream.
+ * Errors: VBGS_EINVAL (NULL), VBGS_EIO (cannot write or read the file, bad
+ * magic, version, size or checksum), VBGS_ENOMEM, VBGS_ECUDA. */
+int vbgs_save_state(vbgs_ctx *ctx, const char *path);
+int vbgs_load_state(vbgs_ctx **out, const char *path, const vbgs_options *opt);
+
+/* No paper counterpart: the consistency check that options.checks runs
+ * after every frame, on caller data (host arrays): dS (K x 28 statistics),
+ * points (N x 6), lse (N, may be NULL).  *ok = 1 when every statistic and
+ * lse_n is finite, every count non-negative, |sum_k dS_k0 - N| <= tol
+ * max(N, 1) and |sum_k dS_k(1..6) - sum_n x_n| <= tol max(|sum_n x_n|, 1)
+ * (Euclidean norms); else *ok = 0.  Temporary device memory is allocated
+ * and freed; the call synchronises.  Errors: VBGS_EINVAL, VBGS_ENOMEM,
+ * VBGS_ECUDA (message from vbgs_last_error(NULL)). */
+int vbgs_check_frame(const double *dS, int K, const double *points, int64_t N, const double *lse, double tol,
+                     int *ok);
 
 /* Eq. 3's statistics Delta S (K x F) of the last iteration of the last
  * vbgs_update, and its per-point lse_n (N_last doubles) of Alg. 1's
@@ -305,22 +371,39 @@ int vbgs_probe_peaks(int device, double *out);
  * per-point lse_n (N doubles) and the frame statistics
  * Delta S = sum_n r_nk [1, x_n, upper(x_n x_n^T)] (K x 28 doubles) into the
  * caller's DEVICE buffers lse_out and dS_out; points is an N x 6 DEVICE
- * array.  The context state is not changed (the same values vbgs_update
- * with one iteration would compute for its E-step).
+ * array (host pointers are rejected with VBGS_EINVAL before any launch).
+ * Arithmetic: an FP64 context runs the FP64 CUDA-core E-step (the values of
+ * vbgs_update's first E-step to FP64 rounding); FP32, FP16X3 and BF16X3
+ * contexts all run the FP32 CUDA-core E-step (factored quadratic form in FP32,
+ * FP64 cross-split sums; not the tensor-core kernels), within the FP32 form's
+ * tolerance of the FP64 result.  The posterior and the statistics of the
+ * context are not changed (its launch count and last error are).
  * Scratch memory comes from one static device array of
  * VBGS_NOALLOC_SCRATCH_BYTES held by every GPU that loads the library until
  * the process exits; the call fails with VBGS_EINVAL when
- * 8 N + max(2 N, 28 K) doubles (plus N / 256 block sums) exceed it, e.g.
+ * 32 + 8 N + max(2 N, 28 K) doubles exceed it, e.g.
  * N = 40,000 points with K = 50,000 components fit.  The array's device
- * address is looked up by the first call on each device (with that device
- * current), so make that first call before any stream capture.  All calls
- * share the array: calls that overlap on the GPU race; calls on one stream
- * are ordered.  The points are validated (one stream synchronisation);
- * results are enqueued on the context's stream without a final sync.
- * Errors: VBGS_EINVAL (NULL, N < 0, sizes beyond the array, non-finite
- * points), VBGS_ECUDA. */
+ * address is looked up by the first call in each CUDA context (with its
+ * device current), so make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race; calls on one
+ * stream are ordered.  Every call validates the points and synchronises the
+ * context's stream once to read the result of that check; the results are
+ * enqueued on the stream after it without a final sync.
+ * Errors: VBGS_EINVAL (NULL, N < 0, a host pointer, sizes beyond the array,
+ * non-finite points), VBGS_ECUDA. */
 #define VBGS_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
 int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N, double *lse_out, double *dS_out);
+
+/* No paper counterpart (failure handling).  Set the limit, in SM clock
+ * cycles, of the bounded waits between the warp roles of the tensor-core
+ * kernels on the current device (default ~2 s; cycles <= 0 restores it).
+ * Such a wait that gives up sets the frame's timeout flag: the kernels stop
+ * issuing work, wait (with the full limit) for the copies and MMAs already
+ * issued, release their tensor memory and return, and the call reports
+ * VBGS_ETIMEOUT with S_past unchanged.  A very short limit makes those
+ * waits give up as a stalled pipeline would, which is how the timeout path
+ * is tested.  Affects every context on the device.  Errors: VBGS_ECUDA. */
+int vbgs_set_wait_limit(long long cycles);
 
 /* No paper counterpart.  Message of the last failure on ctx (or of the last failure with no context
  * when ctx is NULL).  Never NULL. */

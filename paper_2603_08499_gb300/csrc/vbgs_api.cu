@@ -10,6 +10,7 @@
 // read-back of host outputs.
 #include "vbgs_internal.cuh"
 #include <math.h>
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 #include <algorithm>
@@ -463,7 +464,7 @@ int prop_alloc(vbgs_ctx *ctx)
     P.nparam = kNParam;
     // He-uniform initial weights from a fixed seed, zero biases
     std::vector<float> w(kNParam, 0.f);
-    uint64_t seed = 0x5eedF00Dull;
+    uint64_t seed = ctx->seed ? ctx->seed : 0x5eedF00Dull;
     auto fill = [&](size_t off, int fan_out, int fan_in) {
         const double a = std::sqrt(6.0 / fan_in);
         for (size_t i = 0; i < (size_t)fan_out * fan_in; i++)
@@ -626,7 +627,7 @@ int prop_estep(vbgs_ctx *ctx, int64_t N, bool last_iter)
     prop_bounds(X, N, P.cpar, P.ub, ctx->stream);
     ctx->launches += 1;
     CU(cudaMemsetAsync(P.counters, 0, sizeof(unsigned long long) * 8, ctx->stream));
-    const uint32_t seed = (uint32_t)(P.frame * 0x9E3779B1ull) ^ 0xA5A5A5A5u;
+    const uint32_t seed = (uint32_t)(P.frame * 0x9E3779B1ull) ^ 0xA5A5A5A5u ^ (uint32_t)(ctx->seed ^ (ctx->seed >> 32));
     // candidate rounds: score the pending candidates cluster-major, then
     // merge and select the next clusters by the certificate
     prop_cand_init(P.top, N, P.cand, P.ncand, P.pend, P.run, P.cpart, ctx->stream);
@@ -746,10 +747,15 @@ int check_flags(vbgs_ctx *ctx)
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->prof.collect();
     if (fl[FL_BAD_POINT]) return fail(ctx, VBGS_EINVAL, "non-finite point coordinate");
+    // a wait that gave up leaves partial statistics behind, which can make a
+    // posterior fail too: the timeout is the cause to report
+    if (fl[FL_TIMEOUT]) return fail(ctx, VBGS_ETIMEOUT, "a bounded device wait gave up");
     if (fl[FL_NONPD])
         return fail(ctx, VBGS_ENUMERIC, "posterior W^-1 of component %d is not positive definite",
                     fl[FL_NONPD] - 1);
-    if (fl[FL_TIMEOUT]) return fail(ctx, VBGS_ETIMEOUT, "a bounded device wait gave up");
+    if (fl[FL_CHECK])
+        return fail(ctx, VBGS_ECHECK, "a consistency check of the frame's results failed (non-finite statistics or "
+                                      "lse, a negative count, or counts / first moments not conserved)");
     return VBGS_OK;
 }
 
@@ -799,6 +805,12 @@ int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters, bool carry_prior)
         if ((rc = run_mstep(ctx, ctx->d_dS, carry_prior && last))) return rc;
         if (carry_prior && last) ctx->next_written = true;
         if (prop && it + 1 < n_iters && (rc = prop_refresh(ctx, true))) return rc;
+    }
+    if (ctx->checks) {
+        if (launch_check_frame(ctx->d_dS, ctx->K, ctx->d_X, N, prop ? nullptr : ctx->d_lse,
+                               ctx->precision == VBGS_FP64 ? 1e-9 : 1e-3, ctx->d_flags, ctx->stream, &ctx->prof) < 0)
+            return fail(ctx, VBGS_ECUDA, "check launch failed");
+        ctx->launches += 1;
     }
     if (launch_commit(ctx->d_Spast, ctx->d_dS, ctx->K, ctx->d_flags, ctx->stream, &ctx->prof) < 0)
         return fail(ctx, VBGS_ECUDA, "commit launch failed");
@@ -1175,6 +1187,64 @@ extern "C" int vbgs_proposal_clusters(vbgs_ctx *ctx, float *centroids, int *clus
     return VBGS_OK;
 }
 
+extern "C" int vbgs_kmeans(const float *points, int K, float *centroids, int lloyd_iters, int *cluster_of)
+{
+    if (K < 0 || (K > 0 && (!points || !centroids)) || lloyd_iters < 0 || lloyd_iters > 64)
+        return fail(nullptr, VBGS_EINVAL, "vbgs_kmeans: need K >= 0, points, centroids and 0 <= lloyd_iters <= 64");
+    if (K == 0) return VBGS_OK;
+    for (size_t i = 0; i < (size_t)K * 6; i++)
+        if (!std::isfinite(points[i])) return fail(nullptr, VBGS_EINVAL, "vbgs_kmeans: non-finite point");
+    for (int i = 0; i < kPG * 6; i++)
+        if (!std::isfinite(centroids[i])) return fail(nullptr, VBGS_EINVAL, "vbgs_kmeans: non-finite centroid");
+    // A local context only carries dalloc's error message; release() frees
+    // every buffer whatever fails.
+    vbgs_ctx tmp_ctx;
+    vbgs_ctx *ctx = &tmp_ctx;
+    float *d_pts = nullptr, *d_cent = nullptr;
+    int *d_order = nullptr, *d_cstart = nullptr;
+    unsigned int *d_skey = nullptr;
+    SortBuffers sb;
+    cudaStream_t st = nullptr;
+    auto release = [&]() {
+        cudaFree(d_pts); cudaFree(d_cent); cudaFree(d_order); cudaFree(d_cstart); cudaFree(d_skey);
+        cudaFree(sb.keys_in); cudaFree(sb.keys_out); cudaFree(sb.idx_in); cudaFree(sb.temp);
+        if (st) cudaStreamDestroy(st);
+        cudaGetLastError();
+    };
+    int rc = VBGS_OK;
+    const size_t tb = sort_temp_bytes(K);
+    unsigned char *temp = nullptr;
+    if ((rc = dalloc(ctx, &d_pts, (size_t)K * 6)) || (rc = dalloc(ctx, &d_cent, (size_t)kPG * 6)) ||
+        (rc = dalloc(ctx, &d_order, (size_t)K)) || (rc = dalloc(ctx, &d_cstart, (size_t)kPG + 1)) ||
+        (rc = dalloc(ctx, &d_skey, (size_t)K)) || (rc = dalloc(ctx, &sb.keys_in, (size_t)K)) ||
+        (rc = dalloc(ctx, &sb.keys_out, (size_t)K)) || (rc = dalloc(ctx, &sb.idx_in, (size_t)K)) ||
+        (rc = dalloc(ctx, &temp, tb))) {
+        sb.temp = temp;
+        release();
+        return fail(nullptr, rc, "%s", ctx->err.c_str());
+    }
+    sb.temp = temp;
+    sb.temp_bytes = tb;
+    sb.cap = K;
+    std::vector<int> order(K), cstart(kPG + 1);
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_pts, points, sizeof(float) * K * 6, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_cent, centroids, sizeof(float) * kPG * 6, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && prop_launch_lloyd(d_pts, K, d_cent, sb, d_order, d_skey, d_cstart, lloyd_iters, st))
+        e = cudaErrorLaunchFailure;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(centroids, d_cent, sizeof(float) * kPG * 6, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(order.data(), d_order, sizeof(int) * K, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cstart.data(), d_cstart, sizeof(int) * (kPG + 1), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return fail(nullptr, VBGS_ECUDA, "vbgs_kmeans: %s", cudaGetErrorString(e));
+    if (cluster_of)
+        for (int g = 0; g < kPG; g++)
+            for (int i = cstart[g]; i < cstart[g + 1]; i++) cluster_of[order[i]] = g;
+    return VBGS_OK;
+}
+
 extern "C" int vbgs_proposal_bounds(vbgs_ctx *ctx, const double *points, int64_t N, float *ub, int *cluster_of)
 {
     if (!ctx || !ctx->prop.on) return fail(ctx, VBGS_EINVAL, "the context has no proposal");
@@ -1219,6 +1289,76 @@ int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_splits)
     return VBGS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Continual state to and from a file (Alg. 1's model and statistics buffer,
+// plus everything the next frame reads, so that a resumed stream continues
+// bit for bit).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kStateMagic[8] = {'V', 'B', 'G', 'S', 'S', 'T', 'A', 'T'};
+constexpr int32_t kStateVersion = 1;
+
+struct StateHeader {
+    char magic[8];
+    int32_t version, K, D, precision, flags, has_prop, next_prior_ready, coef_epoch, plan_epoch, tune_p1, tune_p2,
+        prop_step, prop_centroids_ready, n_sections;
+    int64_t prop_frames_trained;
+    uint64_t prop_frame, seed;
+    double alpha0, beta0, nu0, W0[36], box_lo[3], box_inv_ext[3];
+};
+
+// One device array of the state: where it lives and its size in bytes.
+struct StateSection {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<StateSection> state_sections(vbgs_ctx *ctx)
+{
+    const int K = ctx->K;
+    const size_t nt = (size_t)(K + 127) / 128;
+    std::vector<StateSection> v = {
+        {ctx->d_m0, sizeof(double) * K * 6},
+        {ctx->d_Spast, sizeof(double) * K * VBGS_F},
+        {ctx->d_dS, sizeof(double) * K * VBGS_F},
+        {ctx->d_rec, sizeof(double) * K * VBGS_REC},
+        {ctx->d_rec32, sizeof(float) * K * VBGS_REC},
+        {ctx->d_pcache, sizeof(double) * mstep_cache_doubles(K)},
+        {ctx->d_pcache_next, sizeof(double) * mstep_prior_cache_doubles(K)},
+        {ctx->d_scal, sizeof(double) * SC_COUNT},
+        {ctx->d_kperm, sizeof(int) * K},
+        {ctx->d_kinv, sizeof(int) * K},
+        {ctx->d_tile_dirty, sizeof(int) * 6 * nt},
+        {ctx->d_tc_tiles, tc_tile_bytes(K)},
+        {ctx->d_tc_hdr, sizeof(float) * tc_hdr_floats(K)},
+    };
+    if (ctx->prop.on) {
+        const PropState &P = ctx->prop;
+        v.push_back({P.cent, sizeof(float) * kPG * 6});
+        v.push_back({P.w, sizeof(float) * kNParam});
+        v.push_back({P.wq, sizeof(float) * kNParam});
+        v.push_back({P.am, sizeof(float) * kNParam});
+        v.push_back({P.av, sizeof(float) * kNParam});
+    }
+    return v;
+}
+
+// 64-bit FNV-1a over a byte range, continuing from h.
+uint64_t fnv1a(uint64_t h, const void *p, size_t n)
+{
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; i++) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+constexpr uint64_t kFnvBasis = 0xcbf29ce484222325ull;
+
+} // namespace
+
 extern "C" {
 
 int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_options *opt)
@@ -1260,6 +1400,10 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     ctx->K = K;
     ctx->precision = precision;
     ctx->flags = opt ? opt->flags : 0;
+    ctx->checks = opt ? opt->checks : 0;
+    ctx->seed = opt ? opt->seed : 0;
+    if (opt && opt->autotune_cache) ctx->autotune_cache = opt->autotune_cache;
+    for (int i = 0; i < 36; i++) ctx->W0_h[i] = W0[i];
     {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -1367,6 +1511,19 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
 int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, double *elbo_trace)
 {
     int rc;
+    if (ctx && !ctx->autotune_cache.empty() && is_tc(ctx) && !ctx->prop.on && N > 0 && points && n_iters >= 1) {
+        // the work decomposition of this size class: tuned (or read from the
+        // cache file) on the first frame of the class, reused after
+        const int cls = (int)std::lround(std::log2((double)N));
+        auto it = std::find_if(ctx->tuned.begin(), ctx->tuned.end(), [&](const auto &e) { return e.first == cls; });
+        if (it == ctx->tuned.end()) {
+            if ((rc = vbgs_autotune(ctx, points, N, ctx->autotune_cache.c_str()))) return rc;
+            ctx->tuned.push_back({cls, {ctx->tune_p1, ctx->tune_p2}});
+        } else {
+            ctx->tune_p1 = it->second.first;
+            ctx->tune_p2 = it->second.second;
+        }
+    }
     // points are checked during the frame (the proposal's training must not
     // see bad ones, so with the proposal they are checked first)
     if ((rc = update_prepare(ctx, points, N, n_iters, ctx && !ctx->prop.on))) return rc;
@@ -1604,6 +1761,214 @@ const char *vbgs_profile_name(int i)
 {
     static const char *names[VBGS_PROF_COUNT] = {"pass1", "merge", "pass2", "reduce", "mstep", "misc", "plan"};
     return (i >= 0 && i < VBGS_PROF_COUNT) ? names[i] : "?";
+}
+
+int vbgs_save_state(vbgs_ctx *ctx, const char *path)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (!path) return fail(ctx, VBGS_EINVAL, "vbgs_save_state: path is NULL");
+    int rc;
+    if ((rc = join_side(ctx))) return rc;
+    CU(cudaStreamSynchronize(ctx->stream));
+    StateHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kStateMagic, 8);
+    h.version = kStateVersion;
+    h.K = ctx->K;
+    h.D = ctx->D;
+    h.precision = ctx->precision;
+    h.flags = ctx->flags;
+    h.has_prop = ctx->prop.on ? 1 : 0;
+    h.next_prior_ready = ctx->next_prior_ready ? 1 : 0;
+    h.coef_epoch = ctx->coef_epoch;
+    h.plan_epoch = ctx->plan_epoch;
+    h.tune_p1 = ctx->tune_p1;
+    h.tune_p2 = ctx->tune_p2;
+    h.prop_step = ctx->prop.step;
+    h.prop_centroids_ready = ctx->prop.centroids_ready ? 1 : 0;
+    h.prop_frames_trained = ctx->prop.frames_trained;
+    h.prop_frame = ctx->prop.frame;
+    h.seed = ctx->seed;
+    h.alpha0 = ctx->mp.alpha0;
+    h.beta0 = ctx->mp.beta0;
+    h.nu0 = ctx->mp.nu0;
+    for (int i = 0; i < 36; i++) h.W0[i] = ctx->W0_h[i];
+    for (int i = 0; i < 3; i++) {
+        h.box_lo[i] = ctx->box.lo[i];
+        h.box_inv_ext[i] = ctx->box.inv_ext[i];
+    }
+    const std::vector<StateSection> secs = state_sections(ctx);
+    h.n_sections = (int32_t)secs.size();
+    size_t total = 0;
+    for (const auto &q : secs) total += q.bytes;
+    std::vector<unsigned char> buf(total);
+    size_t off = 0;
+    for (const auto &q : secs) {
+        CU(cudaMemcpyAsync(buf.data() + off, q.dev, q.bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        off += q.bytes;
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    std::vector<uint64_t> sizes;
+    for (const auto &q : secs) sizes.push_back((uint64_t)q.bytes);
+    uint64_t sum = fnv1a(kFnvBasis, &h, sizeof h);
+    sum = fnv1a(sum, sizes.data(), sizeof(uint64_t) * sizes.size());
+    sum = fnv1a(sum, buf.data(), buf.size());
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return fail(ctx, VBGS_EIO, "vbgs_save_state: cannot open %s for writing", tmp.c_str());
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1 &&
+              fwrite(sizes.data(), sizeof(uint64_t), sizes.size(), f) == sizes.size() &&
+              fwrite(buf.data(), 1, buf.size(), f) == buf.size() && fwrite(&sum, sizeof sum, 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return fail(ctx, VBGS_EIO, "vbgs_save_state: writing %s failed", path);
+    }
+    return VBGS_OK;
+}
+
+int vbgs_load_state(vbgs_ctx **out, const char *path, const vbgs_options *opt)
+{
+    if (!out) return fail(nullptr, VBGS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!path) return fail(nullptr, VBGS_EINVAL, "vbgs_load_state: path is NULL");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(nullptr, VBGS_EIO, "vbgs_load_state: cannot open %s", path);
+    std::vector<unsigned char> file;
+    {
+        unsigned char chunk[1 << 16];
+        size_t n;
+        while ((n = fread(chunk, 1, sizeof chunk, f)) > 0) file.insert(file.end(), chunk, chunk + n);
+        fclose(f);
+    }
+    StateHeader h;
+    if (file.size() < sizeof h + sizeof(uint64_t)) return fail(nullptr, VBGS_EIO, "vbgs_load_state: %s is too short", path);
+    memcpy(&h, file.data(), sizeof h);
+    if (memcmp(h.magic, kStateMagic, 8) != 0 || h.version != kStateVersion)
+        return fail(nullptr, VBGS_EIO, "vbgs_load_state: %s is not a state file of this version", path);
+    if (h.K <= 0 || h.D != VBGS_D || h.n_sections <= 0 || h.n_sections > 64)
+        return fail(nullptr, VBGS_EIO, "vbgs_load_state: bad header in %s", path);
+    const size_t sizes_off = sizeof h, data_off = sizes_off + sizeof(uint64_t) * h.n_sections;
+    if (file.size() < data_off + sizeof(uint64_t)) return fail(nullptr, VBGS_EIO, "vbgs_load_state: %s is truncated", path);
+    std::vector<uint64_t> sizes(h.n_sections);
+    memcpy(sizes.data(), file.data() + sizes_off, sizeof(uint64_t) * h.n_sections);
+    uint64_t total = 0;
+    for (uint64_t b : sizes) total += b;
+    if (file.size() != data_off + total + sizeof(uint64_t))
+        return fail(nullptr, VBGS_EIO, "vbgs_load_state: %s has the wrong size", path);
+    uint64_t sum_file;
+    memcpy(&sum_file, file.data() + data_off + total, sizeof sum_file);
+    if (fnv1a(kFnvBasis, file.data(), data_off + total) != sum_file)
+        return fail(nullptr, VBGS_EIO, "vbgs_load_state: checksum mismatch in %s", path);
+    // The prior as it stands (m0 from the first section) and the saved form.
+    if (sizes[0] != sizeof(double) * (size_t)h.K * 6) return fail(nullptr, VBGS_EIO, "vbgs_load_state: bad m0 section");
+    std::vector<double> m0((size_t)h.K * 6);
+    memcpy(m0.data(), file.data() + data_off, sizes[0]);
+    vbgs_prior pr;
+    pr.alpha0 = h.alpha0;
+    pr.beta0 = h.beta0;
+    pr.nu0 = h.nu0;
+    pr.m0 = m0.data();
+    pr.W0 = h.W0;
+    vbgs_options o;
+    memset(&o, 0, sizeof o);
+    o.precision = h.precision;
+    o.flags = h.flags;
+    o.seed = h.seed;
+    if (opt) {
+        o.cuda_stream = opt->cuda_stream;
+        o.checks = opt->checks;
+        o.autotune_cache = opt->autotune_cache;
+    }
+    vbgs_ctx *ctx = nullptr;
+    int rc = vbgs_init(&ctx, &pr, h.K, h.D, &o);
+    if (rc) return rc;
+    const std::vector<StateSection> secs = state_sections(ctx);
+    if ((int)secs.size() != h.n_sections) {
+        vbgs_destroy(ctx);
+        return fail(nullptr, VBGS_EIO, "vbgs_load_state: %s has %d sections, the context %zu", path, h.n_sections,
+                    secs.size());
+    }
+    size_t off = data_off;
+    for (size_t i = 0; i < secs.size(); i++) {
+        if (sizes[i] != secs[i].bytes) {
+            vbgs_destroy(ctx);
+            return fail(nullptr, VBGS_EIO, "vbgs_load_state: section %zu of %s has the wrong size", i, path);
+        }
+        const cudaError_t e = cudaMemcpyAsync(secs[i].dev, file.data() + off, secs[i].bytes, cudaMemcpyHostToDevice,
+                                              ctx->stream);
+        if (e != cudaSuccess) {
+            vbgs_destroy(ctx);
+            return fail(nullptr, VBGS_ECUDA, "vbgs_load_state: %s", cudaGetErrorString(e));
+        }
+        off += secs[i].bytes;
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        vbgs_destroy(ctx);
+        return fail(nullptr, VBGS_ECUDA, "vbgs_load_state: copy to the device failed");
+    }
+    ctx->m0_h = m0;
+    ctx->next_prior_ready = h.next_prior_ready != 0;
+    ctx->coef_epoch = h.coef_epoch;
+    ctx->plan_epoch = h.plan_epoch;
+    ctx->tune_p1 = h.tune_p1;
+    ctx->tune_p2 = h.tune_p2;
+    for (int i = 0; i < 3; i++) {
+        ctx->box.lo[i] = h.box_lo[i];
+        ctx->box.inv_ext[i] = h.box_inv_ext[i];
+    }
+    if (ctx->prop.on) {
+        ctx->prop.step = h.prop_step;
+        ctx->prop.centroids_ready = h.prop_centroids_ready != 0;
+        ctx->prop.frames_trained = h.prop_frames_trained;
+        ctx->prop.rep[7] = (double)h.prop_frames_trained;
+        ctx->prop.frame = h.prop_frame;
+    }
+    *out = ctx;
+    return VBGS_OK;
+}
+
+int vbgs_check_frame(const double *dS, int K, const double *points, int64_t N, const double *lse, double tol,
+                     int *ok)
+{
+    if (!dS || K <= 0 || N < 0 || (N > 0 && !points) || !ok || !(tol >= 0))
+        return fail(nullptr, VBGS_EINVAL, "vbgs_check_frame: need dS, K > 0, N >= 0, points, ok and tol >= 0");
+    vbgs_ctx tmp_ctx;
+    double *d_dS = nullptr, *d_X = nullptr, *d_lse = nullptr;
+    int *d_flags = nullptr;
+    auto release = [&]() {
+        cudaFree(d_dS); cudaFree(d_X); cudaFree(d_lse); cudaFree(d_flags);
+        cudaGetLastError();
+    };
+    int rc;
+    if ((rc = dalloc(&tmp_ctx, &d_dS, (size_t)K * VBGS_F)) || (rc = dalloc(&tmp_ctx, &d_X, (size_t)std::max<int64_t>(N, 1) * VBGS_XS)) ||
+        (rc = dalloc(&tmp_ctx, &d_lse, (size_t)std::max<int64_t>(N, 1))) || (rc = dalloc(&tmp_ctx, &d_flags, (size_t)FL_COUNT))) {
+        release();
+        return fail(nullptr, rc, "%s", tmp_ctx.err.c_str());
+    }
+    std::vector<double> X((size_t)std::max<int64_t>(N, 1) * VBGS_XS, 0.0);
+    for (int64_t n = 0; n < N; n++)
+        for (int q = 0; q < 6; q++) X[(size_t)n * VBGS_XS + q] = points[(size_t)n * 6 + q];
+    int fl[FL_COUNT] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpy(d_dS, dS, sizeof(double) * K * VBGS_F, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_X, X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && lse && N > 0) e = cudaMemcpy(d_lse, lse, sizeof(double) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d_flags, 0, sizeof(int) * FL_COUNT);
+    Prof off;
+    if (e == cudaSuccess &&
+        launch_check_frame(d_dS, K, d_X, N, lse && N > 0 ? d_lse : nullptr, tol, d_flags, nullptr, &off) < 0)
+        e = cudaErrorLaunchFailure;
+    if (e == cudaSuccess) e = cudaMemcpy(fl, d_flags, sizeof fl, cudaMemcpyDeviceToHost);
+    release();
+    if (e != cudaSuccess) return fail(nullptr, VBGS_ECUDA, "vbgs_check_frame: %s", cudaGetErrorString(e));
+    *ok = fl[FL_CHECK] == 0;
+    return VBGS_OK;
+}
+
+int vbgs_set_wait_limit(long long cycles)
+{
+    if (tc_set_wait_limit(cycles)) return fail(nullptr, VBGS_ECUDA, "vbgs_set_wait_limit: cudaMemcpyToSymbol failed");
+    return VBGS_OK;
 }
 
 const char *vbgs_last_error(const vbgs_ctx *ctx)

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_merge(const double2 *__restrict__ part,
         if (minlse && w * 32 < N) minlse[w] = vm;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && lse_part) {
         double t = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += sh[i];
         lse_part[blockIdx.x] = t;
@@ -478,7 +478,8 @@ int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats
 //
 // The array lives in the library's device image: every GPU that loads the
 // library holds it until the process exits.  Its device address is looked up
-// once per device, by the first call made with that device current.  All
+// once per device (per CUDA context on it), by the first call made with that
+// device current, and passed to the kernels as a pointer.  All
 // calls share the one array and it keeps the last call's contents; calls
 // that overlap on the GPU (different streams, or contexts on other host
 // threads) race on it.
@@ -488,32 +489,77 @@ namespace {
 constexpr size_t kNoAllocDoubles = VBGS_NOALLOC_SCRATCH_BYTES / sizeof(double);
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
-constexpr int kMaxDevices = 64;
+// The scratch array's device address per CUDA context.  A module is loaded
+// into each context that uses it, so the address belongs to the context, not
+// to the device ordinal: after cudaDeviceReset (or a primary context released
+// and created again) the array may sit elsewhere, and the lookup is repeated
+// for the new context.
+constexpr int kMaxContexts = 64;
 std::mutex g_noalloc_mu;
-double *g_noalloc_addr[kMaxDevices] = {};
+struct NoallocSlot { void *cuctx; double *addr; };
+NoallocSlot g_noalloc_slots[kMaxContexts] = {};
+int g_noalloc_used = 0;
 
-// Device address of the scratch array on the current device (set-up on the
-// first call per device).  Returns nullptr on failure with *why set.
+typedef int (*CtxGetCurrentFn)(void **);
+
+// Handle of the calling thread's current CUDA context (nullptr if none).
+void *current_cuctx()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(f);
+        cudaGetLastError();
+        looked = true;
+    }
+    void *c = nullptr;
+    if (!fn || fn(&c) != 0) return nullptr;
+    return c;
+}
+
+// Device address of the scratch array in the current context (set-up on the
+// first call per context, with its device current).  Returns nullptr on
+// failure with *why set.
 double *noalloc_scratch(const char **why)
 {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
         cudaGetLastError();
         *why = "no current CUDA device";
         return nullptr;
     }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            *why = "cudaGetSymbolAddress of the scratch array failed";
-            return nullptr;
-        }
-        g_noalloc_addr[dev] = static_cast<double *>(p);
+    void *cc = current_cuctx();
+    for (int i = 0; cc && i < g_noalloc_used; i++)
+        if (g_noalloc_slots[i].cuctx == cc) return g_noalloc_slots[i].addr;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        *why = "cudaGetSymbolAddress of the scratch array failed";
+        return nullptr;
     }
-    return g_noalloc_addr[dev];
+    // The lookup makes the device's primary context current if no context was.
+    if (!cc) cc = current_cuctx();
+    if (!cc) return static_cast<double *>(p);
+    // A full table starts over: the oldest contexts are the likeliest gone.
+    if (g_noalloc_used == kMaxContexts) g_noalloc_used = 0;
+    g_noalloc_slots[g_noalloc_used++] = {cc, static_cast<double *>(p)};
+    return static_cast<double *>(p);
+}
+
+bool on_device(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 __global__ void k_lse_subtract_psi(double *__restrict__ lse, int64_t N, const double *__restrict__ scal)
@@ -539,6 +585,9 @@ extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N
     if (!ctx) return VBGS_EINVAL;
     if (N < 0 || !dS_out || (N > 0 && (!points || !lse_out)))
         return noalloc_fail(ctx, VBGS_EINVAL, "vbgs_estep_noalloc: need N >= 0 and device points, lse, dS");
+    // Host memory handed to a kernel would fault it: every array must be device memory.
+    if ((N > 0 && (!on_device(points) || !on_device(lse_out))) || !on_device(dS_out))
+        return noalloc_fail(ctx, VBGS_EINVAL, "vbgs_estep_noalloc: points, lse_out and dS_out must be device memory");
     const cudaStream_t st = ctx->stream;
     const int K = ctx->K;
     const char *why = "";
@@ -549,19 +598,18 @@ extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N
             return noalloc_fail(ctx, VBGS_ECUDA, "vbgs_estep_noalloc: clearing dS failed");
         return VBGS_OK;
     }
-    // Scratch layout (doubles): scalars | flags | lse block sums | points N x 8 | split partials.
+    // Scratch layout (doubles): flags | (unused) | points N x 8 | split partials.
     auto round_up = [](size_t v) { return (v + 31) & ~size_t(31); };
-    const size_t o_scal = 0, o_flags = SC_COUNT, o_lsep = 32;
+    const size_t o_flags = 0;
     const int mb = (int)((N + 255) / 256);
-    const size_t o_X = o_lsep + round_up((size_t)mb + 1);
+    const size_t o_X = 32;
     const size_t o_part = o_X + round_up((size_t)N * VBGS_XS);
     const size_t avail = o_part < kNoAllocDoubles ? kNoAllocDoubles - o_part : 0;
     if (avail < (size_t)N * 2 || avail < (size_t)K * 28)
         return noalloc_fail(ctx, VBGS_EINVAL,
                             "vbgs_estep_noalloc: N = " + std::to_string(N) + ", K = " + std::to_string(K) +
                             " need more than the " + std::to_string(VBGS_NOALLOC_SCRATCH_BYTES) +
-                            "-byte scratch array (8 N + max(2 N, 28 K) doubles plus block sums)");
-    double *scal = base + o_scal;
+                            "-byte scratch array (32 + 8 N + max(2 N, 28 K) doubles)");
     int *flags = reinterpret_cast<int *>(base + o_flags);
     double *X = base + o_X;
     double *part = base + o_part;
@@ -595,8 +643,7 @@ extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N
     dim3 g1(pl.p1_blocks, pl.p1_splits);
     if (f64) k_pass1<double, kPPT64><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec, K, pl.kps, p1, nullptr);
     else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec32, K, pl.kps, p1, nullptr);
-    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, nullptr, lse_out, base + o_lsep, nullptr);
-    launch_pdl(k_sum, 1, 1024, 0, st, base + o_lsep, mb, scal + SC_SUM_LSE);
+    k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, nullptr, lse_out, nullptr, nullptr);
     dim3 g2(pl.p2_tiles, pl.p2_splits);
     if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part, nullptr, nullptr, 1, 1, nullptr);
     else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part, nullptr, nullptr, 1, 1, nullptr);
@@ -604,6 +651,7 @@ extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N
                                                     ctx->d_kperm, dS_out);
     k_lse_subtract_psi<<<mb, 256, 0, st>>>(lse_out, N, ctx->d_scal);
     if (cudaGetLastError() != cudaSuccess) return noalloc_fail(ctx, VBGS_ECUDA, "vbgs_estep_noalloc: launch failed");
-    ctx->launches = 7;
+    // memset + 2 staging kernels, pass 1, merge, pass 2, reduce, lse shift
+    ctx->launches = 8;
     return VBGS_OK;
 }

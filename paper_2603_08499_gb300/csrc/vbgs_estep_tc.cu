@@ -36,6 +36,9 @@
 
 namespace vbgs {
 
+// Limit of the waits between warp roles (cycles); vbgs_set_wait_limit.
+__device__ long long g_wait_limit = 4000000000LL;
+
 namespace {
 
 constexpr int kRows = 128;          // points per CTA tile (MMA M)
@@ -85,17 +88,21 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity)
                  : "memory");
     return ok != 0;
 }
-// Bounded wait on a barrier phase; false on timeout.  A normal wait also
-// gives up as soon as another thread of the grid has timed out; a drain wait
-// (for copies and MMAs this thread issued) only stops at its own limit.
+// Bounded wait on a barrier phase; false on timeout.  A normal wait (one
+// warp role waiting for another) gives up after g_wait_limit cycles, or as
+// soon as another thread of the grid has timed out; a drain wait (for copies
+// and MMAs this thread issued, which complete on their own) keeps the full
+// kSpinCycles, so that nothing is in flight when the shared memory and TMEM
+// are released.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity, int *flags, bool drain = false)
 {
     if (mbar_try(b, parity)) return true;
     const long long t0 = clock64();
+    const long long limit = drain ? kSpinCycles : g_wait_limit;
     for (;;) {
         if (mbar_try(b, parity)) return true;
         if (!drain && *(volatile int *)&flags[FL_TIMEOUT]) return false;
-        if (clock64() - t0 > kSpinCycles) {
+        if (clock64() - t0 > limit) {
             atomicExch(&flags[FL_TIMEOUT], 1);
             return false;
         }
@@ -1861,6 +1868,12 @@ int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start
                minlse);
     pf->end(st);
     return launch_block_sum(lse_part, mb, sum_out, st, pf) < 0 ? -1 : 2;
+}
+
+int tc_set_wait_limit(long long cycles)
+{
+    const long long v = cycles > 0 ? cycles : kSpinCycles;
+    return cudaMemcpyToSymbol(g_wait_limit, &v, sizeof v) == cudaSuccess ? 0 : -1;
 }
 
 } // namespace vbgs

@@ -72,6 +72,7 @@ enum FlagSlot {
     FL_BAD_POINT = 0,  // a non-finite coordinate was staged
     FL_NONPD = 1,      // index + 1 of a component whose W^-1 is not PD (0 = none)
     FL_TIMEOUT = 2,
+    FL_CHECK = 3,      // a consistency check of the frame's results failed
     FL_COUNT = 4
 };
 
@@ -215,6 +216,12 @@ int launch_comp_order(const double *m0, const double *Spast, int K, double beta0
                       SortBuffers &sb, int *kperm, int *kinv, cudaStream_t st, Prof *pf);
 int launch_commit(double *Spast, const double *dS, int K, const int *flags, cudaStream_t st, Prof *pf);
 int launch_elbo(double *scal, int64_t N, double *elbo_out, cudaStream_t st, Prof *pf);
+// Consistency checks of a frame's results (options.checks): sets
+// flags[FL_CHECK] unless every count, moment and lse is finite, every count
+// non-negative, sum_k dS_k0 = N and sum_k dS_k(1..6) = sum_n x_n within tol
+// (relative).  X: staged points (N x 8); lse may be null.
+int launch_check_frame(const double *dS, int K, const double *X, int64_t N, const double *lse, double tol,
+                       int *flags, cudaStream_t st, Prof *pf);
 
 // E-step of the CUDA-core forms: FP64 (precision == VBGS_FP64) or FP32.
 int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats, cudaStream_t st,
@@ -228,6 +235,9 @@ int launch_pass2_fp32(const EstepBuffers &B, int tpb, int tkc, cudaStream_t st, 
 // (FP16/BF16 hi/lo, 16 KB each, in the MMA's shared-memory layout) with a
 // 32-float frame header each, and pass 1 on tcgen05 with TMEM accumulators.
 size_t tc_tile_bytes(int K);
+// Limit (SM cycles) of the waits between warp roles of the tensor-core
+// kernels on the current device; cycles <= 0 restores the default (~2 s).
+int tc_set_wait_limit(long long cycles);
 size_t tc_hdr_floats(int K);
 size_t tc_tmax_floats(int64_t N, int K);
 // dirty: ntiles flags (records rewritten since the tile's last build), then
@@ -266,6 +276,8 @@ int launch_block_sum(const double *part, int n, double *sum_out, cudaStream_t st
 // Learned proposal (vbgs_proposal.cu).
 int prop_launch_kmeans(const float *rec32, int K, float csc, float *pts, float *cent, SortBuffers &sb, int *order,
                        unsigned int *skey, int *cstart, int lloyd_iters, cudaStream_t st);
+int prop_launch_lloyd(const float *pts, int K, float *cent, SortBuffers &sb, int *order, unsigned int *skey,
+                      int *cstart, int lloyd_iters, cudaStream_t st);
 int prop_launch_certificate(const double *rec, const float *rec32, const int *order, const unsigned int *skey,
                             const int *cstart, int K, const double *Spast, const double *dS, const int *kperm,
                             float xmax, float *cpar, double *cscr, float *mscr, cudaStream_t st);
@@ -359,6 +371,11 @@ struct vbgs_ctx {
     int K = 0, D = 6;
     int precision = VBGS_FP64;
     int flags = 0;
+    int checks = 0;                            // options.checks: consistency checks after every frame
+    uint64_t seed = 0;                         // options.seed (0: the library's default)
+    std::string autotune_cache;                // options.autotune_cache (empty: automatic decomposition)
+    std::vector<std::pair<int, std::pair<int, int>>> tuned;   // size class -> work decomposition from the cache
+    double W0_h[36] = {};                      // the prior's Wishart scale as given
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;               // KL terms of the M-step, beside the next E-step
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

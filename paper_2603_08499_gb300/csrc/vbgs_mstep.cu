@@ -806,13 +806,74 @@ __global__ void __launch_bounds__(128) k_mstep_finalize(const double *__restrict
     }
 }
 
-// S_past += Delta S, skipped when the last posterior update failed.
+// S_past += Delta S, skipped when anything of the frame failed: a bad point,
+// a posterior update, a bounded wait or a consistency check.
 __global__ void k_commit(double *__restrict__ Spast, const double *__restrict__ dS, size_t n,
                          const int *__restrict__ flags)
 {
     pdl_wait();
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && flags[FL_NONPD] == 0 && flags[FL_BAD_POINT] == 0) Spast[i] += dS[i];
+    if (i < n && flags[FL_NONPD] == 0 && flags[FL_BAD_POINT] == 0 && flags[FL_TIMEOUT] == 0 &&
+        flags[FL_CHECK] == 0)
+        Spast[i] += dS[i];
+}
+
+// Consistency checks of a frame (one block): every statistic and lse_n
+// finite, counts non-negative, and the two conservation laws of Eq. 3 --
+// sum_k N_k = N (responsibilities sum to one per point) and
+// sum_k S1_k = sum_n x_n -- within a relative tolerance.
+__global__ void __launch_bounds__(1024) k_check_frame(const double *__restrict__ dS, int K,
+                                                      const double *__restrict__ X, int64_t N,
+                                                      const double *__restrict__ lse, double tol,
+                                                      int *__restrict__ flags)
+{
+    pdl_wait();
+    __shared__ double sh[32][14];
+    __shared__ int bad_sh;
+    if (threadIdx.x == 0) bad_sh = 0;
+    __syncthreads();
+    double acc[14];
+#pragma unroll
+    for (int q = 0; q < 14; q++) acc[q] = 0.0;
+    int bad = 0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const double *r = dS + (size_t)k * 28;
+        for (int q = 0; q < 28; q++) bad |= !isfinite(r[q]);
+        bad |= r[0] < 0.0;
+#pragma unroll
+        for (int q = 0; q < 7; q++) acc[q] += r[q];
+    }
+    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+        const double *x = X + (size_t)n * VBGS_XS;
+        acc[7] += 1.0;
+#pragma unroll
+        for (int q = 0; q < 6; q++) acc[8 + q] += x[q];
+        if (lse) bad |= !isfinite(lse[n]);
+    }
+    if (bad) atomicOr(&bad_sh, 1);
+#pragma unroll
+    for (int q = 0; q < 14; q++) {
+        double v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[14];
+        for (int q = 0; q < 14; q++) {
+            t[q] = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t[q] += sh[w][q];
+        }
+        bool ok = !bad_sh && fabs(t[0] - t[7]) <= tol * fmax(t[7], 1.0);
+        double d2 = 0.0, n2 = 0.0;
+        for (int q = 0; q < 6; q++) {
+            d2 += (t[1 + q] - t[8 + q]) * (t[1 + q] - t[8 + q]);
+            n2 += t[8 + q] * t[8 + q];
+        }
+        ok = ok && isfinite(d2) && sqrt(d2) <= tol * fmax(sqrt(n2), 1.0);
+        if (!ok) flags[FL_CHECK] = 1;
+    }
 }
 
 __global__ void k_elbo(double *__restrict__ scal, double N, double *__restrict__ out)
@@ -946,6 +1007,15 @@ int launch_commit(double *Spast, const double *dS, int K, const int *flags, cuda
     size_t n = (size_t)K * 28;
     pf->begin(VBGS_PROF_MISC, st);
     launch_pdl(k_commit, (unsigned)((n + 255) / 256), 256, 0, st, Spast, dS, n, flags);
+    pf->end(st);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_check_frame(const double *dS, int K, const double *X, int64_t N, const double *lse, double tol,
+                       int *flags, cudaStream_t st, Prof *pf)
+{
+    pf->begin(VBGS_PROF_MISC, st);
+    launch_pdl(k_check_frame, 1, 1024, 0, st, dS, K, X, N, lse, tol, flags);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }

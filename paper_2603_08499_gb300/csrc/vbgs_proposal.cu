@@ -1218,6 +1218,15 @@ int prop_launch_kmeans(const float *rec32, int K, float csc, float *pts, float *
                        unsigned int *skey, int *cstart, int lloyd_iters, cudaStream_t st)
 {
     k_means_of_records<<<(K + 255) / 256, 256, 0, st>>>(rec32, K, csc, pts);
+    return prop_launch_lloyd(pts, K, cent, sb, order, skey, cstart, lloyd_iters, st);
+}
+
+// lloyd_iters rounds of (nearest centroid, centroid = mean of its members),
+// then the nearest-centroid assignment of the final centroids: skey / order
+// hold the sorted assignment, cstart the cluster boundaries.
+int prop_launch_lloyd(const float *pts, int K, float *cent, SortBuffers &sb, int *order, unsigned int *skey,
+                      int *cstart, int lloyd_iters, cudaStream_t st)
+{
     for (int it = 0; it <= lloyd_iters; it++) {
         k_assign<<<(K + 255) / 256, 256, 0, st>>>(pts, K, cent, sb.keys_in, sb.idx_in);
         size_t bytes = sb.temp_bytes;

@@ -24,6 +24,8 @@ VBGS_ENOMEM = -2
 VBGS_ECUDA = -3
 VBGS_ENUMERIC = -4
 VBGS_ETIMEOUT = -5
+VBGS_ECHECK = -6
+VBGS_EIO = -7
 
 VBGS_FP64 = 0
 VBGS_FP16X3 = 1
@@ -50,7 +52,8 @@ EXPORTS = [
     "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_pairs", "vbgs_profile_name", "vbgs_probe_peaks",
     "vbgs_estep_noalloc", "vbgs_update_batched", "vbgs_autotune", "vbgs_get_tuning", "vbgs_set_tuning",
     "vbgs_proposal_report", "vbgs_proposal_weights", "vbgs_proposal_grad", "vbgs_proposal_clusters",
-    "vbgs_proposal_bounds", "vbgs_reassign", "vbgs_last_error", "vbgs_destroy",
+    "vbgs_proposal_bounds", "vbgs_kmeans", "vbgs_reassign", "vbgs_save_state", "vbgs_load_state",
+    "vbgs_check_frame", "vbgs_set_wait_limit", "vbgs_last_error", "vbgs_destroy",
 ]
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 PROF_COUNT = 7
@@ -65,7 +68,7 @@ class VbgsError(RuntimeError):
 
 class vbgs_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("flags", C.c_int), ("cuda_stream", C.c_void_p),
-                ("reserved1", C.c_uint64)]
+                ("checks", C.c_int), ("autotune_cache", C.c_char_p), ("seed", C.c_uint64)]
 
 
 class vbgs_prior(C.Structure):
@@ -116,6 +119,11 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
     lib.vbgs_proposal_grad.argtypes = [C.c_void_p, _FP, _FP, C.c_int, _FP, _FP, C.POINTER(C.c_int)]
     lib.vbgs_proposal_clusters.argtypes = [C.c_void_p, _FP, C.POINTER(C.c_int)]
     lib.vbgs_proposal_bounds.argtypes = [C.c_void_p, _DP, C.c_int64, _FP, C.POINTER(C.c_int)]
+    lib.vbgs_kmeans.argtypes = [_FP, C.c_int, _FP, C.c_int, C.POINTER(C.c_int)]
+    lib.vbgs_save_state.argtypes = [C.c_void_p, C.c_char_p]
+    lib.vbgs_load_state.argtypes = [C.POINTER(C.c_void_p), C.c_char_p, C.POINTER(vbgs_options)]
+    lib.vbgs_check_frame.argtypes = [_DP, C.c_int, _DP, C.c_int64, _DP, C.c_double, C.POINTER(C.c_int)]
+    lib.vbgs_set_wait_limit.argtypes = [C.c_longlong]
     return lib
 
 
@@ -164,16 +172,53 @@ def _points_ptr(points):
 
 # ---- C-named functions ------------------------------------------------------
 
+def _options(precision: int = VBGS_FP64, flags: int = 0, cuda_stream: int | None = None, checks: bool = False,
+             autotune_cache: str | None = None, seed: int = 0) -> vbgs_options:
+    return vbgs_options(int(precision), int(flags), C.c_void_p(cuda_stream or None), int(bool(checks)),
+                        autotune_cache.encode() if autotune_cache else None, int(seed))
+
+
 def vbgs_init(alpha0: float, beta0: float, nu0: float, m0, W0, precision: int = VBGS_FP64,
-              cuda_stream: int | None = None, flags: int = 0):
+              cuda_stream: int | None = None, flags: int = 0, checks: bool = False,
+              autotune_cache: str | None = None, seed: int = 0):
     m0a = _host_f64(m0)
     K = m0a.shape[0]
     W0a = _host_f64(W0, (D, D))
     pr = vbgs_prior(alpha0, beta0, nu0, _dp(m0a), _dp(W0a))
-    opt = vbgs_options(int(precision), int(flags), C.c_void_p(cuda_stream or None), 0)
+    opt = _options(precision, flags, cuda_stream, checks, autotune_cache, seed)
     ctx = C.c_void_p()
     _check(lib().vbgs_init(C.byref(ctx), C.byref(pr), K, m0a.shape[1], C.byref(opt)), None)
     return ctx
+
+
+def vbgs_save_state(ctx, path: str) -> None:
+    _check(lib().vbgs_save_state(ctx, str(path).encode()), ctx)
+
+
+def vbgs_load_state(path: str, cuda_stream: int | None = None, checks: bool = False,
+                    autotune_cache: str | None = None):
+    opt = _options(cuda_stream=cuda_stream, checks=checks, autotune_cache=autotune_cache)
+    ctx = C.c_void_p()
+    _check(lib().vbgs_load_state(C.byref(ctx), str(path).encode(), C.byref(opt)), None)
+    return ctx
+
+
+def vbgs_check_frame(dS, points, lse=None, tol: float = 1e-9) -> bool:
+    """The frame consistency check of options.checks on host arrays."""
+    S = _host_f64(dS)
+    X = _host_f64(points)
+    if S.ndim != 2 or S.shape[1] != F or X.ndim != 2 or X.shape[1] != D:
+        raise ValueError("dS must be K x 28 and points N x 6")
+    lp = None
+    if lse is not None:
+        la = _host_f64(lse).ravel()
+        if la.size != X.shape[0]:
+            raise ValueError("lse needs one value per point")
+        lp = _dp(la)
+    ok = C.c_int(0)
+    _check(lib().vbgs_check_frame(_dp(S), S.shape[0], _dp(X) if X.size else None, X.shape[0], lp, float(tol),
+                                  C.byref(ok)), None)
+    return bool(ok.value)
 
 
 def vbgs_update(ctx, points, n_iters: int) -> np.ndarray:
@@ -278,14 +323,43 @@ def vbgs_probe_peaks(device: int = 0) -> dict:
             "sms": int(out[3])}
 
 
-def vbgs_estep_noalloc(ctx, points, lse_out, dS_out) -> None:
+def _device_f64(t, shape, what: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+def vbgs_estep_noalloc(ctx, points, lse_out, dS_out, K: int | None = None) -> None:
     """E-step into caller-owned device buffers with no allocation by the
-    library (torch CUDA tensors: points N x 6, lse_out N, dS_out K x 28,
-    all float64).  Results are enqueued on the context's stream."""
-    ptr, N, keep = _points_ptr(points)
-    _check(lib().vbgs_estep_noalloc(ctx, ptr, N, C.c_void_p(lse_out.data_ptr() if N else None),
+    library (contiguous float64 CUDA tensors: points N x 6, lse_out N,
+    dS_out K x 28).  Results are enqueued on the context's stream.  The
+    library itself rejects host pointers; these checks also catch wrong
+    shapes and dtypes, which the C ABI cannot see."""
+    import torch
+    if not isinstance(points, torch.Tensor) or points.dim() != 2:
+        raise ValueError("points must be an N x 6 float64 CUDA tensor")
+    N = points.shape[0]
+    _device_f64(points, (N, D), "points")
+    _device_f64(lse_out, (N,), "lse_out")
+    if K is not None:
+        _device_f64(dS_out, (K, F), "dS_out")
+    elif dS_out.dim() != 2 or dS_out.shape[1] != F:
+        raise ValueError("dS_out must be K x 28")
+    else:
+        _device_f64(dS_out, tuple(dS_out.shape), "dS_out")
+    _check(lib().vbgs_estep_noalloc(ctx, C.c_void_p(points.data_ptr() if N else None), N,
+                                    C.c_void_p(lse_out.data_ptr() if N else None),
                                     C.c_void_p(dS_out.data_ptr())), ctx)
-    del keep
+
+
+def vbgs_estep_noalloc_raw(ctx, points_ptr: int, N: int, lse_ptr: int, dS_ptr: int) -> int:
+    """The C entry point with raw addresses and no checks in Python (returns
+    the status code): for tests of the library's own argument checks."""
+    return int(lib().vbgs_estep_noalloc(ctx, C.c_void_p(points_ptr or None), int(N), C.c_void_p(lse_ptr or None),
+                                        C.c_void_p(dS_ptr or None)))
 
 
 def vbgs_update_batched(ctxs, points_list, n_iters: int) -> np.ndarray:
@@ -370,6 +444,27 @@ def vbgs_proposal_bounds(ctx, points, K: int):
     return ub, cl
 
 
+def vbgs_kmeans(points, centroids, lloyd_iters: int):
+    """Lloyd's algorithm from the given centroids (1024 x 6) on K x 6 points:
+    returns (centroids, nearest-centroid assignment of the points)."""
+    x = np.ascontiguousarray(points, dtype=np.float32)
+    if x.ndim != 2 or x.shape[1] != 6:
+        raise ValueError("points must be K x 6")
+    c = np.array(centroids, dtype=np.float32, copy=True, order="C")
+    if c.shape != (PROP_CLUSTERS, 6):
+        raise ValueError(f"centroids must be {PROP_CLUSTERS} x 6")
+    cl = np.zeros(max(x.shape[0], 1), dtype=np.int32)
+    _check(lib().vbgs_kmeans(_fp(x) if x.size else None, x.shape[0], _fp(c), int(lloyd_iters),
+                             cl.ctypes.data_as(C.POINTER(C.c_int))), None)
+    return c, cl[:x.shape[0]]
+
+
+def vbgs_set_wait_limit(cycles: int) -> None:
+    """Limit (SM cycles) of the waits between warp roles of the tensor-core
+    kernels on the current device; <= 0 restores the default."""
+    _check(lib().vbgs_set_wait_limit(int(cycles)), None)
+
+
 def vbgs_last_error(ctx=None) -> str:
     return lib().vbgs_last_error(ctx).decode(errors="replace")
 
@@ -382,13 +477,29 @@ def vbgs_destroy(ctx) -> None:
 class Model:
     """One VBGS mixture on the GPU (owns a vbgs_ctx)."""
 
-    def __init__(self, prior: dict, precision: str | int = "fp64", cuda_stream: int | None = None,
-                 flags: int = 0):
+    def __init__(self, prior: dict | None, precision: str | int = "fp64", cuda_stream: int | None = None,
+                 flags: int = 0, checks: bool = False, autotune_cache: str | None = None, seed: int = 0,
+                 _ctx=None, _K: int = 0):
+        self.ctx = None
+        if _ctx is not None:        # Model.load
+            self.K, self.ctx = int(_K), _ctx
+            return
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.K = int(np.asarray(prior["m0"]).shape[0])
-        self.ctx = None
         self.ctx = vbgs_init(prior["alpha0"], prior["beta0"], prior["nu0"], prior["m0"], prior["W0"],
-                             p, cuda_stream, flags)
+                             p, cuda_stream, flags, checks, autotune_cache, seed)
+
+    @classmethod
+    def load(cls, path: str, cuda_stream: int | None = None, checks: bool = False,
+             autotune_cache: str | None = None) -> "Model":
+        """A model resumed from a file vbgs_save_state wrote."""
+        ctx = vbgs_load_state(path, cuda_stream, checks, autotune_cache)
+        with open(path, "rb") as f:
+            K = int(np.frombuffer(f.read(16), dtype=np.int32)[3])   # magic (8 bytes), version, K
+        return cls(None, _ctx=ctx, _K=K)
+
+    def save(self, path: str) -> None:
+        vbgs_save_state(self.ctx, path)
 
     def update(self, points, n_iters: int) -> np.ndarray:
         return vbgs_update(self.ctx, points, n_iters)

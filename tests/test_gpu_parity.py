@@ -271,9 +271,9 @@ def test_full_size_room_frame_sampled(V, form):
     trace = m.update(torch.from_numpy(X).cuda(), 3)
     dS = m.frame_stats()
     N = X.shape[0]
-    assert abs(dS[:, 0].sum() - N) <= (1e-9 if form == "fp64" else 1e-3) * N
-    assert O.relerr(dS[:, 1:7].sum(0), X.sum(0)) <= (1e-12 if form == "fp64" else 1e-3)
-    assert np.all(np.diff(trace) >= -(1e-9 if form == "fp64" else 1e-5) * abs(trace[-1]))
+    assert abs(dS[:, 0].sum() - N) <= (1e-9 if form == "fp64" else 1e-4) * N
+    assert O.relerr(dS[:, 1:7].sum(0), X.sum(0)) <= (1e-12 if form == "fp64" else 1e-4)
+    assert np.all(np.diff(trace) >= -(1e-9 if form == "fp64" else 1e-6) * abs(trace[-1]))
     # the ELBO of the first iteration is under the prior: check sampled points
     m2 = V.Model(pr, form)
     e, lse = m2.elbo(X, want_lse=True)
@@ -292,3 +292,25 @@ def test_profile_counts_launches(V):
     prof = m.profile_read()
     assert prof["pass1"][1] == 2 and prof["pass2"][1] == 2 and prof["pass1"][0] > 0
     assert sum(n for _, n in prof.values()) == m.launches()
+
+
+@pytest.mark.parametrize("form", ["fp16x3", "fp64"])
+def test_stream_runs_are_bitwise_reproducible(V, form):
+    """Two runs of the same room stream (4 frames, K = 20,000, 3 iterations
+    each) through fresh contexts give bit-identical ELBO traces, statistics,
+    posteriors and lse: no result depends on the order in which atomics
+    compact the M-step's component list or on scheduling."""
+    import torch
+    room = synth.Room(seed=9)
+    pr = synth.room_prior(20_000, seed=9)
+    frames = [torch.from_numpy(synth.room_frame(t, seed=9, width=120, height=120, room=room)).cuda()
+              for t in range(4)]
+    runs = []
+    for _ in range(2):
+        m = V.Model(pr, form)
+        tr = np.array([m.update(X, 3) for X in frames])
+        post = m.posterior()
+        runs.append((tr, m.stats(), m.lse(frames[-1].shape[0]), post["m"], post["Winv"]))
+        m.close()
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)

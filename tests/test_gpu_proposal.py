@@ -95,6 +95,82 @@ def test_kmeans_assignment_is_nearest_centroid(V, room_state):
     m.close()
 
 
+def _nearest(X, C):
+    """Nearest centroid from the definition (FP64 distances of the FP32
+    values, ties to the lower index) and the gap to the nearest centroid at
+    another position: assignments whose gap is within FP32 rounding of the
+    distances may differ between FP32 and FP64 arithmetic."""
+    d2 = ((X[:, None, :].astype(np.float64) - C[None].astype(np.float64)) ** 2).sum(-1)
+    a = d2.argmin(1)
+    best = d2[np.arange(X.shape[0]), a]
+    same_pos = np.all(C[None, :, :] == C[a][:, None, :], axis=2)
+    other = np.where(same_pos, np.inf, d2).min(1)
+    ambiguous = other - best <= 1e-5 * (1.0 + best)
+    return a, ambiguous
+
+
+def _kmeans_case(seed=31, K=20_000):
+    """Points in 300 blobs; warm-start centroids drawn from the points, with
+    an exact duplicate pair (the tie rule) and two far-away centroids that no
+    point is nearest to (empty clusters keep their centroids)."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(-3, 3, (300, 6))
+    X = (centres[rng.integers(0, 300, K)] + 0.2 * rng.standard_normal((K, 6))).astype(np.float32)
+    C0 = X[rng.choice(K, 1024, replace=False)].copy()
+    C0[700] = C0[5]
+    C0[1000] = 1e3
+    C0[1023] = -1e3
+    return X, C0
+
+
+def test_kmeans_lloyd_step_against_definition(V):
+    """One Lloyd step against its definition: every point to its nearest
+    centroid (ties to the lower index), every centroid to the mean of its
+    members, empty clusters keep their centroids; the returned assignment is
+    the nearest of the returned centroids."""
+    X, C0 = _kmeans_case()
+    C1, cl = V.vbgs_kmeans(X, C0, 1)
+    a0, amb0 = _nearest(X, C0)
+    scale = float(np.abs(X).max())
+    touched = np.zeros(1024, bool)
+    touched[a0[amb0]] = True
+    for g in range(1024):
+        mem = a0 == g
+        if not mem.any():
+            assert np.array_equal(C1[g], C0[g]), g          # empty: kept bit for bit
+        elif not touched[g]:
+            ref = X[mem].astype(np.float64).mean(0)
+            assert np.max(np.abs(C1[g] - ref)) <= 2e-6 * scale, (g, C1[g], ref)
+    # the duplicate: no point goes to the higher index of the tied pair
+    assert not np.any(a0 == 700) and np.array_equal(C1[700], C0[700])
+    assert np.array_equal(C1[1000], C0[1000]) and np.array_equal(C1[1023], C0[1023])
+    # the assignment under the returned centroids
+    a1, amb1 = _nearest(X, C1)
+    assert np.all((cl == a1) | amb1)
+    assert np.mean(amb1) < 1e-3
+
+
+def test_kmeans_warm_start_and_ties(V):
+    """Two Lloyd iterations equal one iteration warm-started from one
+    iteration (bit for bit); exactly tied centroids assign to the lower index."""
+    X, C0 = _kmeans_case(seed=32, K=5_000)
+    C2, cl2 = V.vbgs_kmeans(X, C0, 2)
+    C1, _ = V.vbgs_kmeans(X, C0, 1)
+    C11, cl11 = V.vbgs_kmeans(X, C1, 1)
+    assert np.array_equal(C2, C11) and np.array_equal(cl2, cl11)
+    # every point equidistant from two identical centroids goes to the lower one
+    C = np.zeros((1024, 6), np.float32)
+    C[:] = 50.0
+    C[3] = C[9] = X.mean(0)
+    _, cl = V.vbgs_kmeans(X, C, 0)
+    assert np.all(cl == 3)
+    # zero iterations only assign: centroids unchanged
+    C0b, cl0 = V.vbgs_kmeans(X, C0, 0)
+    assert np.array_equal(C0b, C0)
+    a0, amb0 = _nearest(X, C0)
+    assert np.all((cl0 == a0) | amb0)
+
+
 def test_certificate_bounds_every_cluster_mass(V, room_state):
     pr, S, X2 = room_state
     K = pr["m0"].shape[0]
