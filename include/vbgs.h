@@ -355,6 +355,18 @@ int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset);
 int vbgs_profile_pairs(vbgs_ctx *ctx, int64_t *pass1_pairs, int64_t *pass2_pairs);
 const char *vbgs_profile_name(int i);
 
+/* No paper counterpart (measurement).  The duration of the dominant kernel
+ * without its neighbours: the last tensor-core pass-1 launch of the
+ * context (the E-step's logits and online log-sum-exp) is launched again,
+ * once to count the (point, component) pairs it evaluates and once to warm
+ * up, then reps times back to back between two CUDA events on the
+ * context's stream; *ms_per_launch receives the mean time per launch and
+ * *pairs_per_launch (may be NULL) the pairs.  The relaunches rewrite the
+ * same partial results, so the context's state is unchanged.  Needs a
+ * tensor-core context whose buffers have not been reallocated since that
+ * launch.  Synchronises.  Errors: VBGS_EINVAL, VBGS_ECUDA, VBGS_ETIMEOUT. */
+int vbgs_profile_replay(vbgs_ctx *ctx, int reps, double *ms_per_launch, int64_t *pairs_per_launch);
+
 /* No paper counterpart (measurement).  Measure this GPU's arithmetic peaks
  * with short probe kernels (a few
  * milliseconds each, device `device`): out[0] FP64 FMA TFLOP/s, out[1] FP32
@@ -393,6 +405,35 @@ int vbgs_probe_peaks(int device, double *out);
  * non-finite points), VBGS_ECUDA. */
 #define VBGS_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
 int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N, double *lse_out, double *dS_out);
+
+/* The quality metric of the paper (Sec. 5.1, Setup): render
+ * the current posterior prior0 (+) S_past at a held-out camera and score it
+ * by PSNR = 10 log10(255^2 / MSE), MSE over all pixels and RGB channels on
+ * a 0..255 scale.  The paper does not describe its renderer; here every
+ * component that data has reached (accumulated count N_k >= 1; the others
+ * hold only the prior and are left out) is a splat at its spatial posterior
+ * mean with the expected
+ * spatial covariance W_s^-1 / (nu - d - 1) of its Wishart posterior (d = 6;
+ * 3 for the split model's spatial block), the colour posterior mean clamped
+ * to [0, 1] and opacity 0.99, projected by elliptical weighted averaging
+ * (perspective Jacobian, +0.3 px^2 on the screen covariance's diagonal;
+ * splats nearer than 0.1 m to the camera plane left out) and composited
+ * front to back at pixel centres in increasing camera depth (ties by
+ * component index): alpha = min(0.99, 0.99 exp(-q / 2)) with q the squared
+ * screen-space Mahalanobis distance, alpha < 1/255 skipped, black
+ * background.  A pixel stops compositing once its transmittance is below
+ * 1e-7.  camera: 13 doubles, host: centre o (3), the camera-to-world
+ * rotation Rwc (9, row-major; pixel (u, v) looks along
+ * Rwc ((u + 1/2 - width/2) / f, (v + 1/2 - height/2) / f, 1)), focal length
+ * f in pixels.  image (height x width x 3 floats, host, may be NULL)
+ * receives the rendering; with reference (same layout, host, in [0, 1]) psnr
+ * (may be NULL) receives the PSNR against it.  device_ms (may be NULL): the
+ * device time of the render's kernels (CUDA events).  The call allocates
+ * its buffers on first use (kept by the context) and synchronises.
+ * Errors: VBGS_EINVAL (NULL ctx or camera, sizes outside 1..16384, a PSNR
+ * without a reference, non-finite camera, f <= 0), VBGS_ECUDA. */
+int vbgs_render(vbgs_ctx *ctx, const double *camera, int width, int height, float *image, const float *reference,
+                double *psnr, double *device_ms);
 
 /* No paper counterpart (failure handling).  Set the limit, in SM clock
  * cycles, of the bounded waits between the warp roles of the tensor-core

@@ -1,4 +1,4 @@
-"""Splat rendering of a fitted mixture and the PSNR of Sec. 4.1 --
+"""Splat rendering of a fitted mixture and the PSNR of Sec. 5.1 --
 TEST INFRASTRUCTURE ONLY.
 
 Only tests/, ``__graft_entry__.smoke()`` and bench.py's CPU-baseline /
@@ -7,11 +7,14 @@ library.
 
 The paper measures reconstruction quality as PSNR = 10 log10(255^2 / MSE)
 on held-out views, MSE the mean over all pixels and RGB channels of the
-squared differences of the two images on a 0..255 scale (Sec. 4.1); it does
+squared differences of the two images on a 0..255 scale (Sec. 5.1); it does
 not describe how the mixture is rendered.  Readings (each stated in the
 design notes):
 
-* every component is a splat at its spatial posterior mean m_s with the
+* every component that data has reached -- accumulated count N_k >= 1, at
+  least one point's worth of responsibility -- is a splat; the others hold
+  only the prior, which says nothing about the scene, and are left out;
+* a splat sits at its spatial posterior mean m_s with the
   expected spatial covariance E[Sigma_s] = W_s^-1 / (nu - d - 1) of its
   Wishart posterior (d = 6 for the joint model, taking the spatial block of
   W^-1; d = 3 for the split model's spatial block), its colour the colour
@@ -38,6 +41,7 @@ import numpy as np
 
 NEAR = 0.1
 LOW_PASS = 0.3
+MIN_COUNT = 1.0
 ALPHA_MAX = 0.99
 ALPHA_MIN = 1.0 / 255.0
 
@@ -91,10 +95,18 @@ def render(mu, Sigma, colour, cam: dict, opacity: float = ALPHA_MAX) -> np.ndarr
     return out.reshape(H, W, 3)
 
 
-def render_posterior(post: dict, cam: dict, d: int = 6, opacity: float = ALPHA_MAX) -> np.ndarray:
-    """Render a joint posterior (m K x 6, Winv K x 6 x 6, nu K)."""
-    m = np.asarray(post["m"], dtype=np.float64)
-    return render(m[:, :3], expected_spatial_cov(post["Winv"], post["nu"], d), m[:, 3:], cam, opacity)
+def drawn(counts) -> np.ndarray:
+    """Indices of the components that are splats: accumulated count >= 1."""
+    return np.flatnonzero(np.asarray(counts, dtype=np.float64) >= MIN_COUNT)
+
+
+def render_posterior(post: dict, cam: dict, counts, d: int = 6, opacity: float = ALPHA_MAX) -> np.ndarray:
+    """Render a joint posterior (m K x 6, Winv K x 6 x 6, nu K) whose
+    components have accumulated the counts N_k (K)."""
+    k = drawn(counts)
+    m = np.asarray(post["m"], dtype=np.float64)[k]
+    return render(m[:, :3], expected_spatial_cov(np.asarray(post["Winv"])[k], np.asarray(post["nu"])[k], d),
+                  m[:, 3:], cam, opacity)
 
 
 def psnr(img, ref) -> float:

@@ -368,6 +368,7 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
                                 ctx->d_tile_dirty + (ctx->K + 127) / 128, ctx->plan_epoch, &item_start, ctx->stream,
                                 &ctx->prof);
         ctx->plan_epoch = ctx->coef_epoch;
+        ctx->prof.p1_last.alloc_gen = ctx->alloc_gen;
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ctx->launches += l;
         l = launch_lse_merge_tc(ctx->d_part, N, item_start, lse, ctx->d_lse2f, ctx->d_lse_part,
@@ -845,6 +846,7 @@ void free_all(vbgs_ctx *ctx)
         for (void *p : pp)
             if (p) cudaFree(p);
     }
+    render_free(ctx->rb);
     if (ctx->side) cudaStreamSynchronize(ctx->side);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -1963,6 +1965,48 @@ int vbgs_check_frame(const double *dS, int K, const double *points, int64_t N, c
     if (e != cudaSuccess) return fail(nullptr, VBGS_ECUDA, "vbgs_check_frame: %s", cudaGetErrorString(e));
     *ok = fl[FL_CHECK] == 0;
     return VBGS_OK;
+}
+
+int vbgs_render(vbgs_ctx *ctx, const double *camera, int width, int height, float *image, const float *reference,
+                double *psnr, double *device_ms)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (!camera || width <= 0 || height <= 0 || width > 16384 || height > 16384 || (psnr && !reference))
+        return fail(ctx, VBGS_EINVAL, "vbgs_render: need a camera, 0 < width, height <= 16384, and a reference "
+                                      "image for the PSNR");
+    for (int i = 0; i < 13; i++)
+        if (!std::isfinite(camera[i])) return fail(ctx, VBGS_EINVAL, "vbgs_render: non-finite camera");
+    if (!(camera[12] > 0)) return fail(ctx, VBGS_EINVAL, "vbgs_render: the focal length must be positive");
+    int rc;
+    if ((rc = join_side(ctx))) return rc;
+    std::string why;
+    if (render_frame(ctx->d_m0, ctx->d_Spast, ctx->mp, ctx->mp.split ? 3 : 6, ctx->K, camera, width, height, ctx->rb,
+                     image, reference, psnr, device_ms, ctx->stream, why))
+        return fail(ctx, VBGS_ECUDA, "vbgs_render: %s", why.c_str());
+    return VBGS_OK;
+}
+
+int vbgs_profile_replay(vbgs_ctx *ctx, int reps, double *ms_per_launch, int64_t *pairs_per_launch)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (reps < 1 || !ms_per_launch) return fail(ctx, VBGS_EINVAL, "vbgs_profile_replay: need reps >= 1 and an output");
+    const Pass1Launch &L = ctx->prof.p1_last;
+    if (!is_tc(ctx) || !L.valid || L.alloc_gen != ctx->alloc_gen)
+        return fail(ctx, VBGS_EINVAL, "vbgs_profile_replay: no tensor-core pass-1 launch on the current buffers");
+    int rc;
+    if ((rc = join_side(ctx))) return rc;
+    unsigned long long *d_cnt = nullptr;
+    CU(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
+    CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), ctx->stream));
+    float ms = 0.f;
+    const int r = tc_replay_pass1(L, reps, d_cnt, ctx->stream, &ms);
+    unsigned long long pairs = 0;
+    const cudaError_t e = cudaMemcpy(&pairs, d_cnt, sizeof pairs, cudaMemcpyDeviceToHost);
+    cudaFree(d_cnt);
+    if (r || e != cudaSuccess) return fail(ctx, VBGS_ECUDA, "vbgs_profile_replay: replay failed");
+    *ms_per_launch = ms;
+    if (pairs_per_launch) *pairs_per_launch = (int64_t)pairs;
+    return check_flags(ctx);
 }
 
 int vbgs_set_wait_limit(long long cycles)

@@ -1848,6 +1848,27 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
     if (tc_set_attributes()) return -1;
     pf->begin(VBGS_PROF_PASS1, st);
     const int *lst = tmax ? list : nullptr;
+    {
+        Pass1Launch &L = pf->p1_last;
+        L.valid = true;
+        L.bf16 = bf16;
+        L.grid = target;
+        L.smem = smem;
+        L.Xhl = Xhl;
+        L.N = N;
+        L.K = K;
+        L.ntiles = ntiles;
+        L.tiles = tiles;
+        L.hdr = hdr;
+        L.list = lst;
+        L.item_tile = item_tile;
+        L.item_lo = item_lo;
+        L.item_hi = item_hi;
+        L.nitems = nitems;
+        L.part = part;
+        L.tmax = tmax;
+        L.flags = flags;
+    }
     if (bf16)
         launch_pdl(k_pass1_tc<true>, target, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
                                                            item_hi, nitems, part, tmax, flags, pairs1);
@@ -1868,6 +1889,32 @@ int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start
                minlse);
     pf->end(st);
     return launch_block_sum(lse_part, mb, sum_out, st, pf) < 0 ? -1 : 2;
+}
+
+int tc_replay_pass1(const Pass1Launch &L, int reps, unsigned long long *pairs, cudaStream_t st, float *ms)
+{
+    if (!L.valid || reps < 1) return -1;
+    auto launch = [&](unsigned long long *pc) {
+        if (L.bf16)
+            return launch_pdl(k_pass1_tc<true>, L.grid, kThreadsTC, L.smem, st, L.Xhl, L.N, L.K, L.tiles, L.hdr,
+                              L.ntiles, L.list, L.item_tile, L.item_lo, L.item_hi, L.nitems, L.part, L.tmax, L.flags,
+                              pc);
+        return launch_pdl(k_pass1_tc<false>, L.grid, kThreadsTC, L.smem, st, L.Xhl, L.N, L.K, L.tiles, L.hdr,
+                          L.ntiles, L.list, L.item_tile, L.item_lo, L.item_hi, L.nitems, L.part, L.tmax, L.flags, pc);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1;
+    bool ok = launch(pairs) == cudaSuccess && launch(nullptr) == cudaSuccess &&   // counted, then a warm-up
+              cudaEventRecord(e0, st) == cudaSuccess;
+    for (int r = 0; ok && r < reps; r++) ok = launch(nullptr) == cudaSuccess;
+    ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+    float t = 0.f;
+    ok = ok && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok) return -1;
+    *ms = t / (float)reps;
+    return 0;
 }
 
 int tc_set_wait_limit(long long cycles)

@@ -76,9 +76,27 @@ enum FlagSlot {
     FL_COUNT = 4
 };
 
+// Arguments of the last tensor-core pass-1 launch (vbgs_profile_replay).
+struct Pass1Launch {
+    bool valid = false, bf16 = false;
+    int grid = 0;
+    size_t smem = 0;
+    int64_t alloc_gen = -1;            // the context's allocation generation at the launch
+    const float *Xhl = nullptr;
+    int64_t N = 0;
+    int K = 0, ntiles = 0;
+    const unsigned char *tiles = nullptr;
+    const float *hdr = nullptr;
+    const int *list = nullptr, *item_tile = nullptr, *item_lo = nullptr, *item_hi = nullptr, *nitems = nullptr;
+    float2 *part = nullptr;
+    float *tmax = nullptr;
+    int *flags = nullptr;
+};
+
 // Per-kernel event timing (enabled by vbgs_profile_enable).  Launchers call
 // begin()/end() around each kernel; collect() runs after a stream sync.
 struct Prof {
+    Pass1Launch p1_last;
     bool on = false;
     unsigned mask = ~0u;                // classes timed (bit c)
     std::vector<cudaEvent_t> pool;
@@ -235,6 +253,11 @@ int launch_pass2_fp32(const EstepBuffers &B, int tpb, int tkc, cudaStream_t st, 
 // (FP16/BF16 hi/lo, 16 KB each, in the MMA's shared-memory layout) with a
 // 32-float frame header each, and pass 1 on tcgen05 with TMEM accumulators.
 size_t tc_tile_bytes(int K);
+// Relaunch a recorded pass-1 launch: once with the pair counter (zeroed by
+// the caller) to count its pairs, then reps times back to back (programmatic
+// dependent launch, as in the stream) between two events; *ms = mean time per
+// launch.  The launch is idempotent: it rewrites the same partials.
+int tc_replay_pass1(const Pass1Launch &L, int reps, unsigned long long *pairs, cudaStream_t st, float *ms);
 // Limit (SM cycles) of the waits between warp roles of the tensor-core
 // kernels on the current device; cycles <= 0 restores the default (~2 s).
 int tc_set_wait_limit(long long cycles);
@@ -324,6 +347,33 @@ void prop_init_centroids(const float *rec32, int K, float csc, float *cent, cuda
 void prop_sum_final(const double *part, int n, double *out, cudaStream_t st);
 int prop_exact_rows(const int *exact, int64_t N, SortBuffers &sb, unsigned int *skey, int *erows, cudaStream_t st);
 
+// Splat rendering (vbgs_render.cu): buffers grown on demand, kept by the context.
+struct RenderBuffers {
+    float4 *sp = nullptr;                       // K x 3 splat records
+    int4 *rect = nullptr;                       // K tile rectangles
+    long long *cnt = nullptr, *off = nullptr;   // K + 1 tile counts and their exclusive sums
+    unsigned long long *zkey = nullptr, *zkey_s = nullptr;
+    int *zidx = nullptr, *zidx_s = nullptr, *rank = nullptr;
+    unsigned long long *ekey = nullptr, *ekey_s = nullptr;   // (tile << 32 | depth rank) per covered tile
+    int *eval = nullptr, *eval_s = nullptr;
+    int2 *range = nullptr;                      // per tile: [first, last) of its sorted entries
+    float *img = nullptr, *ref = nullptr;
+    double *part = nullptr, *out = nullptr;
+    void *temp = nullptr;
+    size_t temp_bytes = 0;
+    size_t cap_sp = 0, cap_rect = 0, cap_cnt = 0, cap_off = 0, cap_zkey = 0, cap_zkey_s = 0, cap_zidx = 0,
+           cap_zidx_s = 0, cap_rank = 0, cap_ekey = 0, cap_ekey_s = 0, cap_eval = 0, cap_eval_s = 0, cap_range = 0,
+           cap_img = 0, cap_ref = 0, cap_part = 0, cap_out = 0;
+};
+// Render the posterior prior0 (+) S (K components; d = 6 joint, 3 split) at
+// the camera (o[3], Rwc[9] row-major camera-to-world, f) into image (host,
+// H x W x 3, may be null); with ref (host, H x W x 3) also the PSNR.
+// device_ms: event time of the render's kernels.  0 on success, -1 with why.
+int render_frame(const double *m0, const double *S, const MstepParams &P, int d, int K, const double *camera,
+                 int W, int H, RenderBuffers &B, float *image, const float *ref, double *psnr, double *device_ms,
+                 cudaStream_t st, std::string &why);
+void render_free(RenderBuffers &B);
+
 } // namespace vbgs
 
 // State of the learned proposal of a context (VBGS_FLAG_PROPOSAL).
@@ -392,6 +442,7 @@ struct vbgs_ctx {
     vbgs::BoxParams box{};
     vbgs::SortBuffers sb;
     vbgs::ReassignBuffers ra;
+    vbgs::RenderBuffers rb;
     int *d_kperm = nullptr, *d_kinv = nullptr, *d_pidx = nullptr;
     double *d_Xs = nullptr;          // staged points in Morton order
     float *d_tmax = nullptr, *d_minlse = nullptr;

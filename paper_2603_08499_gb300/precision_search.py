@@ -1,4 +1,4 @@
-"""Automatic mixed-precision search (Sec. 3.2): a precision map for the
+"""Automatic mixed-precision search (Sec. 4.2): a precision map for the
 operations of a staged computation f = f_L o ... o f_1 that minimises the
 measured latency T(f^Pi) subject to the relative error of Eq. relerr,
 err(Pi) = ||y^h - f^Pi(x)||_2 / max(||y^h||_2, tau) <= eps, against the

@@ -53,7 +53,8 @@ EXPORTS = [
     "vbgs_estep_noalloc", "vbgs_update_batched", "vbgs_autotune", "vbgs_get_tuning", "vbgs_set_tuning",
     "vbgs_proposal_report", "vbgs_proposal_weights", "vbgs_proposal_grad", "vbgs_proposal_clusters",
     "vbgs_proposal_bounds", "vbgs_kmeans", "vbgs_reassign", "vbgs_save_state", "vbgs_load_state",
-    "vbgs_check_frame", "vbgs_set_wait_limit", "vbgs_last_error", "vbgs_destroy",
+    "vbgs_check_frame", "vbgs_set_wait_limit", "vbgs_render", "vbgs_profile_replay", "vbgs_last_error",
+    "vbgs_destroy",
 ]
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 PROF_COUNT = 7
@@ -124,6 +125,8 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
     lib.vbgs_load_state.argtypes = [C.POINTER(C.c_void_p), C.c_char_p, C.POINTER(vbgs_options)]
     lib.vbgs_check_frame.argtypes = [_DP, C.c_int, _DP, C.c_int64, _DP, C.c_double, C.POINTER(C.c_int)]
     lib.vbgs_set_wait_limit.argtypes = [C.c_longlong]
+    lib.vbgs_render.argtypes = [C.c_void_p, _DP, C.c_int, C.c_int, _FP, _FP, _DP, _DP]
+    lib.vbgs_profile_replay.argtypes = [C.c_void_p, C.c_int, _DP, C.POINTER(C.c_int64)]
     return lib
 
 
@@ -316,6 +319,15 @@ def vbgs_profile_pairs(ctx) -> tuple[int, int]:
     return int(a.value), int(b.value)
 
 
+def vbgs_profile_replay(ctx, reps: int = 100) -> tuple[float, int]:
+    """(ms per launch, pairs per launch) of the last tensor-core pass-1
+    launch replayed reps times back to back."""
+    ms = np.zeros(1)
+    pairs = C.c_int64(0)
+    _check(lib().vbgs_profile_replay(ctx, int(reps), _dp(ms), C.byref(pairs)), ctx)
+    return float(ms[0]), int(pairs.value)
+
+
 def vbgs_probe_peaks(device: int = 0) -> dict:
     out = np.zeros(4)
     _check(lib().vbgs_probe_peaks(device, _dp(out)), None)
@@ -459,6 +471,31 @@ def vbgs_kmeans(points, centroids, lloyd_iters: int):
     return c, cl[:x.shape[0]]
 
 
+def camera_array(cam: dict) -> np.ndarray:
+    """The 13 doubles of vbgs_render's camera from a view dict (o, Rwc, f)."""
+    return np.concatenate([np.asarray(cam["o"], dtype=np.float64).ravel(),
+                           np.asarray(cam["Rwc"], dtype=np.float64).ravel(), [float(cam["f"])]])
+
+
+def vbgs_render(ctx, cam: dict, reference=None, want_image: bool = True):
+    """Render the posterior at a camera (dict with o, Rwc, f, width, height);
+    returns (image H x W x 3 float32 or None, PSNR against reference or None,
+    device ms)."""
+    W, H = int(cam["width"]), int(cam["height"])
+    c = camera_array(cam)
+    img = np.zeros((H, W, 3), dtype=np.float32) if want_image else None
+    ref = None
+    if reference is not None:
+        ref = np.ascontiguousarray(reference, dtype=np.float32)
+        if ref.shape != (H, W, 3):
+            raise ValueError(f"reference must be {H} x {W} x 3")
+    p = np.zeros(1)
+    ms = np.zeros(1)
+    _check(lib().vbgs_render(ctx, _dp(c), W, H, _fp(img), _fp(ref), _dp(p) if ref is not None else None, _dp(ms)),
+           ctx)
+    return img, (float(p[0]) if ref is not None else None), float(ms[0])
+
+
 def vbgs_set_wait_limit(cycles: int) -> None:
     """Limit (SM cycles) of the waits between warp roles of the tensor-core
     kernels on the current device; <= 0 restores the default."""
@@ -500,6 +537,9 @@ class Model:
 
     def save(self, path: str) -> None:
         vbgs_save_state(self.ctx, path)
+
+    def render(self, cam: dict, reference=None, want_image: bool = True):
+        return vbgs_render(self.ctx, cam, reference, want_image)
 
     def update(self, points, n_iters: int) -> np.ndarray:
         return vbgs_update(self.ctx, points, n_iters)

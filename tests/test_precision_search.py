@@ -1,4 +1,4 @@
-"""The three-pass mixed-precision search (Sec. 3.2) on CPU: hand-built error
+"""The three-pass mixed-precision search (Sec. 4.2) on CPU: hand-built error
 and latency models whose answers follow from the passes' definitions, the
 error constraint on random graphs, and a staged numpy computation shaped like
 compute_elbo_delta (differences, triangular solve, quadratic form, logit,

@@ -88,3 +88,22 @@ def test_psnr_closed_forms():
     assert RD.psnr(a, a) == float("inf")
     assert abs(RD.psnr(a, a + 0.1) - 20.0) < 1e-9                       # -20 log10(0.1)
     assert abs(RD.psnr(a, a - 1 / 255) - 20 * np.log10(255.0)) < 1e-9   # one grey level everywhere
+
+
+def test_only_components_with_data_are_drawn():
+    """render_posterior draws exactly the components whose accumulated count
+    is at least one point: one below (0.999) leaves the image as without it,
+    one at 1.0 changes it; the posterior's own values are used unchanged."""
+    cam = _cam()
+    K = 3
+    post = {"m": np.array([[0.0, 0.0, 2.0, 1.0, 0.0, 0.0], [0.05, 0.0, 2.5, 0.0, 1.0, 0.0],
+                           [-0.05, 0.0, 3.0, 0.0, 0.0, 1.0]]),
+            "Winv": np.array([np.eye(6) * 0.01 * (i + 1) for i in range(K)]), "nu": np.full(K, 12.0)}
+    full = RD.render_posterior(post, cam, np.array([5.0, 1.0, 2.0]))
+    cov = RD.expected_spatial_cov(post["Winv"], post["nu"], 6)
+    assert np.array_equal(full, RD.render(post["m"][:, :3], cov, post["m"][:, 3:], cam))
+    part = RD.render_posterior(post, cam, np.array([5.0, 0.999, 2.0]))
+    keep = [0, 2]
+    assert np.array_equal(part, RD.render(post["m"][keep, :3], cov[keep], post["m"][keep, 3:], cam))
+    assert not np.allclose(part, full)
+    assert np.all(RD.render_posterior(post, cam, np.zeros(K)) == 0.0)
