@@ -513,8 +513,10 @@ def proposal_measure(V, form, n_warm, n_steps, stream, flush, log_frames=False):
     frames = make_frames(n_warm + n_steps, seed=5)
     dev = [torch.from_numpy(X).cuda() for X in frames]
     out = {}
-    for name, flags in (("proposal", V.VBGS_FLAG_PROPOSAL), ("full", 0)):
+    for name, flags in (("proposal", V.VBGS_FLAG_PROPOSAL), ("frozen", V.VBGS_FLAG_PROPOSAL), ("full", 0)):
         m = V.Model(prior, form, cuda_stream=stream.cuda_stream, flags=flags)
+        if name == "frozen":
+            V.vbgs_proposal_config(m.ctx, 0, 3e-3)      # the same network, never trained
         times, pairs, reps, traces = [], 0, [], []
         for t, X in enumerate(dev):
             if t == len(dev) - 1:
@@ -533,10 +535,11 @@ def proposal_measure(V, form, n_warm, n_steps, stream, flush, log_frames=False):
                 traces.append(tr)
                 if flags:
                     reps.append(V.vbgs_proposal_report(m.ctx))
+        keep = name == "proposal"
         out[name] = {"value": pairs / sum(times), "ms_per_frame": 1e3 * sum(times) / len(times), "reps": reps,
                      "state_before_last": state_before_last, "final": m.stats(), "traces": traces,
-                     "model": m if flags else None}
-        if not flags:
+                     "model": m if keep else None}
+        if not keep:
             m.close()
     # one-frame error: the trained proposal model from the full form's state
     mp = out["proposal"]["model"]
@@ -553,6 +556,12 @@ def proposal_measure(V, form, n_warm, n_steps, stream, flush, log_frames=False):
     dS64 = m64.stats() - S0
     m64.close()
     rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+    def cand_stats(reps_):
+        live = [r for r in reps_ if not r["frame_exact"]]
+        n = max(sum(r["points"] for r in live), 1)
+        return {"candidate_pair_fraction": float(sum(r["cand_pairs"] for r in live) / (n * K_PROP)),
+                "clusters_added_per_point": float(sum(r["added_clusters"] for r in live) / n)}
 
     def err_vs(tr_a, dS_a):
         sel = dS64[:, 0] >= 1.0
@@ -581,6 +590,12 @@ def proposal_measure(V, form, n_warm, n_steps, stream, flush, log_frames=False):
             "elbo": rel(tr, out["full"]["traces"][-1]), "N": rel(dS[:, 0], dS0[:, 0]),
             "S1": rel(dS[:, 1:7], dS0[:, 1:7]), "S2": rel(dS[:, 7:], dS0[:, 7:]),
             "what": "last frame, 3 iterations, proposal model from the full form's state before it"},
+        "ablation_trained_vs_frozen_network": {
+            "trained": dict(cand_stats(out["proposal"]["reps"]), ms_per_frame=out["proposal"]["ms_per_frame"],
+                            train_loss_last=reps[-1]["train_loss"]),
+            "frozen": dict(cand_stats(out["frozen"]["reps"]), ms_per_frame=out["frozen"]["ms_per_frame"]),
+            "what": ("the same stream with the network trained online (8 epochs per frame, Adam 3e-3) and frozen at "
+                     "its initial weights, the same certificate expansion; timed frames")},
         "one_frame_error_vs_fp64": {
             "proposal": err_vs(tr, dS), form + "_full_estep": err_vs(out["full"]["traces"][-1], dS0),
             "what": ("last frame, 3 iterations, from the full form's state before it, against the FP64 form (Eq. "
@@ -720,7 +735,7 @@ def run_ours(args):
 
     if rank == 0 and not args.no_proposal:
         try:
-            extra["proposal"] = proposal_measure(V, form, 3, 12, stream, flush)
+            extra["proposal"] = proposal_measure(V, form, 20, 10, stream, flush)
         except Exception as exc:   # reported, never fatal to the headline line
             extra["proposal"] = {"error": f"{type(exc).__name__}: {exc}"}
 

@@ -186,9 +186,11 @@ int vbgs_set_tuning(vbgs_ctx *ctx, int pass1_tiles, int pass2_chunks);
  * A certified bound of the responsibility mass outside them sends points
  * above 1e-3 to the exact E-step, as does a seeded 1% audit sample, which
  * measures the true missed mass; a frame with more than 20% such points runs
- * exact.  The network is trained on the GPU (forward, backward, Adam lr 1e-3,
- * minibatches of 4096, one epoch per frame) on the cluster masses of the exact
- * E-steps of each frame.
+ * exact.  The network is trained on the GPU (forward, backward, Adam lr 3e-3,
+ * minibatches of up to 4096 points dealt round-robin from the frame's up to
+ * 16,384 labelled points, 8 epochs per frame by default; the GEMMs on the
+ * tensor cores, BF16 operands with activations split hi/lo, FP32
+ * accumulation) on the cluster masses of the exact E-steps of each frame.
  * vbgs_proposal_report fills out[11]: candidate pairs scored, fallback
  * points, audit points, audit max and mean missed mass, frame ran exact
  * (0/1), mean training loss of the last epoch, frames trained, pairs of the
@@ -210,6 +212,12 @@ int vbgs_set_tuning(vbgs_ctx *ctx, int pass1_tiles, int pass2_chunks);
  * frame.  The proposal is host-driven (one synchronisation per iteration)
  * and is not available in vbgs_update_batched. */
 int vbgs_proposal_report(vbgs_ctx *ctx, double *out);
+/* No paper counterpart: the proposal network's training schedule -- epochs
+ * over each frame's labelled points (0: the network is not trained; it keeps
+ * its initial or loaded weights) and the Adam learning rate.  Defaults: 8
+ * epochs, 3e-3.  Errors: VBGS_EINVAL (no proposal, epochs outside 0..1000,
+ * learning_rate outside (0, 1)). */
+int vbgs_proposal_config(vbgs_ctx *ctx, int epochs, double learning_rate);
 int vbgs_proposal_weights(vbgs_ctx *ctx, float *get, const float *set);
 int vbgs_proposal_grad(vbgs_ctx *ctx, const float *inputs, const float *labels, int B, float *loss, float *grad,
                        int *top);

@@ -397,15 +397,14 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
 // ---------------------------------------------------------------------------
 // Learned proposal (host side).  Constants of the method: G = 1024 clusters,
 // top-4 proposals, missed-mass threshold 1e-3, 1% audit, a frame with more
-// than 20% fallback points runs exact, 2 Lloyd iterations per refresh, Adam
-// lr 1e-3, minibatches of 4096, one epoch over each frame's labelled points.
+// than 20% fallback points runs exact, 2 Lloyd iterations per refresh;
+// training by default 8 epochs (Adam, lr 3e-3) of minibatches of up to 4096
+// over each frame's labelled points (vbgs_proposal_config).
 // ---------------------------------------------------------------------------
 constexpr int kPG = VBGS_PROP_CLUSTERS, kPTop = VBGS_PROP_TOP, kMB = 4096, kHid = 128;
 constexpr float kPropThresh = 1e-3f;
 constexpr uint32_t kAuditPerMille = 10;
 constexpr double kExactFrameFrac = 0.2;
-constexpr float kPropLr = 1e-3f;
-constexpr int kPropEpochs = 2;
 constexpr int64_t kPropTrainPoints = 16384;
 constexpr int kPropRounds = 6;   // candidate rounds: the top 4, then up to 8 clusters per round; the last adds none
 constexpr size_t kOffB1 = 128 * 6, kOffW2 = kOffB1 + 128, kOffB2 = kOffW2 + 128 * 128, kOffW3 = kOffB2 + 128,
@@ -462,6 +461,15 @@ int prop_alloc(vbgs_ctx *ctx)
         (rc = dalloc(ctx, &P.pstart, (size_t)kPG + 1)) || (rc = dalloc(ctx, &P.item_start, (size_t)kPG + 1)) ||
         (rc = dalloc(ctx, &P.fbase, (size_t)kPG + 1)))
         return rc;
+    {
+        // split-K partials of the largest GEMMs of a minibatch
+        const size_t gneed = std::max({mlp_gemm_part_floats(kPG, kHid, kMB), mlp_gemm_part_floats(kMB, kHid, kPG),
+                                       mlp_gemm_part_floats(kHid, kHid, kMB), mlp_gemm_part_floats(kHid, 6, kMB),
+                                       mlp_gemm_part_floats(kMB, kHid, kHid), mlp_gemm_part_floats(kMB, kPG, kHid),
+                                       mlp_gemm_part_floats(kMB, kHid, 6), (size_t)1});
+        if ((rc = dalloc(ctx, &P.gpart, gneed))) return rc;
+        P.gpart_cap = gneed;
+    }
     P.nparam = kNParam;
     // He-uniform initial weights from a fixed seed, zero biases
     std::vector<float> w(kNParam, 0.f);
@@ -534,9 +542,15 @@ void mlp_forward(vbgs_ctx *ctx, const float *Xin, int B)
 {
     PropState &P = ctx->prop;
     const float *q = P.wq;
-    prop_gemm(B, kHid, 6, Xin, 6, 1, q, 1, 6, P.h1, kHid, q + kOffB1, true, false, ctx->stream);
-    prop_gemm(B, kHid, kHid, P.h1, kHid, 1, q + kOffW2, 1, kHid, P.h2, kHid, q + kOffB2, true, false, ctx->stream);
-    prop_gemm(B, kPG, kHid, P.h2, kHid, 1, q + kOffW3, 1, kHid, P.z, kPG, q + kOffB3, false, false, ctx->stream);
+    float *gp = P.gpart;
+    const size_t gc = P.gpart_cap;
+    int *fl = ctx->d_flags;
+    ctx->launches += prop_gemm(B, kHid, 6, Xin, 6, 1, q, 1, 6, true, P.h1, kHid, q + kOffB1, true, false, gp, gc, fl,
+                               ctx->stream);
+    ctx->launches += prop_gemm(B, kHid, kHid, P.h1, kHid, 1, q + kOffW2, 1, kHid, true, P.h2, kHid, q + kOffB2, true,
+                               false, gp, gc, fl, ctx->stream);
+    ctx->launches += prop_gemm(B, kPG, kHid, P.h2, kHid, 1, q + kOffW3, 1, kHid, true, P.z, kPG, q + kOffB3, false,
+                               false, gp, gc, fl, ctx->stream);
 }
 
 // dz (= dLoss/dlogits) -> parameter gradients of the minibatch
@@ -545,16 +559,26 @@ void mlp_backward(vbgs_ctx *ctx, const float *Xin, int B)
     PropState &P = ctx->prop;
     const float *q = P.wq;
     float *g = P.grad;
-    prop_gemm(kPG, kHid, B, P.dz, 1, kPG, P.h2, kHid, 1, g + kOffW3, kHid, nullptr, false, false, ctx->stream);
-    prop_colsum(P.dz, B, kPG, g + kOffB3, ctx->stream);
-    prop_gemm(B, kHid, kPG, P.dz, kPG, 1, q + kOffW3, kHid, 1, P.dh2, kHid, nullptr, false, false, ctx->stream);
-    prop_relu_bwd(P.dh2, P.h2, (size_t)B * kHid, ctx->stream);
-    prop_gemm(kHid, kHid, B, P.dh2, 1, kHid, P.h1, kHid, 1, g + kOffW2, kHid, nullptr, false, false, ctx->stream);
-    prop_colsum(P.dh2, B, kHid, g + kOffB2, ctx->stream);
-    prop_gemm(B, kHid, kHid, P.dh2, kHid, 1, q + kOffW2, kHid, 1, P.dh1, kHid, nullptr, false, false, ctx->stream);
-    prop_relu_bwd(P.dh1, P.h1, (size_t)B * kHid, ctx->stream);
-    prop_gemm(kHid, 6, B, P.dh1, 1, kHid, Xin, 6, 1, g, 6, nullptr, false, false, ctx->stream);
-    prop_colsum(P.dh1, B, kHid, g + kOffB1, ctx->stream);
+    float *gp = P.gpart;
+    const size_t gc = P.gpart_cap;
+    int *fl = ctx->d_flags;
+    cudaStream_t st = ctx->stream;
+    int l = 0;
+    l += prop_gemm(kPG, kHid, B, P.dz, 1, kPG, P.h2, kHid, 1, false, g + kOffW3, kHid, nullptr, false, false, gp, gc,
+                   fl, st);
+    prop_colsum(P.dz, B, kPG, g + kOffB3, st);
+    l += prop_gemm(B, kHid, kPG, P.dz, kPG, 1, q + kOffW3, kHid, 1, true, P.dh2, kHid, nullptr, false, false, gp, gc,
+                   fl, st);
+    prop_relu_bwd(P.dh2, P.h2, (size_t)B * kHid, st);
+    l += prop_gemm(kHid, kHid, B, P.dh2, 1, kHid, P.h1, kHid, 1, false, g + kOffW2, kHid, nullptr, false, false, gp,
+                   gc, fl, st);
+    prop_colsum(P.dh2, B, kHid, g + kOffB2, st);
+    l += prop_gemm(B, kHid, kHid, P.dh2, kHid, 1, q + kOffW2, kHid, 1, true, P.dh1, kHid, nullptr, false, false, gp,
+                   gc, fl, st);
+    prop_relu_bwd(P.dh1, P.h1, (size_t)B * kHid, st);
+    l += prop_gemm(kHid, 6, B, P.dh1, 1, kHid, Xin, 6, 1, false, g, 6, nullptr, false, false, gp, gc, fl, st);
+    prop_colsum(P.dh1, B, kHid, g + kOffB1, st);
+    ctx->launches += l + 5;
 }
 
 // Proposal of the frame: top-4 clusters of every (sorted) point.
@@ -566,7 +590,7 @@ int prop_propose(vbgs_ctx *ctx, const double *X, int64_t N)
         prop_inputs(X + off * VBGS_XS, nullptr, 1, B, ctx->box, P.Xin, ctx->stream);
         mlp_forward(ctx, P.Xin, B);
         prop_softmax_top(P.z, B, nullptr, nullptr, P.top + off * kPTop, nullptr, ctx->stream);
-        ctx->launches += 5;
+        ctx->launches += 2;   // inputs and top-4; mlp_forward counts its GEMMs
     }
     return cudaGetLastError() == cudaSuccess ? VBGS_OK : fail(ctx, VBGS_ECUDA, "proposal inference failed");
 }
@@ -575,18 +599,19 @@ int prop_propose(vbgs_ctx *ctx, const double *X, int64_t N)
 int prop_train(vbgs_ctx *ctx)
 {
     PropState &P = ctx->prop;
-    if (P.n_lab <= 0) return VBGS_OK;
+    if (P.n_lab <= 0 || P.epochs <= 0) return VBGS_OK;
     CU(cudaMemsetAsync(P.loss, 0, sizeof(float) * 2, ctx->stream));
-    for (int epoch = 0; epoch < kPropEpochs; epoch++) {
-        if (epoch == kPropEpochs - 1) CU(cudaMemsetAsync(P.loss, 0, sizeof(float) * 2, ctx->stream));
-        for (int64_t off = 0; off < P.n_lab; off += kMB) {
-            const int B = (int)std::min<int64_t>(kMB, P.n_lab - off);
+    for (int epoch = 0; epoch < P.epochs; epoch++) {
+        if (epoch == P.epochs - 1) CU(cudaMemsetAsync(P.loss, 0, sizeof(float) * 2, ctx->stream));
+        for (int64_t b = 0; b < P.lab_nb; b++) {
+            const int64_t off = b * P.lab_S;
+            const int B = (int)((P.n_lab - b + P.lab_nb - 1) / P.lab_nb);   // samples b, b + nb, ...
             const float *Xin = P.Xin + off * 6;
             mlp_forward(ctx, Xin, B);
             prop_softmax_top(P.z, B, P.Q + off * kPG, P.dz, nullptr, P.loss, ctx->stream);
             mlp_backward(ctx, Xin, B);
-            prop_adam(P.w, P.wq, P.am, P.av, P.grad, kNParam, kPropLr, ++P.step, ctx->stream);
-            ctx->launches += 15;
+            prop_adam(P.w, P.wq, P.am, P.av, P.grad, kNParam, P.lr, ++P.step, ctx->stream);
+            ctx->launches += 2;   // softmax and Adam; the forward and backward count theirs
         }
     }
     P.frames_trained++;
@@ -604,9 +629,13 @@ void prop_label(vbgs_ctx *ctx, const double *X, const double *lse, int64_t n, co
     PropState &P = ctx->prop;
     const int64_t stride = std::max<int64_t>((n + kPropTrainPoints - 1) / kPropTrainPoints, 1);
     const int64_t m = (n + stride - 1) / stride;
-    prop_labels(X, lse, rows, stride, m, ctx->d_rec32, P.order, P.cstart, P.ub, P.Q, ctx->stream);
-    prop_inputs(X, nullptr, stride, m, ctx->box, P.Xin, ctx->stream);
+    // minibatch b takes samples b, b + nb, ...: every minibatch spans the frame
+    const int64_t nb = std::max<int64_t>((m + kMB - 1) / kMB, 1), S = (m + nb - 1) / nb;
+    prop_labels(X, lse, rows, stride, m, ctx->d_rec32, P.order, P.cstart, P.ub, P.Q, ctx->stream, nb, S);
+    prop_inputs(X, nullptr, stride, m, ctx->box, P.Xin, ctx->stream, nb, S);
     P.n_lab = m;
+    P.lab_nb = nb;
+    P.lab_S = S;
     ctx->launches += 2;
 }
 
@@ -842,7 +871,7 @@ void free_all(vbgs_ctx *ctx)
         void *pp[] = {P.cent, P.kpts, P.cpar, P.cscr, P.mscr, P.ub, P.order, P.cstart, P.skey, P.w, P.wq, P.am, P.av, P.grad, P.top, P.cand,
                       P.exact, P.erows, P.plist, P.pstart, P.pkey, P.ekey, P.lse_c, P.Xe, P.lse_e, P.lsum, P.bound,
                       P.audit, P.counters, P.Xin, P.Q, P.h1, P.h2, P.z, P.dz, P.dh2, P.dh1, P.loss,
-                      P.item_start, P.fbase, P.part2, P.apart, P.ncand, P.pend, P.run, P.cpart};
+                      P.item_start, P.fbase, P.part2, P.apart, P.ncand, P.pend, P.run, P.cpart, P.gpart};
         for (void *p : pp)
             if (p) cudaFree(p);
     }
@@ -1169,6 +1198,16 @@ extern "C" int vbgs_proposal_grad(vbgs_ctx *ctx, const float *inputs, const floa
     return VBGS_OK;
 }
 
+extern "C" int vbgs_proposal_config(vbgs_ctx *ctx, int epochs, double learning_rate)
+{
+    if (!ctx || !ctx->prop.on) return fail(ctx, VBGS_EINVAL, "the context has no proposal");
+    if (epochs < 0 || epochs > 1000 || !(learning_rate > 0) || !(learning_rate < 1))
+        return fail(ctx, VBGS_EINVAL, "vbgs_proposal_config: need 0 <= epochs <= 1000 and 0 < learning_rate < 1");
+    ctx->prop.epochs = epochs;
+    ctx->prop.lr = (float)learning_rate;
+    return VBGS_OK;
+}
+
 extern "C" int vbgs_proposal_clusters(vbgs_ctx *ctx, float *centroids, int *cluster_of)
 {
     if (!ctx || !ctx->prop.on) return fail(ctx, VBGS_EINVAL, "the context has no proposal");
@@ -1304,7 +1343,8 @@ constexpr int32_t kStateVersion = 1;
 struct StateHeader {
     char magic[8];
     int32_t version, K, D, precision, flags, has_prop, next_prior_ready, coef_epoch, plan_epoch, tune_p1, tune_p2,
-        prop_step, prop_centroids_ready, n_sections;
+        prop_step, prop_centroids_ready, n_sections, prop_epochs;
+    float prop_lr;
     int64_t prop_frames_trained;
     uint64_t prop_frame, seed;
     double alpha0, beta0, nu0, W0[36], box_lo[3], box_inv_ext[3];
@@ -1788,6 +1828,8 @@ int vbgs_save_state(vbgs_ctx *ctx, const char *path)
     h.tune_p2 = ctx->tune_p2;
     h.prop_step = ctx->prop.step;
     h.prop_centroids_ready = ctx->prop.centroids_ready ? 1 : 0;
+    h.prop_epochs = ctx->prop.epochs;
+    h.prop_lr = ctx->prop.lr;
     h.prop_frames_trained = ctx->prop.frames_trained;
     h.prop_frame = ctx->prop.frame;
     h.seed = ctx->seed;
@@ -1922,6 +1964,8 @@ int vbgs_load_state(vbgs_ctx **out, const char *path, const vbgs_options *opt)
     if (ctx->prop.on) {
         ctx->prop.step = h.prop_step;
         ctx->prop.centroids_ready = h.prop_centroids_ready != 0;
+        ctx->prop.epochs = h.prop_epochs;
+        ctx->prop.lr = h.prop_lr;
         ctx->prop.frames_trained = h.prop_frames_trained;
         ctx->prop.rep[7] = (double)h.prop_frames_trained;
         ctx->prop.frame = h.prop_frame;

@@ -30,6 +30,7 @@
 // (8-row group) stride 512 B.  Coefficient tiles are built in global memory
 // in exactly this layout so one bulk copy stages them.
 #include "vbgs_internal.cuh"
+#include "vbgs_tc.cuh"
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <algorithm>
@@ -63,31 +64,6 @@ struct __align__(1024) Smem {
     unsigned int tmem_base;
 };
 
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long *b)
-{
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, uint32_t bytes)
-{
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(su32(b)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(su32(b)), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
 // Bounded wait on a barrier phase; false on timeout.  A normal wait (one
 // warp role waiting for another) gives up after g_wait_limit cycles, or as
 // soon as another thread of the grid has timed out; a drain wait (for copies
@@ -134,33 +110,6 @@ __host__ __device__ constexpr uint32_t idesc_f16()
            ((uint32_t)(kRows >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-                 "l"(a), "l"(b), "r"(idesc), "r"(acc)
-                 : "memory");
-}
-__device__ __forceinline__ void mma_commit(unsigned long long *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar)) : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                 "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                 : "r"(taddr)
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float ex2f(float x)
 {
@@ -1064,21 +1013,6 @@ struct __align__(128) Smem2 {
     unsigned int tmem_base;
 };
 
-__device__ __forceinline__ uint64_t smem_desc_sbo(const void *p, uint32_t sbo)
-{
-    const uint32_t a = su32(p);
-    uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(128u >> 4) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-template <bool BF16>
-__host__ __device__ constexpr uint32_t idesc_mn(int M, int Ncols)
-{
-    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((uint32_t)(Ncols >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
 __device__ __forceinline__ int b1_off(int pt, int f) { return (pt >> 3) * 512 + (f >> 3) * 128 + (pt & 7) * 16 + (f & 7) * 2; }
 __device__ __forceinline__ int b2_off(int f, int pt) { return (f >> 3) * 1024 + (pt >> 3) * 128 + (f & 7) * 16 + (pt & 7) * 2; }
 __device__ __forceinline__ int p_off(int m, int pt) { return (m >> 3) * 1024 + (pt >> 3) * 128 + (m & 7) * 16 + (pt & 7) * 2; }

@@ -308,14 +308,24 @@ void prop_bounds(const double *X, int64_t N, const float *cpar, float *UB, cudaS
 size_t prop_cpar_floats();
 size_t prop_cscr_doubles();
 size_t prop_mscr_floats(int K);
-void prop_gemm(int M, int N, int K, const float *A, int sam, int sak, const float *B, int sbk, int sbn, float *C,
-               int ldc, const float *bias, bool relu, bool accumulate, cudaStream_t st);
+// The network's GEMMs: C = act(A B^T + bias) (+ C) on the tensor cores
+// (vbgs_mlp_tc.cu); B(n, k) = B[n * sbn + k * sbk]; exact_b: B holds BF16
+// values (the weights), else it is split hi/lo like A.  part: split-K
+// workspace (mlp_gemm_part_floats).  Returns the launches, -1 on failure.
+int prop_gemm(int M, int N, int K, const float *A, int sam, int sak, const float *B, int sbk, int sbn, bool exact_b,
+              float *C, int ldc, const float *bias, bool relu, bool accumulate, float *part, size_t part_floats,
+              int *flags, cudaStream_t st);
+int mlp_gemm_tc(int M, int N, int K, const float *A, int sam, int sak, bool split_a, const float *B, int sbn,
+                int sbk, bool split_b, float *C, int ldc, const float *bias, bool relu, bool accumulate, float *part,
+                size_t part_floats, int *flags, cudaStream_t st);
+size_t mlp_gemm_part_floats(int M, int N, int K);
 void prop_colsum(const float *X, int M, int Nc, float *out, cudaStream_t st);
 void prop_relu_bwd(float *dH, const float *H, size_t n, cudaStream_t st);
 void prop_softmax_top(const float *Z, int B, const float *Q, float *dZ, int *top, float *loss_sum, cudaStream_t st);
 void prop_adam(float *w, float *wq, float *m, float *v, const float *g, size_t n, float lr, int step, cudaStream_t st);
+// nb, S: deal the samples round-robin into nb minibatches of stride S (1, 0: in order)
 void prop_inputs(const double *X, const int *rows, int64_t rstride, int64_t n, const BoxParams &box, float *out,
-                 cudaStream_t st);
+                 cudaStream_t st, int64_t nb = 1, int64_t S = 0);
 void prop_cand_init(const int *top, int64_t N, int *cand, int *ncand, int *pend, float2 *run, float2 *part,
                     cudaStream_t st);
 int prop_pend_lists(const int *cand, const int *ncand, const int *pend, int64_t N, SortBuffers &sb,
@@ -336,7 +346,8 @@ void prop_cand_pass2(const double *X, const double *lse_c, const float *rec32, c
                      const unsigned int *skey, int K, const int *pstart, const int *plist, const int *item_start,
                      const long long *fbase, int n_items, float *part, const int *kperm, double *dS, cudaStream_t st);
 void prop_labels(const double *Xe, const double *lse_e, const int *rows, int64_t rstride, int64_t ne,
-                 const float *rec32, const int *order, const int *cstart, const float *UB, float *Q, cudaStream_t st);
+                 const float *rec32, const int *order, const int *cstart, const float *UB, float *Q, cudaStream_t st,
+                 int64_t nb, int64_t S);
 size_t prop_audit_floats(int64_t ne, int K);
 void prop_audit(const double *X, const int *erows, int64_t ne, const int *exact, const double *lse_c,
                 const float *rec32, int K, float *scratch, float *audit_missed, cudaStream_t st);
@@ -349,7 +360,7 @@ int prop_exact_rows(const int *exact, int64_t N, SortBuffers &sb, unsigned int *
 
 // Splat rendering (vbgs_render.cu): buffers grown on demand, kept by the context.
 struct RenderBuffers {
-    float4 *sp = nullptr;                       // K x 3 splat records
+    float4 *sp = nullptr;                       // K splat records of 4 float4
     int4 *rect = nullptr;                       // K tile rectangles
     long long *cnt = nullptr, *off = nullptr;   // K + 1 tile counts and their exclusive sums
     unsigned long long *zkey = nullptr, *zkey_s = nullptr;
@@ -396,8 +407,13 @@ struct PropState {
     // network: [W1 128x6 | b1 128 | W2 128x128 | b2 128 | W3 1024x128 | b3 1024]
     size_t nparam = 0;
     float *w = nullptr, *wq = nullptr, *am = nullptr, *av = nullptr, *grad = nullptr;
+    float *gpart = nullptr;          // split-K partials of the GEMMs
+    size_t gpart_cap = 0;
     int step = 0;
     int64_t frames_trained = 0;
+    int epochs = 8;                  // training epochs per frame (0: the network is not trained)
+    float lr = 3e-3f;                // Adam learning rate
+    int64_t lab_nb = 1, lab_S = 0;   // minibatches of the frame's labelled points and their slot stride
     // per frame
     int64_t ncap = 0;
     int *top = nullptr, *cand = nullptr, *exact = nullptr, *erows = nullptr, *plist = nullptr, *pstart = nullptr;

@@ -492,55 +492,6 @@ __global__ void __launch_bounds__(128) k_bounds(const double *__restrict__ X, in
 }
 
 // ------------------------------------------------------------------ MLP -----
-// Generic tiled FP32 GEMM with strides: C[m][n] = act(sum_k A[m][k] B[k][n] + bias[n]) (+ C if accumulate).
-// A(m,k) = A[m * sam + k * sak], B(k,n) = B[k * sbk + n * sbn], C row-major ldc.
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float *__restrict__ A, int sam, int sak,
-                                              const float *__restrict__ B, int sbk, int sbn, float *__restrict__ C,
-                                              int ldc, const float *__restrict__ bias, int relu, int accumulate)
-{
-    __shared__ float As[16][65];
-    __shared__ float Bs[16][65];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    // tile loads walk the operand's unit-stride dimension across threads
-    const bool a_kfast = (sak == 1), b_nfast = (sbn == 1);
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
-            const int kk = a_kfast ? (i & 15) : (i >> 6), mm = a_kfast ? (i >> 4) : (i & 63);
-            const int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? A[(size_t)m * sam + (size_t)k * sak] : 0.f;
-            const int kb = b_nfast ? (i >> 6) : (i & 15), nn = b_nfast ? (i & 63) : (i >> 4);
-            const int n = n0 + nn, k2 = k0 + kb;
-            Bs[kb][nn] = (n < N && k2 < K) ? B[(size_t)k2 * sbk + (size_t)n * sbn] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; kk++) {
-            float a[4], bb[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) { a[i] = As[kk][ty * 4 + i]; bb[i] = Bs[kk][tx * 4 + i]; }
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
-            if (m < M && n < N) {
-                float v = acc[i][j] + (bias ? bias[n] : 0.f);
-                if (relu) v = fmaxf(v, 0.f);
-                float *c = C + (size_t)m * ldc + n;
-                *c = accumulate ? *c + v : v;
-            }
-        }
-}
-
 // Column sums (bias gradients): out[n] = sum_m X[m][n]; a block per 32
 // columns, 8 row phases reduced in a fixed order.
 __global__ void __launch_bounds__(256) k_colsum(const float *__restrict__ X, int M, int Nc, float *__restrict__ out)
@@ -643,17 +594,26 @@ __global__ void k_adam(float *__restrict__ w, float *__restrict__ wq, float *__r
 }
 
 // Network inputs: positions mapped to [-1, 1] by the Morton box, colours to [-1, 1].
+// Slot of sample i when the samples are dealt round-robin into nb minibatches
+// of stride S (minibatch b holds samples b, b + nb, ...: each spans the whole
+// frame instead of one region of its Morton order); nb = 1: slot i.
+__device__ __forceinline__ int64_t deal_slot(int64_t i, int64_t nb, int64_t S)
+{
+    return nb > 1 ? (i % nb) * S + i / nb : i;
+}
+
 __global__ void k_mlp_inputs(const double *__restrict__ X, const int *__restrict__ rows, int64_t rstride, int64_t n,
-                             BoxParams box, float *__restrict__ out)
+                             BoxParams box, int64_t nb, int64_t S, float *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t r = rows ? rows[i] : i * rstride;
     const double *x = X + r * VBGS_XS;
+    float *o = out + deal_slot(i, nb, S) * 6;
 #pragma unroll
-    for (int q = 0; q < 3; q++) out[i * 6 + q] = (float)((x[q] - box.lo[q]) * box.inv_ext[q] * 2.0 - 1.0);
+    for (int q = 0; q < 3; q++) o[q] = (float)((x[q] - box.lo[q]) * box.inv_ext[q] * 2.0 - 1.0);
 #pragma unroll
-    for (int q = 3; q < 6; q++) out[i * 6 + q] = (float)(x[q] * 2.0 - 1.0);
+    for (int q = 3; q < 6; q++) o[q] = (float)(x[q] * 2.0 - 1.0);
 }
 
 // ------------------------------------------------------- candidate E-step ----
@@ -1078,7 +1038,7 @@ __global__ void __launch_bounds__(256) k_labels(const double *__restrict__ Xe, c
                                                 const int *__restrict__ rows, int64_t rstride, int64_t ne,
                                                 const float *__restrict__ rec32, const int *__restrict__ order,
                                                 const int *__restrict__ cstart, const float *__restrict__ UB,
-                                                float *__restrict__ Q)
+                                                int64_t nb, int64_t S, float *__restrict__ Q)
 {
     const int lane = threadIdx.x & 31;
     const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1087,7 +1047,7 @@ __global__ void __launch_bounds__(256) k_labels(const double *__restrict__ Xe, c
 #pragma unroll
     for (int i = 0; i < 6; i++) x[i] = (float)Xe[n * rstride * VBGS_XS + i];
     const float l2 = (float)(lse_e[n * rstride] * 1.4426950408889634);
-    float *q = Q + n * kG;
+    float *q = Q + deal_slot(n, nb, S) * kG;
     const float *ub = UB + (int64_t)(rows ? rows[n * rstride] : n * rstride) * kG;
     for (int g0 = 0; g0 < kG; g0 += 32) {
         const int g = g0 + lane;
@@ -1258,11 +1218,12 @@ size_t prop_cpar_floats() { return (size_t)kG * kCP; }
 size_t prop_cscr_doubles() { return (size_t)kG * kCScr; }
 size_t prop_mscr_floats(int K) { return (size_t)K * kMS; }
 
-void prop_gemm(int M, int N, int K, const float *A, int sam, int sak, const float *B, int sbk, int sbn, float *C,
-               int ldc, const float *bias, bool relu, bool accumulate, cudaStream_t st)
+int prop_gemm(int M, int N, int K, const float *A, int sam, int sak, const float *B, int sbk, int sbn, bool exact_b,
+              float *C, int ldc, const float *bias, bool relu, bool accumulate, float *part, size_t part_floats,
+              int *flags, cudaStream_t st)
 {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    k_gemm<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, relu ? 1 : 0, accumulate ? 1 : 0);
+    return mlp_gemm_tc(M, N, K, A, sam, sak, true, B, sbn, sbk, !exact_b, C, ldc, bias, relu, accumulate, part,
+                       part_floats, flags, st);
 }
 
 void prop_colsum(const float *X, int M, int Nc, float *out, cudaStream_t st)
@@ -1288,9 +1249,9 @@ void prop_adam(float *w, float *wq, float *m, float *v, const float *g, size_t n
 }
 
 void prop_inputs(const double *X, const int *rows, int64_t rstride, int64_t n, const BoxParams &box, float *out,
-                 cudaStream_t st)
+                 cudaStream_t st, int64_t nb, int64_t S)
 {
-    if (n > 0) k_mlp_inputs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, rows, rstride, n, box, out);
+    if (n > 0) k_mlp_inputs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, rows, rstride, n, box, nb, S, out);
 }
 
 void prop_cand_init(const int *top, int64_t N, int *cand, int *ncand, int *pend, float2 *run, float2 *part,
@@ -1371,11 +1332,12 @@ void prop_cand_pass2(const double *X, const double *lse_c, const float *rec32, c
 }
 
 void prop_labels(const double *Xe, const double *lse_e, const int *rows, int64_t rstride, int64_t ne,
-                 const float *rec32, const int *order, const int *cstart, const float *UB, float *Q, cudaStream_t st)
+                 const float *rec32, const int *order, const int *cstart, const float *UB, float *Q, cudaStream_t st,
+                 int64_t nb, int64_t S)
 {
     if (ne > 0)
         k_labels<<<(unsigned)((ne * 32 + 255) / 256), 256, 0, st>>>(Xe, lse_e, rows, rstride, ne, rec32, order,
-                                                                     cstart, UB, Q);
+                                                                     cstart, UB, nb, S, Q);
 }
 
 size_t prop_audit_floats(int64_t ne, int K) { return (size_t)std::max<int64_t>(ne, 1) * ((K + 255) / 256) * 2; }

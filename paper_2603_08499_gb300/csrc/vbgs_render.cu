@@ -17,7 +17,7 @@
 // GB300 layout of the work:
 //   k_splat_prep   a thread per component: posterior (FP64, from S_past and
 //                  the prior), camera transform, screen covariance and its
-//                  inverse (FP64 -> FP32), the screen rectangle of 16 x 16
+//                  inverse, the screen rectangle of 16 x 16
 //                  pixel tiles that holds every pixel with alpha >= 1/255
 //                  (q <= 2 ln(255 * 0.99): the ellipse's bounding box), a
 //                  64-bit depth key.
@@ -30,14 +30,15 @@
 //                  contiguous and front to back.
 //   k_raster       a CTA per tile (256 threads, a pixel each): batches of
 //                  256 splats staged in shared memory, each pixel composites
-//                  them in FP32 (one ex2 per splat and pixel); a pixel stops
+//                  them (the quadratic form in FP64, alpha and the colour in
+//                  FP32, one expm1 per splat and pixel); a pixel stops
 //                  once its transmittance is below 1e-7 (what remains can
 //                  change its colour by less than 1e-7), the CTA once all
 //                  its pixels have.
 //   k_mse_part, k_psnr  FP64 sum of squared differences (0..255 scale) and
 //                  the PSNR, on the device.
-// The work is bound by the exp unit and FP32 issue (splats x covered
-// pixels), like the E-step: no contraction to put on the tensor cores.
+// The work is splats x covered pixels of a few FP64 and FP32 operations and
+// one exp each: no contraction to put on the tensor cores.
 #include "vbgs_internal.cuh"
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
@@ -50,26 +51,29 @@ constexpr int kTile = 16;                   // tile edge in pixels
 constexpr int kRT = kTile * kTile;          // threads per raster CTA
 constexpr double kNear = 0.1;               // splats closer to the camera plane are left out
 constexpr double kLowPass = 0.3;            // px^2 on the screen covariance's diagonal
-constexpr float kAlphaMax = 0.99f;
-constexpr float kOpacity = 0.99f;
+constexpr float kOpacity = 0.99f;            // alpha = min(0.99, o e^(-q/2)) with o = 0.99: the cap never binds
+constexpr float kOneMinusOpacity = 0.01f;    // 1 - o, rounded once (not 1 - 0.99f)
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-7f;
 constexpr double kMinCount = 1.0;           // components with fewer points' worth of data are not drawn
+
+// A splat as the rasteriser reads it: centre and inverse screen covariance
+// in FP64 -- the quadratic form of a thin splat seen edge-on cancels: its
+// terms reach 1e3 where q <= 11 matters, so FP32 would move alpha by ~1e-5,
+// and a pixel far along a long splat's major axis has a minor-axis offset
+// that FP32 cannot resolve -- and the colour in FP32.  64 bytes.
+struct __align__(16) Splat {
+    double u, v, ca, cb, cc;
+    float r, g, b, pad;
+};
+static_assert(sizeof(Splat) == 64, "splat record size");
 
 struct Camera {
     double o[3], Rwc[9], f;
     int W, H, tiles_x, tiles_y;
 };
 
-__device__ __forceinline__ float ex2a(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Per component: splat record (u, v, conic a, b | conic c, r, g, b | u_lo,
-// v_lo, -, -), tile
+// Per component: splat record, tile
 // rectangle, tile count and depth key (all-ones when left out).
 __global__ void k_splat_prep(const double *__restrict__ m0, const double *__restrict__ S, MstepParams P, int d, int K,
                              Camera cam, float4 *__restrict__ sp, int4 *__restrict__ rect, long long *__restrict__ cnt,
@@ -153,13 +157,15 @@ __global__ void k_splat_prep(const double *__restrict__ m0, const double *__rest
     rect[k] = make_int4(tx0, ty0, tx1, ty1);
     cnt[k] = (long long)(tx1 - tx0 + 1) * (ty1 - ty0 + 1);
     zkey[k] = (unsigned long long)__double_as_longlong(z);   // z > 0: the bits order as the values
-    // the centre as FP32 hi/lo pairs: an FP32 centre alone would be off by up
-    // to 1.5e-5 px at 200 px, which moves alpha by ~1e-4 for a narrow splat
-    const float uh = (float)u, vh = (float)v;
-    sp[(size_t)k * 3] = make_float4(uh, vh, (float)(C[1][1] / det), (float)(-C[0][1] / det));
-    sp[(size_t)k * 3 + 1] = make_float4((float)(C[0][0] / det), (float)fmin(fmax(m[3], 0.0), 1.0),
-                                        (float)fmin(fmax(m[4], 0.0), 1.0), (float)fmin(fmax(m[5], 0.0), 1.0));
-    sp[(size_t)k * 3 + 2] = make_float4((float)(u - (double)uh), (float)(v - (double)vh), 0.f, 0.f);
+    Splat &o = reinterpret_cast<Splat *>(sp)[k];
+    o.u = u;
+    o.v = v;
+    o.ca = C[1][1] / det;
+    o.cb = -C[0][1] / det;
+    o.cc = C[0][0] / det;
+    o.r = (float)fmin(fmax(m[3], 0.0), 1.0);
+    o.g = (float)fmin(fmax(m[4], 0.0), 1.0);
+    o.b = (float)fmin(fmax(m[5], 0.0), 1.0);
 }
 
 __global__ void k_rank(const int *__restrict__ sorted_idx, int K, int *__restrict__ rank)
@@ -197,41 +203,42 @@ __global__ void __launch_bounds__(kRT) k_raster(const float4 *__restrict__ sp, c
                                                 const int2 *__restrict__ range, int W, int H, int tiles_x,
                                                 float *__restrict__ img)
 {
-    __shared__ float4 s0[kRT], s1[kRT];
-    __shared__ float2 s2[kRT];
+    __shared__ Splat sh[kRT];
     const int tile = blockIdx.x, tid = threadIdx.x;
     const int px = (tile % tiles_x) * kTile + (tid % kTile), py = (tile / tiles_x) * kTile + tid / kTile;
     const bool inside = px < W && py < H;
-    const float cx = (float)px + 0.5f, cy = (float)py + 0.5f;
+    const double cx = (double)px + 0.5, cy = (double)py + 0.5;
     const int2 r = range[tile];
     float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
     bool done = !inside;
-    constexpr float kHalfLog2e = -0.72134752044448170f;   // -log2(e) / 2
     for (int b = r.x; b < r.y; b += kRT) {
         if (__syncthreads_and(done)) break;
         const int i = b + tid;
         if (i < r.y) {
             const int k = val[i];
-            s0[tid] = sp[(size_t)k * 3];
-            s1[tid] = sp[(size_t)k * 3 + 1];
-            const float4 lo = sp[(size_t)k * 3 + 2];
-            s2[tid] = make_float2(lo.x, lo.y);
+            sh[tid] = reinterpret_cast<const Splat *>(sp)[k];
         }
         __syncthreads();
         const int n = min(kRT, r.y - b);
         if (!done) {
             for (int j = 0; j < n; j++) {
-                const float4 a = s0[j], c = s1[j];
-                const float2 l = s2[j];
-                const float dx = (cx - a.x) - l.x, dy = (cy - a.y) - l.y;
-                const float q = fmaf(a.z * dx, dx, fmaf(2.f * a.w * dx, dy, c.x * dy * dy));
-                const float al = fminf(kAlphaMax, kOpacity * ex2a(kHalfLog2e * q));
+                const Splat &a = sh[j];
+                const double dx = cx - a.u, dy = cy - a.v;
+                const float q = (float)fma(a.ca * dx, dx, fma(2.0 * a.cb * dx, dy, a.cc * dy * dy));
+                // alpha = o e^(-q/2) <= 0.99 (the cap never binds at o = 0.99)
+                // and 1 - alpha = (1 - o) - o (e^(-q/2) - 1) from expm1:
+                // 1 - alpha of a nearly opaque splat is ~0.01, so an exp
+                // accurate to a few units of 2^-24 relative to 1 would give it
+                // a relative error ~100 times larger, and every splat behind
+                // it would inherit that through the transmittance
+                const float em = expm1f(-0.5f * q);
+                const float al = fmaf(kOpacity, em, kOpacity);
                 if (al < kAlphaMin) continue;
                 const float w = T * al;
-                cr = fmaf(w, c.y, cr);
-                cg = fmaf(w, c.z, cg);
-                cb = fmaf(w, c.w, cb);
-                T *= 1.f - al;
+                cr = fmaf(w, a.r, cr);
+                cg = fmaf(w, a.g, cg);
+                cb = fmaf(w, a.b, cb);
+                T *= fmaf(-kOpacity, em, kOneMinusOpacity);
                 if (T < kTStop) {
                     done = true;
                     break;
@@ -335,7 +342,7 @@ int render_frame(const double *m0, const double *S, const MstepParams &P, int d,
     int tile_bits = 1;
     while ((1 << tile_bits) < ntiles) tile_bits++;
 
-    RCU(grow(&B.sp, B.cap_sp, (size_t)K * 3));
+    RCU(grow(&B.sp, B.cap_sp, (size_t)K * 4));
     RCU(grow(&B.rect, B.cap_rect, (size_t)K));
     RCU(grow(&B.cnt, B.cap_cnt, (size_t)K + 1));
     RCU(grow(&B.off, B.cap_off, (size_t)K + 1));

@@ -51,7 +51,8 @@ EXPORTS = [
     "vbgs_set_stats", "vbgs_get_frame_stats", "vbgs_get_lse", "vbgs_last_launch_count",
     "vbgs_profile_enable", "vbgs_profile_read", "vbgs_profile_pairs", "vbgs_profile_name", "vbgs_probe_peaks",
     "vbgs_estep_noalloc", "vbgs_update_batched", "vbgs_autotune", "vbgs_get_tuning", "vbgs_set_tuning",
-    "vbgs_proposal_report", "vbgs_proposal_weights", "vbgs_proposal_grad", "vbgs_proposal_clusters",
+    "vbgs_proposal_report", "vbgs_proposal_config", "vbgs_proposal_weights", "vbgs_proposal_grad",
+    "vbgs_proposal_clusters",
     "vbgs_proposal_bounds", "vbgs_kmeans", "vbgs_reassign", "vbgs_save_state", "vbgs_load_state",
     "vbgs_check_frame", "vbgs_set_wait_limit", "vbgs_render", "vbgs_profile_replay", "vbgs_last_error",
     "vbgs_destroy",
@@ -116,6 +117,7 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
     lib.vbgs_set_tuning.argtypes = [C.c_void_p, C.c_int, C.c_int]
     _FP = C.POINTER(C.c_float)
     lib.vbgs_proposal_report.argtypes = [C.c_void_p, _DP]
+    lib.vbgs_proposal_config.argtypes = [C.c_void_p, C.c_int, C.c_double]
     lib.vbgs_proposal_weights.argtypes = [C.c_void_p, _FP, _FP]
     lib.vbgs_proposal_grad.argtypes = [C.c_void_p, _FP, _FP, C.c_int, _FP, _FP, C.POINTER(C.c_int)]
     lib.vbgs_proposal_clusters.argtypes = [C.c_void_p, _FP, C.POINTER(C.c_int)]
@@ -417,6 +419,11 @@ def vbgs_proposal_report(ctx) -> dict:
     out = np.zeros(11)
     _check(lib().vbgs_proposal_report(ctx, _dp(out)), ctx)
     return dict(zip(PROP_REPORT, out.tolist()))
+
+
+def vbgs_proposal_config(ctx, epochs: int = 8, learning_rate: float = 3e-3) -> None:
+    """Training schedule of the proposal network (epochs 0: not trained)."""
+    _check(lib().vbgs_proposal_config(ctx, int(epochs), float(learning_rate)), ctx)
 
 
 def vbgs_proposal_weights(ctx, set_to=None) -> np.ndarray:
