@@ -214,7 +214,7 @@ def run_reference(args):
 
 
 def timed_stream(V, prior, dev_frames, form, warmup, steps, stream, flush, profile=False, host_frames=None,
-                 flags=0, keep_last_state=False, tuning=None, replay=0):
+                 flags=0, keep_last_state=False, tuning=None, replay=0, knobs=0):
     """Run warmup + steps frames through a fresh model; per-step device times
     with CUDA events (or host wall time for host inputs).  tuning: the
     tensor-core work decomposition (pass-1 tiles, pass-2 chunks per item) to
@@ -223,6 +223,8 @@ def timed_stream(V, prior, dev_frames, form, warmup, steps, stream, flush, profi
     m = V.Model(prior, form, cuda_stream=stream.cuda_stream, flags=flags)
     if tuning:
         V.vbgs_set_tuning(m.ctx, *tuning)
+    if knobs:
+        V.vbgs_set_precision_knobs(m.ctx, knobs)
     traces, times, launches = [], [], 0
     pairs = 0
     state_before_last = None
@@ -672,6 +674,23 @@ def run_ours(args):
         tuning = V.vbgs_get_tuning(mt.ctx)
         mt.close()
 
+    # the mixed-precision search of Sec. 4.2 on this form's knobs (not timed):
+    # a white-noise frame (points uniform in the room box, uniform colours)
+    # from the FP64 form's state after the warm-up frames
+    knobs, psearch = 0, None
+    if form in ("fp16x3", "bf16x3") and not args.no_precision_search:
+        from paper_2603_08499_gb300 import precision_search as PS
+        ms = V.Model(prior, "fp64", cuda_stream=stream.cuda_stream)
+        for t in range(args.warmup):
+            ms.update(dev[t], ITERS)
+        S_search = ms.stats()
+        ms.close()
+        rng = np.random.default_rng(11)
+        lo, hi = np.array(synth.ROOM_LO), np.array(synth.ROOM_HI)
+        Xw = np.concatenate([rng.uniform(lo, hi, (40_000, 3)), rng.uniform(0, 1, (40_000, 3))], axis=1)
+        psearch = PS.search_kernel_map(V, prior, S_search, torch.from_numpy(Xw).cuda(), eps=args.eps, form=form)
+        knobs = psearch["knobs"]
+
     clocks = ClockSampler(lrank)
     if ws > 1:
         dist.barrier()
@@ -681,7 +700,7 @@ def run_ours(args):
     # its kernel with its neighbours); the dominant kernel's duration comes
     # from replaying its last launch alone right after the timed frames
     res = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, flags=args.flags,
-                       tuning=tuning, replay=REPLAYS)
+                       tuning=tuning, replay=REPLAYS, knobs=knobs)
     clk = clocks.stop()
     torch.cuda.synchronize()
     dev_time, total_pairs = job_totals(sum(res["times"]), res["pairs"], ws)
@@ -694,7 +713,7 @@ def run_ours(args):
     e2e_runs = []
     for _ in range(E2E_REPEATS):
         res_e2e = timed_stream(V, prior, dev, form, args.warmup, args.steps, stream, flush, host_frames=host,
-                               flags=args.flags, tuning=tuning)
+                               flags=args.flags, tuning=tuning, knobs=knobs)
         e2e_time, _ = job_totals(sum(res_e2e["times"]), 0.0, ws)
         e2e_runs.append(total_pairs / e2e_time)
     e2e_value = statistics.median(e2e_runs)
@@ -723,6 +742,8 @@ def run_ours(args):
         # one-frame error: the form from the FP64 stream's state before its last frame
         S0, S1 = ref["state_before_last"], ref["final_state"]
         m = V.Model(prior, form, cuda_stream=stream.cuda_stream, flags=args.flags)
+        if knobs:
+            V.vbgs_set_precision_knobs(m.ctx, knobs)
         m.set_stats(S0)
         tr = m.update(dev[args.warmup + args.steps - 1], ITERS)
         dS, dS0 = m.stats() - S0, S1 - S0
@@ -745,7 +766,7 @@ def run_ours(args):
         # bracketed by events (outside the timed measurement)
         nb = min(args.steps, 5)
         bd = timed_stream(V, prior, dev, form, args.warmup, nb, stream, flush, profile=True, flags=args.flags,
-                          tuning=tuning)
+                          tuning=tuning, knobs=knobs)
         breakdown = {k: v[0] / nb for k, v in (bd["prof"] or {}).items()}
         _, rl_all = roofline(form, bd["prof"], bd["prof_pairs"], peaks, sum(bd["times"]) * 1e3)
         try:
@@ -793,6 +814,16 @@ def run_ours(args):
                                     "sample": (f"first {cpu_info['points_per_frame']} points of 2 timed frames, "
                                                f"K={K_COMP}, {ITERS} iterations each, FP64 oracle "
                                                f"({cpu_info['seconds']} s)")}
+        if psearch is not None:
+            line["precision_search"] = {
+                "eps": psearch["eps"], "feasible": psearch["feasible"], "knobs": psearch["knobs"],
+                "left_out": psearch["left_out"], "err": psearch["err"], "err_all_kept": psearch["err_all_kept"],
+                "latency_ms": psearch["latency_ms"], "latency_ms_all_kept": psearch["latency_ms_all_kept"],
+                "evaluations": psearch["evaluations"],
+                "what": ("Sec. 4.2's three passes over the six lo terms of the tensor-core products (levels hi, hi+lo) "
+                         "on a white-noise frame (40,000 points uniform in the room box and colour cube) from the FP64 "
+                         "form's state after the warm-up frames; err = Eq. relerr of lse and N, S1, S2 of one "
+                         "iteration against the FP64 form; the headline runs with the chosen map")}
         line.update(extra)
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -817,6 +848,8 @@ def main():
     ap.add_argument("--flags", type=int, default=0,
                     help="VBGS_FLAG_* bits: 1 = caller's order, 2 = no pass-2 tile skipping (3 = plain)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eps", type=float, default=1e-6, help="tolerance of the mixed-precision search (Eq. relerr)")
+    ap.add_argument("--no-precision-search", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="only the timed stream (no e2e, comparisons or extras): for ncu captures")
     ap.add_argument("--replays", type=int, default=0,

@@ -443,6 +443,30 @@ int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N, double *l
 int vbgs_render(vbgs_ctx *ctx, const double *camera, int width, int height, float *image, const float *reference,
                 double *psnr, double *device_ms);
 
+/* Per-operation precision of the tensor-core forms, the knobs the
+ * mixed-precision search of Sec. 4.2 chooses between (precision_search.py
+ * drives it with measured error and latency).  Every product of the passes
+ * is a sum of hi*hi, hi*lo and lo*hi terms of FP16 (or BF16) operand pairs;
+ * a set bit leaves one lo term out, the operand then carries its hi part
+ * alone (11 or 8 significant bits instead of ~22 or ~16):
+ *   VBGS_KNOB_P1_PHI_LO  pass 1 (logits): the points' features
+ *   VBGS_KNOB_P1_C_LO    pass 1: the components' coefficients
+ *   VBGS_KNOB_P2_PHI_LO  pass 2, recomputed logits: the points' features
+ *   VBGS_KNOB_P2_C_LO    pass 2, recomputed logits: the coefficients
+ *   VBGS_KNOB_P2_P_LO    pass 2, statistics: the responsibilities
+ *   VBGS_KNOB_P2_S_LO    pass 2, statistics: the points' features
+ * 0 (the default) keeps every term.  The CUDA-core forms ignore the knobs.
+ * Errors: VBGS_EINVAL (NULL ctx, unknown bits). */
+#define VBGS_KNOB_P1_PHI_LO 1u
+#define VBGS_KNOB_P1_C_LO   2u
+#define VBGS_KNOB_P2_PHI_LO 4u
+#define VBGS_KNOB_P2_C_LO   8u
+#define VBGS_KNOB_P2_P_LO   16u
+#define VBGS_KNOB_P2_S_LO   32u
+#define VBGS_KNOB_ALL       63u
+int vbgs_set_precision_knobs(vbgs_ctx *ctx, unsigned int knobs);
+unsigned int vbgs_get_precision_knobs(const vbgs_ctx *ctx);
+
 /* No paper counterpart (failure handling).  Set the limit, in SM clock
  * cycles, of the bounded waits between the warp roles of the tensor-core
  * kernels on the current device (default ~2 s; cycles <= 0 restores it).

@@ -316,16 +316,24 @@ int frame_start_from_next(vbgs_ctx *ctx, bool moved, const int *kinv_old)
     return VBGS_OK;
 }
 
-// Morton order of the frame's points (sorted staging copy) and of the
-// components by their posterior mean at frame start.
-int order_frame(vbgs_ctx *ctx, int64_t N, bool points)
+constexpr int kResortFrames = 4;   // frames between refreshes of the components' Morton order
+
+// Whether this frame refreshes the components' Morton order.
+bool resort_due(const vbgs_ctx *ctx) { return ctx->frame_count % kResortFrames == 0; }
+
+// Morton order of the frame's points (sorted staging copy) and, with comps,
+// of the components by their posterior mean at frame start.
+int order_frame(vbgs_ctx *ctx, int64_t N, bool points, bool comps = true)
 {
     ctx->last_sorted = false;
     if (ctx->flags & VBGS_FLAG_NO_REORDER) return VBGS_OK;
-    int l = launch_comp_order(ctx->d_m0, ctx->d_Spast, ctx->K, ctx->mp.beta0, ctx->box, ctx->sb, ctx->d_kperm,
+    int l;
+    if (comps) {
+        l = launch_comp_order(ctx->d_m0, ctx->d_Spast, ctx->K, ctx->mp.beta0, ctx->box, ctx->sb, ctx->d_kperm,
                               ctx->d_kinv, ctx->stream, &ctx->prof);
-    if (l < 0) return fail(ctx, VBGS_ECUDA, "component ordering failed");
-    ctx->launches += 2;
+        if (l < 0) return fail(ctx, VBGS_ECUDA, "component ordering failed");
+        ctx->launches += 2;
+    }
     if (points && N > 0) {
         l = launch_point_order(ctx->d_X, N, ctx->box, ctx->sb, ctx->d_Xs, ctx->d_pidx, ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "point ordering failed");
@@ -366,20 +374,22 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
                                 ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_rec32, ctx->d_part, ctx->part_cap, B.tmax,
                                 ctx->d_p1plan, ctx->d_p1ub, ctx->d_flags, ctx->num_sms, ctx->tune_p1,
                                 ctx->d_tile_dirty + (ctx->K + 127) / 128, ctx->plan_epoch, &item_start, ctx->stream,
-                                &ctx->prof);
+                                &ctx->prof, ctx->tc_knobs);
         ctx->plan_epoch = ctx->coef_epoch;
         ctx->prof.p1_last.alloc_gen = ctx->alloc_gen;
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ctx->launches += l;
         l = launch_lse_merge_tc(ctx->d_part, N, item_start, lse, ctx->d_lse2f, ctx->d_lse_part,
-                                B.tmax ? ctx->d_minlse : nullptr, ctx->d_scal + SC_SUM_LSE, ctx->stream, &ctx->prof);
+                                B.tmax ? ctx->d_minlse : nullptr, ctx->d_scal + SC_SUM_LSE,
+                                reinterpret_cast<unsigned int *>(ctx->d_scal + SC_MERGE_DONE), ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "lse merge launch failed");
         ctx->launches += l;
         if (want_stats) {
             l = launch_pass2_tc(ctx->d_Xhl, ctx->d_lse2f, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
                                 ctx->d_rec, B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
                                 ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->tune_p2,
-                                ctx->d_tile_dirty + 2 * ((ctx->K + 127) / 128), same_points, ctx->stream, &ctx->prof);
+                                ctx->d_tile_dirty + 2 * ((ctx->K + 127) / 128), same_points, ctx->stream, &ctx->prof,
+                                ctx->tc_knobs);
             if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
                                    cudaGetErrorString(cudaGetLastError()));
             ctx->launches += l;
@@ -809,13 +819,20 @@ int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters, bool carry_prior)
     int rc;
     const bool from_next = carry_prior && ctx->next_prior_ready;
     const bool reorder = !(ctx->flags & VBGS_FLAG_NO_REORDER);
+    // The components' Morton order is refreshed on every kResortFrames-th
+    // frame of the context (their means move little from frame to frame, so
+    // the order changes little; any order gives the same results up to the
+    // order of sums).  A schedule by frame count alone keeps a batched and a
+    // per-scene stream on the same orders.
+    const bool resort = reorder && resort_due(ctx);
+    ctx->frame_count++;
     ctx->next_prior_ready = false;
     ctx->next_written = false;
-    if (from_next && reorder) std::swap(ctx->d_kinv, ctx->d_kinv_alt);   // keep the old inverse order
-    if ((rc = order_frame(ctx, N, true))) return rc;
+    if (from_next && resort) std::swap(ctx->d_kinv, ctx->d_kinv_alt);   // keep the old inverse order
+    if ((rc = order_frame(ctx, N, true, resort))) return rc;
     // Posterior entering the frame: the effective prior prior0 (+) S_past.
     if (from_next) {
-        if ((rc = frame_start_from_next(ctx, reorder, ctx->d_kinv_alt))) return rc;
+        if ((rc = frame_start_from_next(ctx, resort, ctx->d_kinv_alt))) return rc;
     } else if ((rc = run_mstep(ctx, nullptr))) return rc;
     const bool prop = ctx->prop.on && N > 0;
     if (prop) {
@@ -1008,6 +1025,7 @@ extern "C" int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const 
         key.push_back((int64_t)(uintptr_t)scenes[i]);
         key.push_back(N[i]);
         key.push_back(scenes[i]->tune_p1 * 1000 + scenes[i]->tune_p2);
+        key.push_back(resort_due(scenes[i]) ? 1 : 0);   // the frame's launches include the component order
         key.push_back(scenes[i]->alloc_gen);
     }
     cudaGraphExec_t exec = nullptr;
@@ -1345,6 +1363,8 @@ struct StateHeader {
     int32_t version, K, D, precision, flags, has_prop, next_prior_ready, coef_epoch, plan_epoch, tune_p1, tune_p2,
         prop_step, prop_centroids_ready, n_sections, prop_epochs;
     float prop_lr;
+    uint32_t tc_knobs;
+    int64_t frame_count;
     int64_t prop_frames_trained;
     uint64_t prop_frame, seed;
     double alpha0, beta0, nu0, W0[36], box_lo[3], box_inv_ext[3];
@@ -1829,6 +1849,8 @@ int vbgs_save_state(vbgs_ctx *ctx, const char *path)
     h.prop_step = ctx->prop.step;
     h.prop_centroids_ready = ctx->prop.centroids_ready ? 1 : 0;
     h.prop_epochs = ctx->prop.epochs;
+    h.tc_knobs = ctx->tc_knobs;
+    h.frame_count = ctx->frame_count;
     h.prop_lr = ctx->prop.lr;
     h.prop_frames_trained = ctx->prop.frames_trained;
     h.prop_frame = ctx->prop.frame;
@@ -1957,6 +1979,8 @@ int vbgs_load_state(vbgs_ctx **out, const char *path, const vbgs_options *opt)
     ctx->plan_epoch = h.plan_epoch;
     ctx->tune_p1 = h.tune_p1;
     ctx->tune_p2 = h.tune_p2;
+    ctx->tc_knobs = h.tc_knobs;
+    ctx->frame_count = h.frame_count;
     for (int i = 0; i < 3; i++) {
         ctx->box.lo[i] = h.box_lo[i];
         ctx->box.inv_ext[i] = h.box_inv_ext[i];
@@ -2052,6 +2076,16 @@ int vbgs_profile_replay(vbgs_ctx *ctx, int reps, double *ms_per_launch, int64_t 
     if (pairs_per_launch) *pairs_per_launch = (int64_t)pairs;
     return check_flags(ctx);
 }
+
+int vbgs_set_precision_knobs(vbgs_ctx *ctx, unsigned int knobs)
+{
+    if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
+    if (knobs & ~(unsigned)VBGS_KNOB_ALL) return fail(ctx, VBGS_EINVAL, "vbgs_set_precision_knobs: unknown bits");
+    ctx->tc_knobs = knobs;
+    return VBGS_OK;
+}
+
+unsigned int vbgs_get_precision_knobs(const vbgs_ctx *ctx) { return ctx ? ctx->tc_knobs : 0u; }
 
 int vbgs_set_wait_limit(long long cycles)
 {

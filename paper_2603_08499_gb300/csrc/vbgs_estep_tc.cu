@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restr
                                                             const int *__restrict__ nitems,
                                                             float2 *__restrict__ part, float *__restrict__ tmax,
                                                             int *__restrict__ flags,
-                                                            unsigned long long *__restrict__ pairs)
+                                                            unsigned long long *__restrict__ pairs, uint32_t knobs)
 {
     pdl_wait();
     using HT = typename H<BF16>::T;
@@ -636,10 +636,14 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restr
             // k-steps of 16 features: the descriptor start advances by two core matrices (256 B)
             mma(d, smem_desc(Ahi), smem_desc(Bhi), idesc, 0u);
             mma(d, smem_desc(Ahi + 256), smem_desc(Bhi + 256), idesc, 1u);
-            mma(d, smem_desc(Ahi), smem_desc(Blo), idesc, 1u);
-            mma(d, smem_desc(Ahi + 256), smem_desc(Blo + 256), idesc, 1u);
-            mma(d, smem_desc(Alo), smem_desc(Bhi), idesc, 1u);
-            mma(d, smem_desc(Alo + 256), smem_desc(Bhi + 256), idesc, 1u);
+            if (!(knobs & VBGS_KNOB_P1_C_LO)) {      // coefficients' lo term
+                mma(d, smem_desc(Ahi), smem_desc(Blo), idesc, 1u);
+                mma(d, smem_desc(Ahi + 256), smem_desc(Blo + 256), idesc, 1u);
+            }
+            if (!(knobs & VBGS_KNOB_P1_PHI_LO)) {    // features' lo term
+                mma(d, smem_desc(Alo), smem_desc(Bhi), idesc, 1u);
+                mma(d, smem_desc(Alo + 256), smem_desc(Bhi + 256), idesc, 1u);
+            }
             mma_commit(&S.bar_mma[s]);
             mma_commit(&S.bar_bfree[sb]);
             n_mma = jj + 1;
@@ -1142,7 +1146,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
                                                             const int *__restrict__ nitems,
                                                             const double *__restrict__ rec,
                                                             float *__restrict__ part, int *__restrict__ flags,
-                                                            unsigned long long *__restrict__ pairs)
+                                                            unsigned long long *__restrict__ pairs, uint32_t knobs)
 {
     pdl_wait();
     using HT = typename H<BF16>::T;
@@ -1405,10 +1409,14 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
             const unsigned char *Bh = S.B1[s], *Bl = S.B1[s] + kB1Bytes;
             mma(d, smem_desc_sbo(Ahi, 512), smem_desc_sbo(Bh, 512), id1, 0u);
             mma(d, smem_desc_sbo(Ahi + 256, 512), smem_desc_sbo(Bh + 256, 512), id1, 1u);
-            mma(d, smem_desc_sbo(Ahi, 512), smem_desc_sbo(Bl, 512), id1, 1u);
-            mma(d, smem_desc_sbo(Ahi + 256, 512), smem_desc_sbo(Bl + 256, 512), id1, 1u);
-            mma(d, smem_desc_sbo(Alo, 512), smem_desc_sbo(Bh, 512), id1, 1u);
-            mma(d, smem_desc_sbo(Alo + 256, 512), smem_desc_sbo(Bh + 256, 512), id1, 1u);
+            if (!(knobs & VBGS_KNOB_P2_PHI_LO)) {    // the points' features, lo term
+                mma(d, smem_desc_sbo(Ahi, 512), smem_desc_sbo(Bl, 512), id1, 1u);
+                mma(d, smem_desc_sbo(Ahi + 256, 512), smem_desc_sbo(Bl + 256, 512), id1, 1u);
+            }
+            if (!(knobs & VBGS_KNOB_P2_C_LO)) {      // the coefficients, lo term
+                mma(d, smem_desc_sbo(Alo, 512), smem_desc_sbo(Bh, 512), id1, 1u);
+                mma(d, smem_desc_sbo(Alo + 256, 512), smem_desc_sbo(Bh + 256, 512), id1, 1u);
+            }
             mma_commit(&S.bar_d1full[s]);
         };
         // MMA1 of the first chunk
@@ -1439,8 +1447,10 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
 #pragma unroll
             for (int t = 0; t < kChunk2 / 16; t++) {
                 mma(d2, smem_desc_sbo(Pp + 256 * t, 1024), smem_desc_sbo(Bh + 256 * t, 1024), id2, t > 0 ? 1u : 0u);
-                mma(d2, smem_desc_sbo(Pp + 256 * t, 1024), smem_desc_sbo(Bl + 256 * t, 1024), id2, 1u);
-                mma(d2, smem_desc_sbo(Pl + 256 * t, 1024), smem_desc_sbo(Bh + 256 * t, 1024), id2, 1u);
+                if (!(knobs & VBGS_KNOB_P2_S_LO))    // the statistics' features, lo term
+                    mma(d2, smem_desc_sbo(Pp + 256 * t, 1024), smem_desc_sbo(Bl + 256 * t, 1024), id2, 1u);
+                if (!(knobs & VBGS_KNOB_P2_P_LO))    // the responsibilities, lo term
+                    mma(d2, smem_desc_sbo(Pl + 256 * t, 1024), smem_desc_sbo(Bh + 256 * t, 1024), id2, 1u);
             }
             mma_commit(&S.bar_stfree[s]);
             n_proc = u + 1;
@@ -1570,7 +1580,7 @@ size_t tc_plan_ints(int64_t N, int K)
 int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
-                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf)
+                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs)
 {
     unsigned long long *pairs = pf->on ? pf->d_pairs : nullptr;
     const int ntiles = (K + kCols - 1) / kCols;
@@ -1598,11 +1608,11 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
     if (bf16)
         launch_pdl(k_pass2_tc<true>, tcap, kThreadsTC, smem, st, Xhl, lse2f, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
                                                          list, item_tile, item_lo, item_hi, nitems, rec, fpart, flags,
-                                                         pairs);
+                                                         pairs, knobs);
     else
         launch_pdl(k_pass2_tc<false>, tcap, kThreadsTC, smem, st, Xhl, lse2f, N, K, tiles, hdr, ntiles, tmax ? counts : nullptr,
                                                           list, item_tile, item_lo, item_hi, nitems, rec, fpart, flags,
-                                                         pairs);
+                                                         pairs, knobs);
     pf->end(st);
     pf->begin(VBGS_PROF_REDUCE, st);
     launch_pdl(k_reduce_items, ntiles * 4, 128, 0, st, fpart, item_start, K, rec, kperm, dS, nz, skip_zero && nz);
@@ -1672,10 +1682,12 @@ __global__ void k_split_points(const double *__restrict__ X, int64_t N, float *_
 // the smallest lse per 32 points and per-block FP64 sums of lse.
 __global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part, const int *__restrict__ item_start,
                                                  int64_t N, double *__restrict__ lse, float *__restrict__ lse2f,
-                                                 double *__restrict__ lse_part, float *__restrict__ minlse)
+                                                 double *__restrict__ lse_part, float *__restrict__ minlse,
+                                                 unsigned int *__restrict__ done, double *__restrict__ sum_out)
 {
     pdl_wait();
     __shared__ double sh[2];
+    __shared__ bool last;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
     if (n < N) {
@@ -1706,7 +1718,26 @@ __global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part
         if (minlse && w * 32 < N) minlse[w] = vm;
     }
     __syncthreads();
-    if (threadIdx.x == 0) lse_part[blockIdx.x] = sh[0] + sh[1];
+    // the block sums, added in block order by the last block to finish (the
+    // same sum on every run); it leaves the counter at zero for the next merge
+    if (threadIdx.x == 0) {
+        lse_part[blockIdx.x] = sh[0] + sh[1];
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(lse_part + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *sum_out = sh[0] + sh[1];
+        *done = 0u;
+    }
 }
 
 // Pass-1 work items: at most kItemCap1 + point tiles, so item partials of
@@ -1728,7 +1759,7 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
                     const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
                     size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
                     int tiles_per_item, const int *tile_epoch, int since, const int **item_start_out,
-                    cudaStream_t st, Prof *pf)
+                    cudaStream_t st, Prof *pf, uint32_t knobs)
 {
     float2 *part = reinterpret_cast<float2 *>(part_buf);
     int launches = 0;
@@ -1802,27 +1833,28 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
         L.part = part;
         L.tmax = tmax;
         L.flags = flags;
+        L.knobs = knobs;
     }
     if (bf16)
         launch_pdl(k_pass1_tc<true>, target, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
-                                                           item_hi, nitems, part, tmax, flags, pairs1);
+                                                           item_hi, nitems, part, tmax, flags, pairs1, knobs);
     else
         launch_pdl(k_pass1_tc<false>, target, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
-                                                            item_hi, nitems, part, tmax, flags, pairs1);
+                                                            item_hi, nitems, part, tmax, flags, pairs1, knobs);
     pf->end(st);
     *item_start_out = item_start;
     return cudaGetLastError() == cudaSuccess ? launches + (tmax ? 4 : 2) : -1;
 }
 
 int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
-                        double *lse_part, float *minlse, double *sum_out, cudaStream_t st, Prof *pf)
+                        double *lse_part, float *minlse, double *sum_out, unsigned int *done, cudaStream_t st, Prof *pf)
 {
     const int mb = (int)((N + 63) / 64);
     pf->begin(VBGS_PROF_MERGE, st);
     launch_pdl(k_merge_tc, mb, 64, 0, st, reinterpret_cast<const float2 *>(part_buf), item_start, N, lse, lse2f, lse_part,
-               minlse);
+               minlse, done, sum_out);
     pf->end(st);
-    return launch_block_sum(lse_part, mb, sum_out, st, pf) < 0 ? -1 : 2;
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 int tc_replay_pass1(const Pass1Launch &L, int reps, unsigned long long *pairs, cudaStream_t st, float *ms)
@@ -1832,9 +1864,10 @@ int tc_replay_pass1(const Pass1Launch &L, int reps, unsigned long long *pairs, c
         if (L.bf16)
             return launch_pdl(k_pass1_tc<true>, L.grid, kThreadsTC, L.smem, st, L.Xhl, L.N, L.K, L.tiles, L.hdr,
                               L.ntiles, L.list, L.item_tile, L.item_lo, L.item_hi, L.nitems, L.part, L.tmax, L.flags,
-                              pc);
+                              pc, L.knobs);
         return launch_pdl(k_pass1_tc<false>, L.grid, kThreadsTC, L.smem, st, L.Xhl, L.N, L.K, L.tiles, L.hdr,
-                          L.ntiles, L.list, L.item_tile, L.item_lo, L.item_hi, L.nitems, L.part, L.tmax, L.flags, pc);
+                          L.ntiles, L.list, L.item_tile, L.item_lo, L.item_hi, L.nitems, L.part, L.tmax, L.flags, pc,
+                          L.knobs);
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1;

@@ -65,6 +65,7 @@ enum ScalarSlot {
     SC_KL_TOTAL = 1,   // sum_k KL_NW + KL_Dir
     SC_SUM_LSE = 2,    // sum_n lse_n (without -psi term)
     SC_PSI_ESTEP = 3,  // psi(sum alpha) of the posterior the last E-step ran under
+    SC_MERGE_DONE = 7, // (as an unsigned int) blocks of the lse merge finished; 0 between merges
     SC_COUNT = 8
 };
 
@@ -91,6 +92,7 @@ struct Pass1Launch {
     float2 *part = nullptr;
     float *tmax = nullptr;
     int *flags = nullptr;
+    uint32_t knobs = 0;
 };
 
 // Per-kernel event timing (enabled by vbgs_profile_enable).  Launchers call
@@ -274,7 +276,7 @@ size_t tc_p1ub_floats(int64_t N, int K);
 int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
-                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf);
+                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs);
 int tc_pass1_auto_splits(int64_t N, int K, int num_sms);
 int tc_set_attributes();
 // Pass 1 on the tensor cores over balanced work items (point tile, list of
@@ -290,10 +292,10 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
                     const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
                     size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
                     int tiles_per_item, const int *tile_epoch, int since, const int **item_start_out,
-                    cudaStream_t st, Prof *pf);
+                    cudaStream_t st, Prof *pf, uint32_t knobs);
 // lse from pass 1's FP32 item partials, minlse per 32 points, sum of lse.
 int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
-                        double *lse_part, float *minlse, double *sum_out, cudaStream_t st, Prof *pf);
+                        double *lse_part, float *minlse, double *sum_out, unsigned int *done, cudaStream_t st, Prof *pf);
 int launch_block_sum(const double *part, int n, double *sum_out, cudaStream_t st, Prof *pf);
 
 // Learned proposal (vbgs_proposal.cu).
@@ -480,6 +482,8 @@ struct vbgs_ctx {
     int plan_epoch = 0;                    // coef_epoch at the last pass-1 plan
     int num_sms = 152;
     int tune_p1 = 0, tune_p2 = 0;          // work decomposition of the tensor-core passes (0 = automatic)
+    uint32_t tc_knobs = 0;                 // VBGS_KNOB_*: lo terms left out of the tensor-core products
+    int64_t frame_count = 0;               // frames processed (schedule of the components' Morton order)
     int64_t alloc_gen = 0;                 // bumped by every (re)allocation: cached graphs check it
     size_t tmax_cap = 0;
     bool last_sorted = false;

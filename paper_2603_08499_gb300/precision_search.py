@@ -28,7 +28,10 @@ search runs the paper's three passes in order:
    taken as T(Pi with C one level up) - T(Pi) on the whole function, which
    charges a cast only where raising the region removes it.
 
-Host logic only: it evaluates the callbacks and never touches a device.
+The search itself is host logic: it evaluates the callbacks and never
+touches a device.  kernel_problem / search_kernel_map (at the end) build the
+callbacks for the library's tensor-core E-step, which run it through the C
+ABI.
 """
 from __future__ import annotations
 
@@ -158,3 +161,96 @@ def search(p: Problem) -> dict:
     c3 = latency_aware(p, c2)
     return {"precision_aware": c1, "structure_aware": c2, "final": c3,
             "map": [p.levels[i] for i in c3], "err": p.err(c3), "evaluations": p.evaluations}
+
+
+# ---------------------------------------------------------------------------
+# The search applied to the library's tensor-core E-step: its operations are
+# the six lo terms of the hi/lo products (vbgs.KNOBS: pass-1 features and
+# coefficients, pass-2 recomputed-logit features and coefficients, pass-2
+# responsibilities and statistics features), each at level "hi" (the term
+# left out) or "hi+lo" (kept).  err is Eq. relerr of the E-step's outputs --
+# the per-point lse_n and the statistics N, S1, S2 of one iteration -- against
+# the FP64 form from the same state; latency the measured device time of the
+# two passes.  Edges: the operands of one product, and the operands the two
+# passes share (the point features, the coefficient tiles, the logits that
+# make the responsibilities).
+# ---------------------------------------------------------------------------
+KNOB_EDGES = [(0, 1), (2, 3), (4, 5), (0, 2), (1, 3), (3, 4)]
+
+
+def knobs_of(cfg) -> int:
+    """Knob bits of a configuration: bit i set where op i is at level 0 (hi)."""
+    return sum(1 << i for i, lv in enumerate(cfg) if lv == 0)
+
+
+def kernel_problem(V, prior, S, X, eps: float, form: str = "fp16x3", reps: int = 3) -> Problem:
+    """A Problem over the tensor-core E-step's knobs on the frame X (device
+    N x 6) from the statistics S.  The callbacks run the library."""
+    import numpy as np
+
+    def run(form_, knobs, profile):
+        m = V.Model(prior, form_)
+        if knobs:
+            V.vbgs_set_precision_knobs(m.ctx, knobs)
+        m.set_stats(S)
+        if profile:
+            m.profile(V.prof_only(0, 2))
+            m.profile_read(reset=True)
+        tr = m.update(X, 1)
+        out = (tr, m.lse(X.shape[0]), m.frame_stats())
+        ms = None
+        if profile:
+            p = m.profile_read()
+            ms = p["pass1"][0] + p["pass2"][0]
+        m.close()
+        return out, ms
+
+    ref, _ = run("fp64", 0, False)
+
+    def rel(a, b):
+        a, b = np.asarray(a, dtype=np.float64).ravel(), np.asarray(b, dtype=np.float64).ravel()
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+    cache = {}
+
+    def err(cfg):
+        k = knobs_of(cfg)
+        if k not in cache:
+            try:
+                (tr, lse, dS), _ = run(form, k, False)
+                e = max(rel(lse, ref[1]), rel(dS[:, 0], ref[2][:, 0]), rel(dS[:, 1:7], ref[2][:, 1:7]),
+                        rel(dS[:, 7:], ref[2][:, 7:]), rel(tr, ref[0]))
+                cache[k] = e if np.isfinite(e) else float("inf")
+            except V.VbgsError:
+                # statistics so far off that a posterior is not positive
+                # definite (or non-finite): no tolerance admits the map
+                cache[k] = float("inf")
+        return cache[k]
+
+    def latency(cfg):
+        k = knobs_of(cfg)
+        try:
+            return float(np.median([run(form, k, True)[1] for _ in range(reps)]))
+        except V.VbgsError:
+            return float("inf")
+
+    return Problem(n_ops=6, edges=KNOB_EDGES, levels=("hi", "hi+lo"), err=err, latency=latency, eps=eps)
+
+
+def search_kernel_map(V, prior, S, X, eps: float = 1e-6, form: str = "fp16x3") -> dict:
+    """Run the three passes on the library's knobs; the result's "knobs" is
+    the map for vbgs_set_precision_knobs, with its error and the latency of
+    the all-kept and the chosen maps."""
+    p = kernel_problem(V, prior, S, X, eps, form)
+    res = search(p)
+    full = tuple([1] * 6)
+    res["knobs"] = knobs_of(res["final"])
+    res["left_out"] = [V.KNOBS[i] for i in range(6) if res["final"][i] == 0]
+    res["err_all_kept"] = p.err(full)
+    res["eps"] = eps
+    res["feasible"] = res["err"] <= eps
+    res["latency_ms"] = p.latency(res["final"])
+    res["latency_ms_all_kept"] = p.latency(full)
+    for k in ("precision_aware", "structure_aware", "final"):
+        res[k] = list(res[k])
+    return res

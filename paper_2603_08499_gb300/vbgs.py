@@ -54,9 +54,10 @@ EXPORTS = [
     "vbgs_proposal_report", "vbgs_proposal_config", "vbgs_proposal_weights", "vbgs_proposal_grad",
     "vbgs_proposal_clusters",
     "vbgs_proposal_bounds", "vbgs_kmeans", "vbgs_reassign", "vbgs_save_state", "vbgs_load_state",
-    "vbgs_check_frame", "vbgs_set_wait_limit", "vbgs_render", "vbgs_profile_replay", "vbgs_last_error",
-    "vbgs_destroy",
+    "vbgs_check_frame", "vbgs_set_wait_limit", "vbgs_render", "vbgs_profile_replay", "vbgs_set_precision_knobs",
+    "vbgs_get_precision_knobs", "vbgs_last_error", "vbgs_destroy",
 ]
+KNOBS = ["P1_PHI_LO", "P1_C_LO", "P2_PHI_LO", "P2_C_LO", "P2_P_LO", "P2_S_LO"]   # bit i: leave that lo term out
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 PROF_COUNT = 7
 PROF_NAMES = ["pass1", "merge", "pass2", "reduce", "mstep", "misc", "plan"]
@@ -129,6 +130,9 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
     lib.vbgs_set_wait_limit.argtypes = [C.c_longlong]
     lib.vbgs_render.argtypes = [C.c_void_p, _DP, C.c_int, C.c_int, _FP, _FP, _DP, _DP]
     lib.vbgs_profile_replay.argtypes = [C.c_void_p, C.c_int, _DP, C.POINTER(C.c_int64)]
+    lib.vbgs_set_precision_knobs.argtypes = [C.c_void_p, C.c_uint]
+    lib.vbgs_get_precision_knobs.argtypes = [C.c_void_p]
+    lib.vbgs_get_precision_knobs.restype = C.c_uint
     return lib
 
 
@@ -501,6 +505,15 @@ def vbgs_render(ctx, cam: dict, reference=None, want_image: bool = True):
     _check(lib().vbgs_render(ctx, _dp(c), W, H, _fp(img), _fp(ref), _dp(p) if ref is not None else None, _dp(ms)),
            ctx)
     return img, (float(p[0]) if ref is not None else None), float(ms[0])
+
+
+def vbgs_set_precision_knobs(ctx, knobs: int) -> None:
+    """Leave out the lo terms of the set bits (KNOBS) in the tensor-core passes."""
+    _check(lib().vbgs_set_precision_knobs(ctx, int(knobs)), ctx)
+
+
+def vbgs_get_precision_knobs(ctx) -> int:
+    return int(lib().vbgs_get_precision_knobs(ctx))
 
 
 def vbgs_set_wait_limit(cycles: int) -> None:
