@@ -70,11 +70,16 @@ typedef enum {
     VBGS_FP32 = 3
 } vbgs_precision;
 
-/* Option flags.  By default points (per frame) and components (per frame,
- * by posterior mean) are processed in Morton order, and pass 2 skips every
- * (point chunk, component tile) whose responsibilities are all below e^-50,
- * a bound taken from the tile maxima of pass 1; neither changes a result
- * beyond rounding.  The plain form sets both flags. */
+/* Option flags.  By default points (per frame) and components (by
+ * posterior mean, refreshed every fourth frame) are processed in Morton
+ * order, and the passes skip the (point tile, component tile) pairs whose
+ * responsibilities are all below e^-t by a certified bound (pass 1: a bound
+ * of the tile's logits over the points' box against a lower bound of their
+ * lse; pass 2: the tile maxima pass 1 measured); a point then loses at most
+ * K e^-t of its mass: t = ln K + 37 in the FP64 form (~1e-16) and ln K + 20
+ * in the FP32 and tensor-core forms (~2e-9, below FP32 resolution).
+ * Neither changes a result beyond the form's rounding.  The plain form sets
+ * both flags. */
 #define VBGS_FLAG_NO_REORDER 1   /* process in the caller's order */
 #define VBGS_FLAG_NO_SKIP    2   /* evaluate every tile in pass 2 */
 #define VBGS_FLAG_PROPOSAL   4   /* learned candidate proposal (see vbgs_proposal_report) */
@@ -100,8 +105,8 @@ typedef enum {
  *     frame, leaves S_past unchanged.  0 = off.
  *   autotune_cache: tensor-core forms only; non-NULL = before the first frame
  *     of each size class (rounded log2 N) pick the work decomposition with
- *     vbgs_autotune on that frame's points, read from / appended to this
- *     text file; NULL = the automatic decomposition.  The path is copied.
+ *     vbgs_autotune on that frame's points, read from / added to this JSON
+ *     file; NULL = the automatic decomposition.  The path is copied.
  *   seed: seed of the library's own random draws (the proposal network's
  *     initial weights and its audit sample); 0 = the library's default. */
 typedef struct {
@@ -152,10 +157,17 @@ int vbgs_update(vbgs_ctx *ctx, const double *points, int64_t N, int n_iters, dou
  * every scene runs the same frame update as vbgs_update(scenes[i],
  * points[i], N[i], n_iters), all of them as the branches of one CUDA graph
  * launched once, so small scenes fill the SMs that large ones leave idle.
- * The graph is cached by (scenes, N, n_iters, tuning) and replayed for later
- * frames of the same shapes.  Points are host or device arrays as in
- * vbgs_update; elbo_traces is n_scenes x n_iters (host, may be NULL).  Work
- * runs on internal streams after each scene's own stream has drained.
+ * The graph's branches are created in decreasing N K (longest first).  The
+ * graph is cached by (scenes, N, n_iters, tuning, component-order schedule)
+ * and replayed for later frames of the same shapes.  Points are host or
+ * device arrays as in vbgs_update; elbo_traces is n_scenes x n_iters (host,
+ * may be NULL).  Ordering: the graph starts after the work already queued on
+ * every scene's own stream and each scene's stream waits for the graph's
+ * end (events, no host wait); inside, the scenes run on the library's own
+ * streams (a graph's branches need a stream each).  The call synchronises
+ * once, to return the ELBO traces.  Unlike vbgs_update, each frame starts
+ * from a posterior recomputed from S_past (a replayed graph cannot take the
+ * carried one), which agrees with it bit for bit.
  * Errors as vbgs_update; the message names the scene.  Not thread-safe. */
 int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const double *const *points,
                         const int64_t *N, int n_iters, double *elbo_traces);
@@ -167,8 +179,10 @@ int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const double *con
  * skip bounds into such items, one CTA each) for this context's K and frames
  * of N
  * points, by timing 4 x 4 candidates on `points` (one E-step each; the model
- * state is unchanged).  With cache_path, the choice is read from / appended
- * to that text file keyed by form, rounded log2 N and K, and SM count.  The
+ * state is unchanged).  With cache_path, the choice is read from / added to
+ * that JSON file, {"<form>_N2^<log2 N>_K2^<log2 K>_sms<SMs>": [pass-1 tiles,
+ * pass-2 chunks], ...} (rounded log2 of N and K; written to path.tmp and
+ * renamed over path; VBGS_EIO when that fails).  The
  * CUDA-core forms have nothing to tune (returns VBGS_OK).  vbgs_get_tuning
  * reports the current choice (0 = automatic). */
 int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, const char *cache_path);

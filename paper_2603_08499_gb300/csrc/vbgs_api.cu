@@ -368,13 +368,14 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
     const bool skip = want_stats && !(ctx->flags & VBGS_FLAG_NO_SKIP);
     B.tmax = skip ? ctx->d_tmax : nullptr;
     B.minlse = skip ? ctx->d_minlse : nullptr;
+    B.skip_nats = (float)ctx->skip_nats;
     if (is_tc(ctx)) {
         const int *item_start = nullptr;
         int l = launch_pass1_tc(B.X, ctx->d_Xhl, same_points, N, ctx->K, ctx->precision == VBGS_BF16X3,
                                 ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_rec32, ctx->d_part, ctx->part_cap, B.tmax,
                                 ctx->d_p1plan, ctx->d_p1ub, ctx->d_flags, ctx->num_sms, ctx->tune_p1,
                                 ctx->d_tile_dirty + (ctx->K + 127) / 128, ctx->plan_epoch, &item_start, ctx->stream,
-                                &ctx->prof, ctx->tc_knobs);
+                                &ctx->prof, ctx->tc_knobs, ctx->skip_nats);
         ctx->plan_epoch = ctx->coef_epoch;
         ctx->prof.p1_last.alloc_gen = ctx->alloc_gen;
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -389,7 +390,7 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
                                 ctx->d_rec, B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
                                 ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->tune_p2,
                                 ctx->d_tile_dirty + 2 * ((ctx->K + 127) / 128), same_points, ctx->stream, &ctx->prof,
-                                ctx->tc_knobs);
+                                ctx->tc_knobs, ctx->skip_nats);
             if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
                                    cudaGetErrorString(cudaGetLastError()));
             ctx->launches += l;
@@ -922,8 +923,8 @@ struct BatchRuntime {
     std::mutex mu;
     cudaStream_t main = nullptr;
     std::vector<cudaStream_t> pool;
-    std::vector<cudaEvent_t> ev;
-    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> ev, ev_own;
+    cudaEvent_t fork = nullptr, done = nullptr;
     std::vector<GraphEntry> cache;   // most recent first, a few entries
     int device = -1;
 };
@@ -937,21 +938,26 @@ int batch_streams(int n)
         g_batch.device = dev;
         g_batch.pool.clear();
         g_batch.ev.clear();
+        g_batch.ev_own.clear();
         g_batch.cache.clear();
         g_batch.main = nullptr;
         g_batch.fork = nullptr;
+        g_batch.done = nullptr;
     }
     if (!g_batch.main) {
         if (cudaStreamCreateWithFlags(&g_batch.main, cudaStreamNonBlocking) != cudaSuccess) return -1;
         if (cudaEventCreateWithFlags(&g_batch.fork, cudaEventDisableTiming) != cudaSuccess) return -1;
+        if (cudaEventCreateWithFlags(&g_batch.done, cudaEventDisableTiming) != cudaSuccess) return -1;
     }
     while ((int)g_batch.pool.size() < n) {
         cudaStream_t st;
-        cudaEvent_t e;
+        cudaEvent_t e, eo;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return -1;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return -1;
+        if (cudaEventCreateWithFlags(&eo, cudaEventDisableTiming) != cudaSuccess) return -1;
         g_batch.pool.push_back(st);
         g_batch.ev.push_back(e);
+        g_batch.ev_own.push_back(eo);
     }
     return 0;
 }
@@ -990,13 +996,16 @@ extern "C" int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const 
     if (batch_streams(n_scenes) || tc_set_attributes())
         return fail(nullptr, VBGS_ECUDA, "vbgs_update_batched: stream set-up failed");
     vbgs_ctx *ctx = nullptr;   // for CU() error reporting
-    // Honour work already queued on each scene's own stream, then run every
-    // scene on a stream of the pool for the duration of the call.
+    // Every scene runs on a stream of the pool for the duration of the call,
+    // after the work already queued on its own stream (an event, no host
+    // wait); each scene's own stream waits for the graph at the end, so work
+    // the caller queues there later is ordered after this call's.
     std::vector<cudaStream_t> own(n_scenes);
     std::vector<bool> prof_on(n_scenes);
     for (int i = 0; i < n_scenes; i++) {
         own[i] = scenes[i]->stream;
-        CU(cudaStreamSynchronize(own[i]));
+        CU(cudaEventRecord(g_batch.ev_own[i], own[i]));
+        CU(cudaStreamWaitEvent(g_batch.pool[i], g_batch.ev_own[i], 0));
         scenes[i]->stream = g_batch.pool[i];
         prof_on[i] = scenes[i]->prof.on;
         scenes[i]->prof.on = false;   // no event records inside the graph
@@ -1042,7 +1051,15 @@ extern "C" int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const 
             return fail(nullptr, VBGS_ECUDA, "vbgs_update_batched: capture failed to start");
         }
         cudaEventRecord(g_batch.fork, g_batch.main);
-        for (int i = 0; i < n_scenes && rc == VBGS_OK; i++) {
+        // branches in decreasing N K (longest processing time first): the
+        // largest scenes' kernels are the first ready, the small ones fill in
+        std::vector<int> lpt(n_scenes);
+        for (int i = 0; i < n_scenes; i++) lpt[i] = i;
+        std::stable_sort(lpt.begin(), lpt.end(), [&](int a, int b) {
+            return (double)N[a] * scenes[a]->K > (double)N[b] * scenes[b]->K;
+        });
+        for (int q = 0; q < n_scenes && rc == VBGS_OK; q++) {
+            const int i = lpt[q];
             cudaStreamWaitEvent(g_batch.pool[i], g_batch.fork, 0);
             rc = update_enqueue(scenes[i], N[i], n_iters, false);   // graphs replay: no carried prior
             cudaEventRecord(g_batch.ev[i], g_batch.pool[i]);
@@ -1074,6 +1091,8 @@ extern "C" int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const 
         restore();
         return fail(nullptr, VBGS_ECUDA, "vbgs_update_batched: graph launch failed");
     }
+    CU(cudaEventRecord(g_batch.done, g_batch.main));
+    for (int i = 0; i < n_scenes; i++) CU(cudaStreamWaitEvent(own[i], g_batch.done, 0));
     // 3. results: ELBO traces and flags of every scene, one synchronisation
     std::vector<int> fl((size_t)n_scenes * FL_COUNT);
     for (int i = 0; i < n_scenes; i++) {
@@ -1098,6 +1117,50 @@ extern "C" int vbgs_update_batched(vbgs_ctx *const *scenes, int n_scenes, const 
 // ---------------------------------------------------------------------------
 // Autotuner of the tensor-core work decomposition.
 // ---------------------------------------------------------------------------
+namespace {
+
+// The autotuner's cache: a JSON object {"size class key": [pass-1 tiles,
+// pass-2 chunks], ...}, one entry per line.  The reader accepts exactly that
+// shape (what write_tuning_json writes); anything else reads as empty.
+std::map<std::string, std::pair<int, int>> read_tuning_json(const char *path)
+{
+    std::map<std::string, std::pair<int, int>> out;
+    FILE *f = fopen(path, "r");
+    if (!f) return out;
+    std::string text;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, n);
+    fclose(f);
+    size_t i = 0;
+    while ((i = text.find('"', i)) != std::string::npos) {
+        const size_t j = text.find('"', i + 1);
+        if (j == std::string::npos) break;
+        const std::string k = text.substr(i + 1, j - i - 1);
+        int a = 0, b = 0;
+        if (sscanf(text.c_str() + j + 1, " : [ %d , %d ]", &a, &b) == 2 && a >= 0 && b >= 0) out[k] = {a, b};
+        i = j + 1;
+    }
+    return out;
+}
+
+bool write_tuning_json(const char *path, const std::map<std::string, std::pair<int, int>> &entries)
+{
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fprintf(f, "{\n");
+    size_t c = 0;
+    for (const auto &e : entries)
+        fprintf(f, "  \"%s\": [%d, %d]%s\n", e.first.c_str(), e.second.first, e.second.second,
+                ++c < entries.size() ? "," : "");
+    fprintf(f, "}\n");
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), path) == 0;
+}
+
+} // namespace
+
 extern "C" int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, const char *cache_path)
 {
     if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
@@ -1107,18 +1170,14 @@ extern "C" int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, con
     const int nb = (int)std::lround(std::log2((double)N)), kb = (int)std::lround(std::log2((double)ctx->K));
     char key[96];
     snprintf(key, sizeof key, "form%d_N2^%d_K2^%d_sms%d", ctx->precision, nb, kb, ctx->num_sms);
+    std::map<std::string, std::pair<int, int>> entries;
     if (cache_path) {
-        if (FILE *f = fopen(cache_path, "r")) {
-            char k2[96];
-            int a, b;
-            while (fscanf(f, "%95s %d %d", k2, &a, &b) == 3)
-                if (!strcmp(k2, key)) {
-                    ctx->tune_p1 = a;
-                    ctx->tune_p2 = b;
-                    fclose(f);
-                    return VBGS_OK;
-                }
-            fclose(f);
+        entries = read_tuning_json(cache_path);
+        auto it = entries.find(key);
+        if (it != entries.end()) {
+            ctx->tune_p1 = it->second.first;
+            ctx->tune_p2 = it->second.second;
+            return VBGS_OK;
         }
     }
     int rc;
@@ -1153,11 +1212,12 @@ extern "C" int vbgs_autotune(vbgs_ctx *ctx, const double *points, int64_t N, con
     ctx->tune_p1 = b1;
     ctx->tune_p2 = b2;
     if ((rc = check_flags(ctx))) return rc;
-    if (cache_path)
-        if (FILE *f = fopen(cache_path, "a")) {
-            fprintf(f, "%s %d %d\n", key, b1, b2);
-            fclose(f);
-        }
+    if (cache_path) {
+        entries = read_tuning_json(cache_path);   // entries other contexts added meanwhile
+        entries[key] = {b1, b2};
+        if (!write_tuning_json(cache_path, entries))
+            return fail(ctx, VBGS_EIO, "vbgs_autotune: cannot write %s", cache_path);
+    }
     return VBGS_OK;
 }
 
@@ -1463,6 +1523,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     ctx->precision = precision;
     ctx->flags = opt ? opt->flags : 0;
     ctx->checks = opt ? opt->checks : 0;
+    ctx->skip_nats = skip_nats_for(precision, K);
     ctx->seed = opt ? opt->seed : 0;
     if (opt && opt->autotune_cache) ctx->autotune_cache = opt->autotune_cache;
     for (int i = 0; i < 36; i++) ctx->W0_h[i] = W0[i];

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ v, int 
 // With tile maxima (tmax: largest logit of every (tpb-point block, tkc-
 // component block), nkc column blocks) and per-32-point minima of lse, a
 // 64-point chunk is skipped when the largest of the maxima it touches minus
-// the smallest lse of its points is below -kSkipNats (uniform across the CTA).
+// the smallest lse of its points is below -skip_nats (uniform across the CTA).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X,
                                                     const double *__restrict__ lse, int64_t N,
@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X
                                                     double *__restrict__ part,
                                                     const float *__restrict__ tmax,
                                                     const float *__restrict__ minlse,
-                                                    int tpb, int tkc, unsigned long long *__restrict__ pairs)
+                                                    int tpb, int tkc, unsigned long long *__restrict__ pairs,
+                                                    float skip_nats)
 {
     constexpr bool kAnchored = sizeof(T) == 4;
     __shared__ T spt[kChunkN * 28];   // per point: x[6], lse, upper(x x^T)[21] (FP64 only)
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_pass2(const double *__restrict__ X
             for (int64_t r = nc / tpb; r <= (nc + cnt - 1) / tpb; r++)
                 for (int c = c_lo; c <= c_hi; c++) b = fmaxf(b, tmax[r * nkc + c]);
             for (int64_t w = nc / 32; w <= (nc + cnt - 1) / 32; w++) lmin = fminf(lmin, minlse[w]);
-            if (b - lmin < -(float)kSkipNats) continue;
+            if (b - lmin < -skip_nats) continue;
         }
         if (pairs && threadIdx.x == 0) atomicAdd(pairs, (unsigned long long)cnt * (unsigned long long)min(kThreads, K - kt0));
         __syncthreads();
@@ -371,6 +372,12 @@ constexpr int kPPT32 = 2;
 
 } // namespace
 
+double skip_nats_for(int precision, int K)
+{
+    const double t = std::log((double)std::max(K, 1)) + (precision == VBGS_FP64 ? 37.0 : 20.0);
+    return std::max(t, 20.0);
+}
+
 int launch_block_sum(const double *part, int n, double *sum_out, cudaStream_t st, Prof *pf)
 {
     pf->begin(VBGS_PROF_MERGE, st);
@@ -404,7 +411,7 @@ int launch_pass2_fp32(const EstepBuffers &B, int tpb, int tkc, cudaStream_t st, 
     dim3 g2(pl.p2_tiles, pl.p2_splits);
     pf->begin(VBGS_PROF_PASS2, st);
     k_pass2<float><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec32, B.K, B.part, B.tmax, B.minlse, tpb, tkc,
-                                            pf->on ? pf->d_pairs : nullptr);
+                                            pf->on ? pf->d_pairs : nullptr, B.skip_nats);
     pf->end(st);
     pf->begin(VBGS_PROF_REDUCE, st);
     k_reduce_splits<<<(B.K + 127) / 128, 128, 0, st>>>(B.part, pl.p2_splits, B.K, B.rec32, B.kperm, B.dS);
@@ -450,9 +457,11 @@ int launch_estep_cuda_core(const EstepBuffers &B, int precision, bool want_stats
         dim3 g2(pl.p2_tiles, pl.p2_splits);
         pf->begin(VBGS_PROF_PASS2, st);
         if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec, B.K, B.part,
-                                                          tmax, B.minlse, 256, kChunkK, pf->on ? pf->d_pairs : nullptr);
+                                                          tmax, B.minlse, 256, kChunkK, pf->on ? pf->d_pairs : nullptr,
+                                                          B.skip_nats);
         else     k_pass2<float><<<g2, kThreads, 0, st>>>(B.X, B.lse, B.N, pl.nps, B.rec32, B.K, B.part,
-                                                         tmax, B.minlse, 256, kChunkK, pf->on ? pf->d_pairs : nullptr);
+                                                         tmax, B.minlse, 256, kChunkK, pf->on ? pf->d_pairs : nullptr,
+                                                         B.skip_nats);
         pf->end(st);
         pf->begin(VBGS_PROF_REDUCE, st);
         k_reduce_splits<<<(B.K + 127) / 128, 128, 0, st>>>(B.part, pl.p2_splits, B.K,
@@ -645,8 +654,10 @@ extern "C" int vbgs_estep_noalloc(vbgs_ctx *ctx, const double *points, int64_t N
     else     k_pass1<float, kPPT32><<<g1, kThreads, 0, st>>>(X, N, ctx->d_rec32, K, pl.kps, p1, nullptr);
     k_merge<<<mb, 256, 0, st>>>(p1, pl.p1_splits, N, nullptr, lse_out, nullptr, nullptr);
     dim3 g2(pl.p2_tiles, pl.p2_splits);
-    if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part, nullptr, nullptr, 1, 1, nullptr);
-    else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part, nullptr, nullptr, 1, 1, nullptr);
+    if (f64) k_pass2<double><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec, K, part, nullptr, nullptr, 1, 1, nullptr,
+                                                        0.f);
+    else     k_pass2<float><<<g2, kThreads, 0, st>>>(X, lse_out, N, pl.nps, ctx->d_rec32, K, part, nullptr, nullptr, 1, 1, nullptr,
+                                                       0.f);
     k_reduce_splits<<<(K + 127) / 128, 128, 0, st>>>(part, pl.p2_splits, K, f64 ? nullptr : ctx->d_rec32,
                                                     ctx->d_kperm, dS_out);
     k_lse_subtract_psi<<<mb, 256, 0, st>>>(lse_out, N, ctx->d_scal);

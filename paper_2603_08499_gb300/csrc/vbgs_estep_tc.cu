@@ -700,7 +700,6 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restr
 // Tiles with ub(P, j) < LB_P - 50 nats hold only pairs with r < e^-50 and are
 // not evaluated.  One CTA per point tile, thread = point.
 // ---------------------------------------------------------------------------
-constexpr float kSkipLog2 = 72.13475204444817f;   // 50 nats in log2 units
 
 __device__ __forceinline__ float logit32_rec(const float *__restrict__ r, const float x[6])
 {
@@ -869,7 +868,7 @@ __global__ void __launch_bounds__(kListThreads) k_p1_lists(const double *__restr
                                                            const float *__restrict__ ub, int *__restrict__ list,
                                                            int *__restrict__ counts, float2 *__restrict__ lbc,
                                                            const int *__restrict__ tile_epoch, int since,
-                                                           float *__restrict__ tmax)
+                                                           float *__restrict__ tmax, float skip_log2)
 {
     pdl_wait();
     // the pass-1 tile maxima of this point tile's four 32-row blocks start at
@@ -958,7 +957,7 @@ __global__ void __launch_bounds__(kListThreads) k_p1_lists(const double *__restr
 
     for (int j0 = 0; j0 < ntiles; j0 += kListThreads) {
         const int j = j0 + t;
-        const bool keep = j < ntiles && u[j] >= LB - kSkipLog2;
+        const bool keep = j < ntiles && u[j] >= LB - skip_log2;
         const unsigned bb = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) wsum[w] = __popc(bb);
         __syncthreads();
@@ -1023,7 +1022,7 @@ __device__ __forceinline__ int p_off(int m, int pt) { return (m >> 3) * 1024 + (
 
 // The pass-2 skip bound of a 64-point chunk against tile j (uniform per CTA).
 __device__ __forceinline__ bool chunk_skipped(const float *tmax, const float *minlse, int64_t N, int ntiles, int j,
-                                              int64_t c0)
+                                              int64_t c0, float skip_nats)
 {
     if (!tmax) return false;
     const int64_t r0 = c0 / 32, r1 = (min(N, c0 + kChunk2) - 1) / 32;
@@ -1032,7 +1031,7 @@ __device__ __forceinline__ bool chunk_skipped(const float *tmax, const float *mi
         b = fmaxf(b, tmax[r * ntiles + j]);
         l = fminf(l, minlse[r]);
     }
-    return b - l < -(float)kSkipNats;
+    return b - l < -skip_nats;
 }
 
 
@@ -1041,7 +1040,7 @@ __device__ __forceinline__ bool chunk_skipped(const float *tmax, const float *mi
 // One block per tile; counts[j] and list[j * nchunks + i].
 __global__ void __launch_bounds__(256) k_p2_plan(const float *__restrict__ tmax, const float *__restrict__ minlse,
                                                  int64_t N, int ntiles, int *__restrict__ counts,
-                                                 int *__restrict__ list)
+                                                 int *__restrict__ list, float skip_nats)
 {
     pdl_wait();
     __shared__ int wsum[8];
@@ -1052,7 +1051,7 @@ __global__ void __launch_bounds__(256) k_p2_plan(const float *__restrict__ tmax,
     __syncthreads();
     for (int64_t c0 = 0; c0 < nchunks; c0 += 256) {
         const int64_t c = c0 + t;
-        const bool keep = c < nchunks && !chunk_skipped(tmax, minlse, N, ntiles, j, c * kChunk2);
+        const bool keep = c < nchunks && !chunk_skipped(tmax, minlse, N, ntiles, j, c * kChunk2, skip_nats);
         const unsigned b = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) wsum[w] = __popc(b);
         __syncthreads();
@@ -1580,8 +1579,9 @@ size_t tc_plan_ints(int64_t N, int K)
 int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
-                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs)
+                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats_d)
 {
+    const float skip_nats = (float)skip_nats_d;
     unsigned long long *pairs = pf->on ? pf->d_pairs : nullptr;
     const int ntiles = (K + kCols - 1) / kCols;
     const int64_t nchunks = (N + kChunk2 - 1) / kChunk2;
@@ -1597,7 +1597,7 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
     int *item_tile = item_start + ntiles + 1, *item_lo = item_tile + icap, *item_hi = item_lo + icap;
     int *nitems = item_hi + icap;
     pf->begin(VBGS_PROF_PLAN, st);
-    if (tmax) launch_pdl(k_p2_plan, ntiles, 256, 0, st, tmax, minlse, N, ntiles, counts, list);
+    if (tmax) launch_pdl(k_p2_plan, ntiles, 256, 0, st, tmax, minlse, N, ntiles, counts, list, skip_nats);
     launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ntiles, nchunks, cmin, tcap, item_start, item_tile,
                                    item_lo, item_hi, nitems);
     pf->end(st);
@@ -1759,7 +1759,7 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
                     const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
                     size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
                     int tiles_per_item, const int *tile_epoch, int since, const int **item_start_out,
-                    cudaStream_t st, Prof *pf, uint32_t knobs)
+                    cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats)
 {
     float2 *part = reinterpret_cast<float2 *>(part_buf);
     int launches = 0;
@@ -1804,7 +1804,7 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
         launch_pdl(k_p1_ub, dim3(ntiles, (ptiles + kCols - 1) / kCols), kCols, 0, st, boxes, ptiles, K, ntiles,
                    rec32, p1ub, te, since);
         launch_pdl(k_p1_lists, ptiles, kListThreads, 0, st, X, N, K, ntiles, rec32, p1ub, list, counts, lbc, te,
-                   since, tmax);
+                   since, tmax, (float)(skip_nats * 1.4426950408889634));
     }
     launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ptiles, ntiles, tmin, target, item_start, item_tile,
                                    item_lo, item_hi, nitems);

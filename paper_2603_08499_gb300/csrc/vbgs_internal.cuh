@@ -183,10 +183,14 @@ size_t reassign_temp_bytes(int64_t n);
 // Returns the kernel launches issued, or -1.
 int launch_reassign(const ReassignArgs &a, ReassignBuffers &rb, cudaStream_t st);
 
-// Pass 2 skips a (64-point chunk, 128-component tile) when the tile's largest
-// logit minus the smallest lse of the chunk's 256-point block is below this
-// (natural units): every skipped r_nk < e^-50 < 2e-22.
-constexpr double kSkipNats = 50.0;
+// Skipping: pass 1 leaves out a (point tile, component tile) and pass 2 a
+// (point chunk, component tile) when the tile's certified largest logit is
+// more than t nats below a lower bound of the points' lse: every left-out
+// r_nk < e^-t, so a point loses at most K e^-t of its mass.  t = ln K + 37
+// in the FP64 form (at most e^-37 ~ 1e-16, FP64 rounding) and ln K + 20 in
+// the FP32 and tensor-core forms (e^-20 ~ 2e-9, below FP32's 6e-8), at
+// least 20 nats.
+double skip_nats_for(int precision, int K);
 
 // Arguments of one E-step (pass 1 + pass 2) over a staged frame.
 struct EstepBuffers {
@@ -204,6 +208,7 @@ struct EstepBuffers {
     const int *kperm;     // position -> component (nullptr: identity)
     float *tmax;          // pass-1 tile maxima [N/256][K/64] (nullptr: no skipping)
     float *minlse;        // per 256-point block min of lse
+    float skip_nats;      // skip threshold t (skip_nats_for)
 };
 
 // ---- kernels / launchers (return number of launches, or -1 on error) ----
@@ -276,7 +281,7 @@ size_t tc_p1ub_floats(int64_t N, int K);
 int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
-                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs);
+                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats);
 int tc_pass1_auto_splits(int64_t N, int K, int num_sms);
 int tc_set_attributes();
 // Pass 1 on the tensor cores over balanced work items (point tile, list of
@@ -292,7 +297,7 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
                     const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
                     size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
                     int tiles_per_item, const int *tile_epoch, int since, const int **item_start_out,
-                    cudaStream_t st, Prof *pf, uint32_t knobs);
+                    cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats);
 // lse from pass 1's FP32 item partials, minlse per 32 points, sum of lse.
 int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
                         double *lse_part, float *minlse, double *sum_out, unsigned int *done, cudaStream_t st, Prof *pf);
@@ -484,6 +489,7 @@ struct vbgs_ctx {
     int tune_p1 = 0, tune_p2 = 0;          // work decomposition of the tensor-core passes (0 = automatic)
     uint32_t tc_knobs = 0;                 // VBGS_KNOB_*: lo terms left out of the tensor-core products
     int64_t frame_count = 0;               // frames processed (schedule of the components' Morton order)
+    double skip_nats = 50.0;               // skip threshold (skip_nats_for)
     int64_t alloc_gen = 0;                 // bumped by every (re)allocation: cached graphs check it
     size_t tmax_cap = 0;
     bool last_sorted = false;

@@ -82,13 +82,15 @@ def test_autotune_choice_is_cached_and_keeps_results(V, tmp_path):
     pr = synth.room_prior(6_000, seed=6)
     X = torch.from_numpy(synth.room_frame(0, seed=6, width=120, height=120, room=room)).cuda()
     m = V.Model(pr, "fp16x3")
-    cache = str(tmp_path / "tune.txt")
+    import json
+    cache = str(tmp_path / "tune.json")
     p1, p2 = V.vbgs_autotune(m.ctx, X, cache)
     assert p1 >= 1 and p2 >= 1
-    assert open(cache).read().count("\n") == 1
+    entries = json.load(open(cache))
+    assert list(entries.values()) == [[p1, p2]] and list(entries)[0].startswith("form1_N2^")
     m2 = V.Model(pr, "fp16x3")
     assert V.vbgs_autotune(m2.ctx, X, cache) == (p1, p2)   # read back, not re-timed
-    assert open(cache).read().count("\n") == 1
+    assert json.load(open(cache)) == entries
     # another split of the work sums FP32 partials in another grouping: the
     # results agree within the form's tolerance (ELBO 1e-4, statistics 1e-3)
     ref = V.Model(pr, "fp16x3")
@@ -96,3 +98,44 @@ def test_autotune_choice_is_cached_and_keeps_results(V, tmp_path):
     e = m.update(X, 3)
     assert O.relerr(e, e_ref) <= 1e-4
     assert O.relerr(m.stats(), ref.stats()) <= 1e-3
+
+
+def test_batched_fp16x3_matches_oracle(V):
+    """The tensor-core form through the batched graph against the FP64 oracle
+    (not only against itself run per scene): uneven scenes, 3 iterations."""
+    sc = scenes(n=4, seed=13)
+    ms = [V.Model(pr, "fp16x3") for _, _, pr in sc]
+    traces = V.vbgs_update_batched([m.ctx for m in ms], [x[0] for x in sc], 3)
+    for i, (X, _, pr) in enumerate(sc):
+        e_ref, S_ref, _, _ = O.cavi_frame(X, pr, np.zeros((pr["m0"].shape[0], 28)), 3)
+        assert O.relerr(traces[i], e_ref) <= 1e-4, i
+        S = ms[i].stats()
+        for sl in (slice(0, 1), slice(1, 7), slice(7, 28)):
+            assert O.relerr(S[:, sl], S_ref[:, sl]) <= 1e-3, (i, sl)
+        ms[i].close()
+
+
+def test_batched_orders_after_each_scenes_stream(V):
+    """Scenes on their own (non-default) streams: update, batched update,
+    update give the same statistics, bit for bit, as the same calls on
+    default-stream contexts (the graph is ordered after each scene's stream
+    and each scene's stream after the graph)."""
+    import torch
+    sc = scenes(n=3, seed=17)
+    streams = [torch.cuda.Stream() for _ in sc]
+    a = [V.Model(pr, "fp64", cuda_stream=s.cuda_stream) for (_, _, pr), s in zip(sc, streams)]
+    b = [V.Model(pr, "fp64") for _, _, pr in sc]
+    for m, x in zip(a, sc):
+        m.update(x[0], 2)
+    V.vbgs_update_batched([m.ctx for m in a], [x[1] for x in sc], 2)
+    for m, x in zip(a, sc):
+        m.update(x[0][::-1].copy(), 2)
+    for m, x in zip(b, sc):
+        m.update(x[0], 2)
+    V.vbgs_update_batched([m.ctx for m in b], [x[1] for x in sc], 2)
+    for m, x in zip(b, sc):
+        m.update(x[0][::-1].copy(), 2)
+    for ma, mb in zip(a, b):
+        assert np.array_equal(ma.stats(), mb.stats())
+        ma.close()
+        mb.close()

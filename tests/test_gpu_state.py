@@ -181,20 +181,21 @@ def test_autotune_cache_option(V, tmp_path):
     back instead of timing, and both give the same results to rounding."""
     pr = synth.room_prior(8_000, seed=47)
     frames = _frames(47, 2, 100, 100)
-    cache = str(tmp_path / "tune.txt")
+    import json
+    cache = str(tmp_path / "tune.json")
     a = V.Model(pr, "fp16x3", autotune_cache=cache)
     ta = [a.update(X, 2) for X in frames]
     tune_a = V.vbgs_get_tuning(a.ctx)
     Sa = a.stats()
     a.close()
-    lines = open(cache).read().split()
-    assert len(lines) == 3 and lines[0].startswith("form1_N2^") and tune_a != (0, 0)
+    entries = json.load(open(cache))
+    assert len(entries) == 1 and list(entries)[0].startswith("form1_N2^") and tune_a != (0, 0)
     b = V.Model(pr, "fp16x3", autotune_cache=cache)
     tb = [b.update(X, 2) for X in frames]
     assert V.vbgs_get_tuning(b.ctx) == tune_a
     assert O.relerr(np.array(tb), np.array(ta)) <= 1e-12 and O.relerr(b.stats(), Sa) <= 1e-12
     b.close()
-    assert open(cache).read().split() == lines       # read, not re-timed
+    assert json.load(open(cache)) == entries       # read, not re-timed
 
 
 def test_timeout_leaves_state_unchanged_and_context_usable(V):
