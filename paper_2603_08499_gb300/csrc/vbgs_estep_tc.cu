@@ -45,11 +45,12 @@ namespace {
 constexpr int kRows = 128;          // points per CTA tile (MMA M)
 constexpr int kCols = 128;          // components per tile (MMA N)
 constexpr int kFeat = 32;           // features (MMA K), 28 used
-constexpr int kStagesB = 4;
+constexpr int kStagesB = 2;
+constexpr int kDB = 1;              // pass-1 accumulator buffers in TMEM (128 columns each)
 constexpr int kOperandBytes = kRows * kFeat * 2;          // 8 KB (hi or lo)
 constexpr int kTileBytes = 2 * kOperandBytes;             // hi + lo
 constexpr int kThreadsTC = 160;
-constexpr int kTmemCols = 2 * kCols;
+constexpr int kTmemCols = kDB * kCols;
 constexpr long long kSpinCycles = 4000000000LL;           // ~2 s at 2 GHz
 
 struct __align__(1024) Smem {
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
 // of each 32-point row block and 128-component tile.
 // ---------------------------------------------------------------------------
 template <bool BF16>
-__global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restrict__ Xhl, int64_t N, int K,
+__global__ void __launch_bounds__(kThreadsTC, 3) k_pass1_tc(const float *__restrict__ Xhl, int64_t N, int K,
                                                             const unsigned char *__restrict__ tiles,
                                                             const float *__restrict__ hdr, int ntiles,
                                                             const int *__restrict__ list,
@@ -543,10 +544,10 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restr
         if (nt > 0) build_A(0);
         for (int jj = 0; jj < nt && ok; jj++) {
             if (jj + 1 < nt) build_A(jj + 1);
-            const int s = jj & 1;
+            const int s = jj % kDB;
             const int tj = tile_at(jj);
             const float scale = hdr[(size_t)tj * 32 + 18];
-            ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_mma[s], (uint32_t)((jj >> 1) & 1), flags));
+            ok = __all_sync(0xffffffffu, mbar_wait(&S.bar_mma[s], (uint32_t)((jj / kDB) & 1), flags));
             if (!ok) break;
             fence_after();
             const int nvalid = min(kCols, K - tj * kCols);   // columns past K are padding
@@ -624,13 +625,13 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restr
             n_loads = jj + 1;
         }
         for (int jj = 0; jj < nt && ok; jj++) {
-            const int s = jj & 1, sb = jj % kStagesB;
+            const int s = jj & 1, ds = jj % kDB, sb = jj % kStagesB;
             ok = mbar_wait(&S.bar_bfull[sb], (uint32_t)((jj / kStagesB) & 1), flags) &&
                  mbar_wait(&S.bar_afull[s], (uint32_t)((jj >> 1) & 1), flags) &&
-                 (jj < 2 || mbar_wait(&S.bar_dfree[s], (uint32_t)(((jj >> 1) - 1) & 1), flags));
+                 (jj < kDB || mbar_wait(&S.bar_dfree[ds], (uint32_t)(((jj / kDB) - 1) & 1), flags));
             if (!ok) break;
             fence_after();
-            const uint32_t d = tmem + (uint32_t)(s * kCols);
+            const uint32_t d = tmem + (uint32_t)(ds * kCols);
             const unsigned char *Ahi = S.A[s], *Alo = S.A[s] + kOperandBytes;
             const unsigned char *Bhi = S.B[sb], *Blo = S.B[sb] + kOperandBytes;
             // k-steps of 16 features: the descriptor start advances by two core matrices (256 B)
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restr
                 mma(d, smem_desc(Alo), smem_desc(Bhi), idesc, 1u);
                 mma(d, smem_desc(Alo + 256), smem_desc(Bhi + 256), idesc, 1u);
             }
-            mma_commit(&S.bar_mma[s]);
+            mma_commit(&S.bar_mma[ds]);
             mma_commit(&S.bar_bfree[sb]);
             n_mma = jj + 1;
             // refill the B stage that the previous tile's MMAs read
@@ -668,9 +669,9 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass1_tc(const float *__restr
             const int last_mma = ((n_mma - 1 - sb) >= 0) ? sb + ((n_mma - 1 - sb) / kStagesB) * kStagesB : -1;
             if (last_mma >= 0) mbar_wait(&S.bar_bfree[sb], (uint32_t)((last_mma / kStagesB) & 1), flags, true);
         }
-        for (int s = 0; s < 2; s++) {
-            const int last = ((n_mma - 1 - s) >= 0) ? s + ((n_mma - 1 - s) / 2) * 2 : -1;
-            if (last >= 0) mbar_wait(&S.bar_mma[s], (uint32_t)((last >> 1) & 1), flags, true);
+        for (int s = 0; s < kDB; s++) {
+            const int last = ((n_mma - 1 - s) >= 0) ? s + ((n_mma - 1 - s) / kDB) * kDB : -1;
+            if (last >= 0) mbar_wait(&S.bar_mma[s], (uint32_t)((last / kDB) & 1), flags, true);
         }
         // a last commit tracks every MMA this thread issued: TMEM is idle after it
         if (n_mma > 0) {
@@ -1490,7 +1491,7 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
                                                       double *__restrict__ dS, int *__restrict__ nz, bool skip_zero)
 {
     pdl_wait();
-    __shared__ float sh[3][32][29];
+    __shared__ float sh[4][32][29];
     const int j = blockIdx.x >> 2, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int m = (blockIdx.x & 3) * 32 + lane;
     const int p = j * kCols + m;
@@ -1509,7 +1510,10 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
     }
     if (nz && threadIdx.x == 0) nz[blockIdx.x] = 1;
     // the item partials are FP32 sums: add them in FP32 (a few terms), then
-    // shift to raw moments in FP64
+    // shift to raw moments in FP64.  An FP64 instruction holds a warp's
+    // sub-partition for 64 cycles, so the FP64 work is spread over the four
+    // warps: warp 0 writes the count and first moments, warps 1-3 seven
+    // second moments each; every warp forms the seven sums it reads.
     float t[28];
 #pragma unroll
     for (int f = 0; f < 28; f++) t[f] = 0.f;
@@ -1522,30 +1526,35 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
                 t[4 * f] += v.x; t[4 * f + 1] += v.y; t[4 * f + 2] += v.z; t[4 * f + 3] += v.w;
             }
         }
-    if (w > 0)
 #pragma unroll
-        for (int f = 0; f < 28; f++) sh[w - 1][lane][f] = t[f];
+    for (int f = 0; f < 28; f++) sh[w][lane][f] = t[f];
     __syncthreads();
-    if (w != 0 || p >= K) return;
-    double d[28];
+    if (p >= K) return;
+    // warp 0's partial plus the sum of the other three, in FP64
+    auto dsum = [&](int f) {
+        return (double)sh[0][lane][f] + ((double)sh[1][lane][f] + (double)sh[2][lane][f] + (double)sh[3][lane][f]);
+    };
+    double d0[7], mk[6];
 #pragma unroll
-    for (int f = 0; f < 28; f++) d[f] = (double)t[f] + ((double)sh[0][lane][f] + (double)sh[1][lane][f] + (double)sh[2][lane][f]);
-    double mk[6];
+    for (int f = 0; f < 7; f++) d0[f] = dsum(f);
 #pragma unroll
     for (int i = 0; i < 6; i++) mk[i] = rec[(size_t)p * VBGS_REC + i];
-    double out[28];
-    out[0] = d[0];
+    const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
+    double *o = dS + dst * 28;
+    if (w == 0) {
+        o[0] = d0[0];
 #pragma unroll
-    for (int i = 0; i < 6; i++) out[1 + i] = d[1 + i] + d[0] * mk[i];
+        for (int i = 0; i < 6; i++) o[1 + i] = d0[1 + i] + d0[0] * mk[i];
+        return;
+    }
+    // second moments u = 7 + 7 (w - 1) .. 7 + 7 w - 1 (upper triangle, row-major)
     int u = 7;
 #pragma unroll
     for (int a = 0; a < 6; a++)
 #pragma unroll
-        for (int b = a; b < 6; b++, u++) out[u] = d[u] + mk[a] * d[1 + b] + d[1 + a] * mk[b] + d[0] * mk[a] * mk[b];
-    const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
-    double2 *o = reinterpret_cast<double2 *>(dS + dst * 28);
-#pragma unroll
-    for (int f = 0; f < 14; f++) o[f] = make_double2(out[2 * f], out[2 * f + 1]);
+        for (int b = a; b < 6; b++, u++)
+            if (u >= 7 * w && u < 7 * w + 7)
+                o[u] = dsum(u) + mk[a] * d0[1 + b] + d0[1 + a] * mk[b] + d0[0] * mk[a] * mk[b];
 }
 
 } // namespace
