@@ -273,13 +273,13 @@ def timed_stream(V, prior, dev_frames, form, warmup, steps, stream, flush, profi
 E2E_REPEATS = 3
 
 # DRAM traffic of one k_pass1_tc launch of the room stream (K = 50,000, FP16x3):
-# dram__bytes_read.sum + dram__bytes_write.sum, the mean of the two pass-1
-# launches of an ncu --set full capture on frames of 40,000 points (8.598 and
-# 8.603 MB read, no write): the 391 coefficient tiles of 16 KB (6.4 MB), the
-# split points (1.9 MB) and the tile lists, each read once.  It belongs to the
+# dram__bytes_read.sum + dram__bytes_write.sum of the two replayed main pass-1
+# launches of an ncu --set full capture on frames of 40,000 points (6.575 MB
+# read each, no write): the coefficient tiles of 16 KB that some tile list
+# holds, the split points and the lists, each read once.  It belongs to the
 # kernel source with this digest; once the kernel is edited the figure is
 # stale and the line reports null.
-PASS1_TRAFFIC = {"bytes": 8.60e6, "sha1": "caef7f2b60f64c4af7e259aafc087da82311a296"}
+PASS1_TRAFFIC = {"bytes": 6.575e6, "sha1": "5f029cfcf55c3a42b215fd28054819f18c8db2cd"}
 CSRC = Path(__file__).resolve().parent / "paper_2603_08499_gb300" / "csrc"
 
 

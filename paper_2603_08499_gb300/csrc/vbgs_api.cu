@@ -371,16 +371,17 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
     B.skip_nats = (float)ctx->skip_nats;
     if (is_tc(ctx)) {
         const int *item_start = nullptr;
+        const double *seed_part = nullptr;
         int l = launch_pass1_tc(B.X, ctx->d_Xhl, same_points, N, ctx->K, ctx->precision == VBGS_BF16X3,
                                 ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_rec32, ctx->d_part, ctx->part_cap, B.tmax,
                                 ctx->d_p1plan, ctx->d_p1ub, ctx->d_flags, ctx->num_sms, ctx->tune_p1,
-                                ctx->d_tile_dirty + (ctx->K + 127) / 128, ctx->plan_epoch, &item_start, ctx->stream,
-                                &ctx->prof, ctx->tc_knobs, ctx->skip_nats);
+                                ctx->d_tile_dirty + (ctx->K + 127) / 128, ctx->plan_epoch, &item_start, &seed_part,
+                                ctx->stream, &ctx->prof, ctx->tc_knobs, ctx->skip_nats);
         ctx->plan_epoch = ctx->coef_epoch;
         ctx->prof.p1_last.alloc_gen = ctx->alloc_gen;
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         ctx->launches += l;
-        l = launch_lse_merge_tc(ctx->d_part, N, item_start, lse, ctx->d_lse2f, ctx->d_lse_part,
+        l = launch_lse_merge_tc(ctx->d_part, seed_part, N, item_start, lse, ctx->d_lse2f, ctx->d_lse_part,
                                 B.tmax ? ctx->d_minlse : nullptr, ctx->d_scal + SC_SUM_LSE,
                                 reinterpret_cast<unsigned int *>(ctx->d_scal + SC_MERGE_DONE), ctx->stream, &ctx->prof);
         if (l < 0) return fail(ctx, VBGS_ECUDA, "lse merge launch failed");
@@ -1416,7 +1417,7 @@ int vbgs_get_tuning(const vbgs_ctx *ctx, int *pass1_splits, int *pass2_splits)
 namespace {
 
 constexpr char kStateMagic[8] = {'V', 'B', 'G', 'S', 'S', 'T', 'A', 'T'};
-constexpr int32_t kStateVersion = 1;
+constexpr int32_t kStateVersion = 2;
 
 struct StateHeader {
     char magic[8];
@@ -1567,6 +1568,7 @@ int vbgs_init(vbgs_ctx **out, const vbgs_prior *prior, int K, int D, const vbgs_
     ctx->mp.want_bounds = 1;   // eigenvalue bounds: pass-1 tile lists and the proposal certificate
     for (int i = 0; i < 36; i++) ctx->mp.W0inv[i] = W0inv[i];
     ctx->mp.split = split ? 1 : 0;
+    ctx->mp.num_sms = ctx->num_sms;
     ctx->m0_h.assign(prior->m0, prior->m0 + (size_t)K * 6);
 
     int rc = VBGS_OK;

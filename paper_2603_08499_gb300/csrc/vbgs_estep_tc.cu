@@ -207,6 +207,19 @@ __device__ __forceinline__ dfl df_from_bits(double v)
     const float l = __uint2float_rn((unsigned)(b & 0x1fffffffu)) * scale;
     return {h, sgn ? -l : l};
 }
+// FP32 -> FP64 without an FP64 instruction: the exponent rebiased and the
+// significand widened, exact for zeros and normal numbers; subnormals,
+// infinities and NaNs take the conversion instruction.
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned ex = (b >> 23) & 0xffu;
+    const unsigned long long sgn = (unsigned long long)(b & 0x80000000u) << 32;
+    if ((b << 1) == 0u) return __longlong_as_double((long long)sgn);
+    if (ex == 0u || ex == 0xffu) return (double)f;
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(ex + 896u) << 52) |
+                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
 // sqrt(log2 e) and log2 e as double-float pairs
 constexpr float kS2h = 1.2011224031448364f, kS2l = 5.641613398665868e-09f;
 constexpr float kL2Eh = 1.4426950216293335f, kL2El = 1.925963033500011e-08f;
@@ -695,28 +708,11 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_pass1_tc(const float *__restr
 // colour Schur complement, full precision):
 //   l_k(x) <= c_k - 1/2 max(lp d_p^2, lc d_c^2, la (d_p^2 + d_c^2)),
 // with d_p, d_c the distances of m_k to the position and colour boxes of P.
-// ub(P, j) is the largest over the components of tile j.  A lower bound of
-// every point's lse: the exact FP32 lse over the single tile with the largest
-// ub (the log-sum over a subset), less 1 + 1e-5 |lse| for its rounding.
-// Tiles with ub(P, j) < LB_P - 50 nats hold only pairs with r < e^-50 and are
-// not evaluated.  One CTA per point tile, thread = point.
+// A lower bound LB_P of every point's lse is an exact FP32 log-sum over a
+// subset of the components, less 1 + 1e-5 |lse| for its rounding.  Tile j
+// is evaluated only if one of its components' bounds reaches LB_P less the
+// skip threshold; the others hold only pairs with r below e^-threshold.
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float logit32_rec(const float *__restrict__ r, const float x[6])
-{
-    float d[6];
-#pragma unroll
-    for (int i = 0; i < 6; i++) d[i] = x[i] - r[i];
-    float q = 0.f;
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-        float y = 0.f;
-#pragma unroll
-        for (int jx = 0; jx <= i; jx++) y = fmaf(r[6 + tri(i, jx)], d[jx], y);
-        q = fmaf(y, y, q);
-    }
-    return fmaf(-0.5f, q, r[27]);
-}
 
 // Bounding box (lo[6], hi[6]) of each point tile.
 __global__ void __launch_bounds__(128) k_p1_boxes(const double *__restrict__ X, int64_t N, float *__restrict__ boxes)
@@ -857,39 +853,37 @@ __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, 
     }
 }
 
-// Per point tile: the seed tile (largest ub, ties to the lower index), the
-// lower bound LB of every point's lse from its exact FP32 log-sum, and the
-// list of tiles with ub >= LB - 50 nats, in increasing order.  256 threads:
-// two per point, each over half of the seed tile's components.
-constexpr int kListThreads = 256;
-// lbc[P] = (LB, seed) of the last plan; with tile_epoch, reused when the
-// seed is the same tile and was not rebuilt since epoch `since`.
-__global__ void __launch_bounds__(kListThreads) k_p1_lists(const double *__restrict__ X, int64_t N, int K,
-                                                           int ntiles, const float *__restrict__ rec32,
-                                                           const float *__restrict__ ub, int *__restrict__ list,
-                                                           int *__restrict__ counts, float2 *__restrict__ lbc,
-                                                           const int *__restrict__ tile_epoch, int since,
-                                                           float *__restrict__ tmax, float skip_log2)
+// Pass-1 plan of point tile P around a first pass-1 launch.  k_p1_ub: the
+// largest bound of every component tile over P's box.  k_p1_seed: the seed
+// tile (the largest ub, ties to the lower index), evaluated alone by the
+// first pass-1 launch.  k_p1_plan: LB_P = the smallest over the tile's
+// points of that exact log-sum over a subset of the components, less
+// 1 + 1e-5 |lse|; the list holds the other tiles with ub >= LB_P - threshold,
+// in increasing order.
+constexpr int kPlanThreads = 256;
+constexpr int kPlanWarps = kPlanThreads / 32;
+
+// Writes the seed into list[P * ntiles] and the seed launch's work item P
+// (point tile P, list entries [0, 1)); sets the point tile's pass-1 tile
+// maxima to -inf (pass 1 writes the evaluated tiles).
+__global__ void __launch_bounds__(kPlanThreads) k_p1_seed(int64_t N, int ntiles, int ptiles,
+                                                          const float *__restrict__ ub, int *__restrict__ list,
+                                                          int *__restrict__ sitem_tile, int *__restrict__ sitem_lo,
+                                                          int *__restrict__ sitem_hi, int *__restrict__ snitems,
+                                                          float *__restrict__ tmax)
 {
     pdl_wait();
-    // the pass-1 tile maxima of this point tile's four 32-row blocks start at
-    // -inf (pass 1 writes the evaluated tiles)
-    for (int i = threadIdx.x; i < 4 * ntiles; i += kListThreads) {
-        const int64_t rb = (int64_t)blockIdx.x * 4 + i / ntiles;
+    const int P = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int i = t; i < 4 * ntiles; i += kPlanThreads) {
+        const int64_t rb = (int64_t)P * 4 + i / ntiles;
         if (rb * 32 < N) tmax[rb * ntiles + i % ntiles] = -INFINITY;
     }
-    constexpr int kW = kListThreads / 32;
-    __shared__ float sr[kCols * 28];
-    __shared__ float red[kW];
-    __shared__ int redi[kW];
-    __shared__ int wsum[kW];
-    __shared__ float hm[kRows], hs[kRows];
-    __shared__ int base_sh;
-    const int P = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    __shared__ float red[kPlanWarps];
+    __shared__ int redi[kPlanWarps];
     const float *u = ub + (size_t)P * ntiles;
     float bv = -INFINITY;
     int bj = 0x7fffffff;
-    for (int j = t; j < ntiles; j += kListThreads)
+    for (int j = t; j < ntiles; j += kPlanThreads)
         if (u[j] > bv) { bv = u[j]; bj = j; }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -899,84 +893,70 @@ __global__ void __launch_bounds__(kListThreads) k_p1_lists(const double *__restr
     }
     if (lane == 0) { red[w] = bv; redi[w] = bj; }
     __syncthreads();
-    int js;
-    {
+    if (t == 0) {
         float v = -INFINITY;
         int jx = 0x7fffffff;
-        for (int q = 0; q < kW; q++)
+        for (int q = 0; q < kPlanWarps; q++)
             if (red[q] > v || (red[q] == v && redi[q] < jx)) { v = red[q]; jx = redi[q]; }
-        js = jx == 0x7fffffff ? 0 : jx;
+        list[(size_t)P * ntiles] = jx == 0x7fffffff ? 0 : jx;
+        sitem_tile[P] = P;
+        sitem_lo[P] = 0;
+        sitem_hi[P] = 1;
+        if (P == 0) *snitems = ptiles;
     }
-    const float2 prev = lbc[P];
-    const bool reuse = tile_epoch && (int)prev.y == js && tile_epoch[js] <= since;   // uniform
-    float LB;
-    if (reuse) {
-        LB = prev.x;
-        if (t == 0) base_sh = 0;
-        __syncthreads();
-    } else {
-        const int ks = js * kCols, ns = min(kCols, K - ks);
-        for (int i = t; i < ns * 28; i += kListThreads) {
-            const int mm = i / 28, f = i - mm * 28;
-            sr[i] = rec32[(size_t)(ks + mm) * VBGS_REC + f];
-        }
-        const int pt = t & (kRows - 1), half = t / kRows;
-        const int64_t n = (int64_t)P * kRows + pt;
-        const bool live = n < N;
-        float x[6];
-#pragma unroll
-        for (int i = 0; i < 6; i++) x[i] = (float)X[(live ? n : (int64_t)P * kRows) * VBGS_XS + i];
-        __syncthreads();
-        // (approximate ex2 / lg2: relative errors of a few 2^-22, far inside the
-        // 1 + 1e-5 |lse| margin below)
-        float mx = -INFINITY, sm = 0.f;
-        const int m_end = half ? ns : min(ns, kCols / 2);
-        for (int mm = half * (kCols / 2); mm < m_end; mm++) {
-            const float l = logit32_rec(sr + mm * 28, x);
-            if (l > mx) { sm = sm * ex2f(mx - l) + 1.f; mx = l; }
-            else sm += ex2f(l - mx);
-        }
-        if (half) { hm[pt] = mx; hs[pt] = sm; }
-        __syncthreads();
-        float lb = INFINITY;
-        if (!half) {
-            const float m1 = hm[pt], s1 = hs[pt];
-            if (m1 > mx) { sm = sm * ex2f(mx - m1) + s1; mx = m1; }
-            else if (m1 > -INFINITY) sm += s1 * ex2f(m1 - mx);
-            lb = mx + __log2f(sm);
-            lb = live ? lb - (1.f + 1e-5f * fabsf(lb)) : INFINITY;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lb = fminf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
-        if (lane == 0) red[w] = lb;
-        if (t == 0) base_sh = 0;
-        __syncthreads();
-        LB = red[0];
-        for (int q = 1; q < kW; q++) LB = fminf(LB, red[q]);
-        if (t == 0) lbc[P] = make_float2(LB, (float)js);
-    }
+}
 
-    for (int j0 = 0; j0 < ntiles; j0 += kListThreads) {
+// spart: the seed launch's partials (point tile P: rows P * 128 ..).
+__global__ void __launch_bounds__(kPlanThreads) k_p1_plan(int64_t N, int ntiles, const float2 *__restrict__ spart,
+                                                          const float *__restrict__ ub, int *__restrict__ list,
+                                                          int *__restrict__ counts, float skip_log2)
+{
+    pdl_wait();
+    const int P = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    __shared__ float red[kPlanWarps];
+    __shared__ int wsum[kPlanWarps];
+    __shared__ int base_sh;
+    const float *u = ub + (size_t)P * ntiles;
+    int *row = list + (size_t)P * ntiles;
+    const int js = row[0];
+    // LB: the seed tile's log-sums (log2 units), less 1 + 1e-5 |lse| for the
+    // rounding of the partial and of the final merge
+    float lb = INFINITY;
+    if (t < kRows && (int64_t)P * kRows + t < N) {
+        const float2 q = spart[(size_t)P * kRows + t];
+        const float l = q.x + __log2f(q.y);
+        lb = l - (1.f + 1e-5f * fabsf(l));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lb = fminf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+    if (lane == 0) red[w] = lb;
+    if (t == 0) base_sh = 0;
+    __syncthreads();
+    float LB = red[0];
+    for (int q = 1; q < kPlanWarps; q++) LB = fminf(LB, red[q]);
+    const float thr = LB - skip_log2;
+    // ordered compaction; the reads of a chunk precede its writes, which land
+    // at or before the entries read (row[0], the seed, is read above)
+    for (int j0 = 0; j0 < ntiles; j0 += kPlanThreads) {
         const int j = j0 + t;
-        const bool keep = j < ntiles && u[j] >= LB - skip_log2;
+        const bool keep = j < ntiles && j != js && u[j] >= thr;
         const unsigned bb = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) wsum[w] = __popc(bb);
         __syncthreads();
         int off = base_sh;
         for (int i = 0; i < w; i++) off += wsum[i];
         off += __popc(bb & ((1u << lane) - 1u));
-        if (keep) list[(size_t)P * ntiles + off] = j;
+        if (keep) row[off] = j;
         __syncthreads();
         if (t == 0) {
             int tot = 0;
-            for (int i = 0; i < kW; i++) tot += wsum[i];
+            for (int i = 0; i < kPlanWarps; i++) tot += wsum[i];
             base_sh += tot;
         }
         __syncthreads();
     }
     if (t == 0) counts[P] = base_sh;
 }
-
 
 // ---------------------------------------------------------------------------
 // Pass 2 on the tensor cores: the fused statistics contraction of Eq. 3.
@@ -1509,11 +1489,13 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
         return;
     }
     if (nz && threadIdx.x == 0) nz[blockIdx.x] = 1;
-    // the item partials are FP32 sums: add them in FP32 (a few terms), then
-    // shift to raw moments in FP64.  An FP64 instruction holds a warp's
-    // sub-partition for 64 cycles, so the FP64 work is spread over the four
-    // warps: warp 0 writes the count and first moments, warps 1-3 seven
-    // second moments each; every warp forms the seven sums it reads.
+    // The item partials are FP32 sums: they and the four warp sums are added
+    // in FP32, then shifted to raw moments in FP64.  An FP64 instruction
+    // holds a warp's sub-partition for 64 cycles, so the FP64 part is three
+    // FMAs per second moment, spread over the four warps (warp 0: the count
+    // and first moments, warps 1-3: seven second moments each), and the
+    // FP32 -> FP64 conversions are exact bit manipulations on the integer
+    // pipe.
     float t[28];
 #pragma unroll
     for (int f = 0; f < 28; f++) t[f] = 0.f;
@@ -1530,13 +1512,12 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
     for (int f = 0; f < 28; f++) sh[w][lane][f] = t[f];
     __syncthreads();
     if (p >= K) return;
-    // warp 0's partial plus the sum of the other three, in FP64
-    auto dsum = [&](int f) {
-        return (double)sh[0][lane][f] + ((double)sh[1][lane][f] + (double)sh[2][lane][f] + (double)sh[3][lane][f]);
+    auto fsum = [&](int f) {   // the four warp sums in warp order
+        return f2d_exact((sh[0][lane][f] + sh[1][lane][f]) + (sh[2][lane][f] + sh[3][lane][f]));
     };
     double d0[7], mk[6];
 #pragma unroll
-    for (int f = 0; f < 7; f++) d0[f] = dsum(f);
+    for (int f = 0; f < 7; f++) d0[f] = fsum(f);
 #pragma unroll
     for (int i = 0; i < 6; i++) mk[i] = rec[(size_t)p * VBGS_REC + i];
     const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
@@ -1544,17 +1525,18 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
     if (w == 0) {
         o[0] = d0[0];
 #pragma unroll
-        for (int i = 0; i < 6; i++) o[1 + i] = d0[1 + i] + d0[0] * mk[i];
+        for (int i = 0; i < 6; i++) o[1 + i] = fma(d0[0], mk[i], d0[1 + i]);
         return;
     }
-    // second moments u = 7 + 7 (w - 1) .. 7 + 7 w - 1 (upper triangle, row-major)
+    // second moments u = 7 + 7 (w - 1) .. 7 + 7 w - 1 (upper triangle, row-major):
+    // S2' + S1'_a m_b + m_a S1'_b + (N' m_a) m_b
     int u = 7;
 #pragma unroll
     for (int a = 0; a < 6; a++)
 #pragma unroll
         for (int b = a; b < 6; b++, u++)
             if (u >= 7 * w && u < 7 * w + 7)
-                o[u] = dsum(u) + mk[a] * d0[1 + b] + d0[1 + a] * mk[b] + d0[0] * mk[a] * mk[b];
+                o[u] = fma(d0[0] * mk[a], mk[b], fma(mk[a], d0[1 + b], fma(d0[1 + a], mk[b], fsum(u))));
 }
 
 } // namespace
@@ -1686,10 +1668,12 @@ __global__ void k_split_points(const double *__restrict__ X, int64_t N, float *_
     Xhl[n * 16 + 8 + q] = lo;
 }
 
-// lse_n from the item partials of its point tile (FP32, log2 units: the
-// partials carry the tensor-core pass's FP32 sums), natural-unit lse in FP64,
-// the smallest lse per 32 points and per-block FP64 sums of lse.
+// lse_n from the item partials of its point tile and, with skipping, the
+// seed launch's partial (FP32, log2 units: the partials carry the
+// tensor-core pass's FP32 sums), natural-unit lse in FP64, the smallest lse
+// per 32 points and per-block FP64 sums of lse.
 __global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part, const int *__restrict__ item_start,
+                                                 const float2 *__restrict__ spart,
                                                  int64_t N, double *__restrict__ lse, float *__restrict__ lse2f,
                                                  double *__restrict__ lse_part, float *__restrict__ minlse,
                                                  unsigned int *__restrict__ done, double *__restrict__ sum_out)
@@ -1703,9 +1687,10 @@ __global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part
         const int64_t P = n >> 7;
         const size_t row = (size_t)(n & 127);
         const int q0 = item_start[P], q1 = item_start[P + 1];
-        float M = -INFINITY;
+        const float2 sp = spart ? spart[(size_t)n] : make_float2(-INFINITY, 0.f);
+        float M = sp.x;
         for (int q = q0; q < q1; q++) M = fmaxf(M, part[(size_t)q * kRows + row].x);
-        float sm = 0.f;
+        float sm = sp.y > 0.f ? sp.y * ex2f(sp.x - M) : 0.f;
         for (int q = q0; q < q1; q++) {
             const float2 p = part[(size_t)q * kRows + row];
             if (p.y > 0.f) sm += p.y * ex2f(p.x - M);
@@ -1755,20 +1740,22 @@ constexpr int kItemCap1 = 2048;
 size_t tc_p1plan_ints(int64_t N, int K)
 {
     const size_t pt = (size_t)((N + kRows - 1) / kRows), nt = (size_t)((K + kCols - 1) / kCols);
-    return pt * nt + pt + (pt + 1) + 3 * (kItemCap1 + pt) + 1;
+    // lists, counts, items; the seed launch's items
+    return pt * nt + pt + (pt + 1) + 3 * (kItemCap1 + pt) + 1 + 3 * pt + 1;
 }
 size_t tc_p1ub_floats(int64_t N, int K)
 {
     const size_t pt = (size_t)((N + kRows - 1) / kRows);
-    // ub, the point-tile boxes, then (LB, seed) per tile at an even offset (float2)
-    return pt * (size_t)((K + kCols - 1) / kCols) + 14 * pt + 2;
+    // coarse bounds, the point-tile boxes, then the seed launch's partials
+    // (128 float2 per point tile) at an even offset
+    return pt * (size_t)((K + kCols - 1) / kCols) + 12 * pt + 1 + 2 * (size_t)kRows * pt;
 }
 
 int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, int K, bool bf16,
                     const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
                     size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
                     int tiles_per_item, const int *tile_epoch, int since, const int **item_start_out,
-                    cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats)
+                    const double **seed_part_out, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats)
 {
     float2 *part = reinterpret_cast<float2 *>(part_buf);
     int launches = 0;
@@ -1798,6 +1785,18 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
         }
     }
     const int target = tmax ? std::min(icap, std::max(ptiles + 1, 8 * num_sms)) : icap;
+    const size_t smem = sizeof(Smem) + 1024;
+    if (tc_set_attributes()) return -1;
+    auto pass1 = [&](int grid, const int *lst, const int *it, const int *il, const int *ih, const int *ni,
+                     float2 *out) {
+        if (bf16)
+            launch_pdl(k_pass1_tc<true>, grid, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, it, il, ih,
+                       ni, out, tmax, flags, pairs1, knobs);
+        else
+            launch_pdl(k_pass1_tc<false>, grid, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, it, il, ih,
+                       ni, out, tmax, flags, pairs1, knobs);
+    };
+    *seed_part_out = nullptr;
     pf->begin(VBGS_PROF_PLAN, st);
     if (tmax) {
         float *boxes = p1ub + (size_t)ptiles * ntiles;
@@ -1807,19 +1806,27 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
         }
         // bounds of the tiles rebuilt since the last plan of these points
         const int *te = same_points ? tile_epoch : nullptr;
+        launch_pdl(k_p1_ub, dim3(ntiles, (ptiles + kCols - 1) / kCols), kCols, 0, st, (const float *)boxes, ptiles, K,
+                   ntiles, rec32, p1ub, te, since);
+        int *sitem_tile = nitems + 1, *sitem_lo = sitem_tile + ptiles, *sitem_hi = sitem_lo + ptiles;
+        int *snitems = sitem_hi + ptiles;
         // (float2: 8-byte aligned, so an even float offset)
-        const size_t lbc_off = ((size_t)ptiles * ntiles + 12 * (size_t)ptiles + 1) & ~(size_t)1;
-        float2 *lbc = reinterpret_cast<float2 *>(p1ub + lbc_off);
-        launch_pdl(k_p1_ub, dim3(ntiles, (ptiles + kCols - 1) / kCols), kCols, 0, st, boxes, ptiles, K, ntiles,
-                   rec32, p1ub, te, since);
-        launch_pdl(k_p1_lists, ptiles, kListThreads, 0, st, X, N, K, ntiles, rec32, p1ub, list, counts, lbc, te,
-                   since, tmax, (float)(skip_nats * 1.4426950408889634));
+        float2 *spart = reinterpret_cast<float2 *>(p1ub + (((size_t)ptiles * ntiles + 12 * (size_t)ptiles + 1) & ~(size_t)1));
+        launch_pdl(k_p1_seed, ptiles, kPlanThreads, 0, st, N, ntiles, ptiles, (const float *)p1ub, list, sitem_tile,
+                   sitem_lo, sitem_hi, snitems, tmax);
+        pf->end(st);
+        // the seed tile of every point tile, on the tensor cores
+        pf->begin(VBGS_PROF_PASS1, st);
+        pass1(ptiles, list, sitem_tile, sitem_lo, sitem_hi, snitems, spart);
+        pf->end(st);
+        pf->begin(VBGS_PROF_PLAN, st);
+        launch_pdl(k_p1_plan, ptiles, kPlanThreads, 0, st, N, ntiles, (const float2 *)spart, (const float *)p1ub,
+                   list, counts, (float)(skip_nats * 1.4426950408889634));
+        *seed_part_out = reinterpret_cast<const double *>(spart);
     }
     launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ptiles, ntiles, tmin, target, item_start, item_tile,
                                    item_lo, item_hi, nitems);
     pf->end(st);
-    const size_t smem = sizeof(Smem) + 1024;
-    if (tc_set_attributes()) return -1;
     pf->begin(VBGS_PROF_PASS1, st);
     const int *lst = tmax ? list : nullptr;
     {
@@ -1844,24 +1851,20 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
         L.flags = flags;
         L.knobs = knobs;
     }
-    if (bf16)
-        launch_pdl(k_pass1_tc<true>, target, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
-                                                           item_hi, nitems, part, tmax, flags, pairs1, knobs);
-    else
-        launch_pdl(k_pass1_tc<false>, target, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, item_tile, item_lo,
-                                                            item_hi, nitems, part, tmax, flags, pairs1, knobs);
+    pass1(target, lst, item_tile, item_lo, item_hi, nitems, part);
     pf->end(st);
     *item_start_out = item_start;
-    return cudaGetLastError() == cudaSuccess ? launches + (tmax ? 4 : 2) : -1;
+    return cudaGetLastError() == cudaSuccess ? launches + (tmax ? 6 : 2) : -1;
 }
 
-int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
-                        double *lse_part, float *minlse, double *sum_out, unsigned int *done, cudaStream_t st, Prof *pf)
+int launch_lse_merge_tc(const double *part_buf, const double *seed_part, int64_t N, const int *item_start, double *lse,
+                        float *lse2f, double *lse_part, float *minlse, double *sum_out, unsigned int *done,
+                        cudaStream_t st, Prof *pf)
 {
     const int mb = (int)((N + 63) / 64);
     pf->begin(VBGS_PROF_MERGE, st);
-    launch_pdl(k_merge_tc, mb, 64, 0, st, reinterpret_cast<const float2 *>(part_buf), item_start, N, lse, lse2f, lse_part,
-               minlse, done, sum_out);
+    launch_pdl(k_merge_tc, mb, 64, 0, st, reinterpret_cast<const float2 *>(part_buf), item_start,
+               reinterpret_cast<const float2 *>(seed_part), N, lse, lse2f, lse_part, minlse, done, sum_out);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }

@@ -141,6 +141,7 @@ struct MstepParams {
     int K;
     int want_bounds;   // write the eigenvalue bounds of the proposal certificate (record floats 28-30)
     int split;         // the split model: W^-1 block diagonal (position, colour), 3-D Wishart terms per block
+    int num_sms;       // SMs of the device (grid of the M-step's list kernel)
 };
 
 // Box of the Morton codes (positions only).
@@ -285,22 +286,26 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
 int tc_pass1_auto_splits(int64_t N, int K, int num_sms);
 int tc_set_attributes();
 // Pass 1 on the tensor cores over balanced work items (point tile, list of
-// component tiles).  With tmax (skipping on): the component tiles whose
-// certified logit bound over the point tile is within 50 nats of a lower bound
-// of every point's lse; tmax of the other tiles is -inf.  same_points: X and N
-// are the previous call's (its FP32 split Xhl and point-tile boxes are
-// reused; tile_epoch / since: only the bounds of tiles built after epoch
-// `since` are recomputed, and a point tile's lse lower bound is kept while
-// its seed tile is unchanged).  item_start_out: the
-// item table the lse merge reads.
+// component tiles).  With tmax (skipping on): a first launch evaluates each
+// point tile's seed tile (the largest certified logit bound); its exact
+// log-sums give a lower bound of every point's lse, and the main launch
+// evaluates the other component tiles whose certified bound over the point
+// tile is within the skip threshold of it; tmax of the tiles left out is
+// -inf.  same_points: X and N are the previous call's (its FP32 split Xhl
+// and point-tile boxes are reused; tile_epoch / since: only the bounds of
+// tiles built after epoch `since` are recomputed).  item_start_out: the item
+// table the lse merge reads; seed_part_out: the seed launch's partials
+// (nullptr without skipping).
 int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, int K, bool bf16,
                     const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
                     size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
                     int tiles_per_item, const int *tile_epoch, int since, const int **item_start_out,
-                    cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats);
-// lse from pass 1's FP32 item partials, minlse per 32 points, sum of lse.
-int launch_lse_merge_tc(const double *part_buf, int64_t N, const int *item_start, double *lse, float *lse2f,
-                        double *lse_part, float *minlse, double *sum_out, unsigned int *done, cudaStream_t st, Prof *pf);
+                    const double **seed_part_out, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats);
+// lse from pass 1's FP32 item partials and the seed launch's (nullable),
+// minlse per 32 points, sum of lse.
+int launch_lse_merge_tc(const double *part_buf, const double *seed_part, int64_t N, const int *item_start, double *lse,
+                        float *lse2f, double *lse_part, float *minlse, double *sum_out, unsigned int *done,
+                        cudaStream_t st, Prof *pf);
 int launch_block_sum(const double *part, int n, double *sum_out, cudaStream_t st, Prof *pf);
 
 // Learned proposal (vbgs_proposal.cu).

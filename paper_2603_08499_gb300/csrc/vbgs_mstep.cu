@@ -13,6 +13,7 @@
 // W^-1 = L L^T, and the constant c of log rho) and KL(q || p).
 #include "vbgs_internal.cuh"
 #include <math.h>
+#include <algorithm>
 
 namespace vbgs {
 
@@ -385,18 +386,22 @@ __global__ void __launch_bounds__(64) k_mstep(MstepParams P, const double *__res
 }
 
 // ---------------------------------------------------------------------------
-// M-step of an iteration (dS given).  Few components change in a frame (a few
-// hundred of 50,000 on the room stream), and an FP64 instruction occupies a
-// warp's SM sub-partition for 64 cycles whatever its active lanes, so a
-// thread-per-component kernel is bound by the latency of one component's
+// M-step of an iteration (dS given).  Few components change in an iteration
+// (a few thousand of 50,000 on the room stream), and an FP64 instruction
+// occupies a warp's SM sub-partition for 64 cycles whatever its active lanes,
+// so a thread-per-component kernel is bound by the latency of one component's
 // serial FP64 chain.  k_mstep_scan compacts the components to recompute into
 // a list (the others only hand over q = p); k_mstep_list then computes each
 // five listed components with a warp, six lanes each over the rows of its
 // 6 x 6 matrices (about 300 FP64 instructions per warp instead of 650 for
-// one chain), or, for long lists, one thread per component as k_mstep does.  Every entry is formed by the
-// same operations in the same order as in mstep_thread.
-// ---------------------------------------------------------------------------
-constexpr int kListWarpMax = 5 * 1216;   // longest list computed five components to a warp (2 warps per SM sub-partition)
+// one chain), or, for long lists, one thread per component as k_mstep does.
+// k_mstep_list runs one CTA of four warps per SM (its shared-memory request
+// keeps a second CTA off the SM), so each sub-partition's FP64 pipe serves
+// one warp, and the warps take groups of five from a counter: two busy warps
+// never share a pipe while another stands idle.  Every entry is formed by
+// the same operations in the same order as in mstep_thread.
+constexpr int kListWarpMax = 5 * 1216;   // longest list computed five components to a warp
+constexpr int kListSmem = 120 * 1024;    // dynamic shared memory of k_mstep_list: one CTA per SM
 
 __global__ void __launch_bounds__(128) k_mstep_scan(int K, const double *__restrict__ dS, const int *__restrict__ kperm,
                                                     const double *__restrict__ pc, double *__restrict__ kls,
@@ -588,8 +593,6 @@ __global__ void __launch_bounds__(128) k_mstep_list(MstepParams P, const double 
     pdl_wait();
     const int n = *count;
     if (n <= kListWarpMax) {
-        const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-        if (gw * 5 >= n) return;   // warp-uniform
         const int lane = threadIdx.x & 31, g = lane / 6, r = lane - 6 * (lane / 6);
         const int rr = g < 5 ? r : 0;
         double w0r[6];   // W0^-1 at (min(rr, j), max(rr, j)), selected without indexing the parameter array
@@ -601,7 +604,12 @@ __global__ void __launch_bounds__(128) k_mstep_list(MstepParams P, const double 
             for (int q = 0; q < 36; q++) w = sel64(q == idx, P.W0inv[q], w);
             w0r[j] = w;
         }
-        for (int e0 = gw * 5; e0 < n; e0 += nw * 5) {
+        int *next = const_cast<int *>(count) + 1;   // groups handed out (zeroed with the count)
+        for (;;) {
+            int e0 = 0;
+            if (lane == 0) e0 = atomicAdd(next, 5);
+            e0 = __shfl_sync(0xffffffffu, e0, 0);
+            if (e0 >= n) break;   // warp-uniform
             const int e = e0 + g;
             const bool gv = g < 5 && e < n;
             const int pos = list[gv ? e : e0];
@@ -908,8 +916,9 @@ size_t mstep_prior_cache_doubles(int K) { return (size_t)K * kPC; }
 
 size_t mstep_cache_doubles(int K)
 {
-    // cache, block sums, KL inputs, then the list of components to recompute (K + 1 ints)
-    return (size_t)K * kPC + (size_t)((K + 127) / 128) * 4 + (size_t)K * kKS + (size_t)(K + 2) / 2;
+    // cache, block sums, KL inputs, then the list of components to recompute
+    // (K ints, its count and the list kernel's group counter)
+    return (size_t)K * kPC + (size_t)((K + 127) / 128) * 4 + (size_t)K * kKS + (size_t)(K + 4) / 2;
 }
 
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
@@ -932,13 +941,20 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
         pf->end(st);
     } else {
         int *list = reinterpret_cast<int *>(kls + (size_t)K * kKS), *count = list + K;
-        if (cudaMemsetAsync(count, 0, sizeof(int), st) != cudaSuccess) return -1;
+        if (cudaMemsetAsync(count, 0, 2 * sizeof(int), st) != cudaSuccess) return -1;
         pf->begin(VBGS_PROF_MSTEP, st);
         launch_pdl(k_mstep_scan, (K + 127) / 128, 128, 0, st, K, dS, kperm, cache, kls, list, count);
         pf->end(st);
         pf->begin(VBGS_PROF_MSTEP, st);
-        launch_pdl(k_mstep_list, kListWarpMax / 5 / 4, 128, 0, st, P, m0, Spast, dS, kperm, list, count, rec, rec32,
-                   cache, kls, flags, tile_dirty, cache_next);
+        static bool attr_set = false;
+        if (!attr_set) {
+            if (cudaFuncSetAttribute(k_mstep_list, cudaFuncAttributeMaxDynamicSharedMemorySize, kListSmem) !=
+                cudaSuccess)
+                return -1;
+            attr_set = true;
+        }
+        launch_pdl(k_mstep_list, std::max(1, P.num_sms), 128, kListSmem, st, P, m0, Spast, dS, kperm, list, count,
+                   rec, rec32, cache, kls, flags, tile_dirty, cache_next);
         pf->end(st);
         launches = 4;
     }
