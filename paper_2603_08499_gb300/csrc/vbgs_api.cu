@@ -269,10 +269,13 @@ int run_mstep(vbgs_ctx *ctx, const double *dS, bool write_next = false)
     int rc;
     if ((rc = join_side(ctx))) return rc;
     if (!dS) ctx->next_prior_ready = false;
+    // the list the last E-step built belongs to these statistics only
+    const bool listed = dS == ctx->d_dS && ctx->mstep_listed;
+    ctx->mstep_listed = false;
     int l = launch_mstep(ctx->mp, ctx->d_m0, ctx->d_Spast, dS, ctx->d_kperm, ctx->d_rec, ctx->d_rec32, ctx->d_pcache,
                          ctx->d_flags, ctx->d_scal, is_tc(ctx) ? ctx->d_tile_dirty : nullptr,
                          write_next ? ctx->d_pcache_next : nullptr, ctx->stream, ctx->side, ctx->ev_fork, ctx->ev_join,
-                         &ctx->prof);
+                         &ctx->prof, listed);
     if (l < 0) return fail(ctx, VBGS_ECUDA, "posterior update launch failed");
     ctx->side_pending = true;
     ctx->launches += l;
@@ -387,14 +390,21 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
         if (l < 0) return fail(ctx, VBGS_ECUDA, "lse merge launch failed");
         ctx->launches += l;
         if (want_stats) {
+            // The reduction also builds the M-step's list, which rewrites the
+            // KL hand-off: the KL work of the last M-step (second stream) must
+            // be done first.
+            int rc;
+            if ((rc = join_side(ctx))) return rc;
+            const MstepList ml = mstep_list_view(ctx->d_pcache, ctx->K);
             l = launch_pass2_tc(ctx->d_Xhl, ctx->d_lse2f, N, ctx->K, ctx->precision == VBGS_BF16X3, ctx->d_tc_tiles, ctx->d_tc_hdr,
                                 ctx->d_rec, B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
                                 ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->tune_p2,
                                 ctx->d_tile_dirty + 2 * ((ctx->K + 127) / 128), same_points, ctx->stream, &ctx->prof,
-                                ctx->tc_knobs, ctx->skip_nats);
+                                ctx->tc_knobs, ctx->skip_nats, &ml);
             if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
                                    cudaGetErrorString(cudaGetLastError()));
             ctx->launches += l;
+            ctx->mstep_listed = true;
         }
         return VBGS_OK;
     }
@@ -719,6 +729,7 @@ int prop_estep(vbgs_ctx *ctx, int64_t N, bool last_iter)
         return fail(ctx, VBGS_ECUDA, "exact-row compaction failed");
     prop_gather_rows(X, P.erows, ne, P.Xe, ctx->stream);
     if ((rc = run_estep_on(ctx, P.Xe, ne, P.lse_e, true))) return rc;
+    ctx->mstep_listed = false;   // the candidate statistics are added below
     const size_t aneed = prop_audit_floats(ne, ctx->K);
     if (aneed > P.apart_cap) {
         if ((rc = dalloc(ctx, &P.apart, aneed))) return rc;
@@ -828,6 +839,7 @@ int update_enqueue(vbgs_ctx *ctx, int64_t N, int n_iters, bool carry_prior)
     // per-scene stream on the same orders.
     const bool resort = reorder && resort_due(ctx);
     ctx->frame_count++;
+    ctx->mstep_listed = false;
     ctx->next_prior_ready = false;
     ctx->next_written = false;
     if (from_next && resort) std::swap(ctx->d_kinv, ctx->d_kinv_alt);   // keep the old inverse order

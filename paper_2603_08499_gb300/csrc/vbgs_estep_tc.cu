@@ -1057,12 +1057,15 @@ __global__ void __launch_bounds__(256) k_p2_plan(const float *__restrict__ tmax,
 // total / C + ntiles <= tcap.  item_start[j] is the first item of tile j
 // (exclusive scan); items are in tile order.  One block.
 constexpr int kItemCap = 2048;
+// zero2 (nullable): two ints set to zero for a later kernel of the stream.
 __global__ void __launch_bounds__(1024) k_p2_items(const int *__restrict__ counts, int ntiles, int64_t nchunks,
                                                    int cmin, int tcap, int *__restrict__ item_start,
                                                    int *__restrict__ item_tile, int *__restrict__ item_lo,
-                                                   int *__restrict__ item_hi, int *__restrict__ nitems)
+                                                   int *__restrict__ item_hi, int *__restrict__ nitems,
+                                                   int *__restrict__ zero2)
 {
     pdl_wait();
+    if (zero2 && threadIdx.x < 2) zero2[threadIdx.x] = 0;
     __shared__ long long red[32];
     __shared__ int scan[1024];
     __shared__ int carry_sh, C_sh;
@@ -1465,10 +1468,13 @@ __global__ void __launch_bounds__(kThreadsTC, 2) k_pass2_tc(const float *__restr
 // nz (nullable): per block, whether its rows of dS were last written nonzero;
 // with skip_zero, a block without items whose rows are already zero writes
 // nothing (iterations after the first of a frame: same points and order).
+// ml.list (nullable): warp 0 also enters its 32 positions into the M-step's
+// list (MstepList).
 __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ part,
                                                       const int *__restrict__ item_start, int K,
                                                       const double *__restrict__ rec, const int *__restrict__ kperm,
-                                                      double *__restrict__ dS, int *__restrict__ nz, bool skip_zero)
+                                                      double *__restrict__ dS, int *__restrict__ nz, bool skip_zero,
+                                                      MstepList ml)
 {
     pdl_wait();
     __shared__ float sh[4][32][29];
@@ -1476,16 +1482,40 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
     const int m = (blockIdx.x & 3) * 32 + lane;
     const int p = j * kCols + m;
     const int q0 = item_start[j], q1 = item_start[j + 1];
+    // warp 0, all lanes: position p (zero: its statistics are all zero) into
+    // the M-step's list, or its "q = p" hand-off
+    auto list_entry = [&](bool zero) {
+        if (!ml.list) return;
+        bool act = false;
+        if (p < K) {
+            const size_t k = kperm ? (size_t)kperm[p] : (size_t)p;
+            act = !(zero && ml.pc33[k * ml.pc_stride] != 0.0);
+            if (!act) {
+                double *ks = ml.ks33 + k * ml.ks_stride;
+                ks[0] = 0.0;
+                ks[1] = 0.0;
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, act);
+        if (b) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(ml.count, __popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (act) ml.list[base + __popc(b & ((1u << lane) - 1u))] = p;
+        }
+    };
     if (q0 == q1) {
         // no pair of this tile was evaluated: zero statistics
-        if (skip_zero && nz[blockIdx.x] == 0) return;
-        if (w == 0 && p < K) {
-            const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
-            double2 *o = reinterpret_cast<double2 *>(dS + dst * 28);   // 224-byte rows
+        if (!(skip_zero && nz[blockIdx.x] == 0)) {
+            if (w == 0 && p < K) {
+                const size_t dst = kperm ? (size_t)kperm[p] : (size_t)p;
+                double2 *o = reinterpret_cast<double2 *>(dS + dst * 28);   // 224-byte rows
 #pragma unroll
-            for (int f = 0; f < 14; f++) o[f] = make_double2(0.0, 0.0);
+                for (int f = 0; f < 14; f++) o[f] = make_double2(0.0, 0.0);
+            }
+            if (nz && threadIdx.x == 0) nz[blockIdx.x] = 0;
         }
-        if (nz && threadIdx.x == 0) nz[blockIdx.x] = 0;
+        if (w == 0) list_entry(true);
         return;
     }
     if (nz && threadIdx.x == 0) nz[blockIdx.x] = 1;
@@ -1511,10 +1541,18 @@ __global__ void __launch_bounds__(128) k_reduce_items(const float *__restrict__ 
 #pragma unroll
     for (int f = 0; f < 28; f++) sh[w][lane][f] = t[f];
     __syncthreads();
-    if (p >= K) return;
-    auto fsum = [&](int f) {   // the four warp sums in warp order
-        return f2d_exact((sh[0][lane][f] + sh[1][lane][f]) + (sh[2][lane][f] + sh[3][lane][f]));
+    auto fsum32 = [&](int f) {   // the four warp sums in warp order
+        return (sh[0][lane][f] + sh[1][lane][f]) + (sh[2][lane][f] + sh[3][lane][f]);
     };
+    if (w == 0) {
+        // the raw moments below are all zero exactly when these sums are
+        bool zero = true;
+#pragma unroll
+        for (int f = 0; f < 28; f++) zero = zero && (__float_as_uint(fsum32(f)) << 1) == 0u;
+        list_entry(zero);
+    }
+    if (p >= K) return;
+    auto fsum = [&](int f) { return f2d_exact(fsum32(f)); };
     double d0[7], mk[6];
 #pragma unroll
     for (int f = 0; f < 7; f++) d0[f] = fsum(f);
@@ -1570,7 +1608,8 @@ size_t tc_plan_ints(int64_t N, int K)
 int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
-                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats_d)
+                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats_d,
+                    const MstepList *ml)
 {
     const float skip_nats = (float)skip_nats_d;
     unsigned long long *pairs = pf->on ? pf->d_pairs : nullptr;
@@ -1590,7 +1629,7 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
     pf->begin(VBGS_PROF_PLAN, st);
     if (tmax) launch_pdl(k_p2_plan, ntiles, 256, 0, st, tmax, minlse, N, ntiles, counts, list, skip_nats);
     launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ntiles, nchunks, cmin, tcap, item_start, item_tile,
-                                   item_lo, item_hi, nitems);
+               item_lo, item_hi, nitems, ml ? ml->count : nullptr);
     pf->end(st);
     const size_t smem = sizeof(Smem2) + 128;
     if (tc_set_attributes()) return -1;
@@ -1606,7 +1645,8 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
                                                          pairs, knobs);
     pf->end(st);
     pf->begin(VBGS_PROF_REDUCE, st);
-    launch_pdl(k_reduce_items, ntiles * 4, 128, 0, st, fpart, item_start, K, rec, kperm, dS, nz, skip_zero && nz);
+    launch_pdl(k_reduce_items, ntiles * 4, 128, 0, st, fpart, item_start, K, rec, kperm, dS, nz, skip_zero && nz,
+               ml ? *ml : MstepList{});
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? (tmax ? 4 : 3) : -1;
 }
@@ -1825,7 +1865,7 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
         *seed_part_out = reinterpret_cast<const double *>(spart);
     }
     launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ptiles, ntiles, tmin, target, item_start, item_tile,
-                                   item_lo, item_hi, nitems);
+               item_lo, item_hi, nitems, (int *)nullptr);
     pf->end(st);
     pf->begin(VBGS_PROF_PASS1, st);
     const int *lst = tmax ? list : nullptr;

@@ -225,10 +225,26 @@ size_t mstep_cache_doubles(int K);
 // recomputed component, with its index); after the commit they are the next
 // frame's effective prior bit for bit (the last iteration of a frame), the
 // other components keep q = p.
+// listed: the statistics reduction already built the list of components to
+// recompute (MstepList), so the M-step skips its own scan.
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
                  const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
                  int *tile_dirty, double *cache_next, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork,
-                 cudaEvent_t ev_join, Prof *pf);
+                 cudaEvent_t ev_join, Prof *pf, bool listed = false);
+// The M-step's list of components to recompute, as a statistics reduction
+// builds it while it writes Delta S: a component is listed unless its frame
+// statistics are all zero and its record holds the effective prior
+// (pc33[k * pc_stride] != 0); an unlisted component gets the "q = p" hand-off
+// (ks33[k * ks_stride] and the next double set to zero).  count[0] (entries)
+// and count[1] (the list kernel's group counter) start at zero.
+struct MstepList {
+    const double *pc33;
+    int pc_stride;
+    double *ks33;
+    int ks_stride;
+    int *list, *count;
+};
+MstepList mstep_list_view(double *cache, int K);
 int launch_move_records(const int *kperm, const int *kinv_old, int K, const double *rec, const float *rec32,
                         double *rec_dst, float *rec32_dst, cudaStream_t st, Prof *pf);
 size_t mstep_prior_cache_doubles(int K);
@@ -279,10 +295,12 @@ size_t tc_plan_ints(int64_t N, int K);
 size_t tc_pass2_part_doubles(int K);
 size_t tc_p1plan_ints(int64_t N, int K);
 size_t tc_p1ub_floats(int64_t N, int K);
+// ml (nullable): also build the M-step's list (MstepList) while reducing.
 int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
-                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats);
+                    int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats,
+                    const MstepList *ml = nullptr);
 int tc_pass1_auto_splits(int64_t N, int K, int num_sms);
 int tc_set_attributes();
 // Pass 1 on the tensor cores over balanced work items (point tile, list of
@@ -458,6 +476,7 @@ struct vbgs_ctx {
     cudaStream_t side = nullptr;               // KL terms of the M-step, beside the next E-step
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool side_pending = false;                 // KL work launched on side and not yet joined
+    bool mstep_listed = false;                 // the last E-step built the M-step's list (MstepList)
     // The last M-step of the previous frame wrote d_pcache_next and the
     // commit made it the effective prior of the next frame bit for bit; the
     // records hold the same posterior (at the positions of d_kinv).

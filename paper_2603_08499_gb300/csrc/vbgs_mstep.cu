@@ -921,10 +921,18 @@ size_t mstep_cache_doubles(int K)
     return (size_t)K * kPC + (size_t)((K + 127) / 128) * 4 + (size_t)K * kKS + (size_t)(K + 4) / 2;
 }
 
+MstepList mstep_list_view(double *cache, int K)
+{
+    const int nb = (K + 127) / 128;
+    double *kls = cache + (size_t)K * kPC + (size_t)nb * 4;
+    int *list = reinterpret_cast<int *>(kls + (size_t)K * kKS);
+    return MstepList{cache + 33, kPC, kls + 33, kKS, list, list + K};
+}
+
 int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, const double *dS,
                  const int *kperm, double *rec, float *rec32, double *cache, int *flags, double *scal,
                  int *tile_dirty, double *cache_next, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork,
-                 cudaEvent_t ev_join, Prof *pf)
+                 cudaEvent_t ev_join, Prof *pf, bool listed)
 {
     if (!dS) cache_next = nullptr;
     const int K = P.K;
@@ -941,10 +949,12 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
         pf->end(st);
     } else {
         int *list = reinterpret_cast<int *>(kls + (size_t)K * kKS), *count = list + K;
-        if (cudaMemsetAsync(count, 0, 2 * sizeof(int), st) != cudaSuccess) return -1;
-        pf->begin(VBGS_PROF_MSTEP, st);
-        launch_pdl(k_mstep_scan, (K + 127) / 128, 128, 0, st, K, dS, kperm, cache, kls, list, count);
-        pf->end(st);
+        if (!listed) {
+            if (cudaMemsetAsync(count, 0, 2 * sizeof(int), st) != cudaSuccess) return -1;
+            pf->begin(VBGS_PROF_MSTEP, st);
+            launch_pdl(k_mstep_scan, (K + 127) / 128, 128, 0, st, K, dS, kperm, cache, kls, list, count);
+            pf->end(st);
+        }
         pf->begin(VBGS_PROF_MSTEP, st);
         static bool attr_set = false;
         if (!attr_set) {
@@ -956,7 +966,7 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
         launch_pdl(k_mstep_list, std::max(1, P.num_sms), 128, kListSmem, st, P, m0, Spast, dS, kperm, list, count,
                    rec, rec32, cache, kls, flags, tile_dirty, cache_next);
         pf->end(st);
-        launches = 4;
+        launches = listed ? 3 : 4;
     }
     // KL terms and their sums beside the next E-step
     if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return -1;
