@@ -379,7 +379,8 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
                                 ctx->d_tc_tiles, ctx->d_tc_hdr, ctx->d_rec32, ctx->d_part, ctx->part_cap, B.tmax,
                                 ctx->d_p1plan, ctx->d_p1ub, ctx->d_flags, ctx->num_sms, ctx->tune_p1,
                                 ctx->d_tile_dirty + (ctx->K + 127) / 128, ctx->plan_epoch, &item_start, &seed_part,
-                                ctx->stream, &ctx->prof, ctx->tc_knobs, ctx->skip_nats);
+                                ctx->stream, &ctx->prof, ctx->tc_knobs, ctx->skip_nats,
+                                reinterpret_cast<unsigned int *>(ctx->d_scal + SC_P1_DONE));
         ctx->plan_epoch = ctx->coef_epoch;
         ctx->prof.p1_last.alloc_gen = ctx->alloc_gen;
         if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 1 launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -400,7 +401,8 @@ int run_estep_on(vbgs_ctx *ctx, const double *X, int64_t N, double *lse, bool wa
                                 ctx->d_rec, B.tmax, B.tmax ? ctx->d_minlse : nullptr, ctx->d_plan, ctx->d_part, ctx->part_cap, ctx->d_kperm,
                                 ctx->d_dS, ctx->d_flags, ctx->num_sms, ctx->tune_p2,
                                 ctx->d_tile_dirty + 2 * ((ctx->K + 127) / 128), same_points, ctx->stream, &ctx->prof,
-                                ctx->tc_knobs, ctx->skip_nats, &ml);
+                                ctx->tc_knobs, ctx->skip_nats, reinterpret_cast<unsigned int *>(ctx->d_scal + SC_P2_DONE),
+                                &ml);
             if (l < 0) return fail(ctx, VBGS_ECUDA, "tensor-core pass 2 launch failed (%d): %s", l,
                                    cudaGetErrorString(cudaGetLastError()));
             ctx->launches += l;

@@ -853,6 +853,102 @@ __global__ void __launch_bounds__(128) k_p1_ub(const float *__restrict__ boxes, 
     }
 }
 
+// Work items: every tile's list cut into items of at most C consecutive
+// entries, with C >= cmin chosen so that the items fit the partial buffer
+// (tcap items): sum_j ceil(n_j / C) <= total / C + ntiles <= tcap.
+// item_start[j] is the first item of tile j (exclusive scan); items are in
+// tile order.  One block of blockDim.x threads (a multiple of 32, at most
+// 1024) with scan[65] in shared memory; counts == nullptr: nchunks entries
+// per tile.
+__device__ void build_items(const int *__restrict__ counts, int ntiles, int64_t nchunks, int cmin, int tcap,
+                            int *__restrict__ item_start, int *__restrict__ item_tile, int *__restrict__ item_lo,
+                            int *__restrict__ item_hi, int *__restrict__ nitems, int *scan)
+{
+    __shared__ long long red[32];
+    __shared__ int C_sh;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nt = blockDim.x, nw = nt >> 5;
+    auto cnt = [&](int j) -> int { return counts ? __ldcg(counts + j) : (int)nchunks; };
+    // each thread takes a contiguous run of tiles
+    const int per = (ntiles + nt - 1) / nt, j0 = min(ntiles, t * per), j1 = min(ntiles, j0 + per);
+    long long tot = 0;
+    for (int j = j0; j < j1; j++) tot += cnt(j);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) red[w] = tot;
+    __syncthreads();
+    if (t == 0) {
+        long long sum = 0;
+        for (int i = 0; i < nw; i++) sum += red[i];
+        const long long room = tcap > ntiles ? tcap - ntiles : 1;
+        C_sh = (int)max((long long)cmin, (sum + room - 1) / room);
+    }
+    __syncthreads();
+    const int C = C_sh;
+    int mine = 0;   // items of this thread's tiles
+    for (int j = j0; j < j1; j++) mine += (cnt(j) + C - 1) / C;
+    // exclusive block scan: within the warp by shuffles, then the warp totals
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) scan[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int v = lane < nw ? scan[lane] : 0, iv = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, iv, o);
+            if (lane >= o) iv += u;
+        }
+        if (lane < nw) scan[32 + lane] = iv - v;   // exclusive prefix of warp lane
+        if (lane == nw - 1) scan[64] = iv;         // total
+    }
+    __syncthreads();
+    int start = scan[32 + w] + incl - mine;
+    for (int j = j0; j < j1; j++) {
+        item_start[j] = start;
+        const int c = cnt(j), nj = (c + C - 1) / C;
+        for (int i = 0; i < nj; i++) {
+            item_tile[start + i] = j;
+            item_lo[start + i] = i * C;
+            item_hi[start + i] = min(c, (i + 1) * C);
+        }
+        start += nj;
+    }
+    if (t == 0) {
+        item_start[ntiles] = scan[64];
+        *nitems = scan[64];
+    }
+}
+
+// The work items of a pass, built by the last block of a plan kernel once
+// every block has written its count: done counts the finished blocks (zero
+// between plans: the last block resets it).
+struct ItemsArgs {
+    int cmin, tcap;
+    int *item_start, *item_tile, *item_lo, *item_hi, *nitems;
+    unsigned int *done;
+    int *zero2;   // nullable: two ints set to zero for a later kernel of the stream
+};
+__device__ void items_by_last_block(const int *counts, int ntiles, int64_t nchunks, const ItemsArgs &A, int *scan)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(A.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    build_items(counts, ntiles, nchunks, A.cmin, A.tcap, A.item_start, A.item_tile, A.item_lo, A.item_hi, A.nitems,
+                scan);
+    if (threadIdx.x == 0) {
+        *A.done = 0u;
+        if (A.zero2) { A.zero2[0] = 0; A.zero2[1] = 0; }
+    }
+}
+
 // Pass-1 plan of point tile P around a first pass-1 launch.  k_p1_ub: the
 // largest bound of every component tile over P's box.  k_p1_seed: the seed
 // tile (the largest ub, ties to the lower index), evaluated alone by the
@@ -907,15 +1003,18 @@ __global__ void __launch_bounds__(kPlanThreads) k_p1_seed(int64_t N, int ntiles,
 }
 
 // spart: the seed launch's partials (point tile P: rows P * 128 ..).
+// The last block to finish also builds the main launch's work items
+// (ItemsArgs; the count per point tile is its list's length).
 __global__ void __launch_bounds__(kPlanThreads) k_p1_plan(int64_t N, int ntiles, const float2 *__restrict__ spart,
                                                           const float *__restrict__ ub, int *__restrict__ list,
-                                                          int *__restrict__ counts, float skip_log2)
+                                                          int *__restrict__ counts, float skip_log2, ItemsArgs items)
 {
     pdl_wait();
     const int P = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
     __shared__ float red[kPlanWarps];
     __shared__ int wsum[kPlanWarps];
     __shared__ int base_sh;
+    __shared__ int scan[65];
     const float *u = ub + (size_t)P * ntiles;
     int *row = list + (size_t)P * ntiles;
     const int js = row[0];
@@ -956,6 +1055,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_p1_plan(int64_t N, int ntiles,
         __syncthreads();
     }
     if (t == 0) counts[P] = base_sh;
+    items_by_last_block(counts, (int)gridDim.x, 0, items, scan);
 }
 
 // ---------------------------------------------------------------------------
@@ -1019,13 +1119,15 @@ __device__ __forceinline__ bool chunk_skipped(const float *tmax, const float *mi
 // Work list of pass 2: for every component tile, the 64-point chunks the
 // pass-1 bound does not rule out, in increasing order (deterministic).
 // One block per tile; counts[j] and list[j * nchunks + i].
+// The last block to finish also builds the pass's work items (ItemsArgs).
 __global__ void __launch_bounds__(256) k_p2_plan(const float *__restrict__ tmax, const float *__restrict__ minlse,
                                                  int64_t N, int ntiles, int *__restrict__ counts,
-                                                 int *__restrict__ list, float skip_nats)
+                                                 int *__restrict__ list, float skip_nats, ItemsArgs items)
 {
     pdl_wait();
     __shared__ int wsum[8];
     __shared__ int base_sh;
+    __shared__ int scan[65];
     const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int64_t nchunks = (N + kChunk2 - 1) / kChunk2;
     if (t == 0) base_sh = 0;
@@ -1049,14 +1151,11 @@ __global__ void __launch_bounds__(256) k_p2_plan(const float *__restrict__ tmax,
         __syncthreads();
     }
     if (t == 0) counts[j] = base_sh;
+    items_by_last_block(counts, ntiles, nchunks, items, scan);
 }
 
-// Work items of pass 2: every tile's chunk list cut into items of at most C
-// consecutive entries, with C >= cmin chosen so that the items fit the
-// partial buffer (tcap items of 128 x 28 moments): sum_j ceil(n_j / C) <=
-// total / C + ntiles <= tcap.  item_start[j] is the first item of tile j
-// (exclusive scan); items are in tile order.  One block.
 constexpr int kItemCap = 2048;
+// One block of 1024 threads (the passes without skipping).
 // zero2 (nullable): two ints set to zero for a later kernel of the stream.
 __global__ void __launch_bounds__(1024) k_p2_items(const int *__restrict__ counts, int ntiles, int64_t nchunks,
                                                    int cmin, int tcap, int *__restrict__ item_start,
@@ -1065,56 +1164,9 @@ __global__ void __launch_bounds__(1024) k_p2_items(const int *__restrict__ count
                                                    int *__restrict__ zero2)
 {
     pdl_wait();
+    __shared__ int scan[65];
     if (zero2 && threadIdx.x < 2) zero2[threadIdx.x] = 0;
-    __shared__ long long red[32];
-    __shared__ int scan[1024];
-    __shared__ int carry_sh, C_sh;
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    auto cnt = [&](int j) -> int { return counts ? counts[j] : (int)nchunks; };
-    long long tot = 0;
-    for (int j = t; j < ntiles; j += 1024) tot += cnt(j);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    if (lane == 0) red[w] = tot;
-    __syncthreads();
-    if (t == 0) {
-        long long s = 0;
-        for (int i = 0; i < 32; i++) s += red[i];
-        const long long room = tcap > ntiles ? tcap - ntiles : 1;
-        C_sh = (int)max((long long)cmin, (s + room - 1) / room);
-        carry_sh = 0;
-    }
-    __syncthreads();
-    const int C = C_sh;
-    for (int j0 = 0; j0 < ntiles; j0 += 1024) {
-        const int j = j0 + t;
-        const int nj = j < ntiles ? (cnt(j) + C - 1) / C : 0;
-        scan[t] = nj;
-        __syncthreads();
-        for (int o = 1; o < 1024; o <<= 1) {   // inclusive Hillis-Steele scan
-            const int v = t >= o ? scan[t - o] : 0;
-            __syncthreads();
-            scan[t] += v;
-            __syncthreads();
-        }
-        const int start = carry_sh + scan[t] - nj;
-        if (j < ntiles) {
-            item_start[j] = start;
-            const int c = cnt(j);
-            for (int i = 0; i < nj; i++) {
-                item_tile[start + i] = j;
-                item_lo[start + i] = i * C;
-                item_hi[start + i] = min(c, (i + 1) * C);
-            }
-        }
-        __syncthreads();
-        if (t == 1023) carry_sh += scan[1023];
-        __syncthreads();
-    }
-    if (t == 0) {
-        item_start[ntiles] = carry_sh;
-        *nitems = carry_sh;
-    }
+    build_items(counts, ntiles, nchunks, cmin, tcap, item_start, item_tile, item_lo, item_hi, nitems, scan);
 }
 
 template <bool BF16>
@@ -1609,7 +1661,7 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
                     int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats_d,
-                    const MstepList *ml)
+                    unsigned int *plan_done, const MstepList *ml)
 {
     const float skip_nats = (float)skip_nats_d;
     unsigned long long *pairs = pf->on ? pf->d_pairs : nullptr;
@@ -1627,9 +1679,13 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
     int *item_tile = item_start + ntiles + 1, *item_lo = item_tile + icap, *item_hi = item_lo + icap;
     int *nitems = item_hi + icap;
     pf->begin(VBGS_PROF_PLAN, st);
-    if (tmax) launch_pdl(k_p2_plan, ntiles, 256, 0, st, tmax, minlse, N, ntiles, counts, list, skip_nats);
-    launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ntiles, nchunks, cmin, tcap, item_start, item_tile,
-               item_lo, item_hi, nitems, ml ? ml->count : nullptr);
+    if (tmax)   // the plan's last block builds the work items
+        launch_pdl(k_p2_plan, ntiles, 256, 0, st, tmax, minlse, N, ntiles, counts, list, skip_nats,
+                   ItemsArgs{cmin, tcap, item_start, item_tile, item_lo, item_hi, nitems, plan_done,
+                             ml ? ml->count : nullptr});
+    else
+        launch_pdl(k_p2_items, 1, 1024, 0, st, (const int *)nullptr, ntiles, nchunks, cmin, tcap, item_start,
+                   item_tile, item_lo, item_hi, nitems, ml ? ml->count : nullptr);
     pf->end(st);
     const size_t smem = sizeof(Smem2) + 128;
     if (tc_set_attributes()) return -1;
@@ -1648,7 +1704,7 @@ int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool
     launch_pdl(k_reduce_items, ntiles * 4, 128, 0, st, fpart, item_start, K, rec, kperm, dS, nz, skip_zero && nz,
                ml ? *ml : MstepList{});
     pf->end(st);
-    return cudaGetLastError() == cudaSuccess ? (tmax ? 4 : 3) : -1;
+    return cudaGetLastError() == cudaSuccess ? 3 : -1;
 }
 
 // K-splits of pass 1: many small CTAs (two resident per SM) that the hardware
@@ -1712,15 +1768,20 @@ __global__ void k_split_points(const double *__restrict__ X, int64_t N, float *_
 // seed launch's partial (FP32, log2 units: the partials carry the
 // tensor-core pass's FP32 sums), natural-unit lse in FP64, the smallest lse
 // per 32 points and per-block FP64 sums of lse.
-__global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part, const int *__restrict__ item_start,
-                                                 const float2 *__restrict__ spart,
-                                                 int64_t N, double *__restrict__ lse, float *__restrict__ lse2f,
-                                                 double *__restrict__ lse_part, float *__restrict__ minlse,
-                                                 unsigned int *__restrict__ done, double *__restrict__ sum_out)
+constexpr int kMergeThreads = 256;
+__global__ void __launch_bounds__(kMergeThreads) k_merge_tc(const float2 *__restrict__ part,
+                                                            const int *__restrict__ item_start,
+                                                            const float2 *__restrict__ spart, int64_t N,
+                                                            double *__restrict__ lse, float *__restrict__ lse2f,
+                                                            double *__restrict__ lse_part, float *__restrict__ minlse,
+                                                            unsigned int *__restrict__ done,
+                                                            double *__restrict__ sum_out)
 {
     pdl_wait();
-    __shared__ double sh[2];
+    constexpr int kW = kMergeThreads / 32;
+    __shared__ double sh[kW];
     __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
     if (n < N) {
@@ -1746,16 +1807,18 @@ __global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part
         v += __shfl_down_sync(0xffffffffu, v, o);
         vm = fminf(vm, __shfl_down_sync(0xffffffffu, vm, o));
     }
-    if ((threadIdx.x & 31) == 0) {
-        sh[threadIdx.x >> 5] = v;
-        const int64_t w = (int64_t)blockIdx.x * 2 + (threadIdx.x >> 5);
+    if (lane == 0) {
+        sh[wid] = v;
+        const int64_t w = (int64_t)blockIdx.x * kW + wid;
         if (minlse && w * 32 < N) minlse[w] = vm;
     }
     __syncthreads();
     // the block sums, added in block order by the last block to finish (the
     // same sum on every run); it leaves the counter at zero for the next merge
     if (threadIdx.x == 0) {
-        lse_part[blockIdx.x] = sh[0] + sh[1];
+        double b = 0.0;
+        for (int i = 0; i < kW; i++) b += sh[i];
+        lse_part[blockIdx.x] = b;
         __threadfence();
         last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
@@ -1766,10 +1829,13 @@ __global__ void __launch_bounds__(64) k_merge_tc(const float2 *__restrict__ part
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(lse_part + i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (lane == 0) sh[wid] = t;
     __syncthreads();
     if (threadIdx.x == 0) {
-        *sum_out = sh[0] + sh[1];
+        double tot = 0.0;
+        for (int i = 0; i < kW; i++) tot += sh[i];
+        *sum_out = tot;
         *done = 0u;
     }
 }
@@ -1795,7 +1861,8 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
                     const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
                     size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
                     int tiles_per_item, const int *tile_epoch, int since, const int **item_start_out,
-                    const double **seed_part_out, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats)
+                    const double **seed_part_out, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats,
+                    unsigned int *plan_done)
 {
     float2 *part = reinterpret_cast<float2 *>(part_buf);
     int launches = 0;
@@ -1860,12 +1927,15 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
         pass1(ptiles, list, sitem_tile, sitem_lo, sitem_hi, snitems, spart);
         pf->end(st);
         pf->begin(VBGS_PROF_PLAN, st);
+        // its last block builds the main launch's work items
         launch_pdl(k_p1_plan, ptiles, kPlanThreads, 0, st, N, ntiles, (const float2 *)spart, (const float *)p1ub,
-                   list, counts, (float)(skip_nats * 1.4426950408889634));
+                   list, counts, (float)(skip_nats * 1.4426950408889634),
+                   ItemsArgs{tmin, target, item_start, item_tile, item_lo, item_hi, nitems, plan_done, nullptr});
         *seed_part_out = reinterpret_cast<const double *>(spart);
+    } else {
+        launch_pdl(k_p2_items, 1, 1024, 0, st, (const int *)nullptr, ptiles, ntiles, tmin, target, item_start,
+                   item_tile, item_lo, item_hi, nitems, (int *)nullptr);
     }
-    launch_pdl(k_p2_items, 1, 1024, 0, st, tmax ? counts : nullptr, ptiles, ntiles, tmin, target, item_start, item_tile,
-               item_lo, item_hi, nitems, (int *)nullptr);
     pf->end(st);
     pf->begin(VBGS_PROF_PASS1, st);
     const int *lst = tmax ? list : nullptr;
@@ -1894,16 +1964,16 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
     pass1(target, lst, item_tile, item_lo, item_hi, nitems, part);
     pf->end(st);
     *item_start_out = item_start;
-    return cudaGetLastError() == cudaSuccess ? launches + (tmax ? 6 : 2) : -1;
+    return cudaGetLastError() == cudaSuccess ? launches + (tmax ? 5 : 2) : -1;
 }
 
 int launch_lse_merge_tc(const double *part_buf, const double *seed_part, int64_t N, const int *item_start, double *lse,
                         float *lse2f, double *lse_part, float *minlse, double *sum_out, unsigned int *done,
                         cudaStream_t st, Prof *pf)
 {
-    const int mb = (int)((N + 63) / 64);
+    const int mb = (int)((N + kMergeThreads - 1) / kMergeThreads);
     pf->begin(VBGS_PROF_MERGE, st);
-    launch_pdl(k_merge_tc, mb, 64, 0, st, reinterpret_cast<const float2 *>(part_buf), item_start,
+    launch_pdl(k_merge_tc, mb, kMergeThreads, 0, st, reinterpret_cast<const float2 *>(part_buf), item_start,
                reinterpret_cast<const float2 *>(seed_part), N, lse, lse2f, lse_part, minlse, done, sum_out);
     pf->end(st);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;

@@ -65,6 +65,8 @@ enum ScalarSlot {
     SC_KL_TOTAL = 1,   // sum_k KL_NW + KL_Dir
     SC_SUM_LSE = 2,    // sum_n lse_n (without -psi term)
     SC_PSI_ESTEP = 3,  // psi(sum alpha) of the posterior the last E-step ran under
+    SC_P1_DONE = 4,    // (as an unsigned int) blocks of the pass-1 plan finished; 0 between plans
+    SC_P2_DONE = 5,    // (as an unsigned int) blocks of the pass-2 plan finished; 0 between plans
     SC_MERGE_DONE = 7, // (as an unsigned int) blocks of the lse merge finished; 0 between merges
     SC_COUNT = 8
 };
@@ -295,12 +297,14 @@ size_t tc_plan_ints(int64_t N, int K);
 size_t tc_pass2_part_doubles(int K);
 size_t tc_p1plan_ints(int64_t N, int K);
 size_t tc_p1ub_floats(int64_t N, int K);
-// ml (nullable): also build the M-step's list (MstepList) while reducing.
+// plan_done: the plan's finished-block counter (zero between plans; its last
+// block builds the work items).  ml (nullable): also build the M-step's list
+// (MstepList) while reducing.
 int launch_pass2_tc(const float *Xhl, const float *lse2f, int64_t N, int K, bool bf16, const unsigned char *tiles,
                     const float *hdr, const double *rec, const float *tmax, const float *minlse, int *plan, double *part,
                     size_t part_cap_doubles, const int *kperm, double *dS, int *flags, int num_sms, int splits_override,
                     int *nz, bool skip_zero, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats,
-                    const MstepList *ml = nullptr);
+                    unsigned int *plan_done, const MstepList *ml = nullptr);
 int tc_pass1_auto_splits(int64_t N, int K, int num_sms);
 int tc_set_attributes();
 // Pass 1 on the tensor cores over balanced work items (point tile, list of
@@ -318,7 +322,8 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
                     const unsigned char *tiles, const float *hdr, const float *rec32, double *part_buf,
                     size_t part_cap_doubles, float *tmax, int *p1plan, float *p1ub, int *flags, int num_sms,
                     int tiles_per_item, const int *tile_epoch, int since, const int **item_start_out,
-                    const double **seed_part_out, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats);
+                    const double **seed_part_out, cudaStream_t st, Prof *pf, uint32_t knobs, double skip_nats,
+                    unsigned int *plan_done);
 // lse from pass 1's FP32 item partials and the seed launch's (nullable),
 // minlse per 32 points, sum of lse.
 int launch_lse_merge_tc(const double *part_buf, const double *seed_part, int64_t N, const int *item_start, double *lse,
