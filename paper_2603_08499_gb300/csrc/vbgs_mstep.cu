@@ -440,6 +440,22 @@ __device__ __forceinline__ double sel64(bool a, double x, double y)
     return __longlong_as_double((long long)r);
 }
 
+// The psi terms of row r of a listed component: psi(alpha_q) on row 0, the
+// two halves of psi_6(nu_q / 2) on rows 1, 2 (other rows: unused).
+__device__ __forceinline__ double mstep_psi_term(const MstepParams &P, int r, double aq, double nq)
+{
+    const double xd = r == 1 ? 0.5 * nq - 0.5 * 0 : r == 2 ? 0.5 * nq - 0.5 * 1 : aq;
+    const double yd = dg_digamma(xd);
+    return r == 0    ? yd
+           : !P.split ? 3.0 * yd - (3.0 * xd - 5.0) / ((xd - 1.0) * (xd - 2.0))
+           : r == 1   ? 4.0 * yd - 2.0 / (xd - 1.0)   // mv_digamma_split's two parts
+                      : 2.0 * yd;
+}
+
+// Two warps on different SM sub-partitions sharing one group of components
+// (named barrier `id`, 64 threads).
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
 // Listed components, five to a warp: lanes 6g..6g+5 hold rows r = 0..5 of
 // component g's matrices (lanes 30, 31 idle).  w0r[j] = W0^-1 at
 // (min(r, j), max(r, j)), as nw_from_stats reads it.  The inverse L^-1 is kept
@@ -450,7 +466,8 @@ __device__ __forceinline__ void mstep_group(const MstepParams &P, const double w
                                             const double *__restrict__ dS, int pos, int k, double *__restrict__ rec,
                                             float *__restrict__ rec32, double *__restrict__ pc,
                                             double *__restrict__ kls, int *__restrict__ flags,
-                                            int *__restrict__ tile_dirty, double *__restrict__ cq)
+                                            int *__restrict__ tile_dirty, double *__restrict__ cq,
+                                            const double *term_src, int bar_id)
 {
     constexpr unsigned F = 0xffffffffu;
     auto row = [&](double v, int rr) { return __shfl_sync(F, v, (gb + rr) & 31); };
@@ -511,13 +528,15 @@ __device__ __forceinline__ void mstep_group(const MstepParams &P, const double w
         }
         if (r >= d) Lid[d] = -t * Lid[0];
     }
-    // psi(alpha_q) on row 0, the two halves of psi_6(nu_q / 2) on rows 1, 2
-    const double xd = r == 1 ? 0.5 * nq - 0.5 * 0 : r == 2 ? 0.5 * nq - 0.5 * 1 : aq;
-    const double yd = dg_digamma(xd);
-    const double term = r == 0    ? yd
-                        : !P.split ? 3.0 * yd - (3.0 * xd - 5.0) / ((xd - 1.0) * (xd - 2.0))
-                        : r == 1   ? 4.0 * yd - 2.0 / (xd - 1.0)   // mv_digamma_split's two parts
-                                   : 2.0 * yd;
+    // the psi terms: from the partner warp (term_src, after the pair's
+    // barrier) or computed here
+    double term;
+    if (term_src) {
+        pair_sync(bar_id);
+        term = term_src[threadIdx.x & 31];
+    } else {
+        term = mstep_psi_term(P, r, aq, nq);
+    }
     const double psi_a = row(term, 0);
     double psi_nu = 0.0;
     psi_nu += row(term, 1);
@@ -605,17 +624,51 @@ __global__ void __launch_bounds__(128) k_mstep_list(MstepParams P, const double 
             w0r[j] = w;
         }
         int *next = const_cast<int *>(count) + 1;   // groups handed out (zeroed with the count)
-        for (;;) {
-            int e0 = 0;
-            if (lane == 0) e0 = atomicAdd(next, 5);
-            e0 = __shfl_sync(0xffffffffu, e0, 0);
-            if (e0 >= n) break;   // warp-uniform
-            const int e = e0 + g;
-            const bool gv = g < 5 && e < n;
-            const int pos = list[gv ? e : e0];
-            const int k = kperm ? kperm[pos] : pos;
-            mstep_group(P, w0r, rr, 6 * g, gv, m0, Spast, dS, pos, k, rec, rec32, pc, kls, flags, tile_dirty,
-                        pcq ? pcq + (size_t)e * kPC : nullptr);
+        // Few groups (at most one per warp pair): each pair of warps (on two
+        // SM sub-partitions) shares a group, the odd warp computing its psi
+        // terms beside the even warp's Cholesky chain.  Otherwise each warp
+        // computes whole groups.
+        const int pairs = (int)gridDim.x * ((int)blockDim.x / 64);
+        if (n <= 5 * pairs) {
+            __shared__ int e0_sh[2];
+            __shared__ double term_sh[2][32];
+            const int w = threadIdx.x >> 5, pr = w >> 1, role = w & 1;
+            for (;;) {
+                if (role == 0) {
+                    int e0 = 0;
+                    if (lane == 0) e0 = atomicAdd(next, 5);
+                    e0 = __shfl_sync(0xffffffffu, e0, 0);
+                    if (lane == 0) e0_sh[pr] = e0;
+                }
+                pair_sync(1 + pr);
+                const int e0 = e0_sh[pr];
+                if (e0 >= n) break;   // both warps
+                const int e = e0 + g;
+                const bool gv = g < 5 && e < n;
+                const int pos = list[gv ? e : e0];
+                const int k = kperm ? kperm[pos] : pos;
+                if (role == 1) {
+                    const double st0 = Spast[(size_t)k * 28] + dS[(size_t)k * 28];
+                    term_sh[pr][lane] = mstep_psi_term(P, rr, P.alpha0 + st0, P.nu0 + st0);
+                    pair_sync(1 + pr);
+                } else {
+                    mstep_group(P, w0r, rr, 6 * g, gv, m0, Spast, dS, pos, k, rec, rec32, pc, kls, flags, tile_dirty,
+                                pcq ? pcq + (size_t)e * kPC : nullptr, term_sh[pr], 1 + pr);
+                }
+            }
+        } else {
+            for (;;) {
+                int e0 = 0;
+                if (lane == 0) e0 = atomicAdd(next, 5);
+                e0 = __shfl_sync(0xffffffffu, e0, 0);
+                if (e0 >= n) break;   // warp-uniform
+                const int e = e0 + g;
+                const bool gv = g < 5 && e < n;
+                const int pos = list[gv ? e : e0];
+                const int k = kperm ? kperm[pos] : pos;
+                mstep_group(P, w0r, rr, 6 * g, gv, m0, Spast, dS, pos, k, rec, rec32, pc, kls, flags, tile_dirty,
+                            pcq ? pcq + (size_t)e * kPC : nullptr, nullptr, 0);
+            }
         }
     } else {
         for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
