@@ -34,6 +34,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <cmath>
 
 namespace vbgs {
 
@@ -76,8 +77,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity
     if (mbar_try(b, parity)) return true;
     const long long t0 = clock64();
     const long long limit = drain ? kSpinCycles : g_wait_limit;
-    for (;;) {
+    // the timeout flag (a global load) and the clock are looked at on every
+    // eighth attempt only, so a wait that ends is noticed at the next try_wait
+    for (unsigned it = 1;; it++) {
         if (mbar_try(b, parity)) return true;
+        if ((it & 7u) != 0u) continue;
         if (!drain && *(volatile int *)&flags[FL_TIMEOUT]) return false;
         if (clock64() - t0 > limit) {
             atomicExch(&flags[FL_TIMEOUT], 1);
@@ -448,6 +452,13 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
 // tiles).  part[item * 128 + row] = (max in log2 units, sum of 2^(l - max)).
 // tmax[(point tile * 4 + warp) * ntiles + tile]: largest logit (natural units)
 // of each 32-point row block and 128-component tile.
+// seed (nullable): the seed launch's partials; each row's running maximum
+// starts at its seed maximum, and a 64-column batch whose largest logit lies
+// more than `drop` (log2 units) below the running maximum in every row of the
+// warp is not exponentiated.  With drop = log2 K + 25 the terms left out are
+// at most K 2^-drop = 2^-25 of a row's sum over all components (the sum is at
+// least its largest term, 1 in units of the final maximum): below FP32
+// rounding of the sum.  Its tile maxima are still taken.
 // ---------------------------------------------------------------------------
 template <bool BF16>
 __global__ void __launch_bounds__(kThreadsTC, 3) k_pass1_tc(const float *__restrict__ Xhl, int64_t N, int K,
@@ -460,7 +471,8 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_pass1_tc(const float *__restr
                                                             const int *__restrict__ nitems,
                                                             float2 *__restrict__ part, float *__restrict__ tmax,
                                                             int *__restrict__ flags,
-                                                            unsigned long long *__restrict__ pairs, uint32_t knobs)
+                                                            unsigned long long *__restrict__ pairs, uint32_t knobs,
+                                                            const float2 *__restrict__ seed, float drop)
 {
     pdl_wait();
     using HT = typename H<BF16>::T;
@@ -505,7 +517,7 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_pass1_tc(const float *__restr
             xh[i] = Xhl[nn * 16 + i];
             xl[i] = Xhl[nn * 16 + 8 + i];
         }
-        float mrun = -INFINITY, srun = 0.f;
+        float mrun = seed && n < N ? seed[n].x : -INFINITY, srun = 0.f;
         bool ok = true;
         // frame header of the next tile to build (o_hi, o_lo, 1/s), prefetched one tile ahead
         float hn[18];
@@ -595,6 +607,7 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_pass1_tc(const float *__restr
                 float cm = fmax3(fmax3(mx8[0], mx8[1], mx8[2]), fmax3(mx8[3], mx8[4], mx8[5]), fmaxf(mx8[6], mx8[7]));
                 cm *= scale;
                 tmx = fmaxf(tmx, cm);
+                if (seed && __all_sync(0xffffffffu, cm < mrun - drop)) continue;   // negligible in every row
                 if (cm > mrun) {
                     srun *= ex2f(mrun - cm);
                     mrun = cm;
@@ -1895,14 +1908,18 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
     const size_t smem = sizeof(Smem) + 1024;
     if (tc_set_attributes()) return -1;
     auto pass1 = [&](int grid, const int *lst, const int *it, const int *il, const int *ih, const int *ni,
-                     float2 *out) {
+                     float2 *out, const float2 *seed, float drop) {
         if (bf16)
             launch_pdl(k_pass1_tc<true>, grid, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, it, il, ih,
-                       ni, out, tmax, flags, pairs1, knobs);
+                       ni, out, tmax, flags, pairs1, knobs, seed, drop);
         else
             launch_pdl(k_pass1_tc<false>, grid, kThreadsTC, smem, st, Xhl, N, K, tiles, hdr, ntiles, lst, it, il, ih,
-                       ni, out, tmax, flags, pairs1, knobs);
+                       ni, out, tmax, flags, pairs1, knobs, seed, drop);
     };
+    // batches of the main launch below log2 K + 25 of a row's running maximum
+    // are left out (see k_pass1_tc)
+    const float drop = (float)(std::log2((double)std::max(K, 2)) + 25.0);
+    const float2 *seed_rows = nullptr;
     *seed_part_out = nullptr;
     pf->begin(VBGS_PROF_PLAN, st);
     if (tmax) {
@@ -1924,7 +1941,8 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
         pf->end(st);
         // the seed tile of every point tile, on the tensor cores
         pf->begin(VBGS_PROF_PASS1, st);
-        pass1(ptiles, list, sitem_tile, sitem_lo, sitem_hi, snitems, spart);
+        pass1(ptiles, list, sitem_tile, sitem_lo, sitem_hi, snitems, spart, nullptr, 0.f);
+        seed_rows = spart;
         pf->end(st);
         pf->begin(VBGS_PROF_PLAN, st);
         // its last block builds the main launch's work items
@@ -1960,8 +1978,10 @@ int launch_pass1_tc(const double *X, float *Xhl, bool same_points, int64_t N, in
         L.tmax = tmax;
         L.flags = flags;
         L.knobs = knobs;
+        L.seed = seed_rows;
+        L.drop = drop;
     }
-    pass1(target, lst, item_tile, item_lo, item_hi, nitems, part);
+    pass1(target, lst, item_tile, item_lo, item_hi, nitems, part, seed_rows, drop);
     pf->end(st);
     *item_start_out = item_start;
     return cudaGetLastError() == cudaSuccess ? launches + (tmax ? 5 : 2) : -1;
@@ -1986,10 +2006,10 @@ int tc_replay_pass1(const Pass1Launch &L, int reps, unsigned long long *pairs, c
         if (L.bf16)
             return launch_pdl(k_pass1_tc<true>, L.grid, kThreadsTC, L.smem, st, L.Xhl, L.N, L.K, L.tiles, L.hdr,
                               L.ntiles, L.list, L.item_tile, L.item_lo, L.item_hi, L.nitems, L.part, L.tmax, L.flags,
-                              pc, L.knobs);
+                              pc, L.knobs, L.seed, L.drop);
         return launch_pdl(k_pass1_tc<false>, L.grid, kThreadsTC, L.smem, st, L.Xhl, L.N, L.K, L.tiles, L.hdr,
                           L.ntiles, L.list, L.item_tile, L.item_lo, L.item_hi, L.nitems, L.part, L.tmax, L.flags, pc,
-                          L.knobs);
+                          L.knobs, L.seed, L.drop);
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1;

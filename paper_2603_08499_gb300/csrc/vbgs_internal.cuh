@@ -95,6 +95,8 @@ struct Pass1Launch {
     float *tmax = nullptr;
     int *flags = nullptr;
     uint32_t knobs = 0;
+    const float2 *seed = nullptr;      // the seed launch's partials (batch skipping), or none
+    float drop = 0.f;
 };
 
 // Per-kernel event timing (enabled by vbgs_profile_enable).  Launchers call
