@@ -358,10 +358,13 @@ REPLAYS = 200
 def replay_roofline(form, rep, probe, breakdown, step_ms):
     """Roofline of pass 1 (the dominant kernel) from its replayed last launch
     of the timed frames: pairs evaluated per launch over the mean launch
-    duration against the measured MUFU ex2 peak (one exp per pair)."""
+    duration against the measured MUFU ex2 peak (the algorithmic unit: one
+    exp per pair).  The kernel takes the exponential only of the batches not
+    certified negligible: exp_fraction is the share of pairs it does
+    exponentiate and exp_unit_frac the resulting use of the exp unit."""
     if not rep:
         return None
-    ms, pairs = rep
+    ms, pairs, exp_pairs = rep
     ex2_peak = (probe or {}).get("mufu_ex2_gops") or PEAK_EX2_MEASURED_G
     tpeak, tsrc = measured_tensor_peak()
     achieved = pairs / (ms * 1e-3) / 1e9
@@ -375,6 +378,8 @@ def replay_roofline(form, rep, probe, breakdown, step_ms):
             "peak_source": "measured MUFU ex2 rate (vbgs_probe_peaks on this GB300), of measured",
             "traffic": pass1_traffic(form), "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
             "avg_launch_ms": ms, "pairs_per_launch": pairs,
+            "exp_pairs_per_launch": exp_pairs, "exp_fraction": exp_pairs / pairs if pairs else None,
+            "exp_unit_frac": exp_pairs / (ms * 1e-3) / 1e9 / ex2_peak,
             "timing": (f"the last pass-1 launch of the timed frames replayed {REPLAYS} times back to back (PDL as in "
                        "the stream), CUDA events around the batch on the launching stream, right after the timed "
                        "region"),

@@ -382,12 +382,16 @@ const char *vbgs_profile_name(int i);
  * context (the E-step's logits and online log-sum-exp) is launched again,
  * once to count the (point, component) pairs it evaluates and once to warm
  * up, then reps times back to back between two CUDA events on the
- * context's stream; *ms_per_launch receives the mean time per launch and
- * *pairs_per_launch (may be NULL) the pairs.  The relaunches rewrite the
- * same partial results, so the context's state is unchanged.  Needs a
- * tensor-core context whose buffers have not been reallocated since that
- * launch.  Synchronises.  Errors: VBGS_EINVAL, VBGS_ECUDA, VBGS_ETIMEOUT. */
-int vbgs_profile_replay(vbgs_ctx *ctx, int reps, double *ms_per_launch, int64_t *pairs_per_launch);
+ * context's stream; *ms_per_launch receives the mean time per launch,
+ * *pairs_per_launch (may be NULL) the pairs and *exp_pairs_per_launch (may be
+ * NULL) the pairs whose exponential it takes (the others lie in 64-column
+ * batches certified negligible for every row of a warp).  The relaunches
+ * rewrite the same partial results, so the context's state is unchanged.
+ * Needs a tensor-core context whose buffers have not been reallocated since
+ * that launch.  Synchronises.  Errors: VBGS_EINVAL, VBGS_ECUDA,
+ * VBGS_ETIMEOUT. */
+int vbgs_profile_replay(vbgs_ctx *ctx, int reps, double *ms_per_launch, int64_t *pairs_per_launch,
+                        int64_t *exp_pairs_per_launch);
 
 /* No paper counterpart (measurement).  Measure this GPU's arithmetic peaks
  * with short probe kernels (a few

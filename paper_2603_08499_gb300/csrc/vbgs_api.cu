@@ -1860,8 +1860,8 @@ int vbgs_profile_enable(vbgs_ctx *ctx, int on)
     if (on && ctx->prof.pool.empty()) {
         ctx->prof.pool.resize(4096);
         for (auto &e : ctx->prof.pool) CU(cudaEventCreate(&e));
-        CU(cudaMalloc(&ctx->prof.d_pairs, 2 * sizeof(unsigned long long)));
-        CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, 2 * sizeof(unsigned long long), ctx->stream));
+        CU(cudaMalloc(&ctx->prof.d_pairs, 3 * sizeof(unsigned long long)));
+        CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, 3 * sizeof(unsigned long long), ctx->stream));
     }
     ctx->prof.on = on != 0;
     ctx->prof.mask = on == 1 ? ~0u : (unsigned)on >> 1;
@@ -1877,7 +1877,7 @@ int vbgs_profile_read(vbgs_ctx *ctx, double *ms, int64_t *launches, int reset)
         if (reset) { ctx->prof.ms[i] = 0; ctx->prof.n[i] = 0; }
     }
     if (reset && ctx->prof.d_pairs) {
-        CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, 2 * sizeof(unsigned long long), ctx->stream));
+        CU(cudaMemsetAsync(ctx->prof.d_pairs, 0, 3 * sizeof(unsigned long long), ctx->stream));
         ctx->prof.pass1_pairs = 0;
     }
     return VBGS_OK;
@@ -2131,7 +2131,8 @@ int vbgs_render(vbgs_ctx *ctx, const double *camera, int width, int height, floa
     return VBGS_OK;
 }
 
-int vbgs_profile_replay(vbgs_ctx *ctx, int reps, double *ms_per_launch, int64_t *pairs_per_launch)
+int vbgs_profile_replay(vbgs_ctx *ctx, int reps, double *ms_per_launch, int64_t *pairs_per_launch,
+                        int64_t *exp_pairs_per_launch)
 {
     if (!ctx) return fail(nullptr, VBGS_EINVAL, "ctx is NULL");
     if (reps < 1 || !ms_per_launch) return fail(ctx, VBGS_EINVAL, "vbgs_profile_replay: need reps >= 1 and an output");
@@ -2140,17 +2141,18 @@ int vbgs_profile_replay(vbgs_ctx *ctx, int reps, double *ms_per_launch, int64_t 
         return fail(ctx, VBGS_EINVAL, "vbgs_profile_replay: no tensor-core pass-1 launch on the current buffers");
     int rc;
     if ((rc = join_side(ctx))) return rc;
-    unsigned long long *d_cnt = nullptr;
-    CU(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
-    CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), ctx->stream));
+    unsigned long long *d_cnt = nullptr;   // pairs evaluated, pairs exponentiated
+    CU(cudaMalloc(&d_cnt, 2 * sizeof(unsigned long long)));
+    CU(cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), ctx->stream));
     float ms = 0.f;
     const int r = tc_replay_pass1(L, reps, d_cnt, ctx->stream, &ms);
-    unsigned long long pairs = 0;
-    const cudaError_t e = cudaMemcpy(&pairs, d_cnt, sizeof pairs, cudaMemcpyDeviceToHost);
+    unsigned long long cnt[2] = {0, 0};
+    const cudaError_t e = cudaMemcpy(cnt, d_cnt, sizeof cnt, cudaMemcpyDeviceToHost);
     cudaFree(d_cnt);
     if (r || e != cudaSuccess) return fail(ctx, VBGS_ECUDA, "vbgs_profile_replay: replay failed");
     *ms_per_launch = ms;
-    if (pairs_per_launch) *pairs_per_launch = (int64_t)pairs;
+    if (pairs_per_launch) *pairs_per_launch = (int64_t)cnt[0];
+    if (exp_pairs_per_launch) *exp_pairs_per_launch = (int64_t)cnt[1];
     return check_flags(ctx);
 }
 

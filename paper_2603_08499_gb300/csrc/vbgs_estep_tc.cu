@@ -458,7 +458,8 @@ __global__ void __launch_bounds__(128) k_coef_tiles(const double *__restrict__ r
 // warp is not exponentiated.  With drop = log2 K + 25 the terms left out are
 // at most K 2^-drop = 2^-25 of a row's sum over all components (the sum is at
 // least its largest term, 1 in units of the final maximum): below FP32
-// rounding of the sum.  Its tile maxima are still taken.
+// rounding of the sum.  Its tile maxima are still taken.  pairs (nullable):
+// pairs[0] += pairs evaluated, pairs[1] += pairs whose exponential was taken.
 // ---------------------------------------------------------------------------
 template <bool BF16>
 __global__ void __launch_bounds__(kThreadsTC, 3) k_pass1_tc(const float *__restrict__ Xhl, int64_t N, int K,
@@ -518,6 +519,7 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_pass1_tc(const float *__restr
             xl[i] = Xhl[nn * 16 + 8 + i];
         }
         float mrun = seed && n < N ? seed[n].x : -INFINITY, srun = 0.f;
+        unsigned long long ecols = 0;   // columns exponentiated by this warp (with the pair counters)
         bool ok = true;
         // frame header of the next tile to build (o_hi, o_lo, 1/s), prefetched one tile ahead
         float hn[18];
@@ -608,6 +610,7 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_pass1_tc(const float *__restr
                 cm *= scale;
                 tmx = fmaxf(tmx, cm);
                 if (seed && __all_sync(0xffffffffu, cm < mrun - drop)) continue;   // negligible in every row
+                if (pairs) ecols += (unsigned long long)max(0, min(64, nvalid - c));
                 if (cm > mrun) {
                     srun *= ex2f(mrun - cm);
                     mrun = cm;
@@ -639,6 +642,9 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_pass1_tc(const float *__restr
             for (int jj = 0; jj < nt; jj++) cols += (unsigned long long)min(kCols, K - tile_at(jj) * kCols);
             atomicAdd(pairs, cols * (unsigned long long)min((int64_t)kRows, N - (int64_t)P * kRows));
         }
+        // pairs[1]: the pairs whose exponential was taken
+        const int64_t wrows = min((int64_t)32, N - ((int64_t)P * kRows + warp * 32));
+        if (pairs && lane == 0 && wrows > 0) atomicAdd(pairs + 1, ecols * (unsigned long long)wrows);
     } else if (warp == 4 && lane == 0) {
         // ---------------- copy + MMA issuer ----------------
         constexpr uint32_t idesc = idesc_f16<BF16>();

@@ -129,7 +129,7 @@ def load_library(path: Path | str = LIB_PATH) -> C.CDLL:
     lib.vbgs_check_frame.argtypes = [_DP, C.c_int, _DP, C.c_int64, _DP, C.c_double, C.POINTER(C.c_int)]
     lib.vbgs_set_wait_limit.argtypes = [C.c_longlong]
     lib.vbgs_render.argtypes = [C.c_void_p, _DP, C.c_int, C.c_int, _FP, _FP, _DP, _DP]
-    lib.vbgs_profile_replay.argtypes = [C.c_void_p, C.c_int, _DP, C.POINTER(C.c_int64)]
+    lib.vbgs_profile_replay.argtypes = [C.c_void_p, C.c_int, _DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.vbgs_set_precision_knobs.argtypes = [C.c_void_p, C.c_uint]
     lib.vbgs_get_precision_knobs.argtypes = [C.c_void_p]
     lib.vbgs_get_precision_knobs.restype = C.c_uint
@@ -325,13 +325,14 @@ def vbgs_profile_pairs(ctx) -> tuple[int, int]:
     return int(a.value), int(b.value)
 
 
-def vbgs_profile_replay(ctx, reps: int = 100) -> tuple[float, int]:
-    """(ms per launch, pairs per launch) of the last tensor-core pass-1
-    launch replayed reps times back to back."""
+def vbgs_profile_replay(ctx, reps: int = 100) -> tuple[float, int, int]:
+    """(ms per launch, pairs per launch, pairs exponentiated per launch) of
+    the last tensor-core pass-1 launch replayed reps times back to back."""
     ms = np.zeros(1)
     pairs = C.c_int64(0)
-    _check(lib().vbgs_profile_replay(ctx, int(reps), _dp(ms), C.byref(pairs)), ctx)
-    return float(ms[0]), int(pairs.value)
+    epairs = C.c_int64(0)
+    _check(lib().vbgs_profile_replay(ctx, int(reps), _dp(ms), C.byref(pairs), C.byref(epairs)), ctx)
+    return float(ms[0]), int(pairs.value), int(epairs.value)
 
 
 def vbgs_probe_peaks(device: int = 0) -> dict:
