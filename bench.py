@@ -273,13 +273,13 @@ def timed_stream(V, prior, dev_frames, form, warmup, steps, stream, flush, profi
 E2E_REPEATS = 3
 
 # DRAM traffic of one k_pass1_tc launch of the room stream (K = 50,000, FP16x3):
-# dram__bytes_read.sum + dram__bytes_write.sum of the two replayed main pass-1
-# launches of an ncu --set full capture on frames of 40,000 points (6.575 MB
-# read each, no write): the coefficient tiles of 16 KB that some tile list
-# holds, the split points and the lists, each read once.  It belongs to the
-# kernel source with this digest; once the kernel is edited the figure is
+# dram__bytes_read.sum + dram__bytes_write.sum of two replays of the last main
+# pass-1 launch of the timed frames, captured with ncu --set full (8.294 MB
+# read each, no write): the coefficient tiles that some tile list holds, the
+# split points, the lists and the seed partials, each read once.  It belongs to
+# the kernel source with this digest; once the kernel is edited the figure is
 # stale and the line reports null.
-PASS1_TRAFFIC = {"bytes": 6.575e6, "sha1": "5f029cfcf55c3a42b215fd28054819f18c8db2cd"}
+PASS1_TRAFFIC = {"bytes": 8.294e6, "sha1": "10b414d2d5f62bf26e95fb14fa5dc31f03b363a1"}
 CSRC = Path(__file__).resolve().parent / "paper_2603_08499_gb300" / "csrc"
 
 
@@ -812,7 +812,8 @@ def run_ours(args):
             "probe_peaks": peaks,
             "kernel_ms": breakdown,
             "kernel_ms_what": ("ms per frame by kernel class, from a separate run with CUDA events around every "
-                               "kernel (which serialise the launches); classes on both streams overlap"),
+                               "kernel (which serialise the launches); 'kl' runs on the second stream beside the "
+                               "next E-step"),
         }
         if cpu_val is not None:
             line["cpu_baseline"] = {"value": cpu_val, "unit": UNIT, "cores": cpu_info["cores"], "kind": "oracle",

@@ -358,10 +358,11 @@ enum {
     VBGS_PROF_MERGE = 1,   /* split merge of lse and fixed-order sums */
     VBGS_PROF_PASS2 = 2,   /* recomputed responsibilities x features (Eq. 3) */
     VBGS_PROF_REDUCE = 3,  /* FP64 cross-split statistic reduction */
-    VBGS_PROF_MSTEP = 4,   /* FP64 posterior update, KL terms, records */
+    VBGS_PROF_MSTEP = 4,   /* FP64 posterior update, records, coefficient tiles */
     VBGS_PROF_MISC = 5,    /* staging, ELBO, commit */
     VBGS_PROF_PLAN = 6,    /* tensor-core work lists: tile bounds, skip lists, work items */
-    VBGS_PROF_COUNT = 7
+    VBGS_PROF_KL = 7,      /* KL terms and their sums (second stream, beside the next E-step) */
+    VBGS_PROF_COUNT = 8
 };
 #define VBGS_PROF_ONLY(c) (1 << ((c) + 1))
 /* No paper counterpart (measurement): switch the timing described above on

@@ -1898,7 +1898,7 @@ int vbgs_profile_pairs(vbgs_ctx *ctx, int64_t *pass1_pairs, int64_t *pass2_pairs
 
 const char *vbgs_profile_name(int i)
 {
-    static const char *names[VBGS_PROF_COUNT] = {"pass1", "merge", "pass2", "reduce", "mstep", "misc", "plan"};
+    static const char *names[VBGS_PROF_COUNT] = {"pass1", "merge", "pass2", "reduce", "mstep", "misc", "plan", "kl"};
     return (i >= 0 && i < VBGS_PROF_COUNT) ? names[i] : "?";
 }
 

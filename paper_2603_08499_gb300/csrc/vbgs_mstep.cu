@@ -1024,20 +1024,20 @@ int launch_mstep(const MstepParams &P, const double *m0, const double *Spast, co
     // KL terms and their sums beside the next E-step
     if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) return -1;
     if (!dS) {
-        pf->begin(VBGS_PROF_MSTEP, side);
+        pf->begin(VBGS_PROF_KL, side);
         k_mstep_kl_prior<<<nb, 128, 0, side>>>(K, P.split != 0, kperm, cache, bpart);
         pf->end(side);
     } else {
         const int *list = reinterpret_cast<const int *>(kls + (size_t)K * kKS), *count = list + K;
-        pf->begin(VBGS_PROF_MSTEP, side);
+        pf->begin(VBGS_PROF_KL, side);
         k_mstep_kl_list<<<kKlBlocks, 128, 0, side>>>(P.split != 0, kperm, list, count, cache, kls, cache_next);
         pf->end(side);
-        pf->begin(VBGS_PROF_MSTEP, side);
+        pf->begin(VBGS_PROF_KL, side);
         launch_pdl(k_mstep_kl_sum, nb, 128, 0, side, K, kperm, (const double *)cache, (const double *)kls, bpart);
         pf->end(side);
         launches++;
     }
-    pf->begin(VBGS_PROF_MSTEP, side);
+    pf->begin(VBGS_PROF_KL, side);
     launch_pdl(k_mstep_finalize, 1, 128, 0, side, (const double *)bpart, nb, scal);
     pf->end(side);
     if (cudaEventRecord(ev_join, side) != cudaSuccess) return -1;

@@ -59,8 +59,8 @@ EXPORTS = [
 ]
 KNOBS = ["P1_PHI_LO", "P1_C_LO", "P2_PHI_LO", "P2_C_LO", "P2_P_LO", "P2_S_LO"]   # bit i: leave that lo term out
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
-PROF_COUNT = 7
-PROF_NAMES = ["pass1", "merge", "pass2", "reduce", "mstep", "misc", "plan"]
+PROF_COUNT = 8
+PROF_NAMES = ["pass1", "merge", "pass2", "reduce", "mstep", "misc", "plan", "kl"]
 
 
 class VbgsError(RuntimeError):
