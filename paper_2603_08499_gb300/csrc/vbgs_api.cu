@@ -481,7 +481,7 @@ int prop_alloc(vbgs_ctx *ctx)
         (rc = dalloc(ctx, &P.h1, (size_t)kMB * kHid)) || (rc = dalloc(ctx, &P.h2, (size_t)kMB * kHid)) ||
         (rc = dalloc(ctx, &P.dh1, (size_t)kMB * kHid)) || (rc = dalloc(ctx, &P.dh2, (size_t)kMB * kHid)) ||
         (rc = dalloc(ctx, &P.z, (size_t)kMB * kPG)) || (rc = dalloc(ctx, &P.dz, (size_t)kMB * kPG)) ||
-        (rc = dalloc(ctx, &P.loss, 2)) || (rc = dalloc(ctx, &P.counters, 8)) ||
+        (rc = dalloc(ctx, &P.loss, 2)) || (rc = dalloc(ctx, &P.counters, 16)) ||
         (rc = dalloc(ctx, &P.pstart, (size_t)kPG + 1)) || (rc = dalloc(ctx, &P.item_start, (size_t)kPG + 1)) ||
         (rc = dalloc(ctx, &P.fbase, (size_t)kPG + 1)))
         return rc;
@@ -680,29 +680,26 @@ int prop_estep(vbgs_ctx *ctx, int64_t N, bool last_iter)
     }
     prop_bounds(X, N, P.cpar, P.ub, ctx->stream);
     ctx->launches += 1;
-    CU(cudaMemsetAsync(P.counters, 0, sizeof(unsigned long long) * 8, ctx->stream));
+    CU(cudaMemsetAsync(P.counters, 0, sizeof(unsigned long long) * 16, ctx->stream));
     const uint32_t seed = (uint32_t)(P.frame * 0x9E3779B1ull) ^ 0xA5A5A5A5u ^ (uint32_t)(ctx->seed ^ (ctx->seed >> 32));
     // candidate rounds: score the pending candidates cluster-major, then
-    // merge and select the next clusters by the certificate
+    // merge and select the next clusters by the certificate.  All rounds are
+    // enqueued without a host read; a round after one that added no cluster
+    // returns at once on the device (its count, counters[8 + round], is 0).
     prop_cand_init(P.top, N, P.cand, P.ncand, P.pend, P.run, P.cpart, ctx->stream);
     ctx->launches += 1;
+    static_assert(8 + kPropRounds <= 16, "per-round counts fit the counter array");
     for (int round = 0; round < kPropRounds; round++) {
-        if (prop_pend_lists(P.cand, P.ncand, P.pend, N, ctx->sb, P.pkey, P.plist, P.pstart, ctx->stream) ||
+        const unsigned long long *prev = round ? P.counters + 8 + round - 1 : nullptr;
+        if (prop_pend_lists(P.cand, P.ncand, P.pend, N, prev, ctx->sb, P.pkey, P.plist, P.pstart, ctx->stream) ||
             prop_cand_items(P.pstart, P.cstart, false, P.item_start, P.fbase, ctx->stream))
             return fail(ctx, VBGS_ECUDA, "candidate lists failed");
-        int n_items = 0;
-        CU(cudaMemcpyAsync(&n_items, P.item_start + kPG, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
-        prop_cand_score(X, ctx->d_rec32, P.order, P.cstart, P.pstart, P.plist, P.item_start, n_items, P.cpart,
+        prop_cand_score(X, ctx->d_rec32, P.order, P.cstart, P.pstart, P.plist, P.item_start, N, prev, P.cpart,
                         ctx->stream);
-        CU(cudaMemsetAsync(P.counters + 4, 0, sizeof(unsigned long long), ctx->stream));
         prop_cand_select(P.ub, N, P.cstart, kPropThresh, round == kPropRounds - 1, seed, kAuditPerMille, P.cand,
-                         P.ncand, P.pend, P.run, P.cpart, P.lse_c, P.bound, P.exact, P.counters, ctx->stream);
+                         P.ncand, P.pend, P.run, P.cpart, P.lse_c, P.bound, P.exact, P.counters, prev,
+                         P.counters + 8 + round, ctx->stream);
         ctx->launches += 7;
-        unsigned long long added = 0;
-        CU(cudaMemcpyAsync(&added, P.counters + 4, sizeof added, cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
-        if (!added) break;
     }
     prop_cand_count(P.exact, P.ncand, P.cand, P.cstart, N, P.counters, ctx->stream);
     ctx->launches += 1;

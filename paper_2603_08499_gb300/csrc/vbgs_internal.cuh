@@ -365,13 +365,20 @@ void prop_inputs(const double *X, const int *rows, int64_t rstride, int64_t n, c
                  cudaStream_t st, int64_t nb = 1, int64_t S = 0);
 void prop_cand_init(const int *top, int64_t N, int *cand, int *ncand, int *pend, float2 *run, float2 *part,
                     cudaStream_t st);
-int prop_pend_lists(const int *cand, const int *ncand, const int *pend, int64_t N, SortBuffers &sb,
-                    unsigned int *skey, int *plist, int *pstart, cudaStream_t st);
+// One candidate round; prev_added (nullable: the first round) is the previous
+// round's count of added clusters, and a round after one that added none
+// does nothing.  The score grid is an upper bound of the round's items.
+int prop_pend_lists(const int *cand, const int *ncand, const int *pend, int64_t N,
+                    const unsigned long long *prev_added, SortBuffers &sb, unsigned int *skey, int *plist,
+                    int *pstart, cudaStream_t st);
+int64_t prop_score_items_max(int64_t N);
 void prop_cand_score(const double *X, const float *rec32, const int *order, const int *cstart, const int *pstart,
-                     const int *plist, const int *item_start, int n_items, float2 *part, cudaStream_t st);
+                     const int *plist, const int *item_start, int64_t N, const unsigned long long *prev_added,
+                     float2 *part, cudaStream_t st);
 void prop_cand_select(const float *UB, int64_t N, const int *cstart, float thresh, bool final_round, uint32_t seed,
                       uint32_t audit_per_mille, int *cand, int *ncand, int *pend, float2 *run, float2 *part,
-                      double *lse_c, float *bound, int *exact, unsigned long long *counters, cudaStream_t st);
+                      double *lse_c, float *bound, int *exact, unsigned long long *counters,
+                      const unsigned long long *prev_added, unsigned long long *added_out, cudaStream_t st);
 void prop_cand_count(const int *exact, const int *ncand, const int *cand, const int *cstart, int64_t N,
                      unsigned long long *counters, cudaStream_t st);
 void prop_gather_rows(const double *X, const int *rows, int64_t n, double *Xe, cudaStream_t st);
@@ -457,7 +464,7 @@ struct PropState {
     unsigned int *pkey = nullptr, *ekey = nullptr;
     double *lse_c = nullptr, *Xe = nullptr, *lse_e = nullptr, *lsum = nullptr;
     float *bound = nullptr, *audit = nullptr;
-    unsigned long long *counters = nullptr;   // [0] candidate pairs, [1] fallback, [2] audit, [3] added, [4] added in a round
+    unsigned long long *counters = nullptr;   // [0] candidate pairs, [1] fallback, [2] audit, [3] added, [8 + r] added in round r
     int *ncand = nullptr, *pend = nullptr;    // candidate count and first unscored slot per point
     float2 *run = nullptr, *cpart = nullptr;  // running (max, sum) per point; per-slot partials
     bool frame_exact = false;

@@ -650,7 +650,10 @@ __device__ __forceinline__ float warp_max(float v)
 // candidates' mass, it adds the clusters with the largest bounds (up to
 // kAddMax per round, no more than the bound says are needed), which the next
 // round scores.  The last round's select writes the lse, the bound and the
-// point's status (0 proposal, 1 fallback, 2 seeded audit).
+// point's status (0 proposal, 1 fallback, 2 seeded audit).  Every round is
+// enqueued without a host read: a round's kernels return at once when the
+// round before it added no cluster (prev_added, that round's count, is 0),
+// so the rounds after the first that adds nothing change no state.
 constexpr int kAddMax = 8;
 constexpr int kPB = 128;   // points per work item of the cluster-major kernels
 
@@ -672,9 +675,10 @@ __global__ void __launch_bounds__(256) k_cand_init(const int *__restrict__ top, 
 // (cluster, point * 32 + slot) keys of the pending candidate slots (at most
 // kAddMax per point: the top 4, or one round's additions).
 __global__ void k_pend_keys(const int *__restrict__ cand, const int *__restrict__ ncand,
-                            const int *__restrict__ pend, int64_t N, unsigned int *__restrict__ key,
-                            int *__restrict__ val)
+                            const int *__restrict__ pend, int64_t N, const unsigned long long *__restrict__ prev_added,
+                            unsigned int *__restrict__ key, int *__restrict__ val)
 {
+    if (prev_added && *prev_added == 0ull) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * kAddMax) return;
     const int64_t n = i / kAddMax;
@@ -688,11 +692,15 @@ constexpr int kSM = 256;   // member records staged per pass of k_cand_score
 __global__ void __launch_bounds__(kPB) k_cand_score(const double *__restrict__ X, const float *__restrict__ rec32,
                                                     const int *__restrict__ order, const int *__restrict__ cstart,
                                                     const int *__restrict__ pstart, const int *__restrict__ plist,
-                                                    const int *__restrict__ item_start, float2 *__restrict__ part)
+                                                    const int *__restrict__ item_start,
+                                                    const unsigned long long *__restrict__ prev_added,
+                                                    float2 *__restrict__ part)
 {
     __shared__ __align__(16) float sr[kSM * 28];
     __shared__ int sg;
     const int item = blockIdx.x;
+    // the grid is an upper bound of the item count (item_start[kG])
+    if ((prev_added && *prev_added == 0ull) || item >= item_start[kG]) return;
     if (threadIdx.x == 0) {
         int lo = 0, hi = kG;   // largest g with item_start[g] <= item
         while (hi - lo > 1) {
@@ -738,8 +746,11 @@ __global__ void __launch_bounds__(256) k_cand_select(const float *__restrict__ U
                                                      int *__restrict__ pend, float2 *__restrict__ run,
                                                      float2 *__restrict__ part, double *__restrict__ lse_c,
                                                      float *__restrict__ bound, int *__restrict__ exact,
-                                                     unsigned long long *__restrict__ counters)
+                                                     unsigned long long *__restrict__ counters,
+                                                     const unsigned long long *__restrict__ prev_added,
+                                                     unsigned long long *__restrict__ added_out)
 {
+    if (prev_added && *prev_added == 0ull) return;
     const int lane = threadIdx.x & 31;
     const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (n >= N) return;
@@ -808,7 +819,7 @@ __global__ void __launch_bounds__(256) k_cand_select(const float *__restrict__ U
         ncand[n] = nc;
         bound[n] = mm;
         lse_c[n] = (double)l2 * 0.6931471805599453;   // natural units
-        if (added) atomicAdd(&counters[4], (unsigned long long)added);
+        if (added) atomicAdd(added_out, (unsigned long long)added);
         atomicAdd(&counters[0], new_pairs);
         if (!added) {
             // seeded audit sample: a hash of (seed, point index)
@@ -1260,11 +1271,13 @@ void prop_cand_init(const int *top, int64_t N, int *cand, int *ncand, int *pend,
     if (N > 0) k_cand_init<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(top, N, cand, ncand, pend, run, part);
 }
 
-int prop_pend_lists(const int *cand, const int *ncand, const int *pend, int64_t N, SortBuffers &sb,
-                    unsigned int *skey, int *plist, int *pstart, cudaStream_t st)
+int prop_pend_lists(const int *cand, const int *ncand, const int *pend, int64_t N,
+                    const unsigned long long *prev_added, SortBuffers &sb, unsigned int *skey, int *plist,
+                    int *pstart, cudaStream_t st)
 {
     const int64_t n = N * kAddMax;
-    k_pend_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, ncand, pend, N, sb.keys_in, sb.idx_in);
+    k_pend_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, ncand, pend, N, prev_added, sb.keys_in,
+                                                            sb.idx_in);
     size_t bytes = sb.temp_bytes;
     if (cub::DeviceRadixSort::SortPairs(sb.temp, bytes, sb.keys_in, skey, sb.idx_in, plist, (int)n, 0, 11, st) !=
         cudaSuccess)
@@ -1273,21 +1286,27 @@ int prop_pend_lists(const int *cand, const int *ncand, const int *pend, int64_t 
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+int64_t prop_score_items_max(int64_t N) { return (N * kAddMax + kPB - 1) / kPB + kG + 1; }
+
 void prop_cand_score(const double *X, const float *rec32, const int *order, const int *cstart, const int *pstart,
-                     const int *plist, const int *item_start, int n_items, float2 *part, cudaStream_t st)
+                     const int *plist, const int *item_start, int64_t N, const unsigned long long *prev_added,
+                     float2 *part, cudaStream_t st)
 {
-    if (n_items > 0)
-        k_cand_score<<<(unsigned)n_items, kPB, 0, st>>>(X, rec32, order, cstart, pstart, plist, item_start, part);
+    if (N > 0)
+        k_cand_score<<<(unsigned)prop_score_items_max(N), kPB, 0, st>>>(X, rec32, order, cstart, pstart, plist,
+                                                                        item_start, prev_added, part);
 }
 
 void prop_cand_select(const float *UB, int64_t N, const int *cstart, float thresh, bool final_round, uint32_t seed,
                       uint32_t audit_per_mille, int *cand, int *ncand, int *pend, float2 *run, float2 *part,
-                      double *lse_c, float *bound, int *exact, unsigned long long *counters, cudaStream_t st)
+                      double *lse_c, float *bound, int *exact, unsigned long long *counters,
+                      const unsigned long long *prev_added, unsigned long long *added_out, cudaStream_t st)
 {
     if (N > 0)
         k_cand_select<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(UB, N, cstart, thresh, final_round ? 1 : 0,
                                                                           seed, audit_per_mille, cand, ncand, pend,
-                                                                          run, part, lse_c, bound, exact, counters);
+                                                                          run, part, lse_c, bound, exact, counters,
+                                                                          prev_added, added_out);
 }
 
 void prop_cand_count(const int *exact, const int *ncand, const int *cand, const int *cstart, int64_t N,
