@@ -756,6 +756,10 @@ __global__ void __launch_bounds__(256) k_cand_select(const float *__restrict__ U
     if (n >= N) return;
     int nc = ncand[n];
     const int p = pend[n];
+    // a point whose last select added nothing (pend == ncand; never in the
+    // first round, which starts from the top 4) has nothing to merge and would
+    // write back the bound, lse and status it holds: it is done
+    if (p == nc) return;
     // candidate membership: lane l holds clusters 32 j + l
     const int my = lane < nc ? cand[n * kMaxCand + lane] : -1;
     uint32_t mine = 0u;
