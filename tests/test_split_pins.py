@@ -56,6 +56,33 @@ def test_k1_converged_elbo_is_the_exact_evidence_of_both_blocks():
     assert abs(e_joint[1] - ev) > 1e-3 * abs(ev)
 
 
+def test_k1_stream_carries_s_past_and_equals_the_batch_of_both_frames():
+    """K = 1: every responsibility is 1, so a frame adds sum_n phi(x_n) (Eq. 3,
+    phi = [1, x, upper(x x^T)] row-major) to S_past; two frames streamed
+    through cavi_frame, the second from the first's S_past, give each block
+    the conjugate posterior of both frames together (closed form)."""
+    rng = np.random.default_rng(24)
+    prior = _prior(1, rng)
+    X1 = rng.standard_normal((20, 6)) * 0.5 + 0.2
+    X2 = rng.standard_normal((25, 6)) * 0.7 - 0.1
+    iu = np.triu_indices(6)
+
+    def phi_sum(X):
+        return np.concatenate([[X.shape[0]], X.sum(axis=0), (X.T @ X)[iu]])
+
+    _, S1, _, _ = SP.cavi_frame(X1, prior, np.zeros((1, 28)), 2)
+    _, S2, _, dS2 = SP.cavi_frame(X2, prior, S1, 2)
+    assert np.allclose(dS2[0], phi_sum(X2), rtol=1e-12, atol=1e-9)
+    assert np.allclose(S2[0], phi_sum(X1) + phi_sum(X2), rtol=1e-12, atol=1e-9)
+    X = np.concatenate([X1, X2])
+    q_s, q_c = SP.mstep(prior, S2)
+    for q, sl in ((q_s, slice(0, 3)), (q_c, slice(3, 6))):
+        ref = CF.nw_posterior_centred(X[:, sl], prior["m0"][0, sl], prior["beta0"], prior["W0"][sl, sl],
+                                      prior["nu0"])
+        assert np.allclose(q["m"][0], ref["m"], rtol=1e-12, atol=1e-12)
+        assert np.allclose(q["Winv"][0], ref["Winv"], rtol=1e-10, atol=1e-10)
+
+
 def _sample_nw(q, k, M, rng):
     """M draws of (mu, Lambda) from NW(m, beta, W, nu) of component k."""
     W = np.linalg.inv(q["Winv"][k])
